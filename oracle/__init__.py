@@ -1,0 +1,11 @@
+"""CPU oracle for the Hough-transform track-finding path (test infrastructure).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.
+"""
+from . import oracle
+from .oracle import (build, tables, vote, peaks, associate, vote_z, atan2,
+                     run_event)
+
+__all__ = ["oracle", "build", "tables", "vote", "peaks", "associate", "vote_z",
+           "atan2", "run_event"]

@@ -1,0 +1,344 @@
+/*
+ * ht_oracle.c -- plain, slow CPU oracle for Hough-transform track finding.
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load this library.  The product (the CUDA
+ * library and its binding) never calls it and shares no code with it.
+ *
+ * Method: Halyo, LeGresley, Lujan, "Massively Parallel Computing and the
+ * Search for Jets and Black Holes at the LHC", arXiv:1309.6275.
+ *   Section 5   the Hough transform: every instance of a parametrised feature
+ *               starts at zero votes; each input adds one vote to every
+ *               instance that would contain it; local maxima of the vote
+ *               space are the candidate features, which costlier steps then
+ *               confirm.
+ *   Section 6   (Fig. 5) hits -> transform -> peak finding -> refinement.
+ *   Section 7   the peak finder is tuned for tracks of 7 or more hits.
+ * The paper gives no formulas, bin layout or tie rules.  The readings used
+ * here (each marked "reading") are stated where they are applied.
+ *
+ * Arithmetic: IEEE binary64, round to nearest.  Compile with -O2
+ * -ffp-contract=off and without fast-math, so that every + - * / sqrt below is
+ * one correctly rounded operation in the order written.
+ *
+ * Parametrisation (reading; the paper says only that the transform measures
+ * the transverse momentum of prompt or displaced tracks):
+ *   signed curvature rho (> 0 counter-clockwise), transverse impact
+ *   parameter d0 and azimuth phi0 at the perigee.  A circle with these
+ *   parameters passes through hit (x, y) iff
+ *     F(d0) = rho d0^2 + 2 (1 + rho s) d0 + (rho r^2 + 2 s) = 0,
+ *   s = x sin phi0 - y cos phi0,  c = x cos phi0 + y sin phi0,  r^2 = x^2 + y^2,
+ *   with discriminant / 4   D = 1 - (rho c)^2.
+ *   rho and phi0 are sampled at bin centres; d0 is solved and binned.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef struct {
+    int32_t n_rho, n_d0, n_phi0;
+    int32_t n_z0, n_cot;
+    int32_t threshold;
+    int64_t count_max;  /* saturation value of a cell: 65535 (uint16) or 2^31-1 */
+    double rho_max, d0_half, z0_max, cot_max;
+} or_geom;
+
+static const double OR_PI = 3.141592653589793;        /* nearest double to pi */
+static const double OR_HALF_PI = 1.5707963267948966;  /* OR_PI / 2, exact */
+
+/* Axis tables (reading): phi0_k = (2k + 1 - N) pi / N covers [-pi, pi);
+ * rho_i = (2i + 1 - N) rho_max / N covers [-rho_max, rho_max). */
+void or_tables(const or_geom *g, double *phi0, double *sn, double *cs, double *rho)
+{
+    for (int32_t k = 0; k < g->n_phi0; ++k) {
+        double p = (double)(2 * k + 1 - g->n_phi0) * (OR_PI / (double)g->n_phi0);
+        phi0[k] = p;
+        sn[k] = sin(p);
+        cs[k] = cos(p);
+    }
+    for (int32_t i = 0; i < g->n_rho; ++i)
+        rho[i] = (double)(2 * i + 1 - g->n_rho) * (g->rho_max / (double)g->n_rho);
+}
+
+/* d0 binning (reading): width delta = 2 d0_half / n_d0, bin coordinate
+ * u = d0 / delta + (n_d0 / 2 + 0.5), bin j = floor(u), valid iff 0 <= u < n_d0.
+ * So d0 = 0 is the centre of bin n_d0 / 2 (prompt tracks do not straddle an
+ * edge) and the axis covers [-d0_half - delta/2, d0_half - delta/2). */
+static double d0_delta(const or_geom *g) { return 2.0 * g->d0_half / (double)g->n_d0; }
+static double d0_offset(const or_geom *g) { return (double)g->n_d0 * 0.5 + 0.5; }
+
+/* The d0 bins voted by one hit in one (rho_i, phi0_k) column.
+ * Forward condition (reading): only c > 0 votes -- the hit lies on the first
+ * half turn.  Without it every circle would also appear as its mirror
+ * (-rho, -d0, phi0 + pi) and every track would give two peaks.
+ * Both real roots of F vote (both can be physical: the second is a hit past a
+ * quarter turn).  A double root (D == 0) votes once.
+ * Stable roots: q = -(b + sgn(b) sqrt(D)), b = 1 + rho s, sgn(0) = +1;
+ * roots q / rho (rho != 0) and (rho r^2 + 2 s) / q (q != 0).
+ * Returns the number of in-range roots written to j[]; *n_edge counts those
+ * whose bin coordinate lies within 1e-5 of an integer. */
+static int cell_bins(const or_geom *g, float xf, float yf, double sn, double cs,
+                     double rho, int32_t j[2], int64_t *n_edge)
+{
+    const double delta = d0_delta(g), off = d0_offset(g);
+    const double x = (double)xf, y = (double)yf;
+    const double s = x * sn - y * cs;
+    const double c = x * cs + y * sn;
+    if (!(c > 0.0))
+        return 0;
+    const double r2 = x * x + y * y;
+    const double b = 1.0 + rho * s;
+    const double pc = rho * c;
+    const double D = 1.0 - pc * pc;
+    if (D < 0.0)
+        return 0;
+    const double sq = sqrt(D);
+    const double q = -(b + (b >= 0.0 ? sq : -sq));
+    const double C = rho * r2 + 2.0 * s;
+    double root[2];
+    int nr = 0;
+    if (rho != 0.0)
+        root[nr++] = q / rho;
+    if (q != 0.0 && !(D == 0.0 && rho != 0.0))
+        root[nr++] = C / q;
+    int nv = 0;
+    for (int t = 0; t < nr; ++t) {
+        const double u = root[t] / delta + off;
+        if (u >= 0.0 && u < (double)g->n_d0) {
+            const double fl = floor(u);
+            const double fr = u - fl;
+            j[nv++] = (int32_t)fl;
+            if (fr < 1e-5 || fr > 1.0 - 1e-5)
+                ++*n_edge;
+        }
+    }
+    return nv;
+}
+
+/* Section 5 vote.  acc[(i n_d0 + j) n_phi0 + k] for rows i in [i_begin, i_end)
+ * (the caller zeroes acc; rows outside the range are not touched, so callers
+ * may split rows across threads).  Each vote adds one, saturating at
+ * count_max (reading).  stats[0] += votes cast, stats[1] += edge votes. */
+void or_vote(const or_geom *g, const float *x, const float *y, int64_t n,
+             int32_t i_begin, int32_t i_end, int64_t *acc, int64_t *stats)
+{
+    double *phi0 = malloc(sizeof(double) * g->n_phi0);
+    double *sn = malloc(sizeof(double) * g->n_phi0);
+    double *cs = malloc(sizeof(double) * g->n_phi0);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    or_tables(g, phi0, sn, cs, rho);
+    int64_t votes = 0, edge = 0;
+    for (int64_t h = 0; h < n; ++h)
+        for (int32_t i = i_begin; i < i_end; ++i)
+            for (int32_t k = 0; k < g->n_phi0; ++k) {
+                int32_t j[2];
+                const int nv = cell_bins(g, x[h], y[h], sn[k], cs[k], rho[i], j, &edge);
+                for (int t = 0; t < nv; ++t) {
+                    int64_t *cell = &acc[((int64_t)i * g->n_d0 + j[t]) * g->n_phi0 + k];
+                    if (*cell < g->count_max)
+                        ++*cell;
+                    ++votes;
+                }
+            }
+    stats[0] += votes;
+    stats[1] += edge;
+    free(phi0); free(sn); free(cs); free(rho);
+}
+
+/* Peak finding (Sections 5 and 6: local maxima of the vote space; Section 7:
+ * tuned for 7 or more hits per track).  Reading: cell l = (i n_d0 + j) n_phi0 + k
+ * is a peak iff acc[l] >= threshold and, for every existing one of its 26
+ * neighbours l' (rho and d0 do not wrap, phi0 wraps modulo n_phi0),
+ * acc[l] > acc[l'] when l' < l and acc[l] >= acc[l'] when l' > l -- so of a
+ * plateau only the cell of smallest index can be a peak.
+ * Rows i in [i_begin, i_end) are scanned in increasing l.  The first `cap`
+ * peaks are written as {i, j, k, count}; the number found is returned. */
+int64_t or_peaks(const or_geom *g, const int64_t *acc, int32_t i_begin, int32_t i_end,
+                 int32_t *out, int64_t cap)
+{
+    const int32_t NR = g->n_rho, ND = g->n_d0, NP = g->n_phi0;
+    int64_t cnt = 0;
+    for (int32_t i = i_begin; i < i_end; ++i)
+        for (int32_t j = 0; j < ND; ++j)
+            for (int32_t k = 0; k < NP; ++k) {
+                const int64_t l = ((int64_t)i * ND + j) * NP + k;
+                const int64_t v = acc[l];
+                if (v < g->threshold)
+                    continue;
+                int peak = 1;
+                for (int di = -1; di <= 1 && peak; ++di)
+                    for (int dj = -1; dj <= 1 && peak; ++dj)
+                        for (int dk = -1; dk <= 1 && peak; ++dk) {
+                            if (di == 0 && dj == 0 && dk == 0)
+                                continue;
+                            const int32_t ii = i + di, jj = j + dj;
+                            if (ii < 0 || ii >= NR || jj < 0 || jj >= ND)
+                                continue;
+                            const int32_t kk = (k + dk + NP) % NP;
+                            const int64_t l2 = ((int64_t)ii * ND + jj) * NP + kk;
+                            const int64_t v2 = acc[l2];
+                            if (l2 < l ? !(v > v2) : !(v >= v2))
+                                peak = 0;
+                        }
+                if (!peak)
+                    continue;
+                if (cnt < cap) {
+                    out[4 * cnt + 0] = i;
+                    out[4 * cnt + 1] = j;
+                    out[4 * cnt + 2] = k;
+                    out[4 * cnt + 3] = (int32_t)v;
+                }
+                ++cnt;
+            }
+    return cnt;
+}
+
+/* Candidate confirmation (Section 5: "more expensive computations" confirm a
+ * candidate).  Reading: hit h is compatible with candidate m = (i_m, j_m, k_m)
+ * iff one of its votes lies in a cell with |i - i_m| <= 1, |j - j_m| <= 1 and
+ * circular |k - k_m| <= 1.  The hit goes to the compatible candidate of
+ * largest count, ties to the smallest m; -1 if none.
+ * Hits hit_idx[0..n_sel) are processed (all n hits when hit_idx is NULL). */
+void or_associate(const or_geom *g, const float *x, const float *y,
+                  const int64_t *hit_idx, int64_t n_sel,
+                  const int32_t *peaks, int64_t npk, int32_t *assign)
+{
+    double *phi0 = malloc(sizeof(double) * g->n_phi0);
+    double *sn = malloc(sizeof(double) * g->n_phi0);
+    double *cs = malloc(sizeof(double) * g->n_phi0);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    or_tables(g, phi0, sn, cs, rho);
+    int64_t edge = 0;
+    for (int64_t t = 0; t < n_sel; ++t) {
+        const int64_t h = hit_idx ? hit_idx[t] : t;
+        int32_t best = -1, best_count = -1;
+        for (int64_t m = 0; m < npk; ++m) {
+            const int32_t im = peaks[4 * m], jm = peaks[4 * m + 1], km = peaks[4 * m + 2];
+            const int32_t cm = peaks[4 * m + 3];
+            int compat = 0;
+            for (int a = -1; a <= 1 && !compat; ++a) {
+                const int32_t ii = im + a;
+                if (ii < 0 || ii >= g->n_rho)
+                    continue;
+                for (int dk = -1; dk <= 1 && !compat; ++dk) {
+                    const int32_t kk = (km + dk + g->n_phi0) % g->n_phi0;
+                    int32_t j[2];
+                    const int nv = cell_bins(g, x[h], y[h], sn[kk], cs[kk], rho[ii], j, &edge);
+                    for (int v = 0; v < nv; ++v)
+                        if (abs(j[v] - jm) <= 1)
+                            compat = 1;
+                }
+            }
+            if (compat && cm > best_count) {
+                best = (int32_t)m;
+                best_count = cm;
+            }
+        }
+        assign[t] = best;
+    }
+    free(phi0); free(sn); free(cs); free(rho);
+}
+
+/* atan2 from basic operations only, so that a second implementation that
+ * follows the same steps reproduces it bit for bit.  Method: reduce to
+ * t = min(|y|, |x|) / max(|y|, |x|) in [0, 1]; apply the half-angle identity
+ * atan(t) = 2 atan(t / (1 + sqrt(1 + t^2))) three times (|t| <= tan(pi/32));
+ * sum the Maclaurin series atan(t) = sum_n (-1)^n t^(2n+1) / (2n+1) to n = 10
+ * by Horner's rule; undo the reductions.  Error: a few ulp.
+ * Returns 0 for (0, 0); atan2(-0.0, x < 0) returns +pi (sign of zero ignored). */
+static double atan_unit(double t)
+{
+    for (int h = 0; h < 3; ++h)
+        t = t / (1.0 + sqrt(1.0 + t * t));
+    const double t2 = t * t;
+    double p = 1.0 / 21.0;
+    for (int k = 9; k >= 0; --k)
+        p = 1.0 / (double)(2 * k + 1) - t2 * p;
+    return 8.0 * (t * p);
+}
+
+double or_atan2(double y, double x)
+{
+    if (x == 0.0 && y == 0.0)
+        return 0.0;
+    const double ax = fabs(x), ay = fabs(y);
+    double a;
+    if (ay <= ax)
+        a = atan_unit(ay / ax);
+    else
+        a = OR_HALF_PI - atan_unit(ax / ay);
+    if (x < 0.0)
+        a = OR_PI - a;
+    return y < 0.0 ? -a : a;
+}
+
+void or_atan2_array(const double *y, const double *x, int64_t n, double *out)
+{
+    for (int64_t t = 0; t < n; ++t)
+        out[t] = or_atan2(y[t], x[t]);
+}
+
+/* Second vote in (z0, cot theta) per candidate (reading; the paper is
+ * transverse-plane only).  For candidate m at cell centres
+ * (rho_i, d0_j = (j - n_d0/2) delta, phi0_k) and each hit assigned to it:
+ * turning angle theta = atan2(rho c, 1 + rho (s + d0_j)), arc length
+ * L = theta / rho (L = c when rho == 0); for each cot-theta centre
+ * t_q = (2q + 1 - n_cot) cot_max / n_cot: z0 = z - L t_q, bin
+ * u = (z0 + z0_max) / dz with dz = 2 z0_max / n_z0, n = floor(u), valid iff
+ * 0 <= u < n_z0.  Output per candidate: argmax {n, q, count} over the
+ * n_z0 x n_cot histogram, ties to the smallest n n_cot + q; {-1, -1, 0} when
+ * no vote was cast.
+ * Candidates cand[0..n_cand) are processed; out has 3 int32 per listed one. */
+void or_vote_z(const or_geom *g, const float *x, const float *y, const float *z,
+               int64_t n, const int32_t *assign, const int32_t *peaks,
+               const int64_t *cand, int64_t n_cand, int32_t *out)
+{
+    double *phi0 = malloc(sizeof(double) * g->n_phi0);
+    double *sn = malloc(sizeof(double) * g->n_phi0);
+    double *cs = malloc(sizeof(double) * g->n_phi0);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    or_tables(g, phi0, sn, cs, rho);
+    const int32_t NZ = g->n_z0, NC = g->n_cot;
+    const double delta = d0_delta(g);
+    const double dz = 2.0 * g->z0_max / (double)NZ;
+    const double cstep = g->cot_max / (double)NC;
+    int64_t *hist = malloc(sizeof(int64_t) * (size_t)NZ * NC);
+    for (int64_t t = 0; t < n_cand; ++t) {
+        const int64_t m = cand[t];
+        const int32_t im = peaks[4 * m], jm = peaks[4 * m + 1], km = peaks[4 * m + 2];
+        memset(hist, 0, sizeof(int64_t) * (size_t)NZ * NC);
+        const double r = rho[im];
+        const double d0c = ((double)jm - 0.5 * (double)g->n_d0) * delta;
+        for (int64_t h = 0; h < n; ++h) {
+            if (assign[h] != m)
+                continue;
+            const double xd = x[h], yd = y[h], zd = z[h];
+            const double s = xd * sn[km] - yd * cs[km];
+            const double c = xd * cs[km] + yd * sn[km];
+            double L;
+            if (r == 0.0)
+                L = c;
+            else
+                L = or_atan2(r * c, 1.0 + r * (s + d0c)) / r;
+            for (int32_t q = 0; q < NC; ++q) {
+                const double tq = (double)(2 * q + 1 - NC) * cstep;
+                const double z0 = zd - L * tq;
+                const double u = (z0 + g->z0_max) / dz;
+                if (u >= 0.0 && u < (double)NZ)
+                    ++hist[(int64_t)floor(u) * NC + q];
+            }
+        }
+        int64_t best = -1, bc = 0;
+        for (int64_t b = 0; b < (int64_t)NZ * NC; ++b)
+            if (hist[b] > bc) {
+                bc = hist[b];
+                best = b;
+            }
+        out[3 * t + 0] = best < 0 ? -1 : (int32_t)(best / NC);
+        out[3 * t + 1] = best < 0 ? -1 : (int32_t)(best % NC);
+        out[3 * t + 2] = (int32_t)bc;
+    }
+    free(hist);
+    free(phi0); free(sn); free(cs); free(rho);
+}

@@ -1,0 +1,213 @@
+"""Python front end of the CPU oracle (ht_oracle.c).
+
+TEST INFRASTRUCTURE.  Only the test suite, ``__graft_entry__.smoke()`` and the
+benchmark's CPU-baseline leg import this module.  It shares no code with the
+CUDA path and never imports it.
+
+Every function here marshals numpy arrays into the C oracle.  Work is split
+across threads only along axes whose results are independent (rows of the
+accumulator, hits, candidates); ctypes releases the GIL during each call, and
+no arithmetic is reordered.
+"""
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "ht_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "libht_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# gcc flags: every floating-point operation stays a single IEEE op (no FMA
+# contraction, no fast-math); portable across x86_64 and aarch64.
+CFLAGS = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fPIC", "-shared", "-std=c11"]
+
+
+def build(force=False):
+    """Compile the oracle library in-tree (oracle/_build/libht_oracle.so)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB_PATH)
+            and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC)):
+        return _LIB_PATH
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *CFLAGS, "-o", tmp, _SRC, "-lm"])
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+class OrGeom(ctypes.Structure):
+    _fields_ = [("n_rho", ctypes.c_int32), ("n_d0", ctypes.c_int32),
+                ("n_phi0", ctypes.c_int32), ("n_z0", ctypes.c_int32),
+                ("n_cot", ctypes.c_int32), ("threshold", ctypes.c_int32),
+                ("count_max", ctypes.c_int64), ("rho_max", ctypes.c_double),
+                ("d0_half", ctypes.c_double), ("z0_max", ctypes.c_double),
+                ("cot_max", ctypes.c_double)]
+
+
+def _geom(g):
+    cm = 65535 if g.get("count_bits", 32) == 16 else 2147483647
+    return OrGeom(g["n_rho"], g["n_d0"], g["n_phi0"], g["n_z0"], g["n_cot"],
+                  g["threshold"], cm, g["rho_max"], g["d0_half"], g["z0_max"],
+                  g["cot_max"])
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build()
+            L = ctypes.CDLL(path)
+            P = ctypes.POINTER
+            G = P(OrGeom)
+            vp = ctypes.c_void_p
+            i64, i32 = ctypes.c_int64, ctypes.c_int32
+            L.or_tables.argtypes = [G, vp, vp, vp, vp]
+            L.or_vote.argtypes = [G, vp, vp, i64, i32, i32, vp, vp]
+            L.or_peaks.argtypes = [G, vp, i32, i32, vp, i64]
+            L.or_peaks.restype = i64
+            L.or_associate.argtypes = [G, vp, vp, vp, i64, vp, i64, vp]
+            L.or_atan2.argtypes = [ctypes.c_double, ctypes.c_double]
+            L.or_atan2.restype = ctypes.c_double
+            L.or_atan2_array.argtypes = [vp, vp, i64, vp]
+            L.or_vote_z.argtypes = [G, vp, vp, vp, i64, vp, vp, vp, i64, vp]
+            _lib = L
+        return _lib
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _threads(threads):
+    return max(1, threads if threads else (os.cpu_count() or 1))
+
+
+def _chunks(n, parts):
+    parts = max(1, min(parts, n)) if n > 0 else 1
+    edges = np.linspace(0, n, parts + 1).astype(np.int64)
+    return [(int(a), int(b)) for a, b in zip(edges[:-1], edges[1:]) if b > a]
+
+
+def tables(g):
+    """(phi0, sin phi0, cos phi0, rho) float64 axis tables."""
+    G = _geom(g)
+    phi0 = np.empty(g["n_phi0"]); sn = np.empty_like(phi0); cs = np.empty_like(phi0)
+    rho = np.empty(g["n_rho"])
+    lib().or_tables(ctypes.byref(G), _p(phi0), _p(sn), _p(cs), _p(rho))
+    return phi0, sn, cs, rho
+
+
+def vote(g, x, y, threads=None):
+    """Accumulator int64 [n_rho, n_d0, n_phi0] and stats {votes, edge}."""
+    G = _geom(g)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    acc = np.zeros((g["n_rho"], g["n_d0"], g["n_phi0"]), np.int64)
+    rows = _chunks(g["n_rho"], _threads(threads) * 2)
+    stats = np.zeros((len(rows), 2), np.int64)
+
+    def run(t):
+        a, b = rows[t]
+        lib().or_vote(ctypes.byref(G), _p(x), _p(y), x.shape[0], a, b, _p(acc),
+                      _p(stats[t]))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, range(len(rows))))
+    tot = stats.sum(0)
+    return acc, {"votes": int(tot[0]), "edge": int(tot[1])}
+
+
+def peaks(g, acc, cap=None, threads=None):
+    """Peaks sorted by logical index: (int32 [min(count, cap), 4], count)."""
+    G = _geom(g)
+    acc = np.ascontiguousarray(acc, np.int64)
+    rows = _chunks(g["n_rho"], _threads(threads) * 2)
+    outs = [None] * len(rows)
+
+    def run(t):
+        a, b = rows[t]
+        n = lib().or_peaks(ctypes.byref(G), _p(acc), a, b, None, 0)
+        buf = np.zeros((max(n, 1), 4), np.int32)
+        lib().or_peaks(ctypes.byref(G), _p(acc), a, b, _p(buf), n)
+        outs[t] = buf[:n]
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, range(len(rows))))
+    allp = np.concatenate(outs) if outs else np.zeros((0, 4), np.int32)
+    count = allp.shape[0]
+    if cap is not None:
+        allp = allp[:cap]
+    return np.ascontiguousarray(allp), count
+
+
+def associate(g, x, y, pk, hit_idx=None, threads=None):
+    """Assignment int32 per selected hit (all hits if hit_idx is None)."""
+    G = _geom(g)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    pk = np.ascontiguousarray(pk, np.int32).reshape(-1, 4)
+    if hit_idx is None:
+        hit_idx = np.arange(x.shape[0], dtype=np.int64)
+    hit_idx = np.ascontiguousarray(hit_idx, np.int64)
+    out = np.full(hit_idx.shape[0], -1, np.int32)
+    parts = _chunks(hit_idx.shape[0], _threads(threads) * 4)
+
+    def run(ab):
+        a, b = ab
+        sub = hit_idx[a:b].copy()
+        o = np.empty(b - a, np.int32)
+        lib().or_associate(ctypes.byref(G), _p(x), _p(y), _p(sub), b - a, _p(pk),
+                           pk.shape[0], _p(o))
+        out[a:b] = o
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, parts))
+    return out
+
+
+def vote_z(g, x, y, z, assign, pk, cand=None, threads=None):
+    """Per-candidate (z0, cot theta) argmax: int32 [n_cand, 3] = {n, q, count}."""
+    G = _geom(g)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    z = np.ascontiguousarray(z, np.float32)
+    assign = np.ascontiguousarray(assign, np.int32)
+    pk = np.ascontiguousarray(pk, np.int32).reshape(-1, 4)
+    if cand is None:
+        cand = np.arange(pk.shape[0], dtype=np.int64)
+    cand = np.ascontiguousarray(cand, np.int64)
+    out = np.zeros((cand.shape[0], 3), np.int32)
+    parts = _chunks(cand.shape[0], _threads(threads) * 4)
+
+    def run(ab):
+        a, b = ab
+        sub = cand[a:b].copy()
+        o = np.zeros((b - a, 3), np.int32)
+        lib().or_vote_z(ctypes.byref(G), _p(x), _p(y), _p(z), x.shape[0], _p(assign),
+                        _p(pk), _p(sub), b - a, _p(o))
+        out[a:b] = o
+
+    if cand.shape[0]:
+        with ThreadPoolExecutor(_threads(threads)) as ex:
+            list(ex.map(run, parts))
+    return out
+
+
+def atan2(y, x):
+    """The oracle's basic-operation atan2, elementwise over float64 arrays."""
+    y = np.ascontiguousarray(y, np.float64); x = np.ascontiguousarray(x, np.float64)
+    out = np.empty_like(y)
+    lib().or_atan2_array(_p(y), _p(x), y.shape[0], _p(out))
+    return out
+
+
+def run_event(g, x, y, z, cap=None, threads=None):
+    """The whole path on one event: acc, stats, peaks, count, assign, zres."""
+    acc, st = vote(g, x, y, threads)
+    pk, cnt = peaks(g, acc, cap, threads)
+    asg = associate(g, x, y, pk, threads=threads)
+    zr = vote_z(g, x, y, z, asg, pk, threads=threads)
+    return dict(acc=acc, stats=st, peaks=pk, count=cnt, assign=asg, zres=zr)
