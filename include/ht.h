@@ -1,0 +1,190 @@
+/*
+ * ht.h -- C ABI of the GB300 Hough-transform track-finding library (libht).
+ *
+ * Method: Halyo, LeGresley, Lujan, "Massively Parallel Computing and the
+ * Search for Jets and Black Holes at the LHC", arXiv:1309.6275.  Section 5
+ * defines the transform (each input adds a vote to every parametrised
+ * feature that contains it; local maxima of the vote space are candidates;
+ * costlier computations then confirm them); Section 6 (Fig. 5) chains
+ * transform -> peak finding -> refinement; Section 7 tunes the peak finder
+ * for tracks of 7 or more hits.  The paper gives no formulas or bin layout;
+ * the readings used here are stated beside each call.
+ *
+ * Conventions shared by every call
+ *  - Units: cm.  Hits are float32 structure-of-arrays (x[], y[], z[]).
+ *  - Parameter space: signed curvature rho (> 0 counter-clockwise),
+ *    transverse impact parameter d0, azimuth phi0 at the perigee.  A hit
+ *    (x, y) lies on the circle (rho, d0, phi0) iff
+ *      rho d0^2 + 2 (1 + rho s) d0 + (rho r^2 + 2 s) = 0,
+ *      s = x sin phi0 - y cos phi0,  c = x cos phi0 + y sin phi0.
+ *  - Axes: rho_i = (2i + 1 - n_rho) rho_max / n_rho,
+ *    phi0_k = (2k + 1 - n_phi0) pi / n_phi0 (phi0 wraps),
+ *    d0 bin j holds u = d0 / delta + n_d0 / 2 + 1/2 in [j, j + 1),
+ *    delta = 2 d0_half / n_d0 (d0 = 0 is a bin centre).
+ *  - Accumulator: n_rho x n_d0 x n_phi0 cells of uint16 (count_bits 16) or
+ *    int32 (count_bits 32), logical index l = (i n_d0 + j) n_phi0 + k,
+ *    counts saturate at the type maximum.
+ *  - Every pointer argument is DEVICE memory owned by the caller unless
+ *    marked "host".  Calls are asynchronous on `stream` (NULL = the legacy
+ *    default stream), never synchronise the host and keep every count in
+ *    device memory, except ht_run_event which is synchronous.
+ *  - Every call returns an ht_status; no C++ exception crosses the ABI.  On
+ *    failure ht_last_error() returns a description (per host thread).
+ *  - Results are bit-identical to the plain fp64 CPU definition of each
+ *    step: float32 arithmetic decides only votes it can prove are at least
+ *    its error bound away from every decision edge; the others are redone
+ *    in float64 with the definition's operation order.
+ */
+#ifndef HT_H
+#define HT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;                       /* = cudaStream_t */
+typedef struct CUstream_st *ht_stream;
+
+typedef int32_t ht_status;
+#define HT_OK 0
+#define HT_ERR_ARG 1        /* invalid argument (null, size, alignment) */
+#define HT_ERR_CAPACITY 2   /* a size exceeds what the call supports      */
+#define HT_ERR_CUDA 3       /* a CUDA runtime call or launch failed       */
+#define HT_ERR_TIMEOUT 4    /* a bounded device-side wait gave up         */
+
+/* Geometry of the parameter space.  Requirements checked by
+ * ht_geometry_create: n_rho >= 1; n_d0 in [2, 1024]; n_phi0 >= 8 and a
+ * multiple of 8; n_z0, n_cot in [1, 1024]; threshold >= 1;
+ * count_bits 16 or 32; rho_max, d0_half, z0_max, cot_max > 0. */
+typedef struct ht_geometry_desc {
+    int32_t n_rho, n_d0, n_phi0;
+    int32_t n_z0, n_cot;
+    int32_t threshold;   /* peak threshold T (Section 7: tracks of >= 7 hits) */
+    int32_t count_bits;  /* 16: uint16 cells; 32: int32 cells */
+    int32_t reserved;    /* set to 0 */
+    double rho_max;      /* curvature half range, 1/cm */
+    double d0_half;      /* d0 half range, cm */
+    double z0_max;       /* z0 axis covers [-z0_max, z0_max), cm */
+    double cot_max;      /* cot(theta) axis covers [-cot_max, cot_max) */
+} ht_geometry_desc;
+
+typedef struct ht_geometry ht_geometry;   /* opaque handle */
+
+/* A candidate track: cell indices and its vote count. */
+typedef struct ht_peak { int32_t i_rho, j_d0, k_phi0, count; } ht_peak;
+
+/* Result of the (z0, cot theta) vote of one candidate. */
+typedef struct ht_zres { int32_t n_z0, m_cot, count; } ht_zres;
+
+/* Create a geometry handle on the current CUDA device.  The library owns the
+ * handle and its device tables (sin/cos phi0 and rho in float32 and float64,
+ * a few KB), computed on the host in float64 and uploaded.  *out receives the
+ * handle.  Errors: HT_ERR_ARG (desc or out null, a requirement above
+ * violated), HT_ERR_CUDA. */
+ht_status ht_geometry_create(const ht_geometry_desc *desc, ht_geometry **out);
+
+/* Release a handle and its device tables (NULL is accepted).  The caller
+ * must make sure no work using the handle is still queued. */
+ht_status ht_geometry_destroy(ht_geometry *g);
+
+/* Description of the last failure on this host thread ("" if none). */
+const char *ht_last_error(void);
+
+/* Bytes of one accumulator: n_rho * n_d0 * n_phi0 * (count_bits / 8). */
+size_t ht_accumulator_bytes(const ht_geometry *g);
+
+/* Hough vote (Section 5).  For each hit h, row i and column k with c > 0,
+ * every real root d0 of the circle equation (a double root once) whose bin
+ * coordinate lies in [0, n_d0) adds one vote to cell (i, j, k).  Reading:
+ * c > 0 keeps the first half turn only, so a track gives one peak, not a
+ * mirror pair.
+ *   x, y      n_hits float32 each, 16-byte aligned (device).
+ *   n_hits    >= 0 (0 writes an all-zero accumulator).
+ *   acc       accumulator (device, 16-byte aligned, ht_accumulator_bytes);
+ *             every cell is written, so it needs no clearing.
+ *   stats     NULL or 3 device uint64: votes cast, cells redone in float64,
+ *             votes whose bin coordinate lies within 1e-5 of an edge.  The
+ *             call zeroes them first.
+ * Errors: HT_ERR_ARG (null pointer with n_hits > 0, misalignment, n_hits < 0),
+ * HT_ERR_CUDA. */
+ht_status ht_vote(const ht_geometry *g, const float *x, const float *y,
+                  int32_t n_hits, void *acc, uint64_t *stats, ht_stream stream);
+
+/* Peak finding (Sections 5-7).  Reading: cell l is a peak iff its count is
+ * >= threshold and, for each existing 26-neighbour l' (rho and d0 do not
+ * wrap, phi0 wraps), count(l) > count(l') when l' < l and count(l) >=
+ * count(l') when l' > l.  Peaks are written in increasing l.
+ *   acc        accumulator from ht_vote (device).
+ *   peaks      cap entries (device); the first min(total, cap) are written.
+ *   cap        >= 0.
+ *   d_count    one device int32: the total number of peaks (may exceed cap).
+ *   workspace  ht_find_peaks_workspace_size(g) bytes of device scratch,
+ *              256-byte aligned; contents need no initialisation.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+size_t ht_find_peaks_workspace_size(const ht_geometry *g);
+ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks,
+                        int32_t cap, int32_t *d_count, void *workspace,
+                        size_t workspace_bytes, ht_stream stream);
+
+/* Hit association, the confirming step of Section 5.  Reading: hit h is
+ * compatible with candidate m iff one of its votes (exactly as ht_vote casts
+ * them) lies in a cell with |i - i_m| <= 1, |j - j_m| <= 1 and circular
+ * |k - k_m| <= 1; it is assigned to the compatible candidate of largest
+ * count, ties to the smallest m, else -1.  Candidates are
+ * peaks[0 .. min(*d_count, cap)), in increasing l (ht_find_peaks order).
+ *   assign     n_hits int32 (device).
+ *   workspace  ht_associate_workspace_size(g, n_hits) bytes, 256-byte aligned.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+size_t ht_associate_workspace_size(const ht_geometry *g, int32_t n_hits);
+ht_status ht_associate(const ht_geometry *g, const float *x, const float *y,
+                       int32_t n_hits, const ht_peak *peaks,
+                       const int32_t *d_count, int32_t cap, int32_t *assign,
+                       void *workspace, size_t workspace_bytes, ht_stream stream);
+
+/* Second vote in (z0, cot theta) per candidate (reading; the paper is
+ * transverse-plane only).  At the candidate's cell centres
+ * (rho_i, d0_j = (j - n_d0/2) delta, phi0_k), each assigned hit has turning
+ * angle theta = atan2(rho c, 1 + rho (s + d0_j)) and arc length
+ * L = theta / rho (L = c if rho == 0); for each cot centre
+ * t_q = (2q + 1 - n_cot) cot_max / n_cot it votes z0 = z - L t_q into bin
+ * floor((z0 + z0_max) / dz), dz = 2 z0_max / n_z0, if inside [0, n_z0).
+ * Output per candidate: the cell of most votes {n, q, count}, ties to the
+ * smallest n n_cot + q; {-1, -1, 0} if it received none.  atan2 here is a
+ * fixed sequence of basic operations (three half-angle reductions and a
+ * 10-term Maclaurin series), so results are reproducible bit for bit.
+ *   out        cap entries (device); the first min(*d_count, cap) are written.
+ *   workspace  ht_vote_z_workspace_size(g, n_hits, cap) bytes, 256-aligned.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+size_t ht_vote_z_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap);
+ht_status ht_vote_z(const ht_geometry *g, const float *x, const float *y,
+                    const float *z, int32_t n_hits, const int32_t *assign,
+                    const ht_peak *peaks, const int32_t *d_count, int32_t cap,
+                    ht_zres *out, void *workspace, size_t workspace_bytes,
+                    ht_stream stream);
+
+/* The whole path for one event from HOST buffers (Fig. 5 up to the
+ * refinement step): copies the hits to the device, runs ht_vote,
+ * ht_find_peaks, ht_associate and ht_vote_z on `stream`, copies the results
+ * back and synchronises the stream before returning.
+ *   hx, hy, hz   host float32 arrays of n_hits (pinned memory is faster).
+ *   workspace    ht_event_workspace_size(g, n_hits, cap) bytes of device
+ *                memory, 256-byte aligned (holds hits, accumulator, peaks,
+ *                assignments, z results and scratch).
+ *   h_peaks      host, cap entries; h_count host int32 (total peaks);
+ *   h_assign     host, n_hits; h_zres host, cap entries;
+ *   h_stats      host, 3 uint64 (may be NULL).
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+size_t ht_event_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap);
+ht_status ht_run_event(const ht_geometry *g, const float *hx, const float *hy,
+                       const float *hz, int32_t n_hits, void *workspace,
+                       size_t workspace_bytes, ht_peak *h_peaks, int32_t cap,
+                       int32_t *h_count, int32_t *h_assign, ht_zres *h_zres,
+                       uint64_t *h_stats, ht_stream stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HT_H */

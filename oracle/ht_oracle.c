@@ -240,6 +240,52 @@ void or_associate(const or_geom *g, const float *x, const float *y,
     free(phi0); free(sn); free(cs); free(rho);
 }
 
+/* The same association rule by a second route, for full-size events: hit h
+ * casts its votes (the vote's own cell_bins); each vote cell and its 26
+ * neighbours are looked up in cand_at[] (candidate index of every cell, -1
+ * if none), and the compatible candidate of largest count, smallest index
+ * wins.  Hits hit_idx[0..n_sel). */
+void or_associate_dense(const or_geom *g, const float *x, const float *y,
+                        const int64_t *hit_idx, int64_t n_sel, const int32_t *peaks,
+                        const int32_t *cand_at, int32_t *assign)
+{
+    double *phi0 = malloc(sizeof(double) * g->n_phi0);
+    double *sn = malloc(sizeof(double) * g->n_phi0);
+    double *cs = malloc(sizeof(double) * g->n_phi0);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    or_tables(g, phi0, sn, cs, rho);
+    const int32_t NR = g->n_rho, ND = g->n_d0, NP = g->n_phi0;
+    int64_t edge = 0;
+    for (int64_t t = 0; t < n_sel; ++t) {
+        const int64_t h = hit_idx[t];
+        int32_t best = -1, best_count = -1;
+        for (int32_t i = 0; i < NR; ++i)
+            for (int32_t k = 0; k < NP; ++k) {
+                int32_t j[2];
+                const int nv = cell_bins(g, x[h], y[h], sn[k], cs[k], rho[i], j, &edge);
+                for (int v = 0; v < nv; ++v)
+                    for (int di = -1; di <= 1; ++di)
+                        for (int dj = -1; dj <= 1; ++dj)
+                            for (int dk = -1; dk <= 1; ++dk) {
+                                const int32_t ii = i + di, jj = j[v] + dj;
+                                if (ii < 0 || ii >= NR || jj < 0 || jj >= ND)
+                                    continue;
+                                const int32_t kk = (k + dk + NP) % NP;
+                                const int32_t m = cand_at[((int64_t)ii * ND + jj) * NP + kk];
+                                if (m < 0)
+                                    continue;
+                                const int32_t cm = peaks[4 * m + 3];
+                                if (cm > best_count || (cm == best_count && m < best)) {
+                                    best = m;
+                                    best_count = cm;
+                                }
+                            }
+            }
+        assign[t] = best;
+    }
+    free(phi0); free(sn); free(cs); free(rho);
+}
+
 /* atan2 from basic operations only, so that a second implementation that
  * follows the same steps reproduces it bit for bit.  Method: reduce to
  * t = min(|y|, |x|) / max(|y|, |x|) in [0, 1]; apply the half-angle identity
@@ -289,10 +335,12 @@ void or_atan2_array(const double *y, const double *x, int64_t n, double *out)
  * 0 <= u < n_z0.  Output per candidate: argmax {n, q, count} over the
  * n_z0 x n_cot histogram, ties to the smallest n n_cot + q; {-1, -1, 0} when
  * no vote was cast.
- * Candidates cand[0..n_cand) are processed; out has 3 int32 per listed one. */
+ * Candidates cand[0..n_cand) are processed; the hits assigned to cand[t] are
+ * list[off[t] .. off[t + 1]) (grouped by the caller); out has 3 int32 per
+ * listed candidate. */
 void or_vote_z(const or_geom *g, const float *x, const float *y, const float *z,
-               int64_t n, const int32_t *assign, const int32_t *peaks,
-               const int64_t *cand, int64_t n_cand, int32_t *out)
+               const int32_t *peaks, const int64_t *cand, int64_t n_cand,
+               const int64_t *off, const int64_t *list, int32_t *out)
 {
     double *phi0 = malloc(sizeof(double) * g->n_phi0);
     double *sn = malloc(sizeof(double) * g->n_phi0);
@@ -310,9 +358,8 @@ void or_vote_z(const or_geom *g, const float *x, const float *y, const float *z,
         memset(hist, 0, sizeof(int64_t) * (size_t)NZ * NC);
         const double r = rho[im];
         const double d0c = ((double)jm - 0.5 * (double)g->n_d0) * delta;
-        for (int64_t h = 0; h < n; ++h) {
-            if (assign[h] != m)
-                continue;
+        for (int64_t e = off[t]; e < off[t + 1]; ++e) {
+            const int64_t h = list[e];
             const double xd = x[h], yd = y[h], zd = z[h];
             const double s = xd * sn[km] - yd * cs[km];
             const double c = xd * cs[km] + yd * sn[km];

@@ -75,7 +75,8 @@ def lib():
             L.or_atan2.argtypes = [ctypes.c_double, ctypes.c_double]
             L.or_atan2.restype = ctypes.c_double
             L.or_atan2_array.argtypes = [vp, vp, i64, vp]
-            L.or_vote_z.argtypes = [G, vp, vp, vp, i64, vp, vp, vp, i64, vp]
+            L.or_vote_z.argtypes = [G, vp, vp, vp, vp, vp, i64, vp, vp, vp]
+            L.or_associate_dense.argtypes = [G, vp, vp, vp, i64, vp, vp, vp]
             _lib = L
         return _lib
 
@@ -103,21 +104,28 @@ def tables(g):
     return phi0, sn, cs, rho
 
 
-def vote(g, x, y, threads=None):
-    """Accumulator int64 [n_rho, n_d0, n_phi0] and stats {votes, edge}."""
+def vote(g, x, y, threads=None, rows=None):
+    """Accumulator int64 [n_rho, n_d0, n_phi0] and stats {votes, edge}.
+
+    rows=(a, b) computes only rho rows [a, b) and returns acc[a:b] (each row
+    of the vote depends only on that row)."""
     G = _geom(g)
     x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
-    acc = np.zeros((g["n_rho"], g["n_d0"], g["n_phi0"]), np.int64)
-    rows = _chunks(g["n_rho"], _threads(threads) * 2)
-    stats = np.zeros((len(rows), 2), np.int64)
+    r0, r1 = (0, g["n_rho"]) if rows is None else rows
+    acc = np.zeros((g["n_rho"], g["n_d0"], g["n_phi0"]), np.int64) if rows is None else \
+        np.zeros((r1 - r0, g["n_d0"], g["n_phi0"]), np.int64)
+    base = 0 if rows is None else r0 * g["n_d0"] * g["n_phi0"] * 8
+    parts = [(a + r0, b + r0) for a, b in _chunks(r1 - r0, _threads(threads) * 2)]
+    stats = np.zeros((len(parts), 2), np.int64)
+    accp = acc.ctypes.data - base
 
     def run(t):
-        a, b = rows[t]
-        lib().or_vote(ctypes.byref(G), _p(x), _p(y), x.shape[0], a, b, _p(acc),
-                      _p(stats[t]))
+        a, b = parts[t]
+        lib().or_vote(ctypes.byref(G), _p(x), _p(y), x.shape[0], a, b,
+                      ctypes.c_void_p(accp), _p(stats[t]))
 
     with ThreadPoolExecutor(_threads(threads)) as ex:
-        list(ex.map(run, range(len(rows))))
+        list(ex.map(run, range(len(parts))))
     tot = stats.sum(0)
     return acc, {"votes": int(tot[0]), "edge": int(tot[1])}
 
@@ -169,6 +177,34 @@ def associate(g, x, y, pk, hit_idx=None, threads=None):
     return out
 
 
+def associate_dense(g, x, y, pk, hit_idx=None, threads=None):
+    """Association by enumerating each hit's votes against a cell -> candidate
+    map (same rule as associate(); the route used for full-size events)."""
+    G = _geom(g)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    pk = np.ascontiguousarray(pk, np.int32).reshape(-1, 4)
+    cand_at = np.full(g["n_rho"] * g["n_d0"] * g["n_phi0"], -1, np.int32)
+    lidx = (pk[:, 0].astype(np.int64) * g["n_d0"] + pk[:, 1]) * g["n_phi0"] + pk[:, 2]
+    cand_at[lidx] = np.arange(pk.shape[0], dtype=np.int32)
+    if hit_idx is None:
+        hit_idx = np.arange(x.shape[0], dtype=np.int64)
+    hit_idx = np.ascontiguousarray(hit_idx, np.int64)
+    out = np.full(hit_idx.shape[0], -1, np.int32)
+    parts = _chunks(hit_idx.shape[0], _threads(threads) * 4)
+
+    def run(ab):
+        a, b = ab
+        sub = hit_idx[a:b].copy()
+        o = np.empty(b - a, np.int32)
+        lib().or_associate_dense(ctypes.byref(G), _p(x), _p(y), _p(sub), b - a, _p(pk),
+                                 _p(cand_at), _p(o))
+        out[a:b] = o
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, parts))
+    return out
+
+
 def vote_z(g, x, y, z, assign, pk, cand=None, threads=None):
     """Per-candidate (z0, cot theta) argmax: int32 [n_cand, 3] = {n, q, count}."""
     G = _geom(g)
@@ -179,15 +215,25 @@ def vote_z(g, x, y, z, assign, pk, cand=None, threads=None):
     if cand is None:
         cand = np.arange(pk.shape[0], dtype=np.int64)
     cand = np.ascontiguousarray(cand, np.int64)
+    # group hit indices by assigned candidate (marshalling, no arithmetic)
+    order = np.argsort(assign, kind="stable").astype(np.int64)
+    sa = assign[order]
+    lo = np.searchsorted(sa, cand, side="left")
+    hi = np.searchsorted(sa, cand, side="right")
     out = np.zeros((cand.shape[0], 3), np.int32)
     parts = _chunks(cand.shape[0], _threads(threads) * 4)
 
     def run(ab):
         a, b = ab
-        sub = cand[a:b].copy()
+        c_sub = cand[a:b].copy()
+        lists = [order[lo[t]:hi[t]] for t in range(a, b)]
+        off = np.zeros(b - a + 1, np.int64)
+        off[1:] = np.cumsum([len(v) for v in lists])
+        lst = np.concatenate(lists) if lists else np.zeros(0, np.int64)
+        lst = np.ascontiguousarray(lst, np.int64)
         o = np.zeros((b - a, 3), np.int32)
-        lib().or_vote_z(ctypes.byref(G), _p(x), _p(y), _p(z), x.shape[0], _p(assign),
-                        _p(pk), _p(sub), b - a, _p(o))
+        lib().or_vote_z(ctypes.byref(G), _p(x), _p(y), _p(z), _p(pk), _p(c_sub), b - a,
+                        _p(off), _p(lst), _p(o))
         out[a:b] = o
 
     if cand.shape[0]:
@@ -208,6 +254,6 @@ def run_event(g, x, y, z, cap=None, threads=None):
     """The whole path on one event: acc, stats, peaks, count, assign, zres."""
     acc, st = vote(g, x, y, threads)
     pk, cnt = peaks(g, acc, cap, threads)
-    asg = associate(g, x, y, pk, threads=threads)
+    asg = associate_dense(g, x, y, pk, threads=threads)
     zr = vote_z(g, x, y, z, asg, pk, threads=threads)
     return dict(acc=acc, stats=st, peaks=pk, count=cnt, assign=asg, zres=zr)

@@ -1,0 +1,239 @@
+// ht_internal.cuh -- device-side geometry, exact and guarded cell evaluators.
+//
+// Shared by the kernels of libht.  Nothing here is part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ht.h"
+
+namespace ht {
+
+// ---------------------------------------------------------------------------
+// Geometry as the kernels see it (passed by value).  Every float64 value is
+// computed on the host with the same expression as the plain definition; the
+// float32 copies are roundings of those values.
+struct DevGeom {
+    int n_rho, n_d0, n_phi0, n_z0, n_cot, threshold, count_bits;
+    // d0 axis
+    double delta, off;             // bin width, u = d0 / delta + off
+    float delta_f, inv_delta_f, off_f;
+    float d0lo_f, d0hi_f;          // axis limits extended by 0.01 cm (filters only)
+    float err_scale;               // SAFE * 2^-24 / delta
+    float rho_max_f, drho_f, dmax_f; // |rho| bound, row width, max |d0| (filters)
+    // tables (device)
+    const float *sn32, *cs32, *phi32, *rho32, *invrho32;
+    const double *sn64, *cs64, *rho64;
+    // z vote
+    double dz, z0_max, cstep;      // dz = 2 z0_max / n_z0, cstep = cot_max / n_cot
+    float inv_dz_f, z0_max_f, cstep_f;
+};
+
+constexpr float kEps = 5.9604644775390625e-8f;   // 2^-24, float32 unit roundoff
+constexpr float kSafe = 4.0f;                    // slack on first-order error bounds
+constexpr double kPi = 3.141592653589793;
+constexpr double kHalfPi = 1.5707963267948966;
+
+// ---------------------------------------------------------------------------
+// Exact evaluation of one (hit, rho_i, phi0_k) column in float64, one
+// correctly rounded operation at a time in the definition's order (the _rn
+// intrinsics forbid contraction into FMA).  Writes the in-range bins to j[]
+// and returns their number; *n_edge counts bin coordinates within 1e-5 of an
+// integer.
+__device__ __forceinline__ int cell_bins64(const DevGeom &G, float xf, float yf,
+                                           int i, int k, int j[2], int *n_edge)
+{
+    const double x = (double)xf, y = (double)yf;
+    const double sn = G.sn64[k], cs = G.cs64[k], rho = G.rho64[i];
+    const double s = __dsub_rn(__dmul_rn(x, sn), __dmul_rn(y, cs));
+    const double c = __dadd_rn(__dmul_rn(x, cs), __dmul_rn(y, sn));
+    if (!(c > 0.0)) return 0;
+    const double r2 = __dadd_rn(__dmul_rn(x, x), __dmul_rn(y, y));
+    const double b = __dadd_rn(1.0, __dmul_rn(rho, s));
+    const double pc = __dmul_rn(rho, c);
+    const double D = __dsub_rn(1.0, __dmul_rn(pc, pc));
+    if (D < 0.0) return 0;
+    const double sq = __dsqrt_rn(D);
+    const double q = -__dadd_rn(b, b >= 0.0 ? sq : -sq);
+    const double C = __dadd_rn(__dmul_rn(rho, r2), __dmul_rn(2.0, s));
+    double root[2];
+    int nr = 0;
+    if (rho != 0.0) root[nr++] = __ddiv_rn(q, rho);
+    if (q != 0.0 && !(D == 0.0 && rho != 0.0)) root[nr++] = __ddiv_rn(C, q);
+    int nv = 0;
+    for (int t = 0; t < nr; ++t) {
+        const double u = __dadd_rn(__ddiv_rn(root[t], G.delta), G.off);
+        if (u >= 0.0 && u < (double)G.n_d0) {
+            const double fl = floor(u);
+            const double fr = __dsub_rn(u, fl);
+            j[nv++] = (int)fl;
+            if (fr < 1e-5 || fr > 1.0 - 1e-5) ++*n_edge;
+        }
+    }
+    return nv;
+}
+
+// ---------------------------------------------------------------------------
+// Guarded float32 evaluation of one column for a hit with s, c (c proven > 0
+// by the caller), r2 = x^2 + y^2 and R1 = |x| + |y|, at row curvature rho
+// (arho = |rho|, ainvrho = |1/rho|, has_b = rho != 0).
+//
+// First-order error bounds (unit roundoff u = 2^-24, rsqrtf <= 2 ulp):
+//   |ds|, |dc| <= 3u R1;  |db| <= u (4|rho|R1 + |b|);
+//   |dD| <= u (10 |rho|R1 |rho c| + |D|);
+//   |dq| <= u Q,  Q = 4|rho|R1 + 2|q| + 5 + (5 (rho R1)^2 + 1/2) / sqrt(D);
+//   root A = C / q:  |d dA| <= u (|1/q| (3|rho| r2 + 6 R1 + |dA| Q) + 4|dA|);
+//   root B = q / rho: |d dB| <= u (|1/rho| Q + 4|dB|);
+// each scaled by kSafe and divided by delta to give bins, plus u|u| for the
+// final fused multiply-add.  A root is decided here only if its coordinate
+// is farther than its bound from every integer (a range edge included) or
+// certainly outside [0, n_d0); D only if |D| exceeds its bound.
+// Returns true when decided: jA, jB = bin or -1, *n_edge updated.  Returns
+// false when the column must be redone by cell_bins64.
+__device__ __forceinline__ bool cell_bins32(const DevGeom &G, float rho, float arho,
+                                            float invrho, float ainvrho, bool has_b,
+                                            float s, float c, float r2, float R1,
+                                            int &jA, int &jB, int &n_edge)
+{
+    jA = -1;
+    jB = -1;
+    const float b = fmaf(rho, s, 1.0f);
+    const float pc = rho * c;
+    const float D = fmaf(-pc, pc, 1.0f);
+    const float P1 = arho * R1;
+    const float eD = (kSafe * kEps) * fmaf(10.0f * P1, fabsf(pc), fabsf(D) + 1.0f);
+    if (D < -eD) return true;          // certainly no real root
+    if (D <= eD) return false;         // tangent within error: exact path
+    const float rs = rsqrtf(D);
+    const float sq = D * rs;
+    const float q = -(b + copysignf(sq, b));
+    const float C = fmaf(rho, r2, 2.0f * s);
+    const float iq = __frcp_rn(q);
+    const float Q = fmaf(fmaf(5.0f * P1, P1, 0.5f), rs, fmaf(2.0f, fabsf(q), fmaf(4.0f, P1, 5.0f)));
+    const float nd = (float)G.n_d0;
+    // root A
+    const float dA = C * iq;
+    const float uA = fmaf(dA, G.inv_delta_f, G.off_f);
+    const float eA = fmaf(fmaf(fabsf(iq), fmaf(fabsf(dA), Q, fmaf(3.0f * arho, r2, 6.0f * R1)),
+                               4.0f * fabsf(dA)),
+                          G.err_scale, (kSafe * kEps) * fabsf(uA));
+    const bool outA = (uA + eA < 0.0f) || (uA - eA >= nd);
+    const float fA = floorf(uA);
+    const float frA = uA - fA;
+    const float dist_A = fminf(frA, 1.0f - frA);
+    if (!outA) {
+        if (!(dist_A > eA)) return false;
+        jA = (int)fA;
+        n_edge += dist_A < 1e-5f;
+    }
+    if (has_b) {
+        const float dB = q * invrho;
+        const float uB = fmaf(dB, G.inv_delta_f, G.off_f);
+        const float eB = fmaf(fmaf(ainvrho, Q, 4.0f * fabsf(dB)), G.err_scale,
+                              (kSafe * kEps) * fabsf(uB));
+        const bool outB = (uB + eB < 0.0f) || (uB - eB >= nd);
+        if (!outB) {
+            const float fB = floorf(uB);
+            const float frB = uB - fB;
+            const float dist_B = fminf(frB, 1.0f - frB);
+            if (!(dist_B > eB)) return false;
+            jB = (int)fB;
+            n_edge += dist_B < 1e-5f;
+        }
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// Phase-1 filters shared by the tile kernels.
+//
+// Angular window of a hit: any circle with |rho| <= rho_max through a hit at
+// radius r whose perigee lies within dmax of the origin has its phi0 within
+//   asin(min(1, rho_max (r + dmax) / 2)) + asin(min(1, dmax / r))
+// of the hit's azimuth (half the turning angle along the chord from the
+// perigee, plus the angle the chord makes with the hit's radius), and c > 0
+// bounds it by pi/2.  A 1e-3 rad margin covers float32 rounding.
+__device__ __forceinline__ float hit_window(const DevGeom &G, float r)
+{
+    const float a = asinf(fminf(1.0f, G.rho_max_f * (r + G.dmax_f) * 0.5f)) +
+                    asinf(fminf(1.0f, G.dmax_f / fmaxf(r, 1e-30f)));
+    return fminf(a, (float)kHalfPi) + 1e-3f;
+}
+
+__device__ __forceinline__ float wrap_pi(float d)
+{
+    if (d > (float)kPi) d -= 2.0f * (float)kPi;
+    if (d < -(float)kPi) d += 2.0f * (float)kPi;
+    return d;
+}
+
+// Curvature range reached by circles through a hit (s, c) with perigee d0 in
+// the (extended) axis: rho = g(w) = -2 w / (w^2 + c^2), w = d0 + s, which
+// falls on |w| < c and rises outside, so its extremes over an interval are at
+// the ends or at w = -c (max 1/c) and w = c (min -1/c).  Used only to skip
+// (hit, column) pairs that cannot vote in a block of rows; callers keep a
+// full-row margin and skip the test for c <= 1 cm.
+__device__ __forceinline__ void rho_range(const DevGeom &G, float s, float c,
+                                          float &gmin, float &gmax)
+{
+    const float wlo = G.d0lo_f + s, whi = G.d0hi_f + s;
+    const float c2 = c * c;
+    const float glo = __fdividef(-2.0f * wlo, fmaf(wlo, wlo, c2));
+    const float ghi = __fdividef(-2.0f * whi, fmaf(whi, whi, c2));
+    const float ic = __frcp_rn(c);
+    gmax = (wlo <= -c && -c <= whi) ? ic : fmaxf(glo, ghi);
+    gmin = (wlo <= c && c <= whi) ? -ic : fminf(glo, ghi);
+}
+
+// ---------------------------------------------------------------------------
+// atan2 from basic float64 operations in a fixed order (three half-angle
+// reductions atan t = 2 atan(t / (1 + sqrt(1 + t^2))), then the Maclaurin
+// series of atan to t^21 by Horner's rule), so that any implementation that
+// follows the same steps with correctly rounded operations gives the same
+// bits.  (0, 0) -> 0; the sign of a zero y is ignored.
+__device__ __forceinline__ double atan_unit64(double t)
+{
+#pragma unroll 1
+    for (int h = 0; h < 3; ++h)
+        t = __ddiv_rn(t, __dadd_rn(1.0, __dsqrt_rn(__dadd_rn(1.0, __dmul_rn(t, t)))));
+    const double t2 = __dmul_rn(t, t);
+    double p = __ddiv_rn(1.0, 21.0);
+#pragma unroll 1
+    for (int k = 9; k >= 0; --k)
+        p = __dsub_rn(__ddiv_rn(1.0, (double)(2 * k + 1)), __dmul_rn(t2, p));
+    return __dmul_rn(8.0, __dmul_rn(t, p));
+}
+
+__device__ __forceinline__ double atan2_basic64(double y, double x)
+{
+    if (x == 0.0 && y == 0.0) return 0.0;
+    const double ax = fabs(x), ay = fabs(y);
+    double a;
+    if (ay <= ax)
+        a = atan_unit64(__ddiv_rn(ay, ax));
+    else
+        a = __dsub_rn(kHalfPi, atan_unit64(__ddiv_rn(ax, ay)));
+    if (x < 0.0) a = __dsub_rn(kPi, a);
+    return y < 0.0 ? -a : a;
+}
+
+// ---------------------------------------------------------------------------
+// Host-side launchers (one per kernel file).
+cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n, void *acc,
+                        unsigned long long *stats, cudaStream_t st);
+cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
+                         int *d_count, void *ws, cudaStream_t st);
+size_t peaks_workspace_bytes(const DevGeom &G);
+cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, int n,
+                             const ht_peak *peaks, const int *d_count, int cap, int *assign,
+                             void *ws, cudaStream_t st);
+size_t associate_workspace_bytes(const DevGeom &G, int n);
+cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, const float *z,
+                          int n, const int *assign, const ht_peak *peaks, const int *d_count,
+                          int cap, ht_zres *out, void *ws, cudaStream_t st);
+size_t vote_z_workspace_bytes(const DevGeom &G, int n, int cap);
+
+inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace ht

@@ -1,0 +1,164 @@
+// k_peaks.cu -- 3x3x3 local-maximum peak finding over the accumulator with
+// order-preserving compaction (Sections 5-7 of arXiv:1309.6275: candidates
+// are the local maxima of the vote space; the threshold reflects the peak
+// finder's tuning for tracks of 7 or more hits).
+//
+// Design (GB300, HBM-bound stencil):
+//  * A CTA of 256 threads owns one segment row (i, j-block, k-block): thread
+//    = phi0 column k, and the CTA walks d0 bins j over its block keeping a
+//    rolling 3 (rho) x 3 (d0) x 3 (phi0) window in registers, so each step
+//    loads one new d0 slice (9 coalesced loads per thread, neighbours in
+//    phi0 served from L1).  Rows beyond rho/d0 edges read as absent; phi0
+//    wraps.
+//  * Compaction keeps increasing logical index l = (i n_d0 + j) n_phi0 + k:
+//    pass 1 counts the peaks of every (i, j, k-block) segment, a
+//    single-CTA scan turns counts into offsets (and the total), pass 2
+//    recomputes and writes each peak at its segment offset plus its rank in
+//    the CTA (warp ballots + a per-warp prefix).  Segments are ordered by l,
+//    so the output is too.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ht_internal.cuh"
+
+namespace ht {
+namespace {
+
+constexpr int kPkThreads = 256;   // phi0 columns per CTA
+constexpr int kJB = 16;           // d0 bins walked per CTA
+constexpr int kScanThreads = 1024;
+
+template <typename T, bool WRITE>
+__global__ void __launch_bounds__(kPkThreads)
+k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
+        const int *__restrict__ segoff, ht_peak *__restrict__ out, int cap)
+{
+    const int NP = G.n_phi0, ND = G.n_d0, NR = G.n_rho;
+    const int nkb = (NP + kPkThreads - 1) / kPkThreads;
+    const int kb = blockIdx.x, i = blockIdx.z;
+    const int k = kb * kPkThreads + threadIdx.x;
+    const bool kok = k < NP;
+    const int km = (k == 0) ? NP - 1 : k - 1;
+    const int kp = (k >= NP - 1) ? 0 : k + 1;
+    const int j0 = blockIdx.y * kJB, j1 = min(j0 + kJB, ND);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    __shared__ int wcnt[kPkThreads / 32];
+
+    int w[3][3][3];  // [rho -1..+1][d0 -1..+1][phi0 -1..+1]; -1 = absent
+    auto load = [&](int slot, int jj) {
+#pragma unroll
+        for (int di = 0; di < 3; ++di) {
+            const int ii = i + di - 1;
+            const bool ok = kok && ii >= 0 && ii < NR && jj >= 0 && jj < ND;
+            const size_t rowb = ok ? ((size_t)ii * ND + jj) * NP : 0;
+            w[di][slot][0] = ok ? (int)acc[rowb + km] : -1;
+            w[di][slot][1] = ok ? (int)acc[rowb + k] : -1;
+            w[di][slot][2] = ok ? (int)acc[rowb + kp] : -1;
+        }
+    };
+    load(0, j0 - 1);
+    load(1, j0);
+    for (int j = j0; j < j1; ++j) {
+        load(2, j + 1);
+        const int v = w[1][1][1];
+        bool pk = kok && v >= G.threshold;
+        // rows i-1 and d0 bin j-1 (at row i) precede l: strictly greater;
+        // rows i+1 and d0 bin j+1 follow l: greater or equal.
+#pragma unroll
+        for (int dj = 0; dj < 3; ++dj)
+#pragma unroll
+            for (int dk = 0; dk < 3; ++dk) {
+                pk = pk && (v > w[0][dj][dk]) && (v >= w[2][dj][dk]);
+            }
+#pragma unroll
+        for (int dk = 0; dk < 3; ++dk) pk = pk && (v > w[1][0][dk]) && (v >= w[1][2][dk]);
+        // same (i, j): phi0 neighbours; their order flips across the wrap
+        pk = pk && ((k != 0) ? (v > w[1][1][0]) : (v >= w[1][1][0]));
+        pk = pk && ((k != NP - 1) ? (v >= w[1][1][2]) : (v > w[1][1][2]));
+
+        const int seg = (i * ND + j) * nkb + kb;
+        if (!WRITE) {
+            const int c = __syncthreads_count(pk);
+            if (threadIdx.x == 0) segcnt[seg] = c;
+        } else {
+            const unsigned bal = __ballot_sync(0xffffffffu, pk);
+            if (lane == 0) wcnt[warp] = __popc(bal);
+            __syncthreads();
+            int pos = segoff[seg] + __popc(bal & ((1u << lane) - 1u));
+            for (int w2 = 0; w2 < warp; ++w2) pos += wcnt[w2];
+            if (pk && pos < cap) out[pos] = ht_peak{i, j, k, v};
+            __syncthreads();
+        }
+#pragma unroll
+        for (int di = 0; di < 3; ++di)
+#pragma unroll
+            for (int dk = 0; dk < 3; ++dk) {
+                w[di][0][dk] = w[di][1][dk];
+                w[di][1][dk] = w[di][2][dk];
+            }
+    }
+}
+
+// Exclusive scan of cnt[0..n) into off[0..n) with one CTA; *total = sum.
+__global__ void __launch_bounds__(kScanThreads)
+k_scan(const int *__restrict__ cnt, int *__restrict__ off, int n, int *__restrict__ total)
+{
+    __shared__ int part[kScanThreads];
+    const int per = (n + kScanThreads - 1) / kScanThreads;
+    const int a = min(n, threadIdx.x * per), b = min(n, a + per);
+    int s = 0;
+    for (int t = a; t < b; ++t) s += cnt[t];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = 1; o < kScanThreads; o <<= 1) {
+        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+        __syncthreads();
+        part[threadIdx.x] += v;
+        __syncthreads();
+    }
+    int run = part[threadIdx.x] - s;
+    for (int t = a; t < b; ++t) {
+        const int c = cnt[t];
+        off[t] = run;
+        run += c;
+    }
+    if (threadIdx.x == kScanThreads - 1) *total = part[kScanThreads - 1];
+}
+
+template <typename T>
+cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, int *d_count,
+                      int *segcnt, int *segoff, cudaStream_t st)
+{
+    const int nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
+    dim3 grid(nkb, (G.n_d0 + kJB - 1) / kJB, G.n_rho);
+    const int nseg = G.n_rho * G.n_d0 * nkb;
+    k_peaks<T, false><<<grid, kPkThreads, 0, st>>>(G, acc, segcnt, nullptr, nullptr, 0);
+    k_scan<<<1, kScanThreads, 0, st>>>(segcnt, segoff, nseg, d_count);
+    k_peaks<T, true><<<grid, kPkThreads, 0, st>>>(G, acc, nullptr, segoff, peaks, cap);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t peaks_workspace_bytes(const DevGeom &G)
+{
+    const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
+    const size_t nseg = (size_t)G.n_rho * G.n_d0 * nkb;
+    return 2 * align256(nseg * 4);
+}
+
+cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
+                         int *d_count, void *ws, cudaStream_t st)
+{
+    const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
+    const size_t nseg = (size_t)G.n_rho * G.n_d0 * nkb;
+    int *segcnt = reinterpret_cast<int *>(ws);
+    int *segoff = reinterpret_cast<int *>(reinterpret_cast<char *>(ws) + align256(nseg * 4));
+    if (G.count_bits == 16)
+        return run_peaks(G, reinterpret_cast<const uint16_t *>(acc), peaks, cap, d_count, segcnt,
+                         segoff, st);
+    return run_peaks(G, reinterpret_cast<const int32_t *>(acc), peaks, cap, d_count, segcnt,
+                     segoff, st);
+}
+
+}  // namespace ht

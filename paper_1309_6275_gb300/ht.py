@@ -1,0 +1,223 @@
+"""Thin Python binding of libht (include/ht.h), argument marshalling only.
+
+Every function here forwards torch CUDA tensors (device pointers) or pinned
+host tensors to the C ABI of the same name; all arithmetic runs in libht's
+CUDA kernels.  There is no CPU or PyTorch fallback: if the library cannot be
+built or loaded, importing this module raises.
+
+Tensor conventions:
+  hits          float32 [n] each (x, y, z), contiguous, on the geometry's GPU
+  accumulator   int16 (viewed as uint16) or int32 [n_rho, n_d0, n_phi0]
+  peaks         int32 [cap, 4] = {i_rho, j_d0, k_phi0, count}
+  d_count       int32 [1]
+  assign        int32 [n]
+  zres          int32 [cap, 3] = {n_z0, m_cot, count}
+  stats         int64 [3] (uint64 counters: votes, float64 redos, edge votes)
+  workspace     uint8, at least the size the matching *_workspace_size gives
+"""
+import ctypes
+import os
+
+import torch
+
+from . import build as _build
+
+_lib = None
+
+
+class HTError(RuntimeError):
+    pass
+
+
+class _Desc(ctypes.Structure):
+    _fields_ = [("n_rho", ctypes.c_int32), ("n_d0", ctypes.c_int32),
+                ("n_phi0", ctypes.c_int32), ("n_z0", ctypes.c_int32),
+                ("n_cot", ctypes.c_int32), ("threshold", ctypes.c_int32),
+                ("count_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("rho_max", ctypes.c_double), ("d0_half", ctypes.c_double),
+                ("z0_max", ctypes.c_double), ("cot_max", ctypes.c_double)]
+
+
+# (name, restype, argtypes) of every exported function, as in include/ht.h
+_P, _I32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
+SIGNATURES = [
+    ("ht_last_error", ctypes.c_char_p, []),
+    ("ht_geometry_create", _I32, [ctypes.POINTER(_Desc), ctypes.POINTER(_P)]),
+    ("ht_geometry_destroy", _I32, [_P]),
+    ("ht_accumulator_bytes", _SZ, [_P]),
+    ("ht_vote", _I32, [_P, _P, _P, _I32, _P, _P, _P]),
+    ("ht_find_peaks_workspace_size", _SZ, [_P]),
+    ("ht_find_peaks", _I32, [_P, _P, _P, _I32, _P, _P, _SZ, _P]),
+    ("ht_associate_workspace_size", _SZ, [_P, _I32]),
+    ("ht_associate", _I32, [_P, _P, _P, _I32, _P, _P, _I32, _P, _P, _SZ, _P]),
+    ("ht_vote_z_workspace_size", _SZ, [_P, _I32, _I32]),
+    ("ht_vote_z", _I32, [_P, _P, _P, _P, _I32, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
+    ("ht_event_workspace_size", _SZ, [_P, _I32, _I32]),
+    ("ht_run_event", _I32, [_P, _P, _P, _P, _I32, _P, _SZ, _P, _I32, _P, _P, _P, _P, _P]),
+    ("ht_probe_shared_atomic_rate", _I32, [_I32, ctypes.POINTER(ctypes.c_double), _P]),
+]
+
+
+def library_path():
+    return _build.LIB
+
+
+def lib():
+    """Load libht (building it first if its sources are newer)."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise HTError(f"libht not found at {path}")
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status, what):
+    if status != 0:
+        msg = lib().ht_last_error().decode(errors="replace")
+        raise HTError(f"{what} failed (status {status}): {msg}")
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+class Geometry:
+    """Owns an ht_geometry handle created on the current CUDA device."""
+
+    def __init__(self, g):
+        self.desc = dict(g)
+        d = _Desc(g["n_rho"], g["n_d0"], g["n_phi0"], g["n_z0"], g["n_cot"],
+                  g["threshold"], g.get("count_bits", 32), 0, g["rho_max"],
+                  g["d0_half"], g["z0_max"], g["cot_max"])
+        h = ctypes.c_void_p()
+        _check(lib().ht_geometry_create(ctypes.byref(d), ctypes.byref(h)),
+               "ht_geometry_create")
+        self.handle = h
+        self.shape = (g["n_rho"], g["n_d0"], g["n_phi0"])
+        self.acc_dtype = torch.int16 if g.get("count_bits", 32) == 16 else torch.int32
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ht_geometry_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def accumulator_bytes(self):
+        return lib().ht_accumulator_bytes(self.handle)
+
+    def find_peaks_workspace_size(self):
+        return lib().ht_find_peaks_workspace_size(self.handle)
+
+    def associate_workspace_size(self, n_hits):
+        return lib().ht_associate_workspace_size(self.handle, n_hits)
+
+    def vote_z_workspace_size(self, n_hits, cap):
+        return lib().ht_vote_z_workspace_size(self.handle, n_hits, cap)
+
+    def event_workspace_size(self, n_hits, cap):
+        return lib().ht_event_workspace_size(self.handle, n_hits, cap)
+
+    def new_accumulator(self, device="cuda"):
+        return torch.empty(self.shape, dtype=self.acc_dtype, device=device)
+
+
+def ht_vote(g, x, y, acc, stats=None, stream=None):
+    n = x.numel()
+    _check(lib().ht_vote(g.handle, _ptr(x), _ptr(y), n, _ptr(acc), _ptr(stats),
+                         _stream(stream)), "ht_vote")
+
+
+def ht_find_peaks(g, acc, peaks, cap, d_count, workspace, stream=None):
+    _check(lib().ht_find_peaks(g.handle, _ptr(acc), _ptr(peaks), cap, _ptr(d_count),
+                               _ptr(workspace), workspace.numel(), _stream(stream)),
+           "ht_find_peaks")
+
+
+def ht_associate(g, x, y, peaks, d_count, cap, assign, workspace, stream=None):
+    _check(lib().ht_associate(g.handle, _ptr(x), _ptr(y), x.numel(), _ptr(peaks),
+                              _ptr(d_count), cap, _ptr(assign), _ptr(workspace),
+                              workspace.numel(), _stream(stream)), "ht_associate")
+
+
+def ht_vote_z(g, x, y, z, assign, peaks, d_count, cap, out, workspace, stream=None):
+    _check(lib().ht_vote_z(g.handle, _ptr(x), _ptr(y), _ptr(z), x.numel(), _ptr(assign),
+                           _ptr(peaks), _ptr(d_count), cap, _ptr(out), _ptr(workspace),
+                           workspace.numel(), _stream(stream)), "ht_vote_z")
+
+
+def ht_run_event(g, hx, hy, hz, workspace, h_peaks, cap, h_count, h_assign, h_zres,
+                 h_stats=None, stream=None):
+    """Host-buffer path: hx, hy, hz and the outputs are CPU tensors."""
+    _check(lib().ht_run_event(g.handle, _ptr(hx), _ptr(hy), _ptr(hz), hx.numel(),
+                              _ptr(workspace), workspace.numel(), _ptr(h_peaks), cap,
+                              _ptr(h_count), _ptr(h_assign), _ptr(h_zres), _ptr(h_stats),
+                              _stream(stream)), "ht_run_event")
+
+
+def ht_probe_shared_atomic_rate(iters=4096, stream=None):
+    """Measured conflict-free shared-memory atomicAdd rate (atomics/s)."""
+    v = ctypes.c_double()
+    _check(lib().ht_probe_shared_atomic_rate(iters, ctypes.byref(v), _stream(stream)),
+           "ht_probe_shared_atomic_rate")
+    return v.value
+
+
+class EventPipeline:
+    """Device buffers for one event of up to `max_hits` hits and `cap`
+    candidates, and the four calls of the path in order."""
+
+    def __init__(self, g, max_hits, cap, device="cuda"):
+        self.g, self.cap, self.max_hits = g, cap, max_hits
+        dev = torch.device(device)
+        self.acc = g.new_accumulator(dev)
+        self.peaks = torch.empty((max(cap, 1), 4), dtype=torch.int32, device=dev)
+        self.count = torch.zeros(1, dtype=torch.int32, device=dev)
+        self.assign = torch.empty(max(max_hits, 1), dtype=torch.int32, device=dev)
+        self.zres = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=dev)
+        self.stats = torch.zeros(3, dtype=torch.int64, device=dev)
+        ws = max(g.find_peaks_workspace_size(), g.associate_workspace_size(max_hits),
+                 g.vote_z_workspace_size(max_hits, cap))
+        self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
+
+    def run(self, x, y, z, stream=None):
+        n = x.numel()
+        assert n <= self.max_hits
+        g = self.g
+        ht_vote(g, x, y, self.acc, self.stats, stream)
+        ht_find_peaks(g, self.acc, self.peaks, self.cap, self.count, self.workspace, stream)
+        ht_associate(g, x, y, self.peaks, self.count, self.cap, self.assign[:n],
+                     self.workspace, stream)
+        ht_vote_z(g, x, y, z, self.assign[:n], self.peaks, self.count, self.cap, self.zres,
+                  self.workspace, stream)
+
+    def results(self, n):
+        """Copy results to numpy (synchronises)."""
+        import numpy as np
+        cnt = int(self.count.item())
+        k = min(cnt, self.cap)
+        acc = self.acc.cpu().numpy()
+        if acc.dtype == np.int16:
+            acc = acc.view(np.uint16)
+        return dict(acc=acc, count=cnt, peaks=self.peaks[:k].cpu().numpy(),
+                    assign=self.assign[:n].cpu().numpy(), zres=self.zres[:k].cpu().numpy(),
+                    stats=self.stats.cpu().numpy().astype(np.uint64))

@@ -1,0 +1,55 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path through the C ABI
+binding and the oracle on the same seeded inputs."""
+import functools
+
+import numpy as np
+
+import oracle
+import synth
+
+
+def cuda_ok():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+def to_dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_event(g, x, y, z, cap):
+    """The four calls of the path on one event; results as numpy arrays."""
+    import torch
+    from paper_1309_6275_gb300 import ht
+    G = ht.Geometry(g)
+    p = ht.EventPipeline(G, max(len(x), 1), cap)
+    p.run(to_dev(x), to_dev(y), to_dev(z))
+    torch.cuda.synchronize()
+    r = p.results(len(x))
+    G.close()
+    return r
+
+
+@functools.lru_cache(maxsize=8)
+def oracle_event(name, seed, threshold=None):
+    """Cached oracle run of a generated event: (event, geometry, results)."""
+    g = synth.geometry_of(name)
+    if threshold is not None:
+        g["threshold"] = threshold
+    ev = synth.make_event(synth.CONFIGS[name]["gen"], seed)
+    acc, st = oracle.vote(g, ev.x, ev.y)
+    pk, cnt = oracle.peaks(g, acc)
+    return ev, g, dict(acc=acc, stats=st, peaks=pk, count=cnt)
+
+
+def assert_same_acc(gpu_acc, ora_acc):
+    a = np.asarray(gpu_acc).astype(np.int64)
+    b = np.asarray(ora_acc).astype(np.int64)
+    assert a.shape == b.shape
+    bad = np.argwhere(a != b)
+    assert bad.shape[0] == 0, (f"{bad.shape[0]} cells differ; first {bad[:5].tolist()} "
+                               f"gpu {a[tuple(bad[:5].T)].tolist()} oracle {b[tuple(bad[:5].T)].tolist()}")

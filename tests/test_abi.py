@@ -1,0 +1,62 @@
+"""The C-ABI library builds, loads and exports every symbol include/ht.h
+declares (no compute call: this runs without a GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    syms = set()
+    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if name.endswith(".h"):
+            hdr = open(os.path.join(ROOT, "include", name)).read()
+            syms |= set(re.findall(r"^(?:ht_status|size_t|const char \*)\s*\**\s*(ht_\w+)\(",
+                                   hdr, re.M))
+    return syms
+
+
+def test_header_declares_the_path():
+    syms = declared_symbols()
+    for s in ("ht_geometry_create", "ht_geometry_destroy", "ht_vote", "ht_find_peaks",
+              "ht_associate", "ht_vote_z", "ht_last_error", "ht_run_event"):
+        assert s in syms
+
+
+def test_library_exports_every_declared_symbol():
+    from paper_1309_6275_gb300 import build
+    try:
+        path = build.build()
+    except (OSError, RuntimeError) as e:      # no nvcc on this machine
+        pytest.skip(f"cannot build libht here: {e}")
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (ht_\w+)$", out, re.M))
+    missing = declared_symbols() - exported
+    assert not missing, f"declared but not exported: {missing}"
+    lib = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert hasattr(lib, s)
+
+
+def test_binding_signatures_cover_the_header():
+    from paper_1309_6275_gb300 import ht
+    assert {n for n, _, _ in ht.SIGNATURES} == declared_symbols()
+
+
+def test_create_rejects_bad_geometry_without_touching_the_gpu():
+    """Argument checks come before any CUDA call."""
+    from paper_1309_6275_gb300 import ht
+    try:
+        lib = ht.lib()
+    except Exception as e:
+        pytest.skip(f"cannot load libht here: {e}")
+    d = ht._Desc(64, 64, 60, 128, 128, 7, 32, 0, 0.01, 10.0, 32.0, 6.5)   # n_phi0 % 8 != 0
+    h = ctypes.c_void_p()
+    assert lib.ht_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1
+    assert b"unsupported" in lib.ht_last_error()
+    assert lib.ht_geometry_create(None, ctypes.byref(h)) == 1

@@ -167,3 +167,18 @@ def test_z_vote_of_a_straight_track():
     zr = oracle.vote_z(g, x, y, z, np.zeros(len(x), np.int32),
                        np.array([[i, j, k, len(x)]], np.int32))
     assert zr.tolist() == [[nz, q, len(x)]]
+
+
+@pytest.mark.parametrize("name,stride", [("single_64", 1), ("event100_256", 400)])
+def test_dense_association_route_agrees(name, stride):
+    """The full-size route (each hit's votes against a cell -> candidate map)
+    and the per-candidate 9-column route give the same assignment."""
+    g = synth.geometry_of(name)
+    ev = synth.make_event(synth.CONFIGS[name]["gen"], 2)
+    acc, _ = oracle.vote(g, ev.x, ev.y)
+    pk, _ = oracle.peaks(g, acc)
+    sel = np.arange(0, ev.n_hits, stride)
+    a = oracle.associate(g, ev.x, ev.y, pk, hit_idx=sel)
+    b = oracle.associate_dense(g, ev.x, ev.y, pk, hit_idx=sel)
+    assert np.array_equal(a, b)
+    assert (a >= 0).mean() > 0.2
