@@ -190,7 +190,7 @@ def run_ours(args):
 
     vote_t0 = [torch.cuda.Event(enable_timing=True) for _ in events]
     vote_t1 = [torch.cuda.Event(enable_timing=True) for _ in events]
-    votes_dev = torch.zeros(len(events), dtype=torch.int64, device="cuda")
+    votes_dev = torch.zeros((len(events), 2), dtype=torch.int64, device="cuda")
 
     def step(timed_vote=False):
         for e, (x, y, z) in enumerate(dev_hits):
@@ -199,7 +199,7 @@ def run_ours(args):
             ht.ht_vote(G, x, y, pipe.acc, pipe.stats)
             if timed_vote:
                 vote_t1[e].record(stream)
-                votes_dev[e] = pipe.stats[0]
+                votes_dev[e] = pipe.stats
             ht.ht_find_peaks(G, pipe.acc, pipe.peaks, CAP, pipe.count, pipe.workspace)
             n = x.numel()
             ht.ht_associate(G, x, y, pipe.peaks, pipe.count, CAP, pipe.assign[:n], pipe.workspace)
@@ -218,6 +218,7 @@ def run_ours(args):
         clocks.start()
     step_ms, vote_ms = [], []
     votes_total = 0
+    redo_total = 0
     for s in range(args.steps):
         flush.fill_(s & 0xff)                          # evict L2 before the step
         a = torch.cuda.Event(enable_timing=True)
@@ -228,7 +229,9 @@ def run_ours(args):
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
         vote_ms.append(sum(vote_t0[e].elapsed_time(vote_t1[e]) for e in range(len(events))))
-        votes_total += int(votes_dev.sum().item())
+        vsum = votes_dev.sum(0).tolist()
+        votes_total += int(vsum[0])
+        redo_total += int(vsum[1])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -292,6 +295,7 @@ def run_ours(args):
             "peak_source": "measured here: conflict-free shared atomicAdd microbenchmark "
                            "(ht_probe_shared_atomic_rate)",
             "vote_kernel_ms_per_event": 1e3 * vote_s / (args.steps * n_ev),
+            "float64_redo_per_vote": redo_total / max(votes_total, 1),
             "vote_share_of_step": vote_s / total_s,
             "hbm_gbs_measured": peaks.get("hbm_gbs")}
     line = {

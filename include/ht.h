@@ -105,9 +105,9 @@ size_t ht_accumulator_bytes(const ht_geometry *g);
  *   n_hits    >= 0 (0 writes an all-zero accumulator).
  *   acc       accumulator (device, 16-byte aligned, ht_accumulator_bytes);
  *             every cell is written, so it needs no clearing.
- *   stats     NULL or 3 device uint64: votes cast, cells redone in float64,
- *             votes whose bin coordinate lies within 1e-5 of an edge.  The
- *             call zeroes them first.
+ *   stats     NULL or 2 device uint64: votes cast, and (hit, row, column)
+ *             evaluations redone in float64 because float32 could not prove
+ *             their bins.  The call zeroes them first.
  * Errors: HT_ERR_ARG (null pointer with n_hits > 0, misalignment, n_hits < 0),
  * HT_ERR_CUDA. */
 ht_status ht_vote(const ht_geometry *g, const float *x, const float *y,
@@ -175,7 +175,7 @@ ht_status ht_vote_z(const ht_geometry *g, const float *x, const float *y,
  *                assignments, z results and scratch).
  *   h_peaks      host, cap entries; h_count host int32 (total peaks);
  *   h_assign     host, n_hits; h_zres host, cap entries;
- *   h_stats      host, 3 uint64 (may be NULL).
+ *   h_stats      host, 2 uint64 as ht_vote's stats (may be NULL).
  * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
 size_t ht_event_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap);
 ht_status ht_run_event(const ht_geometry *g, const float *hx, const float *hy,

@@ -97,9 +97,10 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     }
     for (int i = 0; i < NR; ++i) rho[i] = (double)(2 * i + 1 - NR) * (d->rho_max / (double)NR);
 
-    // one device block: float64 sn, cs, rho | float32 sn, cs, phi, rho, 1/rho
+    // one device block: float64 sn, cs, rho | float32 sn, cs, phi, rho, 1/rho,
+    // and the float32 remainders sn - (float)sn, cs - (float)cs, rho - (float)rho
     const size_t b64 = sizeof(double) * (2 * (size_t)NP + NR);
-    const size_t b32 = sizeof(float) * (3 * (size_t)NP + 2 * (size_t)NR);
+    const size_t b32 = sizeof(float) * (5 * (size_t)NP + 3 * (size_t)NR);
     const size_t bytes = ht::align256(b64) + ht::align256(b32);
     char *h = new char[bytes];
     memset(h, 0, bytes);
@@ -117,6 +118,12 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
         h32[3 * NP + i] = (float)rho[i];
         h32[3 * NP + NR + i] = rho[i] != 0.0 ? (float)(1.0 / rho[i]) : 0.0f;
     }
+    float *hlo = h32 + 3 * NP + 2 * NR;
+    for (int k = 0; k < NP; ++k) {
+        hlo[k] = (float)(sn[k] - (double)(float)sn[k]);
+        hlo[NP + k] = (float)(cs[k] - (double)(float)cs[k]);
+    }
+    for (int i = 0; i < NR; ++i) hlo[2 * NP + i] = (float)(rho[i] - (double)(float)rho[i]);
     e = cudaMalloc(&g->d_tables, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_tables, h, bytes, cudaMemcpyHostToDevice);
     delete[] phi; delete[] sn; delete[] cs; delete[] rho; delete[] h;
@@ -136,16 +143,20 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     G.off = (double)ND * 0.5 + 0.5;
     G.delta_f = (float)G.delta;
     G.inv_delta_f = (float)(1.0 / G.delta);
+    G.inv_delta_lo = (float)(1.0 / G.delta - (double)G.inv_delta_f);
     G.off_f = (float)G.off;
     G.d0lo_f = (float)(-G.off * G.delta) - 0.01f;
     G.d0hi_f = (float)(((double)ND - G.off) * G.delta) + 0.01f;
     G.err_scale = (float)(ht::kSafe * (double)ht::kEps / G.delta);
+    G.dext_f = (float)((G.off + 0.5) * G.delta * 1.0001 + 0.01);
+    G.e3 = G.err_scale * 6.0f * G.dext_f + ht::kSafe * ht::kEps * (float)(ND + 1);
     G.rho_max_f = (float)d->rho_max * 1.0001f;
     G.drho_f = (float)(2.0 * d->rho_max / (double)NR);
     G.dmax_f = (float)(G.off * G.delta) + 0.01f;
     G.sn64 = d64; G.cs64 = d64 + NP; G.rho64 = d64 + 2 * NP;
     G.sn32 = d32; G.cs32 = d32 + NP; G.phi32 = d32 + 2 * NP;
     G.rho32 = d32 + 3 * NP; G.invrho32 = d32 + 3 * NP + NR;
+    G.snlo = d32 + 3 * NP + 2 * NR; G.cslo = G.snlo + NP; G.rholo = G.cslo + NP;
     G.dz = 2.0 * d->z0_max / (double)d->n_z0;
     G.z0_max = d->z0_max;
     G.cstep = d->cot_max / (double)d->n_cot;
@@ -196,7 +207,7 @@ ht_status ht_vote(const ht_geometry *g, const float *x, const float *y, int32_t 
     if (!aligned(acc, 16) || (x && !aligned(x, 16)) || (y && !aligned(y, 16)))
         return fail(HT_ERR_ARG, "ht_vote: pointers must be 16-byte aligned");
     cudaError_t e = cudaSuccess;
-    if (stats) e = cudaMemsetAsync(stats, 0, 3 * sizeof(uint64_t), S(stream));
+    if (stats) e = cudaMemsetAsync(stats, 0, 2 * sizeof(uint64_t), S(stream));
     if (e == cudaSuccess)
         e = ht::launch_vote(g->G, x, y, n_hits, acc,
                             reinterpret_cast<unsigned long long *>(stats), S(stream));
@@ -355,7 +366,7 @@ ht_status ht_run_event(const ht_geometry *g, const float *hx, const float *hy, c
                   w.scratch_bytes, stream);
     if (s != HT_OK) return s;
     HT_TRY(cudaMemcpyAsync(h_count, w.count, 4, cudaMemcpyDeviceToHost, st));
-    if (h_stats) HT_TRY(cudaMemcpyAsync(h_stats, w.stats, 24, cudaMemcpyDeviceToHost, st));
+    if (h_stats) HT_TRY(cudaMemcpyAsync(h_stats, w.stats, 16, cudaMemcpyDeviceToHost, st));
     if (n_hits > 0) HT_TRY(cudaMemcpyAsync(h_assign, w.assign, hb, cudaMemcpyDeviceToHost, st));
     HT_TRY(cudaStreamSynchronize(st));
     const int32_t np = *h_count < cap ? *h_count : cap;

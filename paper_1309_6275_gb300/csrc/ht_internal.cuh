@@ -21,10 +21,14 @@ struct DevGeom {
     float delta_f, inv_delta_f, off_f;
     float d0lo_f, d0hi_f;          // axis limits extended by 0.01 cm (filters only)
     float err_scale;               // SAFE * 2^-24 / delta
+    float dext_f;                  // |d0| of any root within half a bin of the axis, + margin
+    float e3;                      // geometry part of the root bounds, in bins
     float rho_max_f, drho_f, dmax_f; // |rho| bound, row width, max |d0| (filters)
     // tables (device)
     const float *sn32, *cs32, *phi32, *rho32, *invrho32;
     const double *sn64, *cs64, *rho64;
+    const float *snlo, *cslo, *rholo;  // float64 value - float32 table, as float32
+    float inv_delta_lo;                // 1/delta - inv_delta_f
     // z vote
     double dz, z0_max, cstep;      // dz = 2 z0_max / n_z0, cstep = cot_max / n_cot
     float inv_dz_f, z0_max_f, cstep_f;
@@ -41,7 +45,7 @@ constexpr double kHalfPi = 1.5707963267948966;
 // intrinsics forbid contraction into FMA).  Writes the in-range bins to j[]
 // and returns their number; *n_edge counts bin coordinates within 1e-5 of an
 // integer.
-__device__ __forceinline__ int cell_bins64(const DevGeom &G, float xf, float yf,
+static __device__ __noinline__ int cell_bins64(const DevGeom &G, float xf, float yf,
                                            int i, int k, int j[2], int *n_edge)
 {
     const double x = (double)xf, y = (double)yf;
@@ -75,74 +79,104 @@ __device__ __forceinline__ int cell_bins64(const DevGeom &G, float xf, float yf,
 }
 
 // ---------------------------------------------------------------------------
-// Guarded float32 evaluation of one column for a hit with s, c (c proven > 0
-// by the caller), r2 = x^2 + y^2 and R1 = |x| + |y|, at row curvature rho
-// (arho = |rho|, ainvrho = |1/rho|, has_b = rho != 0).
+// Guarded float32 evaluation of one (hit, rho row, phi0 column).
 //
-// First-order error bounds (unit roundoff u = 2^-24, rsqrtf <= 2 ulp):
-//   |ds|, |dc| <= 3u R1;  |db| <= u (4|rho|R1 + |b|);
-//   |dD| <= u (10 |rho|R1 |rho c| + |D|);
-//   |dq| <= u Q,  Q = 4|rho|R1 + 2|q| + 5 + (5 (rho R1)^2 + 1/2) / sqrt(D);
-//   root A = C / q:  |d dA| <= u (|1/q| (3|rho| r2 + 6 R1 + |dA| Q) + 4|dA|);
-//   root B = q / rho: |d dB| <= u (|1/rho| Q + 4|dB|);
-// each scaled by kSafe and divided by delta to give bins, plus u|u| for the
-// final fused multiply-add.  A root is decided here only if its coordinate
-// is farther than its bound from every integer (a range edge included) or
-// certainly outside [0, n_d0); D only if |D| exceeds its bound.
-// Returns true when decided: jA, jB = bin or -1, *n_edge updated.  Returns
-// false when the column must be redone by cell_bins64.
-__device__ __forceinline__ bool cell_bins32(const DevGeom &G, float rho, float arho,
-                                            float invrho, float ainvrho, bool has_b,
-                                            float s, float c, float r2, float R1,
-                                            int &jA, int &jB, int &n_edge)
+// First-order error bounds, unit roundoff u = 2^-24 (the approximate MUFU
+// reciprocal and reciprocal square root add <= 2u and <= 4.3u relative):
+//   |ds|, |dc| <= 3u R1  (R1 = |x| + |y|);   |dD| <= u (10 (rho R1)^2 + 1);
+//   |dq| <= u (Qa + Qb / sqrt(D)),  Qa = 6|rho|R1 + 9,  Qb = 5 (rho R1)^2 + 1/2;
+//   root A = C / q:  |d dA| <= u (|1/q| (3|rho| r2 + 6 R1 + |dA| (Qa + Qb/sqrt D)) + 6 |dA|);
+//   root B = q / rho: |d dB| <= u (|1/rho| (Qa + Qb/sqrt D) + 6 |dB|).
+// Each is scaled by kSafe and divided by delta (bins), plus u|u| for the
+// final fused multiply-add.  With |rho| bounded by the tile's largest and
+// |d0| by dext (a root within half a bin of the axis), the bounds reduce to
+//   eA = |1/q| (E1 + E2 / sqrt D) + E3,   eB = |1/rho| err_scale (Qa + Qb / sqrt D) + E3
+// with E1, E2 (and Qa, Qb, the D bound eD) constant per (hit, column) item
+// and E3 constant per geometry.  A root is decided here only if its bound is
+// below 1/4 bin and its coordinate is farther than the bound from every
+// integer (range edges included) or more than half a bin outside the axis;
+// otherwise the whole column is redone by cell_bins64.
+struct Item {
+    float s, c, r2, eD;    // hit geometry in this column; D bound
+    float E1, E2, Qa, Qb;  // root-A bound constants; root-B constants (scaled)
+};
+
+enum : int { kDecided = 0, kRedo = 1 };
+
+__device__ __forceinline__ float rcp_approx(float v)
+{
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+__device__ __forceinline__ float rsqrt_approx(float v)
+{
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+
+// Bin of a root with coordinate u and bound e: j >= 0 (vote), -1 (certainly
+// outside the axis) or -2 (undecided: redo in float64).
+__device__ __forceinline__ int decide(float u, float e, float nd)
+{
+    if (!(e < 0.25f)) return -2;
+    if (u < -0.5f || u >= nd + 0.5f) return -1;
+    const float f = floorf(u);
+    const float fr = u - f;
+    if (!(fminf(fr, 1.0f - fr) > e)) return -2;
+    return (f >= 0.0f && f < nd) ? (int)f : -1;
+}
+
+// Returns kDecided with jA, jB (bin or -1) or kRedo.
+__device__ __forceinline__ int eval32(const DevGeom &G, float rho, float invrho_es,
+                                      float invrho, bool need_b, const Item &it, int &jA,
+                                      int &jB)
 {
     jA = -1;
     jB = -1;
-    const float b = fmaf(rho, s, 1.0f);
-    const float pc = rho * c;
+    const float b = fmaf(rho, it.s, 1.0f);
+    const float pc = rho * it.c;
     const float D = fmaf(-pc, pc, 1.0f);
-    const float P1 = arho * R1;
-    const float eD = (kSafe * kEps) * fmaf(10.0f * P1, fabsf(pc), fabsf(D) + 1.0f);
-    if (D < -eD) return true;          // certainly no real root
-    if (D <= eD) return false;         // tangent within error: exact path
-    const float rs = rsqrtf(D);
+    if (D <= it.eD) return D < -it.eD ? kDecided : kRedo;
+    const float rs = rsqrt_approx(D);
     const float sq = D * rs;
     const float q = -(b + copysignf(sq, b));
-    const float C = fmaf(rho, r2, 2.0f * s);
-    const float iq = __frcp_rn(q);
-    const float Q = fmaf(fmaf(5.0f * P1, P1, 0.5f), rs, fmaf(2.0f, fabsf(q), fmaf(4.0f, P1, 5.0f)));
+    const float C = fmaf(rho, it.r2, it.s + it.s);
+    const float iq = rcp_approx(q);
     const float nd = (float)G.n_d0;
-    // root A
-    const float dA = C * iq;
-    const float uA = fmaf(dA, G.inv_delta_f, G.off_f);
-    const float eA = fmaf(fmaf(fabsf(iq), fmaf(fabsf(dA), Q, fmaf(3.0f * arho, r2, 6.0f * R1)),
-                               4.0f * fabsf(dA)),
-                          G.err_scale, (kSafe * kEps) * fabsf(uA));
-    const bool outA = (uA + eA < 0.0f) || (uA - eA >= nd);
-    const float fA = floorf(uA);
-    const float frA = uA - fA;
-    const float dist_A = fminf(frA, 1.0f - frA);
-    if (!outA) {
-        if (!(dist_A > eA)) return false;
-        jA = (int)fA;
-        n_edge += dist_A < 1e-5f;
+    const float uA = fmaf(C * iq, G.inv_delta_f, G.off_f);
+    const float eA = fmaf(fabsf(iq), fmaf(it.E2, rs, it.E1), G.e3);
+    jA = decide(uA, eA, nd);
+    if (jA == -2) return kRedo;
+    if (need_b) {
+        const float uB = fmaf(q * invrho, G.inv_delta_f, G.off_f);
+        const float eB = fmaf(invrho_es, fmaf(it.Qb, rs, it.Qa), G.e3);
+        jB = decide(uB, eB, nd);
+        if (jB == -2) return kRedo;
     }
-    if (has_b) {
-        const float dB = q * invrho;
-        const float uB = fmaf(dB, G.inv_delta_f, G.off_f);
-        const float eB = fmaf(fmaf(ainvrho, Q, 4.0f * fabsf(dB)), G.err_scale,
-                              (kSafe * kEps) * fabsf(uB));
-        const bool outB = (uB + eB < 0.0f) || (uB - eB >= nd);
-        if (!outB) {
-            const float fB = floorf(uB);
-            const float frB = uB - fB;
-            const float dist_B = fminf(frB, 1.0f - frB);
-            if (!(dist_B > eB)) return false;
-            jB = (int)fB;
-            n_edge += dist_B < 1e-5f;
-        }
-    }
-    return true;
+    return kDecided;
+}
+
+// Per-(hit, column) constants for eval32; rt = largest |rho| of the tile.
+__device__ __forceinline__ Item make_item(const DevGeom &G, float s, float c, float r2,
+                                          float R1, float rt)
+{
+    Item it;
+    it.s = s;
+    it.c = c;
+    it.r2 = r2;
+    const float P = rt * R1;
+    const float Qa = fmaf(6.0f, P, 9.0f);
+    const float Qb = fmaf(5.0f * P, P, 0.5f);
+    it.eD = (kSafe * kEps) * fmaf(10.0f * P, P, 2.0f);
+    const float Ea = fmaf(3.0f * rt, r2, 6.0f * R1);
+    it.E1 = G.err_scale * fmaf(G.dext_f, Qa, Ea);
+    it.E2 = G.err_scale * G.dext_f * Qb;
+    it.Qa = Qa;
+    it.Qb = Qb;
+    return it;
 }
 
 // ---------------------------------------------------------------------------
@@ -235,5 +269,9 @@ cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, cons
 size_t vote_z_workspace_bytes(const DevGeom &G, int n, int cap);
 
 inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+size_t scan_tmp_bytes(int n_cap);
+cudaError_t scan_exclusive(const int *in, int *out, int *out2, int n_cap, const int *d_n,
+                           int *total, void *tmp, cudaStream_t st);
 
 }  // namespace ht

@@ -12,7 +12,7 @@
 //    wraps.
 //  * Compaction keeps increasing logical index l = (i n_d0 + j) n_phi0 + k:
 //    pass 1 counts the peaks of every (i, j, k-block) segment, a
-//    single-CTA scan turns counts into offsets (and the total), pass 2
+//    device-wide scan turns counts into offsets (and the total), pass 2
 //    recomputes and writes each peak at its segment offset plus its rank in
 //    the CTA (warp ballots + a per-warp prefix).  Segments are ordered by l,
 //    so the output is too.
@@ -26,7 +26,6 @@ namespace {
 
 constexpr int kPkThreads = 256;   // phi0 columns per CTA
 constexpr int kJB = 16;           // d0 bins walked per CTA
-constexpr int kScanThreads = 1024;
 
 template <typename T, bool WRITE>
 __global__ void __launch_bounds__(kPkThreads)
@@ -99,41 +98,16 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
     }
 }
 
-// Exclusive scan of cnt[0..n) into off[0..n) with one CTA; *total = sum.
-__global__ void __launch_bounds__(kScanThreads)
-k_scan(const int *__restrict__ cnt, int *__restrict__ off, int n, int *__restrict__ total)
-{
-    __shared__ int part[kScanThreads];
-    const int per = (n + kScanThreads - 1) / kScanThreads;
-    const int a = min(n, threadIdx.x * per), b = min(n, a + per);
-    int s = 0;
-    for (int t = a; t < b; ++t) s += cnt[t];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int run = part[threadIdx.x] - s;
-    for (int t = a; t < b; ++t) {
-        const int c = cnt[t];
-        off[t] = run;
-        run += c;
-    }
-    if (threadIdx.x == kScanThreads - 1) *total = part[kScanThreads - 1];
-}
-
 template <typename T>
 cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, int *d_count,
-                      int *segcnt, int *segoff, cudaStream_t st)
+                      int *segcnt, int *segoff, void *tmp, cudaStream_t st)
 {
     const int nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     dim3 grid(nkb, (G.n_d0 + kJB - 1) / kJB, G.n_rho);
     const int nseg = G.n_rho * G.n_d0 * nkb;
     k_peaks<T, false><<<grid, kPkThreads, 0, st>>>(G, acc, segcnt, nullptr, nullptr, 0);
-    k_scan<<<1, kScanThreads, 0, st>>>(segcnt, segoff, nseg, d_count);
+    cudaError_t e = scan_exclusive(segcnt, segoff, nullptr, nseg, nullptr, d_count, tmp, st);
+    if (e != cudaSuccess) return e;
     k_peaks<T, true><<<grid, kPkThreads, 0, st>>>(G, acc, nullptr, segoff, peaks, cap);
     return cudaGetLastError();
 }
@@ -144,7 +118,7 @@ size_t peaks_workspace_bytes(const DevGeom &G)
 {
     const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     const size_t nseg = (size_t)G.n_rho * G.n_d0 * nkb;
-    return 2 * align256(nseg * 4);
+    return 2 * align256((nseg + 1) * 4) + scan_tmp_bytes((int)nseg);
 }
 
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
@@ -152,13 +126,15 @@ cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int 
 {
     const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     const size_t nseg = (size_t)G.n_rho * G.n_d0 * nkb;
-    int *segcnt = reinterpret_cast<int *>(ws);
-    int *segoff = reinterpret_cast<int *>(reinterpret_cast<char *>(ws) + align256(nseg * 4));
+    char *p = reinterpret_cast<char *>(ws);
+    int *segcnt = reinterpret_cast<int *>(p);
+    int *segoff = reinterpret_cast<int *>(p + align256((nseg + 1) * 4));
+    void *tmp = p + 2 * align256((nseg + 1) * 4);
     if (G.count_bits == 16)
         return run_peaks(G, reinterpret_cast<const uint16_t *>(acc), peaks, cap, d_count, segcnt,
-                         segoff, st);
+                         segoff, tmp, st);
     return run_peaks(G, reinterpret_cast<const int32_t *>(acc), peaks, cap, d_count, segcnt,
-                     segoff, st);
+                     segoff, tmp, st);
 }
 
 }  // namespace ht

@@ -4,22 +4,22 @@
 //
 // Design (GB300):
 //  * One CTA owns a parameter-space tile of 32 rho rows x KT phi0 columns x
-//    all n_d0 bins, held in shared memory: uint32 vote counters for the
-//    vote, the best candidate key per cell for the association.  Rows are
-//    padded to n_d0 + 1 words, so 32 rows at the same d0 bin fall in 32
-//    different banks.
+//    all n_d0 bins, held in shared memory row-fastest ([column][d0][row]):
+//    uint32 vote counters for the vote, candidate keys for the association.
+//    Lane = row, so a warp's 32 shared accesses always fall in 32 distinct
+//    banks whatever d0 bins the rows hit.
 //  * The CTA streams the hits in chunks of blockDim.  Phase 1 (one thread per
 //    hit): an angular window and a curvature-range test select the (hit,
-//    column) pairs that can vote in the tile; survivors are appended to a
-//    shared work list with one atomic per warp (warp-aggregated append).
-//    Phase 2 (one warp per item): lane = rho row, so the 32 atomics a warp
-//    issues hit 32 distinct cells in 32 distinct banks.
-//  * Arithmetic: guarded float32 (cell_bins32); every column it cannot prove
-//    is redone in float64 in the definition's order (cell_bins64), so the
-//    votes are bit-identical to the float64 definition.  The work is integer
+//    column) pairs that can vote in the tile, and compute each pair's error
+//    bound constants once; survivors are appended to a shared work list with
+//    one atomic per warp (warp-aggregated append).  Phase 2 (one warp per
+//    item): lane = rho row evaluates its root(s) with eval32.
+//  * Arithmetic: guarded float32 (eval32); every column it cannot prove is
+//    redone in float64 in the definition's order (cell_bins64), so the votes
+//    are bit-identical to the float64 definition.  The work is integer
 //    counting: no tensor cores.
-//  * Vote write-back stores every cell once, saturated, with vector stores:
-//    the accumulator needs no clearing and crosses HBM once.
+//  * Vote write-back stores every cell once, saturated, so the accumulator
+//    needs no clearing and crosses HBM once.
 //  * Association: each tile first scatters the candidates whose 3x3x3 box
 //    meets it into the tile (atomicMax of key = count << 32 | ~m), then
 //    replays the vote and takes, per hit, the maximum key over the cells it
@@ -27,20 +27,13 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df32.cuh"
 #include "ht_internal.cuh"
 
 namespace ht {
 namespace {
 
 constexpr int kThreads = 256;
-
-template <typename T, int KT>
-struct VecOf;  // KT counts of type T as one aligned store
-template <> struct VecOf<uint16_t, 2> { using type = uint32_t; };
-template <> struct VecOf<uint16_t, 4> { using type = uint2; };
-template <> struct VecOf<uint16_t, 8> { using type = uint4; };
-template <> struct VecOf<int32_t, 2> { using type = uint2; };
-template <> struct VecOf<int32_t, 4> { using type = uint4; };
 
 template <typename OutT>
 __device__ __forceinline__ OutT saturate(uint32_t v)
@@ -49,20 +42,21 @@ __device__ __forceinline__ OutT saturate(uint32_t v)
     return (OutT)(v > 2147483647u ? 2147483647u : v);
 }
 
-// Shared work list of (hit, column) items, structure of arrays.
+// Shared work list of (hit, column) items.
 struct WorkList {
-    float *s, *c, *r2, *R1;
-    int *meta;          // hit << 6 | unsure << 5 | column-in-tile
+    float4 *a, *b;   // Item fields {s, c, r2, eD}, {E1, E2, Qa, Qb}
+    int *meta;       // hit << 6 | needB << 5 | unsure << 4 | column-in-tile
 };
+
+constexpr int kMetaUnsure = 16, kMetaNeedB = 32, kMetaCol = 15;
+constexpr size_t kItemBytes = 36;
 
 __device__ __forceinline__ WorkList carve_worklist(unsigned char *p, int cap)
 {
     WorkList w;
-    w.s = reinterpret_cast<float *>(p);
-    w.c = w.s + cap;
-    w.r2 = w.c + cap;
-    w.R1 = w.r2 + cap;
-    w.meta = reinterpret_cast<int *>(w.R1 + cap);
+    w.a = reinterpret_cast<float4 *>(p);
+    w.b = w.a + cap;
+    w.meta = reinterpret_cast<int *>(w.b + cap);
     return w;
 }
 
@@ -71,7 +65,7 @@ template <int KT>
 struct TileCtx {
     int i0, k0, irow;
     bool row_ok, has_b;
-    float rho, invrho, arho, ainvrho, rho_lo, rho_hi;
+    float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB;
     float sk[KT], ck[KT], pk[KT];
 
     __device__ __forceinline__ void init(const DevGeom &G, int lane)
@@ -83,11 +77,14 @@ struct TileCtx {
         rho = row_ok ? G.rho32[irow] : 0.0f;
         invrho = row_ok ? G.invrho32[irow] : 0.0f;
         has_b = row_ok && (G.rho64[irow] != 0.0);
-        arho = fabsf(rho);
-        ainvrho = fabsf(invrho);
+        invrho_es = fabsf(invrho) * G.err_scale;
         const int ilast = min(i0 + 31, G.n_rho - 1);
         rho_lo = G.rho32[i0] - G.drho_f;
         rho_hi = G.rho32[ilast] + G.drho_f;
+        rt = fmaxf(fabsf(G.rho32[i0]), fabsf(G.rho32[ilast])) * 1.0001f;
+        // the second root q / rho can reach the axis only if |1 + rho s| <=
+        // |rho| dext, i.e. |s| >= 1 / rt - dext for the rows of this tile
+        sB = rt > 0.0f ? __frcp_rn(rt) - G.dext_f - 0.01f : 3.0e38f;
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
             sk[kl] = G.sn32[k0 + kl];
@@ -106,7 +103,8 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
                                         int lane, int *qn, const WorkList &W)
 {
     float is_[KT], ic_[KT];
-    unsigned sel = 0u, unsure = 0u;
+    int fl_[KT];
+    unsigned sel = 0u;
     float r2 = 0.0f, R1 = 0.0f;
     if (h < n) {
         const float xh = x[h], yh = y[h];
@@ -121,14 +119,17 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
             const float s = fmaf(xh, T.sk[kl], -(yh * T.ck[kl]));
             const float c = fmaf(xh, T.ck[kl], yh * T.sk[kl]);
             if (c < -Ec) continue;
+            int f = 0;
             if (c <= Ec) {
-                unsure |= 1u << kl;
+                f |= kMetaUnsure;
             } else if (c > 1.0f) {
                 float gmin, gmax;
                 rho_range(G, s, c, gmin, gmax);
                 if (gmax < T.rho_lo || gmin > T.rho_hi) continue;
             }
+            if (fabsf(s) >= T.sB) f |= kMetaNeedB;
             sel |= 1u << kl;
+            fl_[kl] = f;
             is_[kl] = s;
             ic_[kl] = c;
         }
@@ -147,37 +148,61 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
 #pragma unroll
     for (int kl = 0; kl < KT; ++kl) {
         if (sel & (1u << kl)) {
-            W.s[pos] = is_[kl];
-            W.c[pos] = ic_[kl];
-            W.r2[pos] = r2;
-            W.R1[pos] = R1;
-            W.meta[pos] = (h << 6) | (int)(((unsure >> kl) & 1u) << 5) | kl;
+            const Item it = make_item(G, is_[kl], ic_[kl], r2, R1, T.rt);
+            W.a[pos] = make_float4(it.s, it.c, it.r2, it.eD);
+            W.b[pos] = make_float4(it.E1, it.E2, it.Qa, it.Qb);
+            W.meta[pos] = (h << 6) | fl_[kl] | kl;
             ++pos;
         }
     }
 }
 
-// Bins of item `it` for the lane's row: guarded float32, else float64.
+// Bins of work item t for the lane's row by guarded float32: the number of
+// bins written to jj, or -1 when the column must be redone in float64.
 template <int KT>
-__device__ __forceinline__ int item_bins(const DevGeom &G, const TileCtx<KT> &T,
-                                         const float *__restrict__ x,
-                                         const float *__restrict__ y, const WorkList &W,
-                                         int it, int jj[2], int &n_edge, int &n_fb)
+__device__ __forceinline__ int item_bins32(const DevGeom &G, const TileCtx<KT> &T,
+                                           const WorkList &W, int t, int m, int jj[2])
 {
-    const int m = W.meta[it];
-    if (!(m & 32)) {
-        int jA, jB;
-        if (cell_bins32(G, T.rho, T.arho, T.invrho, T.ainvrho, T.has_b, W.s[it], W.c[it],
-                        W.r2[it], W.R1[it], jA, jB, n_edge)) {
-            int nv = 0;
-            if (jA >= 0) jj[nv++] = jA;
-            if (jB >= 0) jj[nv++] = jB;
-            return nv;
-        }
-    }
-    ++n_fb;
-    const int hh = m >> 6;
-    return cell_bins64(G, x[hh], y[hh], T.irow, T.k0 + (m & 31), jj, &n_edge);
+    if (m & kMetaUnsure) return -1;
+    const float4 a = W.a[t], b = W.b[t];
+    const Item it{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+    int jA, jB;
+    if (eval32(G, T.rho, T.invrho_es, T.invrho, T.has_b && (m & kMetaNeedB), it, jA, jB) !=
+        kDecided)
+        return -1;
+    int nv = 0;
+    if (jA >= 0) jj[nv++] = jA;
+    if (jB >= 0) jj[nv++] = jB;
+    return nv;
+}
+
+// Deferred redo requests: (hit, row-in-tile, column) pairs whose bins
+// float32 could not prove.  Drained by all threads of the CTA at the end of
+// the tile (or when half full), through the double-float tier and, rarely,
+// float64 (slow on this part), so neither runs as a lone divergent lane.
+constexpr int kRedoCap = 1024;
+constexpr size_t kRedoBytes = (size_t)kRedoCap * 8;
+
+struct RedoQueue {
+    int *hit, *rc;   // rc = row << 4 | column
+};
+
+__device__ __forceinline__ RedoQueue carve_redo(unsigned char *p)
+{
+    RedoQueue q;
+    q.hit = reinterpret_cast<int *>(p);
+    q.rc = q.hit + kRedoCap;
+    return q;
+}
+
+// Push a redo request; false if the queue is full (caller redoes it now).
+__device__ __forceinline__ bool push_redo(const RedoQueue &Q, int *n, int hit, int row, int col)
+{
+    const int slot = atomicAdd(n, 1);
+    if (slot >= kRedoCap) return false;
+    Q.hit[slot] = hit;
+    Q.rc[slot] = (row << 4) | col;
+    return true;
 }
 
 // ------------------------------------------------------------------ vote
@@ -187,23 +212,31 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
        OutT *__restrict__ acc, unsigned long long *__restrict__ stats)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int ND = G.n_d0, NDP = ND + 1;
+    const int ND = G.n_d0;
     constexpr int QCAP = kThreads * KT;
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);
-    const WorkList W = carve_worklist(reinterpret_cast<unsigned char *>(cnt + KT * 32 * NDP), QCAP);
-    __shared__ int qn[2];
-    __shared__ unsigned long long s_stats[3];
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][ND][32]
+    unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * ND * 32);
+    const WorkList W = carve_worklist(p, QCAP);
+    const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
+    __shared__ int qn[2], rn;
+    __shared__ unsigned long long s_stats[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = kThreads / 32;
     TileCtx<KT> T;
     T.init(G, lane);
-    for (int t = threadIdx.x; t < KT * 32 * NDP; t += kThreads) cnt[t] = 0u;
-    if (threadIdx.x < 2) qn[threadIdx.x] = 0;
-    if (threadIdx.x < 3) s_stats[threadIdx.x] = 0ull;
+    {
+        uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
+        for (int t = threadIdx.x; t < KT * ND * 8; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
+    }
+    if (threadIdx.x < 2) {
+        qn[threadIdx.x] = 0;
+        s_stats[threadIdx.x] = 0ull;
+    }
+    if (threadIdx.x == 0) rn = 0;
     __syncthreads();
 
-    int my_votes = 0, my_fb = 0, my_edge = 0;
+    int my_votes = 0, my_fb = 0;
     int parity = 0;
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
         collect<KT>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W);
@@ -211,26 +244,60 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;   // last read before the previous barrier
         if (T.row_ok) {
-            for (int it = warp; it < nq; it += nwarps) {
-                uint32_t *col = cnt + ((W.meta[it] & 31) * 32 + lane) * NDP;
+            for (int t = warp; t < nq; t += nwarps) {
+                const int m = W.meta[t];
+                uint32_t *col = cnt + (m & kMetaCol) * ND * 32 + lane;
                 int jj[2];
-                const int nv = item_bins<KT>(G, T, x, y, W, it, jj, my_edge, my_fb);
-                for (int t = 0; t < nv; ++t) atomicAdd(col + jj[t], 1u);
+                int nv = item_bins32<KT>(G, T, W, t, m, jj);
+                if (nv < 0) {
+                    ++my_fb;
+                    if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
+                    nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                }
+                if (nv > 0) atomicAdd(col + jj[0] * 32, 1u);
+                if (nv > 1) atomicAdd(col + jj[1] * 32, 1u);
                 my_votes += nv;
             }
         }
         __syncthreads();
+        // drain the deferred redos when the queue is half full or at the end
+        const int nr = min(rn, kRedoCap);
+        if (nr >= kRedoCap / 2 || base + kThreads >= n) {
+            for (int t = threadIdx.x; t < nr; t += kThreads) {
+                const int h = R.hit[t], rc = R.rc[t];
+                const int il = rc >> 4, kl = rc & 15;
+                int jj[2];
+                const int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
+                uint32_t *col = cnt + kl * ND * 32 + il;
+                for (int v = 0; v < nv; ++v) atomicAdd(col + jj[v] * 32, 1u);
+                my_votes += nv;
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) rn = 0;
+        }
     }
+    __syncthreads();
 
-    using Vec = typename VecOf<OutT, KT>::type;
+    // write-back: thread = (row, d0 bin); the KT counts of a row go out as
+    // one vector of KT * sizeof(OutT) bytes
     for (int t = threadIdx.x; t < 32 * ND; t += kThreads) {
-        const int il = t / ND, j = t - il * ND;
+        const int il = t & 31, j = t >> 5;
         const int i = T.i0 + il;
-        if (i >= G.n_rho) break;
-        union { Vec v; OutT e[KT]; } u;
+        if (i >= G.n_rho) continue;
+        __align__(16) OutT e[KT];
 #pragma unroll
-        for (int kl = 0; kl < KT; ++kl) u.e[kl] = saturate<OutT>(cnt[(kl * 32 + il) * NDP + j]);
-        *reinterpret_cast<Vec *>(acc + ((size_t)i * ND + j) * G.n_phi0 + T.k0) = u.v;
+        for (int kl = 0; kl < KT; ++kl) e[kl] = saturate<OutT>(cnt[(kl * ND + j) * 32 + il]);
+        OutT *dst = acc + ((size_t)i * ND + j) * G.n_phi0 + T.k0;
+        if constexpr (KT * sizeof(OutT) == 16) {
+            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(e);
+        } else if constexpr (KT * sizeof(OutT) == 8) {
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(e);
+        } else if constexpr (KT * sizeof(OutT) == 4) {
+            *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(e);
+        } else {
+#pragma unroll
+            for (int kl = 0; kl < KT; ++kl) dst[kl] = e[kl];
+        }
     }
 
     if (stats) {
@@ -238,15 +305,13 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
         for (int o = 16; o > 0; o >>= 1) {
             my_votes += __shfl_xor_sync(0xffffffffu, my_votes, o);
             my_fb += __shfl_xor_sync(0xffffffffu, my_fb, o);
-            my_edge += __shfl_xor_sync(0xffffffffu, my_edge, o);
         }
         if (lane == 0) {
             atomicAdd(&s_stats[0], (unsigned long long)my_votes);
             atomicAdd(&s_stats[1], (unsigned long long)my_fb);
-            atomicAdd(&s_stats[2], (unsigned long long)my_edge);
         }
         __syncthreads();
-        if (threadIdx.x < 3) atomicAdd(&stats[threadIdx.x], s_stats[threadIdx.x]);
+        if (threadIdx.x < 2) atomicAdd(&stats[threadIdx.x], s_stats[threadIdx.x]);
     }
 }
 
@@ -271,21 +336,27 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
         unsigned long long *__restrict__ gbest)
 {
     extern __shared__ __align__(16) unsigned char smem[];
-    const int ND = G.n_d0, NDP = ND + 1, NP = G.n_phi0;
+    const int ND = G.n_d0, NP = G.n_phi0;
     constexpr int QCAP = kThreads * KT;
-    unsigned long long *map = reinterpret_cast<unsigned long long *>(smem);
-    unsigned long long *bestk = map + KT * 32 * NDP;
-    const WorkList W = carve_worklist(reinterpret_cast<unsigned char *>(bestk + kThreads), QCAP);
-    __shared__ int qn[2];
+    unsigned long long *map = reinterpret_cast<unsigned long long *>(smem);   // [KT][ND][32]
+    unsigned long long *bestk = map + KT * ND * 32;
+    unsigned char *p = reinterpret_cast<unsigned char *>(bestk + kThreads);
+    const WorkList W = carve_worklist(p, QCAP);
+    const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
+    __shared__ int qn[2], rn;
     __shared__ int band[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = kThreads / 32;
     TileCtx<KT> T;
     T.init(G, lane);
-    for (int t = threadIdx.x; t < KT * 32 * NDP; t += kThreads) map[t] = 0ull;
+    {
+        uint4 *m4 = reinterpret_cast<uint4 *>(map);
+        for (int t = threadIdx.x; t < KT * ND * 16; t += kThreads) m4[t] = make_uint4(0, 0, 0, 0);
+    }
     bestk[threadIdx.x] = 0ull;
     if (threadIdx.x < 2) qn[threadIdx.x] = 0;
+    if (threadIdx.x == 0) rn = 0;
     const int ncand = min(*d_count, cap);
     if (threadIdx.x == 0) {
         const int ib0 = max(T.i0 - 1, 0), ib1 = min(T.i0 + 32, G.n_rho - 1);
@@ -296,49 +367,62 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
 
     // scatter each candidate's 3x3x3 box into the tile
     for (int m = band[0] + threadIdx.x; m < band[1]; m += kThreads) {
-        const ht_peak p = peaks[m];
-        const unsigned long long key =
-            ((unsigned long long)(unsigned)p.count << 32) | (0xffffffffull - (unsigned)m);
+        const ht_peak pk = peaks[m];
+        int kls[3];
+        bool any = false;
 #pragma unroll
-        for (int dk = -1; dk <= 1; ++dk) {
-            int kk = p.k_phi0 + dk;
+        for (int d = 0; d < 3; ++d) {
+            int kk = pk.k_phi0 - 1 + d;
             kk += (kk < 0) ? NP : 0;
             kk -= (kk >= NP) ? NP : 0;
-            const int kl = kk - T.k0;
+            kls[d] = kk - T.k0;
+            any |= (kls[d] >= 0 && kls[d] < KT);
+        }
+        if (!any) continue;
+        const unsigned long long key =
+            ((unsigned long long)(unsigned)pk.count << 32) | (0xffffffffull - (unsigned)m);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const int kl = kls[d];
             if (kl < 0 || kl >= KT) continue;
             for (int di = -1; di <= 1; ++di) {
-                const int ii = p.i_rho + di, il = ii - T.i0;
+                const int ii = pk.i_rho + di, il = ii - T.i0;
                 if (il < 0 || il >= 32 || ii >= G.n_rho) continue;
                 for (int dj = -1; dj <= 1; ++dj) {
-                    const int jj = p.j_d0 + dj;
+                    const int jj = pk.j_d0 + dj;
                     if (jj < 0 || jj >= ND) continue;
-                    atomicMax(&map[(kl * 32 + il) * NDP + jj], key);
+                    atomicMax(&map[(kl * ND + jj) * 32 + il], key);
                 }
             }
         }
     }
     __syncthreads();
 
-    int my_edge = 0, my_fb = 0;
     int parity = 0;
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
         collect<KT>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W);
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;
-        for (int it = warp; it < nq; it += nwarps) {
+        for (int t = warp; t < nq; t += nwarps) {
+            const int m = W.meta[t];
             unsigned long long key = 0ull;
             if (T.row_ok) {
-                const unsigned long long *col = map + ((W.meta[it] & 31) * 32 + lane) * NDP;
+                const unsigned long long *col = map + (m & kMetaCol) * ND * 32 + lane;
                 int jj[2];
-                const int nv = item_bins<KT>(G, T, x, y, W, it, jj, my_edge, my_fb);
-                for (int t = 0; t < nv; ++t) key = max(key, col[jj[t]]);
+                int nv = item_bins32<KT>(G, T, W, t, m, jj);
+                if (nv < 0 && !push_redo(R, &rn, m >> 6, lane, m & kMetaCol))
+                    nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                if (nv > 0) key = col[jj[0] * 32];
+                if (nv > 1) key = max(key, col[jj[1] * 32]);
             }
-            if (__any_sync(0xffffffffu, key != 0ull)) {
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1)
-                    key = max(key, __shfl_xor_sync(0xffffffffu, key, o));
-                if (lane == 0 && key) atomicMax(&bestk[(W.meta[it] >> 6) - base], key);
+            // warp max of (count, -m): high word first, then low word among ties
+            const unsigned hi = __reduce_max_sync(0xffffffffu, (unsigned)(key >> 32));
+            if (hi) {
+                const unsigned lo = __reduce_max_sync(
+                    0xffffffffu, (unsigned)(key >> 32) == hi ? (unsigned)key : 0u);
+                if (lane == 0)
+                    atomicMax(&bestk[(m >> 6) - base], ((unsigned long long)hi << 32) | lo);
             }
         }
         __syncthreads();
@@ -347,6 +431,23 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
         if (b) {
             atomicMax(&gbest[base + threadIdx.x], b);
             bestk[threadIdx.x] = 0ull;
+        }
+        // drain the deferred redos when the queue is half full or at the end;
+        // their keys go straight to the global per-hit maximum
+        const int nr = min(rn, kRedoCap);
+        if (nr >= kRedoCap / 2 || base + kThreads >= n) {
+            for (int t = threadIdx.x; t < nr; t += kThreads) {
+                const int h = R.hit[t], rc = R.rc[t];
+                const int il = rc >> 4, kl = rc & 15;
+                int jj[2];
+                const int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
+                const unsigned long long *col = map + kl * ND * 32 + il;
+                unsigned long long key = 0ull;
+                for (int v = 0; v < nv; ++v) key = max(key, col[jj[v] * 32]);
+                if (key) atomicMax(&gbest[h], key);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) rn = 0;
         }
     }
 }
@@ -361,28 +462,28 @@ __global__ void k_assoc_final(const unsigned long long *__restrict__ gbest, int 
 }
 
 // ---------------------------------------------------------------- launch
-template <int KT, typename OutT>
+template <int KT>
 size_t vote_smem(const DevGeom &G)
 {
-    return (size_t)KT * 32 * (G.n_d0 + 1) * 4 + (size_t)kThreads * KT * 20;
+    return (size_t)KT * 32 * G.n_d0 * 4 + (size_t)kThreads * KT * kItemBytes + kRedoBytes;
 }
 
 template <int KT>
 size_t assoc_smem(const DevGeom &G)
 {
-    return (size_t)KT * 32 * (G.n_d0 + 1) * 8 + (size_t)kThreads * 8 + (size_t)kThreads * KT * 20;
+    return (size_t)KT * 32 * G.n_d0 * 8 + (size_t)kThreads * 8 + (size_t)kThreads * KT * kItemBytes +
+           kRedoBytes;
 }
 
-constexpr size_t kSmemBudget = 100 * 1024;   // two CTAs per SM
+constexpr size_t kSmemBudget = 110 * 1024;   // two CTAs per SM
 
 template <int KT, typename OutT>
 cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                            unsigned long long *stats, cudaStream_t st)
 {
-    const size_t smem = vote_smem<KT, OutT>(G);
     dim3 grid(G.n_phi0 / KT, (G.n_rho + 31) / 32);
-    k_vote<KT, OutT><<<grid, kThreads, smem, st>>>(G, x, y, n, reinterpret_cast<OutT *>(acc),
-                                                  stats);
+    k_vote<KT, OutT><<<grid, kThreads, vote_smem<KT>(G), st>>>(
+        G, x, y, n, reinterpret_cast<OutT *>(acc), stats);
     return cudaGetLastError();
 }
 
@@ -391,9 +492,9 @@ cudaError_t launch_assoc_kt(const DevGeom &G, const float *x, const float *y, in
                             const ht_peak *peaks, const int *d_count, int cap,
                             unsigned long long *gbest, cudaStream_t st)
 {
-    const size_t smem = assoc_smem<KT>(G);
     dim3 grid(G.n_phi0 / KT, (G.n_rho + 31) / 32);
-    k_assoc<KT><<<grid, kThreads, smem, st>>>(G, x, y, n, peaks, d_count, cap, gbest);
+    k_assoc<KT><<<grid, kThreads, assoc_smem<KT>(G), st>>>(G, x, y, n, peaks, d_count, cap,
+                                                           gbest);
     return cudaGetLastError();
 }
 
@@ -404,8 +505,9 @@ cudaError_t launch_assoc_kt(const DevGeom &G, const float *x, const float *y, in
 cudaError_t prepare_tile_kernels(int max_smem)
 {
     const void *fns[] = {(const void *)k_vote<8, uint16_t>, (const void *)k_vote<4, uint16_t>,
-                         (const void *)k_vote<2, uint16_t>, (const void *)k_vote<4, int32_t>,
-                         (const void *)k_vote<2, int32_t>,  (const void *)k_assoc<4>,
+                         (const void *)k_vote<2, uint16_t>, (const void *)k_vote<1, uint16_t>,
+                         (const void *)k_vote<4, int32_t>,  (const void *)k_vote<2, int32_t>,
+                         (const void *)k_vote<1, int32_t>,  (const void *)k_assoc<4>,
                          (const void *)k_assoc<2>,          (const void *)k_assoc<1>};
     for (const void *f : fns) {
         cudaFuncAttributes fa;
@@ -421,8 +523,7 @@ cudaError_t prepare_tile_kernels(int max_smem)
 // Largest tile shared memory any geometry with n_d0 bins needs.
 size_t tile_smem_need(const DevGeom &G)
 {
-    size_t v = G.count_bits == 16 ? vote_smem<2, uint16_t>(G) : vote_smem<2, int32_t>(G);
-    size_t a = assoc_smem<1>(G);
+    const size_t v = vote_smem<1>(G), a = assoc_smem<1>(G);
     return v > a ? v : a;
 }
 
@@ -432,15 +533,19 @@ cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n,
                         unsigned long long *stats, cudaStream_t st)
 {
     if (G.count_bits == 16) {
-        if (vote_smem<8, uint16_t>(G) <= kSmemBudget)
+        if (vote_smem<8>(G) <= kSmemBudget)
             return launch_vote_kt<8, uint16_t>(G, x, y, n, acc, stats, st);
-        if (vote_smem<4, uint16_t>(G) <= kSmemBudget)
+        if (vote_smem<4>(G) <= kSmemBudget)
             return launch_vote_kt<4, uint16_t>(G, x, y, n, acc, stats, st);
-        return launch_vote_kt<2, uint16_t>(G, x, y, n, acc, stats, st);
+        if (vote_smem<2>(G) <= kSmemBudget)
+            return launch_vote_kt<2, uint16_t>(G, x, y, n, acc, stats, st);
+        return launch_vote_kt<1, uint16_t>(G, x, y, n, acc, stats, st);
     }
-    if (vote_smem<4, int32_t>(G) <= kSmemBudget)
+    if (vote_smem<4>(G) <= kSmemBudget)
         return launch_vote_kt<4, int32_t>(G, x, y, n, acc, stats, st);
-    return launch_vote_kt<2, int32_t>(G, x, y, n, acc, stats, st);
+    if (vote_smem<2>(G) <= kSmemBudget)
+        return launch_vote_kt<2, int32_t>(G, x, y, n, acc, stats, st);
+    return launch_vote_kt<1, int32_t>(G, x, y, n, acc, stats, st);
 }
 
 size_t associate_workspace_bytes(const DevGeom &, int n)

@@ -30,7 +30,6 @@ namespace ht {
 namespace {
 
 constexpr int kBigThreads = 256;
-constexpr int kScanThreads = 1024;
 
 struct ZCand {
     float rho, invrho, sn, cs, d0c;
@@ -129,35 +128,6 @@ __global__ void k_z_count(const int *__restrict__ assign, int n, const int *__re
         const int a = assign[h];
         if (a >= 0 && a < ncand) atomicAdd(&cnt[a], 1);
     }
-}
-
-// Exclusive scan over the first min(*d_count, cap) counts; off has one more
-// entry (the total); cur receives a copy of the offsets.
-__global__ void __launch_bounds__(kScanThreads)
-k_z_scan(const int *__restrict__ cnt, const int *__restrict__ d_count, int cap,
-         int *__restrict__ off, int *__restrict__ cur)
-{
-    __shared__ int part[kScanThreads];
-    const int n = min(*d_count, cap);
-    const int per = (n + kScanThreads - 1) / kScanThreads;
-    const int a = min(n, threadIdx.x * per), b = min(n, a + per);
-    int s = 0;
-    for (int t = a; t < b; ++t) s += cnt[t];
-    part[threadIdx.x] = s;
-    __syncthreads();
-    for (int o = 1; o < kScanThreads; o <<= 1) {
-        const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-        __syncthreads();
-        part[threadIdx.x] += v;
-        __syncthreads();
-    }
-    int run = part[threadIdx.x] - s;
-    for (int t = a; t < b; ++t) {
-        off[t] = run;
-        cur[t] = run;
-        run += cnt[t];
-    }
-    if (threadIdx.x == kScanThreads - 1) off[n] = part[kScanThreads - 1];
 }
 
 __global__ void k_z_scatter(const int *__restrict__ assign, int n, const int *__restrict__ d_count,
@@ -291,6 +261,7 @@ k_z_big(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
 
 struct ZWs {
     int *cnt, *off, *cur, *list, *big, *nbig;
+    void *tmp;
 };
 
 ZWs carve(void *ws, int n, int cap)
@@ -302,6 +273,7 @@ ZWs carve(void *ws, int n, int cap)
     w.cur = reinterpret_cast<int *>(p); p += align256((size_t)(cap + 1) * 4);
     w.big = reinterpret_cast<int *>(p); p += align256((size_t)(cap + 1) * 4);
     w.nbig = reinterpret_cast<int *>(p); p += 256;
+    w.tmp = p; p += scan_tmp_bytes(cap);
     w.list = reinterpret_cast<int *>(p);
     return w;
 }
@@ -310,7 +282,8 @@ ZWs carve(void *ws, int n, int cap)
 
 size_t vote_z_workspace_bytes(const DevGeom &, int n, int cap)
 {
-    return 4 * align256((size_t)(cap + 1) * 4) + 256 + align256((size_t)(n > 0 ? n : 1) * 4);
+    return 4 * align256((size_t)(cap + 1) * 4) + 256 + scan_tmp_bytes(cap) +
+           align256((size_t)(n > 0 ? n : 1) * 4);
 }
 
 size_t z_big_smem(const DevGeom &G) { return (size_t)G.n_z0 * G.n_cot * 4; }
@@ -336,7 +309,8 @@ cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, cons
     if (e != cudaSuccess) return e;
     const int nb = n > 0 ? min(4096, (n + 255) / 256) : 1;
     if (n > 0) k_z_count<<<nb, 256, 0, st>>>(assign, n, d_count, cap, w.cnt);
-    k_z_scan<<<1, kScanThreads, 0, st>>>(w.cnt, d_count, cap, w.off, w.cur);
+    e = scan_exclusive(w.cnt, w.off, w.cur, cap, d_count, nullptr, w.tmp, st);
+    if (e != cudaSuccess) return e;
     if (n > 0) k_z_scatter<<<nb, 256, 0, st>>>(assign, n, d_count, cap, w.cur, w.list);
     const int warps_needed = cap;
     const int blocks = min(152 * 16, (warps_needed + 7) / 8);

@@ -12,7 +12,7 @@ Tensor conventions:
   d_count       int32 [1]
   assign        int32 [n]
   zres          int32 [cap, 3] = {n_z0, m_cot, count}
-  stats         int64 [3] (uint64 counters: votes, float64 redos, edge votes)
+  stats         int64 [2] (uint64 counters: votes, float64 redos)
   workspace     uint8, at least the size the matching *_workspace_size gives
 """
 import ctypes
@@ -194,7 +194,7 @@ class EventPipeline:
         self.count = torch.zeros(1, dtype=torch.int32, device=dev)
         self.assign = torch.empty(max(max_hits, 1), dtype=torch.int32, device=dev)
         self.zres = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=dev)
-        self.stats = torch.zeros(3, dtype=torch.int64, device=dev)
+        self.stats = torch.zeros(2, dtype=torch.int64, device=dev)
         ws = max(g.find_peaks_workspace_size(), g.associate_workspace_size(max_hits),
                  g.vote_z_workspace_size(max_hits, cap))
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)

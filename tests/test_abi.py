@@ -27,12 +27,16 @@ def test_header_declares_the_path():
         assert s in syms
 
 
+def _have_nvcc():
+    import shutil
+    return os.path.exists("/usr/local/cuda/bin/nvcc") or shutil.which("nvcc") is not None
+
+
 def test_library_exports_every_declared_symbol():
     from paper_1309_6275_gb300 import build
-    try:
-        path = build.build()
-    except (OSError, RuntimeError) as e:      # no nvcc on this machine
-        pytest.skip(f"cannot build libht here: {e}")
+    if not _have_nvcc():
+        pytest.skip("no nvcc on this machine")
+    path = build.build()          # a compile or link error fails the test
     out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
                          text=True).stdout
     exported = set(re.findall(r"\bT (ht_\w+)$", out, re.M))
@@ -51,10 +55,9 @@ def test_binding_signatures_cover_the_header():
 def test_create_rejects_bad_geometry_without_touching_the_gpu():
     """Argument checks come before any CUDA call."""
     from paper_1309_6275_gb300 import ht
-    try:
-        lib = ht.lib()
-    except Exception as e:
-        pytest.skip(f"cannot load libht here: {e}")
+    if not _have_nvcc():
+        pytest.skip("no nvcc on this machine")
+    lib = ht.lib()
     d = ht._Desc(64, 64, 60, 128, 128, 7, 32, 0, 0.01, 10.0, 32.0, 6.5)   # n_phi0 % 8 != 0
     h = ctypes.c_void_p()
     assert lib.ht_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1

@@ -203,7 +203,7 @@ def test_host_buffer_entry_point(name):
     hz = torch.zeros((cap, 3), dtype=torch.int32).pin_memory()
     ha = torch.zeros(n, dtype=torch.int32).pin_memory()
     hc = torch.zeros(1, dtype=torch.int32)
-    hs = torch.zeros(3, dtype=torch.int64)
+    hs = torch.zeros(2, dtype=torch.int64)
     hx, hy, hzz = (torch.from_numpy(a).pin_memory() for a in (ev.x, ev.y, ev.z))
     ht.ht_run_event(G, hx, hy, hzz, ws, hp, cap, hc, ha, hz, hs)
     k = min(int(hc[0]), cap)
