@@ -135,10 +135,13 @@ ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks,
  * |k - k_m| <= 1; it is assigned to the compatible candidate of largest
  * count, ties to the smallest m, else -1.  Candidates are
  * peaks[0 .. min(*d_count, cap)), in increasing l (ht_find_peaks order).
+ * The candidates must be ht_find_peaks output (no two of them adjacent);
+ * other lists give unspecified assignments.
  *   assign     n_hits int32 (device).
- *   workspace  ht_associate_workspace_size(g, n_hits) bytes, 256-byte aligned.
+ *   workspace  ht_associate_workspace_size(g, n_hits, cap) bytes, 256-byte
+ *              aligned.
  * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
-size_t ht_associate_workspace_size(const ht_geometry *g, int32_t n_hits);
+size_t ht_associate_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap);
 ht_status ht_associate(const ht_geometry *g, const float *x, const float *y,
                        int32_t n_hits, const ht_peak *peaks,
                        const int32_t *d_count, int32_t cap, int32_t *assign,

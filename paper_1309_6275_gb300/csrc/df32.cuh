@@ -79,9 +79,8 @@ __device__ __forceinline__ F2 df_sqrt(F2 a)   // a.hi > 0
 // j >= 0, -1 (outside the axis) or -2 (undecided).
 __device__ __forceinline__ int decide_df(F2 u, float e, float nd)
 {
-    if (!(e < 0.25f)) return -2;
     const float uh = u.hi + u.lo;
-    if (uh < -0.5f || uh >= nd + 0.5f) return -1;
+    if (uh + 2.0f * e < -0.5f || uh - 2.0f * e >= nd + 0.5f) return -1;
     const float f = floorf(uh);
     // distances to the integers below and above, each in double-float so
     // that its leading part is accurate relative to its own (small) size

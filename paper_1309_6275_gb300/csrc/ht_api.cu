@@ -234,9 +234,9 @@ ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks, i
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_find_peaks");
 }
 
-size_t ht_associate_workspace_size(const ht_geometry *g, int32_t n_hits)
+size_t ht_associate_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap)
 {
-    return g ? ht::associate_workspace_bytes(g->G, n_hits) : 0;
+    return g ? ht::associate_workspace_bytes(g->G, n_hits, cap) : 0;
 }
 
 ht_status ht_associate(const ht_geometry *g, const float *x, const float *y, int32_t n_hits,
@@ -249,7 +249,8 @@ ht_status ht_associate(const ht_geometry *g, const float *x, const float *y, int
     if (n_hits < 0 || n_hits > kMaxHits || cap < 0)
         return fail(HT_ERR_ARG, "ht_associate: n_hits %d or cap %d out of range", n_hits, cap);
     if (n_hits > 0 && (!x || !y || !assign)) return fail(HT_ERR_ARG, "ht_associate: null hits");
-    if (workspace_bytes < ht::associate_workspace_bytes(g->G, n_hits) || !aligned(workspace, 256))
+    if (workspace_bytes < ht::associate_workspace_bytes(g->G, n_hits, cap) ||
+        !aligned(workspace, 256))
         return fail(HT_ERR_ARG, "ht_associate: workspace too small or misaligned");
     cudaError_t e = ht::launch_associate(g->G, x, y, n_hits, peaks, d_count, cap, assign,
                                          workspace, S(stream));
@@ -309,7 +310,7 @@ EventWs carve_event(const ht_geometry *g, void *base, int32_t n, int32_t cap)
     w.zres = reinterpret_cast<ht_zres *>(p); p += align256((size_t)(cap > 0 ? cap : 1) * 12);
     w.stats = reinterpret_cast<uint64_t *>(p); p += 256;
     size_t s = ht::peaks_workspace_bytes(g->G);
-    const size_t sa = ht::associate_workspace_bytes(g->G, n);
+    const size_t sa = ht::associate_workspace_bytes(g->G, n, cap);
     const size_t sz = ht::vote_z_workspace_bytes(g->G, n, cap);
     if (sa > s) s = sa;
     if (sz > s) s = sz;

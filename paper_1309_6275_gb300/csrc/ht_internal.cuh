@@ -118,15 +118,17 @@ __device__ __forceinline__ float rsqrt_approx(float v)
 }
 
 // Bin of a root with coordinate u and bound e: j >= 0 (vote), -1 (certainly
-// outside the axis) or -2 (undecided: redo in float64).
+// outside the axis) or -2 (undecided: redo).  Branch-free.  If u lies within
+// e of the axis but outside it, its distance to the edge integer is below e,
+// so it is undecided rather than misbinned; a NaN bound or coordinate is
+// undecided too.
 __device__ __forceinline__ int decide(float u, float e, float nd)
 {
-    if (!(e < 0.25f)) return -2;
-    if (u < -0.5f || u >= nd + 0.5f) return -1;
     const float f = floorf(u);
     const float fr = u - f;
-    if (!(fminf(fr, 1.0f - fr) > e)) return -2;
-    return (f >= 0.0f && f < nd) ? (int)f : -1;
+    const bool out = (u + e < 0.0f) | (u - e >= nd);
+    const bool ok = fminf(fr, 1.0f - fr) > e;
+    return out ? -1 : (ok ? (int)f : -2);
 }
 
 // Returns kDecided with jA, jB (bin or -1) or kRedo.
@@ -134,29 +136,31 @@ __device__ __forceinline__ int eval32(const DevGeom &G, float rho, float invrho_
                                       float invrho, bool need_b, const Item &it, int &jA,
                                       int &jB)
 {
-    jA = -1;
-    jB = -1;
     const float b = fmaf(rho, it.s, 1.0f);
     const float pc = rho * it.c;
     const float D = fmaf(-pc, pc, 1.0f);
-    if (D <= it.eD) return D < -it.eD ? kDecided : kRedo;
-    const float rs = rsqrt_approx(D);
-    const float sq = D * rs;
+    const bool none = D < -it.eD;          // certainly no real root
+    const bool tangent = D <= it.eD;       // sign of D not proven
+    const float Dp = fmaxf(D, 1e-30f);
+    const float rs = rsqrt_approx(Dp);
+    const float sq = Dp * rs;
     const float q = -(b + copysignf(sq, b));
     const float C = fmaf(rho, it.r2, it.s + it.s);
     const float iq = rcp_approx(q);
     const float nd = (float)G.n_d0;
     const float uA = fmaf(C * iq, G.inv_delta_f, G.off_f);
     const float eA = fmaf(fabsf(iq), fmaf(it.E2, rs, it.E1), G.e3);
-    jA = decide(uA, eA, nd);
-    if (jA == -2) return kRedo;
+    int a = decide(uA, eA, nd);
+    int bb = -1;
     if (need_b) {
         const float uB = fmaf(q * invrho, G.inv_delta_f, G.off_f);
         const float eB = fmaf(invrho_es, fmaf(it.Qb, rs, it.Qa), G.e3);
-        jB = decide(uB, eB, nd);
-        if (jB == -2) return kRedo;
+        bb = decide(uB, eB, nd);
     }
-    return kDecided;
+    jA = tangent ? -1 : a;
+    jB = tangent ? -1 : bb;
+    if (none) return kDecided;
+    return (tangent | (a == -2) | (bb == -2)) ? kRedo : kDecided;
 }
 
 // Per-(hit, column) constants for eval32; rt = largest |rho| of the tile.
@@ -262,7 +266,7 @@ size_t peaks_workspace_bytes(const DevGeom &G);
 cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, int n,
                              const ht_peak *peaks, const int *d_count, int cap, int *assign,
                              void *ws, cudaStream_t st);
-size_t associate_workspace_bytes(const DevGeom &G, int n);
+size_t associate_workspace_bytes(const DevGeom &G, int n, int cap);
 cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, const float *z,
                           int n, const int *assign, const ht_peak *peaks, const int *d_count,
                           int cap, ht_zres *out, void *ws, cudaStream_t st);

@@ -180,7 +180,7 @@ __device__ __forceinline__ int item_bins32(const DevGeom &G, const TileCtx<KT> &
 // float32 could not prove.  Drained by all threads of the CTA at the end of
 // the tile (or when half full), through the double-float tier and, rarely,
 // float64 (slow on this part), so neither runs as a lone divergent lane.
-constexpr int kRedoCap = 1024;
+constexpr int kRedoCap = 512;
 constexpr size_t kRedoBytes = (size_t)kRedoCap * 8;
 
 struct RedoQueue {
@@ -206,16 +206,34 @@ __device__ __forceinline__ bool push_redo(const RedoQueue &Q, int *n, int hit, i
 }
 
 // ------------------------------------------------------------------ vote
-template <int KT, typename OutT>
-__global__ void __launch_bounds__(kThreads, 2)
+// PACK: two 16-bit counters per shared word (d0 bins 2w and 2w + 1), which
+// halves the tile.  Exact while no cell can reach 65536 votes in the tile: a
+// cell gets at most two votes per hit, so it is used only for n <= 32767.
+template <bool PACK>
+__device__ __forceinline__ void tile_add(uint32_t *col, int j)
+{
+    if (PACK) atomicAdd(col + (j >> 1) * 32, 1u << ((j & 1) << 4));
+    else atomicAdd(col + j * 32, 1u);
+}
+
+template <bool PACK>
+__device__ __forceinline__ uint32_t tile_get(const uint32_t *cnt, int ND, int kl, int j, int il)
+{
+    if (PACK) return (cnt[(kl * (ND >> 1) + (j >> 1)) * 32 + il] >> ((j & 1) << 4)) & 0xffffu;
+    return cnt[(kl * ND + j) * 32 + il];
+}
+
+template <int KT, typename OutT, bool PACK>
+__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
 k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
        OutT *__restrict__ acc, unsigned long long *__restrict__ stats)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
+    const int NW = PACK ? (ND >> 1) : ND;                  // words per column-row
     constexpr int QCAP = kThreads * KT;
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][ND][32]
-    unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * ND * 32);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][NW][32]
+    unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * NW * 32);
     const WorkList W = carve_worklist(p, QCAP);
     const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
     __shared__ int qn[2], rn;
@@ -227,7 +245,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
     T.init(G, lane);
     {
         uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
-        for (int t = threadIdx.x; t < KT * ND * 8; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
+        for (int t = threadIdx.x; t < KT * NW * 8; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
     }
     if (threadIdx.x < 2) {
         qn[threadIdx.x] = 0;
@@ -236,7 +254,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
     if (threadIdx.x == 0) rn = 0;
     __syncthreads();
 
-    int my_votes = 0, my_fb = 0;
+    int my_fb = 0;
     int parity = 0;
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
         collect<KT>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W);
@@ -246,7 +264,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
         if (T.row_ok) {
             for (int t = warp; t < nq; t += nwarps) {
                 const int m = W.meta[t];
-                uint32_t *col = cnt + (m & kMetaCol) * ND * 32 + lane;
+                uint32_t *col = cnt + (m & kMetaCol) * NW * 32 + lane;
                 int jj[2];
                 int nv = item_bins32<KT>(G, T, W, t, m, jj);
                 if (nv < 0) {
@@ -254,9 +272,8 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
                     if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
                     nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
                 }
-                if (nv > 0) atomicAdd(col + jj[0] * 32, 1u);
-                if (nv > 1) atomicAdd(col + jj[1] * 32, 1u);
-                my_votes += nv;
+                if (nv > 0) tile_add<PACK>(col, jj[0]);
+                if (nv > 1) tile_add<PACK>(col, jj[1]);
             }
         }
         __syncthreads();
@@ -268,9 +285,8 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
                 const int il = rc >> 4, kl = rc & 15;
                 int jj[2];
                 const int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
-                uint32_t *col = cnt + kl * ND * 32 + il;
-                for (int v = 0; v < nv; ++v) atomicAdd(col + jj[v] * 32, 1u);
-                my_votes += nv;
+                uint32_t *col = cnt + kl * NW * 32 + il;
+                for (int v = 0; v < nv; ++v) tile_add<PACK>(col, jj[v]);
             }
             __syncthreads();
             if (threadIdx.x == 0) rn = 0;
@@ -279,14 +295,20 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
     __syncthreads();
 
     // write-back: thread = (row, d0 bin); the KT counts of a row go out as
-    // one vector of KT * sizeof(OutT) bytes
+    // one vector of KT * sizeof(OutT) bytes.  Votes are summed here (tile
+    // counters never saturate: they hold at most 2 n).
+    unsigned long long my_votes = 0;
     for (int t = threadIdx.x; t < 32 * ND; t += kThreads) {
         const int il = t & 31, j = t >> 5;
         const int i = T.i0 + il;
         if (i >= G.n_rho) continue;
         __align__(16) OutT e[KT];
 #pragma unroll
-        for (int kl = 0; kl < KT; ++kl) e[kl] = saturate<OutT>(cnt[(kl * ND + j) * 32 + il]);
+        for (int kl = 0; kl < KT; ++kl) {
+            const uint32_t v = tile_get<PACK>(cnt, ND, kl, j, il);
+            my_votes += v;
+            e[kl] = saturate<OutT>(v);
+        }
         OutT *dst = acc + ((size_t)i * ND + j) * G.n_phi0 + T.k0;
         if constexpr (KT * sizeof(OutT) == 16) {
             *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(e);
@@ -307,7 +329,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
             my_fb += __shfl_xor_sync(0xffffffffu, my_fb, o);
         }
         if (lane == 0) {
-            atomicAdd(&s_stats[0], (unsigned long long)my_votes);
+            atomicAdd(&s_stats[0], my_votes);
             atomicAdd(&s_stats[1], (unsigned long long)my_fb);
         }
         __syncthreads();
@@ -461,11 +483,184 @@ __global__ void k_assoc_final(const unsigned long long *__restrict__ gbest, int 
     assign[h] = b ? (int)(0xffffffffu - (unsigned)(b & 0xffffffffull)) : -1;
 }
 
+// ------------------------------------- association with 32-bit keys
+// For uint16 accumulators (counts <= 65535).  A pre-pass lists, for every
+// tile, the candidates whose 3x3x3 box touches it; the tile sorts its list by
+// candidate index, so a 16-bit rank is monotone in m, and scatters
+// key = count << 16 | (65535 - rank) with native 32-bit shared atomicMax.
+// Peaks form an independent set of the 26-neighbour grid (of two adjacent
+// cells at most one can be a peak), so a tile's list holds at most one
+// candidate per 2x2x2 block of its 34 x (KT + 2) x n_d0 halo region.
+__device__ __forceinline__ int tiles_of(const ht_peak &p, int NR, int NP, int KT, int nct,
+                                        int out[4])
+{
+    const int rt0 = max(p.i_rho - 1, 0) >> 5, rt1 = min(p.i_rho + 1, NR - 1) >> 5;
+    int ct[3], nc = 0;
+#pragma unroll
+    for (int d = -1; d <= 1; ++d) {
+        int kk = p.k_phi0 + d;
+        kk += (kk < 0) ? NP : 0;
+        kk -= (kk >= NP) ? NP : 0;
+        const int c = kk / KT;
+        bool dup = false;
+        for (int u = 0; u < nc; ++u) dup |= (ct[u] == c);
+        if (!dup) ct[nc++] = c;
+    }
+    int no = 0;
+    for (int rt = rt0; rt <= rt1; ++rt)
+        for (int u = 0; u < nc; ++u) out[no++] = rt * nct + ct[u];
+    return no;
+}
+
+__global__ void k_cand_tiles(const ht_peak *__restrict__ peaks, const int *__restrict__ d_count,
+                             int cap, int NR, int NP, int KT, int nct, int *__restrict__ tcnt,
+                             int *__restrict__ tcur, int *__restrict__ list)
+{
+    const int ncand = min(*d_count, cap);
+    for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < ncand; m += gridDim.x * blockDim.x) {
+        int t[4];
+        const int nt = tiles_of(peaks[m], NR, NP, KT, nct, t);
+        for (int u = 0; u < nt; ++u) {
+            if (list) list[atomicAdd(&tcur[t[u]], 1)] = m;
+            else atomicAdd(&tcnt[t[u]], 1);
+        }
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 3)
+k_assoc32(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
+          const ht_peak *__restrict__ peaks, const int *__restrict__ toff,
+          const int *__restrict__ tlist, int lcap, unsigned long long *__restrict__ gbest)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int ND = G.n_d0;
+    constexpr int QCAP = kThreads * KT;
+    uint32_t *map = reinterpret_cast<uint32_t *>(smem);          // [KT][ND][32]
+    int *local = reinterpret_cast<int *>(map + KT * ND * 32);    // sorted candidate indices
+    uint32_t *bestk = reinterpret_cast<uint32_t *>(local + lcap);
+    unsigned char *p = reinterpret_cast<unsigned char *>(bestk + kThreads);
+    const WorkList W = carve_worklist(p, QCAP);
+    const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
+    __shared__ int qn[2], rn;
+
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int nwarps = kThreads / 32;
+    TileCtx<KT> T;
+    T.init(G, lane);
+    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    const int l0 = toff[tile];
+    const int L = min(toff[tile + 1] - l0, lcap);
+
+    // sort the tile's candidates by index: bitonic sort in the map's space
+    int P = 1;
+    while (P < L) P <<= 1;
+    int *sb = reinterpret_cast<int *>(map);
+    for (int t = threadIdx.x; t < P; t += kThreads) sb[t] = t < L ? tlist[l0 + t] : 0x7fffffff;
+    __syncthreads();
+    for (int k2 = 2; k2 <= P; k2 <<= 1)
+        for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+            for (int t = threadIdx.x; t < P; t += kThreads) {
+                const int o = t ^ j2;
+                if (o > t) {
+                    const int a = sb[t], b = sb[o];
+                    const bool up = (t & k2) == 0;
+                    if ((a > b) == up) { sb[t] = b; sb[o] = a; }
+                }
+            }
+            __syncthreads();
+        }
+    for (int t = threadIdx.x; t < L; t += kThreads) local[t] = sb[t];
+    __syncthreads();
+    {
+        uint4 *m4 = reinterpret_cast<uint4 *>(map);
+        for (int t = threadIdx.x; t < KT * ND * 8; t += kThreads) m4[t] = make_uint4(0, 0, 0, 0);
+    }
+    bestk[threadIdx.x] = 0u;
+    if (threadIdx.x < 2) qn[threadIdx.x] = 0;
+    if (threadIdx.x == 0) rn = 0;
+    __syncthreads();
+
+    // scatter each candidate's box, key = count << 16 | (65535 - rank)
+    for (int r = threadIdx.x; r < L; r += kThreads) {
+        const ht_peak pk = peaks[local[r]];
+        const uint32_t key = ((uint32_t)pk.count << 16) | (uint32_t)(0xffff - r);
+#pragma unroll
+        for (int d = -1; d <= 1; ++d) {
+            int kk = pk.k_phi0 + d;
+            kk += (kk < 0) ? G.n_phi0 : 0;
+            kk -= (kk >= G.n_phi0) ? G.n_phi0 : 0;
+            const int kl = kk - T.k0;
+            if (kl < 0 || kl >= KT) continue;
+            for (int di = -1; di <= 1; ++di) {
+                const int ii = pk.i_rho + di, il = ii - T.i0;
+                if (il < 0 || il >= 32 || ii >= G.n_rho) continue;
+                for (int dj = -1; dj <= 1; ++dj) {
+                    const int jj = pk.j_d0 + dj;
+                    if (jj < 0 || jj >= ND) continue;
+                    atomicMax(&map[(kl * ND + jj) * 32 + il], key);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    auto to64 = [&](uint32_t k32) -> unsigned long long {
+        const int m = local[0xffff - (int)(k32 & 0xffffu)];
+        return ((unsigned long long)(k32 >> 16) << 32) | (0xffffffffull - (unsigned)m);
+    };
+
+    int parity = 0;
+    for (int base = 0; base < n; base += kThreads, parity ^= 1) {
+        collect<KT>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W);
+        __syncthreads();
+        const int nq = qn[parity];
+        if (threadIdx.x == 0) qn[parity ^ 1] = 0;
+        for (int t = warp; t < nq; t += nwarps) {
+            const int m = W.meta[t];
+            uint32_t key = 0u;
+            if (T.row_ok) {
+                const uint32_t *col = map + (m & kMetaCol) * ND * 32 + lane;
+                int jj[2];
+                int nv = item_bins32<KT>(G, T, W, t, m, jj);
+                if (nv < 0 && !push_redo(R, &rn, m >> 6, lane, m & kMetaCol))
+                    nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                if (nv > 0) key = col[jj[0] * 32];
+                if (nv > 1) key = max(key, col[jj[1] * 32]);
+            }
+            const uint32_t top = __reduce_max_sync(0xffffffffu, key);
+            if (top && lane == 0) atomicMax(&bestk[(m >> 6) - base], top);
+        }
+        __syncthreads();
+        const uint32_t b = bestk[threadIdx.x];
+        if (b) {
+            atomicMax(&gbest[base + threadIdx.x], to64(b));
+            bestk[threadIdx.x] = 0u;
+        }
+        const int nr = min(rn, kRedoCap);
+        if (nr >= kRedoCap / 2 || base + kThreads >= n) {
+            for (int t = threadIdx.x; t < nr; t += kThreads) {
+                const int h = R.hit[t], rc = R.rc[t];
+                const int il = rc >> 4, kl = rc & 15;
+                int jj[2];
+                const int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
+                const uint32_t *col = map + kl * ND * 32 + il;
+                uint32_t key = 0u;
+                for (int v = 0; v < nv; ++v) key = max(key, col[jj[v] * 32]);
+                if (key) atomicMax(&gbest[h], to64(key));
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) rn = 0;
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launch
 template <int KT>
-size_t vote_smem(const DevGeom &G)
+size_t vote_smem(const DevGeom &G, bool pack)
 {
-    return (size_t)KT * 32 * G.n_d0 * 4 + (size_t)kThreads * KT * kItemBytes + kRedoBytes;
+    return (size_t)KT * 32 * (pack ? G.n_d0 / 2 : G.n_d0) * 4 + (size_t)kThreads * KT * kItemBytes +
+           kRedoBytes;
 }
 
 template <int KT>
@@ -475,15 +670,59 @@ size_t assoc_smem(const DevGeom &G)
            kRedoBytes;
 }
 
-constexpr size_t kSmemBudget = 110 * 1024;   // two CTAs per SM
+template <int KT>
+int assoc32_lcap(const DevGeom &G)
+{
+    return 17 * ((KT + 3) / 2) * ((G.n_d0 + 1) / 2) + 32;
+}
 
-template <int KT, typename OutT>
+template <int KT>
+size_t assoc32_smem(const DevGeom &G)
+{
+    const size_t map = (size_t)KT * 32 * G.n_d0 * 4;
+    size_t sortbuf = 1;
+    while (sortbuf < (size_t)assoc32_lcap<KT>(G)) sortbuf <<= 1;
+    return (map > sortbuf * 4 ? map : sortbuf * 4) + (size_t)assoc32_lcap<KT>(G) * 4 +
+           (size_t)kThreads * 4 + (size_t)kThreads * KT * kItemBytes + kRedoBytes;
+}
+
+constexpr size_t kSmemBudget2 = 110 * 1024;   // two CTAs per SM
+constexpr size_t kSmemBudget3 = 75 * 1024;    // three CTAs per SM
+
+template <int KT, typename OutT, bool PACK>
 cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                            unsigned long long *stats, cudaStream_t st)
 {
     dim3 grid(G.n_phi0 / KT, (G.n_rho + 31) / 32);
-    k_vote<KT, OutT><<<grid, kThreads, vote_smem<KT>(G), st>>>(
+    k_vote<KT, OutT, PACK><<<grid, kThreads, vote_smem<KT>(G, PACK), st>>>(
         G, x, y, n, reinterpret_cast<OutT *>(acc), stats);
+    return cudaGetLastError();
+}
+
+template <int KT>
+cudaError_t launch_assoc32_kt(const DevGeom &G, const float *x, const float *y, int n,
+                              const ht_peak *peaks, const int *d_count, int cap,
+                              unsigned long long *gbest, char *ws, cudaStream_t st)
+{
+    const int nct = G.n_phi0 / KT, nrt = (G.n_rho + 31) / 32, ntiles = nct * nrt;
+    int *tcnt = reinterpret_cast<int *>(ws);
+    int *toff = reinterpret_cast<int *>(ws + align256((size_t)(ntiles + 1) * 4));
+    int *tcur = reinterpret_cast<int *>(ws + 2 * align256((size_t)(ntiles + 1) * 4));
+    void *tmp = ws + 3 * align256((size_t)(ntiles + 1) * 4);
+    int *tlist = reinterpret_cast<int *>(ws + 3 * align256((size_t)(ntiles + 1) * 4) +
+                                         scan_tmp_bytes(ntiles));
+    cudaError_t e = cudaMemsetAsync(tcnt, 0, (size_t)ntiles * 4, st);
+    if (e != cudaSuccess) return e;
+    const int nb = min(4096, (cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1);
+    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, KT, nct, tcnt,
+                                     nullptr, nullptr);
+    e = scan_exclusive(tcnt, toff, tcur, ntiles, nullptr, nullptr, tmp, st);
+    if (e != cudaSuccess) return e;
+    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, KT, nct, nullptr,
+                                     tcur, tlist);
+    dim3 grid(nct, nrt);
+    k_assoc32<KT><<<grid, kThreads, assoc32_smem<KT>(G), st>>>(G, x, y, n, peaks, toff, tlist,
+                                                               assoc32_lcap<KT>(G), gbest);
     return cudaGetLastError();
 }
 
@@ -504,11 +743,15 @@ cudaError_t launch_assoc_kt(const DevGeom &G, const float *x, const float *y, in
 // still passes only what the chosen tile needs).  Called once per device.
 cudaError_t prepare_tile_kernels(int max_smem)
 {
-    const void *fns[] = {(const void *)k_vote<8, uint16_t>, (const void *)k_vote<4, uint16_t>,
-                         (const void *)k_vote<2, uint16_t>, (const void *)k_vote<1, uint16_t>,
-                         (const void *)k_vote<4, int32_t>,  (const void *)k_vote<2, int32_t>,
-                         (const void *)k_vote<1, int32_t>,  (const void *)k_assoc<4>,
-                         (const void *)k_assoc<2>,          (const void *)k_assoc<1>};
+    const void *fns[] = {
+        (const void *)k_vote<4, uint16_t, true>,  (const void *)k_vote<2, uint16_t, true>,
+        (const void *)k_vote<1, uint16_t, true>,  (const void *)k_vote<8, uint16_t, false>,
+        (const void *)k_vote<4, uint16_t, false>, (const void *)k_vote<2, uint16_t, false>,
+        (const void *)k_vote<1, uint16_t, false>, (const void *)k_vote<4, int32_t, false>,
+        (const void *)k_vote<2, int32_t, false>,  (const void *)k_vote<1, int32_t, false>,
+        (const void *)k_assoc<4>,                 (const void *)k_assoc<2>,
+        (const void *)k_assoc<1>,                 (const void *)k_assoc32<4>,
+        (const void *)k_assoc32<2>,               (const void *)k_assoc32<1>};
     for (const void *f : fns) {
         cudaFuncAttributes fa;
         cudaError_t e = cudaFuncGetAttributes(&fa, f);
@@ -523,34 +766,52 @@ cudaError_t prepare_tile_kernels(int max_smem)
 // Largest tile shared memory any geometry with n_d0 bins needs.
 size_t tile_smem_need(const DevGeom &G)
 {
-    const size_t v = vote_smem<1>(G), a = assoc_smem<1>(G);
-    return v > a ? v : a;
+    const size_t v = vote_smem<1>(G, false), a = assoc_smem<1>(G), a32 = assoc32_smem<1>(G);
+    return v > a ? (v > a32 ? v : a32) : (a > a32 ? a : a32);
 }
 
-// Tile width: the widest KT whose tile and work list leave room for two CTAs
-// per SM.
+// Tile shape: packed 16-bit counters with three CTAs per SM when the output
+// is uint16, n_d0 even and n <= 32767; otherwise 32-bit counters, two CTAs
+// per SM.  KT is the widest tile that fits.
 cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                         unsigned long long *stats, cudaStream_t st)
 {
     if (G.count_bits == 16) {
-        if (vote_smem<8>(G) <= kSmemBudget)
-            return launch_vote_kt<8, uint16_t>(G, x, y, n, acc, stats, st);
-        if (vote_smem<4>(G) <= kSmemBudget)
-            return launch_vote_kt<4, uint16_t>(G, x, y, n, acc, stats, st);
-        if (vote_smem<2>(G) <= kSmemBudget)
-            return launch_vote_kt<2, uint16_t>(G, x, y, n, acc, stats, st);
-        return launch_vote_kt<1, uint16_t>(G, x, y, n, acc, stats, st);
+        if (n <= 32767 && G.n_d0 % 2 == 0) {
+            if (vote_smem<4>(G, true) <= kSmemBudget3)
+                return launch_vote_kt<4, uint16_t, true>(G, x, y, n, acc, stats, st);
+            if (vote_smem<2>(G, true) <= kSmemBudget3)
+                return launch_vote_kt<2, uint16_t, true>(G, x, y, n, acc, stats, st);
+            if (vote_smem<1>(G, true) <= kSmemBudget3)
+                return launch_vote_kt<1, uint16_t, true>(G, x, y, n, acc, stats, st);
+        }
+        if (vote_smem<8>(G, false) <= kSmemBudget2)
+            return launch_vote_kt<8, uint16_t, false>(G, x, y, n, acc, stats, st);
+        if (vote_smem<4>(G, false) <= kSmemBudget2)
+            return launch_vote_kt<4, uint16_t, false>(G, x, y, n, acc, stats, st);
+        if (vote_smem<2>(G, false) <= kSmemBudget2)
+            return launch_vote_kt<2, uint16_t, false>(G, x, y, n, acc, stats, st);
+        return launch_vote_kt<1, uint16_t, false>(G, x, y, n, acc, stats, st);
     }
-    if (vote_smem<4>(G) <= kSmemBudget)
-        return launch_vote_kt<4, int32_t>(G, x, y, n, acc, stats, st);
-    if (vote_smem<2>(G) <= kSmemBudget)
-        return launch_vote_kt<2, int32_t>(G, x, y, n, acc, stats, st);
-    return launch_vote_kt<1, int32_t>(G, x, y, n, acc, stats, st);
+    if (vote_smem<4>(G, false) <= kSmemBudget2)
+        return launch_vote_kt<4, int32_t, false>(G, x, y, n, acc, stats, st);
+    if (vote_smem<2>(G, false) <= kSmemBudget2)
+        return launch_vote_kt<2, int32_t, false>(G, x, y, n, acc, stats, st);
+    return launch_vote_kt<1, int32_t, false>(G, x, y, n, acc, stats, st);
 }
 
-size_t associate_workspace_bytes(const DevGeom &, int n)
+// Association workspace: per-hit best keys, then (uint16 geometries) the
+// per-tile candidate lists: counts, offsets, cursors, scan scratch and up to
+// four tile entries per candidate.
+size_t associate_workspace_bytes(const DevGeom &G, int n, int cap)
 {
-    return align256((size_t)(n > 0 ? n : 1) * 8);
+    size_t b = align256((size_t)(n > 0 ? n : 1) * 8);
+    const int KT = 4;   // the narrowest tiling used below has the most tiles
+    const int ntiles = (G.n_phi0 / 1) * ((G.n_rho + 31) / 32);
+    (void)KT;
+    b += 3 * align256((size_t)(ntiles + 1) * 4) + scan_tmp_bytes(ntiles) +
+         align256((size_t)(cap > 0 ? cap : 1) * 4 * 4);
+    return b;
 }
 
 cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, int n,
@@ -559,14 +820,23 @@ cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, i
 {
     if (n == 0) return cudaSuccess;
     unsigned long long *gbest = reinterpret_cast<unsigned long long *>(ws);
+    char *rest = reinterpret_cast<char *>(ws) + align256((size_t)n * 8);
     cudaError_t e = cudaMemsetAsync(gbest, 0, (size_t)n * 8, st);
     if (e != cudaSuccess) return e;
-    if (assoc_smem<4>(G) <= kSmemBudget)
+    if (G.count_bits == 16 && cap > 0) {
+        if (assoc32_smem<4>(G) <= kSmemBudget3)
+            e = launch_assoc32_kt<4>(G, x, y, n, peaks, d_count, cap, gbest, rest, st);
+        else if (assoc32_smem<2>(G) <= kSmemBudget3)
+            e = launch_assoc32_kt<2>(G, x, y, n, peaks, d_count, cap, gbest, rest, st);
+        else
+            e = launch_assoc32_kt<1>(G, x, y, n, peaks, d_count, cap, gbest, rest, st);
+    } else if (assoc_smem<4>(G) <= kSmemBudget2) {
         e = launch_assoc_kt<4>(G, x, y, n, peaks, d_count, cap, gbest, st);
-    else if (assoc_smem<2>(G) <= kSmemBudget)
+    } else if (assoc_smem<2>(G) <= kSmemBudget2) {
         e = launch_assoc_kt<2>(G, x, y, n, peaks, d_count, cap, gbest, st);
-    else
+    } else {
         e = launch_assoc_kt<1>(G, x, y, n, peaks, d_count, cap, gbest, st);
+    }
     if (e != cudaSuccess) return e;
     k_assoc_final<<<(n + 255) / 256, 256, 0, st>>>(gbest, n, assign);
     return cudaGetLastError();

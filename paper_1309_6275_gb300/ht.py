@@ -48,7 +48,7 @@ SIGNATURES = [
     ("ht_vote", _I32, [_P, _P, _P, _I32, _P, _P, _P]),
     ("ht_find_peaks_workspace_size", _SZ, [_P]),
     ("ht_find_peaks", _I32, [_P, _P, _P, _I32, _P, _P, _SZ, _P]),
-    ("ht_associate_workspace_size", _SZ, [_P, _I32]),
+    ("ht_associate_workspace_size", _SZ, [_P, _I32, _I32]),
     ("ht_associate", _I32, [_P, _P, _P, _I32, _P, _P, _I32, _P, _P, _SZ, _P]),
     ("ht_vote_z_workspace_size", _SZ, [_P, _I32, _I32]),
     ("ht_vote_z", _I32, [_P, _P, _P, _P, _I32, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
@@ -128,8 +128,8 @@ class Geometry:
     def find_peaks_workspace_size(self):
         return lib().ht_find_peaks_workspace_size(self.handle)
 
-    def associate_workspace_size(self, n_hits):
-        return lib().ht_associate_workspace_size(self.handle, n_hits)
+    def associate_workspace_size(self, n_hits, cap):
+        return lib().ht_associate_workspace_size(self.handle, n_hits, cap)
 
     def vote_z_workspace_size(self, n_hits, cap):
         return lib().ht_vote_z_workspace_size(self.handle, n_hits, cap)
@@ -195,7 +195,7 @@ class EventPipeline:
         self.assign = torch.empty(max(max_hits, 1), dtype=torch.int32, device=dev)
         self.zres = torch.empty((max(cap, 1), 3), dtype=torch.int32, device=dev)
         self.stats = torch.zeros(2, dtype=torch.int64, device=dev)
-        ws = max(g.find_peaks_workspace_size(), g.associate_workspace_size(max_hits),
+        ws = max(g.find_peaks_workspace_size(), g.associate_workspace_size(max_hits, cap),
                  g.vote_z_workspace_size(max_hits, cap))
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
 
