@@ -129,6 +129,26 @@ ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks,
                         int32_t cap, int32_t *d_count, void *workspace,
                         size_t workspace_bytes, ht_stream stream);
 
+/* ht_find_peaks for callers that cannot allocate device memory: identical
+ * results, but its scratch is a fixed array inside the library instead of a
+ * caller-provided workspace.  Some callers cannot call cudaMalloc at all --
+ * trigger code that must not allocate once data taking has started, or code
+ * embedded in a host framework that owns every device allocation and hands
+ * its plug-ins no allocator -- and this entry point is for them.  The paper
+ * has no counterpart; it is an interface convenience only.
+ *   Limit: n_rho * n_d0 * ceil(n_phi0 / 256) <= 524288 (about 4 MiB of
+ *   scratch, held on every GPU that loads the library until the process
+ *   exits); larger geometries get HT_ERR_CAPACITY.
+ *   The first call on a device (made with that device current) looks up the
+ *   scratch's device address; make that first call before any stream capture.
+ *   All calls share the one array: calls that overlap on the GPU (different
+ *   streams, or different host threads) race and give wrong results, so
+ *   serialise them.  Nothing in the array needs clearing between calls.
+ *   Other arguments as ht_find_peaks.
+ * Errors: HT_ERR_ARG, HT_ERR_CAPACITY, HT_ERR_CUDA. */
+ht_status ht_find_peaks_noalloc(const ht_geometry *g, const void *acc, ht_peak *peaks,
+                                int32_t cap, int32_t *d_count, ht_stream stream);
+
 /* Hit association, the confirming step of Section 5.  Reading: hit h is
  * compatible with candidate m iff one of its votes (exactly as ht_vote casts
  * them) lies in a cell with |i - i_m| <= 1, |j - j_m| <= 1 and circular

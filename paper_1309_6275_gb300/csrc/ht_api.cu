@@ -22,13 +22,6 @@ cudaError_t prepare_z_kernels(int max_smem);
 size_t z_big_smem(const DevGeom &G);
 }  // namespace ht
 
-struct ht_geometry {
-    ht_geometry_desc desc;
-    ht::DevGeom G;
-    void *d_tables;
-    int device;
-};
-
 namespace {
 
 thread_local char g_err[512] = "";
@@ -59,6 +52,13 @@ cudaStream_t S(ht_stream s) { return reinterpret_cast<cudaStream_t>(s); }
 constexpr int32_t kMaxHits = 1 << 25;   // hit index must fit 25 bits in the work list
 
 }  // namespace
+
+namespace ht {
+ht_status set_error(ht_status s, const char *msg)
+{
+    return fail(s, "%s", msg);
+}
+}  // namespace ht
 
 extern "C" {
 

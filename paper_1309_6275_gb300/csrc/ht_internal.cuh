@@ -272,10 +272,21 @@ cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, cons
                           int cap, ht_zres *out, void *ws, cudaStream_t st);
 size_t vote_z_workspace_bytes(const DevGeom &G, int n, int cap);
 
-inline size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Records msg as this host thread's ht_last_error() text; returns s.
+ht_status set_error(ht_status s, const char *msg);
 
 size_t scan_tmp_bytes(int n_cap);
 cudaError_t scan_exclusive(const int *in, int *out, int *out2, int n_cap, const int *d_n,
                            int *total, void *tmp, cudaStream_t st);
 
 }  // namespace ht
+
+// The geometry handle behind the opaque ht_geometry of the C ABI.
+struct ht_geometry {
+    ht_geometry_desc desc;
+    ht::DevGeom G;
+    void *d_tables;
+    int device;
+};

@@ -22,9 +22,11 @@
 #include "ht_internal.cuh"
 
 namespace ht {
-namespace {
 
 constexpr int kPkThreads = 256;   // phi0 columns per CTA
+
+namespace {
+
 constexpr int kJB = 16;           // d0 bins walked per CTA
 
 template <typename T, bool WRITE>
@@ -138,3 +140,62 @@ cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int 
 }
 
 }  // namespace ht
+
+// ---------------------------------------------------------------------------
+// Peak finding without any allocation (ht_find_peaks_noalloc in ht.h).
+//
+// The scratch that ht_find_peaks takes from the caller's workspace -- one
+// count and one offset per (rho row, d0 bin, phi0 block of 256) segment plus
+// the scan's block sums -- lives here in a file-scope device array, sized
+// for at most kNoallocMaxSegments segments.  Every GPU that loads the library
+// holds it until the process exits.  The array's name is only a host-side
+// stand-in in host code, so its device address is looked up once per device
+// with cudaGetSymbolAddress (on the first call made with that device
+// current) and passed to the kernels.  Nothing in it needs clearing between
+// calls: each word a call reads was written earlier in the same call.
+#include <mutex>
+
+namespace {
+
+constexpr int kNoallocMaxSegments = 1 << 19;
+constexpr size_t kNoallocSegBytes = ht::align256(((size_t)kNoallocMaxSegments + 1) * 4);
+constexpr size_t kNoallocScratchBytes =
+    2 * kNoallocSegBytes + ht::align256(((size_t)kNoallocMaxSegments / 4096 + 2) * 4);
+constexpr int kNoallocMaxDevices = 64;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+std::once_flag g_noalloc_once[kNoallocMaxDevices];
+void *g_noalloc_ptr[kNoallocMaxDevices];
+cudaError_t g_noalloc_status[kNoallocMaxDevices];
+
+}  // namespace
+
+extern "C" ht_status ht_find_peaks_noalloc(const ht_geometry *g, const void *acc, ht_peak *peaks,
+                                           int32_t cap, int32_t *d_count, ht_stream stream)
+{
+    if (!g || !acc || !d_count || (cap > 0 && !peaks))
+        return ht::set_error(HT_ERR_ARG, "ht_find_peaks_noalloc: null argument");
+    if (cap < 0) return ht::set_error(HT_ERR_ARG, "ht_find_peaks_noalloc: cap < 0");
+    const size_t nkb = (g->G.n_phi0 + ht::kPkThreads - 1) / ht::kPkThreads;
+    const size_t nseg = (size_t)g->G.n_rho * g->G.n_d0 * nkb;
+    if (nseg > (size_t)kNoallocMaxSegments)
+        return ht::set_error(HT_ERR_CAPACITY,
+                             "ht_find_peaks_noalloc: geometry has more than 524288 segments "
+                             "(n_rho * n_d0 * ceil(n_phi0 / 256)); use ht_find_peaks");
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, "ht_find_peaks_noalloc: cudaGetDevice");
+    if (dev < 0 || dev >= kNoallocMaxDevices)
+        return ht::set_error(HT_ERR_ARG, "ht_find_peaks_noalloc: device index above 63");
+    std::call_once(g_noalloc_once[dev], [dev] {
+        g_noalloc_status[dev] = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
+    });
+    if (g_noalloc_status[dev] != cudaSuccess)
+        return ht::set_error(HT_ERR_CUDA,
+                             "ht_find_peaks_noalloc: cudaGetSymbolAddress of the scratch failed");
+    e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, g_noalloc_ptr[dev],
+                         reinterpret_cast<cudaStream_t>(stream));
+    if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+    return HT_OK;
+}

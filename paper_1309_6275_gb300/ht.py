@@ -48,6 +48,7 @@ SIGNATURES = [
     ("ht_vote", _I32, [_P, _P, _P, _I32, _P, _P, _P]),
     ("ht_find_peaks_workspace_size", _SZ, [_P]),
     ("ht_find_peaks", _I32, [_P, _P, _P, _I32, _P, _P, _SZ, _P]),
+    ("ht_find_peaks_noalloc", _I32, [_P, _P, _P, _I32, _P, _P]),
     ("ht_associate_workspace_size", _SZ, [_P, _I32, _I32]),
     ("ht_associate", _I32, [_P, _P, _P, _I32, _P, _P, _I32, _P, _P, _SZ, _P]),
     ("ht_vote_z_workspace_size", _SZ, [_P, _I32, _I32]),
@@ -151,6 +152,12 @@ def ht_find_peaks(g, acc, peaks, cap, d_count, workspace, stream=None):
     _check(lib().ht_find_peaks(g.handle, _ptr(acc), _ptr(peaks), cap, _ptr(d_count),
                                _ptr(workspace), workspace.numel(), _stream(stream)),
            "ht_find_peaks")
+
+
+def ht_find_peaks_noalloc(g, acc, peaks, cap, d_count, stream=None):
+    """ht_find_peaks with the library's fixed internal scratch (no workspace)."""
+    _check(lib().ht_find_peaks_noalloc(g.handle, _ptr(acc), _ptr(peaks), cap, _ptr(d_count),
+                                       _stream(stream)), "ht_find_peaks_noalloc")
 
 
 def ht_associate(g, x, y, peaks, d_count, cap, assign, workspace, stream=None):
