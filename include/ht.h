@@ -207,6 +207,54 @@ ht_status ht_run_event(const ht_geometry *g, const float *hx, const float *hy,
                        int32_t *h_count, int32_t *h_assign, ht_zres *h_zres,
                        uint64_t *h_stats, ht_stream stream);
 
+/* ------------------------------------------------------------------------
+ * Batched runtime: many events, uneven hit counts, one CUDA graph per batch.
+ * The paper processes one event at a time (Fig. 5); a batch runs the same
+ * four steps with identical results per event, but the vote and association
+ * run as persistent kernels over a device queue of (event, tile) items,
+ * largest events first, and the whole batch is captured once into a CUDA
+ * graph and replayed for every later batch with the same number of events.
+ * Requires count_bits 16.
+ * ------------------------------------------------------------------------ */
+typedef struct ht_batch ht_batch;   /* opaque */
+
+/* Create a batch runtime on the current device for up to max_events events,
+ * max_hits hits in total and cap candidates per event.  The runtime allocates
+ * its scratch once here (one accumulator per event slot, candidate lists,
+ * z-vote scratch; about 200 MB per slot for 256x128x512 with cap 2^21) and
+ * owns it.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_hits,
+                          int32_t cap, ht_batch **out);
+ht_status ht_batch_destroy(ht_batch *b);
+
+/* Enable (default) or disable CUDA-graph capture and replay. */
+ht_status ht_batch_set_graphs(ht_batch *b, int32_t enable);
+
+/* Run the path on n_events events whose hits are concatenated in x, y, z
+ * (device, float32) at host offsets h_off[0..n_events] (h_off[0] == 0,
+ * non-decreasing, h_off[n_events] <= max_hits).  Outputs (device, caller-owned):
+ *   peaks   n_events * cap entries; event e's candidates at peaks[e * cap];
+ *   counts  n_events int32 (total peaks of each event, may exceed cap);
+ *   assign  h_off[n_events] int32, candidate index within the hit's event;
+ *   zres    n_events * cap entries, like peaks;
+ *   stats   NULL or 2 * n_events uint64 (votes, float64 redos per event).
+ * Asynchronous on `stream`; the first call for a given n_events and set of
+ * buffer pointers captures the graph.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY,
+ * HT_ERR_CUDA. */
+ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float *z,
+                       const int32_t *h_off, int32_t n_events, ht_peak *peaks,
+                       int32_t *counts, int32_t *assign, ht_zres *zres, uint64_t *stats,
+                       ht_stream stream);
+
+/* Autotune the tile widths (phi0 columns per tile of the packed and unpacked
+ * vote, and of the association) by timing whole batches on the given sample
+ * (arguments as ht_batch_run).  *choice = kt_pack | kt_unpacked << 8 |
+ * kt_assoc << 16.  Synchronises the stream.  Errors: as ht_batch_run. */
+ht_status ht_batch_autotune(ht_batch *b, const float *x, const float *y, const float *z,
+                            const int32_t *h_off, int32_t n_events, ht_peak *peaks,
+                            int32_t *counts, int32_t *assign, ht_zres *zres, int32_t *choice,
+                            ht_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

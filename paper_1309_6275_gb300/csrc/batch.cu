@@ -1,0 +1,404 @@
+// batch.cu -- batched runtime (ht_batch_* in include/ht.h).
+//
+// A batch of events runs as one CUDA graph, captured once per batch shape and
+// replayed: persistent vote and association kernels pop (event, tile) items
+// from device counters (events ordered largest first, so 2k- and 60k-hit
+// events share the GPU without per-event launch tails); peak finding and
+// candidate lists run per event slot; the (z0, cot theta) vote runs over all
+// candidates of the batch at once.  Per-batch data (hit offsets, event order)
+// lives in device memory, uploaded from pinned staging before each replay,
+// so one graph serves every batch with the same number of events.  An
+// autotuner times the tile widths on a sample batch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "ht_internal.cuh"
+
+namespace ht {
+cudaError_t launch_vote_batch(const DevGeom &G, const float *x, const float *y, const int *off,
+                              const int *order, const int *d_nev, uint16_t *acc,
+                              size_t acc_stride, unsigned long long *stats, int *head, bool pack,
+                              int kt, int sms, cudaStream_t st);
+int assoc32_kt(const DevGeom &G);
+int assoc32_ntiles(const DevGeom &G, int kt);
+cudaError_t launch_cand_lists(const DevGeom &G, int kt, const ht_peak *peaks, const int *d_count,
+                              int cap, int *tcnt, int *toff, int *tcur, void *tmp, int *tlist,
+                              cudaStream_t st);
+cudaError_t launch_assoc_batch(const DevGeom &G, int kt, const float *x, const float *y,
+                               const int *off, const int *order, const int *d_nev,
+                               const ht_peak *peaks, int cap, const int *toff, size_t tstride,
+                               const int *tlist, size_t lstride, unsigned long long *gbest,
+                               int *head, int sms, cudaStream_t st);
+cudaError_t launch_assoc_final_batch(const unsigned long long *gbest, const int *off,
+                                     const int *d_nev, int *assign, int max_hits, cudaStream_t st);
+size_t vote_z_batch_workspace_bytes(int n_ev, int cap, int max_hits);
+cudaError_t launch_vote_z_batch(const DevGeom &G, const float *x, const float *y, const float *z,
+                                const int *assign, const int *off, const int *d_nev,
+                                const ht_peak *peaks, const int *counts, int cap, int n_ev,
+                                ht_zres *out, void *ws, int max_hits, cudaStream_t st);
+cudaError_t prepare_batch_kernels(int max_smem);
+}  // namespace ht
+
+namespace {
+
+constexpr int kPackMaxHits = 32767;   // packed 16-bit tile counters are exact up to here
+constexpr int kGraphCache = 4;
+
+struct GraphEntry {
+    int n_ev;
+    const void *ptr[9];
+    cudaGraphExec_t exec;
+};
+
+}  // namespace
+
+struct ht_batch {
+    const ht_geometry *g;
+    int max_events, max_hits, cap, sms;
+    int kt_pack, kt_big, kt_assoc;
+    size_t cells;
+    uint16_t *acc;
+    int *meta;          // [0] n_big [1] n_small [2] n_all [3] pad, off[max_events + 1],
+                        // order_big[max_events], order_small[max_events], order_all[max_events]
+    int *h_meta;        // pinned staging, same layout
+    size_t meta_ints;
+    cudaEvent_t meta_done;
+    bool meta_pending;
+    int *heads;
+    unsigned long long *gbest;
+    char *pk_ws;
+    size_t pk_stride;
+    int ntiles;
+    int *tcnt, *toff, *tcur;
+    char *ttmp;
+    size_t ttmp_stride;
+    int *tlist;
+    size_t lstride;
+    char *z_ws;
+    GraphEntry cache[kGraphCache];
+    int ncache;
+    bool use_graph;
+    cudaStream_t cap_stream;   // private stream that graphs are captured on
+};
+
+namespace {
+
+int *off_of(int *meta) { return meta + 4; }
+int *order_big_of(int *meta, int me) { return meta + 4 + me + 1; }
+int *order_small_of(int *meta, int me) { return meta + 4 + 2 * me + 1; }
+int *order_all_of(int *meta, int me) { return meta + 4 + 3 * me + 1; }
+
+void free_batch(ht_batch *b)
+{
+    if (!b) return;
+    for (int i = 0; i < b->ncache; ++i) cudaGraphExecDestroy(b->cache[i].exec);
+    cudaFree(b->acc);
+    cudaFree(b->meta);
+    cudaFree(b->heads);
+    cudaFree(b->gbest);
+    cudaFree(b->pk_ws);
+    cudaFree(b->tcnt);
+    cudaFree(b->toff);
+    cudaFree(b->tcur);
+    cudaFree(b->ttmp);
+    cudaFree(b->tlist);
+    cudaFree(b->z_ws);
+    if (b->h_meta) cudaFreeHost(b->h_meta);
+    if (b->meta_done) cudaEventDestroy(b->meta_done);
+    if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    delete b;
+}
+
+void clear_graphs(ht_batch *b)
+{
+    for (int i = 0; i < b->ncache; ++i) cudaGraphExecDestroy(b->cache[i].exec);
+    b->ncache = 0;
+}
+
+// Every launch of one batch, in order, on stream st.
+cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z, int n_ev,
+                    ht_peak *peaks, int32_t *counts, int32_t *assign, ht_zres *zres,
+                    uint64_t *stats, cudaStream_t st)
+{
+    const ht::DevGeom &G = b->g->G;
+    const int me = b->max_events;
+    int *meta = b->meta;
+    const int *off = off_of(meta);
+    unsigned long long *st64 = reinterpret_cast<unsigned long long *>(stats);
+    cudaError_t e = cudaMemsetAsync(b->heads, 0, 4 * sizeof(int), st);
+    if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, (size_t)n_ev * 16, st);
+    if (e != cudaSuccess) return e;
+    // vote: events above the packed-counter limit, then the others
+    e = ht::launch_vote_batch(G, x, y, off, order_big_of(meta, me), meta + 0, b->acc, b->cells,
+                              st64, b->heads + 0, false, b->kt_big, b->sms, st);
+    if (e != cudaSuccess) return e;
+    e = ht::launch_vote_batch(G, x, y, off, order_small_of(meta, me), meta + 1, b->acc, b->cells,
+                              st64, b->heads + 1, true, b->kt_pack, b->sms, st);
+    if (e != cudaSuccess) return e;
+    // peaks and candidate tile lists per event slot
+    for (int ev = 0; ev < n_ev; ++ev) {
+        e = ht::launch_peaks(G, b->acc + (size_t)ev * b->cells, peaks + (size_t)ev * b->cap,
+                             b->cap, counts + ev, b->pk_ws + (size_t)ev * b->pk_stride, st);
+        if (e != cudaSuccess) return e;
+        const size_t to = (size_t)ev * (b->ntiles + 1);
+        e = ht::launch_cand_lists(G, b->kt_assoc, peaks + (size_t)ev * b->cap, counts + ev,
+                                  b->cap, b->tcnt + to, b->toff + to, b->tcur + to,
+                                  b->ttmp + (size_t)ev * b->ttmp_stride,
+                                  b->tlist + (size_t)ev * b->lstride, st);
+        if (e != cudaSuccess) return e;
+    }
+    // association over the whole batch
+    e = cudaMemsetAsync(b->gbest, 0, (size_t)b->max_hits * 8, st);
+    if (e != cudaSuccess) return e;
+    e = ht::launch_assoc_batch(G, b->kt_assoc, x, y, off, order_all_of(meta, me), meta + 2, peaks,
+                               b->cap, b->toff, (size_t)b->ntiles + 1, b->tlist, b->lstride,
+                               b->gbest, b->heads + 2, b->sms, st);
+    if (e != cudaSuccess) return e;
+    e = ht::launch_assoc_final_batch(b->gbest, off, meta + 2, assign, b->max_hits, st);
+    if (e != cudaSuccess) return e;
+    return ht::launch_vote_z_batch(G, x, y, z, assign, off, meta + 2, peaks, counts, b->cap, n_ev,
+                                   zres, b->z_ws, b->max_hits, st);
+}
+
+// Upload offsets and the largest-first event orders for this batch.
+ht_status stage_meta(ht_batch *b, const int32_t *h_off, int n_ev, cudaStream_t st)
+{
+    if (b->meta_pending) {
+        cudaError_t e = cudaEventSynchronize(b->meta_done);
+        if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, "ht_batch_run: staging wait");
+        b->meta_pending = false;
+    }
+    const int me = b->max_events;
+    int *hm = b->h_meta;
+    memset(hm, 0, b->meta_ints * sizeof(int));
+    std::vector<int> idx(n_ev);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
+        return h_off[a + 1] - h_off[a] > h_off[c + 1] - h_off[c];
+    });
+    int nb = 0, ns = 0;
+    for (int i = 0; i < n_ev; ++i) {
+        const int ev = idx[i];
+        if (h_off[ev + 1] - h_off[ev] > kPackMaxHits) order_big_of(hm, me)[nb++] = ev;
+        else order_small_of(hm, me)[ns++] = ev;
+        order_all_of(hm, me)[i] = ev;
+    }
+    hm[0] = nb;
+    hm[1] = ns;
+    hm[2] = n_ev;
+    for (int i = 0; i <= n_ev; ++i) off_of(hm)[i] = h_off[i];
+    for (int i = n_ev + 1; i <= me; ++i) off_of(hm)[i] = h_off[n_ev];
+    cudaError_t e = cudaMemcpyAsync(b->meta, hm, b->meta_ints * sizeof(int), cudaMemcpyHostToDevice,
+                                    st);
+    if (e == cudaSuccess) e = cudaEventRecord(b->meta_done, st);
+    if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, "ht_batch_run: staging upload");
+    b->meta_pending = true;
+    return HT_OK;
+}
+
+ht_status check_offsets(const ht_batch *b, const int32_t *h_off, int n_ev)
+{
+    if (!h_off || h_off[0] != 0)
+        return ht::set_error(HT_ERR_ARG, "ht_batch: h_off must start at 0");
+    for (int i = 0; i < n_ev; ++i)
+        if (h_off[i + 1] < h_off[i])
+            return ht::set_error(HT_ERR_ARG, "ht_batch: h_off must be non-decreasing");
+    if (h_off[n_ev] > b->max_hits)
+        return ht::set_error(HT_ERR_CAPACITY, "ht_batch: more hits than max_hits");
+    return HT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_hits, int32_t cap,
+                          ht_batch **out)
+{
+    if (!g || !out) return ht::set_error(HT_ERR_ARG, "ht_batch_create: null argument");
+    *out = nullptr;
+    if (g->desc.count_bits != 16)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_create: batches need count_bits 16");
+    if (max_events < 1 || max_events > 4096 || max_hits < 1 || cap < 1 ||
+        (int64_t)max_events * cap > (int64_t)1 << 30)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_create: sizes out of range");
+    ht_batch *b = new (std::nothrow) ht_batch();
+    if (!b) return ht::set_error(HT_ERR_ARG, "ht_batch_create: out of host memory");
+    b->g = g;
+    b->max_events = max_events;
+    b->max_hits = max_hits;
+    b->cap = cap;
+    b->use_graph = true;
+    const ht::DevGeom &G = g->G;
+    int dev = 0, max_smem = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e == cudaSuccess) e = ht::prepare_batch_kernels(max_smem);
+    b->kt_pack = 0;
+    b->kt_big = 0;
+    b->kt_assoc = ht::assoc32_kt(G);
+    b->cells = (size_t)G.n_rho * G.n_d0 * G.n_phi0;
+    b->meta_ints = 4 + (size_t)max_events + 1 + 3 * (size_t)max_events;
+    b->pk_stride = ht::align256(ht::peaks_workspace_bytes(G));
+    b->ntiles = ht::assoc32_ntiles(G, 1);   // the most tiles any tile width gives
+    b->ttmp_stride = ht::scan_tmp_bytes(b->ntiles);
+    b->lstride = (size_t)6 * cap;     // a candidate's box touches at most 6 tiles
+    const size_t tl = (size_t)max_events * (b->ntiles + 1) * 4;
+    auto M = [&](void **p, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(p, bytes);
+    };
+    M((void **)&b->acc, b->cells * 2 * max_events);
+    M((void **)&b->meta, b->meta_ints * 4);
+    M((void **)&b->heads, 256);
+    M((void **)&b->gbest, (size_t)max_hits * 8);
+    M((void **)&b->pk_ws, b->pk_stride * max_events);
+    M((void **)&b->tcnt, tl);
+    M((void **)&b->toff, tl);
+    M((void **)&b->tcur, tl);
+    M((void **)&b->ttmp, b->ttmp_stride * max_events);
+    M((void **)&b->tlist, b->lstride * sizeof(int) * max_events);
+    M((void **)&b->z_ws, ht::vote_z_batch_workspace_bytes(max_events, cap, max_hits));
+    if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_meta, b->meta_ints * 4);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->meta_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+        free_batch(b);
+        return ht::set_error(HT_ERR_CUDA, "ht_batch_create: allocation or set-up failed");
+    }
+    *out = b;
+    return HT_OK;
+}
+
+ht_status ht_batch_destroy(ht_batch *b)
+{
+    if (b && b->meta_pending) cudaEventSynchronize(b->meta_done);
+    free_batch(b);
+    return HT_OK;
+}
+
+ht_status ht_batch_set_graphs(ht_batch *b, int32_t enable)
+{
+    if (!b) return ht::set_error(HT_ERR_ARG, "ht_batch_set_graphs: null batch");
+    b->use_graph = enable != 0;
+    return HT_OK;
+}
+
+ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float *z,
+                       const int32_t *h_off, int32_t n_events, ht_peak *peaks, int32_t *counts,
+                       int32_t *assign, ht_zres *zres, uint64_t *stats, ht_stream stream)
+{
+    if (!b || !x || !y || !z || !peaks || !counts || !assign || !zres)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run: null argument");
+    if (n_events < 1 || n_events > b->max_events)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run: n_events out of range");
+    ht_status s = check_offsets(b, h_off, n_events);
+    if (s != HT_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    s = stage_meta(b, h_off, n_events, st);
+    if (s != HT_OK) return s;
+    if (!b->use_graph) {
+        cudaError_t e = enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, st);
+        return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    const void *key[9] = {x, y, z, peaks, counts, assign, zres, stats, nullptr};
+    for (int i = 0; i < b->ncache; ++i) {
+        GraphEntry &c = b->cache[i];
+        if (c.n_ev == n_events && memcmp(c.ptr, key, sizeof key) == 0) {
+            cudaError_t e = cudaGraphLaunch(c.exec, st);
+            return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+        }
+    }
+    // capture on the private stream (the caller's may be the legacy default
+    // stream, which cannot be captured); the graph is launched on the caller's
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        const cudaError_t eq =
+            enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, b->cap_stream);
+        e = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (eq != cudaSuccess) e = eq;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+    if (b->ncache == kGraphCache) {
+        cudaGraphExecDestroy(b->cache[0].exec);
+        memmove(&b->cache[0], &b->cache[1], sizeof(GraphEntry) * (kGraphCache - 1));
+        --b->ncache;
+    }
+    GraphEntry &c = b->cache[b->ncache++];
+    c.n_ev = n_events;
+    memcpy(c.ptr, key, sizeof key);
+    c.exec = exec;
+    e = cudaGraphLaunch(exec, st);
+    return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+ht_status ht_batch_autotune(ht_batch *b, const float *x, const float *y, const float *z,
+                            const int32_t *h_off, int32_t n_events, ht_peak *peaks,
+                            int32_t *counts, int32_t *assign, ht_zres *zres, int32_t *choice,
+                            ht_stream stream)
+{
+    if (!b || !choice) return ht::set_error(HT_ERR_ARG, "ht_batch_autotune: null argument");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const ht::DevGeom &G = b->g->G;
+    cudaEvent_t t0, t1;
+    cudaEventCreate(&t0);
+    cudaEventCreate(&t1);
+    const bool graphs = b->use_graph;
+    b->use_graph = false;
+    auto time_run = [&](float &ms) -> ht_status {
+        ht_status s = ht_batch_run(b, x, y, z, h_off, n_events, peaks, counts, assign, zres,
+                                   nullptr, stream);
+        if (s != HT_OK) return s;
+        cudaEventRecord(t0, st);
+        s = ht_batch_run(b, x, y, z, h_off, n_events, peaks, counts, assign, zres, nullptr,
+                         stream);
+        if (s != HT_OK) return s;
+        cudaEventRecord(t1, st);
+        if (cudaEventSynchronize(t1) != cudaSuccess)
+            return ht::set_error(HT_ERR_CUDA, "ht_batch_autotune: timing");
+        cudaEventElapsedTime(&ms, t0, t1);
+        return HT_OK;
+    };
+    const int packs[3] = {4, 2, 1}, bigs[3] = {8, 4, 2}, assocs[3] = {4, 2, 1};
+    int best_pack = 0, best_big = 0, best_assoc = ht::assoc32_kt(G);
+    float best = 3.0e38f, ms = 0.f;
+    ht_status s = HT_OK;
+    const int assoc_default = ht::assoc32_kt(G);
+    for (int ip = 0; ip < 3 && s == HT_OK; ++ip) {
+        b->kt_pack = packs[ip];
+        b->kt_big = bigs[ip];
+        b->kt_assoc = assoc_default;
+        s = time_run(ms);
+        if (s == HT_OK && ms < best) { best = ms; best_pack = packs[ip]; best_big = bigs[ip]; }
+    }
+    b->kt_pack = best_pack;
+    b->kt_big = best_big;
+    best = 3.0e38f;
+    for (int ia = 0; ia < 3 && s == HT_OK; ++ia) {
+        if (assocs[ia] > assoc_default) continue;   // wider tiles do not fit three CTAs per SM
+        b->kt_assoc = assocs[ia];
+        s = time_run(ms);
+        if (s == HT_OK && ms < best) { best = ms; best_assoc = assocs[ia]; }
+    }
+    b->kt_assoc = best_assoc;
+    b->use_graph = graphs;
+    clear_graphs(b);
+    cudaEventDestroy(t0);
+    cudaEventDestroy(t1);
+    if (s != HT_OK) return s;
+    *choice = b->kt_pack | (b->kt_big << 8) | (b->kt_assoc << 16);
+    return HT_OK;
+}
+
+}  // extern "C"

@@ -68,10 +68,10 @@ struct TileCtx {
     float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB;
     float sk[KT], ck[KT], pk[KT];
 
-    __device__ __forceinline__ void init(const DevGeom &G, int lane)
+    __device__ __forceinline__ void init(const DevGeom &G, int lane, int tx, int ty)
     {
-        k0 = blockIdx.x * KT;
-        i0 = blockIdx.y * 32;
+        k0 = tx * KT;
+        i0 = ty * 32;
         irow = i0 + lane;
         row_ok = irow < G.n_rho;
         rho = row_ok ? G.rho32[irow] : 0.0f;
@@ -224,9 +224,10 @@ __device__ __forceinline__ uint32_t tile_get(const uint32_t *cnt, int ND, int kl
 }
 
 template <int KT, typename OutT, bool PACK>
-__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
-k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
-       OutT *__restrict__ acc, unsigned long long *__restrict__ stats)
+__device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restrict__ x,
+                                          const float *__restrict__ y, int n,
+                                          OutT *__restrict__ acc,
+                                          unsigned long long *__restrict__ stats, int tx, int ty)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
@@ -242,7 +243,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = kThreads / 32;
     TileCtx<KT> T;
-    T.init(G, lane);
+    T.init(G, lane, tx, ty);
     {
         uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
         for (int t = threadIdx.x; t < KT * NW * 8; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
@@ -337,6 +338,41 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
     }
 }
 
+template <int KT, typename OutT, bool PACK>
+__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
+k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
+       OutT *__restrict__ acc, unsigned long long *__restrict__ stats)
+{
+    vote_tile<KT, OutT, PACK>(G, x, y, n, acc, stats, blockIdx.x, blockIdx.y);
+}
+
+// Persistent vote over a batch: CTAs pop (event, tile) items from a device
+// counter; items run event by event in the order given (largest events
+// first), so uneven events share the GPU without per-event launch tails.
+template <int KT, typename OutT, bool PACK>
+__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
+k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
+             const int *__restrict__ off, const int *__restrict__ order,
+             const int *__restrict__ d_nev,
+             OutT *__restrict__ acc, size_t acc_stride, unsigned long long *__restrict__ stats,
+             int *__restrict__ head)
+{
+    __shared__ int s_item;
+    const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 31) / 32, ntiles = ntx * nty;
+    const int total = *d_nev * ntiles;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int e = order[item / ntiles], t = item % ntiles;
+        const int a = off[e], n = off[e + 1] - a;
+        vote_tile<KT, OutT, PACK>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
+                                  stats ? stats + 2 * e : nullptr, t % ntx, t / ntx);
+        __syncthreads();
+    }
+}
+
 // ----------------------------------------------------------- association
 __device__ __forceinline__ int lower_bound_l(const ht_peak *__restrict__ pk, int n,
                                              long long l, int ND, int NP)
@@ -371,7 +407,7 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = kThreads / 32;
     TileCtx<KT> T;
-    T.init(G, lane);
+    T.init(G, lane, blockIdx.x, blockIdx.y);
     {
         uint4 *m4 = reinterpret_cast<uint4 *>(map);
         for (int t = threadIdx.x; t < KT * ND * 16; t += kThreads) m4[t] = make_uint4(0, 0, 0, 0);
@@ -491,8 +527,12 @@ __global__ void k_assoc_final(const unsigned long long *__restrict__ gbest, int 
 // Peaks form an independent set of the 26-neighbour grid (of two adjacent
 // cells at most one can be a peak), so a tile's list holds at most one
 // candidate per 2x2x2 block of its 34 x (KT + 2) x n_d0 halo region.
+// Tiles a candidate's box touches: up to 2 row tiles x 3 column tiles (3
+// column tiles only when a tile is one column wide).
+constexpr int kMaxTilesPerCand = 6;
+
 __device__ __forceinline__ int tiles_of(const ht_peak &p, int NR, int NP, int KT, int nct,
-                                        int out[4])
+                                        int out[kMaxTilesPerCand])
 {
     const int rt0 = max(p.i_rho - 1, 0) >> 5, rt1 = min(p.i_rho + 1, NR - 1) >> 5;
     int ct[3], nc = 0;
@@ -518,7 +558,7 @@ __global__ void k_cand_tiles(const ht_peak *__restrict__ peaks, const int *__res
 {
     const int ncand = min(*d_count, cap);
     for (int m = blockIdx.x * blockDim.x + threadIdx.x; m < ncand; m += gridDim.x * blockDim.x) {
-        int t[4];
+        int t[kMaxTilesPerCand];
         const int nt = tiles_of(peaks[m], NR, NP, KT, nct, t);
         for (int u = 0; u < nt; ++u) {
             if (list) list[atomicAdd(&tcur[t[u]], 1)] = m;
@@ -528,10 +568,13 @@ __global__ void k_cand_tiles(const ht_peak *__restrict__ peaks, const int *__res
 }
 
 template <int KT>
-__global__ void __launch_bounds__(kThreads, 3)
-k_assoc32(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
-          const ht_peak *__restrict__ peaks, const int *__restrict__ toff,
-          const int *__restrict__ tlist, int lcap, unsigned long long *__restrict__ gbest)
+__device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__restrict__ x,
+                                             const float *__restrict__ y, int n,
+                                             const ht_peak *__restrict__ peaks,
+                                             const int *__restrict__ toff,
+                                             const int *__restrict__ tlist, int lcap,
+                                             unsigned long long *__restrict__ gbest, int tx,
+                                             int ty)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
@@ -547,8 +590,8 @@ k_assoc32(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, i
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = kThreads / 32;
     TileCtx<KT> T;
-    T.init(G, lane);
-    const int tile = blockIdx.y * gridDim.x + blockIdx.x;
+    T.init(G, lane, tx, ty);
+    const int tile = ty * (G.n_phi0 / KT) + tx;
     const int l0 = toff[tile];
     const int L = min(toff[tile + 1] - l0, lcap);
 
@@ -652,6 +695,45 @@ k_assoc32(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, i
             __syncthreads();
             if (threadIdx.x == 0) rn = 0;
         }
+    }
+}
+
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 3)
+k_assoc32(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
+          const ht_peak *__restrict__ peaks, const int *__restrict__ toff,
+          const int *__restrict__ tlist, int lcap, unsigned long long *__restrict__ gbest)
+{
+    assoc32_tile<KT>(G, x, y, n, peaks, toff, tlist, lcap, gbest, blockIdx.x, blockIdx.y);
+}
+
+// Persistent association over a batch, items as in k_vote_batch.  Event e
+// uses peaks + e * cap, its tile lists at toff + e * (ntiles + 1) and
+// tlist + e * lstride, and its hits' keys at gbest + off[e].
+template <int KT>
+__global__ void __launch_bounds__(kThreads, 3)
+k_assoc32_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
+                const int *__restrict__ off, const int *__restrict__ order,
+                const int *__restrict__ d_nev,
+                const ht_peak *__restrict__ peaks, int cap, const int *__restrict__ toff,
+                size_t tstride, const int *__restrict__ tlist, size_t lstride, int lcap,
+                unsigned long long *__restrict__ gbest, int *__restrict__ head)
+{
+    __shared__ int s_item;
+    const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 31) / 32, ntiles = ntx * nty;
+    const int total = *d_nev * ntiles;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= total) break;
+        const int e = order[item / ntiles], t = item % ntiles;
+        const int a = off[e], n = off[e + 1] - a;
+        if (n > 0)
+            assoc32_tile<KT>(G, x + a, y + a, n, peaks + (size_t)e * cap,
+                             toff + (size_t)e * tstride, tlist + (size_t)e * lstride, lcap,
+                             gbest + a, t % ntx, t / ntx);
+        __syncthreads();
     }
 }
 
@@ -802,7 +884,7 @@ cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n,
 
 // Association workspace: per-hit best keys, then (uint16 geometries) the
 // per-tile candidate lists: counts, offsets, cursors, scan scratch and up to
-// four tile entries per candidate.
+// kMaxTilesPerCand tile entries per candidate.
 size_t associate_workspace_bytes(const DevGeom &G, int n, int cap)
 {
     size_t b = align256((size_t)(n > 0 ? n : 1) * 8);
@@ -810,7 +892,7 @@ size_t associate_workspace_bytes(const DevGeom &G, int n, int cap)
     const int ntiles = (G.n_phi0 / 1) * ((G.n_rho + 31) / 32);
     (void)KT;
     b += 3 * align256((size_t)(ntiles + 1) * 4) + scan_tmp_bytes(ntiles) +
-         align256((size_t)(cap > 0 ? cap : 1) * 4 * 4);
+         align256((size_t)(cap > 0 ? cap : 1) * kMaxTilesPerCand * 4);
     return b;
 }
 
@@ -840,6 +922,135 @@ cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, i
     if (e != cudaSuccess) return e;
     k_assoc_final<<<(n + 255) / 256, 256, 0, st>>>(gbest, n, assign);
     return cudaGetLastError();
+}
+
+// ------------------------------------------------------------- batches
+// Persistent vote of a batch: `order` lists d_nev[0] event slots; every CTA
+// slot of the GPU (SMs x resident CTAs) pops items until the queue is empty.
+// kt selects the tile width (0 = default), pack the 16-bit packed counters
+// (valid when every listed event has <= 32767 hits).  *head must be zero.
+cudaError_t launch_vote_batch(const DevGeom &G, const float *x, const float *y, const int *off,
+                              const int *order, const int *d_nev, uint16_t *acc,
+                              size_t acc_stride, unsigned long long *stats, int *head, bool pack,
+                              int kt, int sms, cudaStream_t st)
+{
+#define HT_VB(KTV, PK)                                                                        \
+    do {                                                                                      \
+        int occ = 0;                                                                          \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vote_batch<KTV, uint16_t, PK>,  \
+                                                      kThreads, vote_smem<KTV>(G, PK));       \
+        k_vote_batch<KTV, uint16_t, PK><<<sms * (occ > 0 ? occ : 1), kThreads,               \
+                                          vote_smem<KTV>(G, PK), st>>>(                       \
+            G, x, y, off, order, d_nev, acc, acc_stride, stats, head);                        \
+        return cudaGetLastError();                                                            \
+    } while (0)
+    if (pack) {
+        if (kt == 0) kt = vote_smem<4>(G, true) <= kSmemBudget3 ? 4
+                        : vote_smem<2>(G, true) <= kSmemBudget3 ? 2 : 1;
+        if (kt == 4 && vote_smem<4>(G, true) <= kSmemBudget2) HT_VB(4, true);
+        if (kt >= 2 && vote_smem<2>(G, true) <= kSmemBudget2) HT_VB(2, true);
+        HT_VB(1, true);
+    }
+    if (kt == 0) kt = vote_smem<8>(G, false) <= kSmemBudget2 ? 8
+                    : vote_smem<4>(G, false) <= kSmemBudget2 ? 4
+                    : vote_smem<2>(G, false) <= kSmemBudget2 ? 2 : 1;
+    if (kt == 8 && vote_smem<8>(G, false) <= kSmemBudget2) HT_VB(8, false);
+    if (kt >= 4 && vote_smem<4>(G, false) <= kSmemBudget2) HT_VB(4, false);
+    if (kt >= 2 && vote_smem<2>(G, false) <= kSmemBudget2) HT_VB(2, false);
+    HT_VB(1, false);
+#undef HT_VB
+}
+
+// Association tile width for uint16 geometries (largest fitting three CTAs
+// per SM) and the matching per-event tile-list sizes.
+int assoc32_kt(const DevGeom &G)
+{
+    return assoc32_smem<4>(G) <= kSmemBudget3 ? 4 : assoc32_smem<2>(G) <= kSmemBudget3 ? 2 : 1;
+}
+
+int assoc32_ntiles(const DevGeom &G, int kt) { return (G.n_phi0 / kt) * ((G.n_rho + 31) / 32); }
+
+// Per-event candidate tile lists (count, scan, scatter) into caller-carved
+// buffers: tcnt/toff/tcur (ntiles + 1), tmp (scan), tlist (6 cap).
+cudaError_t launch_cand_lists(const DevGeom &G, int kt, const ht_peak *peaks, const int *d_count,
+                              int cap, int *tcnt, int *toff, int *tcur, void *tmp, int *tlist,
+                              cudaStream_t st)
+{
+    const int nct = G.n_phi0 / kt, ntiles = assoc32_ntiles(G, kt);
+    cudaError_t e = cudaMemsetAsync(tcnt, 0, (size_t)ntiles * 4, st);
+    if (e != cudaSuccess) return e;
+    const int nb = min(4096, (cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1);
+    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, kt, nct, tcnt,
+                                     nullptr, nullptr);
+    e = scan_exclusive(tcnt, toff, tcur, ntiles, nullptr, nullptr, tmp, st);
+    if (e != cudaSuccess) return e;
+    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, kt, nct, nullptr,
+                                     tcur, tlist);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_assoc_batch(const DevGeom &G, int kt, const float *x, const float *y,
+                               const int *off, const int *order, const int *d_nev,
+                               const ht_peak *peaks, int cap, const int *toff, size_t tstride,
+                               const int *tlist, size_t lstride, unsigned long long *gbest,
+                               int *head, int sms, cudaStream_t st)
+{
+#define HT_AB(KTV)                                                                            \
+    do {                                                                                      \
+        int occ = 0;                                                                          \
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_assoc32_batch<KTV>, kThreads,   \
+                                                      assoc32_smem<KTV>(G));                  \
+        k_assoc32_batch<KTV><<<sms * (occ > 0 ? occ : 1), kThreads, assoc32_smem<KTV>(G),    \
+                               st>>>(G, x, y, off, order, d_nev, peaks, cap, toff, tstride,   \
+                                     tlist, lstride, assoc32_lcap<KTV>(G), gbest, head);      \
+        return cudaGetLastError();                                                            \
+    } while (0)
+    if (kt == 4) HT_AB(4);
+    if (kt == 2) HT_AB(2);
+    HT_AB(1);
+#undef HT_AB
+}
+
+__global__ void k_assoc_final_batch(const unsigned long long *__restrict__ gbest,
+                                    const int *__restrict__ off, const int *__restrict__ d_nev,
+                                    int *__restrict__ assign)
+{
+    const int n = off[*d_nev];
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+        const unsigned long long b = gbest[h];
+        assign[h] = b ? (int)(0xffffffffu - (unsigned)(b & 0xffffffffull)) : -1;
+    }
+}
+
+cudaError_t launch_assoc_final_batch(const unsigned long long *gbest, const int *off,
+                                     const int *d_nev, int *assign, int max_hits, cudaStream_t st)
+{
+    k_assoc_final_batch<<<min(4096, (max_hits + 255) / 256 + 1), 256, 0, st>>>(gbest, off,
+                                                                               d_nev, assign);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_batch_kernels(int max_smem)
+{
+    const void *fns[] = {(const void *)k_vote_batch<4, uint16_t, true>,
+                         (const void *)k_vote_batch<2, uint16_t, true>,
+                         (const void *)k_vote_batch<1, uint16_t, true>,
+                         (const void *)k_vote_batch<8, uint16_t, false>,
+                         (const void *)k_vote_batch<4, uint16_t, false>,
+                         (const void *)k_vote_batch<2, uint16_t, false>,
+                         (const void *)k_vote_batch<1, uint16_t, false>,
+                         (const void *)k_assoc32_batch<4>,
+                         (const void *)k_assoc32_batch<2>,
+                         (const void *)k_assoc32_batch<1>};
+    for (const void *f : fns) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 }  // namespace ht

@@ -140,6 +140,46 @@ __global__ void k_z_scatter(const int *__restrict__ assign, int n, const int *__
     }
 }
 
+// (z0, cot theta) result of one candidate with 1..32 hits list[o .. o + nh),
+// one warp, lane = hit.  Every lane returns the result.
+__device__ __forceinline__ ht_zres z_small_cand(const DevGeom &G, const float *__restrict__ x,
+                                                const float *__restrict__ y,
+                                                const float *__restrict__ z, const ht_peak &pk,
+                                                const int *__restrict__ list, int o, int nh,
+                                                int lane)
+{
+    const ZCand C = z_cand(G, pk);
+    const bool act = lane < nh;
+    float xf = 0.f, yf = 0.f, zf = 0.f, L = 0.f, eL = 0.f;
+    if (act) {
+        const int h = list[o + lane];
+        xf = x[h];
+        yf = y[h];
+        zf = z[h];
+        arc32(C, xf, yf, L, eL);
+    }
+    bool have64 = false;
+    double L64 = 0.0;
+    unsigned best_c = 0u;
+    int best_idx = 0x7fffffff;
+    for (int q = 0; q < G.n_cot; ++q) {
+        const int nb = act ? z_bin(G, C, xf, yf, zf, L, eL, q, have64, L64) : -1;
+        const unsigned peers = __match_any_sync(0xffffffffu, nb);
+        const unsigned key = nb >= 0 ? ((unsigned)__popc(peers) << 16) | (0xffffu - (unsigned)nb) : 0u;
+        const unsigned top = __reduce_max_sync(0xffffffffu, key);
+        if (top) {
+            const unsigned cq = top >> 16;
+            const int idx = (int)(0xffffu - (top & 0xffffu)) * G.n_cot + q;
+            if (cq > best_c || (cq == best_c && idx < best_idx)) {
+                best_c = cq;
+                best_idx = idx;
+            }
+        }
+    }
+    return best_c ? ht_zres{best_idx / G.n_cot, best_idx % G.n_cot, (int)best_c}
+                  : ht_zres{-1, -1, 0};
+}
+
 // One warp per candidate with <= 32 hits; larger ones go to the big list.
 __global__ void k_z_small(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
                           const float *__restrict__ z, const ht_peak *__restrict__ peaks,
@@ -161,46 +201,18 @@ __global__ void k_z_small(DevGeom G, const float *__restrict__ x, const float *_
             if (lane == 0) big[atomicAdd(nbig, 1)] = m;
             continue;
         }
-        const ZCand C = z_cand(G, peaks[m]);
-        const bool act = lane < nh;
-        float xf = 0.f, yf = 0.f, zf = 0.f, L = 0.f, eL = 0.f;
-        if (act) {
-            const int h = list[o + lane];
-            xf = x[h];
-            yf = y[h];
-            zf = z[h];
-            arc32(C, xf, yf, L, eL);
-        }
-        bool have64 = false;
-        double L64 = 0.0;
-        unsigned best_c = 0u;
-        int best_idx = 0x7fffffff;
-        for (int q = 0; q < G.n_cot; ++q) {
-            const int nb = act ? z_bin(G, C, xf, yf, zf, L, eL, q, have64, L64) : -1;
-            const unsigned peers = __match_any_sync(0xffffffffu, nb);
-            const unsigned key = nb >= 0 ? ((unsigned)__popc(peers) << 16) | (0xffffu - (unsigned)nb) : 0u;
-            const unsigned top = __reduce_max_sync(0xffffffffu, key);
-            if (top) {
-                const unsigned cq = top >> 16;
-                const int idx = (int)(0xffffu - (top & 0xffffu)) * G.n_cot + q;
-                if (cq > best_c || (cq == best_c && idx < best_idx)) {
-                    best_c = cq;
-                    best_idx = idx;
-                }
-            }
-        }
-        if (lane == 0)
-            out[m] = best_c ? ht_zres{best_idx / G.n_cot, best_idx % G.n_cot, (int)best_c}
-                            : ht_zres{-1, -1, 0};
+        const ht_zres r = z_small_cand(G, x, y, z, peaks[m], list, o, nh, lane);
+        if (lane == 0) out[m] = r;
     }
 }
 
-// One CTA per candidate of the big list: shared histogram, block argmax.
-__global__ void __launch_bounds__(kBigThreads)
-k_z_big(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
-        const float *__restrict__ z, const ht_peak *__restrict__ peaks,
-        const int *__restrict__ off, const int *__restrict__ list,
-        const int *__restrict__ big, const int *__restrict__ nbig, ht_zres *__restrict__ out)
+// (z0, cot theta) result of one candidate with any number of hits, one CTA:
+// n_z0 x n_cot uint32 histogram in shared memory and a block argmax.
+// Thread 0 returns the result.  All threads must call.
+__device__ __forceinline__ ht_zres z_big_cand(const DevGeom &G, const float *__restrict__ x,
+                                              const float *__restrict__ y,
+                                              const float *__restrict__ z, const ht_peak &pk,
+                                              const int *__restrict__ list, int o, int nh)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     unsigned *hist = reinterpret_cast<unsigned *>(smem);
@@ -208,54 +220,136 @@ k_z_big(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
         sz[kBigThreads];
     __shared__ unsigned long long red[kBigThreads / 32];
     const int NC = G.n_cot, NZ = G.n_z0, ncell = NZ * NC;
+    const ZCand C = z_cand(G, pk);
+    for (int t = threadIdx.x; t < ncell; t += kBigThreads) hist[t] = 0u;
+    for (int c0 = 0; c0 < nh; c0 += kBigThreads) {
+        __syncthreads();
+        const int hc = min(kBigThreads, nh - c0);
+        if (threadIdx.x < hc) {
+            const int h = list[o + c0 + threadIdx.x];
+            sx[threadIdx.x] = x[h];
+            sy[threadIdx.x] = y[h];
+            sz[threadIdx.x] = z[h];
+            arc32(C, sx[threadIdx.x], sy[threadIdx.x], sL[threadIdx.x], seL[threadIdx.x]);
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < hc * NC; t += kBigThreads) {
+            const int hl = t / NC, q = t - hl * NC;
+            bool have64 = false;
+            double L64 = 0.0;
+            const int nbin = z_bin(G, C, sx[hl], sy[hl], sz[hl], sL[hl], seL[hl], q, have64, L64);
+            if (nbin >= 0) atomicAdd(&hist[nbin * NC + q], 1u);
+        }
+    }
+    __syncthreads();
+    // argmax: key = count << 32 | ~index (largest count, then smallest index)
+    unsigned long long bk = 0ull;
+    for (int t = threadIdx.x; t < ncell; t += kBigThreads) {
+        const unsigned c = hist[t];
+        const unsigned long long k = ((unsigned long long)c << 32) | (0xffffffffull - (unsigned)t);
+        if (c && k > bk) bk = k;
+    }
+#pragma unroll
+    for (int s = 16; s > 0; s >>= 1) bk = max(bk, __shfl_xor_sync(0xffffffffu, bk, s));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bk;
+    __syncthreads();
+    ht_zres r{-1, -1, 0};
+    if (threadIdx.x == 0) {
+        unsigned long long b = 0ull;
+        for (int w = 0; w < kBigThreads / 32; ++w) b = max(b, red[w]);
+        if (b) {
+            const int idx = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
+            r = ht_zres{idx / NC, idx % NC, (int)(b >> 32)};
+        }
+    }
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kBigThreads)
+k_z_big(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
+        const float *__restrict__ z, const ht_peak *__restrict__ peaks,
+        const int *__restrict__ off, const int *__restrict__ list,
+        const int *__restrict__ big, const int *__restrict__ nbig, ht_zres *__restrict__ out)
+{
     const int nb = *nbig;
     for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) {
         const int m = big[bi];
-        const int o = off[m], nh = off[m + 1] - o;
-        const ZCand C = z_cand(G, peaks[m]);
-        for (int t = threadIdx.x; t < ncell; t += kBigThreads) hist[t] = 0u;
-        for (int c0 = 0; c0 < nh; c0 += kBigThreads) {
-            __syncthreads();
-            const int hc = min(kBigThreads, nh - c0);
-            if (threadIdx.x < hc) {
-                const int h = list[o + c0 + threadIdx.x];
-                sx[threadIdx.x] = x[h];
-                sy[threadIdx.x] = y[h];
-                sz[threadIdx.x] = z[h];
-                arc32(C, sx[threadIdx.x], sy[threadIdx.x], sL[threadIdx.x], seL[threadIdx.x]);
-            }
-            __syncthreads();
-            for (int t = threadIdx.x; t < hc * NC; t += kBigThreads) {
-                const int hl = t / NC, q = t - hl * NC;
-                bool have64 = false;
-                double L64 = 0.0;
-                const int nbin = z_bin(G, C, sx[hl], sy[hl], sz[hl], sL[hl], seL[hl], q, have64, L64);
-                if (nbin >= 0) atomicAdd(&hist[nbin * NC + q], 1u);
-            }
+        const ht_zres r = z_big_cand(G, x, y, z, peaks[m], list, off[m], off[m + 1] - off[m]);
+        if (threadIdx.x == 0) out[m] = r;
+    }
+}
+
+// ---------------------------------------------------------------- batches
+// Global candidate id g = e * cap + m (event slot e, candidate m); hits carry
+// batch-wide indices; off[0..n_ev] are the events' hit offsets.
+__device__ __forceinline__ int event_of(const int *__restrict__ off, int n_ev, int h)
+{
+    int lo = 0, hi = n_ev;          // off[lo] <= h < off[hi]
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= h) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void k_zb_group(const int *__restrict__ assign, const int *__restrict__ off,
+                           const int *__restrict__ d_nev, const int *__restrict__ counts,
+                           int cap, int *__restrict__ cnt, int *__restrict__ cur,
+                           int *__restrict__ list)
+{
+    const int n_ev = *d_nev, n = off[n_ev];
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+        const int a = assign[h];
+        if (a < 0) continue;
+        const int e = event_of(off, n_ev, h);
+        if (a >= min(counts[e], cap)) continue;
+        const size_t g = (size_t)e * cap + a;
+        if (list) list[atomicAdd(&cur[g], 1)] = h;
+        else atomicAdd(&cnt[g], 1);
+    }
+}
+
+__global__ void k_zb_small(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
+                           const float *__restrict__ z, const ht_peak *__restrict__ peaks,
+                           const int *__restrict__ counts, const int *__restrict__ d_nev,
+                           int cap, const int *__restrict__ off, const int *__restrict__ list,
+                           ht_zres *__restrict__ out, int *__restrict__ big,
+                           int *__restrict__ nbig)
+{
+    const int e = blockIdx.y;
+    if (e >= *d_nev) return;
+    const int ncand = min(counts[e], cap);
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    for (int m = gw; m < ncand; m += nw) {
+        const size_t g = (size_t)e * cap + m;
+        const int o = off[g], nh = off[g + 1] - o;
+        if (nh == 0) {
+            if (lane == 0) out[g] = ht_zres{-1, -1, 0};
+            continue;
         }
-        __syncthreads();
-        // argmax: key = count << 32 | ~index (largest count, then smallest index)
-        unsigned long long bk = 0ull;
-        for (int t = threadIdx.x; t < ncell; t += kBigThreads) {
-            const unsigned c = hist[t];
-            const unsigned long long k = ((unsigned long long)c << 32) | (0xffffffffull - (unsigned)t);
-            if (c && k > bk) bk = k;
+        if (nh > 32) {
+            if (lane == 0) big[atomicAdd(nbig, 1)] = (int)g;
+            continue;
         }
-#pragma unroll
-        for (int s = 16; s > 0; s >>= 1) bk = max(bk, __shfl_xor_sync(0xffffffffu, bk, s));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = bk;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            unsigned long long b = 0ull;
-            for (int w = 0; w < kBigThreads / 32; ++w) b = max(b, red[w]);
-            if (b) {
-                const int idx = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
-                out[m] = ht_zres{idx / NC, idx % NC, (int)(b >> 32)};
-            } else {
-                out[m] = ht_zres{-1, -1, 0};
-            }
-        }
-        __syncthreads();
+        const ht_zres r = z_small_cand(G, x, y, z, peaks[g], list, o, nh, lane);
+        if (lane == 0) out[g] = r;
+    }
+}
+
+__global__ void __launch_bounds__(kBigThreads)
+k_zb_big(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
+         const float *__restrict__ z, const ht_peak *__restrict__ peaks,
+         const int *__restrict__ off, const int *__restrict__ list,
+         const int *__restrict__ big, const int *__restrict__ nbig, ht_zres *__restrict__ out)
+{
+    const int nb = *nbig;
+    for (int bi = blockIdx.x; bi < nb; bi += gridDim.x) {
+        const int g = big[bi];
+        const ht_zres r = z_big_cand(G, x, y, z, peaks[g], list, off[g], off[g + 1] - off[g]);
+        if (threadIdx.x == 0) out[g] = r;
     }
 }
 
@@ -290,11 +384,55 @@ size_t z_big_smem(const DevGeom &G) { return (size_t)G.n_z0 * G.n_cot * 4; }
 
 cudaError_t prepare_z_kernels(int max_smem)
 {
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, k_z_big);
+    const void *fns[] = {(const void *)k_z_big, (const void *)k_zb_big};
+    for (const void *f : fns) {
+        cudaFuncAttributes fa;
+        cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 max_smem - (int)fa.sharedSizeBytes);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+// Batch z vote: candidates of all n_ev event slots at once (global id
+// e * cap + m), hits grouped per candidate with batch-wide indices.
+size_t vote_z_batch_workspace_bytes(int n_ev, int cap, int max_hits)
+{
+    const size_t ng = (size_t)n_ev * cap;
+    return 4 * align256((ng + 1) * 4) + 256 + scan_tmp_bytes((int)ng) +
+           align256((size_t)(max_hits > 0 ? max_hits : 1) * 4);
+}
+
+cudaError_t launch_vote_z_batch(const DevGeom &G, const float *x, const float *y, const float *z,
+                                const int *assign, const int *off, const int *d_nev,
+                                const ht_peak *peaks, const int *counts, int cap, int n_ev,
+                                ht_zres *out, void *ws, int max_hits, cudaStream_t st)
+{
+    const size_t ng = (size_t)n_ev * cap;
+    char *p = reinterpret_cast<char *>(ws);
+    int *cnt = reinterpret_cast<int *>(p); p += align256((ng + 1) * 4);
+    int *zoff = reinterpret_cast<int *>(p); p += align256((ng + 1) * 4);
+    int *cur = reinterpret_cast<int *>(p); p += align256((ng + 1) * 4);
+    int *big = reinterpret_cast<int *>(p); p += align256((ng + 1) * 4);
+    int *nbig = reinterpret_cast<int *>(p); p += 256;
+    void *tmp = p; p += scan_tmp_bytes((int)ng);
+    int *list = reinterpret_cast<int *>(p);
+    cudaError_t e = cudaMemsetAsync(cnt, 0, (ng + 1) * 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nbig, 0, 4, st);
     if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(k_z_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                max_smem - (int)fa.sharedSizeBytes);
+    const int nb = min(4096, max_hits / 256 + 1);
+    k_zb_group<<<nb, 256, 0, st>>>(assign, off, d_nev, counts, cap, cnt, nullptr, nullptr);
+    e = scan_exclusive(cnt, zoff, cur, (int)ng, nullptr, nullptr, tmp, st);
+    if (e != cudaSuccess) return e;
+    k_zb_group<<<nb, 256, 0, st>>>(assign, off, d_nev, counts, cap, nullptr, cur, list);
+    dim3 gs(max(1, min(152 * 8 / max(n_ev, 1), 1024)), n_ev);
+    k_zb_small<<<gs, 256, 0, st>>>(G, x, y, z, peaks, counts, d_nev, cap, zoff, list, out, big,
+                                   nbig);
+    k_zb_big<<<152 * 2, kBigThreads, z_big_smem(G), st>>>(G, x, y, z, peaks, zoff, list, big,
+                                                           nbig, out);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, const float *z,

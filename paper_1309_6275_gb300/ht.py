@@ -56,6 +56,12 @@ SIGNATURES = [
     ("ht_event_workspace_size", _SZ, [_P, _I32, _I32]),
     ("ht_run_event", _I32, [_P, _P, _P, _P, _I32, _P, _SZ, _P, _I32, _P, _P, _P, _P, _P]),
     ("ht_probe_shared_atomic_rate", _I32, [_I32, ctypes.POINTER(ctypes.c_double), _P]),
+    ("ht_batch_create", _I32, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
+    ("ht_batch_destroy", _I32, [_P]),
+    ("ht_batch_set_graphs", _I32, [_P, _I32]),
+    ("ht_batch_run", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
+    ("ht_batch_autotune", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P,
+                                  ctypes.POINTER(_I32), _P]),
 ]
 
 
@@ -228,3 +234,72 @@ class EventPipeline:
         return dict(acc=acc, count=cnt, peaks=self.peaks[:k].cpu().numpy(),
                     assign=self.assign[:n].cpu().numpy(), zres=self.zres[:k].cpu().numpy(),
                     stats=self.stats.cpu().numpy().astype(np.uint64))
+
+
+class Batch:
+    """Batched runtime (ht_batch_*): caller-owned device outputs for up to
+    `max_events` events, `max_hits` hits in total, `cap` candidates each."""
+
+    def __init__(self, g, max_events, max_hits, cap, device="cuda"):
+        import numpy as np
+        self.g, self.max_events, self.max_hits, self.cap = g, max_events, max_hits, cap
+        h = ctypes.c_void_p()
+        _check(lib().ht_batch_create(g.handle, max_events, max_hits, cap, ctypes.byref(h)),
+               "ht_batch_create")
+        self.handle = h
+        dev = torch.device(device)
+        self.peaks = torch.empty((max_events * cap, 4), dtype=torch.int32, device=dev)
+        self.zres = torch.empty((max_events * cap, 3), dtype=torch.int32, device=dev)
+        self.counts = torch.zeros(max_events, dtype=torch.int32, device=dev)
+        self.assign = torch.empty(max(max_hits, 1), dtype=torch.int32, device=dev)
+        self.stats = torch.zeros(2 * max_events, dtype=torch.int64, device=dev)
+        self._off = np.zeros(max_events + 1, np.int32)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ht_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_graphs(self, enable):
+        _check(lib().ht_batch_set_graphs(self.handle, int(bool(enable))), "ht_batch_set_graphs")
+
+    def _offsets(self, offsets):
+        import numpy as np
+        off = np.ascontiguousarray(offsets, np.int32)
+        return off, off.ctypes.data_as(ctypes.c_void_p)
+
+    def run(self, x, y, z, offsets, stream=None):
+        """x, y, z: device float32 (concatenated hits); offsets: host ints."""
+        off, p = self._offsets(offsets)
+        self._keep = off
+        _check(lib().ht_batch_run(self.handle, _ptr(x), _ptr(y), _ptr(z), p, off.shape[0] - 1,
+                                  _ptr(self.peaks), _ptr(self.counts), _ptr(self.assign),
+                                  _ptr(self.zres), _ptr(self.stats), _stream(stream)),
+               "ht_batch_run")
+
+    def autotune(self, x, y, z, offsets, stream=None):
+        off, p = self._offsets(offsets)
+        c = ctypes.c_int32()
+        _check(lib().ht_batch_autotune(self.handle, _ptr(x), _ptr(y), _ptr(z), p,
+                                       off.shape[0] - 1, _ptr(self.peaks), _ptr(self.counts),
+                                       _ptr(self.assign), _ptr(self.zres), ctypes.byref(c),
+                                       _stream(stream)), "ht_batch_autotune")
+        v = c.value
+        return dict(kt_pack=v & 255, kt_unpacked=(v >> 8) & 255, kt_assoc=(v >> 16) & 255)
+
+    def event_results(self, offsets, e):
+        """Results of event e as numpy arrays (synchronises)."""
+        cnt = int(self.counts[e].item())
+        k = min(cnt, self.cap)
+        a, b = int(offsets[e]), int(offsets[e + 1])
+        base = e * self.cap
+        return dict(count=cnt, peaks=self.peaks[base:base + k].cpu().numpy(),
+                    zres=self.zres[base:base + k].cpu().numpy(),
+                    assign=self.assign[a:b].cpu().numpy(),
+                    votes=int(self.stats[2 * e].item()))
