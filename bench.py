@@ -3,10 +3,12 @@
 
 One step = the whole path (vote, 3x3x3 peaks, hit association, (z0, cot theta)
 vote) over every event of the 100-event workload (~10k hits per event,
-256 rho x 128 d0 x 512 phi0 uint16 accumulator, 128 x 128 z grid).  Hits are
-synthetic (seeded generator) and resident in HBM before timing; L2 is flushed
-(256 MiB write) before every timed step; each step is timed with CUDA events
-on the launching stream.
+256 rho x 128 d0 x 512 phi0 uint16 accumulator, 128 x 128 z grid), run by
+the batched runtime (ht_batch_run: persistent queue kernels, CUDA graph
+replay, 25 events per batch).  Hits are synthetic (seeded generator) and
+resident in HBM before timing; L2 is flushed (256 MiB write) before every
+timed step; each step is timed with CUDA events on the launching stream, and
+the stages inside each batch with CUDA events recorded in the graph.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -35,7 +37,6 @@ import synth  # noqa: E402
 WORKLOAD = "event100_256"
 METRIC = "events/s"
 CAP = 1 << 20          # candidate capacity per event (the 10k-hit events give ~5e5)
-KERNELS_PER_EVENT = 11  # vote 1, peaks 3, association 2, z vote 5
 
 
 def parse():
@@ -48,6 +49,8 @@ def parse():
     p.add_argument("--events", type=int, default=None, help="events per step (default: workload's)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-single", action="store_true")
+    p.add_argument("--batch", type=int, default=25, help="events per ht_batch_run")
     return p.parse_args()
 
 
@@ -165,6 +168,22 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# Minimal float32 issue slots of one vote: b, rho*c, D (3 FMA/MUL), rsqrt,
+# sqrt(D), q, C, 1/q, d0, bin coordinate, floor, range test, shared atomic.
+OPS_PER_VOTE = 13
+
+
+def alu_peak_ops(dev_props, peaks):
+    """Issue-limited float32 lane rate: SMs x 128 lanes x max SM clock."""
+    mhz = peaks.get("sm_max_mhz") or 2070.0
+    return dev_props.multi_processor_count * 128 * mhz * 1e6
+
+
+def make_batches(cfg, n_ev, seed0, B):
+    events = [synth.make_event(cfg["gen"], seed0 + e) for e in range(n_ev)]
+    return events, [events[i:i + B] for i in range(0, n_ev, B)]
+
+
 def run_ours(args):
     import torch
     world, rank, local = dist_env()
@@ -178,36 +197,45 @@ def run_ours(args):
     cfg = synth.CONFIGS[args.workload]
     g = dict(cfg["geom"])
     n_ev = args.events or cfg["events"]
+    B = args.batch
     seed0 = cfg["seed0"] + rank * 1_000_003
-    events = [synth.make_event(cfg["gen"], seed0 + e) for e in range(n_ev)]
+    events, batches = make_batches(cfg, n_ev, seed0, B)
     G = ht.Geometry(g)
-    max_hits = max(ev.n_hits for ev in events)
-    pipe = ht.EventPipeline(G, max_hits, CAP)
-    dev_hits = [tuple(torch.from_numpy(a).cuda() for a in (ev.x, ev.y, ev.z)) for ev in events]
+    cap = CAP
+    max_hits = max(sum(ev.n_hits for ev in b) for b in batches)
+    bt = ht.Batch(G, max_events=B, max_hits=max_hits, cap=cap)
+    # inputs resident in HBM: one concatenated x, y, z per batch
+    dev_in = []
+    for b in batches:
+        off = np.zeros(len(b) + 1, np.int32)
+        off[1:] = np.cumsum([ev.n_hits for ev in b])
+        cat = [torch.from_numpy(np.concatenate([getattr(ev, k) for ev in b])).cuda() for k in "xyz"]
+        dev_in.append((off, cat))
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     n_hits_total = sum(ev.n_hits for ev in events)
+    tune = bt.autotune(dev_in[0][1][0], dev_in[0][1][1], dev_in[0][1][2], dev_in[0][0])
 
-    vote_t0 = [torch.cuda.Event(enable_timing=True) for _ in events]
-    vote_t1 = [torch.cuda.Event(enable_timing=True) for _ in events]
-    votes_dev = torch.zeros((len(events), 2), dtype=torch.int64, device="cuda")
+    stage_tot = np.zeros(4)
+    votes_total = 0
+    redo_total = 0
 
-    def step(timed_vote=False):
-        for e, (x, y, z) in enumerate(dev_hits):
-            if timed_vote:
-                vote_t0[e].record(stream)
-            ht.ht_vote(G, x, y, pipe.acc, pipe.stats)
-            if timed_vote:
-                vote_t1[e].record(stream)
-                votes_dev[e] = pipe.stats
-            ht.ht_find_peaks(G, pipe.acc, pipe.peaks, CAP, pipe.count, pipe.workspace)
-            n = x.numel()
-            ht.ht_associate(G, x, y, pipe.peaks, pipe.count, CAP, pipe.assign[:n], pipe.workspace)
-            ht.ht_vote_z(G, x, y, z, pipe.assign[:n], pipe.peaks, pipe.count, CAP, pipe.zres,
-                         pipe.workspace)
+    def step(record=False):
+        nonlocal votes_total, redo_total
+        for off, (x, y, z) in dev_in:
+            bt.run(x, y, z, off)
+            if record:
+                torch.cuda.current_stream().synchronize()
+                stage_tot[:] += np.array(bt.stage_ms())
+                st = bt.stats[:2 * (len(off) - 1)].view(-1, 2).sum(0).tolist()
+                votes_total += int(st[0])
+                redo_total += int(st[1])
 
-    for _ in range(args.warmup):
-        step()
+    for _ in range(args.warmup):        # the same code path as the timed steps
+        step(record=True)
+    stage_tot[:] = 0.0
+    votes_total = 0
+    redo_total = 0
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -216,22 +244,17 @@ def run_ours(args):
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
-    step_ms, vote_ms = [], []
-    votes_total = 0
-    redo_total = 0
+        time.sleep(1.5)          # let nvidia-smi's start-up pass before the timed region
+    step_ms = []
     for s in range(args.steps):
         flush.fill_(s & 0xff)                          # evict L2 before the step
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        step(timed_vote=True)
+        step(record=True)
         b.record(stream)
         b.synchronize()
         step_ms.append(a.elapsed_time(b))
-        vote_ms.append(sum(vote_t0[e].elapsed_time(vote_t1[e]) for e in range(len(events))))
-        vsum = votes_dev.sum(0).tolist()
-        votes_total += int(vsum[0])
-        redo_total += int(vsum[1])
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
@@ -244,31 +267,41 @@ def run_ours(args):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_s = float(t.item())
     value = world * n_ev * args.steps / max_s
-    hit_votes_per_s = world * votes_total / max_s
 
-    # ---- e2e: host buffers through ht_run_event (copies inside the timed region)
+    # ---- e2e: hits from pinned host memory, results read back, per batch
     e2e = None
     if not args.no_e2e:
-        hcap = CAP
-        ws = torch.empty(G.event_workspace_size(max_hits, hcap), dtype=torch.uint8, device="cuda")
-        hin = [tuple(torch.from_numpy(a).pin_memory() for a in (ev.x, ev.y, ev.z)) for ev in events]
-        hp = torch.empty((hcap, 4), dtype=torch.int32).pin_memory()
-        hz = torch.empty((hcap, 3), dtype=torch.int32).pin_memory()
+        hin = [(off, [torch.from_numpy(np.concatenate([getattr(ev, k) for ev in b])).pin_memory()
+                      for k in "xyz"]) for b, (off, _) in zip(batches, dev_in)]
+        dbuf = [torch.empty(max_hits, dtype=torch.float32, device="cuda") for _ in range(3)]
+        hp = torch.empty((B * cap, 4), dtype=torch.int32).pin_memory()
+        hz = torch.empty((B * cap, 3), dtype=torch.int32).pin_memory()
         ha = torch.empty(max_hits, dtype=torch.int32).pin_memory()
-        hc = torch.empty(1, dtype=torch.int32).pin_memory()
-        h2d = sum(12 * ev.n_hits for ev in events)
+        hc = torch.empty(B, dtype=torch.int32).pin_memory()
+        h2d = 12 * n_hits_total
         d2h = 0
 
         def e2e_step():
             nonlocal d2h
             d2h = 0
-            for (x, y, z) in hin:
-                ht.ht_run_event(G, x, y, z, ws, hp, hcap, hc, ha[:x.numel()], hz)
-                k = min(int(hc[0]), hcap)
-                d2h += 4 + 4 * x.numel() + 16 * k + 12 * k
+            for off, hx in hin:
+                nh = int(off[-1])
+                ne = len(off) - 1
+                for d, h in zip(dbuf, hx):
+                    d[:nh].copy_(h, non_blocking=True)
+                bt.run(dbuf[0], dbuf[1], dbuf[2], off)
+                hc[:ne].copy_(bt.counts[:ne], non_blocking=True)
+                ha[:nh].copy_(bt.assign[:nh], non_blocking=True)
+                torch.cuda.current_stream().synchronize()
+                d2h += 4 * ne + 4 * nh
+                for e in range(ne):
+                    k = min(int(hc[e]), cap)
+                    hp[e * cap:e * cap + k].copy_(bt.peaks[e * cap:e * cap + k], non_blocking=True)
+                    hz[e * cap:e * cap + k].copy_(bt.zres[e * cap:e * cap + k], non_blocking=True)
+                    d2h += 28 * k
+                torch.cuda.current_stream().synchronize()
 
         e2e_step()
-        torch.cuda.synchronize()
         tt = []
         for s in range(max(1, args.steps)):
             t0 = time.perf_counter()
@@ -278,40 +311,75 @@ def run_ours(args):
         if dist:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
         e2e = {"value": world * n_ev * len(tt) / float(et.item()), "unit": "events/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "api": "ht_batch_run with host copies of hits in and results out"}
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
 
+    # ---- secondary figures: the single-event C-ABI calls on the same events
+    single = None
+    if not args.no_single:
+        pipe = ht.EventPipeline(G, max(ev.n_hits for ev in events), cap)
+        dev1 = [tuple(torch.from_numpy(getattr(ev, k)).cuda() for k in "xyz") for ev in events]
+        for (x, y, z) in dev1[:2]:
+            pipe.run(x, y, z)
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for (x, y, z) in dev1:
+            pipe.run(x, y, z)
+        b.record()
+        b.synchronize()
+        single = n_ev / (a.elapsed_time(b) / 1e3)
+
+    props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
+    peak_ops = alu_peak_ops(props, peaks)
+    names = ["vote", "peaks+candidate lists", "association", "decode+z vote"]
+    stage_s = stage_tot / 1e3
+    dom = int(np.argmax(stage_s))
+    dom_kernel = {0: "k_vote_batch", 2: "k_assoc32_batch"}.get(dom, names[dom])
+    achieved = OPS_PER_VOTE * votes_total / stage_s[dom] if dom in (0, 2) else None
     atom_rate = ht.ht_probe_shared_atomic_rate(1 << 14)
-    vote_s = sum(vote_ms) / 1e3
-    achieved = votes_total / vote_s                 # one shared atomic per vote
-    roof = {"bound": "alu", "kernel": "k_vote", "achieved": achieved / 1e9,
-            "peak": atom_rate / 1e9, "unit": "Gatomic/s", "frac": achieved / atom_rate,
+    roof = {"bound": "alu", "kernel": dom_kernel,
+            "achieved": achieved / 1e9 if achieved else None,
+            "peak": peak_ops / 1e9, "unit": "Gop/s",
+            "frac": achieved / peak_ops if achieved else None,
             "traffic": None,
-            "peak_source": "measured here: conflict-free shared atomicAdd microbenchmark "
-                           "(ht_probe_shared_atomic_rate)",
-            "vote_kernel_ms_per_event": 1e3 * vote_s / (args.steps * n_ev),
-            "float64_redo_per_vote": redo_total / max(votes_total, 1),
-            "vote_share_of_step": vote_s / total_s,
-            "hbm_gbs_measured": peaks.get("hbm_gbs")}
+            "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x "
+                           f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (issue-limited), "
+                           f"{OPS_PER_VOTE} algorithmic ops per vote",
+            "stage_ms_per_event": {n: 1e3 * v / (args.steps * n_ev) for n, v in zip(names, stage_s)},
+            "vote_share_of_step": stage_s[0] / total_s,
+            "shared_atomic_frac_of_vote": (votes_total / stage_s[0]) / atom_rate,
+            "shared_atomic_peak_gops": atom_rate / 1e9,
+            "float64_redo_per_vote": redo_total / max(votes_total, 1)}
+    launches_per_batch = lambda ne: 2 + 10 * ne + 9
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
-        "data": "synthetic",
+        "data": "synthetic (seeded detector MC)",
         "config": {"workload": args.workload, "events_per_step": n_ev,
-                   "hits_per_step": n_hits_total, "accumulator": "256x128x512 uint16",
-                   "z_grid": "128x128", "l2": "flushed (256 MiB write) before each timed step",
+                   "hits_per_step": n_hits_total,
+                   "geometry": f"{g['n_rho']}x{g['n_d0']}x{g['n_phi0']} uint16, "
+                               f"{g['n_z0']}x{g['n_cot']} z grid, T={g['threshold']}",
+                   "path": f"ht_batch_run, {B} events per batch, CUDA graph replay",
+                   "autotune": tune,
+                   "l2": "flushed (256 MiB write) before each timed step",
                    "parallelism": f"events sharded, {world} rank(s), no collective"},
-        "hit_votes_per_s": hit_votes_per_s,
-        "gpu_launches": KERNELS_PER_EVENT * n_ev * args.steps + args.steps * 0,
+        "hit_votes_per_s": world * votes_total / max_s,
+        "step_ms": [round(v, 3) for v in step_ms],
+        "gpu_launches": args.steps * sum(launches_per_batch(len(b)) for b in batches),
         "roofline": roof,
         "clocks": clk,
     }
+    if single:
+        line["single_event_api_events_per_s"] = single
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:

@@ -246,6 +246,12 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
                        int32_t *counts, int32_t *assign, ht_zres *zres, uint64_t *stats,
                        ht_stream stream);
 
+/* Device time of the stages of the last completed ht_batch_run, in ms:
+ * ms[0] vote, ms[1] peak finding and candidate lists, ms[2] association,
+ * ms[3] assignment decode and (z0, cot theta) vote.  Call after the run's
+ * stream has completed.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_batch_stage_ms(const ht_batch *b, float *ms);
+
 /* Autotune the tile widths (phi0 columns per tile of the packed and unpacked
  * vote, and of the association) by timing whole batches on the given sample
  * (arguments as ht_batch_run).  *choice = kt_pack | kt_unpacked << 8 |

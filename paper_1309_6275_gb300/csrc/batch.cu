@@ -48,7 +48,7 @@ cudaError_t prepare_batch_kernels(int max_smem);
 namespace {
 
 constexpr int kPackMaxHits = 32767;   // packed 16-bit tile counters are exact up to here
-constexpr int kGraphCache = 4;
+constexpr int kGraphCache = 16;
 
 struct GraphEntry {
     int n_ev;
@@ -85,6 +85,7 @@ struct ht_batch {
     int ncache;
     bool use_graph;
     cudaStream_t cap_stream;   // private stream that graphs are captured on
+    cudaEvent_t stage[5];      // recorded around the stages of every run
 };
 
 namespace {
@@ -112,6 +113,8 @@ void free_batch(ht_batch *b)
     if (b->h_meta) cudaFreeHost(b->h_meta);
     if (b->meta_done) cudaEventDestroy(b->meta_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+    for (int i = 0; i < 5; ++i)
+        if (b->stage[i]) cudaEventDestroy(b->stage[i]);
     delete b;
 }
 
@@ -124,8 +127,13 @@ void clear_graphs(ht_batch *b)
 // Every launch of one batch, in order, on stream st.
 cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z, int n_ev,
                     ht_peak *peaks, int32_t *counts, int32_t *assign, ht_zres *zres,
-                    uint64_t *stats, cudaStream_t st)
+                    uint64_t *stats, cudaStream_t st, bool capturing)
 {
+    // stage timers: inside a capture they must become graph nodes
+    auto mark = [&](int i) {
+        return capturing ? cudaEventRecordWithFlags(b->stage[i], st, cudaEventRecordExternal)
+                         : cudaEventRecord(b->stage[i], st);
+    };
     const ht::DevGeom &G = b->g->G;
     const int me = b->max_events;
     int *meta = b->meta;
@@ -133,6 +141,7 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     unsigned long long *st64 = reinterpret_cast<unsigned long long *>(stats);
     cudaError_t e = cudaMemsetAsync(b->heads, 0, 4 * sizeof(int), st);
     if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, (size_t)n_ev * 16, st);
+    if (e == cudaSuccess) e = mark(0);
     if (e != cudaSuccess) return e;
     // vote: events above the packed-counter limit, then the others
     e = ht::launch_vote_batch(G, x, y, off, order_big_of(meta, me), meta + 0, b->acc, b->cells,
@@ -140,6 +149,7 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     if (e != cudaSuccess) return e;
     e = ht::launch_vote_batch(G, x, y, off, order_small_of(meta, me), meta + 1, b->acc, b->cells,
                               st64, b->heads + 1, true, b->kt_pack, b->sms, st);
+    if (e == cudaSuccess) e = mark(1);
     if (e != cudaSuccess) return e;
     // peaks and candidate tile lists per event slot
     for (int ev = 0; ev < n_ev; ++ev) {
@@ -155,15 +165,20 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     }
     // association over the whole batch
     e = cudaMemsetAsync(b->gbest, 0, (size_t)b->max_hits * 8, st);
+    if (e == cudaSuccess) e = mark(2);
     if (e != cudaSuccess) return e;
     e = ht::launch_assoc_batch(G, b->kt_assoc, x, y, off, order_all_of(meta, me), meta + 2, peaks,
                                b->cap, b->toff, (size_t)b->ntiles + 1, b->tlist, b->lstride,
                                b->gbest, b->heads + 2, b->sms, st);
     if (e != cudaSuccess) return e;
+    if (e == cudaSuccess) e = mark(3);
+    if (e != cudaSuccess) return e;
     e = ht::launch_assoc_final_batch(b->gbest, off, meta + 2, assign, b->max_hits, st);
     if (e != cudaSuccess) return e;
-    return ht::launch_vote_z_batch(G, x, y, z, assign, off, meta + 2, peaks, counts, b->cap, n_ev,
-                                   zres, b->z_ws, b->max_hits, st);
+    e = ht::launch_vote_z_batch(G, x, y, z, assign, off, meta + 2, peaks, counts, b->cap, n_ev,
+                                zres, b->z_ws, b->max_hits, st);
+    if (e == cudaSuccess) e = mark(4);
+    return e;
 }
 
 // Upload offsets and the largest-first event orders for this batch.
@@ -269,6 +284,7 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_meta, b->meta_ints * 4);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->meta_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->stage[i]);
     if (e != cudaSuccess) {
         free_batch(b);
         return ht::set_error(HT_ERR_CUDA, "ht_batch_create: allocation or set-up failed");
@@ -305,7 +321,8 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
     s = stage_meta(b, h_off, n_events, st);
     if (s != HT_OK) return s;
     if (!b->use_graph) {
-        cudaError_t e = enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, st);
+        cudaError_t e =
+            enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, st, false);
         return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     }
     const void *key[9] = {x, y, z, peaks, counts, assign, zres, stats, nullptr};
@@ -323,7 +340,7 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const cudaError_t eq =
-            enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, b->cap_stream);
+            enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, b->cap_stream, true);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (eq != cudaSuccess) e = eq;
     }
@@ -341,6 +358,16 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
     c.exec = exec;
     e = cudaGraphLaunch(exec, st);
     return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+ht_status ht_batch_stage_ms(const ht_batch *b, float *ms)
+{
+    if (!b || !ms) return ht::set_error(HT_ERR_ARG, "ht_batch_stage_ms: null argument");
+    for (int i = 0; i < 4; ++i) {
+        cudaError_t e = cudaEventElapsedTime(&ms[i], b->stage[i], b->stage[i + 1]);
+        if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+    }
+    return HT_OK;
 }
 
 ht_status ht_batch_autotune(ht_batch *b, const float *x, const float *y, const float *z,

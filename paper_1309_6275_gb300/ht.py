@@ -60,6 +60,7 @@ SIGNATURES = [
     ("ht_batch_destroy", _I32, [_P]),
     ("ht_batch_set_graphs", _I32, [_P, _I32]),
     ("ht_batch_run", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P]),
+    ("ht_batch_stage_ms", _I32, [_P, _P]),
     ("ht_batch_autotune", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P,
                                   ctypes.POINTER(_I32), _P]),
 ]
@@ -282,6 +283,14 @@ class Batch:
                                   _ptr(self.peaks), _ptr(self.counts), _ptr(self.assign),
                                   _ptr(self.zres), _ptr(self.stats), _stream(stream)),
                "ht_batch_run")
+
+    def stage_ms(self):
+        """[vote, peaks + candidate lists, association, decode + z vote] ms of
+        the last completed run (synchronise first)."""
+        arr = (ctypes.c_float * 4)()
+        _check(lib().ht_batch_stage_ms(self.handle, ctypes.cast(arr, ctypes.c_void_p)),
+               "ht_batch_stage_ms")
+        return list(arr)
 
     def autotune(self, x, y, z, offsets, stream=None):
         off, p = self._offsets(offsets)
