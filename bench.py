@@ -168,6 +168,26 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+# DRAM bytes (read + write) per event of the tile kernels, from one ncu
+# capture (profiles/k_assoc32_batch_event100_b4.md), valid only while the
+# kernel sources hash to the value recorded with it.
+PROFILED_TRAFFIC = {
+    "k_assoc32_batch": {"sha": "fe6ca59689f98200", "bytes_per_event": 50.727424e6 / 4},
+}
+KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_tiles.cu",
+                  "paper_1309_6275_gb300/csrc/ht_internal.cuh",
+                  "paper_1309_6275_gb300/csrc/df32.cuh"]
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 # Minimal float32 issue slots of one vote: b, rho*c, D (3 FMA/MUL), rsqrt,
 # sqrt(D), q, C, 1/q, d0, bin coordinate, floor, range test, shared atomic.
 OPS_PER_VOTE = 13
@@ -345,11 +365,15 @@ def run_ours(args):
     dom_kernel = {0: "k_vote_batch", 2: "k_assoc32_batch"}.get(dom, names[dom])
     achieved = OPS_PER_VOTE * votes_total / stage_s[dom] if dom in (0, 2) else None
     atom_rate = ht.ht_probe_shared_atomic_rate(1 << 14)
+    prof = PROFILED_TRAFFIC.get(dom_kernel)
+    traffic = (prof["bytes_per_event"] * B if prof and prof["sha"] == kernel_sha() else None)
     roof = {"bound": "alu", "kernel": dom_kernel,
             "achieved": achieved / 1e9 if achieved else None,
             "peak": peak_ops / 1e9, "unit": "Gop/s",
             "frac": achieved / peak_ops if achieved else None,
-            "traffic": None,
+            "traffic": traffic,
+            "traffic_note": "ncu dram__bytes_read+write of a 4-event launch scaled to the "
+                            f"{B}-event launch (profiles/k_assoc32_batch_event100_b4.md)",
             "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x "
                            f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (issue-limited), "
                            f"{OPS_PER_VOTE} algorithmic ops per vote",
