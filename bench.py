@@ -236,7 +236,7 @@ def run_ours(args):
     n_hits_total = sum(ev.n_hits for ev in events)
     tune = bt.autotune(dev_in[0][1][0], dev_in[0][1][1], dev_in[0][1][2], dev_in[0][0])
 
-    stage_tot = np.zeros(4)
+    stage_tot = np.zeros(5)
     votes_total = 0
     redo_total = 0
 
@@ -359,11 +359,11 @@ def run_ours(args):
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     peak_ops = alu_peak_ops(props, peaks)
-    names = ["vote", "peaks+candidate lists", "association", "decode+z vote"]
+    names = ["proposal", "vote", "peaks+candidate lists", "association", "decode+z vote"]
     stage_s = stage_tot / 1e3
     dom = int(np.argmax(stage_s))
-    dom_kernel = {0: "k_vote_batch", 2: "k_assoc32_batch"}.get(dom, names[dom])
-    achieved = OPS_PER_VOTE * votes_total / stage_s[dom] if dom in (0, 2) else None
+    dom_kernel = {1: "k_vote_batch", 3: "k_assoc32_batch"}.get(dom, names[dom])
+    achieved = OPS_PER_VOTE * votes_total / stage_s[dom] if dom in (1, 3) else None
     atom_rate = ht.ht_probe_shared_atomic_rate(1 << 14)
     prof = PROFILED_TRAFFIC.get(dom_kernel)
     traffic = (prof["bytes_per_event"] * B if prof and prof["sha"] == kernel_sha() else None)
@@ -378,8 +378,8 @@ def run_ours(args):
                            f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (issue-limited), "
                            f"{OPS_PER_VOTE} algorithmic ops per vote",
             "stage_ms_per_event": {n: 1e3 * v / (args.steps * n_ev) for n, v in zip(names, stage_s)},
-            "vote_share_of_step": stage_s[0] / total_s,
-            "shared_atomic_frac_of_vote": (votes_total / stage_s[0]) / atom_rate,
+            "vote_share_of_step": stage_s[1] / total_s,
+            "shared_atomic_frac_of_vote": (votes_total / stage_s[1]) / atom_rate,
             "shared_atomic_peak_gops": atom_rate / 1e9,
             "float64_redo_per_vote": redo_total / max(votes_total, 1)}
     launches_per_batch = lambda ne: 2 + 10 * ne + 9

@@ -56,9 +56,11 @@ typedef int32_t ht_status;
 #define HT_ERR_TIMEOUT 4    /* a bounded device-side wait gave up         */
 
 /* Geometry of the parameter space.  Requirements checked by
- * ht_geometry_create: n_rho >= 1; n_d0 in [2, 1024]; n_phi0 >= 8 and a
- * multiple of 8; n_z0, n_cot in [1, 1024]; threshold >= 1;
- * count_bits 16 or 32; rho_max, d0_half, z0_max, cot_max > 0. */
+ * ht_geometry_create: n_rho in [1, 65535]; n_d0 in [2, 512]; n_phi0 a
+ * multiple of 8 in [8, 2^20]; n_z0, n_cot in [1, 1024] with
+ * n_z0 * n_cot <= 32768; n_rho * n_d0 * n_phi0 < 2^31; threshold >= 1;
+ * count_bits 16 or 32; rho_max, d0_half, z0_max, cot_max > 0; the tiles
+ * must fit the device's shared memory. */
 typedef struct ht_geometry_desc {
     int32_t n_rho, n_d0, n_phi0;
     int32_t n_z0, n_cot;
@@ -208,6 +210,90 @@ ht_status ht_run_event(const ht_geometry *g, const float *hx, const float *hy,
                        uint64_t *h_stats, ht_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Region masks (learned proposal).  The paper has no learned part; these
+ * calls restrict the Section 5 vote and peak finding to regions that a
+ * per-hit network proposes.  Regions: an 8 x 8 grid of blocks over (rho
+ * row, d0 bin); row i is in rho block i * 8 / n_rho, bin j in d0 block
+ * j * 8 / n_d0, and region 8 * (rho block) + (d0 block) is bit r of a
+ * uint64 mask.  A cell is INSIDE a mask when its region's bit is set, and in
+ * its HALO when an inside cell is at most one row and one bin away.
+ * ------------------------------------------------------------------------ */
+
+/* ht_vote restricted to a mask: every halo cell receives exactly the count
+ * ht_vote gives it; other cells hold unspecified values, and tiles of 32
+ * rows x a few columns that contain no halo cell are not written at all.
+ * Work outside the halo is skipped.  mask: ONE device uint64.  stats: as
+ * ht_vote, counting the votes in halo cells.  Other arguments as ht_vote.
+ * Errors: as ht_vote. */
+ht_status ht_vote_masked(const ht_geometry *g, const float *x, const float *y,
+                         int32_t n_hits, const uint64_t *mask, void *acc, uint64_t *stats,
+                         ht_stream stream);
+
+/* ht_find_peaks restricted to a mask: exactly the peaks ht_find_peaks
+ * reports for the full accumulator that are inside the mask, in the same
+ * order.  Reads only (blocks of) inside cells and their neighbours, so acc
+ * needs only its halo cells right (ht_vote_masked output is enough).
+ * mask: ONE device uint64.  Other arguments as ht_find_peaks.  Errors: as
+ * ht_find_peaks. */
+ht_status ht_find_peaks_masked(const ht_geometry *g, const void *acc, const uint64_t *mask,
+                               ht_peak *peaks, int32_t cap, int32_t *d_count, void *workspace,
+                               size_t workspace_bytes, ht_stream stream);
+
+/* ------------------------------------------------------------------------
+ * Proposal network: per-hit MLP 6 -> 128 -> 128 -> 64 with ReLU and a
+ * softmax over the 64 regions.  Features of a hit (float32, then rounded
+ * to BF16): x/110, y/110, z/(110 sinh 2.5), r/110, atan2(y, x)/pi,
+ * layer/9.  Weights and hidden activations are BF16, sums float32.
+ * Parameters: one flat array of ht_mlp_param_count() values laid out
+ * W1[6][128] b1[128] W2[128][128] b2[128] W3[128][64] b3[64] (W[i][o]
+ * multiplies input i into output o); the training state keeps a float32
+ * master copy and the network reads the BF16 copy.
+ * ------------------------------------------------------------------------ */
+int32_t ht_mlp_param_count(void);
+
+/* Forward pass of n hits (x, y, z float32, layer uint8 device arrays).
+ * Outputs (device, each may be NULL): prob n x 64 float32 (softmax); h1, h2
+ * n x 128 BF16 (hidden activations after ReLU); feat n x 8 BF16 (the six
+ * features, zero padded).  h1, h2 and feat are what ht_mlp_backward needs.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_mlp_forward(const void *params_bf16, const float *x, const float *y, const float *z,
+                         const uint8_t *layer, int32_t n, float *prob, void *h1, void *h2,
+                         void *feat, ht_stream stream);
+
+/* Region masks of n_events events whose hits are concatenated at device
+ * offsets off[0..n_events] (n_hits = off[n_events] total).  mass (device,
+ * n_events x 64 float32) receives the per-event SUM of the hits' softmax
+ * outputs; masks[e] (device) the regions whose mean mass (sum / hits) is
+ * >= tau, plus, if grow is 1, the 8 neighbours of each in the region grid;
+ * every region (all bits) when more than fmax * 64 are selected or the
+ * event is empty.  Sums are float32 atomics, so a mean within about 1e-6 of
+ * tau may fall either way.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_mlp_region_mask(const void *params_bf16, const float *x, const float *y,
+                             const float *z, const uint8_t *layer, const int32_t *off,
+                             int32_t n_events, int32_t n_hits, float tau, float fmax,
+                             int32_t grow, float *mass, uint64_t *masks, ht_stream stream);
+
+/* Gradient of the mean softmax cross entropy over the hits with label >= 0
+ * (labels: device int32, region index or -1 to skip the hit), given the
+ * forward pass's prob, h1, h2 and feat for the same n hits; ADDED into grad
+ * (device, ht_mlp_param_count() float32, in the parameter layout).  The
+ * BF16 roundings of the forward pass count as identity.  workspace:
+ * ht_mlp_backward_workspace_size(n) bytes, 256-byte aligned.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+size_t ht_mlp_backward_workspace_size(int32_t n);
+ht_status ht_mlp_backward(const void *params_bf16, const int32_t *labels, int32_t n,
+                          const float *prob, const void *h1, const void *h2, const void *feat,
+                          float *grad, void *workspace, size_t workspace_bytes, ht_stream stream);
+
+/* One Adam step (Kingma and Ba, bias-corrected, step >= 1) on the float32
+ * master parameters with moments m and v (device, ht_mlp_param_count()
+ * float32 each, updated in place); also writes the BF16 copy.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_mlp_adam(float *params, float *m, float *v, const float *grad, int32_t step,
+                      float lr, float beta1, float beta2, float eps, void *params_bf16,
+                      ht_stream stream);
+
+/* ------------------------------------------------------------------------
  * Batched runtime: many events, uneven hit counts, one CUDA graph per batch.
  * The paper processes one event at a time (Fig. 5); a batch runs the same
  * four steps with identical results per event, but the vote and association
@@ -246,10 +332,41 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
                        int32_t *counts, int32_t *assign, ht_zres *zres, uint64_t *stats,
                        ht_stream stream);
 
-/* Device time of the stages of the last completed ht_batch_run, in ms:
- * ms[0] vote, ms[1] peak finding and candidate lists, ms[2] association,
- * ms[3] assignment decode and (z0, cot theta) vote.  Call after the run's
- * stream has completed.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+/* ht_batch_run with the vote and peak finding of event e restricted to
+ * masks[e] (device, n_events uint64; see ht_vote_masked and
+ * ht_find_peaks_masked): event e's candidates are its ht_batch_run
+ * candidates inside masks[e], and association and the z vote run on them.
+ * Errors: as ht_batch_run. */
+ht_status ht_batch_run_masked(ht_batch *b, const float *x, const float *y, const float *z,
+                              const int32_t *h_off, int32_t n_events, const uint64_t *masks,
+                              ht_peak *peaks, int32_t *counts, int32_t *assign, ht_zres *zres,
+                              uint64_t *stats, ht_stream stream);
+
+/* The proposal used by ht_batch_run_learned. */
+typedef struct ht_proposal {
+    const void *params_bf16;  /* device, ht_mlp_param_count() BF16 values */
+    const uint8_t *layer;     /* device, layer index of every hit (like x) */
+    float tau;                /* region threshold on the mean softmax mass */
+    float fmax;               /* more than fmax * 64 regions: full vote */
+    int32_t grow;             /* 1: add the 8 neighbours of each region */
+    int32_t reserved;         /* set to 0 */
+} ht_proposal;
+
+/* ht_batch_run_masked with the masks computed at the head of the same graph
+ * by ht_mlp_region_mask (proposal *prop) and written to masks (device,
+ * n_events uint64).  tau, fmax and grow are part of the captured graph: a
+ * new value captures a new one.  Errors: as ht_batch_run. */
+ht_status ht_batch_run_learned(ht_batch *b, const float *x, const float *y, const float *z,
+                               const int32_t *h_off, int32_t n_events, const ht_proposal *prop,
+                               uint64_t *masks, ht_peak *peaks, int32_t *counts,
+                               int32_t *assign, ht_zres *zres, uint64_t *stats,
+                               ht_stream stream);
+
+/* Device time of the stages of the last completed batch run, in ms: ms[0]
+ * proposal (0 without one), ms[1] vote, ms[2] peak finding and candidate
+ * lists, ms[3] association, ms[4] assignment decode and (z0, cot theta)
+ * vote.  Call after the run's stream has completed.  Errors: HT_ERR_ARG,
+ * HT_ERR_CUDA. */
 ht_status ht_batch_stage_ms(const ht_batch *b, float *ms);
 
 /* Autotune the tile widths (phi0 columns per tile of the packed and unpacked

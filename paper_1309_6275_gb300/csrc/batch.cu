@@ -9,6 +9,11 @@
 // lives in device memory, uploaded from pinned staging before each replay,
 // so one graph serves every batch with the same number of events.  An
 // autotuner times the tile widths on a sample batch.
+//
+// Masked and learned runs: the vote and the peak finding take a per-event
+// region mask (given by the caller, or computed at the head of the same
+// graph by the proposal MLP from the hits); association and the z vote run
+// unchanged on the masked candidates.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -43,6 +48,15 @@ cudaError_t launch_vote_z_batch(const DevGeom &G, const float *x, const float *y
                                 const ht_peak *peaks, const int *counts, int cap, int n_ev,
                                 ht_zres *out, void *ws, int max_hits, cudaStream_t st);
 cudaError_t prepare_batch_kernels(int max_smem);
+cudaError_t launch_vote_batch_masked(const DevGeom &G, const float *x, const float *y,
+                                     const int *off, const int *order, const int *d_nev,
+                                     uint16_t *acc, size_t acc_stride, unsigned long long *stats,
+                                     int *head, bool pack, int kt, int sms,
+                                     const unsigned long long *masks, cudaStream_t st);
+cudaError_t launch_region_mask(const void *params_bf16, const float *x, const float *y,
+                               const float *z, const uint8_t *layer, const int *off, int n_ev,
+                               int max_hits, float tau, float fmax, int grow, float *mass,
+                               unsigned long long *masks, cudaStream_t st);
 }  // namespace ht
 
 namespace {
@@ -50,9 +64,13 @@ namespace {
 constexpr int kPackMaxHits = 32767;   // packed 16-bit tile counters are exact up to here
 constexpr int kGraphCache = 16;
 
+constexpr int kStages = 5;   // proposal, vote, peaks + lists, association, z vote
+
 struct GraphEntry {
     int n_ev;
-    const void *ptr[9];
+    const void *ptr[12];
+    float tau, fmax;
+    int grow;
     cudaGraphExec_t exec;
 };
 
@@ -81,11 +99,12 @@ struct ht_batch {
     int *tlist;
     size_t lstride;
     char *z_ws;
+    float *mass;        // per-event region masses of the learned proposal
     GraphEntry cache[kGraphCache];
     int ncache;
     bool use_graph;
     cudaStream_t cap_stream;   // private stream that graphs are captured on
-    cudaEvent_t stage[5];      // recorded around the stages of every run
+    cudaEvent_t stage[kStages + 1];   // recorded around the stages of every run
 };
 
 namespace {
@@ -110,10 +129,11 @@ void free_batch(ht_batch *b)
     cudaFree(b->ttmp);
     cudaFree(b->tlist);
     cudaFree(b->z_ws);
+    cudaFree(b->mass);
     if (b->h_meta) cudaFreeHost(b->h_meta);
     if (b->meta_done) cudaEventDestroy(b->meta_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    for (int i = 0; i < 5; ++i)
+    for (int i = 0; i <= kStages; ++i)
         if (b->stage[i]) cudaEventDestroy(b->stage[i]);
     delete b;
 }
@@ -124,10 +144,13 @@ void clear_graphs(ht_batch *b)
     b->ncache = 0;
 }
 
-// Every launch of one batch, in order, on stream st.
+// Every launch of one batch, in order, on stream st.  masks: null (plain
+// vote) or one region mask per event, written first by the proposal when
+// prop is set.
 cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z, int n_ev,
                     ht_peak *peaks, int32_t *counts, int32_t *assign, ht_zres *zres,
-                    uint64_t *stats, cudaStream_t st, bool capturing)
+                    uint64_t *stats, unsigned long long *masks, const ht_proposal *prop,
+                    cudaStream_t st, bool capturing)
 {
     // stage timers: inside a capture they must become graph nodes
     auto mark = [&](int i) {
@@ -143,18 +166,31 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     if (e == cudaSuccess && stats) e = cudaMemsetAsync(stats, 0, (size_t)n_ev * 16, st);
     if (e == cudaSuccess) e = mark(0);
     if (e != cudaSuccess) return e;
-    // vote: events above the packed-counter limit, then the others
-    e = ht::launch_vote_batch(G, x, y, off, order_big_of(meta, me), meta + 0, b->acc, b->cells,
-                              st64, b->heads + 0, false, b->kt_big, b->sms, st);
+    if (prop) {
+        e = ht::launch_region_mask(prop->params_bf16, x, y, z, prop->layer, off, n_ev,
+                                   b->max_hits, prop->tau, prop->fmax, prop->grow, b->mass, masks,
+                                   st);
+        if (e != cudaSuccess) return e;
+    }
+    e = mark(1);
     if (e != cudaSuccess) return e;
-    e = ht::launch_vote_batch(G, x, y, off, order_small_of(meta, me), meta + 1, b->acc, b->cells,
-                              st64, b->heads + 1, true, b->kt_pack, b->sms, st);
-    if (e == cudaSuccess) e = mark(1);
+    // vote: events above the packed-counter limit, then the others
+    auto vote = [&](const int *order, const int *d_nev, int *head, bool pack, int kt) {
+        return masks ? ht::launch_vote_batch_masked(G, x, y, off, order, d_nev, b->acc, b->cells,
+                                                    st64, head, pack, kt, b->sms, masks, st)
+                     : ht::launch_vote_batch(G, x, y, off, order, d_nev, b->acc, b->cells, st64,
+                                             head, pack, kt, b->sms, st);
+    };
+    e = vote(order_big_of(meta, me), meta + 0, b->heads + 0, false, b->kt_big);
+    if (e != cudaSuccess) return e;
+    e = vote(order_small_of(meta, me), meta + 1, b->heads + 1, true, b->kt_pack);
+    if (e == cudaSuccess) e = mark(2);
     if (e != cudaSuccess) return e;
     // peaks and candidate tile lists per event slot
     for (int ev = 0; ev < n_ev; ++ev) {
         e = ht::launch_peaks(G, b->acc + (size_t)ev * b->cells, peaks + (size_t)ev * b->cap,
-                             b->cap, counts + ev, b->pk_ws + (size_t)ev * b->pk_stride, st);
+                             b->cap, counts + ev, b->pk_ws + (size_t)ev * b->pk_stride, st,
+                             masks ? masks + ev : nullptr);
         if (e != cudaSuccess) return e;
         const size_t to = (size_t)ev * (b->ntiles + 1);
         e = ht::launch_cand_lists(G, b->kt_assoc, peaks + (size_t)ev * b->cap, counts + ev,
@@ -165,19 +201,18 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     }
     // association over the whole batch
     e = cudaMemsetAsync(b->gbest, 0, (size_t)b->max_hits * 8, st);
-    if (e == cudaSuccess) e = mark(2);
+    if (e == cudaSuccess) e = mark(3);
     if (e != cudaSuccess) return e;
     e = ht::launch_assoc_batch(G, b->kt_assoc, x, y, off, order_all_of(meta, me), meta + 2, peaks,
                                b->cap, b->toff, (size_t)b->ntiles + 1, b->tlist, b->lstride,
                                b->gbest, b->heads + 2, b->sms, st);
-    if (e != cudaSuccess) return e;
-    if (e == cudaSuccess) e = mark(3);
+    if (e == cudaSuccess) e = mark(4);
     if (e != cudaSuccess) return e;
     e = ht::launch_assoc_final_batch(b->gbest, off, meta + 2, assign, b->max_hits, st);
     if (e != cudaSuccess) return e;
     e = ht::launch_vote_z_batch(G, x, y, z, assign, off, meta + 2, peaks, counts, b->cap, n_ev,
                                 zres, b->z_ws, b->max_hits, st);
-    if (e == cudaSuccess) e = mark(4);
+    if (e == cudaSuccess) e = mark(5);
     return e;
 }
 
@@ -281,10 +316,11 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     M((void **)&b->ttmp, b->ttmp_stride * max_events);
     M((void **)&b->tlist, b->lstride * sizeof(int) * max_events);
     M((void **)&b->z_ws, ht::vote_z_batch_workspace_bytes(max_events, cap, max_hits));
+    M((void **)&b->mass, (size_t)max_events * 64 * sizeof(float));
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_meta, b->meta_ints * 4);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->meta_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
-    for (int i = 0; i < 5 && e == cudaSuccess; ++i) e = cudaEventCreate(&b->stage[i]);
+    for (int i = 0; i <= kStages && e == cudaSuccess; ++i) e = cudaEventCreate(&b->stage[i]);
     if (e != cudaSuccess) {
         free_batch(b);
         return ht::set_error(HT_ERR_CUDA, "ht_batch_create: allocation or set-up failed");
@@ -307,28 +343,40 @@ ht_status ht_batch_set_graphs(ht_batch *b, int32_t enable)
     return HT_OK;
 }
 
-ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float *z,
-                       const int32_t *h_off, int32_t n_events, ht_peak *peaks, int32_t *counts,
-                       int32_t *assign, ht_zres *zres, uint64_t *stats, ht_stream stream)
+}  // extern "C"
+
+namespace {
+
+ht_status run_impl(ht_batch *b, const float *x, const float *y, const float *z,
+                   const int32_t *h_off, int32_t n_events, unsigned long long *masks,
+                   const ht_proposal *prop, ht_peak *peaks, int32_t *counts, int32_t *assign,
+                   ht_zres *zres, uint64_t *stats, ht_stream stream)
 {
     if (!b || !x || !y || !z || !peaks || !counts || !assign || !zres)
         return ht::set_error(HT_ERR_ARG, "ht_batch_run: null argument");
     if (n_events < 1 || n_events > b->max_events)
         return ht::set_error(HT_ERR_ARG, "ht_batch_run: n_events out of range");
+    if (prop && (!prop->params_bf16 || !prop->layer || !masks))
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run_learned: null proposal argument");
     ht_status s = check_offsets(b, h_off, n_events);
     if (s != HT_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     s = stage_meta(b, h_off, n_events, st);
     if (s != HT_OK) return s;
     if (!b->use_graph) {
-        cudaError_t e =
-            enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, st, false);
+        cudaError_t e = enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, masks,
+                                prop, st, false);
         return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     }
-    const void *key[9] = {x, y, z, peaks, counts, assign, zres, stats, nullptr};
+    const void *key[12] = {x,     y,     z,     peaks, counts,
+                           assign, zres, stats, masks, prop ? prop->params_bf16 : nullptr,
+                           prop ? prop->layer : nullptr, nullptr};
+    const float tau = prop ? prop->tau : 0.f, fmax = prop ? prop->fmax : 0.f;
+    const int grow = prop ? prop->grow : 0;
     for (int i = 0; i < b->ncache; ++i) {
         GraphEntry &c = b->cache[i];
-        if (c.n_ev == n_events && memcmp(c.ptr, key, sizeof key) == 0) {
+        if (c.n_ev == n_events && memcmp(c.ptr, key, sizeof key) == 0 && c.tau == tau &&
+            c.fmax == fmax && c.grow == grow) {
             cudaError_t e = cudaGraphLaunch(c.exec, st);
             return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
         }
@@ -339,8 +387,8 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
     cudaGraphExec_t exec = nullptr;
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
-        const cudaError_t eq =
-            enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, b->cap_stream, true);
+        const cudaError_t eq = enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats,
+                                       masks, prop, b->cap_stream, true);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (eq != cudaSuccess) e = eq;
     }
@@ -355,15 +403,51 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
     GraphEntry &c = b->cache[b->ncache++];
     c.n_ev = n_events;
     memcpy(c.ptr, key, sizeof key);
+    c.tau = tau;
+    c.fmax = fmax;
+    c.grow = grow;
     c.exec = exec;
     e = cudaGraphLaunch(exec, st);
     return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
 }
 
+}  // namespace
+
+extern "C" {
+
+ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float *z,
+                       const int32_t *h_off, int32_t n_events, ht_peak *peaks, int32_t *counts,
+                       int32_t *assign, ht_zres *zres, uint64_t *stats, ht_stream stream)
+{
+    return run_impl(b, x, y, z, h_off, n_events, nullptr, nullptr, peaks, counts, assign, zres,
+                    stats, stream);
+}
+
+ht_status ht_batch_run_masked(ht_batch *b, const float *x, const float *y, const float *z,
+                              const int32_t *h_off, int32_t n_events, const uint64_t *masks,
+                              ht_peak *peaks, int32_t *counts, int32_t *assign, ht_zres *zres,
+                              uint64_t *stats, ht_stream stream)
+{
+    if (!masks) return ht::set_error(HT_ERR_ARG, "ht_batch_run_masked: null masks");
+    return run_impl(b, x, y, z, h_off, n_events,
+                    reinterpret_cast<unsigned long long *>(const_cast<uint64_t *>(masks)), nullptr,
+                    peaks, counts, assign, zres, stats, stream);
+}
+
+ht_status ht_batch_run_learned(ht_batch *b, const float *x, const float *y, const float *z,
+                               const int32_t *h_off, int32_t n_events, const ht_proposal *prop,
+                               uint64_t *masks, ht_peak *peaks, int32_t *counts, int32_t *assign,
+                               ht_zres *zres, uint64_t *stats, ht_stream stream)
+{
+    if (!prop) return ht::set_error(HT_ERR_ARG, "ht_batch_run_learned: null proposal");
+    return run_impl(b, x, y, z, h_off, n_events, reinterpret_cast<unsigned long long *>(masks),
+                    prop, peaks, counts, assign, zres, stats, stream);
+}
+
 ht_status ht_batch_stage_ms(const ht_batch *b, float *ms)
 {
     if (!b || !ms) return ht::set_error(HT_ERR_ARG, "ht_batch_stage_ms: null argument");
-    for (int i = 0; i < 4; ++i) {
+    for (int i = 0; i < kStages; ++i) {
         cudaError_t e = cudaEventElapsedTime(&ms[i], b->stage[i], b->stage[i + 1]);
         if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     }

@@ -19,6 +19,8 @@ namespace ht {
 cudaError_t prepare_tile_kernels(int max_smem);
 size_t tile_smem_need(const DevGeom &G);
 cudaError_t prepare_z_kernels(int max_smem);
+cudaError_t prepare_mlp_kernels();
+cudaError_t prepare_masked_vote_kernels(int max_smem);
 size_t z_big_smem(const DevGeom &G);
 }  // namespace ht
 
@@ -175,6 +177,8 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     }
     if (e == cudaSuccess) e = ht::prepare_tile_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_z_kernels(max_smem);
+    if (e == cudaSuccess) e = ht::prepare_masked_vote_kernels(max_smem);
+    if (e == cudaSuccess) e = ht::prepare_mlp_kernels();
     if (e != cudaSuccess) {
         cudaFree(g->d_tables);
         delete g;
@@ -214,6 +218,25 @@ ht_status ht_vote(const ht_geometry *g, const float *x, const float *y, int32_t 
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote");
 }
 
+ht_status ht_vote_masked(const ht_geometry *g, const float *x, const float *y, int32_t n_hits,
+                         const uint64_t *mask, void *acc, uint64_t *stats, ht_stream stream)
+{
+    if (!g || !acc || !mask) return fail(HT_ERR_ARG, "ht_vote_masked: null geometry, mask or accumulator");
+    if (n_hits < 0 || n_hits > kMaxHits)
+        return fail(HT_ERR_ARG, "ht_vote_masked: n_hits %d outside [0, %d]", n_hits, kMaxHits);
+    if (n_hits > 0 && (!x || !y)) return fail(HT_ERR_ARG, "ht_vote_masked: null hit arrays");
+    if (!aligned(acc, 16) || (x && !aligned(x, 16)) || (y && !aligned(y, 16)) ||
+        !aligned(mask, 8))
+        return fail(HT_ERR_ARG, "ht_vote_masked: pointer alignment");
+    cudaError_t e = cudaSuccess;
+    if (stats) e = cudaMemsetAsync(stats, 0, 2 * sizeof(uint64_t), S(stream));
+    if (e == cudaSuccess)
+        e = ht::launch_vote_masked(g->G, x, y, n_hits, acc,
+                                   reinterpret_cast<unsigned long long *>(stats),
+                                   reinterpret_cast<const unsigned long long *>(mask), S(stream));
+    return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_masked");
+}
+
 size_t ht_find_peaks_workspace_size(const ht_geometry *g)
 {
     return g ? ht::peaks_workspace_bytes(g->G) : 0;
@@ -232,6 +255,23 @@ ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks, i
     if (!aligned(workspace, 256)) return fail(HT_ERR_ARG, "ht_find_peaks: workspace alignment");
     cudaError_t e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, workspace, S(stream));
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_find_peaks");
+}
+
+ht_status ht_find_peaks_masked(const ht_geometry *g, const void *acc, const uint64_t *mask,
+                               ht_peak *peaks, int32_t cap, int32_t *d_count, void *workspace,
+                               size_t workspace_bytes, ht_stream stream)
+{
+    if (!g || !acc || !mask || !d_count || !workspace || (cap > 0 && !peaks))
+        return fail(HT_ERR_ARG, "ht_find_peaks_masked: null argument");
+    if (cap < 0) return fail(HT_ERR_ARG, "ht_find_peaks_masked: cap < 0");
+    if (workspace_bytes < ht::peaks_workspace_bytes(g->G))
+        return fail(HT_ERR_ARG, "ht_find_peaks_masked: workspace %zu B < %zu B", workspace_bytes,
+                    ht::peaks_workspace_bytes(g->G));
+    if (!aligned(workspace, 256) || !aligned(mask, 8))
+        return fail(HT_ERR_ARG, "ht_find_peaks_masked: pointer alignment");
+    cudaError_t e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, workspace, S(stream),
+                                     reinterpret_cast<const unsigned long long *>(mask));
+    return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_find_peaks_masked");
 }
 
 size_t ht_associate_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap)

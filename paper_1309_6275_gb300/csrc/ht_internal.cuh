@@ -212,16 +212,55 @@ __device__ __forceinline__ float wrap_pi(float d)
 // the ends or at w = -c (max 1/c) and w = c (min -1/c).  Used only to skip
 // (hit, column) pairs that cannot vote in a block of rows; callers keep a
 // full-row margin and skip the test for c <= 1 cm.
-__device__ __forceinline__ void rho_range(const DevGeom &G, float s, float c,
-                                          float &gmin, float &gmax)
+__device__ __forceinline__ void rho_range_w(float wlo, float whi, float c, float &gmin,
+                                            float &gmax)
 {
-    const float wlo = G.d0lo_f + s, whi = G.d0hi_f + s;
     const float c2 = c * c;
     const float glo = __fdividef(-2.0f * wlo, fmaf(wlo, wlo, c2));
     const float ghi = __fdividef(-2.0f * whi, fmaf(whi, whi, c2));
     const float ic = __frcp_rn(c);
     gmax = (wlo <= -c && -c <= whi) ? ic : fmaxf(glo, ghi);
     gmin = (wlo <= c && c <= whi) ? -ic : fminf(glo, ghi);
+}
+
+__device__ __forceinline__ void rho_range(const DevGeom &G, float s, float c,
+                                          float &gmin, float &gmax)
+{
+    rho_range_w(G.d0lo_f + s, G.d0hi_f + s, c, gmin, gmax);
+}
+
+// ---------------------------------------------------------------------------
+// Regions of the learned proposal: an 8 x 8 grid of blocks over (rho row,
+// d0 bin); row i lies in block i * 8 / n_rho, bin j in block j * 8 / n_d0,
+// and region r = 8 * (rho block) + (d0 block) is bit r of a 64-bit mask.
+// A cell is INSIDE the mask when its region's bit is set; it is in the HALO
+// when some inside cell is at most one row and one bin away.  The masked
+// vote gives every halo cell its full count, so every 26-neighbour of an
+// inside cell is exact and the masked peaks are the full peaks inside.
+__device__ __forceinline__ int region_block(int v, int n) { return (v * 8) / n; }
+
+// First bin (or row) of block b; b = 8 gives n.
+__device__ __forceinline__ int block_first(int b, int n) { return (b * n + 7) / 8; }
+
+// d0 blocks that have an inside cell within one row of row i.
+__device__ __forceinline__ unsigned halo_row_blocks(unsigned long long mask, int i, int NR)
+{
+    unsigned bm = 0u;
+#pragma unroll
+    for (int di = -1; di <= 1; ++di) {
+        const int ii = i + di;
+        if (ii >= 0 && ii < NR) bm |= (unsigned)(mask >> (8 * region_block(ii, NR))) & 0xffu;
+    }
+    return bm;
+}
+
+// Whether bin j of a row whose halo_row_blocks are bm lies in the halo.
+__device__ __forceinline__ bool halo_bin(unsigned bm, int j, int ND)
+{
+    unsigned b = bm >> region_block(j, ND);
+    if (j > 0) b |= bm >> region_block(j - 1, ND);
+    if (j < ND - 1) b |= bm >> region_block(j + 1, ND);
+    return (b & 1u) != 0u;
 }
 
 // ---------------------------------------------------------------------------
@@ -260,8 +299,14 @@ __device__ __forceinline__ double atan2_basic64(double y, double x)
 // Host-side launchers (one per kernel file).
 cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                         unsigned long long *stats, cudaStream_t st);
+// Masked vote: *mask (device) selects the regions; halo cells get full counts.
+cudaError_t launch_vote_masked(const DevGeom &G, const float *x, const float *y, int n,
+                               void *acc, unsigned long long *stats,
+                               const unsigned long long *mask, cudaStream_t st);
+// mask (device, or null for every cell): only peaks inside it are reported.
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
-                         int *d_count, void *ws, cudaStream_t st);
+                         int *d_count, void *ws, cudaStream_t st,
+                         const unsigned long long *mask = nullptr);
 size_t peaks_workspace_bytes(const DevGeom &G);
 cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, int n,
                              const ht_peak *peaks, const int *d_count, int cap, int *assign,

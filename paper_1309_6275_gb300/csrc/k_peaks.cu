@@ -29,10 +29,14 @@ namespace {
 
 constexpr int kJB = 16;           // d0 bins walked per CTA
 
-template <typename T, bool WRITE>
+// MASKED: only cells inside *mask (a learned proposal's regions) can be
+// peaks; a CTA whose bins are all outside reads nothing.  An inside cell's
+// 26 neighbours lie in the mask's halo, which the masked vote fills exactly.
+template <typename T, bool WRITE, bool MASKED>
 __global__ void __launch_bounds__(kPkThreads)
 k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
-        const int *__restrict__ segoff, ht_peak *__restrict__ out, int cap)
+        const int *__restrict__ segoff, ht_peak *__restrict__ out, int cap,
+        const unsigned long long *__restrict__ mask)
 {
     const int NP = G.n_phi0, ND = G.n_d0, NR = G.n_rho;
     const int nkb = (NP + kPkThreads - 1) / kPkThreads;
@@ -44,6 +48,17 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
     const int j0 = blockIdx.y * kJB, j1 = min(j0 + kJB, ND);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     __shared__ int wcnt[kPkThreads / 32];
+    unsigned inside = 0xffu;   // d0 blocks inside the mask in row i's rho block
+    if (MASKED) {
+        inside = (unsigned)(*mask >> (8 * region_block(i, NR))) & 0xffu;
+        const int b0 = region_block(j0, ND), b1 = region_block(j1 - 1, ND);
+        if (!(inside & ((2u << b1) - 1u) & ~((1u << b0) - 1u))) {
+            if (!WRITE)
+                for (int j = j0 + threadIdx.x; j < j1; j += kPkThreads)
+                    segcnt[(i * ND + j) * nkb + kb] = 0;
+            return;   // uniform over the CTA
+        }
+    }
 
     int w[3][3][3];  // [rho -1..+1][d0 -1..+1][phi0 -1..+1]; -1 = absent
     auto load = [&](int slot, int jj) {
@@ -62,7 +77,8 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
     for (int j = j0; j < j1; ++j) {
         load(2, j + 1);
         const int v = w[1][1][1];
-        bool pk = kok && v >= G.threshold;
+        bool pk = kok && v >= G.threshold &&
+                  (!MASKED || ((inside >> region_block(j, ND)) & 1u));
         // rows i-1 and d0 bin j-1 (at row i) precede l: strictly greater;
         // rows i+1 and d0 bin j+1 follow l: greater or equal.
 #pragma unroll
@@ -100,17 +116,20 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
     }
 }
 
-template <typename T>
+template <typename T, bool MASKED>
 cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, int *d_count,
-                      int *segcnt, int *segoff, void *tmp, cudaStream_t st)
+                      int *segcnt, int *segoff, void *tmp, const unsigned long long *mask,
+                      cudaStream_t st)
 {
     const int nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     dim3 grid(nkb, (G.n_d0 + kJB - 1) / kJB, G.n_rho);
     const int nseg = G.n_rho * G.n_d0 * nkb;
-    k_peaks<T, false><<<grid, kPkThreads, 0, st>>>(G, acc, segcnt, nullptr, nullptr, 0);
+    k_peaks<T, false, MASKED><<<grid, kPkThreads, 0, st>>>(G, acc, segcnt, nullptr, nullptr, 0,
+                                                           mask);
     cudaError_t e = scan_exclusive(segcnt, segoff, nullptr, nseg, nullptr, d_count, tmp, st);
     if (e != cudaSuccess) return e;
-    k_peaks<T, true><<<grid, kPkThreads, 0, st>>>(G, acc, nullptr, segoff, peaks, cap);
+    k_peaks<T, true, MASKED><<<grid, kPkThreads, 0, st>>>(G, acc, nullptr, segoff, peaks, cap,
+                                                          mask);
     return cudaGetLastError();
 }
 
@@ -124,7 +143,7 @@ size_t peaks_workspace_bytes(const DevGeom &G)
 }
 
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
-                         int *d_count, void *ws, cudaStream_t st)
+                         int *d_count, void *ws, cudaStream_t st, const unsigned long long *mask)
 {
     const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     const size_t nseg = (size_t)G.n_rho * G.n_d0 * nkb;
@@ -132,11 +151,20 @@ cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int 
     int *segcnt = reinterpret_cast<int *>(p);
     int *segoff = reinterpret_cast<int *>(p + align256((nseg + 1) * 4));
     void *tmp = p + 2 * align256((nseg + 1) * 4);
+    const uint16_t *a16 = reinterpret_cast<const uint16_t *>(acc);
+    const int32_t *a32 = reinterpret_cast<const int32_t *>(acc);
+    if (mask) {
+        if (G.count_bits == 16)
+            return run_peaks<uint16_t, true>(G, a16, peaks, cap, d_count, segcnt, segoff, tmp,
+                                             mask, st);
+        return run_peaks<int32_t, true>(G, a32, peaks, cap, d_count, segcnt, segoff, tmp, mask,
+                                        st);
+    }
     if (G.count_bits == 16)
-        return run_peaks(G, reinterpret_cast<const uint16_t *>(acc), peaks, cap, d_count, segcnt,
-                         segoff, tmp, st);
-    return run_peaks(G, reinterpret_cast<const int32_t *>(acc), peaks, cap, d_count, segcnt,
-                     segoff, tmp, st);
+        return run_peaks<uint16_t, false>(G, a16, peaks, cap, d_count, segcnt, segoff, tmp,
+                                          nullptr, st);
+    return run_peaks<int32_t, false>(G, a32, peaks, cap, d_count, segcnt, segoff, tmp, nullptr,
+                                     st);
 }
 
 }  // namespace ht

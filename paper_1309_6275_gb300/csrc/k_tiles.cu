@@ -27,351 +27,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
-#include "df32.cuh"
-#include "ht_internal.cuh"
+#include "tiles.cuh"
 
 namespace ht {
 namespace {
-
-constexpr int kThreads = 256;
-
-template <typename OutT>
-__device__ __forceinline__ OutT saturate(uint32_t v)
-{
-    if (sizeof(OutT) == 2) return (OutT)(v > 65535u ? 65535u : v);
-    return (OutT)(v > 2147483647u ? 2147483647u : v);
-}
-
-// Shared work list of (hit, column) items.
-struct WorkList {
-    float4 *a, *b;   // Item fields {s, c, r2, eD}, {E1, E2, Qa, Qb}
-    int *meta;       // hit << 6 | needB << 5 | unsure << 4 | column-in-tile
-};
-
-constexpr int kMetaUnsure = 16, kMetaNeedB = 32, kMetaCol = 15;
-constexpr size_t kItemBytes = 36;
-
-__device__ __forceinline__ WorkList carve_worklist(unsigned char *p, int cap)
-{
-    WorkList w;
-    w.a = reinterpret_cast<float4 *>(p);
-    w.b = w.a + cap;
-    w.meta = reinterpret_cast<int *>(w.b + cap);
-    return w;
-}
-
-// Per-tile constants of the lane's row and of the tile's columns.
-template <int KT>
-struct TileCtx {
-    int i0, k0, irow;
-    bool row_ok, has_b;
-    float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB;
-    float sk[KT], ck[KT], pk[KT];
-
-    __device__ __forceinline__ void init(const DevGeom &G, int lane, int tx, int ty)
-    {
-        k0 = tx * KT;
-        i0 = ty * 32;
-        irow = i0 + lane;
-        row_ok = irow < G.n_rho;
-        rho = row_ok ? G.rho32[irow] : 0.0f;
-        invrho = row_ok ? G.invrho32[irow] : 0.0f;
-        has_b = row_ok && (G.rho64[irow] != 0.0);
-        invrho_es = fabsf(invrho) * G.err_scale;
-        const int ilast = min(i0 + 31, G.n_rho - 1);
-        rho_lo = G.rho32[i0] - G.drho_f;
-        rho_hi = G.rho32[ilast] + G.drho_f;
-        rt = fmaxf(fabsf(G.rho32[i0]), fabsf(G.rho32[ilast])) * 1.0001f;
-        // the second root q / rho can reach the axis only if |1 + rho s| <=
-        // |rho| dext, i.e. |s| >= 1 / rt - dext for the rows of this tile
-        sB = rt > 0.0f ? __frcp_rn(rt) - G.dext_f - 0.01f : 3.0e38f;
-#pragma unroll
-        for (int kl = 0; kl < KT; ++kl) {
-            sk[kl] = G.sn32[k0 + kl];
-            ck[kl] = G.cs32[k0 + kl];
-            pk[kl] = G.phi32[k0 + kl];
-        }
-    }
-};
-
-// Phase 1 for hit h (h >= n: no items).  Appends this warp's items to the
-// list with a single atomicAdd on *qn (all 32 lanes must call).
-template <int KT>
-__device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
-                                        const float *__restrict__ x,
-                                        const float *__restrict__ y, int n, int h,
-                                        int lane, int *qn, const WorkList &W)
-{
-    float is_[KT], ic_[KT];
-    int fl_[KT];
-    unsigned sel = 0u;
-    float r2 = 0.0f, R1 = 0.0f;
-    if (h < n) {
-        const float xh = x[h], yh = y[h];
-        r2 = fmaf(xh, xh, yh * yh);
-        R1 = fabsf(xh) + fabsf(yh);
-        const float win = hit_window(G, sqrtf(r2));
-        const float phh = atan2f(yh, xh);
-        const float Ec = (kSafe * 3.0f * kEps) * R1;
-#pragma unroll
-        for (int kl = 0; kl < KT; ++kl) {
-            if (fabsf(wrap_pi(T.pk[kl] - phh)) > win) continue;
-            const float s = fmaf(xh, T.sk[kl], -(yh * T.ck[kl]));
-            const float c = fmaf(xh, T.ck[kl], yh * T.sk[kl]);
-            if (c < -Ec) continue;
-            int f = 0;
-            if (c <= Ec) {
-                f |= kMetaUnsure;
-            } else if (c > 1.0f) {
-                float gmin, gmax;
-                rho_range(G, s, c, gmin, gmax);
-                if (gmax < T.rho_lo || gmin > T.rho_hi) continue;
-            }
-            if (fabsf(s) >= T.sB) f |= kMetaNeedB;
-            sel |= 1u << kl;
-            fl_[kl] = f;
-            is_[kl] = s;
-            ic_[kl] = c;
-        }
-    }
-    const int mine = __popc(sel);
-    int incl = mine;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += v;
-    }
-    int wbase = 0;
-    if (lane == 31 && incl > 0) wbase = atomicAdd(qn, incl);
-    wbase = __shfl_sync(0xffffffffu, wbase, 31);
-    int pos = wbase + incl - mine;
-#pragma unroll
-    for (int kl = 0; kl < KT; ++kl) {
-        if (sel & (1u << kl)) {
-            const Item it = make_item(G, is_[kl], ic_[kl], r2, R1, T.rt);
-            W.a[pos] = make_float4(it.s, it.c, it.r2, it.eD);
-            W.b[pos] = make_float4(it.E1, it.E2, it.Qa, it.Qb);
-            W.meta[pos] = (h << 6) | fl_[kl] | kl;
-            ++pos;
-        }
-    }
-}
-
-// Bins of work item t for the lane's row by guarded float32: the number of
-// bins written to jj, or -1 when the column must be redone in float64.
-template <int KT>
-__device__ __forceinline__ int item_bins32(const DevGeom &G, const TileCtx<KT> &T,
-                                           const WorkList &W, int t, int m, int jj[2])
-{
-    if (m & kMetaUnsure) return -1;
-    const float4 a = W.a[t], b = W.b[t];
-    const Item it{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
-    int jA, jB;
-    if (eval32(G, T.rho, T.invrho_es, T.invrho, T.has_b && (m & kMetaNeedB), it, jA, jB) !=
-        kDecided)
-        return -1;
-    int nv = 0;
-    if (jA >= 0) jj[nv++] = jA;
-    if (jB >= 0) jj[nv++] = jB;
-    return nv;
-}
-
-// Deferred redo requests: (hit, row-in-tile, column) pairs whose bins
-// float32 could not prove.  Drained by all threads of the CTA at the end of
-// the tile (or when half full), through the double-float tier and, rarely,
-// float64 (slow on this part), so neither runs as a lone divergent lane.
-constexpr int kRedoCap = 512;
-constexpr size_t kRedoBytes = (size_t)kRedoCap * 8;
-
-struct RedoQueue {
-    int *hit, *rc;   // rc = row << 4 | column
-};
-
-__device__ __forceinline__ RedoQueue carve_redo(unsigned char *p)
-{
-    RedoQueue q;
-    q.hit = reinterpret_cast<int *>(p);
-    q.rc = q.hit + kRedoCap;
-    return q;
-}
-
-// Push a redo request; false if the queue is full (caller redoes it now).
-__device__ __forceinline__ bool push_redo(const RedoQueue &Q, int *n, int hit, int row, int col)
-{
-    const int slot = atomicAdd(n, 1);
-    if (slot >= kRedoCap) return false;
-    Q.hit[slot] = hit;
-    Q.rc[slot] = (row << 4) | col;
-    return true;
-}
-
-// ------------------------------------------------------------------ vote
-// PACK: two 16-bit counters per shared word (d0 bins 2w and 2w + 1), which
-// halves the tile.  Exact while no cell can reach 65536 votes in the tile: a
-// cell gets at most two votes per hit, so it is used only for n <= 32767.
-template <bool PACK>
-__device__ __forceinline__ void tile_add(uint32_t *col, int j)
-{
-    if (PACK) atomicAdd(col + (j >> 1) * 32, 1u << ((j & 1) << 4));
-    else atomicAdd(col + j * 32, 1u);
-}
-
-template <bool PACK>
-__device__ __forceinline__ uint32_t tile_get(const uint32_t *cnt, int ND, int kl, int j, int il)
-{
-    if (PACK) return (cnt[(kl * (ND >> 1) + (j >> 1)) * 32 + il] >> ((j & 1) << 4)) & 0xffffu;
-    return cnt[(kl * ND + j) * 32 + il];
-}
-
-template <int KT, typename OutT, bool PACK>
-__device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restrict__ x,
-                                          const float *__restrict__ y, int n,
-                                          OutT *__restrict__ acc,
-                                          unsigned long long *__restrict__ stats, int tx, int ty)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    const int ND = G.n_d0;
-    const int NW = PACK ? (ND >> 1) : ND;                  // words per column-row
-    constexpr int QCAP = kThreads * KT;
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][NW][32]
-    unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * NW * 32);
-    const WorkList W = carve_worklist(p, QCAP);
-    const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
-    __shared__ int qn[2], rn;
-    __shared__ unsigned long long s_stats[2];
-
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    constexpr int nwarps = kThreads / 32;
-    TileCtx<KT> T;
-    T.init(G, lane, tx, ty);
-    {
-        uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
-        for (int t = threadIdx.x; t < KT * NW * 8; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
-    }
-    if (threadIdx.x < 2) {
-        qn[threadIdx.x] = 0;
-        s_stats[threadIdx.x] = 0ull;
-    }
-    if (threadIdx.x == 0) rn = 0;
-    __syncthreads();
-
-    int my_fb = 0;
-    int parity = 0;
-    for (int base = 0; base < n; base += kThreads, parity ^= 1) {
-        collect<KT>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W);
-        __syncthreads();
-        const int nq = qn[parity];
-        if (threadIdx.x == 0) qn[parity ^ 1] = 0;   // last read before the previous barrier
-        if (T.row_ok) {
-            for (int t = warp; t < nq; t += nwarps) {
-                const int m = W.meta[t];
-                uint32_t *col = cnt + (m & kMetaCol) * NW * 32 + lane;
-                int jj[2];
-                int nv = item_bins32<KT>(G, T, W, t, m, jj);
-                if (nv < 0) {
-                    ++my_fb;
-                    if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
-                    nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
-                }
-                if (nv > 0) tile_add<PACK>(col, jj[0]);
-                if (nv > 1) tile_add<PACK>(col, jj[1]);
-            }
-        }
-        __syncthreads();
-        // drain the deferred redos when the queue is half full or at the end
-        const int nr = min(rn, kRedoCap);
-        if (nr >= kRedoCap / 2 || base + kThreads >= n) {
-            for (int t = threadIdx.x; t < nr; t += kThreads) {
-                const int h = R.hit[t], rc = R.rc[t];
-                const int il = rc >> 4, kl = rc & 15;
-                int jj[2];
-                const int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
-                uint32_t *col = cnt + kl * NW * 32 + il;
-                for (int v = 0; v < nv; ++v) tile_add<PACK>(col, jj[v]);
-            }
-            __syncthreads();
-            if (threadIdx.x == 0) rn = 0;
-        }
-    }
-    __syncthreads();
-
-    // write-back: thread = (row, d0 bin); the KT counts of a row go out as
-    // one vector of KT * sizeof(OutT) bytes.  Votes are summed here (tile
-    // counters never saturate: they hold at most 2 n).
-    unsigned long long my_votes = 0;
-    for (int t = threadIdx.x; t < 32 * ND; t += kThreads) {
-        const int il = t & 31, j = t >> 5;
-        const int i = T.i0 + il;
-        if (i >= G.n_rho) continue;
-        __align__(16) OutT e[KT];
-#pragma unroll
-        for (int kl = 0; kl < KT; ++kl) {
-            const uint32_t v = tile_get<PACK>(cnt, ND, kl, j, il);
-            my_votes += v;
-            e[kl] = saturate<OutT>(v);
-        }
-        OutT *dst = acc + ((size_t)i * ND + j) * G.n_phi0 + T.k0;
-        if constexpr (KT * sizeof(OutT) == 16) {
-            *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(e);
-        } else if constexpr (KT * sizeof(OutT) == 8) {
-            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<const uint2 *>(e);
-        } else if constexpr (KT * sizeof(OutT) == 4) {
-            *reinterpret_cast<uint32_t *>(dst) = *reinterpret_cast<const uint32_t *>(e);
-        } else {
-#pragma unroll
-            for (int kl = 0; kl < KT; ++kl) dst[kl] = e[kl];
-        }
-    }
-
-    if (stats) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            my_votes += __shfl_xor_sync(0xffffffffu, my_votes, o);
-            my_fb += __shfl_xor_sync(0xffffffffu, my_fb, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&s_stats[0], my_votes);
-            atomicAdd(&s_stats[1], (unsigned long long)my_fb);
-        }
-        __syncthreads();
-        if (threadIdx.x < 2) atomicAdd(&stats[threadIdx.x], s_stats[threadIdx.x]);
-    }
-}
-
-template <int KT, typename OutT, bool PACK>
-__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
-k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
-       OutT *__restrict__ acc, unsigned long long *__restrict__ stats)
-{
-    vote_tile<KT, OutT, PACK>(G, x, y, n, acc, stats, blockIdx.x, blockIdx.y);
-}
-
-// Persistent vote over a batch: CTAs pop (event, tile) items from a device
-// counter; items run event by event in the order given (largest events
-// first), so uneven events share the GPU without per-event launch tails.
-template <int KT, typename OutT, bool PACK>
-__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
-k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
-             const int *__restrict__ off, const int *__restrict__ order,
-             const int *__restrict__ d_nev,
-             OutT *__restrict__ acc, size_t acc_stride, unsigned long long *__restrict__ stats,
-             int *__restrict__ head)
-{
-    __shared__ int s_item;
-    const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 31) / 32, ntiles = ntx * nty;
-    const int total = *d_nev * ntiles;
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= total) break;
-        const int e = order[item / ntiles], t = item % ntiles;
-        const int a = off[e], n = off[e + 1] - a;
-        vote_tile<KT, OutT, PACK>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
-                                  stats ? stats + 2 * e : nullptr, t % ntx, t / ntx);
-        __syncthreads();
-    }
-}
 
 // ----------------------------------------------------------- association
 __device__ __forceinline__ int lower_bound_l(const ht_peak *__restrict__ pk, int n,
@@ -739,13 +398,6 @@ k_assoc32_batch(DevGeom G, const float *__restrict__ x, const float *__restrict_
 
 // ---------------------------------------------------------------- launch
 template <int KT>
-size_t vote_smem(const DevGeom &G, bool pack)
-{
-    return (size_t)KT * 32 * (pack ? G.n_d0 / 2 : G.n_d0) * 4 + (size_t)kThreads * KT * kItemBytes +
-           kRedoBytes;
-}
-
-template <int KT>
 size_t assoc_smem(const DevGeom &G)
 {
     return (size_t)KT * 32 * G.n_d0 * 8 + (size_t)kThreads * 8 + (size_t)kThreads * KT * kItemBytes +
@@ -768,18 +420,6 @@ size_t assoc32_smem(const DevGeom &G)
            (size_t)kThreads * 4 + (size_t)kThreads * KT * kItemBytes + kRedoBytes;
 }
 
-constexpr size_t kSmemBudget2 = 110 * 1024;   // two CTAs per SM
-constexpr size_t kSmemBudget3 = 75 * 1024;    // three CTAs per SM
-
-template <int KT, typename OutT, bool PACK>
-cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int n, void *acc,
-                           unsigned long long *stats, cudaStream_t st)
-{
-    dim3 grid(G.n_phi0 / KT, (G.n_rho + 31) / 32);
-    k_vote<KT, OutT, PACK><<<grid, kThreads, vote_smem<KT>(G, PACK), st>>>(
-        G, x, y, n, reinterpret_cast<OutT *>(acc), stats);
-    return cudaGetLastError();
-}
 
 template <int KT>
 cudaError_t launch_assoc32_kt(const DevGeom &G, const float *x, const float *y, int n,
@@ -825,24 +465,11 @@ cudaError_t launch_assoc_kt(const DevGeom &G, const float *x, const float *y, in
 // still passes only what the chosen tile needs).  Called once per device.
 cudaError_t prepare_tile_kernels(int max_smem)
 {
-    const void *fns[] = {
-        (const void *)k_vote<4, uint16_t, true>,  (const void *)k_vote<2, uint16_t, true>,
-        (const void *)k_vote<1, uint16_t, true>,  (const void *)k_vote<8, uint16_t, false>,
-        (const void *)k_vote<4, uint16_t, false>, (const void *)k_vote<2, uint16_t, false>,
-        (const void *)k_vote<1, uint16_t, false>, (const void *)k_vote<4, int32_t, false>,
-        (const void *)k_vote<2, int32_t, false>,  (const void *)k_vote<1, int32_t, false>,
-        (const void *)k_assoc<4>,                 (const void *)k_assoc<2>,
-        (const void *)k_assoc<1>,                 (const void *)k_assoc32<4>,
-        (const void *)k_assoc32<2>,               (const void *)k_assoc32<1>};
-    for (const void *f : fns) {
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, f);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem - (int)fa.sharedSizeBytes);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    const void *fns[] = {(const void *)k_assoc<4>,   (const void *)k_assoc<2>,
+                         (const void *)k_assoc<1>,   (const void *)k_assoc32<4>,
+                         (const void *)k_assoc32<2>, (const void *)k_assoc32<1>};
+    const cudaError_t e = allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
+    return e == cudaSuccess ? prepare_vote_kernels_t<false>(max_smem) : e;
 }
 
 // Largest tile shared memory any geometry with n_d0 bins needs.
@@ -852,34 +479,10 @@ size_t tile_smem_need(const DevGeom &G)
     return v > a ? (v > a32 ? v : a32) : (a > a32 ? a : a32);
 }
 
-// Tile shape: packed 16-bit counters with three CTAs per SM when the output
-// is uint16, n_d0 even and n <= 32767; otherwise 32-bit counters, two CTAs
-// per SM.  KT is the widest tile that fits.
 cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                         unsigned long long *stats, cudaStream_t st)
 {
-    if (G.count_bits == 16) {
-        if (n <= 32767 && G.n_d0 % 2 == 0) {
-            if (vote_smem<4>(G, true) <= kSmemBudget3)
-                return launch_vote_kt<4, uint16_t, true>(G, x, y, n, acc, stats, st);
-            if (vote_smem<2>(G, true) <= kSmemBudget3)
-                return launch_vote_kt<2, uint16_t, true>(G, x, y, n, acc, stats, st);
-            if (vote_smem<1>(G, true) <= kSmemBudget3)
-                return launch_vote_kt<1, uint16_t, true>(G, x, y, n, acc, stats, st);
-        }
-        if (vote_smem<8>(G, false) <= kSmemBudget2)
-            return launch_vote_kt<8, uint16_t, false>(G, x, y, n, acc, stats, st);
-        if (vote_smem<4>(G, false) <= kSmemBudget2)
-            return launch_vote_kt<4, uint16_t, false>(G, x, y, n, acc, stats, st);
-        if (vote_smem<2>(G, false) <= kSmemBudget2)
-            return launch_vote_kt<2, uint16_t, false>(G, x, y, n, acc, stats, st);
-        return launch_vote_kt<1, uint16_t, false>(G, x, y, n, acc, stats, st);
-    }
-    if (vote_smem<4>(G, false) <= kSmemBudget2)
-        return launch_vote_kt<4, int32_t, false>(G, x, y, n, acc, stats, st);
-    if (vote_smem<2>(G, false) <= kSmemBudget2)
-        return launch_vote_kt<2, int32_t, false>(G, x, y, n, acc, stats, st);
-    return launch_vote_kt<1, int32_t, false>(G, x, y, n, acc, stats, st);
+    return launch_vote_t<false>(G, x, y, n, acc, stats, nullptr, st);
 }
 
 // Association workspace: per-hit best keys, then (uint16 geometries) the
@@ -925,40 +528,13 @@ cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, i
 }
 
 // ------------------------------------------------------------- batches
-// Persistent vote of a batch: `order` lists d_nev[0] event slots; every CTA
-// slot of the GPU (SMs x resident CTAs) pops items until the queue is empty.
-// kt selects the tile width (0 = default), pack the 16-bit packed counters
-// (valid when every listed event has <= 32767 hits).  *head must be zero.
 cudaError_t launch_vote_batch(const DevGeom &G, const float *x, const float *y, const int *off,
                               const int *order, const int *d_nev, uint16_t *acc,
                               size_t acc_stride, unsigned long long *stats, int *head, bool pack,
                               int kt, int sms, cudaStream_t st)
 {
-#define HT_VB(KTV, PK)                                                                        \
-    do {                                                                                      \
-        int occ = 0;                                                                          \
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_vote_batch<KTV, uint16_t, PK>,  \
-                                                      kThreads, vote_smem<KTV>(G, PK));       \
-        k_vote_batch<KTV, uint16_t, PK><<<sms * (occ > 0 ? occ : 1), kThreads,               \
-                                          vote_smem<KTV>(G, PK), st>>>(                       \
-            G, x, y, off, order, d_nev, acc, acc_stride, stats, head);                        \
-        return cudaGetLastError();                                                            \
-    } while (0)
-    if (pack) {
-        if (kt == 0) kt = vote_smem<4>(G, true) <= kSmemBudget3 ? 4
-                        : vote_smem<2>(G, true) <= kSmemBudget3 ? 2 : 1;
-        if (kt == 4 && vote_smem<4>(G, true) <= kSmemBudget2) HT_VB(4, true);
-        if (kt >= 2 && vote_smem<2>(G, true) <= kSmemBudget2) HT_VB(2, true);
-        HT_VB(1, true);
-    }
-    if (kt == 0) kt = vote_smem<8>(G, false) <= kSmemBudget2 ? 8
-                    : vote_smem<4>(G, false) <= kSmemBudget2 ? 4
-                    : vote_smem<2>(G, false) <= kSmemBudget2 ? 2 : 1;
-    if (kt == 8 && vote_smem<8>(G, false) <= kSmemBudget2) HT_VB(8, false);
-    if (kt >= 4 && vote_smem<4>(G, false) <= kSmemBudget2) HT_VB(4, false);
-    if (kt >= 2 && vote_smem<2>(G, false) <= kSmemBudget2) HT_VB(2, false);
-    HT_VB(1, false);
-#undef HT_VB
+    return launch_vote_batch_t<false>(G, x, y, off, order, d_nev, acc, acc_stride, stats, head,
+                                      pack, kt, sms, nullptr, st);
 }
 
 // Association tile width for uint16 geometries (largest fitting three CTAs
@@ -1032,25 +608,9 @@ cudaError_t launch_assoc_final_batch(const unsigned long long *gbest, const int 
 
 cudaError_t prepare_batch_kernels(int max_smem)
 {
-    const void *fns[] = {(const void *)k_vote_batch<4, uint16_t, true>,
-                         (const void *)k_vote_batch<2, uint16_t, true>,
-                         (const void *)k_vote_batch<1, uint16_t, true>,
-                         (const void *)k_vote_batch<8, uint16_t, false>,
-                         (const void *)k_vote_batch<4, uint16_t, false>,
-                         (const void *)k_vote_batch<2, uint16_t, false>,
-                         (const void *)k_vote_batch<1, uint16_t, false>,
-                         (const void *)k_assoc32_batch<4>,
-                         (const void *)k_assoc32_batch<2>,
+    const void *fns[] = {(const void *)k_assoc32_batch<4>, (const void *)k_assoc32_batch<2>,
                          (const void *)k_assoc32_batch<1>};
-    for (const void *f : fns) {
-        cudaFuncAttributes fa;
-        cudaError_t e = cudaFuncGetAttributes(&fa, f);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 max_smem - (int)fa.sharedSizeBytes);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+    return allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
 }
 
 }  // namespace ht

@@ -1,0 +1,485 @@
+// mlp.cu -- the learned region proposal: a per-hit MLP 6 -> 128 -> 128 -> 64
+// over (rho, d0) regions, its training kernels and the per-event region mask
+// (ht_mlp_* in include/ht.h).  The paper has no learned part; this is the
+// proposal's own reading.
+//
+// Numerics: BF16 weights and BF16 activations between layers, products of
+// BF16 values exact in float32, float32 accumulation, float32 logits and
+// softmax.  Features: x/110, y/110, z/(110 sinh 2.5), r/110, phi/pi, layer/9,
+// each computed in float32 (no contraction) and rounded to BF16.
+//
+// Layout of the flat parameter array (float32 master and BF16 copy):
+// W1[6][128] b1[128] W2[128][128] b2[128] W3[128][64] b3[64], W[i][o]
+// multiplying input i into output o.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ht_internal.cuh"
+
+namespace ht {
+namespace {
+
+constexpr int kIn = 6, kH = 128, kOut = 64;
+constexpr int oW1 = 0, ob1 = oW1 + kIn * kH, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
+              oW3 = ob2 + kH, ob3 = oW3 + kH * kOut, kParams = ob3 + kOut;
+constexpr int kFwdThreads = 128;   // one hit per thread
+constexpr float kSinhEta = 6.0502044810397875f;   // sinh(2.5)
+
+__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+// Features of one hit, float32 operations in a fixed order, rounded to BF16.
+__device__ __forceinline__ void hit_features(float x, float y, float z, int layer, float f[kIn])
+{
+    const float r = __fsqrt_rn(__fadd_rn(__fmul_rn(x, x), __fmul_rn(y, y)));
+    f[0] = bf(__fdiv_rn(x, 110.0f));
+    f[1] = bf(__fdiv_rn(y, 110.0f));
+    f[2] = bf(__fdiv_rn(z, __fmul_rn(110.0f, kSinhEta)));
+    f[3] = bf(__fdiv_rn(r, 110.0f));
+    f[4] = bf(__fdiv_rn(atan2f(y, x), 3.14159265358979f));
+    f[5] = bf(__fdiv_rn((float)layer, 9.0f));
+}
+
+struct FwdOut {
+    float *prob;             // n x 64 (or null)
+    __nv_bfloat16 *h1, *h2;  // n x 128 each (or null)
+    __nv_bfloat16 *feat;     // n x 8 (or null), features padded to 8
+    float *mass;             // per-event region mass sums, [event][64] (or null)
+    const int *off;          // event offsets when mass is set
+    int n_ev;
+    const int *d_n;          // (or null) device hit count, read instead of n
+};
+
+__device__ __forceinline__ int event_of_hit(const int *off, int n_ev, int h)
+{
+    int lo = 0, hi = n_ev;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= h) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__global__ void __launch_bounds__(kFwdThreads)
+k_mlp_fwd(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ x,
+          const float *__restrict__ y, const float *__restrict__ z,
+          const uint8_t *__restrict__ layer, int n, FwdOut out)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16 *sW2 = reinterpret_cast<__nv_bfloat16 *>(smem);          // [128][128]
+    __nv_bfloat16 *sW3 = sW2 + kH * kH;                                    // [128][64]
+    __nv_bfloat16 *sW1 = sW3 + kH * kOut;                                  // [6][128]
+    __nv_bfloat16 (*hT)[kFwdThreads] =                                     // layer-1 output,
+        reinterpret_cast<__nv_bfloat16 (*)[kFwdThreads]>(sW1 + kIn * kH);  // transposed
+    float *sb1 = reinterpret_cast<float *>(&hT[kH][0]);
+    float *sb2 = sb1 + kH, *sb3 = sb2 + kH, *smass = sb3 + kOut;
+    __shared__ int sev;
+    if (out.d_n) n = *out.d_n;
+    for (int t = threadIdx.x; t < kIn * kH; t += kFwdThreads) sW1[t] = w[oW1 + t];
+    for (int t = threadIdx.x; t < kH * kH; t += kFwdThreads) sW2[t] = w[oW2 + t];
+    for (int t = threadIdx.x; t < kH * kOut; t += kFwdThreads) sW3[t] = w[oW3 + t];
+    for (int t = threadIdx.x; t < kH; t += kFwdThreads) {
+        sb1[t] = __bfloat162float(w[ob1 + t]);
+        sb2[t] = __bfloat162float(w[ob2 + t]);
+    }
+    for (int t = threadIdx.x; t < kOut; t += kFwdThreads) sb3[t] = __bfloat162float(w[ob3 + t]);
+    __syncthreads();
+
+    for (int base = blockIdx.x * kFwdThreads; base < n; base += gridDim.x * kFwdThreads) {
+        const int h = base + threadIdx.x;
+        const bool act = h < n;
+        float f[kIn];
+        hit_features(act ? x[h] : 0.f, act ? y[h] : 0.f, act ? z[h] : 0.f, act ? layer[h] : 0, f);
+        if (act && out.feat) {
+            __align__(16) __nv_bfloat16 fb[8];
+#pragma unroll
+            for (int i = 0; i < kIn; ++i) fb[i] = __float2bfloat16_rn(f[i]);
+            fb[6] = fb[7] = __float2bfloat16_rn(0.f);
+            *reinterpret_cast<uint4 *>(out.feat + (size_t)h * 8) = *reinterpret_cast<uint4 *>(fb);
+        }
+        // layer 1
+        for (int o = 0; o < kH; ++o) {
+            float a = sb1[o];
+#pragma unroll
+            for (int i = 0; i < kIn; ++i) a = fmaf(f[i], __bfloat162float(sW1[i * kH + o]), a);
+            const __nv_bfloat16 v = __float2bfloat16_rn(fmaxf(a, 0.f));
+            hT[o][threadIdx.x] = v;
+            if (act && out.h1) out.h1[(size_t)h * kH + o] = v;
+        }
+        __syncthreads();
+        // layer 2 in chunks of 8 outputs, folded straight into the logits
+        float lg[kOut];
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) lg[c] = sb3[c];
+        for (int o0 = 0; o0 < kH; o0 += 8) {
+            float a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) a[u] = sb2[o0 + u];
+            for (int i = 0; i < kH; ++i) {
+                const float hv = __bfloat162float(hT[i][threadIdx.x]);
+                const uint4 wv = *reinterpret_cast<const uint4 *>(&sW2[i * kH + o0]);
+                const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
+#pragma unroll
+                for (int u = 0; u < 8; ++u) a[u] = fmaf(hv, __bfloat162float(wb[u]), a[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(a[u], 0.f));
+                if (act && out.h2) out.h2[(size_t)h * kH + o0 + u] = hb;
+                const float hv = __bfloat162float(hb);
+                const uint4 *wr = reinterpret_cast<const uint4 *>(&sW3[(o0 + u) * kOut]);
+#pragma unroll
+                for (int c8 = 0; c8 < kOut / 8; ++c8) {
+                    const uint4 wv = wr[c8];
+                    const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) lg[c8 * 8 + q] = fmaf(hv, __bfloat162float(wb[q]), lg[c8 * 8 + q]);
+                }
+            }
+        }
+        // softmax
+        float mx = lg[0];
+#pragma unroll
+        for (int c = 1; c < kOut; ++c) mx = fmaxf(mx, lg[c]);
+        float s = 0.f;
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) {
+            lg[c] = __expf(lg[c] - mx);
+            s += lg[c];
+        }
+        const float is = __frcp_rn(s);
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) lg[c] *= is;
+        if (act && out.prob) {
+            float4 *pp = reinterpret_cast<float4 *>(out.prob + (size_t)h * kOut);
+#pragma unroll
+            for (int c4 = 0; c4 < kOut / 4; ++c4)
+                pp[c4] = make_float4(lg[4 * c4], lg[4 * c4 + 1], lg[4 * c4 + 2], lg[4 * c4 + 3]);
+        }
+        if (out.mass) {
+            // per-event sums: a chunk of hits may straddle events, so group by
+            // the chunk's first event and send the others straight to global
+            if (threadIdx.x == 0) sev = event_of_hit(out.off, out.n_ev, base);
+            for (int c = threadIdx.x; c < kOut; c += kFwdThreads) smass[c] = 0.f;
+            __syncthreads();
+            const int e = act ? event_of_hit(out.off, out.n_ev, h) : -1;
+            if (act) {
+                if (e == sev) {
+#pragma unroll
+                    for (int c = 0; c < kOut; ++c) atomicAdd(&smass[c], lg[c]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < kOut; ++c) atomicAdd(&out.mass[(size_t)e * kOut + c], lg[c]);
+                }
+            }
+            __syncthreads();
+            for (int c = threadIdx.x; c < kOut; c += kFwdThreads)
+                atomicAdd(&out.mass[(size_t)sev * kOut + c], smass[c]);
+        }
+        __syncthreads();
+    }
+}
+
+// Backward through the activations of one minibatch: dL = (p - onehot) / nl
+// (0 for unlabelled hits), dH2 = (dL W3^T) o [h2 > 0], dH1 = (dH2 W2^T) o [h1 > 0].
+__global__ void __launch_bounds__(kFwdThreads)
+k_mlp_bwd_act(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ prob,
+              const int *__restrict__ labels, const __nv_bfloat16 *__restrict__ h1,
+              const __nv_bfloat16 *__restrict__ h2, int n, const int *__restrict__ d_nlab,
+              float *__restrict__ dL, float *__restrict__ dH2, float *__restrict__ dH1)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    __nv_bfloat16 *sW2 = reinterpret_cast<__nv_bfloat16 *>(smem);
+    __nv_bfloat16 *sW3 = sW2 + kH * kH;
+    float (*dT)[kFwdThreads + 1] = reinterpret_cast<float (*)[kFwdThreads + 1]>(sW3 + kH * kOut);
+    for (int t = threadIdx.x; t < kH * kH; t += kFwdThreads) sW2[t] = w[oW2 + t];
+    for (int t = threadIdx.x; t < kH * kOut; t += kFwdThreads) sW3[t] = w[oW3 + t];
+    __syncthreads();
+    const float inv_nl = 1.0f / (float)max(*d_nlab, 1);
+    for (int base = blockIdx.x * kFwdThreads; base < n; base += gridDim.x * kFwdThreads) {
+        const int h = base + threadIdx.x;
+        const bool act = h < n;
+        const int lab = act ? labels[h] : -1;
+        float d[kOut];
+#pragma unroll
+        for (int c = 0; c < kOut; ++c) {
+            const float pv = act ? prob[(size_t)h * kOut + c] : 0.f;
+            d[c] = lab >= 0 ? (pv - (c == lab ? 1.f : 0.f)) * inv_nl : 0.f;
+        }
+        if (act) {
+            float4 *dp = reinterpret_cast<float4 *>(dL + (size_t)h * kOut);
+#pragma unroll
+            for (int c4 = 0; c4 < kOut / 4; ++c4)
+                dp[c4] = make_float4(d[4 * c4], d[4 * c4 + 1], d[4 * c4 + 2], d[4 * c4 + 3]);
+        }
+        for (int o = 0; o < kH; ++o) {
+            const uint4 *wr = reinterpret_cast<const uint4 *>(&sW3[o * kOut]);
+            float a = 0.f;
+#pragma unroll
+            for (int c8 = 0; c8 < kOut / 8; ++c8) {
+                const uint4 wv = wr[c8];
+                const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a = fmaf(d[c8 * 8 + q], __bfloat162float(wb[q]), a);
+            }
+            const float hv = act ? __bfloat162float(h2[(size_t)h * kH + o]) : 0.f;
+            const float g = hv > 0.f ? a : 0.f;
+            dT[o][threadIdx.x] = g;
+            if (act) dH2[(size_t)h * kH + o] = g;
+        }
+        __syncthreads();
+        for (int i = 0; i < kH; ++i) {
+            const uint4 *wr = reinterpret_cast<const uint4 *>(&sW2[i * kH]);
+            float a = 0.f;
+            for (int o8 = 0; o8 < kH / 8; ++o8) {
+                const uint4 wv = wr[o8];
+                const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) a = fmaf(dT[o8 * 8 + q][threadIdx.x], __bfloat162float(wb[q]), a);
+            }
+            const float hv = act ? __bfloat162float(h1[(size_t)h * kH + i]) : 0.f;
+            if (act) dH1[(size_t)h * kH + i] = hv > 0.f ? a : 0.f;
+        }
+        __syncthreads();
+    }
+}
+
+// C[M][N] += sum_h A[h][M] B[h][N] (A BF16 with row stride lda, B float32
+// with row stride ldb), and bias[N] += sum_h B[h][N] when bias is set.
+// CTA: 256 threads, a 64 x 64 output tile (4 x 4 per thread), hits split
+// across gridDim.z; partial tiles are added with float atomics.
+constexpr int kGT = 64, kGH = 32;
+__global__ void __launch_bounds__(256)
+k_wgrad(const __nv_bfloat16 *__restrict__ A, int lda, const float *__restrict__ B, int ldb,
+        int n, int M, int N, float *__restrict__ C, float *__restrict__ bias)
+{
+    __shared__ float sA[kGH][kGT], sB[kGH][kGT];
+    const int m0 = blockIdx.x * kGT, n0 = blockIdx.y * kGT;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    float acc[4][4] = {};
+    float bacc = 0.f;
+    const int per = (n + gridDim.z - 1) / gridDim.z;
+    const int h0 = blockIdx.z * per, h1 = min(n, h0 + per);
+    for (int hb = h0; hb < h1; hb += kGH) {
+        for (int t = threadIdx.x; t < kGH * kGT; t += 256) {
+            const int r = t / kGT, c = t % kGT;
+            const int hh = hb + r;
+            sA[r][c] = (hh < h1 && m0 + c < M) ? __bfloat162float(A[(size_t)hh * lda + m0 + c]) : 0.f;
+            sB[r][c] = (hh < h1 && n0 + c < N) ? B[(size_t)hh * ldb + n0 + c] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 8
+        for (int r = 0; r < kGH; ++r) {
+            float a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = sA[r][ty * 4 + u];
+                b[u] = sB[r][tx * 4 + u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(a[u], b[v], acc[u][v]);
+        }
+        if (bias && blockIdx.x == 0 && threadIdx.x < kGT)
+            for (int r = 0; r < kGH; ++r) bacc += sB[r][threadIdx.x];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int m = m0 + ty * 4 + u, nn = n0 + tx * 4 + v;
+            if (m < M && nn < N) atomicAdd(&C[(size_t)m * N + nn], acc[u][v]);
+        }
+    if (bias && blockIdx.x == 0 && threadIdx.x < kGT && n0 + threadIdx.x < N)
+        atomicAdd(&bias[n0 + threadIdx.x], bacc);
+}
+
+__global__ void k_count_labels(const int *__restrict__ labels, int n, int *__restrict__ nl)
+{
+    int c = 0;
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x)
+        c += labels[h] >= 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(nl, c);
+}
+
+__global__ void k_adam(float *__restrict__ p, float *__restrict__ m, float *__restrict__ v,
+                       const float *__restrict__ g, int np, float lr, float b1, float b2,
+                       float eps, float c1, float c2, __nv_bfloat16 *__restrict__ pb)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const float gi = g[i];
+    const float mi = fmaf(b1, m[i], (1.f - b1) * gi);
+    const float vi = fmaf(b2, v[i], (1.f - b2) * gi * gi);
+    m[i] = mi;
+    v[i] = vi;
+    const float pi = p[i] - lr * (mi * c1) / (sqrtf(vi * c2) + eps);
+    p[i] = pi;
+    pb[i] = __float2bfloat16_rn(pi);
+}
+
+// Per event: regions whose mean softmax mass is >= tau; with grow, also
+// their 8 neighbours in the 8 x 8 region grid (no wrap); every region when
+// more than fmax of the 64 are selected or the event has no hits.
+__global__ void k_region_mask(const float *__restrict__ mass, const int *__restrict__ off,
+                              int n_ev, float tau, float fmax, int grow,
+                              unsigned long long *__restrict__ mask)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n_ev) return;
+    const int n = off[e + 1] - off[e];
+    unsigned long long bits = 0ull;
+    for (int c = 0; c < kOut; ++c) {
+        const float mm = n > 0 ? mass[(size_t)e * kOut + c] / (float)n : 0.f;
+        if (mm >= tau) bits |= 1ull << c;
+    }
+    if (grow) {
+        // bit 8 rb + db: neighbours in d0 are +-1 within a byte, in rho +-8
+        const unsigned long long c0 = 0x0101010101010101ull, c7 = 0x8080808080808080ull;
+        bits |= ((bits << 1) & ~c0) | ((bits >> 1) & ~c7);
+        bits |= (bits << 8) | (bits >> 8);
+    }
+    mask[e] = ((float)__popcll(bits) > fmax * (float)kOut || n == 0) ? ~0ull : bits;
+}
+
+constexpr size_t kFwdSmem = (size_t)(kH * kH + kH * kOut + kIn * kH + kH * kFwdThreads) * 2 +
+                           (size_t)(2 * kH + 2 * kOut) * 4;
+constexpr size_t kBwdSmem = (size_t)(kH * kH + kH * kOut) * 2 + (size_t)kH * (kFwdThreads + 1) * 4;
+
+}  // namespace
+
+// Region masses and masks of n_ev events whose hits sit at off[] (device);
+// the hit total is read from off[n_ev] on the device, so a captured graph
+// serves any batch of n_ev events with at most max_hits hits.
+cudaError_t launch_region_mask(const void *params_bf16, const float *x, const float *y,
+                               const float *z, const uint8_t *layer, const int *off, int n_ev,
+                               int max_hits, float tau, float fmax, int grow, float *mass,
+                               unsigned long long *masks, cudaStream_t st)
+{
+    cudaError_t e = cudaMemsetAsync(mass, 0, (size_t)n_ev * kOut * sizeof(float), st);
+    if (e != cudaSuccess) return e;
+    if (max_hits > 0) {
+        FwdOut o{nullptr, nullptr, nullptr, nullptr, mass, off, n_ev, off + n_ev};
+        const int blocks = min((max_hits + kFwdThreads - 1) / kFwdThreads, 152 * 8);
+        k_mlp_fwd<<<blocks, kFwdThreads, kFwdSmem, st>>>((const __nv_bfloat16 *)params_bf16, x, y,
+                                                         z, layer, max_hits, o);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    k_region_mask<<<(n_ev + 127) / 128, 128, 0, st>>>(mass, off, n_ev, tau, fmax, grow, masks);
+    return cudaGetLastError();
+}
+
+cudaError_t prepare_mlp_kernels()
+{
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kFwdSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_mlp_bwd_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBwdSmem);
+    return e;
+}
+
+}  // namespace ht
+
+using namespace ht;
+
+extern "C" {
+
+int32_t ht_mlp_param_count(void) { return kParams; }
+
+ht_status ht_mlp_forward(const void *params_bf16, const float *x, const float *y, const float *z,
+                         const uint8_t *layer, int32_t n, float *prob, void *h1, void *h2,
+                         void *feat, ht_stream stream)
+{
+    if (!params_bf16 || n < 0 || (n > 0 && (!x || !y || !z || !layer)))
+        return set_error(HT_ERR_ARG, "ht_mlp_forward: bad argument");
+    if (n == 0) return HT_OK;
+    FwdOut o{prob, (__nv_bfloat16 *)h1, (__nv_bfloat16 *)h2, (__nv_bfloat16 *)feat, nullptr,
+             nullptr, 0, nullptr};
+    const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, 152 * 8);
+    k_mlp_fwd<<<blocks, kFwdThreads, kFwdSmem, reinterpret_cast<cudaStream_t>(stream)>>>(
+        (const __nv_bfloat16 *)params_bf16, x, y, z, layer, n, o);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+ht_status ht_mlp_region_mask(const void *params_bf16, const float *x, const float *y,
+                             const float *z, const uint8_t *layer, const int32_t *off,
+                             int32_t n_events, int32_t n_hits, float tau, float fmax, int32_t grow,
+                             float *mass, uint64_t *masks, ht_stream stream)
+{
+    if (!params_bf16 || !off || !mass || !masks || n_events < 1 || n_hits < 0 ||
+        (n_hits > 0 && (!x || !y || !z || !layer)))
+        return set_error(HT_ERR_ARG, "ht_mlp_region_mask: bad argument");
+    const cudaError_t e = launch_region_mask(params_bf16, x, y, z, layer, off, n_events, n_hits,
+                                             tau, fmax, grow, mass,
+                                             reinterpret_cast<unsigned long long *>(masks),
+                                             reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+size_t ht_mlp_backward_workspace_size(int32_t n)
+{
+    const size_t nh = (size_t)(n > 0 ? n : 1);
+    return align256(nh * kOut * 4) + 2 * align256(nh * kH * 4) + 3 * align256(nh * kH * 2) + 256;
+}
+
+// Gradients (added into grad, float32, kParams entries) of the mean cross
+// entropy over labelled hits of one minibatch whose forward pass stored
+// prob, h1, h2 and feat.
+ht_status ht_mlp_backward(const void *params_bf16, const int32_t *labels, int32_t n,
+                          const float *prob, const void *h1, const void *h2, const void *feat,
+                          float *grad, void *workspace, size_t workspace_bytes, ht_stream stream)
+{
+    if (!params_bf16 || !labels || !prob || !h1 || !h2 || !feat || !grad || !workspace || n < 1)
+        return set_error(HT_ERR_ARG, "ht_mlp_backward: bad argument");
+    if (workspace_bytes < ht_mlp_backward_workspace_size(n))
+        return set_error(HT_ERR_ARG, "ht_mlp_backward: workspace too small");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const size_t nh = (size_t)n;
+    char *p = reinterpret_cast<char *>(workspace);
+    float *dL = reinterpret_cast<float *>(p); p += align256(nh * kOut * 4);
+    float *dH2 = reinterpret_cast<float *>(p); p += align256(nh * kH * 4);
+    float *dH1 = reinterpret_cast<float *>(p); p += align256(nh * kH * 4);
+    p += 3 * align256(nh * kH * 2);
+    int *nl = reinterpret_cast<int *>(p);
+    cudaError_t e = cudaMemsetAsync(nl, 0, 4, st);
+    if (e != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+    k_count_labels<<<min(1024, (n + 255) / 256), 256, 0, st>>>(labels, n, nl);
+    const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, 152 * 4);
+    k_mlp_bwd_act<<<blocks, kFwdThreads, kBwdSmem, st>>>((const __nv_bfloat16 *)params_bf16, prob, labels,
+                                                  (const __nv_bfloat16 *)h1,
+                                                  (const __nv_bfloat16 *)h2, n, nl, dL, dH2, dH1);
+    const int splits = max(1, min(128, n / 512));
+    // dW3 = h2^T dL, db3
+    k_wgrad<<<dim3(kH / kGT, 1, splits), 256, 0, st>>>((const __nv_bfloat16 *)h2, kH, dL, kOut, n,
+                                                       kH, kOut, grad + oW3, grad + ob3);
+    // dW2 = h1^T dH2, db2
+    k_wgrad<<<dim3(kH / kGT, kH / kGT, splits), 256, 0, st>>>((const __nv_bfloat16 *)h1, kH, dH2,
+                                                              kH, n, kH, kH, grad + oW2,
+                                                              grad + ob2);
+    // dW1 = f^T dH1, db1
+    k_wgrad<<<dim3(1, kH / kGT, splits), 256, 0, st>>>((const __nv_bfloat16 *)feat, 8, dH1, kH, n,
+                                                       kIn, kH, grad + oW1, grad + ob1);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+ht_status ht_mlp_adam(float *params, float *m, float *v, const float *grad, int32_t step, float lr,
+                      float beta1, float beta2, float eps, void *params_bf16, ht_stream stream)
+{
+    if (!params || !m || !v || !grad || !params_bf16 || step < 1)
+        return set_error(HT_ERR_ARG, "ht_mlp_adam: bad argument");
+    const float c1 = (float)(1.0 / (1.0 - pow((double)beta1, step)));
+    const float c2 = (float)(1.0 / (1.0 - pow((double)beta2, step)));
+    k_adam<<<(kParams + 255) / 256, 256, 0, reinterpret_cast<cudaStream_t>(stream)>>>(
+        params, m, v, grad, kParams, lr, beta1, beta2, eps, c1, c2, (__nv_bfloat16 *)params_bf16);
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+}  // extern "C"

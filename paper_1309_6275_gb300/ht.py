@@ -14,6 +14,9 @@ Tensor conventions:
   zres          int32 [cap, 3] = {n_z0, m_cot, count}
   stats         int64 [2] (uint64 counters: votes, float64 redos)
   workspace     uint8, at least the size the matching *_workspace_size gives
+  mask          int64 [1] per event (uint64 region bits, see ht_vote_masked)
+  MLP params    float32 master / int16 (BF16 bits) copy [ht_mlp_param_count()]
+  layer         uint8 [n] per hit
 """
 import ctypes
 import os
@@ -36,6 +39,12 @@ class _Desc(ctypes.Structure):
                 ("count_bits", ctypes.c_int32), ("reserved", ctypes.c_int32),
                 ("rho_max", ctypes.c_double), ("d0_half", ctypes.c_double),
                 ("z0_max", ctypes.c_double), ("cot_max", ctypes.c_double)]
+
+
+class _Proposal(ctypes.Structure):
+    _fields_ = [("params_bf16", ctypes.c_void_p), ("layer", ctypes.c_void_p),
+                ("tau", ctypes.c_float), ("fmax", ctypes.c_float),
+                ("grow", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 # (name, restype, argtypes) of every exported function, as in include/ht.h
@@ -63,6 +72,19 @@ SIGNATURES = [
     ("ht_batch_stage_ms", _I32, [_P, _P]),
     ("ht_batch_autotune", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P,
                                   ctypes.POINTER(_I32), _P]),
+    ("ht_vote_masked", _I32, [_P, _P, _P, _I32, _P, _P, _P, _P]),
+    ("ht_find_peaks_masked", _I32, [_P, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
+    ("ht_mlp_param_count", _I32, []),
+    ("ht_mlp_forward", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]),
+    ("ht_mlp_region_mask", _I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, ctypes.c_float,
+                                  ctypes.c_float, _I32, _P, _P, _P]),
+    ("ht_mlp_backward_workspace_size", _SZ, [_I32]),
+    ("ht_mlp_backward", _I32, [_P, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
+    ("ht_mlp_adam", _I32, [_P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float,
+                           ctypes.c_float, ctypes.c_float, _P, _P]),
+    ("ht_batch_run_masked", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
+    ("ht_batch_run_learned", _I32, [_P, _P, _P, _P, _P, _I32, ctypes.POINTER(_Proposal), _P,
+                                    _P, _P, _P, _P, _P, _P]),
 ]
 
 
@@ -159,6 +181,53 @@ def ht_find_peaks(g, acc, peaks, cap, d_count, workspace, stream=None):
     _check(lib().ht_find_peaks(g.handle, _ptr(acc), _ptr(peaks), cap, _ptr(d_count),
                                _ptr(workspace), workspace.numel(), _stream(stream)),
            "ht_find_peaks")
+
+
+def ht_vote_masked(g, x, y, mask, acc, stats=None, stream=None):
+    """Vote restricted to the regions of mask (device int64 [1])."""
+    _check(lib().ht_vote_masked(g.handle, _ptr(x), _ptr(y), x.numel(), _ptr(mask), _ptr(acc),
+                                _ptr(stats), _stream(stream)), "ht_vote_masked")
+
+
+def ht_find_peaks_masked(g, acc, mask, peaks, cap, d_count, workspace, stream=None):
+    _check(lib().ht_find_peaks_masked(g.handle, _ptr(acc), _ptr(mask), _ptr(peaks), cap,
+                                      _ptr(d_count), _ptr(workspace), workspace.numel(),
+                                      _stream(stream)), "ht_find_peaks_masked")
+
+
+def ht_mlp_param_count():
+    return lib().ht_mlp_param_count()
+
+
+def ht_mlp_forward(params_bf16, x, y, z, layer, prob=None, h1=None, h2=None, feat=None,
+                   stream=None):
+    _check(lib().ht_mlp_forward(_ptr(params_bf16), _ptr(x), _ptr(y), _ptr(z), _ptr(layer),
+                                x.numel(), _ptr(prob), _ptr(h1), _ptr(h2), _ptr(feat),
+                                _stream(stream)), "ht_mlp_forward")
+
+
+def ht_mlp_region_mask(params_bf16, x, y, z, layer, off, tau, fmax, grow, mass, masks,
+                       stream=None):
+    """off: device int32 [n_events + 1]; mass float32 [n_events, 64]; masks int64."""
+    _check(lib().ht_mlp_region_mask(_ptr(params_bf16), _ptr(x), _ptr(y), _ptr(z), _ptr(layer),
+                                    _ptr(off), off.numel() - 1, x.numel(), tau, fmax,
+                                    int(grow), _ptr(mass), _ptr(masks), _stream(stream)),
+           "ht_mlp_region_mask")
+
+
+def ht_mlp_backward_workspace_size(n):
+    return lib().ht_mlp_backward_workspace_size(n)
+
+
+def ht_mlp_backward(params_bf16, labels, prob, h1, h2, feat, grad, workspace, stream=None):
+    _check(lib().ht_mlp_backward(_ptr(params_bf16), _ptr(labels), labels.numel(), _ptr(prob),
+                                 _ptr(h1), _ptr(h2), _ptr(feat), _ptr(grad), _ptr(workspace),
+                                 workspace.numel(), _stream(stream)), "ht_mlp_backward")
+
+
+def ht_mlp_adam(params, m, v, grad, step, lr, beta1, beta2, eps, params_bf16, stream=None):
+    _check(lib().ht_mlp_adam(_ptr(params), _ptr(m), _ptr(v), _ptr(grad), step, lr, beta1, beta2,
+                             eps, _ptr(params_bf16), _stream(stream)), "ht_mlp_adam")
 
 
 def ht_find_peaks_noalloc(g, acc, peaks, cap, d_count, stream=None):
@@ -284,10 +353,34 @@ class Batch:
                                   _ptr(self.zres), _ptr(self.stats), _stream(stream)),
                "ht_batch_run")
 
+    def run_masked(self, x, y, z, offsets, masks, stream=None):
+        """run() with event e's vote and peaks restricted to masks[e]
+        (device int64 [n_events])."""
+        off, p = self._offsets(offsets)
+        self._keep = off
+        _check(lib().ht_batch_run_masked(self.handle, _ptr(x), _ptr(y), _ptr(z), p,
+                                         off.shape[0] - 1, _ptr(masks), _ptr(self.peaks),
+                                         _ptr(self.counts), _ptr(self.assign), _ptr(self.zres),
+                                         _ptr(self.stats), _stream(stream)),
+               "ht_batch_run_masked")
+
+    def run_learned(self, x, y, z, layer, offsets, params_bf16, masks, tau, fmax, grow=0,
+                    stream=None):
+        """run() with the masks proposed by the MLP inside the same graph;
+        masks (device int64 [n_events]) receives them."""
+        off, p = self._offsets(offsets)
+        self._keep = off
+        self._prop = _Proposal(params_bf16.data_ptr(), layer.data_ptr(), tau, fmax, int(grow), 0)
+        _check(lib().ht_batch_run_learned(self.handle, _ptr(x), _ptr(y), _ptr(z), p,
+                                          off.shape[0] - 1, ctypes.byref(self._prop),
+                                          _ptr(masks), _ptr(self.peaks), _ptr(self.counts),
+                                          _ptr(self.assign), _ptr(self.zres), _ptr(self.stats),
+                                          _stream(stream)), "ht_batch_run_learned")
+
     def stage_ms(self):
-        """[vote, peaks + candidate lists, association, decode + z vote] ms of
-        the last completed run (synchronise first)."""
-        arr = (ctypes.c_float * 4)()
+        """[proposal, vote, peaks + candidate lists, association, decode + z
+        vote] ms of the last completed run (synchronise first)."""
+        arr = (ctypes.c_float * 5)()
         _check(lib().ht_batch_stage_ms(self.handle, ctypes.cast(arr, ctypes.c_void_p)),
                "ht_batch_stage_ms")
         return list(arr)
