@@ -15,6 +15,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "ht_internal.cuh"
 
 namespace ht {
@@ -351,6 +353,23 @@ constexpr size_t kBwdSmem = (size_t)(kH * kH + kH * kOut) * 2 + (size_t)kH * (kF
 
 }  // namespace
 
+cudaError_t prepare_mlp_kernels();
+
+// The MLP calls need no geometry, so each device's kernel attributes are
+// also set on the first MLP call made with that device current.
+cudaError_t mlp_ready()
+{
+    constexpr int kMaxDev = 64;
+    static std::once_flag once[kMaxDev];
+    static cudaError_t status[kMaxDev];
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    std::call_once(once[dev], [dev] { status[dev] = prepare_mlp_kernels(); });
+    return status[dev];
+}
+
 // Region masses and masks of n_ev events whose hits sit at off[] (device);
 // the hit total is read from off[n_ev] on the device, so a captured graph
 // serves any batch of n_ev events with at most max_hits hits.
@@ -359,7 +378,8 @@ cudaError_t launch_region_mask(const void *params_bf16, const float *x, const fl
                                int max_hits, float tau, float fmax, int grow, float *mass,
                                unsigned long long *masks, cudaStream_t st)
 {
-    cudaError_t e = cudaMemsetAsync(mass, 0, (size_t)n_ev * kOut * sizeof(float), st);
+    cudaError_t e = mlp_ready();
+    if (e == cudaSuccess) e = cudaMemsetAsync(mass, 0, (size_t)n_ev * kOut * sizeof(float), st);
     if (e != cudaSuccess) return e;
     if (max_hits > 0) {
         FwdOut o{nullptr, nullptr, nullptr, nullptr, mass, off, n_ev, off + n_ev};
@@ -398,6 +418,8 @@ ht_status ht_mlp_forward(const void *params_bf16, const float *x, const float *y
     if (!params_bf16 || n < 0 || (n > 0 && (!x || !y || !z || !layer)))
         return set_error(HT_ERR_ARG, "ht_mlp_forward: bad argument");
     if (n == 0) return HT_OK;
+    const cudaError_t pe = mlp_ready();
+    if (pe != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(pe));
     FwdOut o{prob, (__nv_bfloat16 *)h1, (__nv_bfloat16 *)h2, (__nv_bfloat16 *)feat, nullptr,
              nullptr, 0, nullptr};
     const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, 152 * 8);
@@ -440,6 +462,8 @@ ht_status ht_mlp_backward(const void *params_bf16, const int32_t *labels, int32_
     if (workspace_bytes < ht_mlp_backward_workspace_size(n))
         return set_error(HT_ERR_ARG, "ht_mlp_backward: workspace too small");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    const cudaError_t pe = mlp_ready();
+    if (pe != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(pe));
     const size_t nh = (size_t)n;
     char *p = reinterpret_cast<char *>(workspace);
     float *dL = reinterpret_cast<float *>(p); p += align256(nh * kOut * 4);
