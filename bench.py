@@ -51,6 +51,9 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-single", action="store_true")
     p.add_argument("--batch", type=int, default=25, help="events per ht_batch_run")
+    p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--tau", type=float, default=0.02, help="proposal region threshold")
+    p.add_argument("--grow", type=int, default=1, help="proposal region growth (0 or 1)")
     return p.parse_args()
 
 
@@ -197,6 +200,84 @@ def alu_peak_ops(dev_props, peaks):
     """Issue-limited float32 lane rate: SMs x 128 lanes x max SM clock."""
     mhz = peaks.get("sm_max_mhz") or 2070.0
     return dev_props.multi_processor_count * 128 * mhz * 1e6
+
+
+def learned_leg(args, ht, bt, batches, dev_in, g, flush):
+    """The learned-proposal batched path (ht_batch_run_learned) against the
+    plain one on the same resident events: events/s of each (same timing
+    rules as the headline), votes cast, candidates and track-finding
+    efficiency on the first batch."""
+    import torch
+    from paper_1309_6275_gb300 import learned
+    path = learned.default_weights_path("event100_256")
+    if not os.path.exists(path):
+        return None
+    params, meta = learned.load_weights(path)
+    pb = learned.bf16_params(params)
+    lay = [torch.from_numpy(np.concatenate([ev.layer for ev in b]).astype(np.uint8)).cuda()
+           for b in batches]
+    masks = torch.empty(bt.max_events, dtype=torch.int64, device="cuda")
+    fmax = 0.6
+
+    def run(mode):
+        for (off, (x, y, z)), l in zip(dev_in, lay):
+            if mode == "plain":
+                bt.run(x, y, z, off)
+            else:
+                bt.run_learned(x, y, z, l, off, pb, masks, args.tau, fmax, args.grow)
+
+    out = {}
+    stream = torch.cuda.current_stream()
+    for mode in ("learned", "plain"):
+        for _ in range(max(1, args.warmup)):
+            run(mode)
+        torch.cuda.synchronize()
+        t = 0.0
+        for s_ in range(max(1, args.steps)):
+            flush.fill_(s_ & 0xff)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            run(mode)
+            b.record(stream)
+            b.synchronize()
+            t += a.elapsed_time(b) / 1e3
+        n_ev = sum(len(b_) for b_ in batches)
+        out[mode] = {"value": n_ev * max(1, args.steps) / t}
+        # quality on the first batch
+        off, (x, y, z) = dev_in[0]
+        if mode == "plain":
+            bt.run(x, y, z, off)
+        else:
+            bt.run_learned(x, y, z, lay[0], off, pb, masks, args.tau, fmax, args.grow)
+        torch.cuda.synchronize()
+        q = dict(votes=0, cands=0, n_rec=0, fa=0, fc=0)
+        for i, ev in enumerate(batches[0]):
+            r = bt.event_results(off, i)
+            nr, fa, fc = learned.efficiency(g, ev, r["peaks"], r["assign"])
+            q["votes"] += r["votes"]; q["cands"] += r["count"]
+            q["n_rec"] += nr; q["fa"] += fa; q["fc"] += fc
+        out[mode].update(q)
+        if mode == "learned":
+            mk = [int(v) & ((1 << 64) - 1) for v in masks[:len(batches[0])].cpu().tolist()]
+            out[mode]["mean_regions"] = float(np.mean([bin(m).count("1") for m in mk]))
+            out[mode]["fallback_frac"] = float(np.mean([m == (1 << 64) - 1 for m in mk]))
+    L, P = out["learned"], out["plain"]
+    return {"value": L["value"], "unit": "events/s", "plain_value": P["value"],
+            "speedup": L["value"] / P["value"],
+            "vote_frac": L["votes"] / max(P["votes"], 1),
+            "candidate_frac": L["cands"] / max(P["cands"], 1),
+            "eff_candidate": {"plain": P["fc"] / max(P["n_rec"], 1),
+                              "learned": L["fc"] / max(L["n_rec"], 1)},
+            "eff_assign": {"plain": P["fa"] / max(P["n_rec"], 1),
+                           "learned": L["fa"] / max(L["n_rec"], 1)},
+            "quality_sample": f"first batch ({len(batches[0])} events), "
+                              f"{P['n_rec']} reconstructable tracks",
+            "mean_regions": L["mean_regions"], "fallback_frac": L["fallback_frac"],
+            "tau": args.tau, "fmax": fmax, "grow": args.grow,
+            "path": "ht_batch_run_learned (proposal MLP + masked vote/peaks in one graph)",
+            "weights": os.path.relpath(path, ROOT),
+            "trained_on": f"{meta.get('n_events')} {meta.get('workload')} events"}
 
 
 def make_batches(cfg, n_ev, seed0, B):
@@ -356,6 +437,10 @@ def run_ours(args):
         b.synchronize()
         single = n_ev / (a.elapsed_time(b) / 1e3)
 
+    learned_res = None
+    if not args.no_learned:
+        learned_res = learned_leg(args, ht, bt, batches, dev_in, g, flush)
+
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     peak_ops = alu_peak_ops(props, peaks)
@@ -404,6 +489,8 @@ def run_ours(args):
     }
     if single:
         line["single_event_api_events_per_s"] = single
+    if learned_res:
+        line["learned"] = learned_res
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:

@@ -305,3 +305,46 @@ def test_batch_masked_and_learned_runs():
             assert np.array_equal(r[k], res_l[e][k])
     B.close()
     G.close()
+
+
+def test_trained_proposal_gain_over_the_plain_path():
+    """What the committed, trained network buys on the batched-stream
+    workload: far fewer votes and candidates, at a small loss of
+    candidate-level efficiency (tracks outside the proposed regions) and the
+    same assignment-level efficiency."""
+    import torch
+    from paper_1309_6275_gb300 import ht, learned
+    name = "stream2000_256"
+    g = synth.geometry_of(name)
+    evs = list(synth.make_stream(name, 8, 5000))
+    off = np.zeros(len(evs) + 1, np.int32)
+    off[1:] = np.cumsum([e.n_hits for e in evs])
+    cat = lambda k, t: to_dev(np.concatenate([getattr(e, k) for e in evs]).astype(t))
+    x, y, z, layer = cat("x", np.float32), cat("y", np.float32), cat("z", np.float32), cat("layer", np.uint8)
+    params, meta = learned.load_weights(learned.default_weights_path("event100_256"))
+    assert meta["n_events"] >= 100000
+    pb = learned.bf16_params(params)
+    G = ht.Geometry(g)
+    B = ht.Batch(G, max_events=len(evs), max_hits=int(off[-1]), cap=1 << 20)
+    masks = torch.empty(len(evs), dtype=torch.int64, device="cuda")
+    res = {}
+    for mode in ("plain", "learned"):
+        if mode == "plain":
+            B.run(x, y, z, off)
+        else:
+            B.run_learned(x, y, z, layer, off, pb, masks, 0.02, 0.6, 1)
+        torch.cuda.synchronize()
+        q = np.zeros(5, np.int64)
+        for e, ev in enumerate(evs):
+            r = B.event_results(off, e)
+            q += [r["votes"], r["count"], *learned.efficiency(g, ev, r["peaks"], r["assign"])]
+        res[mode] = q
+    P, L = res["plain"], res["learned"]
+    mk = [int(v) & ((1 << 64) - 1) for v in masks.cpu().tolist()]
+    assert all(m != (1 << 64) - 1 for m in mk)          # no fallback to the full vote
+    assert L[0] < 0.7 * P[0] and L[1] < 0.7 * P[1]      # votes, candidates
+    eff = lambda q, k: q[k] / max(q[2], 1)
+    assert eff(L, 4) >= eff(P, 4) - 0.05                # candidate-level efficiency
+    assert abs(eff(L, 3) - eff(P, 3)) <= 0.005          # assignment-level efficiency
+    B.close()
+    G.close()
