@@ -253,6 +253,12 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     const int tile = ty * (G.n_phi0 / KT) + tx;
     const int l0 = toff[tile];
     const int L = min(toff[tile + 1] - l0, lcap);
+    if (L == 0) return;   // no candidate box meets the tile (uniform over the CTA)
+    __shared__ int s_ext[4];   // rows and d0 bins spanned by the candidates
+    if (threadIdx.x == 0) {
+        s_ext[0] = s_ext[2] = 0x7fffffff;
+        s_ext[1] = s_ext[3] = -1;
+    }
 
     // sort the tile's candidates by index: bitonic sort in the map's space
     int P = 1;
@@ -284,8 +290,11 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     __syncthreads();
 
     // scatter each candidate's box, key = count << 16 | (65535 - rank)
+    int emin_i = 0x7fffffff, emax_i = -1, emin_j = 0x7fffffff, emax_j = -1;
     for (int r = threadIdx.x; r < L; r += kThreads) {
         const ht_peak pk = peaks[local[r]];
+        emin_i = min(emin_i, pk.i_rho); emax_i = max(emax_i, pk.i_rho);
+        emin_j = min(emin_j, pk.j_d0); emax_j = max(emax_j, pk.j_d0);
         const uint32_t key = ((uint32_t)pk.count << 16) | (uint32_t)(0xffff - r);
 #pragma unroll
         for (int d = -1; d <= 1; ++d) {
@@ -305,7 +314,33 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
             }
         }
     }
+    emin_i = __reduce_min_sync(0xffffffffu, emin_i);
+    emax_i = __reduce_max_sync(0xffffffffu, emax_i);
+    emin_j = __reduce_min_sync(0xffffffffu, emin_j);
+    emax_j = __reduce_max_sync(0xffffffffu, emax_j);
+    if (lane == 0) {
+        atomicMin(&s_ext[0], emin_i); atomicMax(&s_ext[1], emax_i);
+        atomicMin(&s_ext[2], emin_j); atomicMax(&s_ext[3], emax_j);
+    }
     __syncthreads();
+    // Only votes inside the candidates' boxes matter: phase 1 keeps the
+    // (hit, column) pairs whose circle can reach the boxes' d0 bins within
+    // their rows (the masked vote's filter, with one window).
+    MaskCtx M;
+    {
+        const int jlo = max(s_ext[2] - 1, 0), jhi = min(s_ext[3] + 1, ND - 1);
+        const int ilast = min(T.i0 + 31, G.n_rho - 1);
+        const int ilo = min(max(s_ext[0] - 1, T.i0), ilast);
+        const int ihi = max(min(s_ext[1] + 1, ilast), ilo);
+        M.bm = M.tile_bm = 0u;
+        M.nrun = 1;
+        M.wlo[0] = (float)(((double)jlo - G.off) * G.delta) - 0.01f;
+        M.whi[0] = (float)(((double)jhi + 1.0 - G.off) * G.delta) + 0.01f;
+#pragma unroll
+        for (int r = 1; r < 4; ++r) M.wlo[r] = M.whi[r] = 0.0f;
+        M.rho_lo = G.rho32[ilo] - G.drho_f;
+        M.rho_hi = G.rho32[ihi] + G.drho_f;
+    }
 
     auto to64 = [&](uint32_t k32) -> unsigned long long {
         const int m = local[0xffff - (int)(k32 & 0xffffu)];
@@ -314,7 +349,7 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
 
     int parity = 0;
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
-        collect<KT>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W);
+        collect<KT, true>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W, &M);
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;
