@@ -251,6 +251,7 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
         else:
             bt.run_learned(x, y, z, lay[0], off, pb, masks, args.tau, fmax, args.grow)
         torch.cuda.synchronize()
+        out[mode]["stage_ms"] = [round(v, 3) for v in bt.stage_ms()]
         q = dict(votes=0, cands=0, n_rec=0, fa=0, fc=0)
         for i, ev in enumerate(batches[0]):
             r = bt.event_results(off, i)
@@ -274,15 +275,23 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
             "quality_sample": f"first batch ({len(batches[0])} events), "
                               f"{P['n_rec']} reconstructable tracks",
             "mean_regions": L["mean_regions"], "fallback_frac": L["fallback_frac"],
+            "first_batch_stage_ms": {"stages": ["proposal", "vote", "peaks+lists", "association",
+                                                "decode+z"],
+                                     "plain": P["stage_ms"], "learned": L["stage_ms"]},
             "tau": args.tau, "fmax": fmax, "grow": args.grow,
             "path": "ht_batch_run_learned (proposal MLP + masked vote/peaks in one graph)",
             "weights": os.path.relpath(path, ROOT),
             "trained_on": f"{meta.get('n_events')} {meta.get('workload')} events"}
 
 
-def make_batches(cfg, n_ev, seed0, B):
-    events = [synth.make_event(cfg["gen"], seed0 + e) for e in range(n_ev)]
-    return events, [events[i:i + B] for i in range(0, n_ev, B)]
+def make_batches(cfg, n_ev, world, rank, B):
+    """This rank's events: the job is world * n_ev seeded events, split over
+    the ranks by the LPT partition (weak scaling: about n_ev per rank)."""
+    from paper_1309_6275_gb300 import shard
+    every = [synth.make_event(cfg["gen"], cfg["seed0"] + e) for e in range(world * n_ev)]
+    mine = shard.partition([ev.n_hits for ev in every], world)[rank]
+    events = [every[e] for e in mine]
+    return mine, events, [events[i:i + B] for i in range(0, len(events), B)]
 
 
 def run_ours(args):
@@ -299,8 +308,9 @@ def run_ours(args):
     g = dict(cfg["geom"])
     n_ev = args.events or cfg["events"]
     B = args.batch
-    seed0 = cfg["seed0"] + rank * 1_000_003
-    events, batches = make_batches(cfg, n_ev, seed0, B)
+    ids, events, batches = make_batches(cfg, n_ev, world, rank, B)
+    n_job = world * n_ev           # events of the whole job per step
+    n_ev = len(events)             # this rank's share
     G = ht.Geometry(g)
     cap = CAP
     max_hits = max(sum(ev.n_hits for ev in b) for b in batches)
@@ -362,12 +372,22 @@ def run_ours(args):
     torch.cuda.synchronize()
     clk = clocks.stop() if rank == 0 else None
 
+    # per-event results to rank 0 (the only collective; outside the timing)
+    from paper_1309_6275_gb300 import shard
+    local = {}
+    for (off, (x, y, z)), b, base in zip(dev_in, batches, range(0, n_ev, B)):
+        bt.run(x, y, z, off)
+        cnt = bt.counts[:len(b)].cpu().tolist()
+        for i in range(len(b)):
+            local[int(ids[base + i])] = int(cnt[i])
+    gathered = shard.gather_results(local)
+
     total_s = sum(step_ms) / 1e3
     t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
     if dist:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     max_s = float(t.item())
-    value = world * n_ev * args.steps / max_s
+    value = n_job * args.steps / max_s
 
     # ---- e2e: hits from pinned host memory, results read back, per batch
     e2e = None
@@ -411,7 +431,7 @@ def run_ours(args):
         et = torch.tensor([sum(tt)], dtype=torch.float64, device="cuda")
         if dist:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * n_ev * len(tt) / float(et.item()), "unit": "events/s",
+        e2e = {"value": n_job * len(tt) / float(et.item()), "unit": "events/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "api": "ht_batch_run with host copies of hits in and results out"}
 
@@ -473,20 +493,24 @@ def run_ours(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded detector MC)",
-        "config": {"workload": args.workload, "events_per_step": n_ev,
+        "config": {"workload": args.workload, "events_per_step": n_job,
                    "hits_per_step": n_hits_total,
                    "geometry": f"{g['n_rho']}x{g['n_d0']}x{g['n_phi0']} uint16, "
                                f"{g['n_z0']}x{g['n_cot']} z grid, T={g['threshold']}",
                    "path": f"ht_batch_run, {B} events per batch, CUDA graph replay",
                    "autotune": tune,
                    "l2": "flushed (256 MiB write) before each timed step",
-                   "parallelism": f"events sharded, {world} rank(s), no collective"},
+                   "parallelism": f"events sharded (LPT by hits), {world} rank(s), no "
+                                  "data-path collective; per-event results gathered to "
+                                  "rank 0 after timing"},
         "hit_votes_per_s": world * votes_total / max_s,
         "step_ms": [round(v, 3) for v in step_ms],
         "gpu_launches": args.steps * sum(launches_per_batch(len(b)) for b in batches),
         "roofline": roof,
         "clocks": clk,
     }
+    if gathered is not None:
+        line["events_gathered"] = len(gathered)
     if single:
         line["single_event_api_events_per_s"] = single
     if learned_res:
