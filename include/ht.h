@@ -119,7 +119,7 @@ ht_status ht_vote(const ht_geometry *g, const float *x, const float *y,
  * >= threshold and, for each existing 26-neighbour l' (rho and d0 do not
  * wrap, phi0 wraps), count(l) > count(l') when l' < l and count(l) >=
  * count(l') when l' > l.  Peaks are written in increasing l.
- *   acc        accumulator from ht_vote (device).
+ *   acc        accumulator from ht_vote (device, 16-byte aligned).
  *   peaks      cap entries (device); the first min(total, cap) are written.
  *   cap        >= 0.
  *   d_count    one device int32: the total number of peaks (may exceed cap).

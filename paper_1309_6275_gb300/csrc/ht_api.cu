@@ -21,6 +21,7 @@ size_t tile_smem_need(const DevGeom &G);
 cudaError_t prepare_z_kernels(int max_smem);
 cudaError_t prepare_mlp_kernels();
 cudaError_t prepare_masked_vote_kernels(int max_smem);
+cudaError_t prepare_peaks_kernels();
 size_t z_big_smem(const DevGeom &G);
 }  // namespace ht
 
@@ -178,6 +179,7 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     if (e == cudaSuccess) e = ht::prepare_tile_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_z_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_masked_vote_kernels(max_smem);
+    if (e == cudaSuccess) e = ht::prepare_peaks_kernels();
     if (e == cudaSuccess) e = ht::prepare_mlp_kernels();
     if (e != cudaSuccess) {
         cudaFree(g->d_tables);
@@ -252,7 +254,8 @@ ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks, i
     if (workspace_bytes < ht::peaks_workspace_bytes(g->G))
         return fail(HT_ERR_ARG, "ht_find_peaks: workspace %zu B < %zu B", workspace_bytes,
                     ht::peaks_workspace_bytes(g->G));
-    if (!aligned(workspace, 256)) return fail(HT_ERR_ARG, "ht_find_peaks: workspace alignment");
+    if (!aligned(workspace, 256) || !aligned(acc, 16))
+        return fail(HT_ERR_ARG, "ht_find_peaks: workspace or accumulator alignment");
     cudaError_t e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, workspace, S(stream));
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_find_peaks");
 }
@@ -267,7 +270,7 @@ ht_status ht_find_peaks_masked(const ht_geometry *g, const void *acc, const uint
     if (workspace_bytes < ht::peaks_workspace_bytes(g->G))
         return fail(HT_ERR_ARG, "ht_find_peaks_masked: workspace %zu B < %zu B", workspace_bytes,
                     ht::peaks_workspace_bytes(g->G));
-    if (!aligned(workspace, 256) || !aligned(mask, 8))
+    if (!aligned(workspace, 256) || !aligned(mask, 8) || !aligned(acc, 16))
         return fail(HT_ERR_ARG, "ht_find_peaks_masked: pointer alignment");
     cudaError_t e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, workspace, S(stream),
                                      reinterpret_cast<const unsigned long long *>(mask));

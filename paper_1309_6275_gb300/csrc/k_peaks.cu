@@ -4,18 +4,19 @@
 // finder's tuning for tracks of 7 or more hits).
 //
 // Design (GB300, HBM-bound stencil):
-//  * A CTA of 256 threads owns one segment row (i, j-block, k-block): thread
-//    = phi0 column k, and the CTA walks d0 bins j over its block keeping a
-//    rolling 3 (rho) x 3 (d0) x 3 (phi0) window in registers, so each step
-//    loads one new d0 slice (9 coalesced loads per thread, neighbours in
-//    phi0 served from L1).  Rows beyond rho/d0 edges read as absent; phi0
-//    wraps.
+//  * A CTA of 256 threads owns one segment row (i, j-block of 16 d0 bins,
+//    block of 256 phi0 columns).  It first stages rows i-1..i+1 x bins
+//    j0-1..j0+16 x its columns plus one wrapped column on each side into
+//    shared memory with 16-byte loads, all issued before any is used, so a
+//    CTA waits for memory once instead of once per d0 bin; absent rows and
+//    bins read as -1.  Then thread = phi0 column walks the bins keeping a
+//    rolling 3 x 3 x 3 window in registers (9 shared loads per cell).
 //  * Compaction keeps increasing logical index l = (i n_d0 + j) n_phi0 + k:
 //    pass 1 counts the peaks of every (i, j, k-block) segment, a
 //    device-wide scan turns counts into offsets (and the total), pass 2
 //    recomputes and writes each peak at its segment offset plus its rank in
-//    the CTA (warp ballots + a per-warp prefix).  Segments are ordered by l,
-//    so the output is too.
+//    the CTA (warp ballots kept per bin, one barrier per pass).  Segments
+//    are ordered by l, so the output is too.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,7 +28,10 @@ constexpr int kPkThreads = 256;   // phi0 columns per CTA
 
 namespace {
 
-constexpr int kJB = 16;           // d0 bins walked per CTA
+constexpr int kJB = 16;                         // d0 bins per CTA
+constexpr int kSW = kPkThreads + 2;             // staged columns (one wrapped each side)
+constexpr int kSlices = 3 * (kJB + 2);          // staged (row, bin) slices
+constexpr size_t kPkSmem = (size_t)kSlices * kSW * sizeof(int);
 
 // MASKED: only cells inside *mask (a learned proposal's regions) can be
 // peaks; a CTA whose bins are all outside reads nothing.  An inside cell's
@@ -38,16 +42,14 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         const int *__restrict__ segoff, ht_peak *__restrict__ out, int cap,
         const unsigned long long *__restrict__ mask)
 {
+    extern __shared__ __align__(16) int sw[];            // [slice][kSW], slice = r (kJB+2) + jj
+    __shared__ unsigned bal_s[kJB][kPkThreads / 32];
     const int NP = G.n_phi0, ND = G.n_d0, NR = G.n_rho;
     const int nkb = (NP + kPkThreads - 1) / kPkThreads;
     const int kb = blockIdx.x, i = blockIdx.z;
-    const int k = kb * kPkThreads + threadIdx.x;
-    const bool kok = k < NP;
-    const int km = (k == 0) ? NP - 1 : k - 1;
-    const int kp = (k >= NP - 1) ? 0 : k + 1;
+    const int k0 = kb * kPkThreads, ncol = min(kPkThreads, NP - k0);
     const int j0 = blockIdx.y * kJB, j1 = min(j0 + kJB, ND);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    __shared__ int wcnt[kPkThreads / 32];
     unsigned inside = 0xffu;   // d0 blocks inside the mask in row i's rho block
     if (MASKED) {
         inside = (unsigned)(*mask >> (8 * region_block(i, NR))) & 0xffu;
@@ -60,59 +62,97 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         }
     }
 
-    int w[3][3][3];  // [rho -1..+1][d0 -1..+1][phi0 -1..+1]; -1 = absent
-    auto load = [&](int slot, int jj) {
+    // ---- stage the window: interior columns with 16-byte loads
+    constexpr int VEC = 16 / (int)sizeof(T);
+    const int nvec = ncol / VEC;                         // ncol is a multiple of 8
+    for (int v = threadIdx.x; v < kSlices * nvec; v += kPkThreads) {
+        const int sl = v / nvec, q = v - sl * nvec;
+        const int ii = i - 1 + sl / (kJB + 2), jj = j0 - 1 + sl % (kJB + 2);
+        int *dst = sw + sl * kSW + 1 + q * VEC;
+        if (ii < 0 || ii >= NR || jj < 0 || jj >= ND) {
 #pragma unroll
-        for (int di = 0; di < 3; ++di) {
-            const int ii = i + di - 1;
-            const bool ok = kok && ii >= 0 && ii < NR && jj >= 0 && jj < ND;
-            const size_t rowb = ok ? ((size_t)ii * ND + jj) * NP : 0;
-            w[di][slot][0] = ok ? (int)acc[rowb + km] : -1;
-            w[di][slot][1] = ok ? (int)acc[rowb + k] : -1;
-            w[di][slot][2] = ok ? (int)acc[rowb + kp] : -1;
+            for (int e = 0; e < VEC; ++e) dst[e] = -1;
+        } else {
+            const uint4 u = *reinterpret_cast<const uint4 *>(
+                acc + ((size_t)ii * ND + jj) * NP + k0 + q * VEC);
+            const T *t = reinterpret_cast<const T *>(&u);
+#pragma unroll
+            for (int e = 0; e < VEC; ++e) dst[e] = (int)t[e];
         }
-    };
-    load(0, j0 - 1);
-    load(1, j0);
-    for (int j = j0; j < j1; ++j) {
-        load(2, j + 1);
+    }
+    // the two wrapped neighbour columns of every slice
+    for (int v = threadIdx.x; v < 2 * kSlices; v += kPkThreads) {
+        const int sl = v >> 1, side = v & 1;
+        const int ii = i - 1 + sl / (kJB + 2), jj = j0 - 1 + sl % (kJB + 2);
+        const int kk = side ? (k0 + ncol) % NP : (k0 + NP - 1) % NP;
+        const bool ok = ii >= 0 && ii < NR && jj >= 0 && jj < ND;
+        sw[sl * kSW + (side ? 1 + ncol : 0)] = ok ? (int)acc[((size_t)ii * ND + jj) * NP + kk] : -1;
+    }
+    __syncthreads();
+
+    // ---- walk the bins: w[row][bin][col], bins j-1, j, j+1 at slots 0, 1, 2
+    const int c = threadIdx.x;
+    const bool cok = c < ncol;
+    const int k = k0 + c;
+    const int cc = cok ? c : 0;                           // stays inside the staged row
+    auto S = [&](int r, int jj) -> const int * { return sw + (r * (kJB + 2) + jj) * kSW + cc; };
+    int w[3][3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int sl = 0; sl < 2; ++sl) {
+            const int *q = S(r, sl);
+            w[r][sl][0] = q[0]; w[r][sl][1] = q[1]; w[r][sl][2] = q[2];
+        }
+    unsigned mine = 0u;
+    for (int jl = 0; jl < j1 - j0; ++jl) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const int *q = S(r, jl + 2);
+            w[r][2][0] = q[0]; w[r][2][1] = q[1]; w[r][2][2] = q[2];
+        }
         const int v = w[1][1][1];
-        bool pk = kok && v >= G.threshold &&
-                  (!MASKED || ((inside >> region_block(j, ND)) & 1u));
+        bool pk = cok && v >= G.threshold &&
+                  (!MASKED || ((inside >> region_block(j0 + jl, ND)) & 1u));
         // rows i-1 and d0 bin j-1 (at row i) precede l: strictly greater;
         // rows i+1 and d0 bin j+1 follow l: greater or equal.
 #pragma unroll
         for (int dj = 0; dj < 3; ++dj)
 #pragma unroll
-            for (int dk = 0; dk < 3; ++dk) {
-                pk = pk && (v > w[0][dj][dk]) && (v >= w[2][dj][dk]);
-            }
+            for (int dk = 0; dk < 3; ++dk) pk = pk && (v > w[0][dj][dk]) && (v >= w[2][dj][dk]);
 #pragma unroll
         for (int dk = 0; dk < 3; ++dk) pk = pk && (v > w[1][0][dk]) && (v >= w[1][2][dk]);
         // same (i, j): phi0 neighbours; their order flips across the wrap
         pk = pk && ((k != 0) ? (v > w[1][1][0]) : (v >= w[1][1][0]));
         pk = pk && ((k != NP - 1) ? (v >= w[1][1][2]) : (v > w[1][1][2]));
-
-        const int seg = (i * ND + j) * nkb + kb;
-        if (!WRITE) {
-            const int c = __syncthreads_count(pk);
-            if (threadIdx.x == 0) segcnt[seg] = c;
-        } else {
-            const unsigned bal = __ballot_sync(0xffffffffu, pk);
-            if (lane == 0) wcnt[warp] = __popc(bal);
-            __syncthreads();
-            int pos = segoff[seg] + __popc(bal & ((1u << lane) - 1u));
-            for (int w2 = 0; w2 < warp; ++w2) pos += wcnt[w2];
-            if (pk && pos < cap) out[pos] = ht_peak{i, j, k, v};
-            __syncthreads();
-        }
+        const unsigned bal = __ballot_sync(0xffffffffu, pk);
+        if (lane == 0) bal_s[jl][warp] = bal;
+        mine |= (unsigned)pk << jl;
 #pragma unroll
-        for (int di = 0; di < 3; ++di)
+        for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int dk = 0; dk < 3; ++dk) {
-                w[di][0][dk] = w[di][1][dk];
-                w[di][1][dk] = w[di][2][dk];
+                w[r][0][dk] = w[r][1][dk];
+                w[r][1][dk] = w[r][2][dk];
             }
+    }
+    __syncthreads();
+    if (!WRITE) {
+        for (int jl = threadIdx.x; jl < j1 - j0; jl += kPkThreads) {
+            int cnt = 0;
+#pragma unroll
+            for (int w2 = 0; w2 < kPkThreads / 32; ++w2) cnt += __popc(bal_s[jl][w2]);
+            segcnt[(i * ND + j0 + jl) * nkb + kb] = cnt;
+        }
+        return;
+    }
+    while (mine) {
+        const int jl = __ffs(mine) - 1;
+        mine &= mine - 1u;
+        const int seg = (i * ND + j0 + jl) * nkb + kb;
+        int pos = segoff[seg] + __popc(bal_s[jl][warp] & ((1u << lane) - 1u));
+        for (int w2 = 0; w2 < warp; ++w2) pos += __popc(bal_s[jl][w2]);
+        if (pos < cap) out[pos] = ht_peak{i, j0 + jl, k, S(1, jl + 1)[1]};
     }
 }
 
@@ -124,16 +164,33 @@ cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, i
     const int nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     dim3 grid(nkb, (G.n_d0 + kJB - 1) / kJB, G.n_rho);
     const int nseg = G.n_rho * G.n_d0 * nkb;
-    k_peaks<T, false, MASKED><<<grid, kPkThreads, 0, st>>>(G, acc, segcnt, nullptr, nullptr, 0,
-                                                           mask);
+    k_peaks<T, false, MASKED><<<grid, kPkThreads, kPkSmem, st>>>(G, acc, segcnt, nullptr,
+                                                                 nullptr, 0, mask);
     cudaError_t e = scan_exclusive(segcnt, segoff, nullptr, nseg, nullptr, d_count, tmp, st);
     if (e != cudaSuccess) return e;
-    k_peaks<T, true, MASKED><<<grid, kPkThreads, 0, st>>>(G, acc, nullptr, segoff, peaks, cap,
-                                                          mask);
+    k_peaks<T, true, MASKED><<<grid, kPkThreads, kPkSmem, st>>>(G, acc, nullptr, segoff, peaks,
+                                                                cap, mask);
     return cudaGetLastError();
 }
 
 }  // namespace
+
+// The staged window needs more than the default 48 KB of dynamic shared
+// memory.  Called once per device.
+cudaError_t prepare_peaks_kernels()
+{
+    const void *fns[] = {
+        (const void *)k_peaks<uint16_t, false, false>, (const void *)k_peaks<uint16_t, true, false>,
+        (const void *)k_peaks<uint16_t, false, true>,  (const void *)k_peaks<uint16_t, true, true>,
+        (const void *)k_peaks<int32_t, false, false>,  (const void *)k_peaks<int32_t, true, false>,
+        (const void *)k_peaks<int32_t, false, true>,   (const void *)k_peaks<int32_t, true, true>};
+    for (const void *f : fns) {
+        const cudaError_t e =
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPkSmem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
 
 size_t peaks_workspace_bytes(const DevGeom &G)
 {
@@ -205,6 +262,8 @@ extern "C" ht_status ht_find_peaks_noalloc(const ht_geometry *g, const void *acc
     if (!g || !acc || !d_count || (cap > 0 && !peaks))
         return ht::set_error(HT_ERR_ARG, "ht_find_peaks_noalloc: null argument");
     if (cap < 0) return ht::set_error(HT_ERR_ARG, "ht_find_peaks_noalloc: cap < 0");
+    if (reinterpret_cast<uintptr_t>(acc) % 16 != 0)
+        return ht::set_error(HT_ERR_ARG, "ht_find_peaks_noalloc: accumulator not 16-byte aligned");
     const size_t nkb = (g->G.n_phi0 + ht::kPkThreads - 1) / ht::kPkThreads;
     const size_t nseg = (size_t)g->G.n_rho * g->G.n_d0 * nkb;
     if (nseg > (size_t)kNoallocMaxSegments)
