@@ -178,6 +178,7 @@ PROFILED_TRAFFIC = {
     "k_assoc32_batch": {"sha": "fe6ca59689f98200", "bytes_per_event": 50.727424e6 / 4},
 }
 KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_tiles.cu",
+                  "paper_1309_6275_gb300/csrc/tiles.cuh",
                   "paper_1309_6275_gb300/csrc/ht_internal.cuh",
                   "paper_1309_6275_gb300/csrc/df32.cuh"]
 

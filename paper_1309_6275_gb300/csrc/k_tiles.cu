@@ -226,6 +226,65 @@ __global__ void k_cand_tiles(const ht_peak *__restrict__ peaks, const int *__res
     }
 }
 
+// The same lists built with one shared-memory histogram per CTA: each CTA
+// takes a contiguous chunk of the candidates, counts its (candidate, tile)
+// pairs in shared memory and touches each global tile counter once; the fill
+// pass reserves the CTA's slots per tile with one global atomic and places
+// candidates with shared atomics.  Order inside a tile's list is arbitrary
+// (the association sorts each list).
+__global__ void __launch_bounds__(256)
+k_cand_hist(const ht_peak *__restrict__ peaks, const int *__restrict__ d_count, int cap, int NR,
+            int NP, int KT, int nct, int ntiles, int *__restrict__ tcnt, int *__restrict__ tcur,
+            int *__restrict__ list)
+{
+    extern __shared__ int hist[];   // [ntiles]
+    const int ncand = min(*d_count, cap);
+    const int per = (ncand + gridDim.x - 1) / gridDim.x;
+    const int a = blockIdx.x * per, b = min(ncand, a + per);
+    if (a >= b) return;   // uniform over the CTA
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x) hist[t] = 0;
+    __syncthreads();
+    for (int m = a + threadIdx.x; m < b; m += blockDim.x) {
+        int t[kMaxTilesPerCand];
+        const int nt = tiles_of(peaks[m], NR, NP, KT, nct, t);
+        for (int u = 0; u < nt; ++u) atomicAdd(&hist[t[u]], 1);
+    }
+    __syncthreads();
+    if (!list) {
+        for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+            if (hist[t]) atomicAdd(&tcnt[t], hist[t]);
+        return;
+    }
+    for (int t = threadIdx.x; t < ntiles; t += blockDim.x)
+        if (hist[t]) hist[t] = atomicAdd(&tcur[t], hist[t]);
+    __syncthreads();
+    for (int m = a + threadIdx.x; m < b; m += blockDim.x) {
+        int t[kMaxTilesPerCand];
+        const int nt = tiles_of(peaks[m], NR, NP, KT, nct, t);
+        for (int u = 0; u < nt; ++u) list[atomicAdd(&hist[t[u]], 1)] = m;
+    }
+}
+
+constexpr int kCandHistMaxTiles = 24 * 1024;   // 96 KB of shared counters
+
+// One pass of the candidate tile lists: counts (list null) or fill.
+inline void cand_tiles_pass(const ht_peak *peaks, const int *d_count, int cap, int NR, int NP,
+                            int KT, int nct, int ntiles, int *tcnt, int *tcur, int *list,
+                            cudaStream_t st)
+{
+    if (ntiles <= kCandHistMaxTiles) {
+        int dev = 0, sms = 152;
+        if (cudaGetDevice(&dev) == cudaSuccess)
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        k_cand_hist<<<sms, 256, (size_t)ntiles * 4, st>>>(peaks, d_count, cap, NR, NP, KT, nct,
+                                                          ntiles, tcnt, tcur, list);
+        return;
+    }
+    const int nb = min(4096, (cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1);
+    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, NR, NP, KT, nct, list ? nullptr : tcnt,
+                                     list ? tcur : nullptr, list);
+}
+
 template <int KT>
 __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__restrict__ x,
                                              const float *__restrict__ y, int n,
@@ -470,13 +529,12 @@ cudaError_t launch_assoc32_kt(const DevGeom &G, const float *x, const float *y, 
                                          scan_tmp_bytes(ntiles));
     cudaError_t e = cudaMemsetAsync(tcnt, 0, (size_t)ntiles * 4, st);
     if (e != cudaSuccess) return e;
-    const int nb = min(4096, (cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1);
-    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, KT, nct, tcnt,
-                                     nullptr, nullptr);
+    cand_tiles_pass(peaks, d_count, cap, G.n_rho, G.n_phi0, KT, nct, ntiles, tcnt, nullptr,
+                    nullptr, st);
     e = scan_exclusive(tcnt, toff, tcur, ntiles, nullptr, nullptr, tmp, st);
     if (e != cudaSuccess) return e;
-    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, KT, nct, nullptr,
-                                     tcur, tlist);
+    cand_tiles_pass(peaks, d_count, cap, G.n_rho, G.n_phi0, KT, nct, ntiles, nullptr, tcur, tlist,
+                    st);
     dim3 grid(nct, nrt);
     k_assoc32<KT><<<grid, kThreads, assoc32_smem<KT>(G), st>>>(G, x, y, n, peaks, toff, tlist,
                                                                assoc32_lcap<KT>(G), gbest);
@@ -502,7 +560,8 @@ cudaError_t prepare_tile_kernels(int max_smem)
 {
     const void *fns[] = {(const void *)k_assoc<4>,   (const void *)k_assoc<2>,
                          (const void *)k_assoc<1>,   (const void *)k_assoc32<4>,
-                         (const void *)k_assoc32<2>, (const void *)k_assoc32<1>};
+                         (const void *)k_assoc32<2>, (const void *)k_assoc32<1>,
+                         (const void *)k_cand_hist};
     const cudaError_t e = allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
     return e == cudaSuccess ? prepare_vote_kernels_t<false>(max_smem) : e;
 }
@@ -590,13 +649,12 @@ cudaError_t launch_cand_lists(const DevGeom &G, int kt, const ht_peak *peaks, co
     const int nct = G.n_phi0 / kt, ntiles = assoc32_ntiles(G, kt);
     cudaError_t e = cudaMemsetAsync(tcnt, 0, (size_t)ntiles * 4, st);
     if (e != cudaSuccess) return e;
-    const int nb = min(4096, (cap + 255) / 256 > 0 ? (cap + 255) / 256 : 1);
-    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, kt, nct, tcnt,
-                                     nullptr, nullptr);
+    cand_tiles_pass(peaks, d_count, cap, G.n_rho, G.n_phi0, kt, nct, ntiles, tcnt, nullptr,
+                    nullptr, st);
     e = scan_exclusive(tcnt, toff, tcur, ntiles, nullptr, nullptr, tmp, st);
     if (e != cudaSuccess) return e;
-    k_cand_tiles<<<nb, 256, 0, st>>>(peaks, d_count, cap, G.n_rho, G.n_phi0, kt, nct, nullptr,
-                                     tcur, tlist);
+    cand_tiles_pass(peaks, d_count, cap, G.n_rho, G.n_phi0, kt, nct, ntiles, nullptr, tcur, tlist,
+                    st);
     return cudaGetLastError();
 }
 
