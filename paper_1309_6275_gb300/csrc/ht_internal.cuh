@@ -192,18 +192,18 @@ __device__ __forceinline__ Item make_item(const DevGeom &G, float s, float c, fl
 // of the hit's azimuth (half the turning angle along the chord from the
 // perigee, plus the angle the chord makes with the hit's radius), and c > 0
 // bounds it by pi/2.  A 1e-3 rad margin covers float32 rounding.
-__device__ __forceinline__ float hit_window(const DevGeom &G, float r)
+// Phase 1 tests it as a bound on c = r cos(phi0 - phi_hit): with
+// A = asin(a), B = asin(b) the two terms above, cos(A + B) = sqrt((1 - a^2)(1 - b^2))
+// - a b, and cos(w + 1e-3) >= cos(w) - 1e-3, so c < r (cos(A + B) - 1e-3)
+// implies the column is outside the window (a superset of what it keeps;
+// when A + B passes pi/2 the bound is negative and the c > 0 test rules).
+// No trigonometric call per hit.
+__device__ __forceinline__ float hit_cos_window(const DevGeom &G, float r)
 {
-    const float a = asinf(fminf(1.0f, G.rho_max_f * (r + G.dmax_f) * 0.5f)) +
-                    asinf(fminf(1.0f, G.dmax_f / fmaxf(r, 1e-30f)));
-    return fminf(a, (float)kHalfPi) + 1e-3f;
-}
-
-__device__ __forceinline__ float wrap_pi(float d)
-{
-    if (d > (float)kPi) d -= 2.0f * (float)kPi;
-    if (d < -(float)kPi) d += 2.0f * (float)kPi;
-    return d;
+    const float a = fminf(1.0f, G.rho_max_f * (r + G.dmax_f) * 0.5f);
+    const float b = fminf(1.0f, G.dmax_f / fmaxf(r, 1e-30f));
+    const float cw = sqrtf(fmaxf(fmaf(-a, a, 1.0f) * fmaf(-b, b, 1.0f), 0.0f)) - a * b;
+    return r * (cw - 1e-3f);
 }
 
 // Curvature range reached by circles through a hit (s, c) with perigee d0 in

@@ -46,7 +46,7 @@ struct TileCtx {
     int i0, k0, irow;
     bool row_ok, has_b;
     float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB;
-    float sk[KT], ck[KT], pk[KT];
+    float sk[KT], ck[KT];
 
     __device__ __forceinline__ void init(const DevGeom &G, int lane, int tx, int ty)
     {
@@ -69,7 +69,6 @@ struct TileCtx {
         for (int kl = 0; kl < KT; ++kl) {
             sk[kl] = G.sn32[k0 + kl];
             ck[kl] = G.cs32[k0 + kl];
-            pk[kl] = G.phi32[k0 + kl];
         }
     }
 };
@@ -133,15 +132,13 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
         const float xh = x[h], yh = y[h];
         r2 = fmaf(xh, xh, yh * yh);
         R1 = fabsf(xh) + fabsf(yh);
-        const float win = hit_window(G, sqrtf(r2));
-        const float phh = atan2f(yh, xh);
+        const float cmin = hit_cos_window(G, sqrtf(r2));
         const float Ec = (kSafe * 3.0f * kEps) * R1;
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
-            if (fabsf(wrap_pi(T.pk[kl] - phh)) > win) continue;
-            const float s = fmaf(xh, T.sk[kl], -(yh * T.ck[kl]));
             const float c = fmaf(xh, T.ck[kl], yh * T.sk[kl]);
-            if (c < -Ec) continue;
+            if (c < cmin || c < -Ec) continue;
+            const float s = fmaf(xh, T.sk[kl], -(yh * T.ck[kl]));
             int f = 0;
             if (c <= Ec) {
                 f |= kMetaUnsure;
