@@ -6,7 +6,8 @@ parameters (forward simulation) and holds none of the Hough-transform
 arithmetic (no voting, binning, peak finding or association).
 """
 from .configs import CONFIGS, KAPPA, B_FIELD, LAYER_R, geometry_of
-from .events import Event, make_event, helix_hits, make_stream
+from .events import Event, make_event, make_jet_event, perigee_of, generate, helix_hits, make_stream
 
 __all__ = ["CONFIGS", "KAPPA", "B_FIELD", "LAYER_R", "geometry_of",
-           "Event", "make_event", "helix_hits", "make_stream"]
+           "Event", "make_event", "make_jet_event", "perigee_of", "generate", "helix_hits",
+           "make_stream"]

@@ -66,6 +66,29 @@ CONFIGS = {
                  d0_disp=20.0, pt_kind="trunc_exp", pt_min=1.0, pt_scale=1.0,
                  pt_max=20.0, noise_frac=0.15),
         events=2000, seed0=0),
+    # Displaced jets (the scenario of Figs. 6 and 8-9): 4 jets of 10 tracks
+    # from vertices at 5-25 cm, dispersion 15-60 degrees, jet tracks
+    # pT = 5 GeV + exponential(10 GeV) truncated at 50 GeV, no prompt tracks,
+    # 5% noise; the 100-event case's track geometry.  Vertex space: 16 radius
+    # bins of 2 cm x 64 azimuth bins, T2 = 5, candidates with >= 9 votes,
+    # beam pipe 3.0 cm.
+    "jets4_256": dict(
+        geom=_geom(256, 128, 512, pt_min=1.0, d0_half=20.0, count_bits=16),
+        gen=dict(kind="jets", n_jets=4, tracks_per_jet=10, r_vertex=(5.0, 25.0),
+                 dispersion_deg=(15.0, 60.0), jet_pt_min=5.0, jet_pt_scale=10.0,
+                 jet_pt_max=50.0, n_prompt=0, pt_kind="trunc_exp", pt_min=1.0,
+                 pt_scale=1.0, pt_max=20.0, noise_frac=0.05),
+        vertex=dict(n_r=16, n_theta=64, r_max=32.0, threshold=5, min_count=9, r_keep=3.0),
+        events=100, seed0=0),
+    # The same with 2960 prompt tracks: 3000 tracks in all (Fig. 10's event).
+    "jets3000_256": dict(
+        geom=_geom(256, 128, 512, pt_min=1.0, d0_half=20.0, count_bits=16),
+        gen=dict(kind="jets", n_jets=4, tracks_per_jet=10, r_vertex=(5.0, 25.0),
+                 dispersion_deg=(15.0, 60.0), jet_pt_min=5.0, jet_pt_scale=10.0,
+                 jet_pt_max=50.0, n_prompt=2960, pt_kind="trunc_exp", pt_min=1.0,
+                 pt_scale=1.0, pt_max=20.0, noise_frac=0.05),
+        vertex=dict(n_r=16, n_theta=64, r_max=32.0, threshold=5, min_count=9, r_keep=3.0),
+        events=20, seed0=0),
 }
 
 

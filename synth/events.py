@@ -41,6 +41,11 @@ class Event:
     cot: np.ndarray = field(default_factory=lambda: np.zeros(0))
     pt: np.ndarray = field(default_factory=lambda: np.zeros(0))
     n_track_hits: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    # displaced-jet truth (jet events only): jet of each track (-1 prompt),
+    # vertex radius and azimuth of each jet
+    jet: np.ndarray = field(default_factory=lambda: np.zeros(0, np.int32))
+    vr: np.ndarray = field(default_factory=lambda: np.zeros(0))
+    vtheta: np.ndarray = field(default_factory=lambda: np.zeros(0))
 
     @property
     def n_hits(self):
@@ -176,10 +181,96 @@ def make_event(gen, seed, target_hits=None):
                  n_track_hits=n_track_hits)
 
 
+def perigee_of(vx, vy, psi, rho):
+    """Perigee parameters (d0, phi0) of the circle of signed curvature rho
+    through (vx, vy) with direction psi there (rho == 0: the straight line).
+
+    The centre is C = V + n_psi / rho with n_psi = (-sin psi, cos psi); the
+    perigee is the circle's point closest to the origin, where the left
+    normal is n = sign(rho) C / |C|, so phi0 = atan2(-n_x, n_y) and
+    d0 = sign(rho) (|C| - 1/|rho|)."""
+    vx, vy, psi, rho = (np.asarray(a, np.float64) for a in (vx, vy, psi, rho))
+    straight = rho == 0.0
+    rs = np.where(straight, 1.0, rho)
+    R = 1.0 / rs
+    cx = vx - R * np.sin(psi)
+    cy = vy + R * np.cos(psi)
+    cn = np.hypot(cx, cy)
+    sg = np.sign(rs)
+    nx, ny = sg * cx / cn, sg * cy / cn
+    d0 = np.where(straight, -vx * np.sin(psi) + vy * np.cos(psi), sg * (cn - np.abs(R)))
+    phi0 = np.where(straight, psi, np.arctan2(-nx, ny))
+    return d0, phi0
+
+
+def make_jet_event(gen, seed):
+    """Displaced-jet event: n_jets jets of tracks_per_jet tracks from vertices
+    at radius uniform in r_vertex and uniform azimuth, track directions
+    uniform within half the jet's dispersion angle (uniform in
+    dispersion_deg) of the vertex's radial direction, plus n_prompt tracks
+    from the origin; hits only on layers outside the vertex; noise hits as
+    in make_event."""
+    rng = _rng(seed)
+    nj, tpj = gen["n_jets"], gen["tracks_per_jet"]
+    vr = rng.uniform(*gen["r_vertex"], nj)
+    vth = rng.uniform(-math.pi, math.pi, nj)
+    disp = np.radians(rng.uniform(*gen["dispersion_deg"], nj))
+    nt_j = nj * tpj
+    jet_of = np.repeat(np.arange(nj), tpj)
+    psi = vth[jet_of] + rng.uniform(-0.5, 0.5, nt_j) * disp[jet_of]
+    q = np.where(rng.random(nt_j) < 0.5, -1.0, 1.0)
+    u = rng.random(nt_j)
+    lo, sc, hi = gen["jet_pt_min"], gen["jet_pt_scale"], gen["jet_pt_max"]
+    pt_j = lo - sc * np.log1p(-u * (1.0 - math.exp(-(hi - lo) / sc)))
+    rho_j = -q * KAPPA * B_FIELD / pt_j
+    vx, vy = vr[jet_of] * np.cos(vth[jet_of]), vr[jet_of] * np.sin(vth[jet_of])
+    d0_j, phi0_j = perigee_of(vx, vy, psi, rho_j)
+    cot_j = np.sinh(rng.uniform(-ETA_MAX, ETA_MAX, nt_j))
+    z0_j = np.repeat(rng.normal(0.0, Z0_SIGMA, nj), tpj)
+    npr = gen.get("n_prompt", 0)
+    rho_p, phi0_p, cot_p, z0_p, pt_p = _draw_tracks(rng, gen, npr)
+    rho = np.concatenate([rho_j, rho_p])
+    d0 = np.concatenate([d0_j, np.zeros(npr)])
+    phi0 = np.concatenate([phi0_j, phi0_p])
+    cot = np.concatenate([cot_j, cot_p])
+    z0 = np.concatenate([z0_j, z0_p])
+    pt = np.concatenate([pt_j, pt_p])
+    jet = np.concatenate([jet_of, np.full(npr, -1)]).astype(np.int32)
+    hx, hy, hz, lay, tr = _tracks_to_hits(rng, rho, d0, phi0, z0, cot)
+    # a jet track starts at its vertex: drop the layers inside it
+    rv_tr = np.where(jet >= 0, vr[np.maximum(jet, 0)], 0.0)
+    keep = np.asarray(LAYER_R)[lay] > rv_tr[tr]
+    hx, hy, hz, lay, tr = hx[keep], hy[keep], hz[keep], lay[keep], tr[keep]
+    n_track_hits = np.bincount(tr, minlength=rho.shape[0]).astype(np.int32)
+    nf = gen["noise_frac"]
+    nn = int(round(nf * hx.shape[0]))
+    nl = rng.integers(0, len(LAYER_R), nn)
+    rl = np.asarray(LAYER_R)[nl]
+    nphi = rng.uniform(-math.pi, math.pi, nn)
+    nz = rng.uniform(-1.0, 1.0, nn) * rl * math.sinh(ETA_MAX)
+    X = np.concatenate([hx, rl * np.cos(nphi)])
+    Y = np.concatenate([hy, rl * np.sin(nphi)])
+    Z = np.concatenate([hz, nz])
+    LAY = np.concatenate([lay, nl]).astype(np.int8)
+    TR = np.concatenate([tr, np.full(nn, -1)]).astype(np.int32)
+    perm = rng.permutation(X.shape[0])
+    return Event(x=X[perm].astype(np.float32), y=Y[perm].astype(np.float32),
+                 z=Z[perm].astype(np.float32), layer=LAY[perm], track=TR[perm],
+                 rho=rho, d0=d0, phi0=phi0, z0=z0, cot=cot, pt=pt,
+                 n_track_hits=n_track_hits, jet=jet, vr=vr, vtheta=vth)
+
+
 def make_stream(name, n_events=None, seed0=None):
     """Yield the events of a named workload (seed = seed0 + event index)."""
     cfg = CONFIGS[name]
     n_events = cfg["events"] if n_events is None else n_events
     seed0 = cfg["seed0"] if seed0 is None else seed0
     for e in range(n_events):
-        yield make_event(cfg["gen"], seed0 + e)
+        yield generate(cfg["gen"], seed0 + e)
+
+
+def generate(gen, seed):
+    """One event of a generator mix (jet mixes go to make_jet_event)."""
+    if gen.get("kind") == "jets":
+        return make_jet_event(gen, seed)
+    return make_event(gen, seed)
