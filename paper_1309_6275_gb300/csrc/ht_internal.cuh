@@ -198,10 +198,14 @@ __device__ __forceinline__ Item make_item(const DevGeom &G, float s, float c, fl
 // implies the column is outside the window (a superset of what it keeps;
 // when A + B passes pi/2 the bound is negative and the c > 0 test rules).
 // No trigonometric call per hit.
-__device__ __forceinline__ float hit_cos_window(const DevGeom &G, float r)
+// r and 1/r come from one approximate reciprocal square root of r^2 (a few
+// units of 2^-23 off, far inside the 1e-3 margin).
+__device__ __forceinline__ float hit_cos_window(const DevGeom &G, float r2)
 {
+    const float ir = rsqrt_approx(fmaxf(r2, 1e-30f));
+    const float r = r2 * ir;
     const float a = fminf(1.0f, G.rho_max_f * (r + G.dmax_f) * 0.5f);
-    const float b = fminf(1.0f, G.dmax_f / fmaxf(r, 1e-30f));
+    const float b = fminf(1.0f, G.dmax_f * ir);
     const float cw = sqrtf(fmaxf(fmaf(-a, a, 1.0f) * fmaf(-b, b, 1.0f), 0.0f)) - a * b;
     return r * (cw - 1e-3f);
 }

@@ -132,7 +132,7 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
         const float xh = x[h], yh = y[h];
         r2 = fmaf(xh, xh, yh * yh);
         R1 = fabsf(xh) + fabsf(yh);
-        const float cmin = hit_cos_window(G, sqrtf(r2));
+        const float cmin = hit_cos_window(G, r2);
         const float Ec = (kSafe * 3.0f * kEps) * R1;
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
