@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--no-single", action="store_true")
     p.add_argument("--batch", type=int, default=25, help="events per ht_batch_run")
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--no-vertex", action="store_true")
     p.add_argument("--tau", type=float, default=0.02, help="proposal region threshold")
     p.add_argument("--grow", type=int, default=1, help="proposal region growth (0 or 1)")
     return p.parse_args()
@@ -175,7 +176,7 @@ def run_reference(args):
 # capture (profiles/k_assoc32_batch_event100_b4.md), valid only while the
 # kernel sources hash to the value recorded with it.
 PROFILED_TRAFFIC = {
-    "k_assoc32_batch": {"sha": "fe6ca59689f98200", "bytes_per_event": 50.727424e6 / 4},
+    "k_assoc32_batch": {"sha": "1922396b5cb82b99", "bytes_per_event": 50.127872e6 / 4},
 }
 KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_tiles.cu",
                   "paper_1309_6275_gb300/csrc/tiles.cuh",
@@ -283,6 +284,62 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
             "path": "ht_batch_run_learned (proposal MLP + masked vote/peaks in one graph)",
             "weights": os.path.relpath(path, ROOT),
             "trained_on": f"{meta.get('n_events')} {meta.get('workload')} events"}
+
+
+def vertex_leg(args):
+    """Displaced-jet finding on the 4-jet workload (100 events of ~400 hits):
+    the batched first transform, then the second transform over its
+    candidates.  Events/s of the pair, the second transform's share of the
+    device time (the paper quotes about +30% for its version), vertex
+    efficiency and fakes per event."""
+    import torch
+    from paper_1309_6275_gb300 import displaced
+    name = "jets4_256"
+    cfg = synth.CONFIGS[name]
+    g, vd = dict(cfg["geom"]), cfg["vertex"]
+    evs = [synth.generate(cfg["gen"], cfg["seed0"] + e) for e in range(cfg["events"])]
+    B = 25
+    batches = [evs[i:i + B] for i in range(0, len(evs), B)]
+    dev_in = []
+    for b in batches:
+        off = np.zeros(len(b) + 1, np.int32)
+        off[1:] = np.cumsum([ev.n_hits for ev in b])
+        dev_in.append((off, [torch.from_numpy(np.concatenate([getattr(ev, k) for ev in b])).cuda()
+                             for k in "xyz"]))
+    pipe = displaced.DisplacedJetPipeline(g, vd, B, max(int(o[-1]) for o, _ in dev_in))
+    for off, (x, y, z) in dev_in:
+        pipe.run(x, y, z, off)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    t1 = t2 = 0.0
+    steps = max(1, args.steps)
+    for _ in range(steps):
+        for off, (x, y, z) in dev_in:
+            ev3 = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+            ev3[0].record(stream)
+            pipe.B.run(x, y, z, off)
+            ev3[1].record(stream)
+            pipe.V.run(pipe.B.peaks, pipe.B.counts, pipe.cap, len(off) - 1)
+            ev3[2].record(stream)
+            ev3[2].synchronize()
+            t1 += ev3[0].elapsed_time(ev3[1]) / 1e3
+            t2 += ev3[1].elapsed_time(ev3[2]) / 1e3
+    jets = found = fakes = 0
+    for (off, (x, y, z)), b in zip(dev_in, batches):
+        pipe.run(x, y, z, off)
+        torch.cuda.synchronize()
+        for e, ev in enumerate(b):
+            nj, nf, nk = displaced.match(vd, ev, pipe.kept(e))
+            jets += nj; found += nf; fakes += nk
+    pipe.close()
+    return {"workload": name, "events": len(evs), "value": len(evs) * steps / (t1 + t2),
+            "unit": "events/s", "first_transform_ms_per_event": 1e3 * t1 / (steps * len(evs)),
+            "second_transform_ms_per_event": 1e3 * t2 / (steps * len(evs)),
+            "second_transform_share": t2 / (t1 + t2),
+            "vertex_efficiency": found / max(jets, 1), "fakes_per_event": fakes / len(evs),
+            "vertex_space": f"{vd['n_r']} x {vd['n_theta']}, T2={vd['threshold']}, "
+                            f"min_count={vd['min_count']}, beam pipe {vd['r_keep']} cm",
+            "path": "ht_batch_run then ht_vertex_vote + ht_vertex_find, 25 events per batch"}
 
 
 def make_batches(cfg, n_ev, world, rank, B):
@@ -462,6 +519,10 @@ def run_ours(args):
     if not args.no_learned:
         learned_res = learned_leg(args, ht, bt, batches, dev_in, g, flush)
 
+    vertex_res = None
+    if not args.no_vertex:
+        vertex_res = vertex_leg(args)
+
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     peak_ops = alu_peak_ops(props, peaks)
@@ -516,6 +577,8 @@ def run_ours(args):
         line["single_event_api_events_per_s"] = single
     if learned_res:
         line["learned"] = learned_res
+    if vertex_res:
+        line["displaced_jets"] = vertex_res
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:

@@ -294,6 +294,64 @@ ht_status ht_mlp_adam(float *params, float *m, float *v, const float *grad, int3
                       ht_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Second transform: displaced vertices (Section 6, Fig. 6; Section 7).
+ * Tracks from one vertex lie on a sinusoid in track-parameter space; a
+ * second Hough transform over the candidates finds those sinusoids and the
+ * same peak finder locates them; features inside the beam pipe are dropped.
+ * Readings: a candidate (i, j, k) is the straight line of its cell centre,
+ * d0 = (j - n_d0/2) delta at phi0_k (the curvature is not used); a vertex
+ * r (cos theta, sin theta) lies on it iff d0 = r sin(theta - phi0).  Vertex
+ * space: theta_q = (2q + 1 - n_theta) pi / n_theta (wrapping) x radius bins
+ * of width dr = r_max / n_r from 0.  In every theta column a candidate with
+ * count >= min_count votes once, at r = d0 / (sin theta_q cos phi0_k -
+ * cos theta_q sin phi0_k), in bin floor(r / dr) if 0 <= r / dr < n_r
+ * (float64 definition, products then difference then two divisions; a zero
+ * denominator gives no vote).  Peaks: the rule of ht_find_peaks on the
+ * 1 x n_r x n_theta array (radius does not wrap, theta does), threshold
+ * T2 = threshold.  Beam-pipe filter: peaks whose radius-bin centre
+ * (j + 1/2) dr is below r_keep come first in peak order; d_first says
+ * where the others start.
+ * ------------------------------------------------------------------------ */
+typedef struct ht_vertex_desc {
+    int32_t n_r, n_theta;   /* n_r in [1, 4096]; n_theta a multiple of 32 */
+    int32_t threshold;      /* T2: tracks through a vertex cell, >= 1 */
+    int32_t min_count;      /* candidates with fewer votes do not vote */
+    double r_max;           /* radius axis [0, r_max), cm */
+    double r_keep;          /* beam-pipe radius, cm (Section 7: 3.0) */
+} ht_vertex_desc;
+
+typedef struct ht_vertex ht_vertex;   /* opaque; uses g's phi0 and d0 axes */
+
+/* Create on the current device for candidates of geometry g (which must
+ * outlive the handle).  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_vertex_create(const ht_geometry *g, const ht_vertex_desc *desc, ht_vertex **out);
+ht_status ht_vertex_destroy(ht_vertex *v);
+
+/* Bytes of one event's vertex accumulator: n_r * n_theta int32. */
+size_t ht_vertex_accumulator_bytes(const ht_vertex *v);
+
+/* Vote n_events events at once: event e's candidates are
+ * cands[e * cap .. e * cap + min(d_count[e], cap)) (ht_find_peaks or
+ * ht_batch_run output); its accumulator is acc + e * n_r * n_theta (device,
+ * int32, [radius bin][theta], every cell written).  stats: NULL or
+ * 2 * n_events uint64 (votes, float64 redos), zeroed first.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_vertex_vote(const ht_vertex *v, const ht_peak *cands, const int32_t *d_count,
+                         int32_t cap, int32_t n_events, int32_t *acc, uint64_t *stats,
+                         ht_stream stream);
+
+/* Peaks of each event's vertex accumulator into out + e * cap ({0, radius
+ * bin, theta bin, count}, increasing index, first min(total, cap)), totals
+ * in d_count[e] and the index of the first peak outside r_keep in
+ * d_first[e].  acc 16-byte aligned; workspace: ht_vertex_workspace_size(v)
+ * bytes, 256-byte aligned, reused by the events in stream order.
+ * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+size_t ht_vertex_workspace_size(const ht_vertex *v);
+ht_status ht_vertex_find(const ht_vertex *v, const int32_t *acc, int32_t n_events,
+                         ht_peak *out, int32_t cap, int32_t *d_count, int32_t *d_first,
+                         void *workspace, size_t workspace_bytes, ht_stream stream);
+
+/* ------------------------------------------------------------------------
  * Batched runtime: many events, uneven hit counts, one CUDA graph per batch.
  * The paper processes one event at a time (Fig. 5); a batch runs the same
  * four steps with identical results per event, but the vote and association

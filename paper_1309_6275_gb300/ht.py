@@ -41,6 +41,12 @@ class _Desc(ctypes.Structure):
                 ("z0_max", ctypes.c_double), ("cot_max", ctypes.c_double)]
 
 
+class _VertexDesc(ctypes.Structure):
+    _fields_ = [("n_r", ctypes.c_int32), ("n_theta", ctypes.c_int32),
+                ("threshold", ctypes.c_int32), ("min_count", ctypes.c_int32),
+                ("r_max", ctypes.c_double), ("r_keep", ctypes.c_double)]
+
+
 class _Proposal(ctypes.Structure):
     _fields_ = [("params_bf16", ctypes.c_void_p), ("layer", ctypes.c_void_p),
                 ("tau", ctypes.c_float), ("fmax", ctypes.c_float),
@@ -85,6 +91,12 @@ SIGNATURES = [
     ("ht_batch_run_masked", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     ("ht_batch_run_learned", _I32, [_P, _P, _P, _P, _P, _I32, ctypes.POINTER(_Proposal), _P,
                                     _P, _P, _P, _P, _P, _P]),
+    ("ht_vertex_create", _I32, [_P, ctypes.POINTER(_VertexDesc), ctypes.POINTER(_P)]),
+    ("ht_vertex_destroy", _I32, [_P]),
+    ("ht_vertex_accumulator_bytes", _SZ, [_P]),
+    ("ht_vertex_workspace_size", _SZ, [_P]),
+    ("ht_vertex_vote", _I32, [_P, _P, _P, _I32, _I32, _P, _P, _P]),
+    ("ht_vertex_find", _I32, [_P, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
 ]
 
 
@@ -263,6 +275,58 @@ def ht_probe_shared_atomic_rate(iters=4096, stream=None):
     _check(lib().ht_probe_shared_atomic_rate(iters, ctypes.byref(v), _stream(stream)),
            "ht_probe_shared_atomic_rate")
     return v.value
+
+
+class Vertex:
+    """Second transform (ht_vertex_*) for candidates of geometry G; vd is a
+    dict with n_r, n_theta, threshold, r_max, r_keep and optional min_count."""
+
+    def __init__(self, G, vd, max_events, cap, device="cuda"):
+        self.G, self.vd, self.cap = G, dict(vd), cap
+        d = _VertexDesc(vd["n_r"], vd["n_theta"], vd["threshold"], vd.get("min_count", 0),
+                        vd["r_max"], vd["r_keep"])
+        h = ctypes.c_void_p()
+        _check(lib().ht_vertex_create(G.handle, ctypes.byref(d), ctypes.byref(h)),
+               "ht_vertex_create")
+        self.handle = h
+        dev = torch.device(device)
+        self.acc = torch.empty((max_events, vd["n_r"], vd["n_theta"]), dtype=torch.int32,
+                               device=dev)
+        self.peaks = torch.empty((max_events * cap, 4), dtype=torch.int32, device=dev)
+        self.counts = torch.zeros(max_events, dtype=torch.int32, device=dev)
+        self.first = torch.zeros(max_events, dtype=torch.int32, device=dev)
+        self.stats = torch.zeros(2 * max_events, dtype=torch.int64, device=dev)
+        self.ws = torch.empty(max(lib().ht_vertex_workspace_size(h), 256), dtype=torch.uint8,
+                              device=dev)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and self.handle.value:
+            lib().ht_vertex_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, cands, d_count, cand_cap, n_events, stream=None):
+        """Vote and find for n_events events of candidates (device peaks laid
+        out e * cand_cap, counts d_count)."""
+        s = _stream(stream)
+        _check(lib().ht_vertex_vote(self.handle, _ptr(cands), _ptr(d_count), cand_cap, n_events,
+                                    _ptr(self.acc), _ptr(self.stats), s), "ht_vertex_vote")
+        _check(lib().ht_vertex_find(self.handle, _ptr(self.acc), n_events, _ptr(self.peaks),
+                                    self.cap, _ptr(self.counts), _ptr(self.first),
+                                    _ptr(self.ws), self.ws.numel(), s), "ht_vertex_find")
+
+    def event_results(self, e):
+        cnt = int(self.counts[e].item())
+        k = min(cnt, self.cap)
+        return dict(acc=self.acc[e].cpu().numpy(), count=cnt,
+                    peaks=self.peaks[e * self.cap:e * self.cap + k].cpu().numpy(),
+                    first=int(self.first[e].item()), votes=int(self.stats[2 * e].item()),
+                    redo=int(self.stats[2 * e + 1].item()))
 
 
 class EventPipeline:
