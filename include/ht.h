@@ -358,7 +358,7 @@ ht_status ht_vertex_find(const ht_vertex *v, const int32_t *acc, int32_t n_event
  * run as persistent kernels over a device queue of (event, tile) items,
  * largest events first, and the whole batch is captured once into a CUDA
  * graph and replayed for every later batch with the same number of events.
- * Requires count_bits 16.
+ * Requires count_bits 16 and an even n_d0 (two 16-bit counters per word).
  * ------------------------------------------------------------------------ */
 typedef struct ht_batch ht_batch;   /* opaque */
 

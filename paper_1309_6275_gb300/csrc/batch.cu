@@ -278,6 +278,8 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     if (max_events < 1 || max_events > 4096 || max_hits < 1 || cap < 1 ||
         (int64_t)max_events * cap > (int64_t)1 << 30)
         return ht::set_error(HT_ERR_ARG, "ht_batch_create: sizes out of range");
+    if (g->desc.n_d0 % 2 != 0)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_create: batches need an even n_d0");
     ht_batch *b = new (std::nothrow) ht_batch();
     if (!b) return ht::set_error(HT_ERR_ARG, "ht_batch_create: out of host memory");
     b->g = g;
