@@ -137,7 +137,7 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
             }
     }
     __syncthreads();
-    if (!WRITE) {
+    if constexpr (!WRITE) {
         for (int jl = threadIdx.x; jl < j1 - j0; jl += kPkThreads) {
             int cnt = 0;
 #pragma unroll

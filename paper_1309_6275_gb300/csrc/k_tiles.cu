@@ -412,6 +412,7 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;
+#pragma unroll 2
         for (int t = warp; t < nq; t += nwarps) {
             const int m = W.meta[t];
             uint32_t key = 0u;

@@ -303,6 +303,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;   // last read before the previous barrier
         if (T.row_ok) {
+#pragma unroll 2
             for (int t = warp; t < nq; t += nwarps) {
                 const int m = W.meta[t];
                 uint32_t *col = cnt + (m & kMetaCol) * NW * 32 + lane;
