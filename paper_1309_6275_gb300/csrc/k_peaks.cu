@@ -144,15 +144,15 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
             for (int w2 = 0; w2 < kPkThreads / 32; ++w2) cnt += __popc(bal_s[jl][w2]);
             segcnt[(i * ND + j0 + jl) * nkb + kb] = cnt;
         }
-        return;
-    }
-    while (mine) {
-        const int jl = __ffs(mine) - 1;
-        mine &= mine - 1u;
-        const int seg = (i * ND + j0 + jl) * nkb + kb;
-        int pos = segoff[seg] + __popc(bal_s[jl][warp] & ((1u << lane) - 1u));
-        for (int w2 = 0; w2 < warp; ++w2) pos += __popc(bal_s[jl][w2]);
-        if (pos < cap) out[pos] = ht_peak{i, j0 + jl, k, S(1, jl + 1)[1]};
+    } else {
+        while (mine) {
+            const int jl = __ffs(mine) - 1;
+            mine &= mine - 1u;
+            const int seg = (i * ND + j0 + jl) * nkb + kb;
+            int pos = segoff[seg] + __popc(bal_s[jl][warp] & ((1u << lane) - 1u));
+            for (int w2 = 0; w2 < warp; ++w2) pos += __popc(bal_s[jl][w2]);
+            if (pos < cap) out[pos] = ht_peak{i, j0 + jl, k, S(1, jl + 1)[1]};
+        }
     }
 }
 
