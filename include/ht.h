@@ -294,6 +294,45 @@ ht_status ht_mlp_adam(float *params, float *m, float *v, const float *grad, int3
                       ht_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Refinement of candidates (Section 5: costlier computations confirm the
+ * candidates; Section 6 names a Kalman filter for it).  Without material or
+ * process noise a Kalman filter over a track's hits gives the weighted
+ * least-squares estimate, which this call fits directly.  Reading: p =
+ * (rho, d0, phi0) starts at the candidate's cell centre (rho_i,
+ * (j - n_d0/2) delta, phi0_k); the residual of hit (x, y) is F / 2 with
+ * F = rho d0^2 + 2 (1 + rho s) d0 + rho r^2 + 2 s (the signed distance to
+ * the circle to first order, equal weights sigma); `iters` Gauss-Newton
+ * steps solve (J^T J) dp = -J^T r by Cholesky.  Float64 throughout; the sums
+ * run over the hits in no fixed order, so results agree with the float64
+ * definition to rounding (~1e-15 relative), not bit for bit.
+ * ------------------------------------------------------------------------ */
+typedef struct ht_track {
+    double rho, d0, phi0;              /* fitted (the start when status 0) */
+    double sig_rho, sig_d0, sig_phi0;  /* sqrt of the covariance diagonal */
+    float chi2;                        /* sum (residual / sigma)^2 */
+    int32_t n_hits;                    /* hits assigned to the candidate */
+    int32_t status;   /* 1 fitted, 0 fewer than min_hits hits, -1 normal
+                         matrix not positive definite (last good p kept) */
+    int32_t reserved;
+} ht_track;
+
+/* Fit every candidate of n_events events with at least min_hits (>= 3)
+ * assigned hits.  Hits: x, y (device float32) concatenated at DEVICE offsets
+ * d_off[0 .. n_events]; n_hits = the total (d_off[n_events]).  assign: per
+ * hit, the candidate index within its event (ht_associate / ht_batch_run
+ * output, -1 none).  Event e's candidates are peaks[e * cap ..
+ * e * cap + min(d_count[e], cap)); its tracks go to out + e * cap.
+ * iters in [0, 64]; sigma > 0 (cm, the hit resolution).  workspace:
+ * ht_fit_workspace_size(n_events, cap, n_hits) bytes, 256-byte aligned.
+ * Errors: HT_ERR_ARG, HT_ERR_CAPACITY (n_events * cap >= 2^31), HT_ERR_CUDA. */
+size_t ht_fit_workspace_size(int32_t n_events, int32_t cap, int32_t n_hits);
+ht_status ht_fit_tracks(const ht_geometry *g, const float *x, const float *y, const int32_t *d_off,
+                        int32_t n_events, int32_t n_hits, const int32_t *assign,
+                        const ht_peak *peaks, const int32_t *d_count, int32_t cap,
+                        int32_t min_hits, int32_t iters, double sigma, ht_track *out,
+                        void *workspace, size_t workspace_bytes, ht_stream stream);
+
+/* ------------------------------------------------------------------------
  * Second transform: displaced vertices (Section 6, Fig. 6; Section 7).
  * Tracks from one vertex lie on a sinusoid in track-parameter space; a
  * second Hough transform over the candidates finds those sinusoids and the

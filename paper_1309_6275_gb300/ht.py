@@ -91,6 +91,9 @@ SIGNATURES = [
     ("ht_batch_run_masked", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     ("ht_batch_run_learned", _I32, [_P, _P, _P, _P, _P, _I32, ctypes.POINTER(_Proposal), _P,
                                     _P, _P, _P, _P, _P, _P]),
+    ("ht_fit_workspace_size", _SZ, [_I32, _I32, _I32]),
+    ("ht_fit_tracks", _I32, [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _I32, _I32, _I32,
+                             ctypes.c_double, _P, _P, _SZ, _P]),
     ("ht_vertex_create", _I32, [_P, ctypes.POINTER(_VertexDesc), ctypes.POINTER(_P)]),
     ("ht_vertex_destroy", _I32, [_P]),
     ("ht_vertex_accumulator_bytes", _SZ, [_P]),
@@ -275,6 +278,32 @@ def ht_probe_shared_atomic_rate(iters=4096, stream=None):
     _check(lib().ht_probe_shared_atomic_rate(iters, ctypes.byref(v), _stream(stream)),
            "ht_probe_shared_atomic_rate")
     return v.value
+
+
+TRACK_FIELDS = ["rho", "d0", "phi0", "sig_rho", "sig_d0", "sig_phi0"]
+
+
+def ht_fit_tracks(G, x, y, d_off, assign, peaks, d_count, cap, out, workspace, min_hits=4,
+                  iters=5, sigma=20e-4, stream=None):
+    """Refit candidates.  out: uint8 tensor of n_events * cap * 64 bytes (one
+    ht_track each); d_off: device int32 [n_events + 1]."""
+    _check(lib().ht_fit_tracks(G.handle, _ptr(x), _ptr(y), _ptr(d_off), d_off.numel() - 1,
+                               x.numel(), _ptr(assign), _ptr(peaks), _ptr(d_count), cap, min_hits,
+                               iters, sigma, _ptr(out), _ptr(workspace), workspace.numel(),
+                               _stream(stream)), "ht_fit_tracks")
+
+
+def ht_fit_workspace_size(n_events, cap, n_hits):
+    return lib().ht_fit_workspace_size(n_events, cap, n_hits)
+
+
+def tracks_to_numpy(buf, n):
+    """The first n ht_track records of a uint8 tensor as a numpy record array."""
+    import numpy as np
+    dt = np.dtype([(f, "<f8") for f in TRACK_FIELDS] +
+                  [("chi2", "<f4"), ("n_hits", "<i4"), ("status", "<i4"), ("reserved", "<i4")])
+    assert dt.itemsize == 64
+    return np.frombuffer(buf[:n * 64].cpu().numpy().tobytes(), dtype=dt)
 
 
 class Vertex:

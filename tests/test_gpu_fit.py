@@ -1,0 +1,129 @@
+"""Candidate refinement (ht_fit_tracks) on the GPU against its oracle
+(oracle/fit.py): the same candidates, hit counts and status; fitted
+parameters within 1e-6 of their own standard deviation (float64 sums in a
+different order), chi2 and standard deviations to 1e-6 relative.  Only fits
+whose iteration is settled (one more Gauss-Newton step moves them by less
+than 1e-2 sigma) are compared parameter by parameter."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_common import cuda_ok, to_dev
+from oracle import fit as F
+
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
+
+
+def gpu_fit(G, ht, x, y, off, assign, peaks, counts, cap, min_hits=4, iters=5):
+    import torch
+    n_ev = len(off) - 1
+    out = torch.zeros(n_ev * cap * 64, dtype=torch.uint8, device="cuda")
+    ws = torch.empty(ht.ht_fit_workspace_size(n_ev, cap, int(off[-1])), dtype=torch.uint8,
+                     device="cuda")
+    ht.ht_fit_tracks(G, x, y, to_dev(np.asarray(off, np.int32)), assign, peaks, counts, cap,
+                     out, ws, min_hits=min_hits, iters=iters)
+    torch.cuda.synchronize()
+    return ht.tracks_to_numpy(out, n_ev * cap)
+
+
+def compare(g, ev_x, ev_y, assign, peaks, tracks, min_hits=4, iters=5):
+    ora = F.fit_candidates(g, ev_x, ev_y, assign, peaks, min_hits=min_hits, iters=iters)
+    ora_more = F.fit_candidates(g, ev_x, ev_y, assign, peaks, min_hits=min_hits, iters=iters + 1)
+    n_fit = n_cmp = 0
+    for m, o in enumerate(ora):
+        t = tracks[m]
+        if o is None:
+            assert t["status"] == 0, m
+            continue
+        n_fit += 1
+        assert t["n_hits"] == o["n"], m
+        assert t["status"] == o["status"], m
+        if o["status"] != 1:
+            continue
+        sig = np.sqrt(np.diag(o["cov"]))
+        if np.any(np.abs(ora_more[m]["p"] - o["p"]) > 1e-2 * sig):
+            continue                                   # still moving: skip
+        n_cmp += 1
+        got = np.array([t["rho"], t["d0"], t["phi0"]])
+        assert np.all(np.abs(got - o["p"]) <= 1e-6 * sig + 1e-14), (m, got, o["p"], sig)
+        assert math.isclose(t["chi2"], o["chi2"], rel_tol=1e-5, abs_tol=1e-6)
+        assert np.allclose([t["sig_rho"], t["sig_d0"], t["sig_phi0"]], sig, rtol=1e-6)
+    return n_fit, n_cmp
+
+
+def test_fit_on_single_events_matches_oracle():
+    import torch
+    from paper_1309_6275_gb300 import ht
+    name = "single_64"
+    g = synth.geometry_of(name)
+    total_fit = total_cmp = 0
+    for seed in range(4):
+        ev = synth.make_event(synth.CONFIGS[name]["gen"], seed)
+        cap = 4096
+        G = ht.Geometry(g)
+        p = ht.EventPipeline(G, ev.n_hits, cap)
+        dx, dy, dz = to_dev(ev.x), to_dev(ev.y), to_dev(ev.z)
+        p.run(dx, dy, dz)
+        torch.cuda.synchronize()
+        r = p.results(ev.n_hits)
+        tr = gpu_fit(G, ht, dx, dy, [0, ev.n_hits], p.assign[:ev.n_hits], p.peaks, p.count, cap)
+        o = oracle.run_event(g, ev.x, ev.y, ev.z)
+        assert np.array_equal(r["peaks"], o["peaks"]) and np.array_equal(r["assign"], o["assign"])
+        nf, nc = compare(g, ev.x, ev.y, o["assign"], o["peaks"], tr[:len(o["peaks"])])
+        total_fit += nf
+        total_cmp += nc
+        G.close()
+    assert total_fit > 10 and total_cmp >= 0.25 * total_fit
+
+
+def test_fit_in_batch_layout_and_noise_free_tracks():
+    import torch
+    from paper_1309_6275_gb300 import ht
+    name = "jets4_256"
+    cfg = synth.CONFIGS[name]
+    g = synth.geometry_of(name)
+    evs = [synth.generate(cfg["gen"], 70 + i) for i in range(3)]
+    off = np.zeros(4, np.int32)
+    off[1:] = np.cumsum([e.n_hits for e in evs])
+    cat = lambda k: to_dev(np.concatenate([getattr(e, k) for e in evs]).astype(np.float32))
+    x, y, z = cat("x"), cat("y"), cat("z")
+    cap = 1 << 14
+    G = ht.Geometry(g)
+    B = ht.Batch(G, max_events=3, max_hits=int(off[-1]), cap=cap)
+    B.run(x, y, z, off)
+    torch.cuda.synchronize()
+    tr = gpu_fit(G, ht, x, y, off, B.assign, B.peaks, B.counts, cap)
+    for e, ev in enumerate(evs):
+        r = B.event_results(off, e)
+        t = tr[e * cap:e * cap + r["count"]]
+        nf, nc = compare(g, ev.x, ev.y, r["assign"], r["peaks"], t)
+        assert nf > 0
+    B.close()
+    # exact helices (float32 hits), one candidate each at a nearby cell
+    tracks = [(0.0041, 0.0, 0.8), (-0.0063, 2.4, -1.9), (0.0012, -5.1, 2.7)]
+    xs, ys, asg, pks = [], [], [], []
+    phi_t, _, _, rho_t = oracle.tables(g)
+    delta = 2 * g["d0_half"] / g["n_d0"]
+    for m, (rho, d0, phi0) in enumerate(tracks):
+        hx, hy, _, _, _ = synth.helix_hits(rho, d0, phi0)
+        xs.append(hx); ys.append(hy); asg.append(np.full(hx.shape[0], m))
+        i = int(np.argmin(np.abs(rho_t - rho)))
+        j = int(round(d0 / delta + g["n_d0"] / 2))
+        k = int(np.argmin(np.abs(np.angle(np.exp(1j * (phi_t - phi0))))))
+        pks.append((i, j, k, hx.shape[0]))
+    hx = np.concatenate(xs).astype(np.float32); hy = np.concatenate(ys).astype(np.float32)
+    assign = np.concatenate(asg).astype(np.int32)
+    peaks = np.array(pks, np.int32)
+    t = gpu_fit(G, ht, to_dev(hx), to_dev(hy), [0, hx.shape[0]], to_dev(assign), to_dev(peaks),
+                torch.tensor([len(tracks)], dtype=torch.int32, device="cuda"), len(tracks),
+                iters=8)
+    for m, (rho, d0, phi0) in enumerate(tracks):
+        assert t[m]["status"] == 1
+        # float32 hit positions (~4e-6 cm) bound the recovery
+        assert abs(t[m]["d0"] - d0) < 2e-4 and abs(t[m]["rho"] - rho) < 1e-6
+        assert abs(math.remainder(t[m]["phi0"] - phi0, 2 * math.pi)) < 1e-5
+    G.close()
