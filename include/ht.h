@@ -310,7 +310,7 @@ typedef struct ht_track {
     double rho, d0, phi0;              /* fitted (the start when status 0) */
     double sig_rho, sig_d0, sig_phi0;  /* sqrt of the covariance diagonal */
     float chi2;                        /* sum (residual / sigma)^2 */
-    int32_t n_hits;                    /* hits assigned to the candidate */
+    int32_t n_hits;                    /* hits in the last fit */
     int32_t status;   /* 1 fitted, 0 fewer than min_hits hits, -1 normal
                          matrix not positive definite (last good p kept) */
     int32_t reserved;
@@ -322,15 +322,21 @@ typedef struct ht_track {
  * hit, the candidate index within its event (ht_associate / ht_batch_run
  * output, -1 none).  Event e's candidates are peaks[e * cap ..
  * e * cap + min(d_count[e], cap)); its tracks go to out + e * cap.
- * iters in [0, 64]; sigma > 0 (cm, the hit resolution).  workspace:
- * ht_fit_workspace_size(n_events, cap, n_hits) bytes, 256-byte aligned.
- * Errors: HT_ERR_ARG, HT_ERR_CAPACITY (n_events * cap >= 2^31), HT_ERR_CUDA. */
+ * iters, iters2 in [0, 64]; sigma > 0 (cm, the hit resolution).  Hit
+ * selection: road > 0 fits only the hits within road (cm) of the cell-centre
+ * circle; cut > 0 then refits, with iters2 more steps, the hits within
+ * cut * sigma of the fitted circle (road, cut <= 0: off).  n_hits is the
+ * number of hits in the last fit; fewer than min_hits gives status 0.
+ * workspace: ht_fit_workspace_size(n_events, cap, n_hits) bytes, 256-byte
+ * aligned.  Errors: HT_ERR_ARG, HT_ERR_CAPACITY (n_events * cap >= 2^31),
+ * HT_ERR_CUDA. */
 size_t ht_fit_workspace_size(int32_t n_events, int32_t cap, int32_t n_hits);
 ht_status ht_fit_tracks(const ht_geometry *g, const float *x, const float *y, const int32_t *d_off,
                         int32_t n_events, int32_t n_hits, const int32_t *assign,
                         const ht_peak *peaks, const int32_t *d_count, int32_t cap,
-                        int32_t min_hits, int32_t iters, double sigma, ht_track *out,
-                        void *workspace, size_t workspace_bytes, ht_stream stream);
+                        int32_t min_hits, int32_t iters, double sigma, double road, double cut,
+                        int32_t iters2, ht_track *out, void *workspace, size_t workspace_bytes,
+                        ht_stream stream);
 
 /* ------------------------------------------------------------------------
  * Second transform: displaced vertices (Section 6, Fig. 6; Section 7).

@@ -22,6 +22,9 @@ what this reading fits directly:
   p += dp (a non-positive pivot stops the fit with status -1).  chi2 =
   sum r^2 / sigma^2 and the covariance sigma^2 (J^T J)^-1 at the final p.
 Only candidates with at least `min_hits` assigned hits are fitted.
+Optional hit selection (the road of a track finder, the outlier cut of a
+Kalman filter): fit only the hits within `road` cm of the cell-centre
+circle, then refit the hits within `cut` sigma of the fitted one.
 All arithmetic float64.
 """
 import math
@@ -91,10 +94,25 @@ def cell_start(g, pk, tables=None):
     return (rho[pk[0]], (pk[1] - 0.5 * g["n_d0"]) * delta, phi0[pk[2]])
 
 
-def fit_candidates(g, x, y, assign, peaks, min_hits=4, iters=5, sigma=20e-4):
-    """Per candidate m: dict(p, chi2, n, cov) or None when fewer than
-    min_hits hits are assigned to it."""
+def select(p, x, y, width):
+    """Hits whose residual at p is at most width (cm) in magnitude."""
+    r, _ = residuals(p, x, y)
+    return np.abs(r) <= width
+
+
+def fit_candidates(g, x, y, assign, peaks, min_hits=4, iters=5, sigma=20e-4, road=None,
+                   cut=None, iters2=3):
+    """Per candidate m: dict(p, chi2, n, cov, status) or None when fewer
+    than min_hits hits are assigned to it.
+
+    With road (cm): only hits within road of the cell-centre circle are
+    fitted; with cut (in sigma): after the fit, the assigned hits within
+    cut * sigma of the fitted circle are refitted with iters2 more steps
+    from the first fit.  n is the number of hits in the last fit; fewer
+    than min_hits there gives status 0 (p is the last start)."""
     assign = np.asarray(assign)
+    x = np.asarray(x, np.float64)
+    y = np.asarray(y, np.float64)
     tables = O.tables(g)
     out = []
     for m, pk in enumerate(np.asarray(peaks)):
@@ -102,7 +120,20 @@ def fit_candidates(g, x, y, assign, peaks, min_hits=4, iters=5, sigma=20e-4):
         if sel.shape[0] < min_hits:
             out.append(None)
             continue
-        p, chi2, cov, st = fit_one(cell_start(g, pk, tables), np.asarray(x, np.float64)[sel],
-                                   np.asarray(y, np.float64)[sel], iters, sigma)
-        out.append(dict(p=p, chi2=chi2, n=int(sel.shape[0]), cov=cov, status=st))
+        xs, ys = x[sel], y[sel]
+        p0 = np.array(cell_start(g, pk, tables), np.float64)
+        keep = select(p0, xs, ys, road) if road is not None else np.ones(sel.shape[0], bool)
+        if keep.sum() < min_hits:
+            out.append(dict(p=p0, chi2=np.nan, n=int(keep.sum()), cov=None, status=0))
+            continue
+        p, chi2, cov, st = fit_one(p0, xs[keep], ys[keep], iters, sigma)
+        n = int(keep.sum())
+        if cut is not None and st == 1:
+            keep = select(p, xs, ys, cut * sigma)
+            n = int(keep.sum())
+            if n < min_hits:
+                out.append(dict(p=p, chi2=np.nan, n=n, cov=None, status=0))
+                continue
+            p, chi2, cov, st = fit_one(p, xs[keep], ys[keep], iters2, sigma)
+        out.append(dict(p=p, chi2=chi2, n=n, cov=cov, status=st))
     return out

@@ -11,6 +11,9 @@
 // rho r^2 + 2 s (the signed distance to the circle to first order); `iters`
 // Gauss-Newton steps solve (J^T J) dp = -J^T r by Cholesky (a non-positive
 // pivot stops with status -1); chi2 and sigma^2 (J^T J)^-1 at the final p.
+// Optional hit selection: only hits within `road` of the cell-centre circle
+// are fitted; then the hits within `cut` sigma of the fitted circle are
+// fitted again with `iters2` steps (the outlier rejection of a track fit).
 //
 // Design (GB300): candidates' hit lists by counting sort (count, scan,
 // scatter); one warp per candidate, lanes over its hits, the normal
@@ -62,24 +65,43 @@ __device__ __forceinline__ double wsum(double v)
     return v;
 }
 
-// Normal equations of the hits list[b .. b + nh) at p: A (6 unique
-// entries), J^T r, sum r^2; every lane gets the sums.
+__device__ __forceinline__ double half_f(double rho, double d0, double s, double r2)
+{
+    return 0.5 * (rho * d0 * d0 + 2.0 * (1.0 + rho * s) * d0 + rho * r2 + 2.0 * s);
+}
+
+// A hit selection: the hits whose residual at q is at most w in magnitude
+// (w = infinity: every hit).
+struct Sel {
+    double q[3];
+    double w;
+};
+
+// Normal equations of the selected hits of list[b .. b + nh) at p: A (6
+// unique entries), J^T r, sum r^2 and their number; every lane gets them.
 __device__ __forceinline__ void normal_eq(const float *__restrict__ x,
                                           const float *__restrict__ y,
                                           const int *__restrict__ list, int b, int nh,
-                                          const double p[3], int lane, double A[6], double g[3],
-                                          double &rr)
+                                          const double p[3], const Sel &S, int lane,
+                                          double A[6], double g[3], double &rr, int &nk)
 {
-    double sn, cs;
+    double sn, cs, qs, qc;
     sincos(p[2], &sn, &cs);
+    sincos(S.q[2], &qs, &qc);
     double a[6] = {0, 0, 0, 0, 0, 0}, gg[3] = {0, 0, 0}, s2 = 0;
+    int k = 0;
     for (int t = lane; t < nh; t += 32) {
         const int h = list[b + t];
         const double xh = (double)x[h], yh = (double)y[h];
+        if (S.w < 1e300) {
+            const double sq = xh * qs - yh * qc;
+            if (!(fabs(half_f(S.q[0], S.q[1], sq, xh * xh + yh * yh)) <= S.w)) continue;
+        }
+        ++k;
         const double s = xh * sn - yh * cs, c = xh * cs + yh * sn;
         const double r2 = xh * xh + yh * yh;
         const double rho = p[0], d0 = p[1];
-        const double r = 0.5 * (rho * d0 * d0 + 2.0 * (1.0 + rho * s) * d0 + rho * r2 + 2.0 * s);
+        const double r = half_f(rho, d0, s, r2);
         const double j0 = 0.5 * (d0 * d0 + 2.0 * s * d0 + r2);
         const double j1 = rho * d0 + 1.0 + rho * s;
         const double j2 = (1.0 + rho * d0) * c;
@@ -93,6 +115,9 @@ __device__ __forceinline__ void normal_eq(const float *__restrict__ x,
 #pragma unroll
     for (int i = 0; i < 3; ++i) g[i] = wsum(gg[i]);
     rr = wsum(s2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k += __shfl_xor_sync(0xffffffffu, k, o);
+    nk = k;
 }
 
 // Cholesky of the symmetric 3 x 3 matrix {A0 A1 A2; . A3 A4; . . A5}:
@@ -114,10 +139,36 @@ __device__ __forceinline__ bool chol3(const double A[6], double L[6])
 }
 
 struct FitArgs {
-    double delta, half_nd, pi_over_np, sigma;
+    double delta, half_nd, pi_over_np, sigma, road, cut;
     const double *rho64;
-    int n_phi0, min_hits, iters;
+    int n_phi0, min_hits, iters, iters2;
 };
+
+// Gauss-Newton steps on the hits that S selects; false (and p kept) when
+// the normal matrix is not positive definite.
+__device__ __forceinline__ bool gauss_newton(const float *__restrict__ x,
+                                             const float *__restrict__ y,
+                                             const int *__restrict__ list, int b, int nh,
+                                             double p[3], const Sel &S, int iters, int lane)
+{
+    double A[6], g[3], rr, L[6];
+    int nk;
+    for (int it = 0; it < iters; ++it) {
+        normal_eq(x, y, list, b, nh, p, S, lane, A, g, rr, nk);
+        if (!chol3(A, L)) return false;               // same sums on every lane
+        // forward then backward substitution: L z = g, L^T dp = z
+        const double z0 = g[0] / L[0];
+        const double z1 = (g[1] - L[1] * z0) / L[2];
+        const double z2 = (g[2] - L[3] * z0 - L[4] * z1) / L[5];
+        const double d2 = z2 / L[5];
+        const double d1 = (z1 - L[4] * d2) / L[2];
+        const double d0 = (z0 - L[1] * d1 - L[3] * d2) / L[0];
+        p[0] -= d0;
+        p[1] -= d1;
+        p[2] -= d2;
+    }
+    return true;
+}
 
 // One warp per candidate (grid.y = event, warps stride over its candidates).
 __global__ void __launch_bounds__(256)
@@ -148,25 +199,35 @@ k_fit_tracks(FitArgs F, const float *__restrict__ x, const float *__restrict__ y
         }
         int status = 1;
         double A[6], g[3], rr, L[6];
-        for (int it = 0; it < F.iters; ++it) {
-            normal_eq(x, y, list, b, nh, p, lane, A, g, rr);
-            if (!chol3(A, L)) {                       // same sums on every lane
-                status = -1;
-                break;
+        int nk;
+        Sel S;
+        S.q[0] = p[0]; S.q[1] = p[1]; S.q[2] = p[2];
+        S.w = F.road > 0.0 ? F.road : 1e308;
+        // the road: hits near the cell-centre circle
+        normal_eq(x, y, list, b, nh, p, S, lane, A, g, rr, nk);
+        bool few = nk < F.min_hits;
+        if (!few) {
+            if (!gauss_newton(x, y, list, b, nh, p, S, F.iters, lane)) status = -1;
+            if (status == 1 && F.cut > 0.0) {
+                // the outlier cut: hits near the fitted circle, fitted again
+                S.q[0] = p[0]; S.q[1] = p[1]; S.q[2] = p[2];
+                S.w = F.cut * F.sigma;
+                normal_eq(x, y, list, b, nh, p, S, lane, A, g, rr, nk);
+                few = nk < F.min_hits;
+                if (!few && !gauss_newton(x, y, list, b, nh, p, S, F.iters2, lane)) status = -1;
             }
-            // forward then backward substitution: L z = g, L^T dp = z
-            const double z0 = g[0] / L[0];
-            const double z1 = (g[1] - L[1] * z0) / L[2];
-            const double z2 = (g[2] - L[3] * z0 - L[4] * z1) / L[5];
-            const double d2 = z2 / L[5];
-            const double d1 = (z1 - L[4] * d2) / L[2];
-            const double d0 = (z0 - L[1] * d1 - L[3] * d2) / L[0];
-            p[0] -= d0;
-            p[1] -= d1;
-            p[2] -= d2;
         }
-        normal_eq(x, y, list, b, nh, p, lane, A, g, rr);
         T.rho = p[0]; T.d0 = p[1]; T.phi0 = p[2];
+        if (few) {
+            T.n_hits = nk;
+            T.sig_rho = T.sig_d0 = T.sig_phi0 = nan("");
+            T.chi2 = nanf("");
+            T.status = 0;
+            if (lane == 0) out[slot] = T;
+            continue;
+        }
+        normal_eq(x, y, list, b, nh, p, S, lane, A, g, rr, nk);
+        T.n_hits = nk;
         T.chi2 = (float)(rr / (F.sigma * F.sigma));
         if (chol3(A, L)) {
             // diagonal of (L L^T)^-1 = columns of L^-1 squared and summed
@@ -202,11 +263,13 @@ size_t ht_fit_workspace_size(int32_t n_events, int32_t cap, int32_t n_hits)
 ht_status ht_fit_tracks(const ht_geometry *g, const float *x, const float *y, const int32_t *d_off,
                         int32_t n_events, int32_t n_hits, const int32_t *assign,
                         const ht_peak *peaks, const int32_t *d_count, int32_t cap,
-                        int32_t min_hits, int32_t iters, double sigma, ht_track *out,
-                        void *workspace, size_t workspace_bytes, ht_stream stream)
+                        int32_t min_hits, int32_t iters, double sigma, double road, double cut,
+                        int32_t iters2, ht_track *out, void *workspace, size_t workspace_bytes,
+                        ht_stream stream)
 {
     if (!g || !d_off || !d_count || !out || !workspace || n_events < 1 || n_hits < 0 || cap < 1 ||
-        min_hits < 3 || iters < 0 || iters > 64 || !(sigma > 0.0) ||
+        min_hits < 3 || iters < 0 || iters > 64 || iters2 < 0 || iters2 > 64 ||
+        !(sigma > 0.0) || road != road || cut != cut ||
         (n_hits > 0 && (!x || !y || !assign)) || !peaks)
         return ht::set_error(HT_ERR_ARG, "ht_fit_tracks: bad argument");
     if ((int64_t)n_events * cap > 0x7fffffffLL)
@@ -242,6 +305,9 @@ ht_status ht_fit_tracks(const ht_geometry *g, const float *x, const float *y, co
         F.half_nd = 0.5 * (double)g->G.n_d0;
         F.pi_over_np = ht::kPi / (double)g->G.n_phi0;
         F.sigma = sigma;
+        F.road = road;
+        F.cut = cut;
+        F.iters2 = iters2;
         F.rho64 = g->G.rho64;
         F.n_phi0 = g->G.n_phi0;
         F.min_hits = min_hits;

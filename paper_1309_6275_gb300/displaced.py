@@ -11,6 +11,30 @@ import math
 import numpy as np
 
 
+def fit_quality(ev, assign, tracks):
+    """For fitted candidates (status 1) whose assigned hits are mostly one
+    track's: d0 and rho residuals against that track's truth and the number
+    of such candidates.  tracks: the event's ht_track records."""
+    assign = np.asarray(assign)
+    res_d0, res_rho, n_fit = [], [], 0
+    for m in range(len(tracks)):
+        if tracks[m]["status"] != 1:
+            continue
+        n_fit += 1
+        tr = ev.track[assign == m]
+        tr = tr[tr >= 0]
+        if tr.size == 0:
+            continue
+        vals, cnts = np.unique(tr, return_counts=True)
+        b = int(np.argmax(cnts))
+        if cnts[b] * 2 <= (assign == m).sum():
+            continue
+        t = vals[b]
+        res_d0.append(tracks[m]["d0"] - ev.d0[t])
+        res_rho.append(tracks[m]["rho"] - ev.rho[t])
+    return n_fit, np.array(res_d0), np.array(res_rho)
+
+
 def vertex_cell(vd, r, theta):
     """(radius bin, azimuth bin) of a vertex position."""
     dr = vd["r_max"] / vd["n_r"]

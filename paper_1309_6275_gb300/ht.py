@@ -93,7 +93,8 @@ SIGNATURES = [
                                     _P, _P, _P, _P, _P, _P]),
     ("ht_fit_workspace_size", _SZ, [_I32, _I32, _I32]),
     ("ht_fit_tracks", _I32, [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _I32, _I32, _I32,
-                             ctypes.c_double, _P, _P, _SZ, _P]),
+                             ctypes.c_double, ctypes.c_double, ctypes.c_double, _I32, _P, _P,
+                             _SZ, _P]),
     ("ht_vertex_create", _I32, [_P, ctypes.POINTER(_VertexDesc), ctypes.POINTER(_P)]),
     ("ht_vertex_destroy", _I32, [_P]),
     ("ht_vertex_accumulator_bytes", _SZ, [_P]),
@@ -284,13 +285,13 @@ TRACK_FIELDS = ["rho", "d0", "phi0", "sig_rho", "sig_d0", "sig_phi0"]
 
 
 def ht_fit_tracks(G, x, y, d_off, assign, peaks, d_count, cap, out, workspace, min_hits=4,
-                  iters=5, sigma=20e-4, stream=None):
+                  iters=5, sigma=20e-4, road=0.0, cut=0.0, iters2=3, stream=None):
     """Refit candidates.  out: uint8 tensor of n_events * cap * 64 bytes (one
     ht_track each); d_off: device int32 [n_events + 1]."""
     _check(lib().ht_fit_tracks(G.handle, _ptr(x), _ptr(y), _ptr(d_off), d_off.numel() - 1,
                                x.numel(), _ptr(assign), _ptr(peaks), _ptr(d_count), cap, min_hits,
-                               iters, sigma, _ptr(out), _ptr(workspace), workspace.numel(),
-                               _stream(stream)), "ht_fit_tracks")
+                               iters, sigma, road, cut, iters2, _ptr(out), _ptr(workspace),
+                               workspace.numel(), _stream(stream)), "ht_fit_tracks")
 
 
 def ht_fit_workspace_size(n_events, cap, n_hits):

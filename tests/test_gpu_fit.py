@@ -18,21 +18,29 @@ pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
 
 
-def gpu_fit(G, ht, x, y, off, assign, peaks, counts, cap, min_hits=4, iters=5):
+SELECTIONS = [dict(), dict(road=1.0, cut=5.0)]
+
+
+def gpu_fit(G, ht, x, y, off, assign, peaks, counts, cap, min_hits=4, iters=5, road=None,
+            cut=None, iters2=3):
     import torch
     n_ev = len(off) - 1
     out = torch.zeros(n_ev * cap * 64, dtype=torch.uint8, device="cuda")
     ws = torch.empty(ht.ht_fit_workspace_size(n_ev, cap, int(off[-1])), dtype=torch.uint8,
                      device="cuda")
     ht.ht_fit_tracks(G, x, y, to_dev(np.asarray(off, np.int32)), assign, peaks, counts, cap,
-                     out, ws, min_hits=min_hits, iters=iters)
+                     out, ws, min_hits=min_hits, iters=iters, road=road or 0.0, cut=cut or 0.0,
+                     iters2=iters2)
     torch.cuda.synchronize()
     return ht.tracks_to_numpy(out, n_ev * cap)
 
 
-def compare(g, ev_x, ev_y, assign, peaks, tracks, min_hits=4, iters=5):
-    ora = F.fit_candidates(g, ev_x, ev_y, assign, peaks, min_hits=min_hits, iters=iters)
-    ora_more = F.fit_candidates(g, ev_x, ev_y, assign, peaks, min_hits=min_hits, iters=iters + 1)
+def compare(g, ev_x, ev_y, assign, peaks, tracks, min_hits=4, iters=5, road=None, cut=None,
+            iters2=3):
+    kw = dict(min_hits=min_hits, road=road, cut=cut)
+    ora = F.fit_candidates(g, ev_x, ev_y, assign, peaks, iters=iters, iters2=iters2, **kw)
+    more = dict(iters=iters, iters2=iters2 + 1) if cut else dict(iters=iters + 1, iters2=iters2)
+    ora_more = F.fit_candidates(g, ev_x, ev_y, assign, peaks, **more, **kw)
     n_fit = n_cmp = 0
     for m, o in enumerate(ora):
         t = tracks[m]
@@ -42,6 +50,8 @@ def compare(g, ev_x, ev_y, assign, peaks, tracks, min_hits=4, iters=5):
         n_fit += 1
         assert t["n_hits"] == o["n"], m
         assert t["status"] == o["status"], m
+        if ora_more[m]["status"] != o["status"]:
+            continue
         if o["status"] != 1:
             continue
         sig = np.sqrt(np.diag(o["cov"]))
@@ -55,7 +65,8 @@ def compare(g, ev_x, ev_y, assign, peaks, tracks, min_hits=4, iters=5):
     return n_fit, n_cmp
 
 
-def test_fit_on_single_events_matches_oracle():
+@pytest.mark.parametrize("sel", SELECTIONS)
+def test_fit_on_single_events_matches_oracle(sel):
     import torch
     from paper_1309_6275_gb300 import ht
     name = "single_64"
@@ -70,14 +81,17 @@ def test_fit_on_single_events_matches_oracle():
         p.run(dx, dy, dz)
         torch.cuda.synchronize()
         r = p.results(ev.n_hits)
-        tr = gpu_fit(G, ht, dx, dy, [0, ev.n_hits], p.assign[:ev.n_hits], p.peaks, p.count, cap)
+        tr = gpu_fit(G, ht, dx, dy, [0, ev.n_hits], p.assign[:ev.n_hits], p.peaks, p.count, cap,
+                     **sel)
         o = oracle.run_event(g, ev.x, ev.y, ev.z)
         assert np.array_equal(r["peaks"], o["peaks"]) and np.array_equal(r["assign"], o["assign"])
-        nf, nc = compare(g, ev.x, ev.y, o["assign"], o["peaks"], tr[:len(o["peaks"])])
+        nf, nc = compare(g, ev.x, ev.y, o["assign"], o["peaks"], tr[:len(o["peaks"])], **sel)
         total_fit += nf
         total_cmp += nc
         G.close()
-    assert total_fit > 10 and total_cmp >= 0.25 * total_fit
+    # with the road most of these small events' candidates keep too few hits
+    # (their status, 0, is compared above); at least some fits are compared
+    assert total_fit > 10 and total_cmp >= (0.25 * total_fit if not sel else 2)
 
 
 def test_fit_in_batch_layout_and_noise_free_tracks():
@@ -96,12 +110,13 @@ def test_fit_in_batch_layout_and_noise_free_tracks():
     B = ht.Batch(G, max_events=3, max_hits=int(off[-1]), cap=cap)
     B.run(x, y, z, off)
     torch.cuda.synchronize()
-    tr = gpu_fit(G, ht, x, y, off, B.assign, B.peaks, B.counts, cap)
-    for e, ev in enumerate(evs):
-        r = B.event_results(off, e)
-        t = tr[e * cap:e * cap + r["count"]]
-        nf, nc = compare(g, ev.x, ev.y, r["assign"], r["peaks"], t)
-        assert nf > 0
+    for sel in SELECTIONS:
+        tr = gpu_fit(G, ht, x, y, off, B.assign, B.peaks, B.counts, cap, **sel)
+        for e, ev in enumerate(evs):
+            r = B.event_results(off, e)
+            t = tr[e * cap:e * cap + r["count"]]
+            nf, nc = compare(g, ev.x, ev.y, r["assign"], r["peaks"], t, **sel)
+            assert nf > 0
     B.close()
     # exact helices (float32 hits), one candidate each at a nearby cell
     tracks = [(0.0041, 0.0, 0.8), (-0.0063, 2.4, -1.9), (0.0012, -5.1, 2.7)]

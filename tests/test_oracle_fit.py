@@ -90,3 +90,24 @@ def test_fit_candidates_selects_by_hit_count():
         assert (f is None) == (n_ass[m] < 4)
         if f is not None:
             assert f["n"] == n_ass[m] and f["status"] in (1, -1)
+
+
+def test_road_and_cut_drop_foreign_hits():
+    """A track's hits plus hits of a crossing track: without selection the fit
+    is pulled away; the road and the cut keep exactly the track's hits."""
+    g = synth.geometry_of("event100_256")
+    import oracle
+    phi_t, _, _, rho_t = oracle.tables(g)
+    delta = 2 * g["d0_half"] / g["n_d0"]
+    i, j, k = 180, 66, 300
+    rho, d0, phi0 = rho_t[i] + 1e-5, (j - 64) * delta + 0.05, phi_t[k] - 0.002
+    hx, hy, _, _, _ = synth.helix_hits(rho, d0, phi0)
+    ox, oy, _, _, _ = synth.helix_hits(-0.004, 6.0, phi0 + 0.3)
+    x = np.concatenate([hx, ox[:4]]); y = np.concatenate([hy, oy[:4]])
+    assign = np.zeros(x.shape[0], np.int32)
+    pk = np.array([[i, j, k, 10]], np.int32)
+    plain = F.fit_candidates(g, x, y, assign, pk)[0]
+    sel = F.fit_candidates(g, x, y, assign, pk, road=1.0, cut=5.0)[0]
+    assert sel["n"] == hx.shape[0] and sel["status"] == 1
+    assert abs(sel["p"][1] - d0) < 1e-9 and abs(sel["p"][0] - rho) < 1e-12
+    assert abs(plain["p"][1] - d0) > 1e-3
