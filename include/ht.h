@@ -241,7 +241,8 @@ ht_status ht_find_peaks_masked(const ht_geometry *g, const void *acc, const uint
 
 /* ------------------------------------------------------------------------
  * Proposal network: per-hit MLP 6 -> 128 -> 128 -> 64 with ReLU and a
- * softmax over the 64 regions.  Features of a hit (float32, then rounded
+ * softmax over the 64 regions; the 128 x 128 and 128 x 64 layers of the
+ * forward pass run on the tensor cores (tcgen05, BF16 in, float32 out).  Features of a hit (float32, then rounded
  * to BF16): x/110, y/110, z/(110 sinh 2.5), r/110, atan2(y, x)/pi,
  * layer/9.  Weights and hidden activations are BF16, sums float32.
  * Parameters: one flat array of ht_mlp_param_count() values laid out
@@ -250,6 +251,11 @@ ht_status ht_find_peaks_masked(const ht_geometry *g, const void *acc, const uint
  * master copy and the network reads the BF16 copy.
  * ------------------------------------------------------------------------ */
 int32_t ht_mlp_param_count(void);
+
+/* Forward passes that gave up waiting for their tensor-core work (bounded
+ * waits; 0 in a healthy run) since the library was loaded; synchronous;
+ * -1 on a CUDA error. */
+int64_t ht_mlp_timeouts(void);
 
 /* Forward pass of n hits (x, y, z float32, layer uint8 device arrays).
  * Outputs (device, each may be NULL): prob n x 64 float32 (softmax); h1, h2

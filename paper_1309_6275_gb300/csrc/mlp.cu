@@ -4,8 +4,8 @@
 // proposal's own reading.
 //
 // Numerics: BF16 weights and BF16 activations between layers, products of
-// BF16 values exact in float32, float32 accumulation, float32 logits and
-// softmax.  Features: x/110, y/110, z/(110 sinh 2.5), r/110, phi/pi, layer/9,
+// BF16 values exact in float32, float32 accumulation (tensor memory for the
+// forward pass's 128-wide layers), float32 logits and softmax.  Features: x/110, y/110, z/(110 sinh 2.5), r/110, phi/pi, layer/9,
 // each computed in float32 (no contraction) and rounded to BF16.
 //
 // Layout of the flat parameter array (float32 master and BF16 copy):
@@ -25,7 +25,7 @@ namespace {
 constexpr int kIn = 6, kH = 128, kOut = 64;
 constexpr int oW1 = 0, ob1 = oW1 + kIn * kH, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
               oW3 = ob2 + kH, ob3 = oW3 + kH * kOut, kParams = ob3 + kOut;
-constexpr int kFwdThreads = 128;   // one hit per thread
+constexpr int kFwdThreads = 128;   // one hit per thread (backward pass)
 constexpr float kSinhEta = 6.0502044810397875f;   // sinh(2.5)
 
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
@@ -62,125 +62,7 @@ __device__ __forceinline__ int event_of_hit(const int *off, int n_ev, int h)
     return lo;
 }
 
-__global__ void __launch_bounds__(kFwdThreads)
-k_mlp_fwd(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ x,
-          const float *__restrict__ y, const float *__restrict__ z,
-          const uint8_t *__restrict__ layer, int n, FwdOut out)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16 *sW2 = reinterpret_cast<__nv_bfloat16 *>(smem);          // [128][128]
-    __nv_bfloat16 *sW3 = sW2 + kH * kH;                                    // [128][64]
-    __nv_bfloat16 *sW1 = sW3 + kH * kOut;                                  // [6][128]
-    __nv_bfloat16 (*hT)[kFwdThreads] =                                     // layer-1 output,
-        reinterpret_cast<__nv_bfloat16 (*)[kFwdThreads]>(sW1 + kIn * kH);  // transposed
-    float *sb1 = reinterpret_cast<float *>(&hT[kH][0]);
-    float *sb2 = sb1 + kH, *sb3 = sb2 + kH, *smass = sb3 + kOut;
-    __shared__ int sev;
-    if (out.d_n) n = *out.d_n;
-    for (int t = threadIdx.x; t < kIn * kH; t += kFwdThreads) sW1[t] = w[oW1 + t];
-    for (int t = threadIdx.x; t < kH * kH; t += kFwdThreads) sW2[t] = w[oW2 + t];
-    for (int t = threadIdx.x; t < kH * kOut; t += kFwdThreads) sW3[t] = w[oW3 + t];
-    for (int t = threadIdx.x; t < kH; t += kFwdThreads) {
-        sb1[t] = __bfloat162float(w[ob1 + t]);
-        sb2[t] = __bfloat162float(w[ob2 + t]);
-    }
-    for (int t = threadIdx.x; t < kOut; t += kFwdThreads) sb3[t] = __bfloat162float(w[ob3 + t]);
-    __syncthreads();
-
-    for (int base = blockIdx.x * kFwdThreads; base < n; base += gridDim.x * kFwdThreads) {
-        const int h = base + threadIdx.x;
-        const bool act = h < n;
-        float f[kIn];
-        hit_features(act ? x[h] : 0.f, act ? y[h] : 0.f, act ? z[h] : 0.f, act ? layer[h] : 0, f);
-        if (act && out.feat) {
-            __align__(16) __nv_bfloat16 fb[8];
-#pragma unroll
-            for (int i = 0; i < kIn; ++i) fb[i] = __float2bfloat16_rn(f[i]);
-            fb[6] = fb[7] = __float2bfloat16_rn(0.f);
-            *reinterpret_cast<uint4 *>(out.feat + (size_t)h * 8) = *reinterpret_cast<uint4 *>(fb);
-        }
-        // layer 1
-        for (int o = 0; o < kH; ++o) {
-            float a = sb1[o];
-#pragma unroll
-            for (int i = 0; i < kIn; ++i) a = fmaf(f[i], __bfloat162float(sW1[i * kH + o]), a);
-            const __nv_bfloat16 v = __float2bfloat16_rn(fmaxf(a, 0.f));
-            hT[o][threadIdx.x] = v;
-            if (act && out.h1) out.h1[(size_t)h * kH + o] = v;
-        }
-        __syncthreads();
-        // layer 2 in chunks of 8 outputs, folded straight into the logits
-        float lg[kOut];
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) lg[c] = sb3[c];
-        for (int o0 = 0; o0 < kH; o0 += 8) {
-            float a[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) a[u] = sb2[o0 + u];
-            for (int i = 0; i < kH; ++i) {
-                const float hv = __bfloat162float(hT[i][threadIdx.x]);
-                const uint4 wv = *reinterpret_cast<const uint4 *>(&sW2[i * kH + o0]);
-                const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
-#pragma unroll
-                for (int u = 0; u < 8; ++u) a[u] = fmaf(hv, __bfloat162float(wb[u]), a[u]);
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const __nv_bfloat16 hb = __float2bfloat16_rn(fmaxf(a[u], 0.f));
-                if (act && out.h2) out.h2[(size_t)h * kH + o0 + u] = hb;
-                const float hv = __bfloat162float(hb);
-                const uint4 *wr = reinterpret_cast<const uint4 *>(&sW3[(o0 + u) * kOut]);
-#pragma unroll
-                for (int c8 = 0; c8 < kOut / 8; ++c8) {
-                    const uint4 wv = wr[c8];
-                    const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) lg[c8 * 8 + q] = fmaf(hv, __bfloat162float(wb[q]), lg[c8 * 8 + q]);
-                }
-            }
-        }
-        // softmax
-        float mx = lg[0];
-#pragma unroll
-        for (int c = 1; c < kOut; ++c) mx = fmaxf(mx, lg[c]);
-        float s = 0.f;
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) {
-            lg[c] = __expf(lg[c] - mx);
-            s += lg[c];
-        }
-        const float is = __frcp_rn(s);
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) lg[c] *= is;
-        if (act && out.prob) {
-            float4 *pp = reinterpret_cast<float4 *>(out.prob + (size_t)h * kOut);
-#pragma unroll
-            for (int c4 = 0; c4 < kOut / 4; ++c4)
-                pp[c4] = make_float4(lg[4 * c4], lg[4 * c4 + 1], lg[4 * c4 + 2], lg[4 * c4 + 3]);
-        }
-        if (out.mass) {
-            // per-event sums: a chunk of hits may straddle events, so group by
-            // the chunk's first event and send the others straight to global
-            if (threadIdx.x == 0) sev = event_of_hit(out.off, out.n_ev, base);
-            for (int c = threadIdx.x; c < kOut; c += kFwdThreads) smass[c] = 0.f;
-            __syncthreads();
-            const int e = act ? event_of_hit(out.off, out.n_ev, h) : -1;
-            if (act) {
-                if (e == sev) {
-#pragma unroll
-                    for (int c = 0; c < kOut; ++c) atomicAdd(&smass[c], lg[c]);
-                } else {
-#pragma unroll
-                    for (int c = 0; c < kOut; ++c) atomicAdd(&out.mass[(size_t)e * kOut + c], lg[c]);
-                }
-            }
-            __syncthreads();
-            for (int c = threadIdx.x; c < kOut; c += kFwdThreads)
-                atomicAdd(&out.mass[(size_t)sev * kOut + c], smass[c]);
-        }
-        __syncthreads();
-    }
-}
+#include "mlp_tc.cuh"
 
 // Backward through the activations of one minibatch: dL = (p - onehot) / nl
 // (0 for unlabelled hits), dH2 = (dL W3^T) o [h2 > 0], dH1 = (dH2 W2^T) o [h1 > 0].
@@ -347,8 +229,6 @@ __global__ void k_region_mask(const float *__restrict__ mass, const int *__restr
     mask[e] = ((float)__popcll(bits) > fmax * (float)kOut || n == 0) ? ~0ull : bits;
 }
 
-constexpr size_t kFwdSmem = (size_t)(kH * kH + kH * kOut + kIn * kH + kH * kFwdThreads) * 2 +
-                           (size_t)(2 * kH + 2 * kOut) * 4;
 constexpr size_t kBwdSmem = (size_t)(kH * kH + kH * kOut) * 2 + (size_t)kH * (kFwdThreads + 1) * 4;
 
 }  // namespace
@@ -383,9 +263,9 @@ cudaError_t launch_region_mask(const void *params_bf16, const float *x, const fl
     if (e != cudaSuccess) return e;
     if (max_hits > 0) {
         FwdOut o{nullptr, nullptr, nullptr, nullptr, mass, off, n_ev, off + n_ev};
-        const int blocks = min((max_hits + kFwdThreads - 1) / kFwdThreads, 152 * 8);
-        k_mlp_fwd<<<blocks, kFwdThreads, kFwdSmem, st>>>((const __nv_bfloat16 *)params_bf16, x, y,
-                                                         z, layer, max_hits, o);
+        const int blocks = min((max_hits + kTcM - 1) / kTcM, 152 * 2);
+        k_mlp_fwd_tc<<<blocks, kTcM, kTcSmem, st>>>((const __nv_bfloat16 *)params_bf16, x, y, z,
+                                                    layer, max_hits, o);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
@@ -395,8 +275,8 @@ cudaError_t launch_region_mask(const void *params_bf16, const float *x, const fl
 
 cudaError_t prepare_mlp_kernels()
 {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kFwdSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kTcSmem);
     if (e == cudaSuccess)
         e = cudaFuncSetAttribute(k_mlp_bwd_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)kBwdSmem);
@@ -411,6 +291,16 @@ extern "C" {
 
 int32_t ht_mlp_param_count(void) { return kParams; }
 
+int64_t ht_mlp_timeouts(void)
+{
+    unsigned int v = 0;
+    if (cudaMemcpyFromSymbol(&v, g_mlp_timeouts, sizeof v) != cudaSuccess) {
+        set_error(HT_ERR_CUDA, "ht_mlp_timeouts: copy");
+        return -1;
+    }
+    return (int64_t)v;
+}
+
 ht_status ht_mlp_forward(const void *params_bf16, const float *x, const float *y, const float *z,
                          const uint8_t *layer, int32_t n, float *prob, void *h1, void *h2,
                          void *feat, ht_stream stream)
@@ -422,8 +312,8 @@ ht_status ht_mlp_forward(const void *params_bf16, const float *x, const float *y
     if (pe != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(pe));
     FwdOut o{prob, (__nv_bfloat16 *)h1, (__nv_bfloat16 *)h2, (__nv_bfloat16 *)feat, nullptr,
              nullptr, 0, nullptr};
-    const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, 152 * 8);
-    k_mlp_fwd<<<blocks, kFwdThreads, kFwdSmem, reinterpret_cast<cudaStream_t>(stream)>>>(
+    const int blocks = min((n + kTcM - 1) / kTcM, 152 * 2);
+    k_mlp_fwd_tc<<<blocks, kTcM, kTcSmem, reinterpret_cast<cudaStream_t>(stream)>>>(
         (const __nv_bfloat16 *)params_bf16, x, y, z, layer, n, o);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));

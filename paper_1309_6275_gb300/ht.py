@@ -81,6 +81,7 @@ SIGNATURES = [
     ("ht_vote_masked", _I32, [_P, _P, _P, _I32, _P, _P, _P, _P]),
     ("ht_find_peaks_masked", _I32, [_P, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
     ("ht_mlp_param_count", _I32, []),
+    ("ht_mlp_timeouts", ctypes.c_int64, []),
     ("ht_mlp_forward", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]),
     ("ht_mlp_region_mask", _I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, ctypes.c_float,
                                   ctypes.c_float, _I32, _P, _P, _P]),
@@ -213,6 +214,11 @@ def ht_find_peaks_masked(g, acc, mask, peaks, cap, d_count, workspace, stream=No
 
 def ht_mlp_param_count():
     return lib().ht_mlp_param_count()
+
+
+def ht_mlp_timeouts():
+    """Forward passes that gave up waiting on their tensor-core work."""
+    return lib().ht_mlp_timeouts()
 
 
 def ht_mlp_forward(params_bf16, x, y, z, layer, prob=None, h1=None, h2=None, feat=None,

@@ -15,7 +15,7 @@ def declared_symbols():
     for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
         if name.endswith(".h"):
             hdr = open(os.path.join(ROOT, "include", name)).read()
-            syms |= set(re.findall(r"^(?:ht_status|size_t|int32_t|const char \*)\s*\**\s*(ht_\w+)\(",
+            syms |= set(re.findall(r"^(?:ht_status|size_t|int32_t|int64_t|const char \*)\s*\**\s*(ht_\w+)\(",
                                    hdr, re.M))
     return syms
 

@@ -79,6 +79,8 @@ def test_forward_matches_oracle():
     for a, b in ((prob.cpu().numpy(), P), (to_np_bf16(h1), H1), (to_np_bf16(h2), H2)):
         assert rel_l2(a, b) <= 1e-2 and cosine(a, b) >= 0.999
     assert np.allclose(prob.cpu().numpy().sum(1), 1.0, atol=1e-5)
+    from paper_1309_6275_gb300 import ht
+    assert ht.ht_mlp_timeouts() == 0
 
 
 def test_gradients_match_oracle():
