@@ -146,6 +146,60 @@ void or_vote(const or_geom *g, const float *x, const float *y, int64_t n,
     free(phi0); free(sn); free(cs); free(rho);
 }
 
+/* Per-hit region proposals (the learned proposal's per-hit variant; the paper
+ * has no learned part).  Regions (reading): an 8 x 8 grid over the rho rows
+ * and d0 bins, cell (i, j) in region 8 (i 8 / n_rho) + (j 8 / n_d0) (integer
+ * division).  A hit may vote in cell (i, j) iff some cell (i', j') with
+ * |i - i'| <= 1 and |j - j'| <= 1 (inside the axes) lies in one of the
+ * regions of its mask: its regions plus a one-cell halo, so that a track
+ * whose peak sits on a region edge keeps the votes around it. */
+static int in_hit_halo(const or_geom *g, uint64_t mask, int32_t i, int32_t j)
+{
+    for (int32_t di = -1; di <= 1; ++di)
+        for (int32_t dj = -1; dj <= 1; ++dj) {
+            const int32_t ii = i + di, jj = j + dj;
+            if (ii < 0 || ii >= g->n_rho || jj < 0 || jj >= g->n_d0)
+                continue;
+            const int32_t r = (ii * 8 / g->n_rho) * 8 + jj * 8 / g->n_d0;
+            if ((mask >> r) & 1u)
+                return 1;
+        }
+    return 0;
+}
+
+/* or_vote with every vote of hit h dropped unless its cell is allowed by
+ * mask[h] (in_hit_halo).  stats[0] counts the votes cast, stats[1] the
+ * in-range roots near a bin edge, allowed or not (as cell_bins counts them). */
+void or_vote_hitmask(const or_geom *g, const float *x, const float *y, const uint64_t *mask,
+                     int64_t n, int32_t i_begin, int32_t i_end, int64_t *acc, int64_t *stats)
+{
+    double *phi0 = malloc(sizeof(double) * g->n_phi0);
+    double *sn = malloc(sizeof(double) * g->n_phi0);
+    double *cs = malloc(sizeof(double) * g->n_phi0);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    or_tables(g, phi0, sn, cs, rho);
+    int64_t votes = 0, edge = 0;
+    for (int64_t h = 0; h < n; ++h)
+        for (int32_t i = i_begin; i < i_end; ++i)
+            for (int32_t k = 0; k < g->n_phi0; ++k) {
+                int32_t j[2];
+                int64_t e = 0;
+                const int nv = cell_bins(g, x[h], y[h], sn[k], cs[k], rho[i], j, &e);
+                for (int t = 0; t < nv; ++t) {
+                    if (!in_hit_halo(g, mask[h], i, j[t]))
+                        continue;
+                    int64_t *cell = &acc[((int64_t)i * g->n_d0 + j[t]) * g->n_phi0 + k];
+                    if (*cell < g->count_max)
+                        ++*cell;
+                    ++votes;
+                }
+                edge += e;
+            }
+    stats[0] += votes;
+    stats[1] += edge;
+    free(phi0); free(sn); free(cs); free(rho);
+}
+
 /* Peak finding (Sections 5 and 6: local maxima of the vote space; Section 7:
  * tuned for 7 or more hits per track).  Reading: cell l = (i n_d0 + j) n_phi0 + k
  * is a peak iff acc[l] >= threshold and, for every existing one of its 26

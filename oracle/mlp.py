@@ -194,3 +194,36 @@ def masked_event(g, x, y, z, mask, cap=None, threads=None, acc=None):
     zr = O.vote_z(g, x, y, z, asg, pk, threads=threads)
     votes = int(acc[halo].sum())
     return dict(acc=acc, halo=halo, peaks=pk, count=count, assign=asg, zres=zr, votes=votes)
+
+
+def hit_topk_masks(prob, k, pmin=0.0):
+    """Per-hit region sets of the per-hit proposal (reading): the k regions
+    of largest probability (ties to the smaller region index) as a 64-bit
+    mask; every region when k >= 64 or when those k probabilities sum to
+    less than pmin (an unsure hit votes everywhere)."""
+    prob = np.asarray(prob, np.float64)
+    out = np.zeros(prob.shape[0], np.uint64)
+    full = np.uint64((1 << 64) - 1)
+    for h in range(prob.shape[0]):
+        if k >= N_REGIONS:
+            out[h] = full
+            continue
+        top = np.argsort(-prob[h], kind="stable")[:k]
+        if prob[h][top].sum() < pmin:
+            out[h] = full
+            continue
+        out[h] = np.uint64(sum(1 << int(r) for r in top))
+    return out
+
+
+def hit_masked_event(g, x, y, z, masks, cap=None, threads=None):
+    """The path with each hit's votes restricted to its region set plus a
+    one-cell halo (Section 5's vote, then the peaks of that accumulator,
+    association and the z vote unchanged).  masks: uint64 per hit."""
+    from . import oracle as O
+    acc, st = O.vote_hitmask(g, x, y, masks, threads)
+    pk, count = O.peaks(g, acc, cap, threads)
+    pk = np.ascontiguousarray(pk)
+    asg = O.associate_dense(g, x, y, pk, threads=threads)
+    zr = O.vote_z(g, x, y, z, asg, pk, threads=threads)
+    return dict(acc=acc, peaks=pk, count=count, assign=asg, zres=zr, votes=st["votes"])

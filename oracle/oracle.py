@@ -69,6 +69,7 @@ def lib():
             i64, i32 = ctypes.c_int64, ctypes.c_int32
             L.or_tables.argtypes = [G, vp, vp, vp, vp]
             L.or_vote.argtypes = [G, vp, vp, i64, i32, i32, vp, vp]
+            L.or_vote_hitmask.argtypes = [G, vp, vp, vp, i64, i32, i32, vp, vp]
             L.or_peaks.argtypes = [G, vp, i32, i32, vp, i64]
             L.or_peaks.restype = i64
             L.or_associate.argtypes = [G, vp, vp, vp, i64, vp, i64, vp]
@@ -123,6 +124,33 @@ def vote(g, x, y, threads=None, rows=None):
         a, b = parts[t]
         lib().or_vote(ctypes.byref(G), _p(x), _p(y), x.shape[0], a, b,
                       ctypes.c_void_p(accp), _p(stats[t]))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, range(len(parts))))
+    tot = stats.sum(0)
+    return acc, {"votes": int(tot[0]), "edge": int(tot[1])}
+
+
+def vote_hitmask(g, x, y, masks, threads=None, rows=None):
+    """The vote with hit h's votes kept only in cells allowed by masks[h]
+    (uint64 per hit: a region set on the 8 x 8 region grid, plus a one-cell
+    halo; see or_vote_hitmask).  Returns (acc, {votes, edge}) like vote;
+    rows=(a, b) computes only rho rows [a, b) and returns acc[a:b]."""
+    G = _geom(g)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    m = np.ascontiguousarray(np.asarray(masks, np.uint64))
+    assert m.shape[0] == x.shape[0]
+    r0, r1 = (0, g["n_rho"]) if rows is None else rows
+    acc = np.zeros((r1 - r0, g["n_d0"], g["n_phi0"]), np.int64)
+    base = r0 * g["n_d0"] * g["n_phi0"] * 8
+    parts = [(a + r0, b + r0) for a, b in _chunks(r1 - r0, _threads(threads) * 2)]
+    stats = np.zeros((len(parts), 2), np.int64)
+    accp = acc.ctypes.data - base
+
+    def run(t):
+        a, b = parts[t]
+        lib().or_vote_hitmask(ctypes.byref(G), _p(x), _p(y), _p(m), x.shape[0], a, b,
+                              ctypes.c_void_p(accp), _p(stats[t]))
 
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(run, range(len(parts))))
