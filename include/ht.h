@@ -229,6 +229,15 @@ ht_status ht_vote_masked(const ht_geometry *g, const float *x, const float *y,
                          int32_t n_hits, const uint64_t *mask, void *acc, uint64_t *stats,
                          ht_stream stream);
 
+/* The vote with one region set per hit: hit h's votes count only in the
+ * halo cells of hit_masks[h] (device, n_hits uint64, 8-byte aligned); every
+ * cell of acc is written (cells no allowed vote reaches hold 0).  With every
+ * mask all ones this is ht_vote.  stats: as ht_vote, counting the votes
+ * cast.  Other arguments as ht_vote.  Errors: as ht_vote. */
+ht_status ht_vote_hit_masked(const ht_geometry *g, const float *x, const float *y,
+                             int32_t n_hits, const uint64_t *hit_masks, void *acc,
+                             uint64_t *stats, ht_stream stream);
+
 /* ht_find_peaks restricted to a mask: exactly the peaks ht_find_peaks
  * reports for the full accumulator that are inside the mask, in the same
  * order.  Reads only (blocks of) inside cells and their neighbours, so acc
@@ -278,6 +287,17 @@ ht_status ht_mlp_region_mask(const void *params_bf16, const float *x, const floa
                              const float *z, const uint8_t *layer, const int32_t *off,
                              int32_t n_events, int32_t n_hits, float tau, float fmax,
                              int32_t grow, float *mass, uint64_t *masks, ht_stream stream);
+
+/* Per-hit region sets (the per-hit proposal): hit_masks[h] (device, n_hits
+ * uint64) gets the topk regions of largest softmax output of hit h (ties to
+ * the smaller region index), or every region (all bits) when topk >= 64 or
+ * those topk outputs sum to less than pmin (float32 sum; a sum within about
+ * 1e-6 of pmin, or outputs within about 1e-6 of each other, may fall either
+ * way).  Feed the result to ht_vote_hit_masked or ht_batch_run_hit_masked.
+ * topk >= 1.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_mlp_hit_masks(const void *params_bf16, const float *x, const float *y,
+                           const float *z, const uint8_t *layer, int32_t n_hits, int32_t topk,
+                           float pmin, uint64_t *hit_masks, ht_stream stream);
 
 /* Gradient of the mean softmax cross entropy over the hits with label >= 0
  * (labels: device int32, region index or -1 to skip the hit), given the
@@ -470,6 +490,35 @@ ht_status ht_batch_run_learned(ht_batch *b, const float *x, const float *y, cons
                                uint64_t *masks, ht_peak *peaks, int32_t *counts,
                                int32_t *assign, ht_zres *zres, uint64_t *stats,
                                ht_stream stream);
+
+/* ht_batch_run with the vote of each hit restricted to its region set:
+ * hit_masks (device, h_off[n_events] uint64 indexed like x, 8-byte aligned)
+ * as in ht_vote_hit_masked.  Peak finding, association and the z vote run
+ * as in ht_batch_run on the restricted accumulator.  Errors: as
+ * ht_batch_run. */
+ht_status ht_batch_run_hit_masked(ht_batch *b, const float *x, const float *y, const float *z,
+                                  const int32_t *h_off, int32_t n_events,
+                                  const uint64_t *hit_masks, ht_peak *peaks, int32_t *counts,
+                                  int32_t *assign, ht_zres *zres, uint64_t *stats,
+                                  ht_stream stream);
+
+/* The per-hit proposal used by ht_batch_run_learned_hits. */
+typedef struct ht_hit_proposal {
+    const void *params_bf16;  /* device, ht_mlp_param_count() BF16 values */
+    const uint8_t *layer;     /* device, layer index of every hit (like x) */
+    int32_t topk;             /* regions per hit, >= 1 (>= 64: every region) */
+    float pmin;               /* top-k output sum below pmin: every region */
+} ht_hit_proposal;
+
+/* ht_batch_run_hit_masked with the region sets computed at the head of the
+ * same graph by ht_mlp_hit_masks (proposal *prop) and written to hit_masks
+ * (device, h_off[n_events] uint64).  topk and pmin are part of the captured
+ * graph.  Errors: as ht_batch_run. */
+ht_status ht_batch_run_learned_hits(ht_batch *b, const float *x, const float *y, const float *z,
+                                    const int32_t *h_off, int32_t n_events,
+                                    const ht_hit_proposal *prop, uint64_t *hit_masks,
+                                    ht_peak *peaks, int32_t *counts, int32_t *assign,
+                                    ht_zres *zres, uint64_t *stats, ht_stream stream);
 
 /* Device time of the stages of the last completed batch run, in ms: ms[0]
  * proposal (0 without one), ms[1] vote, ms[2] peak finding and candidate

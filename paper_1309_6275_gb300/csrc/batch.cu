@@ -13,7 +13,10 @@
 // Masked and learned runs: the vote and the peak finding take a per-event
 // region mask (given by the caller, or computed at the head of the same
 // graph by the proposal MLP from the hits); association and the z vote run
-// unchanged on the masked candidates.
+// unchanged on the masked candidates.  Per-hit runs: the vote takes one
+// region set per hit (given, or the proposal MLP's top-k regions of each
+// hit); peak finding, association and the z vote run unchanged on the
+// restricted accumulator.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -57,6 +60,15 @@ cudaError_t launch_region_mask(const void *params_bf16, const float *x, const fl
                                const float *z, const uint8_t *layer, const int *off, int n_ev,
                                int max_hits, float tau, float fmax, int grow, float *mass,
                                unsigned long long *masks, cudaStream_t st);
+cudaError_t launch_vote_batch_hitmask(const DevGeom &G, const float *x, const float *y,
+                                      const int *off, const int *order, const int *d_nev,
+                                      uint16_t *acc, size_t acc_stride,
+                                      unsigned long long *stats, int *head, bool pack, int kt,
+                                      int sms, const unsigned long long *hit_masks,
+                                      cudaStream_t st);
+cudaError_t launch_hit_masks(const void *params_bf16, const float *x, const float *y,
+                             const float *z, const uint8_t *layer, int n, const int *d_n,
+                             int topk, float pmin, unsigned long long *hit_masks, cudaStream_t st);
 }  // namespace ht
 
 namespace {
@@ -69,9 +81,17 @@ constexpr int kStages = 5;   // proposal, vote, peaks + lists, association, z vo
 struct GraphEntry {
     int n_ev;
     const void *ptr[12];
-    float tau, fmax;
-    int grow;
+    float tau, fmax, pmin;
+    int grow, topk;
     cudaGraphExec_t exec;
+};
+
+// What restricts the vote of one run (all null: the plain path).
+struct Restrict {
+    unsigned long long *masks;        // per event
+    const ht_proposal *prop;          // writes masks first
+    unsigned long long *hit_masks;    // per hit
+    const ht_hit_proposal *hprop;     // writes hit_masks first
 };
 
 }  // namespace
@@ -144,14 +164,16 @@ void clear_graphs(ht_batch *b)
     b->ncache = 0;
 }
 
-// Every launch of one batch, in order, on stream st.  masks: null (plain
-// vote) or one region mask per event, written first by the proposal when
-// prop is set.
+// Every launch of one batch, in order, on stream st.  R.masks: null or one
+// region mask per event, written first by the proposal when R.prop is set;
+// R.hit_masks: null or one region set per hit, written first by the
+// proposal when R.hprop is set.
 cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z, int n_ev,
                     ht_peak *peaks, int32_t *counts, int32_t *assign, ht_zres *zres,
-                    uint64_t *stats, unsigned long long *masks, const ht_proposal *prop,
-                    cudaStream_t st, bool capturing)
+                    uint64_t *stats, const Restrict &R, cudaStream_t st, bool capturing)
 {
+    unsigned long long *masks = R.masks;
+    const ht_proposal *prop = R.prop;
     // stage timers: inside a capture they must become graph nodes
     auto mark = [&](int i) {
         return capturing ? cudaEventRecordWithFlags(b->stage[i], st, cudaEventRecordExternal)
@@ -172,10 +194,18 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
                                    st);
         if (e != cudaSuccess) return e;
     }
+    if (R.hprop) {
+        e = ht::launch_hit_masks(R.hprop->params_bf16, x, y, z, R.hprop->layer, b->max_hits,
+                                 off + n_ev, R.hprop->topk, R.hprop->pmin, R.hit_masks, st);
+        if (e != cudaSuccess) return e;
+    }
     e = mark(1);
     if (e != cudaSuccess) return e;
     // vote: events above the packed-counter limit, then the others
     auto vote = [&](const int *order, const int *d_nev, int *head, bool pack, int kt) {
+        if (R.hit_masks)
+            return ht::launch_vote_batch_hitmask(G, x, y, off, order, d_nev, b->acc, b->cells,
+                                                 st64, head, pack, kt, b->sms, R.hit_masks, st);
         return masks ? ht::launch_vote_batch_masked(G, x, y, off, order, d_nev, b->acc, b->cells,
                                                     st64, head, pack, kt, b->sms, masks, st)
                      : ht::launch_vote_batch(G, x, y, off, order, d_nev, b->acc, b->cells, st64,
@@ -350,35 +380,45 @@ ht_status ht_batch_set_graphs(ht_batch *b, int32_t enable)
 namespace {
 
 ht_status run_impl(ht_batch *b, const float *x, const float *y, const float *z,
-                   const int32_t *h_off, int32_t n_events, unsigned long long *masks,
-                   const ht_proposal *prop, ht_peak *peaks, int32_t *counts, int32_t *assign,
-                   ht_zres *zres, uint64_t *stats, ht_stream stream)
+                   const int32_t *h_off, int32_t n_events, const Restrict &R, ht_peak *peaks,
+                   int32_t *counts, int32_t *assign, ht_zres *zres, uint64_t *stats,
+                   ht_stream stream)
 {
     if (!b || !x || !y || !z || !peaks || !counts || !assign || !zres)
         return ht::set_error(HT_ERR_ARG, "ht_batch_run: null argument");
     if (n_events < 1 || n_events > b->max_events)
         return ht::set_error(HT_ERR_ARG, "ht_batch_run: n_events out of range");
-    if (prop && (!prop->params_bf16 || !prop->layer || !masks))
+    const ht_proposal *prop = R.prop;
+    if (prop && (!prop->params_bf16 || !prop->layer || !R.masks))
         return ht::set_error(HT_ERR_ARG, "ht_batch_run_learned: null proposal argument");
+    if (R.hprop && (!R.hprop->params_bf16 || !R.hprop->layer || !R.hit_masks ||
+                    R.hprop->topk < 1))
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run_learned_hits: bad proposal argument");
+    if (R.hit_masks && (reinterpret_cast<uintptr_t>(R.hit_masks) & 7u))
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run_hit_masked: hit_masks not 8-byte aligned");
     ht_status s = check_offsets(b, h_off, n_events);
     if (s != HT_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     s = stage_meta(b, h_off, n_events, st);
     if (s != HT_OK) return s;
     if (!b->use_graph) {
-        cudaError_t e = enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, masks,
-                                prop, st, false);
+        cudaError_t e = enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats, R, st,
+                                false);
         return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     }
-    const void *key[12] = {x,     y,     z,     peaks, counts,
-                           assign, zres, stats, masks, prop ? prop->params_bf16 : nullptr,
-                           prop ? prop->layer : nullptr, nullptr};
+    const void *params = prop ? prop->params_bf16 : R.hprop ? R.hprop->params_bf16 : nullptr;
+    const void *layer = prop ? (const void *)prop->layer
+                             : R.hprop ? (const void *)R.hprop->layer : nullptr;
+    const void *key[12] = {x,     y,     z,     peaks,  counts, assign,
+                           zres,  stats, R.masks, params, layer,  R.hit_masks};
     const float tau = prop ? prop->tau : 0.f, fmax = prop ? prop->fmax : 0.f;
     const int grow = prop ? prop->grow : 0;
+    const int topk = R.hprop ? R.hprop->topk : 0;
+    const float pmin = R.hprop ? R.hprop->pmin : 0.f;
     for (int i = 0; i < b->ncache; ++i) {
         GraphEntry &c = b->cache[i];
         if (c.n_ev == n_events && memcmp(c.ptr, key, sizeof key) == 0 && c.tau == tau &&
-            c.fmax == fmax && c.grow == grow) {
+            c.fmax == fmax && c.grow == grow && c.topk == topk && c.pmin == pmin) {
             cudaError_t e = cudaGraphLaunch(c.exec, st);
             return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
         }
@@ -390,7 +430,7 @@ ht_status run_impl(ht_batch *b, const float *x, const float *y, const float *z,
     cudaError_t e = cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         const cudaError_t eq = enqueue(b, x, y, z, n_events, peaks, counts, assign, zres, stats,
-                                       masks, prop, b->cap_stream, true);
+                                       R, b->cap_stream, true);
         e = cudaStreamEndCapture(b->cap_stream, &graph);
         if (eq != cudaSuccess) e = eq;
     }
@@ -408,6 +448,8 @@ ht_status run_impl(ht_batch *b, const float *x, const float *y, const float *z,
     c.tau = tau;
     c.fmax = fmax;
     c.grow = grow;
+    c.topk = topk;
+    c.pmin = pmin;
     c.exec = exec;
     e = cudaGraphLaunch(exec, st);
     return e == cudaSuccess ? HT_OK : ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
@@ -421,8 +463,8 @@ ht_status ht_batch_run(ht_batch *b, const float *x, const float *y, const float 
                        const int32_t *h_off, int32_t n_events, ht_peak *peaks, int32_t *counts,
                        int32_t *assign, ht_zres *zres, uint64_t *stats, ht_stream stream)
 {
-    return run_impl(b, x, y, z, h_off, n_events, nullptr, nullptr, peaks, counts, assign, zres,
-                    stats, stream);
+    return run_impl(b, x, y, z, h_off, n_events, Restrict{}, peaks, counts, assign, zres, stats,
+                    stream);
 }
 
 ht_status ht_batch_run_masked(ht_batch *b, const float *x, const float *y, const float *z,
@@ -431,9 +473,9 @@ ht_status ht_batch_run_masked(ht_batch *b, const float *x, const float *y, const
                               uint64_t *stats, ht_stream stream)
 {
     if (!masks) return ht::set_error(HT_ERR_ARG, "ht_batch_run_masked: null masks");
-    return run_impl(b, x, y, z, h_off, n_events,
-                    reinterpret_cast<unsigned long long *>(const_cast<uint64_t *>(masks)), nullptr,
-                    peaks, counts, assign, zres, stats, stream);
+    Restrict R{};
+    R.masks = reinterpret_cast<unsigned long long *>(const_cast<uint64_t *>(masks));
+    return run_impl(b, x, y, z, h_off, n_events, R, peaks, counts, assign, zres, stats, stream);
 }
 
 ht_status ht_batch_run_learned(ht_batch *b, const float *x, const float *y, const float *z,
@@ -442,8 +484,35 @@ ht_status ht_batch_run_learned(ht_batch *b, const float *x, const float *y, cons
                                ht_zres *zres, uint64_t *stats, ht_stream stream)
 {
     if (!prop) return ht::set_error(HT_ERR_ARG, "ht_batch_run_learned: null proposal");
-    return run_impl(b, x, y, z, h_off, n_events, reinterpret_cast<unsigned long long *>(masks),
-                    prop, peaks, counts, assign, zres, stats, stream);
+    Restrict R{};
+    R.masks = reinterpret_cast<unsigned long long *>(masks);
+    R.prop = prop;
+    return run_impl(b, x, y, z, h_off, n_events, R, peaks, counts, assign, zres, stats, stream);
+}
+
+ht_status ht_batch_run_hit_masked(ht_batch *b, const float *x, const float *y, const float *z,
+                                  const int32_t *h_off, int32_t n_events,
+                                  const uint64_t *hit_masks, ht_peak *peaks, int32_t *counts,
+                                  int32_t *assign, ht_zres *zres, uint64_t *stats,
+                                  ht_stream stream)
+{
+    if (!hit_masks) return ht::set_error(HT_ERR_ARG, "ht_batch_run_hit_masked: null hit_masks");
+    Restrict R{};
+    R.hit_masks = reinterpret_cast<unsigned long long *>(const_cast<uint64_t *>(hit_masks));
+    return run_impl(b, x, y, z, h_off, n_events, R, peaks, counts, assign, zres, stats, stream);
+}
+
+ht_status ht_batch_run_learned_hits(ht_batch *b, const float *x, const float *y, const float *z,
+                                    const int32_t *h_off, int32_t n_events,
+                                    const ht_hit_proposal *prop, uint64_t *hit_masks,
+                                    ht_peak *peaks, int32_t *counts, int32_t *assign,
+                                    ht_zres *zres, uint64_t *stats, ht_stream stream)
+{
+    if (!prop) return ht::set_error(HT_ERR_ARG, "ht_batch_run_learned_hits: null proposal");
+    Restrict R{};
+    R.hit_masks = reinterpret_cast<unsigned long long *>(hit_masks);
+    R.hprop = prop;
+    return run_impl(b, x, y, z, h_off, n_events, R, peaks, counts, assign, zres, stats, stream);
 }
 
 ht_status ht_batch_stage_ms(const ht_batch *b, float *ms)

@@ -239,6 +239,29 @@ ht_status ht_vote_masked(const ht_geometry *g, const float *x, const float *y, i
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_masked");
 }
 
+ht_status ht_vote_hit_masked(const ht_geometry *g, const float *x, const float *y,
+                             int32_t n_hits, const uint64_t *hit_masks, void *acc,
+                             uint64_t *stats, ht_stream stream)
+{
+    if (!g || !acc) return fail(HT_ERR_ARG, "ht_vote_hit_masked: null geometry or accumulator");
+    if (n_hits < 0 || n_hits > kMaxHits)
+        return fail(HT_ERR_ARG, "ht_vote_hit_masked: n_hits %d outside [0, %d]", n_hits,
+                    kMaxHits);
+    if (n_hits > 0 && (!x || !y || !hit_masks))
+        return fail(HT_ERR_ARG, "ht_vote_hit_masked: null hit arrays");
+    if (!aligned(acc, 16) || (x && !aligned(x, 16)) || (y && !aligned(y, 16)) ||
+        (hit_masks && !aligned(hit_masks, 8)))
+        return fail(HT_ERR_ARG, "ht_vote_hit_masked: pointer alignment");
+    cudaError_t e = cudaSuccess;
+    if (stats) e = cudaMemsetAsync(stats, 0, 2 * sizeof(uint64_t), S(stream));
+    if (e == cudaSuccess)
+        e = ht::launch_vote_hitmask(g->G, x, y, n_hits, acc,
+                                    reinterpret_cast<unsigned long long *>(stats),
+                                    reinterpret_cast<const unsigned long long *>(hit_masks),
+                                    S(stream));
+    return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_hit_masked");
+}
+
 size_t ht_find_peaks_workspace_size(const ht_geometry *g)
 {
     return g ? ht::peaks_workspace_bytes(g->G) : 0;

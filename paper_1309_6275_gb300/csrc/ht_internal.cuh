@@ -307,6 +307,10 @@ cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n,
 cudaError_t launch_vote_masked(const DevGeom &G, const float *x, const float *y, int n,
                                void *acc, unsigned long long *stats,
                                const unsigned long long *mask, cudaStream_t st);
+// Per-hit vote: hit h's votes count only in the halo cells of hit_masks[h].
+cudaError_t launch_vote_hitmask(const DevGeom &G, const float *x, const float *y, int n,
+                                void *acc, unsigned long long *stats,
+                                const unsigned long long *hit_masks, cudaStream_t st);
 // mask (device, or null for every cell): only peaks inside it are reported.
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
                          int *d_count, void *ws, cudaStream_t st,

@@ -408,7 +408,7 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
 
     int parity = 0;
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
-        collect<KT, true>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W, &M);
+        collect<KT, kModeEvent>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W, &M);
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;
@@ -564,7 +564,7 @@ cudaError_t prepare_tile_kernels(int max_smem)
                          (const void *)k_assoc32<2>, (const void *)k_assoc32<1>,
                          (const void *)k_cand_hist};
     const cudaError_t e = allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
-    return e == cudaSuccess ? prepare_vote_kernels_t<false>(max_smem) : e;
+    return e == cudaSuccess ? prepare_vote_kernels_t<kModePlain>(max_smem) : e;
 }
 
 // Largest tile shared memory any geometry with n_d0 bins needs.
@@ -577,7 +577,7 @@ size_t tile_smem_need(const DevGeom &G)
 cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                         unsigned long long *stats, cudaStream_t st)
 {
-    return launch_vote_t<false>(G, x, y, n, acc, stats, nullptr, st);
+    return launch_vote_t<kModePlain>(G, x, y, n, acc, stats, nullptr, st);
 }
 
 // Association workspace: per-hit best keys, then (uint16 geometries) the
@@ -628,8 +628,8 @@ cudaError_t launch_vote_batch(const DevGeom &G, const float *x, const float *y, 
                               size_t acc_stride, unsigned long long *stats, int *head, bool pack,
                               int kt, int sms, cudaStream_t st)
 {
-    return launch_vote_batch_t<false>(G, x, y, off, order, d_nev, acc, acc_stride, stats, head,
-                                      pack, kt, sms, nullptr, st);
+    return launch_vote_batch_t<kModePlain>(G, x, y, off, order, d_nev, acc, acc_stride, stats,
+                                           head, pack, kt, sms, nullptr, st);
 }
 
 // Association tile width for uint16 geometries (largest fitting three CTAs

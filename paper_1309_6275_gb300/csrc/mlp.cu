@@ -1,12 +1,13 @@
 // mlp.cu -- the learned region proposal: a per-hit MLP 6 -> 128 -> 128 -> 64
 // over (rho, d0) regions, its training kernels and the per-event region mask
-// (ht_mlp_* in include/ht.h).  The paper has no learned part; this is the
-// proposal's own reading.
+// and per-hit region sets (ht_mlp_* in include/ht.h).  The paper has no
+// learned part; this is the proposal's own reading.
 //
 // Numerics: BF16 weights and BF16 activations between layers, products of
 // BF16 values exact in float32, float32 accumulation (tensor memory for the
-// forward pass's 128-wide layers), float32 logits and softmax.  Features: x/110, y/110, z/(110 sinh 2.5), r/110, phi/pi, layer/9,
-// each computed in float32 (no contraction) and rounded to BF16.
+// forward pass's 128-wide layers), float32 logits and softmax.  Features:
+// x/110, y/110, z/(110 sinh 2.5), r/110, phi/pi, layer/9, each computed in
+// float32 (no contraction) and rounded to BF16.
 //
 // Layout of the flat parameter array (float32 master and BF16 copy):
 // W1[6][128] b1[128] W2[128][128] b2[128] W3[128][64] b3[64], W[i][o]
@@ -50,6 +51,9 @@ struct FwdOut {
     const int *off;          // event offsets when mass is set
     int n_ev;
     const int *d_n;          // (or null) device hit count, read instead of n
+    unsigned long long *hmask;   // per-hit top-k region sets (or null)
+    int topk;                    // regions per hit; >= 64: every region
+    float pmin;                  // top-k mass below this: every region
 };
 
 __device__ __forceinline__ int event_of_hit(const int *off, int n_ev, int h)
@@ -273,6 +277,25 @@ cudaError_t launch_region_mask(const void *params_bf16, const float *x, const fl
     return cudaGetLastError();
 }
 
+// Per-hit region sets: the proposal network's top-k regions of every hit.
+// n hits, or *d_n when d_n is set (n then bounds the grid).
+cudaError_t launch_hit_masks(const void *params_bf16, const float *x, const float *y,
+                             const float *z, const uint8_t *layer, int n, const int *d_n,
+                             int topk, float pmin, unsigned long long *hit_masks, cudaStream_t st)
+{
+    cudaError_t e = mlp_ready();
+    if (e != cudaSuccess || n <= 0) return e;
+    FwdOut o{};
+    o.d_n = d_n;
+    o.hmask = hit_masks;
+    o.topk = topk;
+    o.pmin = pmin;
+    const int blocks = min((n + kTcM - 1) / kTcM, 152 * 2);
+    k_mlp_fwd_tc<<<blocks, kTcM, kTcSmem, st>>>((const __nv_bfloat16 *)params_bf16, x, y, z,
+                                                layer, n, o);
+    return cudaGetLastError();
+}
+
 cudaError_t prepare_mlp_kernels()
 {
     cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -331,6 +354,20 @@ ht_status ht_mlp_region_mask(const void *params_bf16, const float *x, const floa
                                              tau, fmax, grow, mass,
                                              reinterpret_cast<unsigned long long *>(masks),
                                              reinterpret_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+}
+
+ht_status ht_mlp_hit_masks(const void *params_bf16, const float *x, const float *y,
+                           const float *z, const uint8_t *layer, int32_t n_hits, int32_t topk,
+                           float pmin, uint64_t *hit_masks, ht_stream stream)
+{
+    if (!params_bf16 || n_hits < 0 || topk < 1 ||
+        (n_hits > 0 && (!x || !y || !z || !layer || !hit_masks)))
+        return set_error(HT_ERR_ARG, "ht_mlp_hit_masks: bad argument");
+    const cudaError_t e = launch_hit_masks(params_bf16, x, y, z, layer, n_hits, nullptr, topk,
+                                           pmin,
+                                           reinterpret_cast<unsigned long long *>(hit_masks),
+                                           reinterpret_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));
 }
 

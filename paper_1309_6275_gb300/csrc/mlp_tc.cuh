@@ -269,6 +269,30 @@ k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ x,
         const float is = __frcp_rn(s);
 #pragma unroll
         for (int c = 0; c < kOut; ++c) lg[c] *= is;
+        if (act && out.hmask) {
+            // top-k regions: k passes of a first-maximum scan (ties go to the
+            // smaller region), then the fallback on their summed probability
+            unsigned long long sel = ~0ull;
+            if (out.topk < kOut) {
+                sel = 0ull;
+                float sum = 0.f;
+                for (int t = 0; t < out.topk; ++t) {
+                    float best = -1.f;
+                    int bi = 0;
+#pragma unroll
+                    for (int c = 0; c < kOut; ++c) {
+                        if (!((sel >> c) & 1ull) && lg[c] > best) {
+                            best = lg[c];
+                            bi = c;
+                        }
+                    }
+                    sel |= 1ull << bi;
+                    sum += best;
+                }
+                if (sum < out.pmin) sel = ~0ull;
+            }
+            out.hmask[h] = sel;
+        }
         if (act && out.prob) {
             float4 *pp = reinterpret_cast<float4 *>(out.prob + (size_t)h * kOut);
 #pragma unroll
@@ -280,7 +304,31 @@ k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ x,
             for (int c = tid; c < kOut; c += kTcM) smass[c] = 0.f;
             __syncthreads();
             const int e = act ? event_of_hit(out.off, out.n_ev, h) : -1;
-            if (act) {
+            if (__all_sync(0xffffffffu, !act || e == sev)) {
+                // the warp's hits are all in event sev: reduce-scatter the 64
+                // sums over the warp (halves exchanged with lane ^ 16, 8, 4,
+                // 2, 1; the lane with that bit set keeps the upper half),
+                // after which lane l holds the sums of regions 2l and 2l + 1
+                const int lane = tid & 31;
+#pragma unroll
+                for (int c = 0; c < kOut; ++c) lg[c] = act ? lg[c] : 0.f;
+#pragma unroll
+                for (int st = 0; st < 5; ++st) {
+                    const int hs = 32 >> st, po = 16 >> st;
+                    const bool up = (lane & po) != 0;
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        if (i < hs) {
+                            const float send = up ? lg[i] : lg[i + hs];
+                            const float keep = up ? lg[i + hs] : lg[i];
+                            lg[i] = keep + __shfl_xor_sync(0xffffffffu, send, po);
+                        }
+                    }
+                }
+                const int c0 = 2 * lane;
+                atomicAdd(&smass[c0], lg[0]);
+                atomicAdd(&smass[c0 + 1], lg[1]);
+            } else if (act) {
                 if (e == sev) {
 #pragma unroll
                     for (int c = 0; c < kOut; ++c) atomicAdd(&smass[c], lg[c]);

@@ -15,6 +15,13 @@ namespace {
 
 constexpr int kThreads = 256;
 
+// Vote modes: the plain vote; one region mask per event (MaskCtx: only halo
+// cells of the mask exact); one region set per hit (HitCtx: each hit votes
+// only in the halo cells of its own regions, on the 8 x 8 grid of
+// ht_internal.cuh).  Association replays votes under kModeEvent with a
+// candidate-box window in MaskCtx.
+constexpr int kModePlain = 0, kModeEvent = 1, kModeHit = 2;
+
 template <typename OutT>
 __device__ __forceinline__ OutT saturate(uint32_t v)
 {
@@ -24,12 +31,18 @@ __device__ __forceinline__ OutT saturate(uint32_t v)
 
 // Shared work list of (hit, column) items.
 struct WorkList {
-    float4 *a, *b;   // Item fields {s, c, r2, eD}, {E1, E2, Qa, Qb}
-    int *meta;       // hit << 6 | needB << 5 | unsure << 4 | column-in-tile
+    float4 *a, *b;           // Item fields {s, c, r2, eD}, {E1, E2, Qa, Qb}
+    int *meta;               // hit << 6 | needB << 5 | unsure << 4 | column-in-tile
+    unsigned long long *hm;  // kModeHit: the hit's region set
 };
 
 constexpr int kMetaUnsure = 16, kMetaNeedB = 32, kMetaCol = 15;
 constexpr size_t kItemBytes = 36;
+
+__host__ __device__ constexpr size_t item_bytes(int mode)
+{
+    return kItemBytes + (mode == kModeHit ? 8 : 0);
+}
 
 __device__ __forceinline__ WorkList carve_worklist(unsigned char *p, int cap)
 {
@@ -37,6 +50,7 @@ __device__ __forceinline__ WorkList carve_worklist(unsigned char *p, int cap)
     w.a = reinterpret_cast<float4 *>(p);
     w.b = w.a + cap;
     w.meta = reinterpret_cast<int *>(w.b + cap);
+    w.hm = reinterpret_cast<unsigned long long *>(w.meta + cap);   // cap is a multiple of 2
     return w;
 }
 
@@ -115,20 +129,57 @@ struct MaskCtx {
     }
 };
 
+// Per-hit region sets as one vote tile sees them.  Phase 1 (lane = hit)
+// ORs the hit's d0-block bits over the rho blocks of the tile's rows and
+// their one-row halo; a hit with none votes nowhere in the tile, the others
+// get one d0 window (their blocks' span widened by the one-bin halo) for the
+// curvature filter.  Phase 2 (lane = row) keeps a bin j of the lane's row
+// when bm & jmask[j] != 0, bm being the hit's d0 blocks over the row's rho
+// block and its neighbours' (shifts sh[]) and jmask[j] the blocks of bins
+// j - 1, j, j + 1 (a shared table).
+struct HitCtx {
+    const unsigned long long *masks;   // the event's per-hit region sets
+    const uint8_t *jmask;              // [n_d0], shared
+    int rb_lo, rb_hi;                  // rho blocks of rows i0 - 1 .. i0 + 32 (clamped)
+    int sh[3];                         // 8 x rho block of rows irow - 1, irow, irow + 1
+    float w_lo0, w_step;               // d0 (cm) of bin 0's lower edge, bin width
+
+    __device__ __forceinline__ unsigned row_bits(unsigned long long hm) const
+    {
+        return (unsigned)((hm >> sh[0]) | (hm >> sh[1]) | (hm >> sh[2])) & 0xffu;
+    }
+};
+
 // Phase 1 for hit h (h >= n: no items).  Appends this warp's items to the
 // list with a single atomicAdd on *qn (all 32 lanes must call).
-template <int KT, bool MASKED = false>
+template <int KT, int MODE = kModePlain>
 __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
                                         const float *__restrict__ x,
                                         const float *__restrict__ y, int n, int h,
                                         int lane, int *qn, const WorkList &W,
-                                        const MaskCtx *M = nullptr)
+                                        const MaskCtx *M = nullptr, const HitCtx *H = nullptr)
 {
     float is_[KT], ic_[KT];
     int fl_[KT];
     unsigned sel = 0u;
     float r2 = 0.0f, R1 = 0.0f;
-    if (h < n) {
+    unsigned long long hm = 0ull;
+    float hwlo = 0.0f, hwhi = 0.0f;
+    bool live = h < n;
+    if (MODE == kModeHit && live) {
+        hm = H->masks[h];
+        unsigned tb = 0u;
+        for (int b = H->rb_lo; b <= H->rb_hi; ++b) tb |= (unsigned)(hm >> (8 * b)) & 0xffu;
+        live = tb != 0u;
+        if (live) {
+            const int ND = G.n_d0;
+            const int lo = max(block_first(__ffs(tb) - 1, ND) - 1, 0);
+            const int hi = min(block_first(32 - __clz(tb), ND), ND - 1);
+            hwlo = fmaf((float)lo, H->w_step, H->w_lo0) - 0.01f;
+            hwhi = fmaf((float)(hi + 1), H->w_step, H->w_lo0) + 0.01f;
+        }
+    }
+    if (live) {
         const float xh = x[h], yh = y[h];
         r2 = fmaf(xh, xh, yh * yh);
         R1 = fabsf(xh) + fabsf(yh);
@@ -144,7 +195,10 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
                 f |= kMetaUnsure;
             } else if (c > 1.0f) {
                 float gmin, gmax;
-                if (MASKED) {
+                if (MODE == kModeHit) {
+                    rho_range_w(hwlo + s, hwhi + s, c, gmin, gmax);
+                    if (gmax < T.rho_lo || gmin > T.rho_hi) continue;
+                } else if (MODE == kModeEvent) {
                     bool reach = false;
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
@@ -184,6 +238,7 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
             W.a[pos] = make_float4(it.s, it.c, it.r2, it.eD);
             W.b[pos] = make_float4(it.E1, it.E2, it.Qa, it.Qb);
             W.meta[pos] = (h << 6) | fl_[kl] | kl;
+            if (MODE == kModeHit) W.hm[pos] = hm;
             ++pos;
         }
     }
@@ -255,14 +310,27 @@ __device__ __forceinline__ uint32_t tile_get(const uint32_t *cnt, int ND, int kl
     return cnt[(kl * ND + j) * 32 + il];
 }
 
-// MASKED: only halo cells of `mask` are exact (others get 0 or a partial
+// Keep the bins jj[0 .. nv) that the hit's region set allows in the lane's
+// row (kModeHit); returns the new count.
+__device__ __forceinline__ int keep_allowed(unsigned bm, const uint8_t *jmask, int nv, int jj[2])
+{
+    int k = 0;
+    if (nv > 0 && (bm & jmask[jj[0]])) jj[k++] = jj[0];
+    if (nv > 1 && (bm & jmask[jj[1]])) jj[k++] = jj[1];
+    return k;
+}
+
+// kModeEvent: only halo cells of `mask` are exact (others get 0 or a partial
 // count); a tile without halo cells returns at once and writes nothing.
-template <int KT, typename OutT, bool PACK, bool MASKED = false>
+// kModeHit: hit h's votes count only in the halo cells of hmask[h]; every
+// cell is written.
+template <int KT, typename OutT, bool PACK, int MODE = kModePlain>
 __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restrict__ x,
                                           const float *__restrict__ y, int n,
                                           OutT *__restrict__ acc,
                                           unsigned long long *__restrict__ stats, int tx, int ty,
-                                          unsigned long long mask = ~0ull)
+                                          unsigned long long mask = ~0ull,
+                                          const unsigned long long *__restrict__ hmask = nullptr)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
@@ -271,7 +339,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][NW][32]
     unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * NW * 32);
     const WorkList W = carve_worklist(p, QCAP);
-    const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
+    const RedoQueue R = carve_redo(p + (size_t)QCAP * item_bytes(MODE));
     __shared__ int qn[2], rn;
     __shared__ unsigned long long s_stats[2];
 
@@ -280,9 +348,28 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     TileCtx<KT> T;
     T.init(G, lane, tx, ty);
     MaskCtx M;
-    if (MASKED) {
+    if (MODE == kModeEvent) {
         M.init(G, mask, T.i0, T.irow, T.row_ok);
         if (M.tile_bm == 0u) return;   // uniform: every warp sees the same rows
+    }
+    HitCtx H;
+    if (MODE == kModeHit) {
+        const int NR = G.n_rho;
+        uint8_t *jm = p + (size_t)QCAP * item_bytes(MODE) + kRedoBytes;
+        for (int j = threadIdx.x; j < ND; j += kThreads)
+            jm[j] = (uint8_t)((1u << region_block(max(j - 1, 0), ND)) |
+                              (1u << region_block(j, ND)) |
+                              (1u << region_block(min(j + 1, ND - 1), ND)));
+        H.masks = hmask;
+        H.jmask = jm;
+        H.rb_lo = region_block(max(T.i0 - 1, 0), NR);
+        H.rb_hi = region_block(min(T.i0 + 32, NR - 1), NR);
+        const int ir = min(T.irow, NR - 1);
+        H.sh[0] = 8 * region_block(max(ir - 1, 0), NR);
+        H.sh[1] = 8 * region_block(ir, NR);
+        H.sh[2] = 8 * region_block(min(ir + 1, NR - 1), NR);
+        H.w_step = G.delta_f;
+        H.w_lo0 = -G.off_f * G.delta_f;
     }
     {
         uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
@@ -298,7 +385,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     int my_fb = 0;
     int parity = 0;
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
-        collect<KT, MASKED>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W, &M);
+        collect<KT, MODE>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W, &M, &H);
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;   // last read before the previous barrier
@@ -314,6 +401,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                     if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
                     nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
                 }
+                if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
                 if (nv > 0) tile_add<PACK>(col, jj[0]);
                 if (nv > 1) tile_add<PACK>(col, jj[1]);
             }
@@ -326,7 +414,10 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                 const int h = R.hit[t], rc = R.rc[t];
                 const int il = rc >> 4, kl = rc & 15;
                 int jj[2];
-                const int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
+                int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
+                if (MODE == kModeHit)
+                    nv = keep_allowed(halo_row_blocks(H.masks[h], T.i0 + il, G.n_rho), H.jmask, nv,
+                                      jj);
                 uint32_t *col = cnt + kl * NW * 32 + il;
                 for (int v = 0; v < nv; ++v) tile_add<PACK>(col, jj[v]);
             }
@@ -344,7 +435,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         const int il = t & 31, j = t >> 5;   // il == lane
         const int i = T.i0 + il;
         if (i >= G.n_rho) continue;
-        const bool keep = !MASKED || halo_bin(M.bm, j, ND);
+        const bool keep = MODE != kModeEvent || halo_bin(M.bm, j, ND);
         __align__(16) OutT e[KT];
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
@@ -380,21 +471,23 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     }
 }
 
-template <int KT, typename OutT, bool PACK, bool MASKED>
+// mask: kModeEvent one device uint64, kModeHit one per hit, else unused.
+template <int KT, typename OutT, bool PACK, int MODE>
 __global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
 k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
        OutT *__restrict__ acc, unsigned long long *__restrict__ stats,
        const unsigned long long *__restrict__ mask)
 {
-    vote_tile<KT, OutT, PACK, MASKED>(G, x, y, n, acc, stats, blockIdx.x, blockIdx.y,
-                                      MASKED ? *mask : ~0ull);
+    vote_tile<KT, OutT, PACK, MODE>(G, x, y, n, acc, stats, blockIdx.x, blockIdx.y,
+                                    MODE == kModeEvent ? *mask : ~0ull, mask);
 }
 
 // Persistent vote over a batch: CTAs pop (event, tile) items from a device
 // counter; items run event by event in the order given (largest events
 // first), so uneven events share the GPU without per-event launch tails.
-// MASKED: event e votes under masks[e].
-template <int KT, typename OutT, bool PACK, bool MASKED>
+// kModeEvent: event e votes under masks[e]; kModeHit: masks holds one region
+// set per hit of the batch (indexed like x).
+template <int KT, typename OutT, bool PACK, int MODE>
 __global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
 k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
              const int *__restrict__ off, const int *__restrict__ order,
@@ -412,30 +505,32 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
         if (item >= total) break;
         const int e = order[item / ntiles], t = item % ntiles;
         const int a = off[e], n = off[e + 1] - a;
-        vote_tile<KT, OutT, PACK, MASKED>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
-                                          stats ? stats + 2 * e : nullptr, t % ntx, t / ntx,
-                                          MASKED ? masks[e] : ~0ull);
+        vote_tile<KT, OutT, PACK, MODE>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
+                                        stats ? stats + 2 * e : nullptr, t % ntx, t / ntx,
+                                        MODE == kModeEvent ? masks[e] : ~0ull,
+                                        MODE == kModeHit ? masks + a : nullptr);
         __syncthreads();
     }
 }
 
 template <int KT>
-size_t vote_smem(const DevGeom &G, bool pack)
+size_t vote_smem(const DevGeom &G, bool pack, int mode = kModePlain)
 {
-    return (size_t)KT * 32 * (pack ? G.n_d0 / 2 : G.n_d0) * 4 + (size_t)kThreads * KT * kItemBytes +
-           kRedoBytes;
+    return (size_t)KT * 32 * (pack ? G.n_d0 / 2 : G.n_d0) * 4 +
+           (size_t)kThreads * KT * item_bytes(mode) + kRedoBytes +
+           (mode == kModeHit ? ((size_t)G.n_d0 + 15) / 16 * 16 : 0);
 }
 
 constexpr size_t kSmemBudget2 = 110 * 1024;   // two CTAs per SM
 constexpr size_t kSmemBudget3 = 75 * 1024;    // three CTAs per SM
 
-template <int KT, typename OutT, bool PACK, bool MASKED>
+template <int KT, typename OutT, bool PACK, int MODE>
 cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                            unsigned long long *stats, const unsigned long long *mask,
                            cudaStream_t st)
 {
     dim3 grid(G.n_phi0 / KT, (G.n_rho + 31) / 32);
-    k_vote<KT, OutT, PACK, MASKED><<<grid, kThreads, vote_smem<KT>(G, PACK), st>>>(
+    k_vote<KT, OutT, PACK, MODE><<<grid, kThreads, vote_smem<KT>(G, PACK, MODE), st>>>(
         G, x, y, n, reinterpret_cast<OutT *>(acc), stats, mask);
     return cudaGetLastError();
 }
@@ -443,25 +538,25 @@ cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int
 // Tile shape: packed 16-bit counters with three CTAs per SM when the output
 // is uint16, n_d0 even and n <= 32767; otherwise 32-bit counters, two CTAs
 // per SM.  KT is the widest tile that fits.
-template <bool MASKED>
+template <int MODE>
 cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                           unsigned long long *stats, const unsigned long long *mask,
                           cudaStream_t st)
 {
-#define HT_V(KTV, OT, PK) return launch_vote_kt<KTV, OT, PK, MASKED>(G, x, y, n, acc, stats, mask, st)
+#define HT_V(KTV, OT, PK) return launch_vote_kt<KTV, OT, PK, MODE>(G, x, y, n, acc, stats, mask, st)
     if (G.count_bits == 16) {
         if (n <= 32767 && G.n_d0 % 2 == 0) {
-            if (vote_smem<4>(G, true) <= kSmemBudget3) HT_V(4, uint16_t, true);
-            if (vote_smem<2>(G, true) <= kSmemBudget3) HT_V(2, uint16_t, true);
-            if (vote_smem<1>(G, true) <= kSmemBudget3) HT_V(1, uint16_t, true);
+            if (vote_smem<4>(G, true, MODE) <= kSmemBudget3) HT_V(4, uint16_t, true);
+            if (vote_smem<2>(G, true, MODE) <= kSmemBudget3) HT_V(2, uint16_t, true);
+            if (vote_smem<1>(G, true, MODE) <= kSmemBudget3) HT_V(1, uint16_t, true);
         }
-        if (vote_smem<8>(G, false) <= kSmemBudget2) HT_V(8, uint16_t, false);
-        if (vote_smem<4>(G, false) <= kSmemBudget2) HT_V(4, uint16_t, false);
-        if (vote_smem<2>(G, false) <= kSmemBudget2) HT_V(2, uint16_t, false);
+        if (vote_smem<8>(G, false, MODE) <= kSmemBudget2) HT_V(8, uint16_t, false);
+        if (vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_V(4, uint16_t, false);
+        if (vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_V(2, uint16_t, false);
         HT_V(1, uint16_t, false);
     }
-    if (vote_smem<4>(G, false) <= kSmemBudget2) HT_V(4, int32_t, false);
-    if (vote_smem<2>(G, false) <= kSmemBudget2) HT_V(2, int32_t, false);
+    if (vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_V(4, int32_t, false);
+    if (vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_V(2, int32_t, false);
     HT_V(1, int32_t, false);
 #undef HT_V
 }
@@ -470,7 +565,7 @@ cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int 
 // slot of the GPU (SMs x resident CTAs) pops items until the queue is empty.
 // kt selects the tile width (0 = default), pack the 16-bit packed counters
 // (valid when every listed event has <= 32767 hits).  *head must be zero.
-template <bool MASKED>
+template <int MODE>
 cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y, const int *off,
                                 const int *order, const int *d_nev, uint16_t *acc,
                                 size_t acc_stride, unsigned long long *stats, int *head,
@@ -481,25 +576,29 @@ cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y
     do {                                                                                      \
         int occ = 0;                                                                          \
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                        \
-            &occ, k_vote_batch<KTV, uint16_t, PK, MASKED>, kThreads, vote_smem<KTV>(G, PK));  \
-        k_vote_batch<KTV, uint16_t, PK, MASKED><<<sms * (occ > 0 ? occ : 1), kThreads,       \
-                                                  vote_smem<KTV>(G, PK), st>>>(               \
+            &occ, k_vote_batch<KTV, uint16_t, PK, MODE>, kThreads,                            \
+            vote_smem<KTV>(G, PK, MODE));                                                     \
+        k_vote_batch<KTV, uint16_t, PK, MODE><<<sms * (occ > 0 ? occ : 1), kThreads,         \
+                                                vote_smem<KTV>(G, PK, MODE), st>>>(           \
             G, x, y, off, order, d_nev, acc, acc_stride, stats, head, masks);                 \
         return cudaGetLastError();                                                            \
     } while (0)
     if (pack) {
-        if (kt == 0) kt = vote_smem<4>(G, true) <= kSmemBudget3 ? 4
-                        : vote_smem<2>(G, true) <= kSmemBudget3 ? 2 : 1;
-        if (kt == 4 && vote_smem<4>(G, true) <= kSmemBudget2) HT_VB(4, true);
-        if (kt >= 2 && vote_smem<2>(G, true) <= kSmemBudget2) HT_VB(2, true);
+        // the per-hit mode's larger items would drop a tuned width to two
+        // CTAs per SM: it keeps three
+        const size_t budget = MODE == kModeHit ? kSmemBudget3 : kSmemBudget2;
+        if (kt == 0) kt = vote_smem<4>(G, true, MODE) <= kSmemBudget3 ? 4
+                        : vote_smem<2>(G, true, MODE) <= kSmemBudget3 ? 2 : 1;
+        if (kt == 4 && vote_smem<4>(G, true, MODE) <= budget) HT_VB(4, true);
+        if (kt >= 2 && vote_smem<2>(G, true, MODE) <= budget) HT_VB(2, true);
         HT_VB(1, true);
     }
-    if (kt == 0) kt = vote_smem<8>(G, false) <= kSmemBudget2 ? 8
-                    : vote_smem<4>(G, false) <= kSmemBudget2 ? 4
-                    : vote_smem<2>(G, false) <= kSmemBudget2 ? 2 : 1;
-    if (kt == 8 && vote_smem<8>(G, false) <= kSmemBudget2) HT_VB(8, false);
-    if (kt >= 4 && vote_smem<4>(G, false) <= kSmemBudget2) HT_VB(4, false);
-    if (kt >= 2 && vote_smem<2>(G, false) <= kSmemBudget2) HT_VB(2, false);
+    if (kt == 0) kt = vote_smem<8>(G, false, MODE) <= kSmemBudget2 ? 8
+                    : vote_smem<4>(G, false, MODE) <= kSmemBudget2 ? 4
+                    : vote_smem<2>(G, false, MODE) <= kSmemBudget2 ? 2 : 1;
+    if (kt == 8 && vote_smem<8>(G, false, MODE) <= kSmemBudget2) HT_VB(8, false);
+    if (kt >= 4 && vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_VB(4, false);
+    if (kt >= 2 && vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_VB(2, false);
     HT_VB(1, false);
 #undef HT_VB
 }
@@ -519,27 +618,27 @@ inline cudaError_t allow_smem(const void *const *fns, int nf, int max_smem)
 
 // Allow every vote kernel the device's opt-in shared memory (each launch
 // still passes only what its tile needs).
-template <bool MASKED>
+template <int MODE>
 cudaError_t prepare_vote_kernels_t(int max_smem)
 {
     const void *fns[] = {
-        (const void *)k_vote<4, uint16_t, true, MASKED>,
-        (const void *)k_vote<2, uint16_t, true, MASKED>,
-        (const void *)k_vote<1, uint16_t, true, MASKED>,
-        (const void *)k_vote<8, uint16_t, false, MASKED>,
-        (const void *)k_vote<4, uint16_t, false, MASKED>,
-        (const void *)k_vote<2, uint16_t, false, MASKED>,
-        (const void *)k_vote<1, uint16_t, false, MASKED>,
-        (const void *)k_vote<4, int32_t, false, MASKED>,
-        (const void *)k_vote<2, int32_t, false, MASKED>,
-        (const void *)k_vote<1, int32_t, false, MASKED>,
-        (const void *)k_vote_batch<4, uint16_t, true, MASKED>,
-        (const void *)k_vote_batch<2, uint16_t, true, MASKED>,
-        (const void *)k_vote_batch<1, uint16_t, true, MASKED>,
-        (const void *)k_vote_batch<8, uint16_t, false, MASKED>,
-        (const void *)k_vote_batch<4, uint16_t, false, MASKED>,
-        (const void *)k_vote_batch<2, uint16_t, false, MASKED>,
-        (const void *)k_vote_batch<1, uint16_t, false, MASKED>};
+        (const void *)k_vote<4, uint16_t, true, MODE>,
+        (const void *)k_vote<2, uint16_t, true, MODE>,
+        (const void *)k_vote<1, uint16_t, true, MODE>,
+        (const void *)k_vote<8, uint16_t, false, MODE>,
+        (const void *)k_vote<4, uint16_t, false, MODE>,
+        (const void *)k_vote<2, uint16_t, false, MODE>,
+        (const void *)k_vote<1, uint16_t, false, MODE>,
+        (const void *)k_vote<4, int32_t, false, MODE>,
+        (const void *)k_vote<2, int32_t, false, MODE>,
+        (const void *)k_vote<1, int32_t, false, MODE>,
+        (const void *)k_vote_batch<4, uint16_t, true, MODE>,
+        (const void *)k_vote_batch<2, uint16_t, true, MODE>,
+        (const void *)k_vote_batch<1, uint16_t, true, MODE>,
+        (const void *)k_vote_batch<8, uint16_t, false, MODE>,
+        (const void *)k_vote_batch<4, uint16_t, false, MODE>,
+        (const void *)k_vote_batch<2, uint16_t, false, MODE>,
+        (const void *)k_vote_batch<1, uint16_t, false, MODE>};
     return allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
 }
 

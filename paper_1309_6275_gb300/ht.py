@@ -15,6 +15,7 @@ Tensor conventions:
   stats         int64 [2] (uint64 counters: votes, float64 redos)
   workspace     uint8, at least the size the matching *_workspace_size gives
   mask          int64 [1] per event (uint64 region bits, see ht_vote_masked)
+  hit_masks     int64 [n] per hit (uint64 region bits, see ht_vote_hit_masked)
   MLP params    float32 master / int16 (BF16 bits) copy [ht_mlp_param_count()]
   layer         uint8 [n] per hit
 """
@@ -53,6 +54,11 @@ class _Proposal(ctypes.Structure):
                 ("grow", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class _HitProposal(ctypes.Structure):
+    _fields_ = [("params_bf16", ctypes.c_void_p), ("layer", ctypes.c_void_p),
+                ("topk", ctypes.c_int32), ("pmin", ctypes.c_float)]
+
+
 # (name, restype, argtypes) of every exported function, as in include/ht.h
 _P, _I32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
 SIGNATURES = [
@@ -80,11 +86,13 @@ SIGNATURES = [
                                   ctypes.POINTER(_I32), _P]),
     ("ht_vote_masked", _I32, [_P, _P, _P, _I32, _P, _P, _P, _P]),
     ("ht_find_peaks_masked", _I32, [_P, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
+    ("ht_vote_hit_masked", _I32, [_P, _P, _P, _I32, _P, _P, _P, _P]),
     ("ht_mlp_param_count", _I32, []),
     ("ht_mlp_timeouts", ctypes.c_int64, []),
     ("ht_mlp_forward", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]),
     ("ht_mlp_region_mask", _I32, [_P, _P, _P, _P, _P, _P, _I32, _I32, ctypes.c_float,
                                   ctypes.c_float, _I32, _P, _P, _P]),
+    ("ht_mlp_hit_masks", _I32, [_P, _P, _P, _P, _P, _I32, _I32, ctypes.c_float, _P, _P]),
     ("ht_mlp_backward_workspace_size", _SZ, [_I32]),
     ("ht_mlp_backward", _I32, [_P, _P, _I32, _P, _P, _P, _P, _P, _P, _SZ, _P]),
     ("ht_mlp_adam", _I32, [_P, _P, _P, _P, _I32, ctypes.c_float, ctypes.c_float,
@@ -92,6 +100,11 @@ SIGNATURES = [
     ("ht_batch_run_masked", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P]),
     ("ht_batch_run_learned", _I32, [_P, _P, _P, _P, _P, _I32, ctypes.POINTER(_Proposal), _P,
                                     _P, _P, _P, _P, _P, _P]),
+    ("ht_batch_run_hit_masked", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P,
+                                       _P]),
+    ("ht_batch_run_learned_hits", _I32, [_P, _P, _P, _P, _P, _I32,
+                                         ctypes.POINTER(_HitProposal), _P, _P, _P, _P, _P, _P,
+                                         _P]),
     ("ht_fit_workspace_size", _SZ, [_I32, _I32, _I32]),
     ("ht_fit_tracks", _I32, [_P, _P, _P, _P, _I32, _I32, _P, _P, _P, _I32, _I32, _I32,
                              ctypes.c_double, ctypes.c_double, ctypes.c_double, _I32, _P, _P,
@@ -206,6 +219,13 @@ def ht_vote_masked(g, x, y, mask, acc, stats=None, stream=None):
                                 _ptr(stats), _stream(stream)), "ht_vote_masked")
 
 
+def ht_vote_hit_masked(g, x, y, hit_masks, acc, stats=None, stream=None):
+    """Vote with hit h restricted to the regions of hit_masks[h] (device int64 [n])."""
+    _check(lib().ht_vote_hit_masked(g.handle, _ptr(x), _ptr(y), x.numel(), _ptr(hit_masks),
+                                    _ptr(acc), _ptr(stats), _stream(stream)),
+           "ht_vote_hit_masked")
+
+
 def ht_find_peaks_masked(g, acc, mask, peaks, cap, d_count, workspace, stream=None):
     _check(lib().ht_find_peaks_masked(g.handle, _ptr(acc), _ptr(mask), _ptr(peaks), cap,
                                       _ptr(d_count), _ptr(workspace), workspace.numel(),
@@ -235,6 +255,13 @@ def ht_mlp_region_mask(params_bf16, x, y, z, layer, off, tau, fmax, grow, mass, 
                                     _ptr(off), off.numel() - 1, x.numel(), tau, fmax,
                                     int(grow), _ptr(mass), _ptr(masks), _stream(stream)),
            "ht_mlp_region_mask")
+
+
+def ht_mlp_hit_masks(params_bf16, x, y, z, layer, topk, pmin, hit_masks, stream=None):
+    """hit_masks (device int64 [n]) receives each hit's top-k region set."""
+    _check(lib().ht_mlp_hit_masks(_ptr(params_bf16), _ptr(x), _ptr(y), _ptr(z), _ptr(layer),
+                                  x.numel(), int(topk), float(pmin), _ptr(hit_masks),
+                                  _stream(stream)), "ht_mlp_hit_masks")
 
 
 def ht_mlp_backward_workspace_size(n):
@@ -476,6 +503,34 @@ class Batch:
                                           _ptr(masks), _ptr(self.peaks), _ptr(self.counts),
                                           _ptr(self.assign), _ptr(self.zres), _ptr(self.stats),
                                           _stream(stream)), "ht_batch_run_learned")
+
+    def run_hit_masked(self, x, y, z, offsets, hit_masks, stream=None):
+        """run() with each hit's vote restricted to hit_masks[h] (device
+        int64 [total hits], indexed like x)."""
+        off, p = self._offsets(offsets)
+        self._keep = off
+        _check(lib().ht_batch_run_hit_masked(self.handle, _ptr(x), _ptr(y), _ptr(z), p,
+                                             off.shape[0] - 1, _ptr(hit_masks),
+                                             _ptr(self.peaks), _ptr(self.counts),
+                                             _ptr(self.assign), _ptr(self.zres),
+                                             _ptr(self.stats), _stream(stream)),
+               "ht_batch_run_hit_masked")
+
+    def run_learned_hits(self, x, y, z, layer, offsets, params_bf16, hit_masks, topk, pmin=0.0,
+                         stream=None):
+        """run() with each hit's region set (its top-k regions) proposed by
+        the MLP inside the same graph; hit_masks (device int64 [total hits])
+        receives them."""
+        off, p = self._offsets(offsets)
+        self._keep = off
+        self._hprop = _HitProposal(params_bf16.data_ptr(), layer.data_ptr(), int(topk),
+                                   float(pmin))
+        _check(lib().ht_batch_run_learned_hits(self.handle, _ptr(x), _ptr(y), _ptr(z), p,
+                                               off.shape[0] - 1, ctypes.byref(self._hprop),
+                                               _ptr(hit_masks), _ptr(self.peaks),
+                                               _ptr(self.counts), _ptr(self.assign),
+                                               _ptr(self.zres), _ptr(self.stats),
+                                               _stream(stream)), "ht_batch_run_learned_hits")
 
     def stage_ms(self):
         """[proposal, vote, peaks + candidate lists, association, decode + z
