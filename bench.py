@@ -55,6 +55,7 @@ def parse():
     p.add_argument("--no-vertex", action="store_true")
     p.add_argument("--tau", type=float, default=0.02, help="proposal region threshold")
     p.add_argument("--grow", type=int, default=1, help="proposal region growth (0 or 1)")
+    p.add_argument("--topk", type=int, default=8, help="regions per hit of the per-hit proposal")
     return p.parse_args()
 
 
@@ -176,7 +177,7 @@ def run_reference(args):
 # capture (profiles/k_assoc32_batch_event100_b4.md), valid only while the
 # kernel sources hash to the value recorded with it.
 PROFILED_TRAFFIC = {
-    "k_assoc32_batch": {"sha": "1922396b5cb82b99", "bytes_per_event": 50.127872e6 / 4},
+    "k_assoc32_batch": {"sha": "df6397072b8c5646", "bytes_per_event": 50.840064e6 / 4},
 }
 KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_tiles.cu",
                   "paper_1309_6275_gb300/csrc/tiles.cuh",
@@ -205,10 +206,11 @@ def alu_peak_ops(dev_props, peaks):
 
 
 def learned_leg(args, ht, bt, batches, dev_in, g, flush):
-    """The learned-proposal batched path (ht_batch_run_learned) against the
-    plain one on the same resident events: events/s of each (same timing
-    rules as the headline), votes cast, candidates and track-finding
-    efficiency on the first batch."""
+    """The learned-proposal batched paths against the plain one on the same
+    resident events: the per-event region mask (ht_batch_run_learned) and
+    the per-hit top-k region sets (ht_batch_run_learned_hits).  Events/s of
+    each (same timing rules as the headline), votes cast, candidates and
+    track-finding efficiency on the first batch."""
     import torch
     from paper_1309_6275_gb300 import learned
     path = learned.default_weights_path("event100_256")
@@ -219,18 +221,24 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
     lay = [torch.from_numpy(np.concatenate([ev.layer for ev in b]).astype(np.uint8)).cuda()
            for b in batches]
     masks = torch.empty(bt.max_events, dtype=torch.int64, device="cuda")
+    hmasks = torch.empty(bt.max_hits, dtype=torch.int64, device="cuda")
     fmax = 0.6
+
+    def run_one(mode, off, x, y, z, l):
+        if mode == "plain":
+            bt.run(x, y, z, off)
+        elif mode == "learned":
+            bt.run_learned(x, y, z, l, off, pb, masks, args.tau, fmax, args.grow)
+        else:
+            bt.run_learned_hits(x, y, z, l, off, pb, hmasks, args.topk, 0.0)
 
     def run(mode):
         for (off, (x, y, z)), l in zip(dev_in, lay):
-            if mode == "plain":
-                bt.run(x, y, z, off)
-            else:
-                bt.run_learned(x, y, z, l, off, pb, masks, args.tau, fmax, args.grow)
+            run_one(mode, off, x, y, z, l)
 
     out = {}
     stream = torch.cuda.current_stream()
-    for mode in ("learned", "plain"):
+    for mode in ("learned", "hits", "plain"):
         for _ in range(max(1, args.warmup)):
             run(mode)
         torch.cuda.synchronize()
@@ -248,10 +256,7 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
         out[mode] = {"value": n_ev * max(1, args.steps) / t}
         # quality on the first batch
         off, (x, y, z) = dev_in[0]
-        if mode == "plain":
-            bt.run(x, y, z, off)
-        else:
-            bt.run_learned(x, y, z, lay[0], off, pb, masks, args.tau, fmax, args.grow)
+        run_one(mode, off, x, y, z, lay[0])
         torch.cuda.synchronize()
         out[mode]["stage_ms"] = [round(v, 3) for v in bt.stage_ms()]
         q = dict(votes=0, cands=0, n_rec=0, fa=0, fc=0)
@@ -265,7 +270,16 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
             mk = [int(v) & ((1 << 64) - 1) for v in masks[:len(batches[0])].cpu().tolist()]
             out[mode]["mean_regions"] = float(np.mean([bin(m).count("1") for m in mk]))
             out[mode]["fallback_frac"] = float(np.mean([m == (1 << 64) - 1 for m in mk]))
-    L, P = out["learned"], out["plain"]
+    L, P, H = out["learned"], out["plain"], out["hits"]
+    per_hit = {"value": H["value"], "unit": "events/s", "speedup": H["value"] / P["value"],
+               "topk": args.topk, "pmin": 0.0,
+               "vote_frac": H["votes"] / max(P["votes"], 1),
+               "candidate_frac": H["cands"] / max(P["cands"], 1),
+               "eff_candidate": H["fc"] / max(H["n_rec"], 1),
+               "eff_assign": H["fa"] / max(H["n_rec"], 1),
+               "first_batch_stage_ms": H["stage_ms"],
+               "path": "ht_batch_run_learned_hits (proposal MLP top-k per hit + per-hit "
+                       "restricted vote in one graph)"}
     return {"value": L["value"], "unit": "events/s", "plain_value": P["value"],
             "speedup": L["value"] / P["value"],
             "vote_frac": L["votes"] / max(P["votes"], 1),
@@ -281,6 +295,7 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
                                                 "decode+z"],
                                      "plain": P["stage_ms"], "learned": L["stage_ms"]},
             "tau": args.tau, "fmax": fmax, "grow": args.grow,
+            "per_hit": per_hit,
             "path": "ht_batch_run_learned (proposal MLP + masked vote/peaks in one graph)",
             "weights": os.path.relpath(path, ROOT),
             "trained_on": f"{meta.get('n_events')} {meta.get('workload')} events"}
