@@ -4,8 +4,8 @@ Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
 leg may import this package.
 """
 from . import oracle
-from .oracle import (build, tables, vote, vote_hitmask, peaks, associate, associate_dense,
-                     vote_z, atan2, run_event)
+from .oracle import (build, tables, edge_tables, vote, vote_hitmask, vote_swept, peaks,
+                     associate, associate_dense, vote_z, atan2, run_event)
 
-__all__ = ["oracle", "build", "tables", "vote", "vote_hitmask", "peaks", "associate",
-           "associate_dense", "vote_z", "atan2", "run_event"]
+__all__ = ["oracle", "build", "tables", "edge_tables", "vote", "vote_hitmask", "vote_swept",
+           "peaks", "associate", "associate_dense", "vote_z", "atan2", "run_event"]

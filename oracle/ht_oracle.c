@@ -61,6 +61,17 @@ void or_tables(const or_geom *g, double *phi0, double *sn, double *cs, double *r
         rho[i] = (double)(2 * i + 1 - g->n_rho) * (g->rho_max / (double)g->n_rho);
 }
 
+/* Column edges (reading): e_k = (2k - N) pi / N, the lower edge of column k
+ * (its centre phi0_k minus pi / N); sin/cos via libm. */
+void or_edge_tables(const or_geom *g, double *sn, double *cs)
+{
+    for (int32_t k = 0; k < g->n_phi0; ++k) {
+        const double e = (double)(2 * k - g->n_phi0) * (OR_PI / (double)g->n_phi0);
+        sn[k] = sin(e);
+        cs[k] = cos(e);
+    }
+}
+
 /* d0 binning (reading): width delta = 2 d0_half / n_d0, bin coordinate
  * u = d0 / delta + (n_d0 / 2 + 0.5), bin j = floor(u), valid iff 0 <= u < n_d0.
  * So d0 = 0 is the centre of bin n_d0 / 2 (prompt tracks do not straddle an
@@ -198,6 +209,144 @@ void or_vote_hitmask(const or_geom *g, const float *x, const float *y, const uin
     stats[0] += votes;
     stats[1] += edge;
     free(phi0); free(sn); free(cs); free(rho);
+}
+
+/* Swept-interval vote (reading; the paper samples phi0 at bin centres and
+ * notes that the transform tolerates data the discretisation cannot
+ * represent exactly).  Column k covers phi0 from its lower edge
+ * e_k = (2k - N) pi / N to e_{(k+1) mod N} (the same angle as e_k + 2 pi / N,
+ * taken from the same table).  The hit's roots are sampled at the lower edge,
+ * the centre phi0_k and the upper edge.  At each sample t the roots exist
+ * when c > 0 and D >= 0; they are labelled by branch, + = (-b + sqrt D) / rho
+ * and - = (-b - sqrt D) / rho (rho == 0: only +, = -s; D == 0: both equal),
+ * and each gets a code: floor(u) inside the axis, -1 below it, n_d0 above.
+ * Per branch, two consecutive samples that both have the root give every
+ * bin between their codes (clamped to the axis; nothing if both are on the
+ * same side outside); a sample whose neighbours lack the root gives its own
+ * bin.  The cell (i, j, k) gets one vote when bin j is in the union of these
+ * ranges over both branches. */
+typedef struct {
+    int ok[2];      /* branch + / - has a root at this sample */
+    int64_t code[2];
+} sweep_sample;
+
+static int64_t u_code(const or_geom *g, double u)
+{
+    if (u < 0.0)
+        return -1;
+    if (u >= (double)g->n_d0)
+        return g->n_d0;
+    return (int64_t)floor(u);
+}
+
+static sweep_sample sweep_at(const or_geom *g, float xf, float yf, double sn, double cs,
+                             double rho)
+{
+    sweep_sample r = {{0, 0}, {0, 0}};
+    const double delta = d0_delta(g), off = d0_offset(g);
+    const double x = (double)xf, y = (double)yf;
+    const double s = x * sn - y * cs;
+    const double c = x * cs + y * sn;
+    if (!(c > 0.0))
+        return r;
+    const double r2 = x * x + y * y;
+    const double b = 1.0 + rho * s;
+    const double pc = rho * c;
+    const double D = 1.0 - pc * pc;
+    if (D < 0.0)
+        return r;
+    const double sq = sqrt(D);
+    const double q = -(b + (b >= 0.0 ? sq : -sq));
+    const double C = rho * r2 + 2.0 * s;
+    if (rho == 0.0) {               /* one root, C / q = -s */
+        r.ok[0] = 1;
+        r.code[0] = u_code(g, (C / q) / delta + off);
+        return r;
+    }
+    if (D == 0.0) {                 /* double root */
+        r.ok[0] = r.ok[1] = 1;
+        r.code[0] = r.code[1] = u_code(g, (q / rho) / delta + off);
+        return r;
+    }
+    const int64_t cA = u_code(g, (C / q) / delta + off);
+    const int64_t cB = u_code(g, (q / rho) / delta + off);
+    /* b >= 0: C / q is the + root and q / rho the - root; b < 0: swapped */
+    r.ok[0] = r.ok[1] = 1;
+    r.code[0] = b >= 0.0 ? cA : cB;
+    r.code[1] = b >= 0.0 ? cB : cA;
+    return r;
+}
+
+/* Marks bins [lo, hi] (clamped) in mark[]; returns nothing. */
+static void mark_range(const or_geom *g, int64_t lo, int64_t hi, unsigned char *mark)
+{
+    if (hi < 0 || lo > g->n_d0 - 1)
+        return;
+    if (lo < 0)
+        lo = 0;
+    if (hi > g->n_d0 - 1)
+        hi = g->n_d0 - 1;
+    for (int64_t j = lo; j <= hi; ++j)
+        mark[j] = 1;
+}
+
+/* Bins swept by one hit in one (rho_i, column k): mark[j] = 1 (mark has
+ * n_d0 entries, cleared by the caller).  sn/cs: the three samples' tables. */
+static void swept_bins(const or_geom *g, float x, float y, const double sn[3],
+                       const double cs[3], double rho, unsigned char *mark)
+{
+    sweep_sample t[3];
+    for (int a = 0; a < 3; ++a)
+        t[a] = sweep_at(g, x, y, sn[a], cs[a], rho);
+    for (int br = 0; br < 2; ++br) {
+        for (int a = 0; a < 2; ++a)
+            if (t[a].ok[br] && t[a + 1].ok[br]) {
+                const int64_t c0 = t[a].code[br], c1 = t[a + 1].code[br];
+                mark_range(g, c0 < c1 ? c0 : c1, c0 < c1 ? c1 : c0, mark);
+            }
+        for (int a = 0; a < 3; ++a) {
+            const int left = a > 0 && t[a - 1].ok[br];
+            const int right = a < 2 && t[a + 1].ok[br];
+            if (t[a].ok[br] && !left && !right)
+                mark_range(g, t[a].code[br], t[a].code[br], mark);
+        }
+    }
+}
+
+/* Swept vote of rows [i_begin, i_end): acc as or_vote (caller zeroes it,
+ * saturating at count_max); stats[0] += votes cast. */
+void or_vote_swept(const or_geom *g, const float *x, const float *y, int64_t n,
+                   int32_t i_begin, int32_t i_end, int64_t *acc, int64_t *stats)
+{
+    const int32_t NP = g->n_phi0, ND = g->n_d0;
+    double *phi0 = malloc(sizeof(double) * NP);
+    double *sn = malloc(sizeof(double) * NP);
+    double *cs = malloc(sizeof(double) * NP);
+    double *esn = malloc(sizeof(double) * NP);
+    double *ecs = malloc(sizeof(double) * NP);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    unsigned char *mark = malloc((size_t)ND);
+    or_tables(g, phi0, sn, cs, rho);
+    or_edge_tables(g, esn, ecs);
+    int64_t votes = 0;
+    for (int64_t h = 0; h < n; ++h)
+        for (int32_t i = i_begin; i < i_end; ++i)
+            for (int32_t k = 0; k < NP; ++k) {
+                const int32_t k1 = (k + 1) % NP;
+                const double s3[3] = {esn[k], sn[k], esn[k1]};
+                const double c3[3] = {ecs[k], cs[k], ecs[k1]};
+                memset(mark, 0, (size_t)ND);
+                swept_bins(g, x[h], y[h], s3, c3, rho[i], mark);
+                for (int32_t j = 0; j < ND; ++j)
+                    if (mark[j]) {
+                        int64_t *cell = &acc[((int64_t)i * ND + j) * NP + k];
+                        if (*cell < g->count_max)
+                            ++*cell;
+                        ++votes;
+                    }
+            }
+    stats[0] += votes;
+    free(phi0); free(sn); free(cs); free(esn); free(ecs); free(rho); free(mark);
 }
 
 /* Peak finding (Sections 5 and 6: local maxima of the vote space; Section 7:

@@ -70,6 +70,8 @@ def lib():
             L.or_tables.argtypes = [G, vp, vp, vp, vp]
             L.or_vote.argtypes = [G, vp, vp, i64, i32, i32, vp, vp]
             L.or_vote_hitmask.argtypes = [G, vp, vp, vp, i64, i32, i32, vp, vp]
+            L.or_vote_swept.argtypes = [G, vp, vp, i64, i32, i32, vp, vp]
+            L.or_edge_tables.argtypes = [G, vp, vp]
             L.or_peaks.argtypes = [G, vp, i32, i32, vp, i64]
             L.or_peaks.restype = i64
             L.or_associate.argtypes = [G, vp, vp, vp, i64, vp, i64, vp]
@@ -156,6 +158,38 @@ def vote_hitmask(g, x, y, masks, threads=None, rows=None):
         list(ex.map(run, range(len(parts))))
     tot = stats.sum(0)
     return acc, {"votes": int(tot[0]), "edge": int(tot[1])}
+
+
+def edge_tables(g):
+    """(sin, cos) of the column lower edges e_k = (2k - N) pi / N, float64."""
+    G = _geom(g)
+    sn = np.empty(g["n_phi0"]); cs = np.empty_like(sn)
+    lib().or_edge_tables(ctypes.byref(G), _p(sn), _p(cs))
+    return sn, cs
+
+
+def vote_swept(g, x, y, threads=None, rows=None):
+    """Swept-interval vote (or_vote_swept): each hit marks, in every (rho
+    row, phi0 column), the d0 bins its roots sweep between the column's
+    edges and centre.  Returns (acc, {votes}); rows=(a, b) computes only
+    rho rows [a, b) and returns acc[a:b]."""
+    G = _geom(g)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    r0, r1 = (0, g["n_rho"]) if rows is None else rows
+    acc = np.zeros((r1 - r0, g["n_d0"], g["n_phi0"]), np.int64)
+    base = r0 * g["n_d0"] * g["n_phi0"] * 8
+    parts = [(a + r0, b + r0) for a, b in _chunks(r1 - r0, _threads(threads) * 2)]
+    stats = np.zeros((len(parts), 2), np.int64)
+    accp = acc.ctypes.data - base
+
+    def run(t):
+        a, b = parts[t]
+        lib().or_vote_swept(ctypes.byref(G), _p(x), _p(y), x.shape[0], a, b,
+                            ctypes.c_void_p(accp), _p(stats[t]))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, range(len(parts))))
+    return acc, {"votes": int(stats[:, 0].sum())}
 
 
 def peaks(g, acc, cap=None, threads=None):
