@@ -53,6 +53,7 @@ def parse():
     p.add_argument("--batch", type=int, default=25, help="events per ht_batch_run")
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--no-vertex", action="store_true")
+    p.add_argument("--no-swept", action="store_true")
     p.add_argument("--tau", type=float, default=0.02, help="proposal region threshold")
     p.add_argument("--grow", type=int, default=1, help="proposal region growth (0 or 1)")
     p.add_argument("--topk", type=int, default=8, help="regions per hit of the per-hit proposal")
@@ -299,6 +300,58 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
             "path": "ht_batch_run_learned (proposal MLP + masked vote/peaks in one graph)",
             "weights": os.path.relpath(path, ROOT),
             "trained_on": f"{meta.get('n_events')} {meta.get('workload')} events"}
+
+
+def swept_leg(args):
+    """Swept-interval phi0 vote against the point vote on the single-event
+    workload (200 events of ~275 hits), at its own 64 phi0 columns and at
+    256: device ms per event for the vote alone and for the whole
+    single-event path (vote, peaks, association, z vote), votes cast,
+    candidates, and track-finding efficiency."""
+    import torch
+    from paper_1309_6275_gb300 import ht, learned
+    name = "single_64"
+    evs = [synth.make_event(synth.CONFIGS[name]["gen"], 1000 + i) for i in range(200)]
+    out = {}
+    for n_phi0 in (64, 256):
+        g = synth.geometry_of(name, n_phi0=n_phi0)
+        G = ht.Geometry(g)
+        P = ht.EventPipeline(G, max(e.n_hits for e in evs), 1 << 16)
+        dev = [tuple(torch.from_numpy(getattr(e, k)).cuda() for k in ("x", "y", "z"))
+               for e in evs]
+        res = {}
+        for swept in (False, True):
+            vote = ht.ht_vote_swept if swept else ht.ht_vote
+            for _ in range(max(3, args.warmup)):
+                P.run(*dev[0], swept=swept)
+            torch.cuda.synchronize()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            for x, y, _z in dev:
+                vote(G, x, y, P.acc, P.stats)
+            b.record()
+            b.synchronize()
+            vote_ms = a.elapsed_time(b) / len(dev)
+            q = np.zeros(5)
+            t = 0.0
+            for e, (x, y, z) in zip(evs, dev):
+                a.record()
+                P.run(x, y, z, swept=swept)
+                b.record()
+                b.synchronize()
+                t += a.elapsed_time(b)
+                r = P.results(e.n_hits)
+                nr, fa, fc = learned.efficiency(g, e, r["peaks"], r["assign"])
+                q += [nr, fa, fc, int(r["stats"][0]), r["count"]]
+            res["swept" if swept else "point"] = {
+                "vote_ms_per_event": round(vote_ms, 4), "path_ms_per_event": round(t / len(dev), 4),
+                "eff_candidate": q[2] / max(q[0], 1), "eff_assign": q[1] / max(q[0], 1),
+                "votes_per_event": q[3] / len(dev), "candidates_per_event": q[4] / len(dev)}
+        out[f"n_phi0_{n_phi0}"] = res
+        G.close()
+    return {"workload": f"{name}: 200 events of ~275 hits, 64x64xN int32, one event per call",
+            "path": "ht_vote_swept then ht_find_peaks, ht_associate, ht_vote_z", **out}
 
 
 def vertex_leg(args):
@@ -563,6 +616,10 @@ def run_ours(args):
     if not args.no_learned:
         learned_res = learned_leg(args, ht, bt, batches, dev_in, g, flush)
 
+    swept_res = None
+    if not args.no_swept:
+        swept_res = swept_leg(args)
+
     vertex_res = None
     if not args.no_vertex:
         vertex_res = vertex_leg(args)
@@ -623,6 +680,8 @@ def run_ours(args):
         line["learned"] = learned_res
     if vertex_res:
         line["displaced_jets"] = vertex_res
+    if swept_res:
+        line["swept_vote"] = swept_res
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:

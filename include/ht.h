@@ -209,6 +209,23 @@ ht_status ht_run_event(const ht_geometry *g, const float *hx, const float *hy,
                        int32_t *h_count, int32_t *h_assign, ht_zres *h_zres,
                        uint64_t *h_stats, ht_stream stream);
 
+/* Swept-interval vote (the paper samples phi0 at bin centres; this variant
+ * votes, in each phi0 column, the d0 range the hit's roots sweep across the
+ * column, for coarse phi0 binning).  The roots are sampled at the column's
+ * lower edge e_k = (2k - N) pi / N, its centre and its upper edge
+ * e_{(k+1) mod N}; at each sample they exist when c > 0 and D >= 0 and are
+ * labelled by branch (+ and - sqrt D); per branch, two consecutive samples
+ * with the root give every bin between their bins (roots beyond the axis
+ * clamp to its ends), a sample whose neighbours lack the root gives its own
+ * bin; a cell gets one vote per hit when its bin is in the union over both
+ * branches.  It contains ht_vote's cells (not its double votes) and tends to
+ * them as n_phi0 grows.  acc: as ht_vote (every cell written).  stats: NULL
+ * or 2 uint64, stats[0] = votes cast, stats[1] = 0.  Peaks, association and
+ * the z vote apply unchanged to acc.  Errors: as ht_vote; HT_ERR_ARG also
+ * when n_d0 needs more shared memory than a tile has. */
+ht_status ht_vote_swept(const ht_geometry *g, const float *x, const float *y, int32_t n_hits,
+                        void *acc, uint64_t *stats, ht_stream stream);
+
 /* ------------------------------------------------------------------------
  * Region masks (learned proposal).  The paper has no learned part; these
  * calls restrict the Section 5 vote and peak finding to regions that a

@@ -277,8 +277,10 @@ static sweep_sample sweep_at(const or_geom *g, float xf, float yf, double sn, do
     return r;
 }
 
-/* Marks bins [lo, hi] (clamped) in mark[]; returns nothing. */
-static void mark_range(const or_geom *g, int64_t lo, int64_t hi, unsigned char *mark)
+/* Marks bins [lo, hi] (clamped) in mark[] and widens the touched span
+ * [*t_lo, *t_hi]. */
+static void mark_range(const or_geom *g, int64_t lo, int64_t hi, unsigned char *mark,
+                       int64_t *t_lo, int64_t *t_hi)
 {
     if (hi < 0 || lo > g->n_d0 - 1)
         return;
@@ -288,13 +290,21 @@ static void mark_range(const or_geom *g, int64_t lo, int64_t hi, unsigned char *
         hi = g->n_d0 - 1;
     for (int64_t j = lo; j <= hi; ++j)
         mark[j] = 1;
+    if (lo < *t_lo)
+        *t_lo = lo;
+    if (hi > *t_hi)
+        *t_hi = hi;
 }
 
 /* Bins swept by one hit in one (rho_i, column k): mark[j] = 1 (mark has
- * n_d0 entries, cleared by the caller).  sn/cs: the three samples' tables. */
+ * n_d0 entries, clear on entry) for j in the touched span [*t_lo, *t_hi]
+ * (empty when *t_lo > *t_hi).  sn/cs: the three samples' tables. */
 static void swept_bins(const or_geom *g, float x, float y, const double sn[3],
-                       const double cs[3], double rho, unsigned char *mark)
+                       const double cs[3], double rho, unsigned char *mark, int64_t *t_lo,
+                       int64_t *t_hi)
 {
+    *t_lo = g->n_d0;
+    *t_hi = -1;
     sweep_sample t[3];
     for (int a = 0; a < 3; ++a)
         t[a] = sweep_at(g, x, y, sn[a], cs[a], rho);
@@ -302,13 +312,13 @@ static void swept_bins(const or_geom *g, float x, float y, const double sn[3],
         for (int a = 0; a < 2; ++a)
             if (t[a].ok[br] && t[a + 1].ok[br]) {
                 const int64_t c0 = t[a].code[br], c1 = t[a + 1].code[br];
-                mark_range(g, c0 < c1 ? c0 : c1, c0 < c1 ? c1 : c0, mark);
+                mark_range(g, c0 < c1 ? c0 : c1, c0 < c1 ? c1 : c0, mark, t_lo, t_hi);
             }
         for (int a = 0; a < 3; ++a) {
             const int left = a > 0 && t[a - 1].ok[br];
             const int right = a < 2 && t[a + 1].ok[br];
             if (t[a].ok[br] && !left && !right)
-                mark_range(g, t[a].code[br], t[a].code[br], mark);
+                mark_range(g, t[a].code[br], t[a].code[br], mark, t_lo, t_hi);
         }
     }
 }
@@ -325,7 +335,7 @@ void or_vote_swept(const or_geom *g, const float *x, const float *y, int64_t n,
     double *esn = malloc(sizeof(double) * NP);
     double *ecs = malloc(sizeof(double) * NP);
     double *rho = malloc(sizeof(double) * g->n_rho);
-    unsigned char *mark = malloc((size_t)ND);
+    unsigned char *mark = calloc((size_t)ND, 1);
     or_tables(g, phi0, sn, cs, rho);
     or_edge_tables(g, esn, ecs);
     int64_t votes = 0;
@@ -335,10 +345,11 @@ void or_vote_swept(const or_geom *g, const float *x, const float *y, int64_t n,
                 const int32_t k1 = (k + 1) % NP;
                 const double s3[3] = {esn[k], sn[k], esn[k1]};
                 const double c3[3] = {ecs[k], cs[k], ecs[k1]};
-                memset(mark, 0, (size_t)ND);
-                swept_bins(g, x[h], y[h], s3, c3, rho[i], mark);
-                for (int32_t j = 0; j < ND; ++j)
+                int64_t t_lo, t_hi;
+                swept_bins(g, x[h], y[h], s3, c3, rho[i], mark, &t_lo, &t_hi);
+                for (int64_t j = t_lo; j <= t_hi; ++j)
                     if (mark[j]) {
+                        mark[j] = 0;
                         int64_t *cell = &acc[((int64_t)i * ND + j) * NP + k];
                         if (*cell < g->count_max)
                             ++*cell;

@@ -21,6 +21,8 @@ size_t tile_smem_need(const DevGeom &G);
 cudaError_t prepare_z_kernels(int max_smem);
 cudaError_t prepare_mlp_kernels();
 cudaError_t prepare_masked_vote_kernels(int max_smem);
+cudaError_t prepare_swept_kernels(int max_smem);
+size_t swept_smem_need(const DevGeom &G);
 cudaError_t prepare_peaks_kernels();
 size_t z_big_smem(const DevGeom &G);
 }  // namespace ht
@@ -100,10 +102,19 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     }
     for (int i = 0; i < NR; ++i) rho[i] = (double)(2 * i + 1 - NR) * (d->rho_max / (double)NR);
 
-    // one device block: float64 sn, cs, rho | float32 sn, cs, phi, rho, 1/rho,
-    // and the float32 remainders sn - (float)sn, cs - (float)cs, rho - (float)rho
-    const size_t b64 = sizeof(double) * (2 * (size_t)NP + NR);
-    const size_t b32 = sizeof(float) * (5 * (size_t)NP + 3 * (size_t)NR);
+    // column lower edges e_k = (2k - N) pi / N (the swept-interval vote)
+    double *esn = new double[NP], *ecs = new double[NP];
+    for (int k = 0; k < NP; ++k) {
+        const double ek = (double)(2 * k - NP) * (ht::kPi / (double)NP);
+        esn[k] = sin(ek);
+        ecs[k] = cos(ek);
+    }
+
+    // one device block: float64 sn, cs, rho, edge sn, edge cs | float32 sn,
+    // cs, phi, rho, 1/rho, the float32 remainders sn - (float)sn,
+    // cs - (float)cs, rho - (float)rho, and float32 edge sn, cs
+    const size_t b64 = sizeof(double) * (4 * (size_t)NP + NR);
+    const size_t b32 = sizeof(float) * (7 * (size_t)NP + 3 * (size_t)NR);
     const size_t bytes = ht::align256(b64) + ht::align256(b32);
     char *h = new char[bytes];
     memset(h, 0, bytes);
@@ -112,6 +123,8 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     memcpy(h64, sn, sizeof(double) * NP);
     memcpy(h64 + NP, cs, sizeof(double) * NP);
     memcpy(h64 + 2 * NP, rho, sizeof(double) * NR);
+    memcpy(h64 + 2 * NP + NR, esn, sizeof(double) * NP);
+    memcpy(h64 + 3 * NP + NR, ecs, sizeof(double) * NP);
     for (int k = 0; k < NP; ++k) {
         h32[k] = (float)sn[k];
         h32[NP + k] = (float)cs[k];
@@ -127,9 +140,15 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
         hlo[NP + k] = (float)(cs[k] - (double)(float)cs[k]);
     }
     for (int i = 0; i < NR; ++i) hlo[2 * NP + i] = (float)(rho[i] - (double)(float)rho[i]);
+    float *hedge = hlo + 2 * NP + NR;
+    for (int k = 0; k < NP; ++k) {
+        hedge[k] = (float)esn[k];
+        hedge[NP + k] = (float)ecs[k];
+    }
     e = cudaMalloc(&g->d_tables, bytes);
     if (e == cudaSuccess) e = cudaMemcpy(g->d_tables, h, bytes, cudaMemcpyHostToDevice);
     delete[] phi; delete[] sn; delete[] cs; delete[] rho; delete[] h;
+    delete[] esn; delete[] ecs;
     if (e != cudaSuccess) {
         if (g->d_tables) cudaFree(g->d_tables);
         delete g;
@@ -160,6 +179,8 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     G.sn32 = d32; G.cs32 = d32 + NP; G.phi32 = d32 + 2 * NP;
     G.rho32 = d32 + 3 * NP; G.invrho32 = d32 + 3 * NP + NR;
     G.snlo = d32 + 3 * NP + 2 * NR; G.cslo = G.snlo + NP; G.rholo = G.cslo + NP;
+    G.esn64 = d64 + 2 * NP + NR; G.ecs64 = G.esn64 + NP;
+    G.esn32 = G.rholo + NR; G.ecs32 = G.esn32 + NP;
     G.dz = 2.0 * d->z0_max / (double)d->n_z0;
     G.z0_max = d->z0_max;
     G.cstep = d->cot_max / (double)d->n_cot;
@@ -179,6 +200,7 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     if (e == cudaSuccess) e = ht::prepare_tile_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_z_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_masked_vote_kernels(max_smem);
+    if (e == cudaSuccess) e = ht::prepare_swept_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_peaks_kernels();
     if (e == cudaSuccess) e = ht::prepare_mlp_kernels();
     if (e != cudaSuccess) {
@@ -260,6 +282,26 @@ ht_status ht_vote_hit_masked(const ht_geometry *g, const float *x, const float *
                                     reinterpret_cast<const unsigned long long *>(hit_masks),
                                     S(stream));
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_hit_masked");
+}
+
+ht_status ht_vote_swept(const ht_geometry *g, const float *x, const float *y, int32_t n_hits,
+                        void *acc, uint64_t *stats, ht_stream stream)
+{
+    if (!g || !acc) return fail(HT_ERR_ARG, "ht_vote_swept: null geometry or accumulator");
+    if (n_hits < 0 || n_hits > kMaxHits)
+        return fail(HT_ERR_ARG, "ht_vote_swept: n_hits %d outside [0, %d]", n_hits, kMaxHits);
+    if (n_hits > 0 && (!x || !y)) return fail(HT_ERR_ARG, "ht_vote_swept: null hit arrays");
+    if (!aligned(acc, 16) || (x && !aligned(x, 16)) || (y && !aligned(y, 16)))
+        return fail(HT_ERR_ARG, "ht_vote_swept: pointer alignment");
+    if (ht::swept_smem_need(g->G) > 200 * 1024)
+        return fail(HT_ERR_ARG, "ht_vote_swept: n_d0 %d too large for the swept tile",
+                    g->G.n_d0);
+    cudaError_t e = cudaSuccess;
+    if (stats) e = cudaMemsetAsync(stats, 0, 2 * sizeof(uint64_t), S(stream));
+    if (e == cudaSuccess)
+        e = ht::launch_vote_swept(g->G, x, y, n_hits, acc,
+                                  reinterpret_cast<unsigned long long *>(stats), S(stream));
+    return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_swept");
 }
 
 size_t ht_find_peaks_workspace_size(const ht_geometry *g)

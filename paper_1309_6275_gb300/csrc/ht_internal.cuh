@@ -28,6 +28,8 @@ struct DevGeom {
     const float *sn32, *cs32, *phi32, *rho32, *invrho32;
     const double *sn64, *cs64, *rho64;
     const float *snlo, *cslo, *rholo;  // float64 value - float32 table, as float32
+    const double *esn64, *ecs64;       // column lower edges e_k = (2k - N) pi / N
+    const float *esn32, *ecs32;
     float inv_delta_lo;                // 1/delta - inv_delta_f
     // z vote
     double dz, z0_max, cstep;      // dz = 2 z0_max / n_z0, cstep = cot_max / n_cot
@@ -307,6 +309,10 @@ cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n,
 cudaError_t launch_vote_masked(const DevGeom &G, const float *x, const float *y, int n,
                                void *acc, unsigned long long *stats,
                                const unsigned long long *mask, cudaStream_t st);
+// Swept-interval vote: each (rho row, phi0 column) votes the d0 bins the
+// hit's roots sweep between the column's edges (k_swept.cu).
+cudaError_t launch_vote_swept(const DevGeom &G, const float *x, const float *y, int n, void *acc,
+                              unsigned long long *stats, cudaStream_t st);
 // Per-hit vote: hit h's votes count only in the halo cells of hit_masks[h].
 cudaError_t launch_vote_hitmask(const DevGeom &G, const float *x, const float *y, int n,
                                 void *acc, unsigned long long *stats,

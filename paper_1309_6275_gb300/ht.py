@@ -87,6 +87,7 @@ SIGNATURES = [
     ("ht_vote_masked", _I32, [_P, _P, _P, _I32, _P, _P, _P, _P]),
     ("ht_find_peaks_masked", _I32, [_P, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
     ("ht_vote_hit_masked", _I32, [_P, _P, _P, _I32, _P, _P, _P, _P]),
+    ("ht_vote_swept", _I32, [_P, _P, _P, _I32, _P, _P, _P]),
     ("ht_mlp_param_count", _I32, []),
     ("ht_mlp_timeouts", ctypes.c_int64, []),
     ("ht_mlp_forward", _I32, [_P, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P]),
@@ -224,6 +225,12 @@ def ht_vote_hit_masked(g, x, y, hit_masks, acc, stats=None, stream=None):
     _check(lib().ht_vote_hit_masked(g.handle, _ptr(x), _ptr(y), x.numel(), _ptr(hit_masks),
                                     _ptr(acc), _ptr(stats), _stream(stream)),
            "ht_vote_hit_masked")
+
+
+def ht_vote_swept(g, x, y, acc, stats=None, stream=None):
+    """Swept-interval vote: each column votes the d0 bins swept across it."""
+    _check(lib().ht_vote_swept(g.handle, _ptr(x), _ptr(y), x.numel(), _ptr(acc), _ptr(stats),
+                               _stream(stream)), "ht_vote_swept")
 
 
 def ht_find_peaks_masked(g, acc, mask, peaks, cap, d_count, workspace, stream=None):
@@ -409,11 +416,12 @@ class EventPipeline:
                  g.vote_z_workspace_size(max_hits, cap))
         self.workspace = torch.empty(ws, dtype=torch.uint8, device=dev)
 
-    def run(self, x, y, z, stream=None):
+    def run(self, x, y, z, stream=None, swept=False):
+        """swept: the swept-interval vote (ht_vote_swept) instead of ht_vote."""
         n = x.numel()
         assert n <= self.max_hits
         g = self.g
-        ht_vote(g, x, y, self.acc, self.stats, stream)
+        (ht_vote_swept if swept else ht_vote)(g, x, y, self.acc, self.stats, stream)
         ht_find_peaks(g, self.acc, self.peaks, self.cap, self.count, self.workspace, stream)
         ht_associate(g, x, y, self.peaks, self.count, self.cap, self.assign[:n],
                      self.workspace, stream)
