@@ -133,10 +133,11 @@ __device__ __forceinline__ int decide(float u, float e, float nd)
     return out ? -1 : (ok ? (int)f : -2);
 }
 
-// Returns kDecided with jA, jB (bin or -1) or kRedo.
+// Returns kDecided with jA, jB (bin or -1) or kRedo.  NEED_B = false: the
+// caller has proven root B out of the axis (jB = -1 without evaluating it).
+template <bool NEED_B>
 __device__ __forceinline__ int eval32(const DevGeom &G, float rho, float invrho_es,
-                                      float invrho, bool need_b, const Item &it, int &jA,
-                                      int &jB)
+                                      float invrho, const Item &it, int &jA, int &jB)
 {
     const float b = fmaf(rho, it.s, 1.0f);
     const float pc = rho * it.c;
@@ -154,7 +155,7 @@ __device__ __forceinline__ int eval32(const DevGeom &G, float rho, float invrho_
     const float eA = fmaf(fabsf(iq), fmaf(it.E2, rs, it.E1), G.e3);
     int a = decide(uA, eA, nd);
     int bb = -1;
-    if (need_b) {
+    if (NEED_B) {
         const float uB = fmaf(q * invrho, G.inv_delta_f, G.off_f);
         const float eB = fmaf(invrho_es, fmaf(it.Qb, rs, it.Qa), G.e3);
         bb = decide(uB, eB, nd);
@@ -224,7 +225,7 @@ __device__ __forceinline__ void rho_range_w(float wlo, float whi, float c, float
     const float c2 = c * c;
     const float glo = __fdividef(-2.0f * wlo, fmaf(wlo, wlo, c2));
     const float ghi = __fdividef(-2.0f * whi, fmaf(whi, whi, c2));
-    const float ic = __frcp_rn(c);
+    const float ic = rcp_approx(c);   // a few ulp: far inside the callers' one-row margin
     gmax = (wlo <= -c && -c <= whi) ? ic : fmaxf(glo, ghi);
     gmin = (wlo <= c && c <= whi) ? -ic : fminf(glo, ghi);
 }

@@ -116,8 +116,12 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
     __syncthreads();
 
     int parity = 0;
+    HitPrefetch pf;
+    pf.start(x, y, n);
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
-        collect<KT>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W);
+        float xh, yh;
+        pf.next(x, y, n, base, xh, yh);
+        collect<KT>(G, T, xh, yh, n, base + threadIdx.x, lane, &qn[parity], W);
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;
@@ -407,8 +411,13 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     };
 
     int parity = 0;
+    HitPrefetch pf;
+    pf.start(x, y, n);
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
-        collect<KT, kModeEvent>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W, &M);
+        float xh, yh;
+        pf.next(x, y, n, base, xh, yh);
+        collect<KT, kModeEvent>(G, T, xh, yh, n, base + threadIdx.x, lane, &qn[parity], W,
+                                &M);
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;

@@ -59,7 +59,7 @@ template <int KT>
 struct TileCtx {
     int i0, k0, irow;
     bool row_ok, has_b;
-    float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB;
+    float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB, cB;
     float sk[KT], ck[KT];
 
     __device__ __forceinline__ void init(const DevGeom &G, int lane, int tx, int ty)
@@ -79,6 +79,10 @@ struct TileCtx {
         // the second root q / rho can reach the axis only if |1 + rho s| <=
         // |rho| dext, i.e. |s| >= 1 / rt - dext for the rows of this tile
         sB = rt > 0.0f ? __frcp_rn(rt) - G.dext_f - 0.01f : 3.0e38f;
+        // |q| = |b| + sqrt(D) >= sqrt(1 - rho^2 c^2), so q / rho also needs
+        // c^2 >= 1 / rho^2 - dext^2 >= 1 / rt^2 - dext^2
+        const float ir = rt > 0.0f ? __frcp_rn(rt) : 3.0e19f;
+        cB = sqrtf(fmaxf(fmaf(ir, ir, -G.dext_f * G.dext_f), 0.0f)) - 0.05f;
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
             sk[kl] = G.sn32[k0 + kl];
@@ -150,14 +154,13 @@ struct HitCtx {
     }
 };
 
-// Phase 1 for hit h (h >= n: no items).  Appends this warp's items to the
-// list with a single atomicAdd on *qn (all 32 lanes must call).
+// Phase 1 for hit h at (xh, yh) (h >= n: no items).  Appends this warp's
+// items to the list with a single atomicAdd on *qn (all 32 lanes must call).
 template <int KT, int MODE = kModePlain>
-__device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
-                                        const float *__restrict__ x,
-                                        const float *__restrict__ y, int n, int h,
-                                        int lane, int *qn, const WorkList &W,
-                                        const MaskCtx *M = nullptr, const HitCtx *H = nullptr)
+__device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, float xh,
+                                        float yh, int n, int h, int lane, int *qn,
+                                        const WorkList &W, const MaskCtx *M = nullptr,
+                                        const HitCtx *H = nullptr)
 {
     float is_[KT], ic_[KT];
     int fl_[KT];
@@ -180,7 +183,6 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
         }
     }
     if (live) {
-        const float xh = x[h], yh = y[h];
         r2 = fmaf(xh, xh, yh * yh);
         R1 = fabsf(xh) + fabsf(yh);
         const float cmin = hit_cos_window(G, r2);
@@ -213,7 +215,7 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
                     if (gmax < T.rho_lo || gmin > T.rho_hi) continue;
                 }
             }
-            if (fabsf(s) >= T.sB) f |= kMetaNeedB;
+            if (fabsf(s) >= T.sB && c >= T.cB) f |= kMetaNeedB;
             sel |= 1u << kl;
             fl_[kl] = f;
             is_[kl] = s;
@@ -244,6 +246,34 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T,
     }
 }
 
+// Hit coordinates of thread `threadIdx.x` in the round starting at base:
+// the next round's are loaded while this round runs.
+struct HitPrefetch {
+    float xn, yn;
+
+    __device__ __forceinline__ void start(const float *__restrict__ x,
+                                          const float *__restrict__ y, int n)
+    {
+        const int h = threadIdx.x;
+        xn = h < n ? __ldg(x + h) : 0.0f;
+        yn = h < n ? __ldg(y + h) : 0.0f;
+    }
+
+    // (xh, yh) of round `base`; issues the loads of round base + blockDim.x
+    __device__ __forceinline__ void next(const float *__restrict__ x,
+                                         const float *__restrict__ y, int n, int base,
+                                         float &xh, float &yh)
+    {
+        xh = xn;
+        yh = yn;
+        const int h = base + (int)blockDim.x + (int)threadIdx.x;
+        if (h < n) {
+            xn = __ldg(x + h);
+            yn = __ldg(y + h);
+        }
+    }
+};
+
 // Bins of work item t for the lane's row by guarded float32: the number of
 // bins written to jj, or -1 when the column must be redone in float64.
 template <int KT>
@@ -254,13 +284,18 @@ __device__ __forceinline__ int item_bins32(const DevGeom &G, const TileCtx<KT> &
     const float4 a = W.a[t], b = W.b[t];
     const Item it{a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
     int jA, jB;
-    if (eval32(G, T.rho, T.invrho_es, T.invrho, T.has_b && (m & kMetaNeedB), it, jA, jB) !=
-        kDecided)
-        return -1;
-    int nv = 0;
-    if (jA >= 0) jj[nv++] = jA;
-    if (jB >= 0) jj[nv++] = jB;
-    return nv;
+    // the flag is per item, so the branch is uniform over the warp; the
+    // common path is compiled without root B
+    if (T.has_b && (m & kMetaNeedB)) {
+        if (eval32<true>(G, T.rho, T.invrho_es, T.invrho, it, jA, jB) != kDecided) return -1;
+        int nv = 0;
+        if (jA >= 0) jj[nv++] = jA;
+        if (jB >= 0) jj[nv++] = jB;
+        return nv;
+    }
+    if (eval32<false>(G, T.rho, T.invrho_es, T.invrho, it, jA, jB) != kDecided) return -1;
+    jj[0] = jA;
+    return jA >= 0 ? 1 : 0;
 }
 
 // Deferred redo requests: (hit, row-in-tile, column) pairs whose bins
@@ -384,8 +419,12 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 
     int my_fb = 0;
     int parity = 0;
+    HitPrefetch pf;
+    pf.start(x, y, n);
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
-        collect<KT, MODE>(G, T, x, y, n, base + threadIdx.x, lane, &qn[parity], W, &M, &H);
+        float xh, yh;
+        pf.next(x, y, n, base, xh, yh);
+        collect<KT, MODE>(G, T, xh, yh, n, base + threadIdx.x, lane, &qn[parity], W, &M, &H);
         __syncthreads();
         const int nq = qn[parity];
         if (threadIdx.x == 0) qn[parity ^ 1] = 0;   // last read before the previous barrier
