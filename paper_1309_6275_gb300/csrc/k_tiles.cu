@@ -60,7 +60,7 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
     unsigned char *p = reinterpret_cast<unsigned char *>(bestk + kThreads);
     const WorkList W = carve_worklist(p, QCAP);
     const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
-    __shared__ int qn[2], rn;
+    __shared__ int qn[2][2], rn;   // [parity][plain, others]
     __shared__ int band[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -72,7 +72,7 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
         for (int t = threadIdx.x; t < KT * ND * 16; t += kThreads) m4[t] = make_uint4(0, 0, 0, 0);
     }
     bestk[threadIdx.x] = 0ull;
-    if (threadIdx.x < 2) qn[threadIdx.x] = 0;
+    if (threadIdx.x < 4) qn[threadIdx.x >> 1][threadIdx.x & 1] = 0;
     if (threadIdx.x == 0) rn = 0;
     const int ncand = min(*d_count, cap);
     if (threadIdx.x == 0) {
@@ -121,11 +121,15 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
         float xh, yh;
         pf.next(x, y, n, base, xh, yh);
-        collect<KT>(G, T, xh, yh, n, base + threadIdx.x, lane, &qn[parity], W);
+        collect<KT>(G, T, xh, yh, n, base + threadIdx.x, lane, qn[parity], W);
         __syncthreads();
-        const int nq = qn[parity];
-        if (threadIdx.x == 0) qn[parity ^ 1] = 0;
-        for (int t = warp; t < nq; t += nwarps) {
+        const int nf = qn[parity][0], nq = nf + qn[parity][1];
+        if (threadIdx.x == 0) {
+            qn[parity ^ 1][0] = 0;
+            qn[parity ^ 1][1] = 0;
+        }
+        for (int tt = warp; tt < nq; tt += nwarps) {
+            const int t = item_slot<KT>(tt, nf);
             const int m = W.meta[t];
             unsigned long long key = 0ull;
             if (T.row_ok) {
@@ -307,7 +311,7 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     unsigned char *p = reinterpret_cast<unsigned char *>(bestk + kThreads);
     const WorkList W = carve_worklist(p, QCAP);
     const RedoQueue R = carve_redo(p + (size_t)QCAP * kItemBytes);
-    __shared__ int qn[2], rn;
+    __shared__ int qn[2][2], rn;   // [parity][plain, others]
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = kThreads / 32;
@@ -348,7 +352,7 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
         for (int t = threadIdx.x; t < KT * ND * 8; t += kThreads) m4[t] = make_uint4(0, 0, 0, 0);
     }
     bestk[threadIdx.x] = 0u;
-    if (threadIdx.x < 2) qn[threadIdx.x] = 0;
+    if (threadIdx.x < 4) qn[threadIdx.x >> 1][threadIdx.x & 1] = 0;
     if (threadIdx.x == 0) rn = 0;
     __syncthreads();
 
@@ -416,13 +420,37 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
         float xh, yh;
         pf.next(x, y, n, base, xh, yh);
-        collect<KT, kModeEvent>(G, T, xh, yh, n, base + threadIdx.x, lane, &qn[parity], W,
+        collect<KT, kModeEvent>(G, T, xh, yh, n, base + threadIdx.x, lane, qn[parity], W,
                                 &M);
         __syncthreads();
-        const int nq = qn[parity];
-        if (threadIdx.x == 0) qn[parity ^ 1] = 0;
+        const int nf = qn[parity][0], ns = qn[parity][1];
+        if (threadIdx.x == 0) {
+            qn[parity ^ 1][0] = 0;
+            qn[parity ^ 1][1] = 0;
+        }
+        // plain items: one root, no flags to test
 #pragma unroll 2
-        for (int t = warp; t < nq; t += nwarps) {
+        for (int t = warp; t < nf; t += nwarps) {
+            const int m = W.meta[t];
+            uint32_t key = 0u;
+            if (T.row_ok) {
+                const uint32_t *col = map + (m & kMetaCol) * ND * 32 + lane;
+                int j;
+                const int r = fast_bin32<KT>(G, T, W, t, j);
+                if (r == kFastVote) {
+                    key = col[j * 32];
+                } else if (r == kFastRedo && !push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) {
+                    int jj[2];
+                    const int nv =
+                        redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                    for (int v = 0; v < nv; ++v) key = max(key, col[jj[v] * 32]);
+                }
+            }
+            const uint32_t top = __reduce_max_sync(0xffffffffu, key);
+            if (top && lane == 0) atomicMax(&bestk[(m >> 6) - base], top);
+        }
+        // unsure items and items whose second root can reach the axis
+        for (int t = QCAP - ns + warp; t < QCAP; t += nwarps) {
             const int m = W.meta[t];
             uint32_t key = 0u;
             if (T.row_ok) {

@@ -155,10 +155,12 @@ struct HitCtx {
 };
 
 // Phase 1 for hit h at (xh, yh) (h >= n: no items).  Appends this warp's
-// items to the list with a single atomicAdd on *qn (all 32 lanes must call).
+// items to the list (all 32 lanes must call): plain items (neither unsure
+// nor needing root B) from the front, counted in q[0], the others from the
+// back of the kThreads * KT slots, counted in q[1].
 template <int KT, int MODE = kModePlain>
 __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, float xh,
-                                        float yh, int n, int h, int lane, int *qn,
+                                        float yh, int n, int h, int lane, int *q,
                                         const WorkList &W, const MaskCtx *M = nullptr,
                                         const HitCtx *H = nullptr)
 {
@@ -222,28 +224,47 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
             ic_[kl] = c;
         }
     }
-    const int mine = __popc(sel);
+    unsigned slow = 0u;
+#pragma unroll
+    for (int kl = 0; kl < KT; ++kl)
+        if ((sel & (1u << kl)) && (fl_[kl] & (kMetaUnsure | kMetaNeedB))) slow |= 1u << kl;
+    // one scan of both counts (plain in the low half, others in the high)
+    const int mine = __popc(sel & ~slow) | (__popc(slow) << 16);
     int incl = mine;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, o);
         if (lane >= o) incl += v;
     }
-    int wbase = 0;
-    if (lane == 31 && incl > 0) wbase = atomicAdd(qn, incl);
-    wbase = __shfl_sync(0xffffffffu, wbase, 31);
-    int pos = wbase + incl - mine;
+    int wf = 0, ws = 0;
+    if (lane == 31) {
+        if (incl & 0xffff) wf = atomicAdd(&q[0], incl & 0xffff);
+        if (incl >> 16) ws = atomicAdd(&q[1], incl >> 16);
+    }
+    wf = __shfl_sync(0xffffffffu, wf, 31);
+    ws = __shfl_sync(0xffffffffu, ws, 31);
+    const int excl = incl - mine;
+    int pf = wf + (excl & 0xffff);
+    int ps = ws + (excl >> 16);
 #pragma unroll
     for (int kl = 0; kl < KT; ++kl) {
         if (sel & (1u << kl)) {
+            const int pos = (slow & (1u << kl)) ? kThreads * KT - 1 - ps++ : pf++;
             const Item it = make_item(G, is_[kl], ic_[kl], r2, R1, T.rt);
             W.a[pos] = make_float4(it.s, it.c, it.r2, it.eD);
             W.b[pos] = make_float4(it.E1, it.E2, it.Qa, it.Qb);
             W.meta[pos] = (h << 6) | fl_[kl] | kl;
             if (MODE == kModeHit) W.hm[pos] = hm;
-            ++pos;
         }
     }
+}
+
+// Slot of the t-th item of a list with nf plain items at the front and the
+// others at the back of the kThreads * KT slots.
+template <int KT>
+__device__ __forceinline__ int item_slot(int t, int nf)
+{
+    return t < nf ? t : kThreads * KT - 1 - (t - nf);
 }
 
 // Hit coordinates of thread `threadIdx.x` in the round starting at base:
@@ -296,6 +317,36 @@ __device__ __forceinline__ int item_bins32(const DevGeom &G, const TileCtx<KT> &
     if (eval32<false>(G, T.rho, T.invrho_es, T.invrho, it, jA, jB) != kDecided) return -1;
     jj[0] = jA;
     return jA >= 0 ? 1 : 0;
+}
+
+// Plain items (not unsure, root B proven out of the axis): eval32<false>'s
+// arithmetic and decisions, returning kFastVote with the bin in j, kFastNone
+// or kFastRedo, without the general path's bookkeeping.
+enum : int { kFastNone = 0, kFastVote = 1, kFastRedo = 2 };
+
+template <int KT>
+__device__ __forceinline__ int fast_bin32(const DevGeom &G, const TileCtx<KT> &T,
+                                          const WorkList &W, int t, int &j)
+{
+    const float4 a = W.a[t], b4 = W.b[t];   // {s, c, r2, eD}, {E1, E2, Qa, Qb}
+    const float b = fmaf(T.rho, a.x, 1.0f);
+    const float pc = T.rho * a.y;
+    const float D = fmaf(-pc, pc, 1.0f);
+    const float Dp = fmaxf(D, 1e-30f);
+    const float rs = rsqrt_approx(Dp);
+    const float sq = Dp * rs;
+    const float q = -(b + copysignf(sq, b));
+    const float C = fmaf(T.rho, a.z, a.x + a.x);
+    const float iq = rcp_approx(q);
+    const float u = fmaf(C * iq, G.inv_delta_f, G.off_f);
+    const float e = fmaf(fabsf(iq), fmaf(b4.y, rs, b4.x), G.e3);
+    const float f = floorf(u);
+    const float fr = u - f;
+    j = (int)f;
+    if (D < -a.w) return kFastNone;                                   // no real root
+    if (D <= a.w) return kFastRedo;                                   // sign of D unproven
+    if ((u + e < 0.0f) | (u - e >= (float)G.n_d0)) return kFastNone; // outside the axis
+    return fminf(fr, 1.0f - fr) > e ? kFastVote : kFastRedo;
 }
 
 // Deferred redo requests: (hit, row-in-tile, column) pairs whose bins
@@ -375,7 +426,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * NW * 32);
     const WorkList W = carve_worklist(p, QCAP);
     const RedoQueue R = carve_redo(p + (size_t)QCAP * item_bytes(MODE));
-    __shared__ int qn[2], rn;
+    __shared__ int qn[2][2], rn;   // [parity][plain, others]
     __shared__ unsigned long long s_stats[2];
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -410,10 +461,8 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
         for (int t = threadIdx.x; t < KT * NW * 8; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
     }
-    if (threadIdx.x < 2) {
-        qn[threadIdx.x] = 0;
-        s_stats[threadIdx.x] = 0ull;
-    }
+    if (threadIdx.x < 4) qn[threadIdx.x >> 1][threadIdx.x & 1] = 0;
+    if (threadIdx.x < 2) s_stats[threadIdx.x] = 0ull;
     if (threadIdx.x == 0) rn = 0;
     __syncthreads();
 
@@ -424,13 +473,35 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
         float xh, yh;
         pf.next(x, y, n, base, xh, yh);
-        collect<KT, MODE>(G, T, xh, yh, n, base + threadIdx.x, lane, &qn[parity], W, &M, &H);
+        collect<KT, MODE>(G, T, xh, yh, n, base + threadIdx.x, lane, qn[parity], W, &M, &H);
         __syncthreads();
-        const int nq = qn[parity];
-        if (threadIdx.x == 0) qn[parity ^ 1] = 0;   // last read before the previous barrier
+        const int nf = qn[parity][0], ns = qn[parity][1];
+        if (threadIdx.x == 0) {   // last read before the previous barrier
+            qn[parity ^ 1][0] = 0;
+            qn[parity ^ 1][1] = 0;
+        }
         if (T.row_ok) {
+            // plain items: one root, no flags to test
 #pragma unroll 2
-            for (int t = warp; t < nq; t += nwarps) {
+            for (int t = warp; t < nf; t += nwarps) {
+                const int m = W.meta[t];
+                uint32_t *col = cnt + (m & kMetaCol) * NW * 32 + lane;
+                int j;
+                const int r = fast_bin32<KT>(G, T, W, t, j);
+                if (r == kFastVote) {
+                    if (MODE != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j]))
+                        tile_add<PACK>(col, j);
+                } else if (r == kFastRedo) {
+                    ++my_fb;
+                    if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
+                    int jj[2];
+                    int nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                    if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
+                    for (int v = 0; v < nv; ++v) tile_add<PACK>(col, jj[v]);
+                }
+            }
+            // unsure items and items whose second root can reach the axis
+            for (int t = kThreads * KT - ns + warp; t < kThreads * KT; t += nwarps) {
                 const int m = W.meta[t];
                 uint32_t *col = cnt + (m & kMetaCol) * NW * 32 + lane;
                 int jj[2];
