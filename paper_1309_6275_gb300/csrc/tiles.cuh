@@ -379,20 +379,43 @@ __device__ __forceinline__ bool push_redo(const RedoQueue &Q, int *n, int hit, i
 }
 
 // ------------------------------------------------------------------ vote
-// PACK: two 16-bit counters per shared word (d0 bins 2w and 2w + 1), which
-// halves the tile.  Exact while no cell can reach 65536 votes in the tile: a
-// cell gets at most two votes per hit, so it is used only for n <= 32767.
-template <bool PACK>
-__device__ __forceinline__ void tile_add(uint32_t *col, int j)
-{
-    if (PACK) atomicAdd(col + (j >> 1) * 32, 1u << ((j & 1) << 4));
-    else atomicAdd(col + j * 32, 1u);
-}
+// PACK: two 16-bit counters per shared word, which halves the tile.  With
+// KT >= 2 a word holds columns 2p and 2p + 1 of one (bin, row), so the
+// increment (1 or 65536) is fixed per work item and a vote costs one address
+// computation; with KT = 1 it holds bins 2w and 2w + 1.  Exact while no cell
+// can reach 65536 votes in the tile: a cell gets at most two votes per hit,
+// so it is used only for n <= 32767.
+template <int KT, bool PACK>
+struct TileCol {
+    uint32_t *base;
+    uint32_t inc;
 
-template <bool PACK>
+    __device__ __forceinline__ TileCol(uint32_t *cnt, int ND, int kl, int lane)
+    {
+        if (PACK && KT > 1) {
+            base = cnt + (kl >> 1) * ND * 32 + lane;
+            inc = 1u << ((kl & 1) << 4);
+        } else if (PACK) {
+            base = cnt + lane;
+            inc = 0u;
+        } else {
+            base = cnt + kl * ND * 32 + lane;
+            inc = 1u;
+        }
+    }
+
+    __device__ __forceinline__ void add(int j) const
+    {
+        if (PACK && KT == 1) atomicAdd(base + (j >> 1) * 32, 1u << ((j & 1) << 4));
+        else atomicAdd(base + j * 32, inc);
+    }
+};
+
+template <int KT, bool PACK>
 __device__ __forceinline__ uint32_t tile_get(const uint32_t *cnt, int ND, int kl, int j, int il)
 {
-    if (PACK) return (cnt[(kl * (ND >> 1) + (j >> 1)) * 32 + il] >> ((j & 1) << 4)) & 0xffffu;
+    if (PACK && KT > 1) return (cnt[((kl >> 1) * ND + j) * 32 + il] >> ((kl & 1) << 4)) & 0xffffu;
+    if (PACK) return (cnt[(j >> 1) * 32 + il] >> ((j & 1) << 4)) & 0xffffu;
     return cnt[(kl * ND + j) * 32 + il];
 }
 
@@ -485,25 +508,24 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 #pragma unroll 2
             for (int t = warp; t < nf; t += nwarps) {
                 const int m = W.meta[t];
-                uint32_t *col = cnt + (m & kMetaCol) * NW * 32 + lane;
+                const TileCol<KT, PACK> col(cnt, ND, m & kMetaCol, lane);
                 int j;
                 const int r = fast_bin32<KT>(G, T, W, t, j);
                 if (r == kFastVote) {
-                    if (MODE != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j]))
-                        tile_add<PACK>(col, j);
+                    if (MODE != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j])) col.add(j);
                 } else if (r == kFastRedo) {
                     ++my_fb;
                     if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
                     int jj[2];
                     int nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
                     if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
-                    for (int v = 0; v < nv; ++v) tile_add<PACK>(col, jj[v]);
+                    for (int v = 0; v < nv; ++v) col.add(jj[v]);
                 }
             }
             // unsure items and items whose second root can reach the axis
             for (int t = kThreads * KT - ns + warp; t < kThreads * KT; t += nwarps) {
                 const int m = W.meta[t];
-                uint32_t *col = cnt + (m & kMetaCol) * NW * 32 + lane;
+                const TileCol<KT, PACK> col(cnt, ND, m & kMetaCol, lane);
                 int jj[2];
                 int nv = item_bins32<KT>(G, T, W, t, m, jj);
                 if (nv < 0) {
@@ -512,8 +534,8 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                     nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
                 }
                 if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
-                if (nv > 0) tile_add<PACK>(col, jj[0]);
-                if (nv > 1) tile_add<PACK>(col, jj[1]);
+                if (nv > 0) col.add(jj[0]);
+                if (nv > 1) col.add(jj[1]);
             }
         }
         __syncthreads();
@@ -528,8 +550,8 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                 if (MODE == kModeHit)
                     nv = keep_allowed(halo_row_blocks(H.masks[h], T.i0 + il, G.n_rho), H.jmask, nv,
                                       jj);
-                uint32_t *col = cnt + kl * NW * 32 + il;
-                for (int v = 0; v < nv; ++v) tile_add<PACK>(col, jj[v]);
+                const TileCol<KT, PACK> col(cnt, ND, kl, il);
+                for (int v = 0; v < nv; ++v) col.add(jj[v]);
             }
             __syncthreads();
             if (threadIdx.x == 0) rn = 0;
@@ -549,7 +571,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         __align__(16) OutT e[KT];
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
-            const uint32_t v = keep ? tile_get<PACK>(cnt, ND, kl, j, il) : 0u;
+            const uint32_t v = keep ? tile_get<KT, PACK>(cnt, ND, kl, j, il) : 0u;
             my_votes += v;
             e[kl] = saturate<OutT>(v);
         }
