@@ -9,8 +9,11 @@
 //    j0-1..j0+16 x its columns plus one wrapped column on each side into
 //    shared memory with 16-byte loads, all issued before any is used, so a
 //    CTA waits for memory once instead of once per d0 bin; absent rows and
-//    bins read as -1.  Then thread = phi0 column walks the bins keeping a
-//    rolling 3 x 3 x 3 window in registers (9 shared loads per cell).
+//    bins read as -1.  Then thread = phi0 column walks the bins keeping, per
+//    row and bin of the rolling 3 x 3 x 3 window, the largest of its three
+//    columns (9 shared loads and 3 three-input maxima per cell); the 26
+//    comparisons become two against the maxima of the preceding and of the
+//    following neighbours.
 //  * Compaction keeps increasing logical index l = (i n_d0 + j) n_phi0 + k:
 //    pass 1 counts the peaks of every (i, j, k-block) segment, a
 //    device-wide scan turns counts into offsets (and the total), pass 2
@@ -90,51 +93,58 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
     }
     __syncthreads();
 
-    // ---- walk the bins: w[row][bin][col], bins j-1, j, j+1 at slots 0, 1, 2
+    // ---- walk the bins.  cm[r][s]: largest of columns k-1, k, k+1 in row
+    // i-1+r at bin j-1+s; c1/n1: the three columns of row i at bins j and
+    // j+1.  A cell is a peak when v >= T, v exceeds every neighbour that
+    // precedes it in l (row i-1, bin j-1 of row i, column k-1 of its own
+    // bin) and is at least every neighbour that follows it (row i+1, bin j+1,
+    // column k+1) -- the two maxima below; across the phi0 wrap the order of
+    // the column neighbours flips.
     const int c = threadIdx.x;
     const bool cok = c < ncol;
     const int k = k0 + c;
     const int cc = cok ? c : 0;                           // stays inside the staged row
     auto S = [&](int r, int jj) -> const int * { return sw + (r * (kJB + 2) + jj) * kSW + cc; };
-    int w[3][3][3];
+    int cm[3][3], c1[3], n1[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl) {
             const int *q = S(r, sl);
-            w[r][sl][0] = q[0]; w[r][sl][1] = q[1]; w[r][sl][2] = q[2];
+            cm[r][sl] = __vimax3_s32(q[0], q[1], q[2]);
+            if (r == 1 && sl == 1) { c1[0] = q[0]; c1[1] = q[1]; c1[2] = q[2]; }
         }
+    const bool wrap_lo = k == 0, wrap_hi = k == NP - 1;
     unsigned mine = 0u;
-    for (int jl = 0; jl < j1 - j0; ++jl) {
+    const int nj = j1 - j0;
 #pragma unroll
-        for (int r = 0; r < 3; ++r) {
-            const int *q = S(r, jl + 2);
-            w[r][2][0] = q[0]; w[r][2][1] = q[1]; w[r][2][2] = q[2];
-        }
-        const int v = w[1][1][1];
-        bool pk = cok && v >= G.threshold &&
-                  (!MASKED || ((inside >> region_block(j0 + jl, ND)) & 1u));
-        // rows i-1 and d0 bin j-1 (at row i) precede l: strictly greater;
-        // rows i+1 and d0 bin j+1 follow l: greater or equal.
+    for (int jl = 0; jl < kJB; ++jl) {
+        if (jl < nj) {   // uniform over the CTA
 #pragma unroll
-        for (int dj = 0; dj < 3; ++dj)
-#pragma unroll
-            for (int dk = 0; dk < 3; ++dk) pk = pk && (v > w[0][dj][dk]) && (v >= w[2][dj][dk]);
-#pragma unroll
-        for (int dk = 0; dk < 3; ++dk) pk = pk && (v > w[1][0][dk]) && (v >= w[1][2][dk]);
-        // same (i, j): phi0 neighbours; their order flips across the wrap
-        pk = pk && ((k != 0) ? (v > w[1][1][0]) : (v >= w[1][1][0]));
-        pk = pk && ((k != NP - 1) ? (v >= w[1][1][2]) : (v > w[1][1][2]));
-        const unsigned bal = __ballot_sync(0xffffffffu, pk);
-        if (lane == 0) bal_s[jl][warp] = bal;
-        mine |= (unsigned)pk << jl;
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int dk = 0; dk < 3; ++dk) {
-                w[r][0][dk] = w[r][1][dk];
-                w[r][1][dk] = w[r][2][dk];
+            for (int r = 0; r < 3; ++r) {
+                const int *q = S(r, jl + 2);
+                cm[r][2] = __vimax3_s32(q[0], q[1], q[2]);
+                if (r == 1) { n1[0] = q[0]; n1[1] = q[1]; n1[2] = q[2]; }
             }
+            const int v = c1[1];
+            const int before = max(__vimax3_s32(cm[0][0], cm[0][1], cm[0][2]),
+                                   __vimax3_s32(cm[1][0], wrap_lo ? -1 : c1[0],
+                                                wrap_hi ? c1[2] : -1));
+            const int after = max(__vimax3_s32(cm[2][0], cm[2][1], cm[2][2]),
+                                  __vimax3_s32(cm[1][2], wrap_lo ? c1[0] : -1,
+                                               wrap_hi ? -1 : c1[2]));
+            const bool pk = cok && v >= G.threshold && v > before && v >= after &&
+                            (!MASKED || ((inside >> region_block(j0 + jl, ND)) & 1u));
+            const unsigned bal = __ballot_sync(0xffffffffu, pk);
+            if (lane == 0) bal_s[jl][warp] = bal;
+            mine |= (unsigned)pk << jl;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cm[r][0] = cm[r][1];
+                cm[r][1] = cm[r][2];
+            }
+            c1[0] = n1[0]; c1[1] = n1[1]; c1[2] = n1[2];
+        }
     }
     __syncthreads();
     if constexpr (!WRITE) {
