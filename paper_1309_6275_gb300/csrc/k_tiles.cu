@@ -322,30 +322,61 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     const int L = min(toff[tile + 1] - l0, lcap);
     if (L == 0) return;   // no candidate box meets the tile (uniform over the CTA)
     __shared__ int s_ext[4];   // rows and d0 bins spanned by the candidates
+    __shared__ int s_mrange[3];   // smallest and largest candidate index, largest count
     if (threadIdx.x == 0) {
         s_ext[0] = s_ext[2] = 0x7fffffff;
         s_ext[1] = s_ext[3] = -1;
+        s_mrange[0] = 0x7fffffff;
+        s_mrange[1] = s_mrange[2] = -1;
     }
-
-    // sort the tile's candidates by index: bitonic sort in the map's space
-    int P = 1;
-    while (P < L) P <<= 1;
-    int *sb = reinterpret_cast<int *>(map);
-    for (int t = threadIdx.x; t < P; t += kThreads) sb[t] = t < L ? tlist[l0 + t] : 0x7fffffff;
     __syncthreads();
-    for (int k2 = 2; k2 <= P; k2 <<= 1)
-        for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
-            for (int t = threadIdx.x; t < P; t += kThreads) {
-                const int o = t ^ j2;
-                if (o > t) {
-                    const int a = sb[t], b = sb[o];
-                    const bool up = (t & k2) == 0;
-                    if ((a > b) == up) { sb[t] = b; sb[o] = a; }
-                }
-            }
-            __syncthreads();
+    // 32-bit cell keys must order (count, -m).  When the tile's candidates
+    // span fewer than 2^20 indices and no count passes 4095 (the usual case)
+    // the key is count << 20 | (2^20 - 1 - (m - m_min)); otherwise the
+    // candidates are sorted and the key is count << 16 | (65535 - rank).
+    {
+        int mlo = 0x7fffffff, mhi = -1, chi = -1;
+        for (int r = threadIdx.x; r < L; r += kThreads) {
+            const int m = tlist[l0 + r];
+            mlo = min(mlo, m);
+            mhi = max(mhi, m);
+            chi = max(chi, peaks[m].count);
         }
-    for (int t = threadIdx.x; t < L; t += kThreads) local[t] = sb[t];
+        mlo = __reduce_min_sync(0xffffffffu, mlo);
+        mhi = __reduce_max_sync(0xffffffffu, mhi);
+        chi = __reduce_max_sync(0xffffffffu, chi);
+        if (lane == 0) {
+            atomicMin(&s_mrange[0], mlo);
+            atomicMax(&s_mrange[1], mhi);
+            atomicMax(&s_mrange[2], chi);
+        }
+    }
+    __syncthreads();
+    const int m_min = s_mrange[0];
+    const bool offs = s_mrange[1] - m_min < (1 << 20) && s_mrange[2] < 4096;   // uniform
+    if (offs) {
+        for (int t = threadIdx.x; t < L; t += kThreads) local[t] = tlist[l0 + t];
+    } else {
+        // sort the tile's candidates by index: bitonic sort in the map's space
+        int P = 1;
+        while (P < L) P <<= 1;
+        int *sb = reinterpret_cast<int *>(map);
+        for (int t = threadIdx.x; t < P; t += kThreads) sb[t] = t < L ? tlist[l0 + t] : 0x7fffffff;
+        __syncthreads();
+        for (int k2 = 2; k2 <= P; k2 <<= 1)
+            for (int j2 = k2 >> 1; j2 > 0; j2 >>= 1) {
+                for (int t = threadIdx.x; t < P; t += kThreads) {
+                    const int o = t ^ j2;
+                    if (o > t) {
+                        const int a = sb[t], b = sb[o];
+                        const bool up = (t & k2) == 0;
+                        if ((a > b) == up) { sb[t] = b; sb[o] = a; }
+                    }
+                }
+                __syncthreads();
+            }
+        for (int t = threadIdx.x; t < L; t += kThreads) local[t] = sb[t];
+    }
     __syncthreads();
     {
         uint4 *m4 = reinterpret_cast<uint4 *>(map);
@@ -356,13 +387,15 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     if (threadIdx.x == 0) rn = 0;
     __syncthreads();
 
-    // scatter each candidate's box, key = count << 16 | (65535 - rank)
+    // scatter each candidate's box with its key
     int emin_i = 0x7fffffff, emax_i = -1, emin_j = 0x7fffffff, emax_j = -1;
     for (int r = threadIdx.x; r < L; r += kThreads) {
         const ht_peak pk = peaks[local[r]];
         emin_i = min(emin_i, pk.i_rho); emax_i = max(emax_i, pk.i_rho);
         emin_j = min(emin_j, pk.j_d0); emax_j = max(emax_j, pk.j_d0);
-        const uint32_t key = ((uint32_t)pk.count << 16) | (uint32_t)(0xffff - r);
+        const uint32_t key =
+            offs ? ((uint32_t)pk.count << 20) | (uint32_t)(0xfffff - (local[r] - m_min))
+                 : ((uint32_t)pk.count << 16) | (uint32_t)(0xffff - r);
 #pragma unroll
         for (int d = -1; d <= 1; ++d) {
             int kk = pk.k_phi0 + d;
@@ -410,8 +443,10 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     }
 
     auto to64 = [&](uint32_t k32) -> unsigned long long {
-        const int m = local[0xffff - (int)(k32 & 0xffffu)];
-        return ((unsigned long long)(k32 >> 16) << 32) | (0xffffffffull - (unsigned)m);
+        const int m = offs ? m_min + (0xfffff - (int)(k32 & 0xfffffu))
+                           : local[0xffff - (int)(k32 & 0xffffu)];
+        const unsigned cnt = offs ? k32 >> 20 : k32 >> 16;
+        return ((unsigned long long)cnt << 32) | (0xffffffffull - (unsigned)m);
     };
 
     int parity = 0;

@@ -147,6 +147,20 @@ def test_uint16_saturation_and_big_candidates():
     assert np.array_equal(r["zres"], zr)
 
 
+def test_association_keys_with_counts_above_4095():
+    """A normal event plus 5000 copies of one of its hits: cells on that
+    hit's curve pass 4095 votes, so association tiles there take the
+    sorted-rank keys while the others use index-offset keys."""
+    g = synth.geometry_of("single_64", count_bits=16)
+    ev = synth.make_event(synth.CONFIGS["single_64"]["gen"], 7)
+    rep = 5000
+    x = np.concatenate([ev.x, np.full(rep, ev.x[3], np.float32)])
+    y = np.concatenate([ev.y, np.full(rep, ev.y[3], np.float32)])
+    z = np.concatenate([ev.z, np.full(rep, ev.z[3], np.float32)])
+    r, pk, _ = full_check(g, x, y, z)
+    assert pk[:, 3].max() > 4095 and (pk[:, 3] < 4096).any()
+
+
 def test_capacity_truncates_the_candidate_list():
     ev = synth.make_event(synth.CONFIGS["single_64"]["gen"], 2)
     g = synth.geometry_of("single_64", threshold=3)
