@@ -32,9 +32,18 @@ constexpr int kPkThreads = 256;   // phi0 columns per CTA
 namespace {
 
 constexpr int kJB = 16;                         // d0 bins per CTA
-constexpr int kSW = kPkThreads + 2;             // staged columns (one wrapped each side)
 constexpr int kSlices = 3 * (kJB + 2);          // staged (row, bin) slices
-constexpr size_t kPkSmem = (size_t)kSlices * kSW * sizeof(int);
+
+// A staged slice holds the CTA's columns at [kOff, kOff + 256) -- 16-byte
+// aligned, so a 16-byte global load lands in one 16-byte shared store --
+// with the wrapped neighbour columns at kOff - 1 and kOff + ncol.
+template <typename T>
+struct Stage {
+    static constexpr int kOff = 16 / (int)sizeof(T);
+    static constexpr int kSW = kPkThreads + 2 * kOff;   // elements per slice
+    static constexpr size_t kBytes = (size_t)kSlices * kSW * sizeof(T);
+};
+constexpr size_t kPkSmemMax = Stage<int32_t>::kBytes;
 
 // MASKED: only cells inside *mask (a learned proposal's regions) can be
 // peaks; a CTA whose bins are all outside reads nothing.  An inside cell's
@@ -45,7 +54,9 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         const int *__restrict__ segoff, ht_peak *__restrict__ out, int cap,
         const unsigned long long *__restrict__ mask)
 {
-    extern __shared__ __align__(16) int sw[];            // [slice][kSW], slice = r (kJB+2) + jj
+    extern __shared__ __align__(16) unsigned char smraw[];
+    T *sw = reinterpret_cast<T *>(smraw);                // [slice][kSW], slice = r (kJB+2) + jj
+    constexpr int kOff = Stage<T>::kOff, kSW = Stage<T>::kSW;
     __shared__ unsigned bal_s[kJB][kPkThreads / 32];
     const int NP = G.n_phi0, ND = G.n_d0, NR = G.n_rho;
     const int nkb = (NP + kPkThreads - 1) / kPkThreads;
@@ -65,23 +76,18 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         }
     }
 
-    // ---- stage the window: interior columns with 16-byte loads
+    // ---- stage the window: interior columns with 16-byte loads and stores.
+    // Absent rows and bins read as 0: a peak has v >= threshold >= 1, so a 0
+    // neighbour never decides a comparison (as no neighbour at all).
     constexpr int VEC = 16 / (int)sizeof(T);
     const int nvec = ncol / VEC;                         // ncol is a multiple of 8
     for (int v = threadIdx.x; v < kSlices * nvec; v += kPkThreads) {
         const int sl = v / nvec, q = v - sl * nvec;
         const int ii = i - 1 + sl / (kJB + 2), jj = j0 - 1 + sl % (kJB + 2);
-        int *dst = sw + sl * kSW + 1 + q * VEC;
-        if (ii < 0 || ii >= NR || jj < 0 || jj >= ND) {
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) dst[e] = -1;
-        } else {
-            const uint4 u = *reinterpret_cast<const uint4 *>(
-                acc + ((size_t)ii * ND + jj) * NP + k0 + q * VEC);
-            const T *t = reinterpret_cast<const T *>(&u);
-#pragma unroll
-            for (int e = 0; e < VEC; ++e) dst[e] = (int)t[e];
-        }
+        uint4 u = make_uint4(0, 0, 0, 0);
+        if (ii >= 0 && ii < NR && jj >= 0 && jj < ND)
+            u = *reinterpret_cast<const uint4 *>(acc + ((size_t)ii * ND + jj) * NP + k0 + q * VEC);
+        *reinterpret_cast<uint4 *>(sw + sl * kSW + kOff + q * VEC) = u;
     }
     // the two wrapped neighbour columns of every slice
     for (int v = threadIdx.x; v < 2 * kSlices; v += kPkThreads) {
@@ -89,7 +95,8 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         const int ii = i - 1 + sl / (kJB + 2), jj = j0 - 1 + sl % (kJB + 2);
         const int kk = side ? (k0 + ncol) % NP : (k0 + NP - 1) % NP;
         const bool ok = ii >= 0 && ii < NR && jj >= 0 && jj < ND;
-        sw[sl * kSW + (side ? 1 + ncol : 0)] = ok ? (int)acc[((size_t)ii * ND + jj) * NP + kk] : -1;
+        sw[sl * kSW + (side ? kOff + ncol : kOff - 1)] =
+            ok ? acc[((size_t)ii * ND + jj) * NP + kk] : (T)0;
     }
     __syncthreads();
 
@@ -104,15 +111,19 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
     const bool cok = c < ncol;
     const int k = k0 + c;
     const int cc = cok ? c : 0;                           // stays inside the staged row
-    auto S = [&](int r, int jj) -> const int * { return sw + (r * (kJB + 2) + jj) * kSW + cc; };
+    // q[-1], q[0], q[1]: columns k - 1, k, k + 1 of slice (r, jj)
+    auto S = [&](int r, int jj) -> const T * {
+        return sw + (r * (kJB + 2) + jj) * kSW + kOff + cc;
+    };
     int cm[3][3], c1[3], n1[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int sl = 0; sl < 2; ++sl) {
-            const int *q = S(r, sl);
-            cm[r][sl] = __vimax3_s32(q[0], q[1], q[2]);
-            if (r == 1 && sl == 1) { c1[0] = q[0]; c1[1] = q[1]; c1[2] = q[2]; }
+            const T *q = S(r, sl);
+            const int a = (int)q[-1], b = (int)q[0], d = (int)q[1];
+            cm[r][sl] = __vimax3_s32(a, b, d);
+            if (r == 1 && sl == 1) { c1[0] = a; c1[1] = b; c1[2] = d; }
         }
     const bool wrap_lo = k == 0, wrap_hi = k == NP - 1;
     unsigned mine = 0u;
@@ -122,17 +133,18 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         if (jl < nj) {   // uniform over the CTA
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const int *q = S(r, jl + 2);
-                cm[r][2] = __vimax3_s32(q[0], q[1], q[2]);
-                if (r == 1) { n1[0] = q[0]; n1[1] = q[1]; n1[2] = q[2]; }
+                const T *q = S(r, jl + 2);
+                const int a = (int)q[-1], b = (int)q[0], d = (int)q[1];
+                cm[r][2] = __vimax3_s32(a, b, d);
+                if (r == 1) { n1[0] = a; n1[1] = b; n1[2] = d; }
             }
             const int v = c1[1];
             const int before = max(__vimax3_s32(cm[0][0], cm[0][1], cm[0][2]),
-                                   __vimax3_s32(cm[1][0], wrap_lo ? -1 : c1[0],
-                                                wrap_hi ? c1[2] : -1));
+                                   __vimax3_s32(cm[1][0], wrap_lo ? 0 : c1[0],
+                                                wrap_hi ? c1[2] : 0));
             const int after = max(__vimax3_s32(cm[2][0], cm[2][1], cm[2][2]),
-                                  __vimax3_s32(cm[1][2], wrap_lo ? c1[0] : -1,
-                                               wrap_hi ? -1 : c1[2]));
+                                  __vimax3_s32(cm[1][2], wrap_lo ? c1[0] : 0,
+                                               wrap_hi ? 0 : c1[2]));
             const bool pk = cok && v >= G.threshold && v > before && v >= after &&
                             (!MASKED || ((inside >> region_block(j0 + jl, ND)) & 1u));
             const unsigned bal = __ballot_sync(0xffffffffu, pk);
@@ -161,7 +173,7 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
             const int seg = (i * ND + j0 + jl) * nkb + kb;
             int pos = segoff[seg] + __popc(bal_s[jl][warp] & ((1u << lane) - 1u));
             for (int w2 = 0; w2 < warp; ++w2) pos += __popc(bal_s[jl][w2]);
-            if (pos < cap) out[pos] = ht_peak{i, j0 + jl, k, S(1, jl + 1)[1]};
+            if (pos < cap) out[pos] = ht_peak{i, j0 + jl, k, (int)S(1, jl + 1)[0]};
         }
     }
 }
@@ -174,12 +186,12 @@ cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, i
     const int nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     dim3 grid(nkb, (G.n_d0 + kJB - 1) / kJB, G.n_rho);
     const int nseg = G.n_rho * G.n_d0 * nkb;
-    k_peaks<T, false, MASKED><<<grid, kPkThreads, kPkSmem, st>>>(G, acc, segcnt, nullptr,
-                                                                 nullptr, 0, mask);
+    k_peaks<T, false, MASKED><<<grid, kPkThreads, Stage<T>::kBytes, st>>>(
+        G, acc, segcnt, nullptr, nullptr, 0, mask);
     cudaError_t e = scan_exclusive(segcnt, segoff, nullptr, nseg, nullptr, d_count, tmp, st);
     if (e != cudaSuccess) return e;
-    k_peaks<T, true, MASKED><<<grid, kPkThreads, kPkSmem, st>>>(G, acc, nullptr, segoff, peaks,
-                                                                cap, mask);
+    k_peaks<T, true, MASKED><<<grid, kPkThreads, Stage<T>::kBytes, st>>>(
+        G, acc, nullptr, segoff, peaks, cap, mask);
     return cudaGetLastError();
 }
 
@@ -196,7 +208,7 @@ cudaError_t prepare_peaks_kernels()
         (const void *)k_peaks<int32_t, false, true>,   (const void *)k_peaks<int32_t, true, true>};
     for (const void *f : fns) {
         const cudaError_t e =
-            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPkSmem);
+            cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPkSmemMax);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
