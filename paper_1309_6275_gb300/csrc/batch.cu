@@ -5,10 +5,12 @@
 // from device counters (events ordered largest first, so 2k- and 60k-hit
 // events share the GPU without per-event launch tails); peak finding and
 // candidate lists run per event slot; the (z0, cot theta) vote runs over all
-// candidates of the batch at once.  Per-batch data (hit offsets, event order)
-// lives in device memory, uploaded from pinned staging before each replay,
-// so one graph serves every batch with the same number of events.  An
-// autotuner times the tile widths on a sample batch.
+// candidates of the batch at once.  The vote and association tiles scan
+// per-event lists of the hits whose angular window meets their columns
+// (k_buckets.cu), built at the head of the vote stage.  Per-batch data (hit
+// offsets, event order) lives in device memory, uploaded from pinned staging
+// before each replay, so one graph serves every batch with the same number
+// of events.  An autotuner times the tile widths on a sample batch.
 //
 // Masked and learned runs: the vote and the peak finding take a per-event
 // region mask (given by the caller, or computed at the head of the same
@@ -32,7 +34,7 @@ namespace ht {
 cudaError_t launch_vote_batch(const DevGeom &G, const float *x, const float *y, const int *off,
                               const int *order, const int *d_nev, uint16_t *acc,
                               size_t acc_stride, unsigned long long *stats, int *head, bool pack,
-                              int kt, int sms, cudaStream_t st);
+                              int kt, int sms, cudaStream_t st, const HitBuckets *hb);
 int assoc32_kt(const DevGeom &G);
 int assoc32_ntiles(const DevGeom &G, int kt);
 cudaError_t launch_cand_lists(const DevGeom &G, int kt, const ht_peak *peaks, const int *d_count,
@@ -42,7 +44,7 @@ cudaError_t launch_assoc_batch(const DevGeom &G, int kt, const float *x, const f
                                const int *off, const int *order, const int *d_nev,
                                const ht_peak *peaks, int cap, const int *toff, size_t tstride,
                                const int *tlist, size_t lstride, unsigned long long *gbest,
-                               int *head, int sms, cudaStream_t st);
+                               int *head, int sms, cudaStream_t st, const HitBuckets *hb);
 cudaError_t launch_assoc_final_batch(const unsigned long long *gbest, const int *off,
                                      const int *d_nev, int *assign, int max_hits, cudaStream_t st);
 size_t vote_z_batch_workspace_bytes(int n_ev, int cap, int max_hits);
@@ -55,7 +57,8 @@ cudaError_t launch_vote_batch_masked(const DevGeom &G, const float *x, const flo
                                      const int *off, const int *order, const int *d_nev,
                                      uint16_t *acc, size_t acc_stride, unsigned long long *stats,
                                      int *head, bool pack, int kt, int sms,
-                                     const unsigned long long *masks, cudaStream_t st);
+                                     const unsigned long long *masks, cudaStream_t st,
+                                     const HitBuckets *hb);
 cudaError_t launch_region_mask(const void *params_bf16, const float *x, const float *y,
                                const float *z, const uint8_t *layer, const int *off, int n_ev,
                                int max_hits, float tau, float fmax, int grow, float *mass,
@@ -65,7 +68,7 @@ cudaError_t launch_vote_batch_hitmask(const DevGeom &G, const float *x, const fl
                                       uint16_t *acc, size_t acc_stride,
                                       unsigned long long *stats, int *head, bool pack, int kt,
                                       int sms, const unsigned long long *hit_masks,
-                                      cudaStream_t st);
+                                      cudaStream_t st, const HitBuckets *hb);
 cudaError_t launch_hit_masks(const void *params_bf16, const float *x, const float *y,
                              const float *z, const uint8_t *layer, int n, const int *d_n,
                              int topk, float pmin, unsigned long long *hit_masks, cudaStream_t st);
@@ -120,6 +123,8 @@ struct ht_batch {
     size_t lstride;
     char *z_ws;
     float *mass;        // per-event region masses of the learned proposal
+    char *bk_ws;        // per-event hit lists by column group (k_buckets.cu)
+    ht::HitBuckets bk;
     GraphEntry cache[kGraphCache];
     int ncache;
     bool use_graph;
@@ -150,6 +155,7 @@ void free_batch(ht_batch *b)
     cudaFree(b->tlist);
     cudaFree(b->z_ws);
     cudaFree(b->mass);
+    cudaFree(b->bk_ws);
     if (b->h_meta) cudaFreeHost(b->h_meta);
     if (b->meta_done) cudaEventDestroy(b->meta_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -201,15 +207,21 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     }
     e = mark(1);
     if (e != cudaSuccess) return e;
+    // the hits each tile scans: lists by column group (every tile width the
+    // batch uses divides the group)
+    e = ht::launch_hit_buckets(G, x, y, off, meta + 2, b->max_hits, b->bk, b->sms, st);
+    if (e != cudaSuccess) return e;
     // vote: events above the packed-counter limit, then the others
     auto vote = [&](const int *order, const int *d_nev, int *head, bool pack, int kt) {
         if (R.hit_masks)
             return ht::launch_vote_batch_hitmask(G, x, y, off, order, d_nev, b->acc, b->cells,
-                                                 st64, head, pack, kt, b->sms, R.hit_masks, st);
+                                                 st64, head, pack, kt, b->sms, R.hit_masks, st,
+                                                 &b->bk);
         return masks ? ht::launch_vote_batch_masked(G, x, y, off, order, d_nev, b->acc, b->cells,
-                                                    st64, head, pack, kt, b->sms, masks, st)
+                                                    st64, head, pack, kt, b->sms, masks, st,
+                                                    &b->bk)
                      : ht::launch_vote_batch(G, x, y, off, order, d_nev, b->acc, b->cells, st64,
-                                             head, pack, kt, b->sms, st);
+                                             head, pack, kt, b->sms, st, &b->bk);
     };
     e = vote(order_big_of(meta, me), meta + 0, b->heads + 0, false, b->kt_big);
     if (e != cudaSuccess) return e;
@@ -235,7 +247,7 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     if (e != cudaSuccess) return e;
     e = ht::launch_assoc_batch(G, b->kt_assoc, x, y, off, order_all_of(meta, me), meta + 2, peaks,
                                b->cap, b->toff, (size_t)b->ntiles + 1, b->tlist, b->lstride,
-                               b->gbest, b->heads + 2, b->sms, st);
+                               b->gbest, b->heads + 2, b->sms, st, &b->bk);
     if (e == cudaSuccess) e = mark(4);
     if (e != cudaSuccess) return e;
     e = ht::launch_assoc_final_batch(b->gbest, off, meta + 2, assign, b->max_hits, st);
@@ -349,6 +361,8 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     M((void **)&b->tlist, b->lstride * sizeof(int) * max_events);
     M((void **)&b->z_ws, ht::vote_z_batch_workspace_bytes(max_events, cap, max_hits));
     M((void **)&b->mass, (size_t)max_events * 64 * sizeof(float));
+    M((void **)&b->bk_ws, ht::hit_bucket_bytes(G, max_events, max_hits));
+    if (e == cudaSuccess) b->bk = ht::carve_hit_buckets(G, max_events, b->bk_ws);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_meta, b->meta_ints * 4);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->meta_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);

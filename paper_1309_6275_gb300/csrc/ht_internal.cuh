@@ -310,6 +310,38 @@ cudaError_t launch_vote(const DevGeom &G, const float *x, const float *y, int n,
 cudaError_t launch_vote_masked(const DevGeom &G, const float *x, const float *y, int n,
                                void *acc, unsigned long long *stats,
                                const unsigned long long *mask, cudaStream_t st);
+// Per-event lists of the hits that can vote in each group of kGroupCols
+// phi0 columns (k_buckets.cu): group g of event e holds cnt[e G + g] local
+// hit indices at ent + start[e G + g], G = ngroups.
+constexpr int kGroupCols = 8;
+struct HitBuckets {
+    int *cnt, *start, *cursor, *ent;
+    void *tmp;
+    int ngroups, ncells;
+};
+// What a tile kernel reads of the lists (ent null: no lists).
+struct BucketView {
+    const int *cnt, *start, *ent;
+    int ngroups;
+
+    __device__ __forceinline__ void list(int e, int k0, const int *&hl, int &nl) const
+    {
+        const int c = e * ngroups + k0 / kGroupCols;
+        hl = ent + start[c];
+        nl = cnt[c];
+    }
+};
+inline BucketView bucket_view(const HitBuckets *b)
+{
+    return b ? BucketView{b->cnt, b->start, b->ent, b->ngroups}
+             : BucketView{nullptr, nullptr, nullptr, 0};
+}
+size_t hit_bucket_bytes(const DevGeom &G, int max_events, int max_hits);
+HitBuckets carve_hit_buckets(const DevGeom &G, int max_events, void *ws);
+cudaError_t launch_hit_buckets(const DevGeom &G, const float *x, const float *y, const int *off,
+                               const int *d_nev, int max_hits, const HitBuckets &b, int sms,
+                               cudaStream_t st);
+
 // Swept-interval vote: each (rho row, phi0 column) votes the d0 bins the
 // hit's roots sweep between the column's edges (k_swept.cu).
 cudaError_t launch_vote_swept(const DevGeom &G, const float *x, const float *y, int n, void *acc,

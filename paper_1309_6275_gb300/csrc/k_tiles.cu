@@ -116,12 +116,14 @@ k_assoc(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int
     __syncthreads();
 
     int parity = 0;
+    const HitSeq S{nullptr, n};
     HitPrefetch pf;
-    pf.start(x, y, n);
+    pf.start(x, y, S);
     for (int base = 0; base < n; base += kThreads, parity ^= 1) {
+        int ha;
         float xh, yh;
-        pf.next(x, y, n, base, xh, yh);
-        collect<KT>(G, T, xh, yh, n, base + threadIdx.x, lane, qn[parity], W);
+        pf.next(x, y, S, base, ha, xh, yh);
+        collect<KT>(G, T, xh, yh, n, base + threadIdx.x, ha, lane, qn[parity], W);
         __syncthreads();
         const int nf = qn[parity][0], nq = nf + qn[parity][1];
         if (threadIdx.x == 0) {
@@ -293,6 +295,8 @@ inline void cand_tiles_pass(const ht_peak *peaks, const int *d_count, int cap, i
                                      list ? tcur : nullptr, list);
 }
 
+// hl (optional): scan only the nl hits hl[0 .. nl) of the event (a superset
+// of those that can vote in the tile's columns); otherwise all n.
 template <int KT>
 __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__restrict__ x,
                                              const float *__restrict__ y, int n,
@@ -300,7 +304,8 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
                                              const int *__restrict__ toff,
                                              const int *__restrict__ tlist, int lcap,
                                              unsigned long long *__restrict__ gbest, int tx,
-                                             int ty)
+                                             int ty, const int *__restrict__ hl = nullptr,
+                                             int nl = 0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
@@ -450,12 +455,14 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
     };
 
     int parity = 0;
+    const HitSeq S{hl, hl ? nl : n};
     HitPrefetch pf;
-    pf.start(x, y, n);
-    for (int base = 0; base < n; base += kThreads, parity ^= 1) {
+    pf.start(x, y, S);
+    for (int base = 0; base < S.n; base += kThreads, parity ^= 1) {
+        int ha;
         float xh, yh;
-        pf.next(x, y, n, base, xh, yh);
-        collect<KT, kModeEvent>(G, T, xh, yh, n, base + threadIdx.x, lane, qn[parity], W,
+        pf.next(x, y, S, base, ha, xh, yh);
+        collect<KT, kModeEvent>(G, T, xh, yh, S.n, base + threadIdx.x, ha, lane, qn[parity], W,
                                 &M);
         __syncthreads();
         const int nf = qn[parity][0], ns = qn[parity][1];
@@ -474,11 +481,14 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
                 const int r = fast_bin32<KT>(G, T, W, t, j);
                 if (r == kFastVote) {
                     key = col[j * 32];
-                } else if (r == kFastRedo && !push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) {
-                    int jj[2];
-                    const int nv =
-                        redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
-                    for (int v = 0; v < nv; ++v) key = max(key, col[jj[v] * 32]);
+                } else if (r == kFastRedo) {
+                    const int hh = S.hit(m >> 6);
+                    if (!push_redo(R, &rn, hh, lane, m & kMetaCol)) {
+                        int jj[2];
+                        const int nv =
+                            redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
+                        for (int v = 0; v < nv; ++v) key = max(key, col[jj[v] * 32]);
+                    }
                 }
             }
             const uint32_t top = __reduce_max_sync(0xffffffffu, key);
@@ -492,8 +502,11 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
                 const uint32_t *col = map + (m & kMetaCol) * ND * 32 + lane;
                 int jj[2];
                 int nv = item_bins32<KT>(G, T, W, t, m, jj);
-                if (nv < 0 && !push_redo(R, &rn, m >> 6, lane, m & kMetaCol))
-                    nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                if (nv < 0) {
+                    const int hh = S.hit(m >> 6);
+                    if (!push_redo(R, &rn, hh, lane, m & kMetaCol))
+                        nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
+                }
                 if (nv > 0) key = col[jj[0] * 32];
                 if (nv > 1) key = max(key, col[jj[1] * 32]);
             }
@@ -501,13 +514,14 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
             if (top && lane == 0) atomicMax(&bestk[(m >> 6) - base], top);
         }
         __syncthreads();
+        // flush this round's per-position best keys (slot t belongs to thread t)
         const uint32_t b = bestk[threadIdx.x];
         if (b) {
-            atomicMax(&gbest[base + threadIdx.x], to64(b));
+            atomicMax(&gbest[ha], to64(b));
             bestk[threadIdx.x] = 0u;
         }
         const int nr = min(rn, kRedoCap);
-        if (nr >= kRedoCap / 2 || base + kThreads >= n) {
+        if (nr >= kRedoCap / 2 || base + kThreads >= S.n) {
             for (int t = threadIdx.x; t < nr; t += kThreads) {
                 const int h = R.hit[t], rc = R.rc[t];
                 const int il = rc >> 4, kl = rc & 15;
@@ -543,7 +557,7 @@ k_assoc32_batch(DevGeom G, const float *__restrict__ x, const float *__restrict_
                 const int *__restrict__ d_nev,
                 const ht_peak *__restrict__ peaks, int cap, const int *__restrict__ toff,
                 size_t tstride, const int *__restrict__ tlist, size_t lstride, int lcap,
-                unsigned long long *__restrict__ gbest, int *__restrict__ head)
+                unsigned long long *__restrict__ gbest, int *__restrict__ head, BucketView bk)
 {
     __shared__ int s_item;
     const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 31) / 32, ntiles = ntx * nty;
@@ -555,10 +569,13 @@ k_assoc32_batch(DevGeom G, const float *__restrict__ x, const float *__restrict_
         if (item >= total) break;
         const int e = order[item / ntiles], t = item % ntiles;
         const int a = off[e], n = off[e + 1] - a;
+        const int *hl = nullptr;
+        int nl = 0;
+        if (bk.ent) bk.list(e, (t % ntx) * KT, hl, nl);
         if (n > 0)
             assoc32_tile<KT>(G, x + a, y + a, n, peaks + (size_t)e * cap,
                              toff + (size_t)e * tstride, tlist + (size_t)e * lstride, lcap,
-                             gbest + a, t % ntx, t / ntx);
+                             gbest + a, t % ntx, t / ntx, hl, nl);
         __syncthreads();
     }
 }
@@ -698,10 +715,10 @@ cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, i
 cudaError_t launch_vote_batch(const DevGeom &G, const float *x, const float *y, const int *off,
                               const int *order, const int *d_nev, uint16_t *acc,
                               size_t acc_stride, unsigned long long *stats, int *head, bool pack,
-                              int kt, int sms, cudaStream_t st)
+                              int kt, int sms, cudaStream_t st, const HitBuckets *hb)
 {
     return launch_vote_batch_t<kModePlain>(G, x, y, off, order, d_nev, acc, acc_stride, stats,
-                                           head, pack, kt, sms, nullptr, st);
+                                           head, pack, kt, sms, nullptr, st, bucket_view(hb));
 }
 
 // Association tile width for uint16 geometries (largest fitting three CTAs
@@ -735,8 +752,9 @@ cudaError_t launch_assoc_batch(const DevGeom &G, int kt, const float *x, const f
                                const int *off, const int *order, const int *d_nev,
                                const ht_peak *peaks, int cap, const int *toff, size_t tstride,
                                const int *tlist, size_t lstride, unsigned long long *gbest,
-                               int *head, int sms, cudaStream_t st)
+                               int *head, int sms, cudaStream_t st, const HitBuckets *hb)
 {
+    const BucketView bk = bucket_view(hb);
 #define HT_AB(KTV)                                                                            \
     do {                                                                                      \
         int occ = 0;                                                                          \
@@ -744,7 +762,7 @@ cudaError_t launch_assoc_batch(const DevGeom &G, int kt, const float *x, const f
                                                       assoc32_smem<KTV>(G));                  \
         k_assoc32_batch<KTV><<<sms * (occ > 0 ? occ : 1), kThreads, assoc32_smem<KTV>(G),    \
                                st>>>(G, x, y, off, order, d_nev, peaks, cap, toff, tstride,   \
-                                     tlist, lstride, assoc32_lcap<KTV>(G), gbest, head);      \
+                                     tlist, lstride, assoc32_lcap<KTV>(G), gbest, head, bk);  \
         return cudaGetLastError();                                                            \
     } while (0)
     if (kt == 4) HT_AB(4);

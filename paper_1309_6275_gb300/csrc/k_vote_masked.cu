@@ -29,10 +29,11 @@ cudaError_t launch_vote_batch_masked(const DevGeom &G, const float *x, const flo
                                      const int *off, const int *order, const int *d_nev,
                                      uint16_t *acc, size_t acc_stride, unsigned long long *stats,
                                      int *head, bool pack, int kt, int sms,
-                                     const unsigned long long *masks, cudaStream_t st)
+                                     const unsigned long long *masks, cudaStream_t st,
+                                     const HitBuckets *hb)
 {
     return launch_vote_batch_t<kModeEvent>(G, x, y, off, order, d_nev, acc, acc_stride, stats,
-                                           head, pack, kt, sms, masks, st);
+                                           head, pack, kt, sms, masks, st, bucket_view(hb));
 }
 
 cudaError_t launch_vote_hitmask(const DevGeom &G, const float *x, const float *y, int n,
@@ -47,10 +48,10 @@ cudaError_t launch_vote_batch_hitmask(const DevGeom &G, const float *x, const fl
                                       uint16_t *acc, size_t acc_stride,
                                       unsigned long long *stats, int *head, bool pack, int kt,
                                       int sms, const unsigned long long *hit_masks,
-                                      cudaStream_t st)
+                                      cudaStream_t st, const HitBuckets *hb)
 {
     return launch_vote_batch_t<kModeHit>(G, x, y, off, order, d_nev, acc, acc_stride, stats,
-                                         head, pack, kt, sms, hit_masks, st);
+                                         head, pack, kt, sms, hit_masks, st, bucket_view(hb));
 }
 
 cudaError_t prepare_masked_vote_kernels(int max_smem)

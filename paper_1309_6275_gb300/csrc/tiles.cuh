@@ -154,13 +154,14 @@ struct HitCtx {
     }
 };
 
-// Phase 1 for hit h at (xh, yh) (h >= n: no items).  Appends this warp's
-// items to the list (all 32 lanes must call): plain items (neither unsure
-// nor needing root B) from the front, counted in q[0], the others from the
-// back of the kThreads * KT slots, counted in q[1].
+// Phase 1 for the hit at position h of the tile's hit sequence (h >= n: no
+// items), hit index ha, at (xh, yh).  Items record the position.  Appends
+// this warp's items to the list (all 32 lanes must call): plain items
+// (neither unsure nor needing root B) from the front, counted in q[0], the
+// others from the back of the kThreads * KT slots, counted in q[1].
 template <int KT, int MODE = kModePlain>
 __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, float xh,
-                                        float yh, int n, int h, int lane, int *q,
+                                        float yh, int n, int h, int ha, int lane, int *q,
                                         const WorkList &W, const MaskCtx *M = nullptr,
                                         const HitCtx *H = nullptr)
 {
@@ -172,7 +173,7 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
     float hwlo = 0.0f, hwhi = 0.0f;
     bool live = h < n;
     if (MODE == kModeHit && live) {
-        hm = H->masks[h];
+        hm = H->masks[ha];
         unsigned tb = 0u;
         for (int b = H->rb_lo; b <= H->rb_hi; ++b) tb |= (unsigned)(hm >> (8 * b)) & 0xffu;
         live = tb != 0u;
@@ -267,31 +268,44 @@ __device__ __forceinline__ int item_slot(int t, int nf)
     return t < nf ? t : kThreads * KT - 1 - (t - nf);
 }
 
-// Hit coordinates of thread `threadIdx.x` in the round starting at base:
-// the next round's are loaded while this round runs.
+// The hits a tile scans: positions 0 .. n - 1 of a list (hit index hl[p])
+// or of the event itself (hl null: hit index p).
+struct HitSeq {
+    const int *hl;
+    int n;
+
+    __device__ __forceinline__ int hit(int p) const { return hl ? __ldg(hl + p) : p; }
+};
+
+// Hit index and coordinates of thread `threadIdx.x` in the round starting
+// at base: the next round's are loaded while this round runs.
 struct HitPrefetch {
+    int hn;
     float xn, yn;
 
-    __device__ __forceinline__ void start(const float *__restrict__ x,
-                                          const float *__restrict__ y, int n)
+    __device__ __forceinline__ void load(const float *__restrict__ x,
+                                         const float *__restrict__ y, const HitSeq &S, int p)
     {
-        const int h = threadIdx.x;
-        xn = h < n ? __ldg(x + h) : 0.0f;
-        yn = h < n ? __ldg(y + h) : 0.0f;
+        hn = p < S.n ? S.hit(p) : 0;
+        xn = p < S.n ? __ldg(x + hn) : 0.0f;
+        yn = p < S.n ? __ldg(y + hn) : 0.0f;
     }
 
-    // (xh, yh) of round `base`; issues the loads of round base + blockDim.x
-    __device__ __forceinline__ void next(const float *__restrict__ x,
-                                         const float *__restrict__ y, int n, int base,
-                                         float &xh, float &yh)
+    __device__ __forceinline__ void start(const float *__restrict__ x,
+                                          const float *__restrict__ y, const HitSeq &S)
     {
+        load(x, y, S, threadIdx.x);
+    }
+
+    // hit and (xh, yh) of round `base`; issues the loads of round base + blockDim.x
+    __device__ __forceinline__ void next(const float *__restrict__ x,
+                                         const float *__restrict__ y, const HitSeq &S, int base,
+                                         int &ha, float &xh, float &yh)
+    {
+        ha = hn;
         xh = xn;
         yh = yn;
-        const int h = base + (int)blockDim.x + (int)threadIdx.x;
-        if (h < n) {
-            xn = __ldg(x + h);
-            yn = __ldg(y + h);
-        }
+        load(x, y, S, base + (int)blockDim.x + (int)threadIdx.x);
     }
 };
 
@@ -433,13 +447,16 @@ __device__ __forceinline__ int keep_allowed(unsigned bm, const uint8_t *jmask, i
 // count); a tile without halo cells returns at once and writes nothing.
 // kModeHit: hit h's votes count only in the halo cells of hmask[h]; every
 // cell is written.
+// hl (optional): the tile scans only the nl hits hl[0 .. nl) of the event
+// (a superset of those that can vote in its columns); otherwise all n.
 template <int KT, typename OutT, bool PACK, int MODE = kModePlain>
 __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restrict__ x,
                                           const float *__restrict__ y, int n,
                                           OutT *__restrict__ acc,
                                           unsigned long long *__restrict__ stats, int tx, int ty,
                                           unsigned long long mask = ~0ull,
-                                          const unsigned long long *__restrict__ hmask = nullptr)
+                                          const unsigned long long *__restrict__ hmask = nullptr,
+                                          const int *__restrict__ hl = nullptr, int nl = 0)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
@@ -491,12 +508,15 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 
     int my_fb = 0;
     int parity = 0;
+    const HitSeq S{hl, hl ? nl : n};
     HitPrefetch pf;
-    pf.start(x, y, n);
-    for (int base = 0; base < n; base += kThreads, parity ^= 1) {
+    pf.start(x, y, S);
+    for (int base = 0; base < S.n; base += kThreads, parity ^= 1) {
+        int ha;
         float xh, yh;
-        pf.next(x, y, n, base, xh, yh);
-        collect<KT, MODE>(G, T, xh, yh, n, base + threadIdx.x, lane, qn[parity], W, &M, &H);
+        pf.next(x, y, S, base, ha, xh, yh);
+        collect<KT, MODE>(G, T, xh, yh, S.n, base + threadIdx.x, ha, lane, qn[parity], W, &M,
+                          &H);
         __syncthreads();
         const int nf = qn[parity][0], ns = qn[parity][1];
         if (threadIdx.x == 0) {   // last read before the previous barrier
@@ -515,9 +535,10 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                     if (MODE != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j])) col.add(j);
                 } else if (r == kFastRedo) {
                     ++my_fb;
-                    if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
+                    const int hh = S.hit(m >> 6);
+                    if (push_redo(R, &rn, hh, lane, m & kMetaCol)) continue;
                     int jj[2];
-                    int nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                    int nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
                     if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
                     for (int v = 0; v < nv; ++v) col.add(jj[v]);
                 }
@@ -530,8 +551,9 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                 int nv = item_bins32<KT>(G, T, W, t, m, jj);
                 if (nv < 0) {
                     ++my_fb;
-                    if (push_redo(R, &rn, m >> 6, lane, m & kMetaCol)) continue;
-                    nv = redo_bins(G, x[m >> 6], y[m >> 6], T.irow, T.k0 + (m & kMetaCol), jj);
+                    const int hh = S.hit(m >> 6);
+                    if (push_redo(R, &rn, hh, lane, m & kMetaCol)) continue;
+                    nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
                 }
                 if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
                 if (nv > 0) col.add(jj[0]);
@@ -541,7 +563,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         __syncthreads();
         // drain the deferred redos when the queue is half full or at the end
         const int nr = min(rn, kRedoCap);
-        if (nr >= kRedoCap / 2 || base + kThreads >= n) {
+        if (nr >= kRedoCap / 2 || base + kThreads >= S.n) {
             for (int t = threadIdx.x; t < nr; t += kThreads) {
                 const int h = R.hit[t], rc = R.rc[t];
                 const int il = rc >> 4, kl = rc & 15;
@@ -619,13 +641,16 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
 // first), so uneven events share the GPU without per-event launch tails.
 // kModeEvent: event e votes under masks[e]; kModeHit: masks holds one region
 // set per hit of the batch (indexed like x).
+// bk (optional, ent null for none): per-event hit lists by column group; a
+// tile scans its group's list instead of the whole event.
 template <int KT, typename OutT, bool PACK, int MODE>
 __global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
 k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
              const int *__restrict__ off, const int *__restrict__ order,
              const int *__restrict__ d_nev,
              OutT *__restrict__ acc, size_t acc_stride, unsigned long long *__restrict__ stats,
-             int *__restrict__ head, const unsigned long long *__restrict__ masks)
+             int *__restrict__ head, const unsigned long long *__restrict__ masks,
+             BucketView bk)
 {
     __shared__ int s_item;
     const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 31) / 32, ntiles = ntx * nty;
@@ -637,10 +662,13 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
         if (item >= total) break;
         const int e = order[item / ntiles], t = item % ntiles;
         const int a = off[e], n = off[e + 1] - a;
+        const int *hl = nullptr;
+        int nl = 0;
+        if (bk.ent) bk.list(e, (t % ntx) * KT, hl, nl);
         vote_tile<KT, OutT, PACK, MODE>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
                                         stats ? stats + 2 * e : nullptr, t % ntx, t / ntx,
                                         MODE == kModeEvent ? masks[e] : ~0ull,
-                                        MODE == kModeHit ? masks + a : nullptr);
+                                        MODE == kModeHit ? masks + a : nullptr, hl, nl);
         __syncthreads();
     }
 }
@@ -702,7 +730,7 @@ cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y
                                 const int *order, const int *d_nev, uint16_t *acc,
                                 size_t acc_stride, unsigned long long *stats, int *head,
                                 bool pack, int kt, int sms, const unsigned long long *masks,
-                                cudaStream_t st)
+                                cudaStream_t st, BucketView bk = BucketView{})
 {
 #define HT_VB(KTV, PK)                                                                        \
     do {                                                                                      \
@@ -712,7 +740,7 @@ cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y
             vote_smem<KTV>(G, PK, MODE));                                                     \
         k_vote_batch<KTV, uint16_t, PK, MODE><<<sms * (occ > 0 ? occ : 1), kThreads,         \
                                                 vote_smem<KTV>(G, PK, MODE), st>>>(           \
-            G, x, y, off, order, d_nev, acc, acc_stride, stats, head, masks);                 \
+            G, x, y, off, order, d_nev, acc, acc_stride, stats, head, masks, bk);             \
         return cudaGetLastError();                                                            \
     } while (0)
     if (pack) {
