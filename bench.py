@@ -54,6 +54,8 @@ def parse():
     p.add_argument("--no-learned", action="store_true")
     p.add_argument("--no-vertex", action="store_true")
     p.add_argument("--no-swept", action="store_true")
+    p.add_argument("--no-autotune", action="store_true",
+                   help="default tile widths (a fixed launch sequence, for profiling)")
     p.add_argument("--tau", type=float, default=0.02, help="proposal region threshold")
     p.add_argument("--grow", type=int, default=1, help="proposal region growth (0 or 1)")
     p.add_argument("--topk", type=int, default=8, help="regions per hit of the per-hit proposal")
@@ -178,7 +180,7 @@ def run_reference(args):
 # capture (profiles/k_assoc32_batch_event100_b4.md), valid only while the
 # kernel sources hash to the value recorded with it.
 PROFILED_TRAFFIC = {
-    "k_assoc32_batch": {"sha": "1d5bca685d3e5b7f", "bytes_per_event": 50.487040e6 / 4},
+    "k_assoc32_batch": {"sha": "5102db8cbd8e5500", "bytes_per_event": 54.354432e6 / 4},
 }
 KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_tiles.cu",
                   "paper_1309_6275_gb300/csrc/tiles.cuh",
@@ -480,7 +482,8 @@ def run_ours(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
     n_hits_total = sum(ev.n_hits for ev in events)
-    tune = bt.autotune(dev_in[0][1][0], dev_in[0][1][1], dev_in[0][1][2], dev_in[0][0])
+    tune = None if args.no_autotune else bt.autotune(dev_in[0][1][0], dev_in[0][1][1],
+                                                     dev_in[0][1][2], dev_in[0][0])
 
     stage_tot = np.zeros(5)
     votes_total = 0

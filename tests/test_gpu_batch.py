@@ -95,3 +95,40 @@ def test_graph_replay_with_new_events_and_autotune():
         assert np.array_equal(r["assign"], s["assign"])
     B.close()
     G.close()
+
+
+@pytest.mark.parametrize("n_phi0", [8, 24, 136])
+def test_hit_lists_on_few_column_groups_and_odd_hits(n_phi0):
+    """Batched tiles scan per-event hit lists by groups of 8 phi0 columns:
+    one group, three, and a count that is not a power of two; events with
+    hits near the origin (windows covering the circle), an empty event, and
+    the rest of a generated event -- results equal the single-event path,
+    which scans every hit."""
+    import torch
+    from paper_1309_6275_gb300 import ht
+    g = synth.geometry_of("event100_256", n_rho=64, n_d0=64, n_phi0=n_phi0)
+    rng = np.random.default_rng(n_phi0)
+    ev = synth.make_event(synth.CONFIGS["event100_256"]["gen"], 40 + n_phi0, target_hits=3000)
+    near = rng.normal(0.0, 0.05, (200, 2)).astype(np.float32)          # r ~ 0.05 cm
+    parts = [(ev.x, ev.y, ev.z), (near[:, 0], near[:, 1], np.zeros(200, np.float32)),
+             (np.zeros(0, np.float32),) * 3, (ev.x[::3], ev.y[::3], ev.z[::3])]
+    off = np.zeros(len(parts) + 1, np.int32)
+    off[1:] = np.cumsum([p[0].shape[0] for p in parts])
+    cat = lambda i: to_dev(np.concatenate([p[i] for p in parts]).astype(np.float32))
+    cap = 1 << 16
+    G = ht.Geometry(g)
+    B = ht.Batch(G, max_events=len(parts), max_hits=int(off[-1]), cap=cap)
+    B.run(cat(0), cat(1), cat(2), off)
+    torch.cuda.synchronize()
+    for e, (px, py, pz) in enumerate(parts):
+        r = B.event_results(off, e)
+        if px.shape[0] == 0:
+            assert r["count"] == 0
+            continue
+        s = gpu_event(g, px, py, pz, cap)
+        assert r["count"] == s["count"], e
+        assert np.array_equal(r["peaks"], s["peaks"]), e
+        assert np.array_equal(r["assign"], s["assign"]), e
+        assert r["votes"] == int(s["stats"][0]), e
+    B.close()
+    G.close()
