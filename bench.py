@@ -653,7 +653,12 @@ def run_ours(args):
             "shared_atomic_frac_of_vote": (votes_total / stage_s[1]) / atom_rate,
             "shared_atomic_peak_gops": atom_rate / 1e9,
             "float64_redo_per_vote": redo_total / max(votes_total, 1)}
-    launches_per_batch = lambda ne: 2 + 10 * ne + 9
+    # kernels one ht_batch_run replays (counted from the ncu launch list of a
+    # fixed sequence): per batch the hit lists (2 + a 3-kernel scan), two vote
+    # launches (packed and unpacked events), association and its decode, the
+    # z vote (4) and its scan (3); per event two peak passes, two
+    # candidate-list histograms and two 3-kernel scans
+    launches_per_batch = lambda ne: 16 + 10 * ne
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps,
