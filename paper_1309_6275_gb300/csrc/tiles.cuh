@@ -357,10 +357,15 @@ __device__ __forceinline__ int fast_bin32(const DevGeom &G, const TileCtx<KT> &T
     const float f = floorf(u);
     const float fr = u - f;
     j = (int)f;
-    if (D < -a.w) return kFastNone;                                   // no real root
-    if (D <= a.w) return kFastRedo;                                   // sign of D unproven
-    if ((u + e < 0.0f) | (u - e >= (float)G.n_d0)) return kFastNone; // outside the axis
-    return fminf(fr, 1.0f - fr) > e ? kFastVote : kFastRedo;
+    // decided as predicates (no early returns): no real root -> none; sign
+    // of D unproven -> redo; outside the axis -> none; else vote if the
+    // coordinate is farther than e from every integer, redo if not
+    const bool none = D < -a.w, tang = D <= a.w;
+    const bool out = (u + e < 0.0f) | (u - e >= (float)G.n_d0);
+    const bool ok = fminf(fr, 1.0f - fr) > e;
+    const bool vote = !tang & !out & ok;
+    const bool redo = !none & (tang | (!out & !ok));
+    return vote ? kFastVote : (redo ? kFastRedo : kFastNone);
 }
 
 // Deferred redo requests: (hit, row-in-tile, column) pairs whose bins
@@ -531,9 +536,12 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                 const TileCol<KT, PACK> col(cnt, ND, m & kMetaCol, lane);
                 int j;
                 const int r = fast_bin32<KT>(G, T, W, t, j);
-                if (r == kFastVote) {
-                    if (MODE != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j])) col.add(j);
-                } else if (r == kFastRedo) {
+                if (r == kFastVote && (MODE != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j])))
+                    col.add(j);
+                // the usual case: no lane needs a redo (lanes of rows past n_rho
+                // do not run this loop, hence the active mask)
+                if (!__any_sync(__activemask(), r == kFastRedo)) continue;
+                if (r == kFastRedo) {
                     ++my_fb;
                     const int hh = S.hit(m >> 6);
                     if (push_redo(R, &rn, hh, lane, m & kMetaCol)) continue;
