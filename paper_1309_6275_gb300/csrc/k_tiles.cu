@@ -479,8 +479,9 @@ __device__ __forceinline__ void assoc32_tile(const DevGeom &G, const float *__re
                 const uint32_t *col = map + (m & kMetaCol) * ND * 32 + lane;
                 int j;
                 const int r = fast_bin32<KT>(G, T, W, t, j);
-                if (r == kFastVote) key = col[j * 32];
-                if (__any_sync(__activemask(), r == kFastRedo) && r == kFastRedo) {
+                if (r == kFastVote) {
+                    key = col[j * 32];
+                } else if (r == kFastRedo) {
                     const int hh = S.hit(m >> 6);
                     if (!push_redo(R, &rn, hh, lane, m & kMetaCol)) {
                         int jj[2];

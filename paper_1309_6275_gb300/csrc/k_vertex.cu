@@ -30,8 +30,8 @@ struct ht_vertex {
     ht_vertex_desc desc;
     const ht_geometry *g;
     ht::DevGeom P;     // the 1 x n_r x n_theta peak search
-    float *d_t32;      // sin, cos theta (float32) [2][n_theta]
-    double *d_t64;     // sin, cos theta (float64) [2][n_theta]
+    float *d_t32;      // sin, cos theta [2][n_theta], then d0 of each bin [n_d0] (float32)
+    double *d_t64;     // the same in float64
     double dr, d0_off;
     float inv_dr_f;
     int j_keep;        // first radius bin whose centre is >= r_keep
@@ -43,6 +43,8 @@ namespace {
 struct VtxArgs {
     const float *st32, *ct32;
     const double *st64, *ct64;
+    const float *d0t32;           // d0 of candidate bin j: (j - n_d0/2) delta
+    const double *d0t64;
     const float *sp32, *cp32;     // track geometry sin/cos phi0
     const double *sp64, *cp64;
     double delta, half_nd, dr;
@@ -68,11 +70,15 @@ k_vertex_vote(VtxArgs A, const ht_peak *__restrict__ peaks, const int *__restric
     const ht_peak *pk = peaks + (size_t)e * cap;
     unsigned long long votes = 0, redo = 0;
     const float nr = (float)A.n_r;
-    for (int m = warp; m < nc; m += kVtxThreads / 32) {
-        const ht_peak p = pk[m];
+    // candidate records are loaded one step ahead of their use
+    constexpr int kStep = kVtxThreads / 32;
+    ht_peak nxt = warp < nc ? pk[warp] : ht_peak{0, 0, 0, 0};
+    for (int m = warp; m < nc; m += kStep) {
+        const ht_peak p = nxt;
+        if (m + kStep < nc) nxt = pk[m + kStep];
         if (p.count < A.min_count) continue;           // uniform over the warp
-        const double d0 = __dmul_rn((double)p.j_d0 - A.half_nd, A.delta);
-        const float d0f = (float)d0;
+        const double d0 = A.d0t64[p.j_d0];             // (j - n_d0/2) delta, as defined
+        const float d0f = A.d0t32[p.j_d0];
         const float sp = A.sp32[p.k_phi0], cp = A.cp32[p.k_phi0];
         const float den = fmaf(st, cp, -(ct * sp));
         const float aden = fabsf(den);
@@ -161,8 +167,9 @@ ht_status ht_vertex_create(const ht_geometry *g, const ht_vertex_desc *d, ht_ver
     int jk = 0;
     while (jk < d->n_r && ((double)jk + 0.5) * v->dr < d->r_keep) ++jk;
     v->j_keep = jk;
-    std::vector<double> t64(2 * NT);
-    std::vector<float> t32(2 * NT);
+    const int ND = g->desc.n_d0;
+    std::vector<double> t64(2 * NT + ND);
+    std::vector<float> t32(2 * NT + ND);
     for (int q = 0; q < NT; ++q) {
         const double th = (double)(2 * q + 1 - NT) * (ht::kPi / (double)NT);
         t64[q] = sin(th);
@@ -170,12 +177,17 @@ ht_status ht_vertex_create(const ht_geometry *g, const ht_vertex_desc *d, ht_ver
         t32[q] = (float)t64[q];
         t32[NT + q] = (float)t64[NT + q];
     }
-    cudaError_t e = cudaMalloc((void **)&v->d_t64, sizeof(double) * 2 * NT);
-    if (e == cudaSuccess) e = cudaMalloc((void **)&v->d_t32, sizeof(float) * 2 * NT);
+    for (int j = 0; j < ND; ++j) {   // the same two float64 operations as the definition
+        t64[2 * NT + j] = ((double)j - v->d0_off) * g->G.delta;
+        t32[2 * NT + j] = (float)t64[2 * NT + j];
+    }
+    const size_t nt = (size_t)2 * NT + ND;
+    cudaError_t e = cudaMalloc((void **)&v->d_t64, sizeof(double) * nt);
+    if (e == cudaSuccess) e = cudaMalloc((void **)&v->d_t32, sizeof(float) * nt);
     if (e == cudaSuccess)
-        e = cudaMemcpy(v->d_t64, t64.data(), sizeof(double) * 2 * NT, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(v->d_t64, t64.data(), sizeof(double) * nt, cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
-        e = cudaMemcpy(v->d_t32, t32.data(), sizeof(float) * 2 * NT, cudaMemcpyHostToDevice);
+        e = cudaMemcpy(v->d_t32, t32.data(), sizeof(float) * nt, cudaMemcpyHostToDevice);
     int dev = 0, max_smem = 0;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess)
@@ -237,6 +249,8 @@ ht_status ht_vertex_vote(const ht_vertex *v, const ht_peak *cands, const int32_t
     A.ct32 = v->d_t32 + v->desc.n_theta;
     A.st64 = v->d_t64;
     A.ct64 = v->d_t64 + v->desc.n_theta;
+    A.d0t32 = v->d_t32 + 2 * v->desc.n_theta;
+    A.d0t64 = v->d_t64 + 2 * v->desc.n_theta;
     A.sp32 = G.sn32;
     A.cp32 = G.cs32;
     A.sp64 = G.sn64;
