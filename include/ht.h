@@ -7,8 +7,8 @@
  * feature that contains it; local maxima of the vote space are candidates;
  * costlier computations then confirm them); Section 6 (Fig. 5) chains
  * transform -> peak finding -> refinement; Section 7 tunes the peak finder
- * for tracks of 7 or more hits.  The paper gives no formulas or bin layout;
- * the readings used here are stated beside each call.
+ * for tracks of at least seven hits.  The paper gives no formulas or bin
+ * layout; the readings used here are stated beside each call.
  *
  * Conventions shared by every call
  *  - Units: cm.  Hits are float32 structure-of-arrays (x[], y[], z[]).

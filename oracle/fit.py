@@ -6,8 +6,8 @@ benchmark's CPU-baseline leg import this module; it shares no code with the
 CUDA path.
 
 Section 5 says costlier computations confirm the candidates, and Section 6
-names a Kalman filter for that step (run on the CPU there, "amenable to a GPU
-implementation").  With no material and no process noise a Kalman filter
+names a Kalman filter for that step (run on the CPU there, with a GPU version
+suggested).  With no material and no process noise a Kalman filter
 over a track's hits computes the weighted least-squares estimate, which is
 what this reading fits directly:
 

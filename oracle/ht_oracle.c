@@ -13,7 +13,7 @@
  *               space are the candidate features, which costlier steps then
  *               confirm.
  *   Section 6   (Fig. 5) hits -> transform -> peak finding -> refinement.
- *   Section 7   the peak finder is tuned for tracks of 7 or more hits.
+ *   Section 7   the peak finder is tuned for tracks of at least seven hits.
  * The paper gives no formulas, bin layout or tie rules.  The readings used
  * here (each marked "reading") are stated where they are applied.
  *
@@ -361,7 +361,8 @@ void or_vote_swept(const or_geom *g, const float *x, const float *y, int64_t n,
 }
 
 /* Peak finding (Sections 5 and 6: local maxima of the vote space; Section 7:
- * tuned for 7 or more hits per track).  Reading: cell l = (i n_d0 + j) n_phi0 + k
+ * tuned for tracks of at least seven hits).  Reading: cell
+ * l = (i n_d0 + j) n_phi0 + k
  * is a peak iff acc[l] >= threshold and, for every existing one of its 26
  * neighbours l' (rho and d0 do not wrap, phi0 wraps modulo n_phi0),
  * acc[l] > acc[l'] when l' < l and acc[l] >= acc[l'] when l' > l -- so of a

@@ -1,8 +1,8 @@
 // k_fit.cu -- refinement of the candidates (ht_fit_tracks in include/ht.h):
 // a least-squares circle fit of each candidate to its assigned hits.
 // Section 5 has costlier computations confirm the candidates and Section 6
-// names a Kalman filter for it (on the CPU there, "amenable to a GPU
-// implementation"); without material or process noise a Kalman filter over
+// names a Kalman filter for it (run on the CPU there, with a GPU version
+// suggested); without material or process noise a Kalman filter over
 // the hits computes the weighted least-squares estimate, fitted here
 // directly.
 //

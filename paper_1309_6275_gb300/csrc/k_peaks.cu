@@ -1,7 +1,7 @@
 // k_peaks.cu -- 3x3x3 local-maximum peak finding over the accumulator with
 // order-preserving compaction (Sections 5-7 of arXiv:1309.6275: candidates
 // are the local maxima of the vote space; the threshold reflects the peak
-// finder's tuning for tracks of 7 or more hits).
+// finder's tuning for tracks of at least seven hits).
 //
 // Design (GB300, HBM-bound stencil):
 //  * A CTA of 256 threads owns one segment row (i, j-block of 16 d0 bins,
