@@ -226,3 +226,31 @@ def test_host_buffer_entry_point(name):
     assert np.array_equal(ha.numpy(), r["assign"])
     assert np.array_equal(hz[:k].numpy(), r["zres"])
     assert int(hs[0]) == int(r["stats"][0])
+
+
+@pytest.mark.parametrize("scene", ["single_64_seed0", "straight_50x10", "helices_4"])
+def test_fixture_scenes_through_the_c_abi(scene):
+    """The GPU path on the oracle's regression scenes (tests/golden/) gives
+    the stored results: accumulator hash, votes, peaks, assignments, z."""
+    import hashlib
+    import importlib.util
+    import json
+    import os
+    here = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+    spec = importlib.util.spec_from_file_location("make_golden",
+                                                  os.path.join(here, "make_golden.py"))
+    mg = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mg)
+    with open(os.path.join(here, "oracle_small_scenes.json")) as f:
+        want = {d["scene"]: d for d in json.load(f)}[scene]
+    for name, g, x, y, z in mg.scenes():
+        if name != scene:
+            continue
+        r = gpu_event(g, x, y, z, 1 << 16)
+        acc = np.ascontiguousarray(r["acc"], np.int64)
+        assert hashlib.sha256(acc.tobytes()).hexdigest() == want["acc_sha256"]
+        assert int(r["stats"][0]) == want["votes"]
+        assert r["count"] == want["count"]
+        assert r["peaks"].tolist() == want["peaks"]
+        assert r["assign"].tolist() == want["assign"]
+        assert r["zres"].tolist() == want["zres"]
