@@ -313,10 +313,11 @@ def efficiency(g, ev, peaks, assign, min_hits=5):
 
 
 def evaluate(weights=None, name="stream2000_256", n_events=100, seed0=0, batch=25, tau=0.02,
-             fmax=0.6, grow=1, cap=1 << 20, log=print):
-    """Plain and learned batched paths on the same events: events/s (device
-    time of whole batches, graphs replayed), votes cast, candidate counts and
-    both efficiencies."""
+             fmax=0.6, grow=1, cap=1 << 20, log=print, topk=8):
+    """Plain and learned batched paths on the same events -- the per-event
+    region mask ("learned") and the per-hit top-k region sets ("hits"):
+    events/s (device time of whole batches, graphs replayed), votes cast,
+    candidate counts and both efficiencies."""
     import torch
     _ensure_path()
     import synth
@@ -338,14 +339,17 @@ def evaluate(weights=None, name="stream2000_256", n_events=100, seed0=0, batch=2
         dev.append((off, cat("x", np.float32), cat("y", np.float32), cat("z", np.float32),
                     cat("layer", np.uint8)))
     masks = torch.empty(batch, dtype=torch.int64, device="cuda")
+    hmasks = torch.empty(max_hits, dtype=torch.int64, device="cuda")
     out = {}
-    for mode in ("plain", "learned"):
+    for mode in ("plain", "learned", "hits"):
         def run(d):
             off, x, y, z, l = d
             if mode == "plain":
                 B.run(x, y, z, off)
-            else:
+            elif mode == "learned":
                 B.run_learned(x, y, z, l, off, pb, masks, tau, fmax, grow)
+            else:
+                B.run_learned_hits(x, y, z, l, off, pb, hmasks, topk, 0.0)
         for d in dev:                    # capture the graphs, warm up
             run(d)
         torch.cuda.synchronize()
@@ -379,8 +383,10 @@ def evaluate(weights=None, name="stream2000_256", n_events=100, seed0=0, batch=2
         log(mode, {k: v for k, v in res.items()})
     out["vote_frac"] = out["learned"]["votes"] / max(out["plain"]["votes"], 1)
     out["speedup"] = out["learned"]["events_per_s"] / out["plain"]["events_per_s"]
+    out["hits_vote_frac"] = out["hits"]["votes"] / max(out["plain"]["votes"], 1)
+    out["hits_speedup"] = out["hits"]["events_per_s"] / out["plain"]["events_per_s"]
     out["params"] = dict(workload=name, events=n_events, seed0=seed0, batch=batch, tau=tau,
-                         fmax=fmax, grow=grow, weights=os.path.basename(weights),
+                         fmax=fmax, grow=grow, topk=topk, weights=os.path.basename(weights),
                          trained_on=meta.get("workload"), train_events=meta.get("n_events"))
     B.close()
     G.close()
@@ -408,6 +414,7 @@ def main(argv=None):
     e.add_argument("--tau", type=float, default=0.02)
     e.add_argument("--fmax", type=float, default=0.6)
     e.add_argument("--grow", type=int, default=1)
+    e.add_argument("--topk", type=int, default=8)
     e.add_argument("--json", default=None)
     a = ap.parse_args(argv)
     if a.cmd == "train":
@@ -415,7 +422,8 @@ def main(argv=None):
                            workers=a.workers or None, out=a.out, resume=a.resume)
         print(json.dumps(dict(weights=path, **meta)))
     else:
-        r = evaluate(a.weights, a.workload, a.events, a.seed0, a.batch, a.tau, a.fmax, a.grow)
+        r = evaluate(a.weights, a.workload, a.events, a.seed0, a.batch, a.tau, a.fmax, a.grow,
+                     topk=a.topk)
         s = json.dumps(r)
         print(s)
         if a.json:

@@ -311,9 +311,10 @@ def test_batch_masked_and_learned_runs():
 
 def test_trained_proposal_gain_over_the_plain_path():
     """What the committed, trained network buys on the batched-stream
-    workload: far fewer votes and candidates, at a small loss of
-    candidate-level efficiency (tracks outside the proposed regions) and the
-    same assignment-level efficiency."""
+    workload: with the per-event mask, far fewer votes and candidates at a
+    small loss of candidate-level efficiency (tracks outside the proposed
+    regions); with the per-hit top-k sets, fewer still and no loss; the same
+    assignment-level efficiency in both."""
     import torch
     from paper_1309_6275_gb300 import ht, learned
     name = "stream2000_256"
@@ -348,5 +349,17 @@ def test_trained_proposal_gain_over_the_plain_path():
     eff = lambda q, k: q[k] / max(q[2], 1)
     assert eff(L, 4) >= eff(P, 4) - 0.05                # candidate-level efficiency
     assert abs(eff(L, 3) - eff(P, 3)) <= 0.005          # assignment-level efficiency
+    # the per-hit proposal (each hit's top 8 regions): a quarter of the votes,
+    # a sixth of the candidates, and no loss of efficiency
+    hm = torch.empty(int(off[-1]), dtype=torch.int64, device="cuda")
+    B.run_learned_hits(x, y, z, layer, off, pb, hm, 8, 0.0)
+    torch.cuda.synchronize()
+    H = np.zeros(5, np.int64)
+    for e, ev in enumerate(evs):
+        r = B.event_results(off, e)
+        H += [r["votes"], r["count"], *learned.efficiency(g, ev, r["peaks"], r["assign"])]
+    assert H[0] < 0.35 * P[0] and H[1] < 0.3 * P[1]
+    assert eff(H, 4) >= eff(P, 4) - 0.005
+    assert abs(eff(H, 3) - eff(P, 3)) <= 0.005
     B.close()
     G.close()
