@@ -208,12 +208,14 @@ def alu_peak_ops(dev_props, peaks):
     return dev_props.multi_processor_count * 128 * mhz * 1e6
 
 
-def learned_leg(args, ht, bt, batches, dev_in, g, flush):
-    """The learned-proposal batched paths against the plain one on the same
-    resident events: the per-event region mask (ht_batch_run_learned) and
-    the per-hit top-k region sets (ht_batch_run_learned_hits).  Events/s of
-    each (same timing rules as the headline), votes cast, candidates and
-    track-finding efficiency on the first batch."""
+def learned_leg(args, ht, flush):
+    """The learned-proposal batched paths against the plain one on the
+    learned configuration's evaluation workload (100 events of the
+    2k-60k-hit batched stream, 25 per batch, resident on the device): the
+    per-event region mask (ht_batch_run_learned) and the per-hit top-k
+    region sets (ht_batch_run_learned_hits).  Events/s of each (same timing
+    rules as the headline), votes cast, candidates and track-finding
+    efficiency over all events."""
     import torch
     from paper_1309_6275_gb300 import learned
     path = learned.default_weights_path("event100_256")
@@ -221,13 +223,27 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
         return None
     params, meta = learned.load_weights(path)
     pb = learned.bf16_params(params)
-    lay = [torch.from_numpy(np.concatenate([ev.layer for ev in b]).astype(np.uint8)).cuda()
-           for b in batches]
-    masks = torch.empty(bt.max_events, dtype=torch.int64, device="cuda")
-    hmasks = torch.empty(bt.max_hits, dtype=torch.int64, device="cuda")
+    name, n_ev, B = "stream2000_256", 100, 25
+    g = synth.geometry_of(name)
+    evs = list(synth.make_stream(name, n_ev, 0))
+    batches = [evs[i:i + B] for i in range(0, n_ev, B)]
+    max_hits = max(sum(e.n_hits for e in b) for b in batches)
+    G = ht.Geometry(g)
+    bt = ht.Batch(G, max_events=B, max_hits=max_hits, cap=CAP)
+    dev_in = []
+    for b in batches:
+        off = np.zeros(len(b) + 1, np.int32)
+        off[1:] = np.cumsum([e.n_hits for e in b])
+        cat = lambda k, t: torch.from_numpy(np.concatenate([getattr(e, k) for e in b]).astype(t)).cuda()
+        dev_in.append((off, cat("x", np.float32), cat("y", np.float32), cat("z", np.float32),
+                       cat("layer", np.uint8)))
+    tune = bt.autotune(dev_in[0][1], dev_in[0][2], dev_in[0][3], dev_in[0][0])
+    masks = torch.empty(B, dtype=torch.int64, device="cuda")
+    hmasks = torch.empty(max_hits, dtype=torch.int64, device="cuda")
     fmax = 0.6
 
-    def run_one(mode, off, x, y, z, l):
+    def run_one(mode, d):
+        off, x, y, z, l = d
         if mode == "plain":
             bt.run(x, y, z, off)
         elif mode == "learned":
@@ -235,15 +251,12 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
         else:
             bt.run_learned_hits(x, y, z, l, off, pb, hmasks, args.topk, 0.0)
 
-    def run(mode):
-        for (off, (x, y, z)), l in zip(dev_in, lay):
-            run_one(mode, off, x, y, z, l)
-
     out = {}
     stream = torch.cuda.current_stream()
     for mode in ("learned", "hits", "plain"):
         for _ in range(max(1, args.warmup)):
-            run(mode)
+            for d in dev_in:
+                run_one(mode, d)
         torch.cuda.synchronize()
         t = 0.0
         for s_ in range(max(1, args.steps)):
@@ -251,52 +264,58 @@ def learned_leg(args, ht, bt, batches, dev_in, g, flush):
             a = torch.cuda.Event(enable_timing=True)
             b = torch.cuda.Event(enable_timing=True)
             a.record(stream)
-            run(mode)
+            for d in dev_in:
+                run_one(mode, d)
             b.record(stream)
             b.synchronize()
             t += a.elapsed_time(b) / 1e3
-        n_ev = sum(len(b_) for b_ in batches)
         out[mode] = {"value": n_ev * max(1, args.steps) / t}
-        # quality on the first batch
-        off, (x, y, z) = dev_in[0]
-        run_one(mode, off, x, y, z, lay[0])
-        torch.cuda.synchronize()
-        out[mode]["stage_ms"] = [round(v, 3) for v in bt.stage_ms()]
+        # quality over every event (one more pass, batch by batch)
         q = dict(votes=0, cands=0, n_rec=0, fa=0, fc=0)
-        for i, ev in enumerate(batches[0]):
-            r = bt.event_results(off, i)
-            nr, fa, fc = learned.efficiency(g, ev, r["peaks"], r["assign"])
-            q["votes"] += r["votes"]; q["cands"] += r["count"]
-            q["n_rec"] += nr; q["fa"] += fa; q["fc"] += fc
+        stages = np.zeros(5)
+        regions = []
+        for d, b in zip(dev_in, batches):
+            run_one(mode, d)
+            torch.cuda.synchronize()
+            stages += np.array(bt.stage_ms())
+            for i, ev in enumerate(b):
+                r = bt.event_results(d[0], i)
+                nr, fa, fc = learned.efficiency(g, ev, r["peaks"], r["assign"])
+                q["votes"] += r["votes"]; q["cands"] += r["count"]
+                q["n_rec"] += nr; q["fa"] += fa; q["fc"] += fc
+            if mode == "learned":
+                regions += [int(v) & ((1 << 64) - 1) for v in masks[:len(b)].cpu().tolist()]
+        q["stage_ms_per_event"] = [round(v / n_ev, 4) for v in stages]
         out[mode].update(q)
         if mode == "learned":
-            mk = [int(v) & ((1 << 64) - 1) for v in masks[:len(batches[0])].cpu().tolist()]
-            out[mode]["mean_regions"] = float(np.mean([bin(m).count("1") for m in mk]))
-            out[mode]["fallback_frac"] = float(np.mean([m == (1 << 64) - 1 for m in mk]))
+            out[mode]["mean_regions"] = float(np.mean([bin(m).count("1") for m in regions]))
+            out[mode]["fallback_frac"] = float(np.mean([m == (1 << 64) - 1 for m in regions]))
+    bt.close()
+    G.close()
     L, P, H = out["learned"], out["plain"], out["hits"]
+    eff = lambda r, k: r[k] / max(r["n_rec"], 1)
     per_hit = {"value": H["value"], "unit": "events/s", "speedup": H["value"] / P["value"],
                "topk": args.topk, "pmin": 0.0,
                "vote_frac": H["votes"] / max(P["votes"], 1),
                "candidate_frac": H["cands"] / max(P["cands"], 1),
-               "eff_candidate": H["fc"] / max(H["n_rec"], 1),
-               "eff_assign": H["fa"] / max(H["n_rec"], 1),
-               "first_batch_stage_ms": H["stage_ms"],
+               "eff_candidate": eff(H, "fc"), "eff_assign": eff(H, "fa"),
+               "stage_ms_per_event": H["stage_ms_per_event"],
                "path": "ht_batch_run_learned_hits (proposal MLP top-k per hit + per-hit "
                        "restricted vote in one graph)"}
     return {"value": L["value"], "unit": "events/s", "plain_value": P["value"],
             "speedup": L["value"] / P["value"],
+            "workload": f"{name}: {n_ev} events of the 2k-60k-hit stream, {B} per batch",
+            "autotune": tune,
             "vote_frac": L["votes"] / max(P["votes"], 1),
             "candidate_frac": L["cands"] / max(P["cands"], 1),
-            "eff_candidate": {"plain": P["fc"] / max(P["n_rec"], 1),
-                              "learned": L["fc"] / max(L["n_rec"], 1)},
-            "eff_assign": {"plain": P["fa"] / max(P["n_rec"], 1),
-                           "learned": L["fa"] / max(L["n_rec"], 1)},
-            "quality_sample": f"first batch ({len(batches[0])} events), "
-                              f"{P['n_rec']} reconstructable tracks",
+            "eff_candidate": {"plain": eff(P, "fc"), "learned": eff(L, "fc")},
+            "eff_assign": {"plain": eff(P, "fa"), "learned": eff(L, "fa")},
+            "quality_sample": f"all {n_ev} events, {P['n_rec']} reconstructable tracks",
             "mean_regions": L["mean_regions"], "fallback_frac": L["fallback_frac"],
-            "first_batch_stage_ms": {"stages": ["proposal", "vote", "peaks+lists", "association",
-                                                "decode+z"],
-                                     "plain": P["stage_ms"], "learned": L["stage_ms"]},
+            "stage_ms_per_event": {"stages": ["proposal", "vote", "peaks+lists", "association",
+                                              "decode+z"],
+                                   "plain": P["stage_ms_per_event"],
+                                   "learned": L["stage_ms_per_event"]},
             "tau": args.tau, "fmax": fmax, "grow": args.grow,
             "per_hit": per_hit,
             "path": "ht_batch_run_learned (proposal MLP + masked vote/peaks in one graph)",
@@ -641,7 +660,7 @@ def run_ours(args):
 
     learned_res = None
     if not args.no_learned:
-        learned_res = learned_leg(args, ht, bt, batches, dev_in, g, flush)
+        learned_res = learned_leg(args, ht, flush)
 
     swept_res = None
     if not args.no_swept:
