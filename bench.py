@@ -695,7 +695,20 @@ def run_ours(args):
             "vote_share_of_step": stage_s[1] / total_s,
             "shared_atomic_frac_of_vote": (votes_total / stage_s[1]) / atom_rate,
             "shared_atomic_peak_gops": atom_rate / 1e9,
-            "float64_redo_per_vote": redo_total / max(votes_total, 1)}
+            "float64_redo_per_vote": redo_total / max(votes_total, 1),
+            # the HBM side of the path: two peak passes each read the accumulator
+            # once (the vote's own write of it is one more pass), against the
+            # measured copy bandwidth
+            "hbm_peaks_stage": {
+                "algorithmic_bytes_per_event": 2 * g["n_rho"] * g["n_d0"] * g["n_phi0"] * 2,
+                "achieved_gbs": (2 * g["n_rho"] * g["n_d0"] * g["n_phi0"] * 2) /
+                                (stage_s[2] / (args.steps * n_ev)) / 1e9,
+                "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+                "frac": (2 * g["n_rho"] * g["n_d0"] * g["n_phi0"] * 2) /
+                        (stage_s[2] / (args.steps * n_ev)) / 1e9 /
+                        peaks.get("hbm_gbs", 6800.0),
+                "note": "peaks + candidate-list stage time; the stage is issue-bound "
+                        "(profiles/k_peaks_event100.md)"}}
     # kernels one ht_batch_run replays (counted from the ncu launch list of a
     # fixed sequence): per batch the hit lists (2 + a 3-kernel scan), two vote
     # launches (packed and unpacked events), association and its decode, the

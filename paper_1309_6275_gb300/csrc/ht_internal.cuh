@@ -10,6 +10,18 @@
 
 namespace ht {
 
+// Streaming multiprocessors of the current device (grid sizing); 152 if the
+// query fails.
+inline int device_sms()
+{
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        return 152;
+    return sms;
+}
+
 // ---------------------------------------------------------------------------
 // Geometry as the kernels see it (passed by value).  Every float64 value is
 // computed on the host with the same expression as the plain definition; the

@@ -283,9 +283,7 @@ inline void cand_tiles_pass(const ht_peak *peaks, const int *d_count, int cap, i
                             cudaStream_t st)
 {
     if (ntiles <= kCandHistMaxTiles) {
-        int dev = 0, sms = 152;
-        if (cudaGetDevice(&dev) == cudaSuccess)
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int sms = device_sms();
         k_cand_hist<<<sms, 256, (size_t)ntiles * 4, st>>>(peaks, d_count, cap, NR, NP, KT, nct,
                                                           ntiles, tcnt, tcur, list);
         return;

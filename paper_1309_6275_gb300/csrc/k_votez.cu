@@ -427,10 +427,10 @@ cudaError_t launch_vote_z_batch(const DevGeom &G, const float *x, const float *y
     e = scan_exclusive(cnt, zoff, cur, (int)ng, nullptr, nullptr, tmp, st);
     if (e != cudaSuccess) return e;
     k_zb_group<<<nb, 256, 0, st>>>(assign, off, d_nev, counts, cap, nullptr, cur, list);
-    dim3 gs(max(1, min(152 * 8 / max(n_ev, 1), 1024)), n_ev);
+    dim3 gs(max(1, min(device_sms() * 8 / max(n_ev, 1), 1024)), n_ev);
     k_zb_small<<<gs, 256, 0, st>>>(G, x, y, z, peaks, counts, d_nev, cap, zoff, list, out, big,
                                    nbig);
-    k_zb_big<<<152 * 2, kBigThreads, z_big_smem(G), st>>>(G, x, y, z, peaks, zoff, list, big,
+    k_zb_big<<<device_sms() * 2, kBigThreads, z_big_smem(G), st>>>(G, x, y, z, peaks, zoff, list, big,
                                                            nbig, out);
     return cudaGetLastError();
 }
@@ -451,10 +451,10 @@ cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, cons
     if (e != cudaSuccess) return e;
     if (n > 0) k_z_scatter<<<nb, 256, 0, st>>>(assign, n, d_count, cap, w.cur, w.list);
     const int warps_needed = cap;
-    const int blocks = min(152 * 16, (warps_needed + 7) / 8);
+    const int blocks = min(device_sms() * 16, (warps_needed + 7) / 8);
     k_z_small<<<blocks, 256, 0, st>>>(G, x, y, z, peaks, d_count, cap, w.off, w.list, out, w.big,
                                       w.nbig);
-    k_z_big<<<152 * 2, kBigThreads, z_big_smem(G), st>>>(G, x, y, z, peaks, w.off, w.list, w.big,
+    k_z_big<<<device_sms() * 2, kBigThreads, z_big_smem(G), st>>>(G, x, y, z, peaks, w.off, w.list, w.big,
                                                           w.nbig, out);
     return cudaGetLastError();
 }

@@ -267,7 +267,7 @@ cudaError_t launch_region_mask(const void *params_bf16, const float *x, const fl
     if (e != cudaSuccess) return e;
     if (max_hits > 0) {
         FwdOut o{nullptr, nullptr, nullptr, nullptr, mass, off, n_ev, off + n_ev};
-        const int blocks = min((max_hits + kTcM - 1) / kTcM, 152 * 2);
+        const int blocks = min((max_hits + kTcM - 1) / kTcM, device_sms() * 2);
         k_mlp_fwd_tc<<<blocks, kTcM, kTcSmem, st>>>((const __nv_bfloat16 *)params_bf16, x, y, z,
                                                     layer, max_hits, o);
         e = cudaGetLastError();
@@ -290,7 +290,7 @@ cudaError_t launch_hit_masks(const void *params_bf16, const float *x, const floa
     o.hmask = hit_masks;
     o.topk = topk;
     o.pmin = pmin;
-    const int blocks = min((n + kTcM - 1) / kTcM, 152 * 2);
+    const int blocks = min((n + kTcM - 1) / kTcM, device_sms() * 2);
     k_mlp_fwd_tc<<<blocks, kTcM, kTcSmem, st>>>((const __nv_bfloat16 *)params_bf16, x, y, z,
                                                 layer, n, o);
     return cudaGetLastError();
@@ -335,7 +335,7 @@ ht_status ht_mlp_forward(const void *params_bf16, const float *x, const float *y
     if (pe != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(pe));
     FwdOut o{prob, (__nv_bfloat16 *)h1, (__nv_bfloat16 *)h2, (__nv_bfloat16 *)feat, nullptr,
              nullptr, 0, nullptr};
-    const int blocks = min((n + kTcM - 1) / kTcM, 152 * 2);
+    const int blocks = min((n + kTcM - 1) / kTcM, device_sms() * 2);
     k_mlp_fwd_tc<<<blocks, kTcM, kTcSmem, reinterpret_cast<cudaStream_t>(stream)>>>(
         (const __nv_bfloat16 *)params_bf16, x, y, z, layer, n, o);
     const cudaError_t e = cudaGetLastError();
@@ -401,7 +401,7 @@ ht_status ht_mlp_backward(const void *params_bf16, const int32_t *labels, int32_
     cudaError_t e = cudaMemsetAsync(nl, 0, 4, st);
     if (e != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     k_count_labels<<<min(1024, (n + 255) / 256), 256, 0, st>>>(labels, n, nl);
-    const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, 152 * 4);
+    const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, device_sms() * 4);
     k_mlp_bwd_act<<<blocks, kFwdThreads, kBwdSmem, st>>>((const __nv_bfloat16 *)params_bf16, prob, labels,
                                                   (const __nv_bfloat16 *)h1,
                                                   (const __nv_bfloat16 *)h2, n, nl, dL, dH2, dH1);
