@@ -132,3 +132,34 @@ def test_hit_lists_on_few_column_groups_and_odd_hits(n_phi0):
         assert r["votes"] == int(s["stats"][0]), e
     B.close()
     G.close()
+
+
+def test_pileup_geometry_batch_equals_single_event_path():
+    """The pile-up-like configuration (512 x 256 x 1024, ~50k hits per event,
+    above the packed-counter limit) through the batched runtime equals the
+    single-event calls; the single-event path is held to the oracle on these
+    events by tests/test_gpu_parity.py."""
+    import torch
+    from paper_1309_6275_gb300 import ht
+    name = "pileup_512"
+    g = synth.geometry_of(name)
+    gen = synth.CONFIGS[name]["gen"]
+    evs = [synth.make_event(gen, 300 + i) for i in range(2)]
+    off = np.zeros(3, np.int32)
+    off[1:] = np.cumsum([e.n_hits for e in evs])
+    cat = lambda k: to_dev(np.concatenate([getattr(e, k) for e in evs]).astype(np.float32))
+    cap = 1 << 22
+    G = ht.Geometry(g)
+    B = ht.Batch(G, max_events=2, max_hits=int(off[-1]), cap=cap)
+    B.run(cat("x"), cat("y"), cat("z"), off)
+    torch.cuda.synchronize()
+    for e, ev in enumerate(evs):
+        r = B.event_results(off, e)
+        s = gpu_event(g, ev.x, ev.y, ev.z, cap)
+        assert r["count"] == s["count"], e
+        assert np.array_equal(r["peaks"], s["peaks"]), e
+        assert np.array_equal(r["assign"], s["assign"]), e
+        assert np.array_equal(r["zres"], s["zres"]), e
+        assert r["votes"] == int(s["stats"][0]), e
+    B.close()
+    G.close()
