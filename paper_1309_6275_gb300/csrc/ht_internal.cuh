@@ -135,13 +135,17 @@ __device__ __forceinline__ float rsqrt_approx(float v)
 // outside the axis) or -2 (undecided: redo).  Branch-free.  If u lies within
 // e of the axis but outside it, its distance to the edge integer is below e,
 // so it is undecided rather than misbinned; a NaN bound or coordinate is
-// undecided too.
+// undecided too.  The distances to the integers below and above are u - f
+// and (f + 1) - u: each is exact whenever it is the smaller one (u >= 0),
+// and for f = -1 the second is -u exactly, at most e when u + e >= 0, so a
+// root within e below the axis is undecided.  (1 - (u - f) would not do:
+// u + 1 is rounded for u in (-1, 0) and can pass the test.)
 __device__ __forceinline__ int decide(float u, float e, float nd)
 {
     const float f = floorf(u);
     const float fr = u - f;
     const bool out = (u + e < 0.0f) | (u - e >= nd);
-    const bool ok = fminf(fr, 1.0f - fr) > e;
+    const bool ok = fminf(fr, (f + 1.0f) - u) > e;
     return out ? -1 : (ok ? (int)f : -2);
 }
 

@@ -48,14 +48,15 @@ __device__ __forceinline__ SwList carve_sw(unsigned char *p, int cap)
 }
 
 // Side-aware bin code of a root: floor(u) inside the axis, -1 certainly
-// below, nd certainly above, -2 undecided.
+// below, nd certainly above, -2 undecided.  For u in (-1, 0) the fraction
+// u + 1 is rounded, so a root within e below the axis is undecided.
 __device__ __forceinline__ int side_code(float u, float e, int nd)
 {
     const float f = floorf(u);
     const float fr = u - f;
     if (u + e < 0.0f) return -1;
     if (u - e >= (float)nd) return nd;
-    return fminf(fr, 1.0f - fr) > e ? (int)f : -2;
+    return (f >= 0.0f && fminf(fr, 1.0f - fr) > e) ? (int)f : -2;
 }
 
 // Root codes of one sample: ok[br] (branch + = 0, - = 1) and code[br].

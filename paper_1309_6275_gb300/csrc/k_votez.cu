@@ -108,7 +108,8 @@ __device__ __forceinline__ int z_bin(const DevGeom &G, const ZCand &C, float xf,
     if (u + err < 0.0f || u - err >= nz) return -1;
     const float f = floorf(u);
     const float fr = u - f;
-    if (fminf(fr, 1.0f - fr) > err) return (int)f;
+    // u + 1 (u in (-1, 0)) is rounded: only f >= 0 is decided here
+    if (f >= 0.0f && fminf(fr, 1.0f - fr) > err) return (int)f;
     if (!have64) {
         L64 = arc64(C, xf, yf);
         have64 = true;

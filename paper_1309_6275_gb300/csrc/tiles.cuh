@@ -359,10 +359,12 @@ __device__ __forceinline__ int fast_bin32(const DevGeom &G, const TileCtx<KT> &T
     j = (int)f;
     // decided as predicates (no early returns): no real root -> none; sign
     // of D unproven -> redo; outside the axis -> none; else vote if the
-    // coordinate is farther than e from every integer, redo if not
+    // coordinate is farther than e from every integer, redo if not (the
+    // distances as in decide(): a root within e below the axis has
+    // (f + 1) - u = -u <= e and is redone, never voted in bin -1)
     const bool none = D < -a.w, tang = D <= a.w;
     const bool out = (u + e < 0.0f) | (u - e >= (float)G.n_d0);
-    const bool ok = fminf(fr, 1.0f - fr) > e;
+    const bool ok = fminf(fr, (f + 1.0f) - u) > e;
     const bool vote = !tang & !out & ok;
     const bool redo = !none & (tang | (!out & !ok));
     return vote ? kFastVote : (redo ? kFastRedo : kFastNone);
