@@ -31,6 +31,21 @@ def gpu_event(g, x, y, z, cap):
     torch.cuda.synchronize()
     r = p.results(len(x))
     G.close()
+    check_assign(r["assign"], r["count"])
+    return r
+
+
+def check_assign(assign, count):
+    """Every assignment is -1 or the index of a found candidate."""
+    a = np.asarray(assign)
+    bad = np.nonzero((a < -1) | (a >= count))[0]
+    assert bad.size == 0, f"{bad.size} assignments out of [-1, {count}): hits {bad[:5].tolist()} -> {a[bad[:5]].tolist()}"
+
+
+def batch_event(B, offsets, e):
+    """Event e's results from a Batch, with the assignment range checked."""
+    r = B.event_results(offsets, e)
+    check_assign(r["assign"], r["count"])
     return r
 
 

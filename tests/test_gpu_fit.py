@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import cuda_ok, to_dev
+from gpu_common import batch_event, cuda_ok, to_dev
 from oracle import fit as F
 
 pytestmark = [pytest.mark.gpu,
@@ -113,7 +113,7 @@ def test_fit_in_batch_layout_and_noise_free_tracks():
     for sel in SELECTIONS:
         tr = gpu_fit(G, ht, x, y, off, B.assign, B.peaks, B.counts, cap, **sel)
         for e, ev in enumerate(evs):
-            r = B.event_results(off, e)
+            r = batch_event(B, off, e)
             t = tr[e * cap:e * cap + r["count"]]
             nf, nc = compare(g, ev.x, ev.y, r["assign"], r["peaks"], t, **sel)
             assert nf > 0

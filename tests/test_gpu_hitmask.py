@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import assert_same_acc, cuda_ok, to_dev
+from gpu_common import assert_same_acc, batch_event, cuda_ok, to_dev
 from oracle import mlp
 
 pytestmark = [pytest.mark.gpu,
@@ -178,7 +178,7 @@ def batch_events(name, seeds):
 
 
 def check_event(B, off, e, res):
-    r = B.event_results(off, e)
+    r = batch_event(B, off, e)
     assert r["count"] == res["count"]
     assert np.array_equal(r["peaks"], res["peaks"])
     assert np.array_equal(r["assign"], res["assign"])

@@ -9,7 +9,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import assert_same_acc, cuda_ok, to_dev
+from gpu_common import assert_same_acc, batch_event, cuda_ok, to_dev
 from oracle import mlp
 
 pytestmark = [pytest.mark.gpu,
@@ -265,7 +265,7 @@ def test_batch_masked_and_learned_runs():
     B.run_masked(x, y, z, off, dm)
     torch.cuda.synchronize()
     # the smallest event against the oracle
-    r = B.event_results(off, 0)
+    r = batch_event(B, off, 0)
     o = mlp.masked_event(g, evs[0].x, evs[0].y, evs[0].z, masks[0], cap=cap)
     assert r["count"] == o["count"] and r["votes"] == o["votes"]
     assert np.array_equal(r["peaks"], o["peaks"])
@@ -274,7 +274,7 @@ def test_batch_masked_and_learned_runs():
     # every event against the single-event path restricted to the mask
     full = [gpu_event(g, e.x, e.y, e.z, cap) for e in evs]
     for e, ev in enumerate(evs):
-        r = B.event_results(off, e)
+        r = batch_event(B, off, e)
         ins = mlp.cell_allowed(g, masks[e])[0]
         pk = full[e]["peaks"]
         keep = ins[pk[:, 0], pk[:, 1]] if pk.shape[0] else np.zeros(0, bool)
@@ -296,11 +296,11 @@ def test_batch_masked_and_learned_runs():
     ht.ht_mlp_region_mask(pb, x, y, z, layer, to_dev(off), 0.02, 0.6, 1, mass, ref)
     torch.cuda.synchronize()
     assert torch.equal(lm, ref)
-    res_l = [B.event_results(off, e) for e in range(4)]
+    res_l = [batch_event(B, off, e) for e in range(4)]
     B.run_masked(x, y, z, off, lm.clone())
     torch.cuda.synchronize()
     for e in range(4):
-        r = B.event_results(off, e)
+        r = batch_event(B, off, e)
         for k in ("count", "votes"):
             assert r[k] == res_l[e][k]
         for k in ("peaks", "assign", "zres"):
@@ -339,7 +339,7 @@ def test_trained_proposal_gain_over_the_plain_path():
         torch.cuda.synchronize()
         q = np.zeros(5, np.int64)
         for e, ev in enumerate(evs):
-            r = B.event_results(off, e)
+            r = batch_event(B, off, e)
             q += [r["votes"], r["count"], *learned.efficiency(g, ev, r["peaks"], r["assign"])]
         res[mode] = q
     P, L = res["plain"], res["learned"]
@@ -356,7 +356,7 @@ def test_trained_proposal_gain_over_the_plain_path():
     torch.cuda.synchronize()
     H = np.zeros(5, np.int64)
     for e, ev in enumerate(evs):
-        r = B.event_results(off, e)
+        r = batch_event(B, off, e)
         H += [r["votes"], r["count"], *learned.efficiency(g, ev, r["peaks"], r["assign"])]
     assert H[0] < 0.35 * P[0] and H[1] < 0.3 * P[1]
     assert eff(H, 4) >= eff(P, 4) - 0.005
