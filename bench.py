@@ -37,6 +37,7 @@ import synth  # noqa: E402
 WORKLOAD = "event100_256"
 METRIC = "events/s"
 CAP = 1 << 20          # candidate capacity per event (the 10k-hit events give ~5e5)
+CAP_OF = {"pileup_512": 1 << 22}   # the 50k-hit events give ~3.7e6
 
 
 def parse():
@@ -152,12 +153,12 @@ def run_reference(args):
     evs = [synth.make_event(cfg["gen"], cfg["seed0"] + e) for e in range(min(n_ev, args.warmup + args.steps))]
     for s in range(args.warmup):
         ev = evs[s % len(evs)]
-        oracle.run_event(g, ev.x, ev.y, ev.z, cap=CAP, threads=cores)
+        oracle.run_event(g, ev.x, ev.y, ev.z, cap=CAP_OF.get(args.workload, CAP), threads=cores)
     times = []
     for s in range(args.steps):
         ev = evs[(args.warmup + s) % len(evs)]
         t = time.perf_counter()
-        oracle.run_event(g, ev.x, ev.y, ev.z, cap=CAP, threads=cores)
+        oracle.run_event(g, ev.x, ev.y, ev.z, cap=CAP_OF.get(args.workload, CAP), threads=cores)
         times.append(time.perf_counter() - t)
     tot = sum(times)
     value = args.steps / tot
@@ -488,7 +489,7 @@ def run_ours(args):
     n_job = world * n_ev           # events of the whole job per step
     n_ev = len(events)             # this rank's share
     G = ht.Geometry(g)
-    cap = CAP
+    cap = CAP_OF.get(args.workload, CAP)
     max_hits = max(sum(ev.n_hits for ev in b) for b in batches)
     bt = ht.Batch(G, max_events=B, max_hits=max_hits, cap=cap)
     # inputs resident in HBM: one concatenated x, y, z per batch
@@ -749,7 +750,7 @@ def run_ours(args):
     if e2e:
         line["e2e"] = e2e
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, events[0], CAP)
+        line["cpu_baseline"] = cpu_baseline(g, events[0], CAP_OF.get(args.workload, CAP))
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
