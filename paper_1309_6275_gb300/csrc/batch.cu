@@ -76,7 +76,6 @@ cudaError_t launch_hit_masks(const void *params_bf16, const float *x, const floa
 
 namespace {
 
-constexpr int kPackMaxHits = 32767;   // packed 16-bit tile counters are exact up to here
 constexpr int kGraphCache = 16;
 
 constexpr int kStages = 5;   // proposal, vote, peaks + lists, association, z vote
@@ -211,7 +210,8 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     // batch uses divides the group)
     e = ht::launch_hit_buckets(G, x, y, off, meta + 2, b->max_hits, b->bk, b->sms, st);
     if (e != cudaSuccess) return e;
-    // vote: events above the packed-counter limit, then the others
+    // vote: the tiles whose hit lists pass the packed-counter limit (in events
+    // above it), then every other tile of every event with packed counters
     auto vote = [&](const int *order, const int *d_nev, int *head, bool pack, int kt) {
         if (R.hit_masks)
             return ht::launch_vote_batch_hitmask(G, x, y, off, order, d_nev, b->acc, b->cells,
@@ -225,7 +225,7 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     };
     e = vote(order_big_of(meta, me), meta + 0, b->heads + 0, false, b->kt_big);
     if (e != cudaSuccess) return e;
-    e = vote(order_small_of(meta, me), meta + 1, b->heads + 1, true, b->kt_pack);
+    e = vote(order_all_of(meta, me), meta + 2, b->heads + 1, true, b->kt_pack);
     if (e == cudaSuccess) e = mark(2);
     if (e != cudaSuccess) return e;
     // peaks and candidate tile lists per event slot
@@ -277,7 +277,7 @@ ht_status stage_meta(ht_batch *b, const int32_t *h_off, int n_ev, cudaStream_t s
     int nb = 0, ns = 0;
     for (int i = 0; i < n_ev; ++i) {
         const int ev = idx[i];
-        if (h_off[ev + 1] - h_off[ev] > kPackMaxHits) order_big_of(hm, me)[nb++] = ev;
+        if (h_off[ev + 1] - h_off[ev] > ht::kPackMaxHits) order_big_of(hm, me)[nb++] = ev;
         else order_small_of(hm, me)[ns++] = ev;
         order_all_of(hm, me)[i] = ev;
     }

@@ -330,6 +330,9 @@ cudaError_t launch_vote_masked(const DevGeom &G, const float *x, const float *y,
 // phi0 columns (k_buckets.cu): group g of event e holds cnt[e G + g] local
 // hit indices at ent + start[e G + g], G = ngroups.
 constexpr int kGroupCols = 8;
+// Packed 16-bit tile counters are exact for tiles scanning up to this many
+// hits (two votes per hit at most in a cell: 2 * 32767 < 2^16).
+constexpr int kPackMaxHits = 32767;
 struct HitBuckets {
     int *cnt, *start, *cursor, *ent;
     void *tmp;

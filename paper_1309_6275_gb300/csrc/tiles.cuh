@@ -675,10 +675,16 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
         const int *hl = nullptr;
         int nl = 0;
         if (bk.ent) bk.list(e, (t % ntx) * KT, hl, nl);
-        vote_tile<KT, OutT, PACK, MODE>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
-                                        stats ? stats + 2 * e : nullptr, t % ntx, t / ntx,
-                                        MODE == kModeEvent ? masks[e] : ~0ull,
-                                        MODE == kModeHit ? masks + a : nullptr, hl, nl);
+        // Packed 16-bit counters take the tiles that scan at most kPackMaxHits
+        // hits (a cell then holds at most 2 kPackMaxHits < 2^16 votes, so no
+        // count carries into its neighbour), unpacked counters the others:
+        // the two launches of a batch split every event's tiles between them
+        // by the scanned list's length (uniform over the CTA).
+        if (PACK == ((bk.ent ? nl : n) <= kPackMaxHits))
+            vote_tile<KT, OutT, PACK, MODE>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
+                                            stats ? stats + 2 * e : nullptr, t % ntx, t / ntx,
+                                            MODE == kModeEvent ? masks[e] : ~0ull,
+                                            MODE == kModeHit ? masks + a : nullptr, hl, nl);
         __syncthreads();
     }
 }

@@ -168,3 +168,42 @@ def test_pileup_geometry_batch_equals_single_event_path(seed0):
         assert np.array_equal(r["assign"][sel], asg), e
     B.close()
     G.close()
+
+
+def test_packed_and_unpacked_tiles_within_one_event():
+    """Tiles whose hit list holds more than 32767 hits take 32-bit counters,
+    the others packed 16-bit ones, within one event: 30000 hits near the beam
+    line (in every column group's list, and all voting near d0 = 0, so cells
+    come close to the 16-bit limit) plus ordinary hits confined to one
+    azimuthal sector, which push only the groups around it past the limit.
+    Results equal the single-event path (32-bit tiles throughout)."""
+    import torch
+    from paper_1309_6275_gb300 import ht
+    g = synth.geometry_of("event100_256", n_rho=64, n_d0=64, n_phi0=64)
+    rng = np.random.default_rng(77)
+    near = rng.normal(0.0, 0.05, (30000, 2)).astype(np.float32)
+    ev = synth.make_event(synth.CONFIGS["event100_256"]["gen"], 78, target_hits=40000)
+    psi = np.arctan2(ev.y, ev.x)
+    sec = (psi > 0.0) & (psi < 0.6)
+    parts = [(np.concatenate([near[:, 0], ev.x[sec]]), np.concatenate([near[:, 1], ev.y[sec]]),
+              np.concatenate([np.zeros(30000, np.float32), ev.z[sec]])),
+             (ev.x[:5000], ev.y[:5000], ev.z[:5000])]
+    assert parts[0][0].shape[0] > 32767
+    off = np.zeros(len(parts) + 1, np.int32)
+    off[1:] = np.cumsum([p[0].shape[0] for p in parts])
+    cat = lambda i: to_dev(np.concatenate([p[i] for p in parts]).astype(np.float32))
+    cap = 1 << 18
+    G = ht.Geometry(g)
+    B = ht.Batch(G, max_events=len(parts), max_hits=int(off[-1]), cap=cap)
+    B.run(cat(0), cat(1), cat(2), off)
+    torch.cuda.synchronize()
+    for e, (px, py, pz) in enumerate(parts):
+        r = batch_event(B, off, e)
+        s = gpu_event(g, px.astype(np.float32), py.astype(np.float32), pz.astype(np.float32), cap)
+        assert r["votes"] == int(s["stats"][0]), e
+        assert r["count"] == s["count"], e
+        assert np.array_equal(r["peaks"], s["peaks"]), e
+        assert np.array_equal(r["assign"], s["assign"]), e
+        assert np.array_equal(r["zres"], s["zres"]), e
+    B.close()
+    G.close()
