@@ -210,8 +210,9 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     // batch uses divides the group)
     e = ht::launch_hit_buckets(G, x, y, off, meta + 2, b->max_hits, b->bk, b->sms, st);
     if (e != cudaSuccess) return e;
-    // vote: the tiles whose hit lists pass the packed-counter limit (in events
-    // above it), then every other tile of every event with packed counters
+    // vote: the tiles whose hit lists pass the packed-counter limit (only
+    // events above it can have such tiles), then every other tile of every
+    // event with packed counters
     auto vote = [&](const int *order, const int *d_nev, int *head, bool pack, int kt) {
         if (R.hit_masks)
             return ht::launch_vote_batch_hitmask(G, x, y, off, order, d_nev, b->acc, b->cells,

@@ -404,8 +404,8 @@ __device__ __forceinline__ bool push_redo(const RedoQueue &Q, int *n, int hit, i
 // KT >= 2 a word holds columns 2p and 2p + 1 of one (bin, row), so the
 // increment (1 or 65536) is fixed per work item and a vote costs one address
 // computation; with KT = 1 it holds bins 2w and 2w + 1.  Exact while no cell
-// can reach 65536 votes in the tile: a cell gets at most two votes per hit,
-// so it is used only for n <= 32767.
+// can reach 65536 votes in the tile: a cell gets at most two votes per
+// scanned hit, so it is used only for tiles scanning at most kPackMaxHits.
 template <int KT, bool PACK>
 struct TileCol {
     uint32_t *base;
@@ -739,8 +739,11 @@ cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int 
 
 // Persistent vote of a batch: `order` lists d_nev[0] event slots; every CTA
 // slot of the GPU (SMs x resident CTAs) pops items until the queue is empty.
-// kt selects the tile width (0 = default), pack the 16-bit packed counters
-// (valid when every listed event has <= 32767 hits).  *head must be zero.
+// kt selects the tile width (0 = default).  pack: this launch takes the
+// listed events' tiles that scan at most kPackMaxHits hits (a column group's
+// hit list with buckets, else the event) with 16-bit packed counters;
+// otherwise it takes their other tiles with 32-bit counters.  *head must be
+// zero.
 template <int MODE>
 cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y, const int *off,
                                 const int *order, const int *d_nev, uint16_t *acc,
