@@ -104,8 +104,8 @@ struct ht_batch {
     int kt_pack, kt_big, kt_assoc;
     size_t cells;
     uint16_t *acc;
-    int *meta;          // [0] n_big [1] n_small [2] n_all [3] pad, off[max_events + 1],
-                        // order_big[max_events], order_small[max_events], order_all[max_events]
+    int *meta;          // [0] n_big [1] pad [2] n_all [3] pad, off[max_events + 1],
+                        // order_big[max_events], order_all[max_events] (largest first)
     int *h_meta;        // pinned staging, same layout
     size_t meta_ints;
     cudaEvent_t meta_done;
@@ -135,8 +135,7 @@ namespace {
 
 int *off_of(int *meta) { return meta + 4; }
 int *order_big_of(int *meta, int me) { return meta + 4 + me + 1; }
-int *order_small_of(int *meta, int me) { return meta + 4 + 2 * me + 1; }
-int *order_all_of(int *meta, int me) { return meta + 4 + 3 * me + 1; }
+int *order_all_of(int *meta, int me) { return meta + 4 + 2 * me + 1; }
 
 void free_batch(ht_batch *b)
 {
@@ -275,15 +274,13 @@ ht_status stage_meta(ht_batch *b, const int32_t *h_off, int n_ev, cudaStream_t s
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int c) {
         return h_off[a + 1] - h_off[a] > h_off[c + 1] - h_off[c];
     });
-    int nb = 0, ns = 0;
+    int nb = 0;
     for (int i = 0; i < n_ev; ++i) {
         const int ev = idx[i];
         if (h_off[ev + 1] - h_off[ev] > ht::kPackMaxHits) order_big_of(hm, me)[nb++] = ev;
-        else order_small_of(hm, me)[ns++] = ev;
         order_all_of(hm, me)[i] = ev;
     }
     hm[0] = nb;
-    hm[1] = ns;
     hm[2] = n_ev;
     for (int i = 0; i <= n_ev; ++i) off_of(hm)[i] = h_off[i];
     for (int i = n_ev + 1; i <= me; ++i) off_of(hm)[i] = h_off[n_ev];
@@ -341,7 +338,7 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     b->kt_big = 0;
     b->kt_assoc = ht::assoc32_kt(G);
     b->cells = (size_t)G.n_rho * G.n_d0 * G.n_phi0;
-    b->meta_ints = 4 + (size_t)max_events + 1 + 3 * (size_t)max_events;
+    b->meta_ints = 4 + (size_t)max_events + 1 + 2 * (size_t)max_events;
     b->pk_stride = ht::align256(ht::peaks_workspace_bytes(G));
     b->ntiles = ht::assoc32_ntiles(G, 1);   // the most tiles any tile width gives
     b->ttmp_stride = ht::scan_tmp_bytes(b->ntiles);
