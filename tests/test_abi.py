@@ -63,3 +63,29 @@ def test_create_rejects_bad_geometry_without_touching_the_gpu():
     assert lib.ht_geometry_create(ctypes.byref(d), ctypes.byref(h)) == 1
     assert b"unsupported" in lib.ht_last_error()
     assert lib.ht_geometry_create(None, ctypes.byref(h)) == 1
+
+
+def test_every_call_rejects_null_arguments_before_any_cuda_call():
+    """Failure detection on the host: each status-returning entry point,
+    given null handles and pointers and zero sizes, returns HT_ERR_ARG with a
+    message naming it (the checks run before any CUDA call, so this needs no
+    GPU); the destroy calls accept null as a no-op."""
+    from paper_1309_6275_gb300 import ht
+    if not _have_nvcc():
+        pytest.skip("no nvcc on this machine")
+    lib = ht.lib()
+    device_only = {"ht_probe_shared_atomic_rate"}   # times a kernel: needs a GPU
+    checked = 0
+    for name, res, args in ht.SIGNATURES:
+        if res is not ht._I32 or name in device_only or name == "ht_mlp_param_count":
+            continue
+        vals = [0.0 if a in (ctypes.c_float, ctypes.c_double)
+                else 0 if a in (ht._I32, ht._SZ, ctypes.c_int64) else None for a in args]
+        status = getattr(lib, name)(*vals)
+        if name.endswith("_destroy"):
+            assert status == 0, name
+            continue
+        assert status == 1, (name, status)          # HT_ERR_ARG
+        assert lib.ht_last_error().decode().startswith(name), (name, lib.ht_last_error())
+        checked += 1
+    assert checked >= 25

@@ -109,3 +109,47 @@ def _dup_worker(rank, world, port):
         sh.gather_results({0: rank})     # both ranks claim event 0: rank 0 raises
     finally:
         dist.destroy_process_group()
+
+
+def _dead_rank_worker(rank, world, port, outdir):
+    import sys
+    from datetime import timedelta
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch.distributed as dist
+    from paper_1309_6275_gb300 import shard as sh
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world, timeout=timedelta(seconds=10))
+    if rank == 1:
+        os._exit(3)                      # dies between steps, before the gather
+    try:
+        sh.gather_results({0: "done"})
+        msg = "gathered"
+    except Exception as e:               # the peer is gone: an error, not a hang
+        msg = f"failed: {type(e).__name__}"
+    with open(os.path.join(outdir, "rank0.txt"), "w") as f:
+        f.write(msg)
+    os._exit(0)
+
+
+def test_a_rank_that_dies_before_the_gather_is_reported_not_waited_for(tmp_path):
+    """Failure detection on the host: rank 1 exits without joining the
+    result gather; rank 0's gather ends with an error within the process
+    group's timeout instead of hanging."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    port = _free_port()
+    ps = [ctx.Process(target=_dead_rank_worker, args=(r, 2, port, str(tmp_path)))
+          for r in range(2)]
+    for p in ps:
+        p.start()
+    for p in ps:
+        p.join(90)
+    alive = [p for p in ps if p.is_alive()]
+    for p in alive:
+        p.kill()
+    assert not alive, "a rank hung"
+    assert ps[1].exitcode == 3
+    assert ps[0].exitcode == 0
+    assert (tmp_path / "rank0.txt").read_text().startswith("failed")
