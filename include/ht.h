@@ -320,8 +320,10 @@ ht_status ht_mlp_hit_masks(const void *params_bf16, const float *x, const float 
  * (labels: device int32, region index or -1 to skip the hit), given the
  * forward pass's prob, h1, h2 and feat for the same n hits; ADDED into grad
  * (device, ht_mlp_param_count() float32, in the parameter layout).  The
- * BF16 roundings of the forward pass count as identity.  workspace:
- * ht_mlp_backward_workspace_size(n) bytes, 256-byte aligned.
+ * BF16 roundings of the forward pass count as identity.  Deterministic: the
+ * same inputs give the same bits (partial sums are added in a fixed order),
+ * so a training run resumed from a checkpoint repeats an uninterrupted one.
+ * workspace: ht_mlp_backward_workspace_size(n) bytes, 256-byte aligned.
  * Errors: HT_ERR_ARG, HT_ERR_CUDA. */
 size_t ht_mlp_backward_workspace_size(int32_t n);
 ht_status ht_mlp_backward(const void *params_bf16, const int32_t *labels, int32_t n,

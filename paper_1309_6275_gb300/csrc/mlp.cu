@@ -132,15 +132,21 @@ k_mlp_bwd_act(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ pro
     }
 }
 
-// C[M][N] += sum_h A[h][M] B[h][N] (A BF16 with row stride lda, B float32
-// with row stride ldb), and bias[N] += sum_h B[h][N] when bias is set.
-// CTA: 256 threads, a 64 x 64 output tile (4 x 4 per thread), hits split
-// across gridDim.z; partial tiles are added with float atomics.
+// Split z of C[M][N] = sum_h A[h][M] B[h][N] (A BF16 with row stride lda,
+// B float32 with row stride ldb) and, when bias is set, of bias[N] =
+// sum_h B[h][N]: the hits are split across gridDim.z and split z stores its
+// partial sums at C + z pstride and bias + z pstride (plain stores: every
+// entry of a split is written by exactly one CTA); k_wgrad_reduce adds the
+// splits in a fixed order, so a training step is bit-reproducible.
+// CTA: 256 threads, a 64 x 64 output tile (4 x 4 per thread).
 constexpr int kGT = 64, kGH = 32;
+constexpr int kMaxSplits = 128;
 __global__ void __launch_bounds__(256)
 k_wgrad(const __nv_bfloat16 *__restrict__ A, int lda, const float *__restrict__ B, int ldb,
-        int n, int M, int N, float *__restrict__ C, float *__restrict__ bias)
+        int n, int M, int N, float *__restrict__ C, float *__restrict__ bias, size_t pstride)
 {
+    C += (size_t)blockIdx.z * pstride;
+    if (bias) bias += (size_t)blockIdx.z * pstride;
     __shared__ float sA[kGH][kGT], sB[kGH][kGT];
     const int m0 = blockIdx.x * kGT, n0 = blockIdx.y * kGT;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
@@ -178,10 +184,20 @@ k_wgrad(const __nv_bfloat16 *__restrict__ A, int lda, const float *__restrict__ 
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
             const int m = m0 + ty * 4 + u, nn = n0 + tx * 4 + v;
-            if (m < M && nn < N) atomicAdd(&C[(size_t)m * N + nn], acc[u][v]);
+            if (m < M && nn < N) C[(size_t)m * N + nn] = acc[u][v];
         }
     if (bias && blockIdx.x == 0 && threadIdx.x < kGT && n0 + threadIdx.x < N)
-        atomicAdd(&bias[n0 + threadIdx.x], bacc);
+        bias[n0 + threadIdx.x] = bacc;
+}
+
+// grad[i] += the splits' partial sums of parameter i, added in split order.
+__global__ void k_wgrad_reduce(const float *__restrict__ part, int splits, float *__restrict__ grad)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= kParams) return;
+    float s = 0.f;
+    for (int z = 0; z < splits; ++z) s += part[(size_t)z * kParams + i];
+    grad[i] += s;
 }
 
 __global__ void k_count_labels(const int *__restrict__ labels, int n, int *__restrict__ nl)
@@ -374,7 +390,8 @@ ht_status ht_mlp_hit_masks(const void *params_bf16, const float *x, const float 
 size_t ht_mlp_backward_workspace_size(int32_t n)
 {
     const size_t nh = (size_t)(n > 0 ? n : 1);
-    return align256(nh * kOut * 4) + 2 * align256(nh * kH * 4) + 3 * align256(nh * kH * 2) + 256;
+    return align256(nh * kOut * 4) + 2 * align256(nh * kH * 4) + 3 * align256(nh * kH * 2) + 256 +
+           align256((size_t)kMaxSplits * kParams * 4);
 }
 
 // Gradients (added into grad, float32, kParams entries) of the mean cross
@@ -398,24 +415,27 @@ ht_status ht_mlp_backward(const void *params_bf16, const int32_t *labels, int32_
     float *dH1 = reinterpret_cast<float *>(p); p += align256(nh * kH * 4);
     p += 3 * align256(nh * kH * 2);
     int *nl = reinterpret_cast<int *>(p);
+    float *part = reinterpret_cast<float *>(p + 256);   // [splits][kParams]
+    const int splits = max(1, min(kMaxSplits, n / 512));
     cudaError_t e = cudaMemsetAsync(nl, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, (size_t)splits * kParams * 4, st);
     if (e != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     k_count_labels<<<min(1024, (n + 255) / 256), 256, 0, st>>>(labels, n, nl);
     const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, device_sms() * 4);
     k_mlp_bwd_act<<<blocks, kFwdThreads, kBwdSmem, st>>>((const __nv_bfloat16 *)params_bf16, prob, labels,
                                                   (const __nv_bfloat16 *)h1,
                                                   (const __nv_bfloat16 *)h2, n, nl, dL, dH2, dH1);
-    const int splits = max(1, min(128, n / 512));
     // dW3 = h2^T dL, db3
     k_wgrad<<<dim3(kH / kGT, 1, splits), 256, 0, st>>>((const __nv_bfloat16 *)h2, kH, dL, kOut, n,
-                                                       kH, kOut, grad + oW3, grad + ob3);
+                                                       kH, kOut, part + oW3, part + ob3, kParams);
     // dW2 = h1^T dH2, db2
     k_wgrad<<<dim3(kH / kGT, kH / kGT, splits), 256, 0, st>>>((const __nv_bfloat16 *)h1, kH, dH2,
-                                                              kH, n, kH, kH, grad + oW2,
-                                                              grad + ob2);
+                                                              kH, n, kH, kH, part + oW2,
+                                                              part + ob2, kParams);
     // dW1 = f^T dH1, db1
     k_wgrad<<<dim3(1, kH / kGT, splits), 256, 0, st>>>((const __nv_bfloat16 *)feat, 8, dH1, kH, n,
-                                                       kIn, kH, grad + oW1, grad + ob1);
+                                                       kIn, kH, part + oW1, part + ob1, kParams);
+    k_wgrad_reduce<<<(kParams + 255) / 256, 256, 0, st>>>(part, splits, grad);
     e = cudaGetLastError();
     return e == cudaSuccess ? HT_OK : set_error(HT_ERR_CUDA, cudaGetErrorString(e));
 }

@@ -363,3 +363,22 @@ def test_trained_proposal_gain_over_the_plain_path():
     assert abs(eff(H, 3) - eff(P, 3)) <= 0.005
     B.close()
     G.close()
+
+
+def test_training_resumed_from_a_checkpoint_repeats_an_uninterrupted_run(tmp_path):
+    """Checkpoint / resume: 2 steps, a checkpoint, then 2 more steps after a
+    resume give the same parameter bits as 4 steps in one run (the backward
+    pass adds its partial sums in a fixed order, so steps are
+    bit-reproducible).  All four steps stay at the constant learning rate of
+    the schedule, so the two runs see the same rates."""
+    from paper_1309_6275_gb300 import learned
+    quiet = lambda *a, **k: None
+    a, b = str(tmp_path / "a.npz"), str(tmp_path / "b.npz")
+    kw = dict(name=C2, per_chunk=8, ckpt_every=0, workers=2, log=quiet)
+    learned.train(n_events=32, out=a, **kw)
+    learned.train(n_events=16, out=b, **kw)
+    learned.train(n_events=32, out=b, resume=b, **kw)
+    pa, ma = learned.load_weights(a)
+    pb, mb = learned.load_weights(b)
+    assert ma["next_event"] == mb["next_event"] == 32
+    assert np.array_equal(pa.view(np.uint32), pb.view(np.uint32))
