@@ -1,0 +1,68 @@
+"""bench.py's host logic, without a GPU: the clock record parsing and its
+throttle reasons, the issue-limited ALU peak, the LPT split of a job's
+events over ranks, and the reference arm's JSON line (the oracle on a tiny
+workload)."""
+import json
+import os
+import subprocess
+import sys
+from collections import namedtuple
+
+import bench
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_clock_record_gives_median_clock_and_active_reasons(tmp_path):
+    path = tmp_path / "clocks.csv"
+    path.write_text(
+        "0, 2070, 2070, 910.1, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active\n"
+        "0, 2055, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active\n"
+        "garbage line\n")
+    s = bench.ClockSampler(0)
+    s.path = str(path)
+    s.f = open(path, "a")
+    s.proc = subprocess.Popen([sys.executable, "-c", "pass"])
+    out = s.stop()
+    assert out["sm_mhz"] == 2055.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
+    assert not path.exists()
+
+
+def test_clock_sampler_without_nvidia_smi_reports_so():
+    s = bench.ClockSampler(0)
+    assert s.stop()["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_alu_peak_is_sms_times_128_lanes_times_clock():
+    Props = namedtuple("Props", "multi_processor_count")
+    assert bench.alu_peak_ops(Props(152), {"sm_max_mhz": 2070.0}) == 152 * 128 * 2070e6
+    assert bench.alu_peak_ops(Props(2), {}) == 2 * 128 * 2070e6
+
+
+def test_make_batches_splits_the_job_over_ranks_once():
+    import synth
+    cfg = dict(synth.CONFIGS["single_64"])
+    seen = []
+    for rank in range(3):
+        ids, events, batches = bench.make_batches(cfg, 4, 3, rank, 2)
+        assert len(events) == len(ids) and sum(len(b) for b in batches) == len(events)
+        assert all(len(b) <= 2 for b in batches)
+        seen += list(ids)
+    assert sorted(seen) == list(range(12))
+
+
+def test_reference_arm_prints_one_json_line_of_the_contract():
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload",
+                        "single_64", "--steps", "2", "--warmup", "1"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == "events/s" and d["value"] > 0
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
