@@ -89,3 +89,57 @@ def test_every_call_rejects_null_arguments_before_any_cuda_call():
         assert lib.ht_last_error().decode().startswith(name), (name, lib.ht_last_error())
         checked += 1
     assert checked >= 25
+
+
+C_PROGRAM = r"""
+#include <stdio.h>
+#include <string.h>
+#include "ht.h"
+
+int main(void)
+{
+    /* n_phi0 = 60 is not a multiple of 8: refused before any CUDA call */
+    ht_geometry_desc d;
+    memset(&d, 0, sizeof d);
+    d.n_rho = 64; d.n_d0 = 64; d.n_phi0 = 60; d.n_z0 = 128; d.n_cot = 128;
+    d.threshold = 7; d.count_bits = 32;
+    d.rho_max = 0.01; d.d0_half = 10.0; d.z0_max = 32.0; d.cot_max = 6.5;
+    ht_geometry *g = NULL;
+    const ht_status s = ht_geometry_create(&d, &g);
+    const ht_status t = ht_vote(NULL, NULL, NULL, 0, NULL, NULL, NULL);
+    printf("%d %d %s\n", (int)s, (int)t, ht_last_error());
+    return (s == HT_ERR_ARG && t == HT_ERR_ARG && g == NULL) ? 0 : 1;
+}
+"""
+
+
+def test_headers_are_plain_c_and_a_c_program_links_and_runs(tmp_path):
+    """The boundary is a C ABI: both headers compile as pedantic C11 (and
+    C++17), and a C program built against libht.so calls it (argument
+    checks only, so no GPU is needed)."""
+    import shutil
+    from paper_1309_6275_gb300 import build
+    if not (_have_nvcc() and shutil.which("gcc") and shutil.which("g++")):
+        pytest.skip("no nvcc or gcc on this machine")
+    inc = os.path.join(ROOT, "include")
+    for name in sorted(os.listdir(inc)):
+        if not name.endswith(".h"):
+            continue
+        for cc, std in (("gcc", "-std=c11"), ("g++", "-std=c++17")):
+            src = f'#include "{name}"\nint main(void) {{ return 0; }}\n'
+            r = subprocess.run([cc, "-x", "c" if cc == "gcc" else "c++", std, "-Wall", "-Wextra",
+                                "-pedantic", "-Werror", "-fsyntax-only", "-I", inc, "-"],
+                               input=src, capture_output=True, text=True)
+            assert r.returncode == 0, (name, cc, r.stderr)
+    lib = build.build()
+    cuda_lib = "/usr/local/cuda/lib64"
+    (tmp_path / "use_ht.c").write_text(C_PROGRAM)
+    exe = str(tmp_path / "use_ht")
+    r = subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-I", inc, str(tmp_path / "use_ht.c"),
+                        lib, f"-Wl,-rpath,{os.path.dirname(lib)}", f"-Wl,-rpath-link,{cuda_lib}",
+                        "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    env = dict(os.environ, LD_LIBRARY_PATH=cuda_lib + ":" + os.environ.get("LD_LIBRARY_PATH", ""))
+    r = subprocess.run([exe], capture_output=True, text=True, env=env, timeout=60)
+    assert r.returncode == 0, (r.stdout, r.stderr)
+    assert r.stdout.startswith("1 1 ht_vote:")
