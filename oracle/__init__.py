@@ -5,7 +5,10 @@ leg may import this package.
 """
 from . import oracle
 from .oracle import (build, tables, edge_tables, vote, vote_hitmask, vote_swept, peaks,
-                     associate, associate_dense, vote_z, atan2, run_event)
+                     associate, associate_dense, vote_z, atan2, run_event, vote_layers,
+                     circle3, confirm, confirm_assign, run_event_tracks, CONFIRM_DEFAULT)
 
 __all__ = ["oracle", "build", "tables", "edge_tables", "vote", "vote_hitmask", "vote_swept",
-           "peaks", "associate", "associate_dense", "vote_z", "atan2", "run_event"]
+           "peaks", "associate", "associate_dense", "vote_z", "atan2", "run_event",
+           "vote_layers", "circle3", "confirm", "confirm_assign", "run_event_tracks",
+           "CONFIRM_DEFAULT"]

@@ -604,3 +604,230 @@ void or_vote_z(const or_geom *g, const float *x, const float *y, const float *z,
     free(hist);
     free(phi0); free(sn); free(cs); free(rho);
 }
+
+/* ------------------------------------------------------------------------
+ * Track finding in dense events: the distinct-layer vote and the candidate
+ * confirmation.
+ *
+ * Reading (the paper's detector has ten layers and its peak finder expects
+ * tracks of seven or more hits, Sections 5 and 7; a track leaves at most one
+ * hit per layer): a cell's count is the number of DISTINCT detector layers
+ * among the hits that vote in it, instead of the number of votes.  Inner
+ * layers are the densest (about a thousand hits on a circle of 25 cm at
+ * 10k hits per event), and with plain counts their hits pile up tens of
+ * votes in every cell of the d0 band they reach, which buries the 10-hit
+ * tracks; counting each layer once removes that pile-up.  The votes are the
+ * plain vote's (cell_bins), hit by hit. */
+
+/* Distinct-layer vote.  layer[h] in [0, 16) is hit h's detector layer;
+ * mask (NULL: every cell allowed) restricts hit h's votes to the cells that
+ * in_hit_halo(mask[h]) allows, as in or_vote_hitmask.  acc holds rows
+ * [i_begin, i_end) (the caller zeroes it): acc[cell] = number of distinct
+ * layers among the hits voting in the cell.  stats[0] += votes cast,
+ * stats[1] += in-range roots near a bin edge (as or_vote counts them). */
+void or_vote_layers(const or_geom *g, const float *x, const float *y, const uint8_t *layer,
+                    const uint64_t *mask, int64_t n, int32_t i_begin, int32_t i_end,
+                    int64_t *acc, int64_t *stats)
+{
+    double *phi0 = malloc(sizeof(double) * g->n_phi0);
+    double *sn = malloc(sizeof(double) * g->n_phi0);
+    double *cs = malloc(sizeof(double) * g->n_phi0);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    or_tables(g, phi0, sn, cs, rho);
+    const int64_t row_cells = (int64_t)g->n_d0 * g->n_phi0;
+    uint32_t *seen = calloc((size_t)((i_end - i_begin) * row_cells), sizeof(uint32_t));
+    int64_t votes = 0, edge = 0;
+    for (int64_t h = 0; h < n; ++h)
+        for (int32_t i = i_begin; i < i_end; ++i)
+            for (int32_t k = 0; k < g->n_phi0; ++k) {
+                int32_t j[2];
+                int64_t e = 0;
+                const int nv = cell_bins(g, x[h], y[h], sn[k], cs[k], rho[i], j, &e);
+                for (int t = 0; t < nv; ++t) {
+                    if (mask && !in_hit_halo(g, mask[h], i, j[t]))
+                        continue;
+                    seen[(int64_t)(i - i_begin) * row_cells + (int64_t)j[t] * g->n_phi0 + k] |=
+                        1u << layer[h];
+                    ++votes;
+                }
+                edge += e;
+            }
+    for (int32_t i = i_begin; i < i_end; ++i)
+        for (int64_t c = 0; c < row_cells; ++c) {
+            const uint32_t bits = seen[(int64_t)(i - i_begin) * row_cells + c];
+            int64_t nl = 0;
+            for (int l = 0; l < 16; ++l)
+                nl += (bits >> l) & 1u;
+            acc[(int64_t)i * row_cells + c] = nl;
+        }
+    stats[0] += votes;
+    stats[1] += edge;
+    free(seen);
+    free(phi0); free(sn); free(cs); free(rho);
+}
+
+typedef struct {
+    int32_t pool;        /* inlier pool: bins within pool of the candidate's bin */
+    int32_t min_layers;  /* a candidate is confirmed with at least this many inlier layers */
+    int32_t n_layers;    /* layers are 0 .. n_layers - 1 (<= 16) */
+    int32_t reserved;
+    double tol;          /* inlier distance to the seed circle, cm */
+} or_confirm_params;
+
+/* Circle through three points (the circumcentre, from coordinates relative
+ * to the first point): with a = P2 - P1, b = P3 - P1 and
+ * d = 2 (a_x b_y - a_y b_x), the centre is P1 + ((b_y |a|^2 - a_y |b|^2) / d,
+ * (a_x |b|^2 - b_x |a|^2) / d) and the radius its distance from P1.
+ * Returns 0 when the points are collinear (d == 0). */
+int or_circle3(double x1, double y1, double x2, double y2, double x3, double y3,
+               double *xc, double *yc, double *R)
+{
+    const double ax = x2 - x1, ay = y2 - y1, bx = x3 - x1, by = y3 - y1;
+    const double d = 2.0 * (ax * by - ay * bx);
+    if (d == 0.0)
+        return 0;
+    const double a2 = ax * ax + ay * ay, b2 = bx * bx + by * by;
+    const double ux = (by * a2 - ay * b2) / d;
+    const double uy = (ax * b2 - bx * a2) / d;
+    *xc = x1 + ux;
+    *yc = y1 + uy;
+    *R = sqrt(ux * ux + uy * uy);
+    return 1;
+}
+
+/* Candidate confirmation (Section 5: costlier computations confirm a
+ * candidate; Fig. 5 refines candidates by a fit).  Reading, for candidate
+ * m = (i, j, k) and every hit h of the event, with the bins b of h's roots
+ * in column (rho_i, phi0_k) exactly as the vote casts them (cell_bins):
+ *   own(h)   some b == j             (h votes in the candidate's cell)
+ *   pool(h)  some |b - j| <= pool    (h is near the cell in this column)
+ * 1. Seed layers: the layers holding exactly one own hit, in increasing
+ *    layer order; fewer than three: not confirmed.  la = the first, lc =
+ *    the last, lb = the one between them whose index is closest to
+ *    (la + lc) / 2 (smaller index on a tie).
+ * 2. Seed circle: through the own hits of la, lb and lc (or_circle3);
+ *    collinear seeds: not confirmed.
+ * 3. Inliers: for each layer, the pool hit of that layer closest to the
+ *    circle, |sqrt((x - xc)^2 + (y - yc)^2) - R| (smaller hit index on a
+ *    tie), if that distance is below tol.
+ * 4. score = the number of inlier layers; confirmed iff score >= min_layers.
+ * Candidates m_begin .. m_end - 1 of peaks[0 .. npk); per candidate:
+ * score[m] (0 when not confirmed), seeds[3 m .. 3 m + 2] (hit indices, -1
+ * when there is no seed) and inl[16 m + l] (the inlier hit of layer l, -1
+ * none; all -1 when not confirmed). */
+void or_confirm(const or_geom *g, const or_confirm_params *p, const float *x, const float *y,
+                const uint8_t *layer, int64_t n, const int32_t *peaks, int64_t m_begin,
+                int64_t m_end, int32_t *score, int32_t *seeds, int32_t *inl)
+{
+    double *phi0 = malloc(sizeof(double) * g->n_phi0);
+    double *sn = malloc(sizeof(double) * g->n_phi0);
+    double *cs = malloc(sizeof(double) * g->n_phi0);
+    double *rho = malloc(sizeof(double) * g->n_rho);
+    or_tables(g, phi0, sn, cs, rho);
+    unsigned char *own = malloc((size_t)(n > 0 ? n : 1));
+    unsigned char *pool = malloc((size_t)(n > 0 ? n : 1));
+    int64_t edge = 0;
+    for (int64_t m = m_begin; m < m_end; ++m) {
+        const int32_t im = peaks[4 * m], jm = peaks[4 * m + 1], km = peaks[4 * m + 2];
+        score[m] = 0;
+        seeds[3 * m] = seeds[3 * m + 1] = seeds[3 * m + 2] = -1;
+        for (int l = 0; l < 16; ++l)
+            inl[16 * m + l] = -1;
+        int32_t n_own[16] = {0}, own_hit[16];
+        for (int64_t h = 0; h < n; ++h) {
+            int32_t j[2];
+            const int nv = cell_bins(g, x[h], y[h], sn[km], cs[km], rho[im], j, &edge);
+            own[h] = pool[h] = 0;
+            for (int v = 0; v < nv; ++v) {
+                if (j[v] == jm)
+                    own[h] = 1;
+                if (abs(j[v] - jm) <= p->pool)
+                    pool[h] = 1;
+            }
+            if (own[h]) {
+                ++n_own[layer[h]];
+                own_hit[layer[h]] = (int32_t)h;
+            }
+        }
+        int32_t sl[16], ns = 0;
+        for (int l = 0; l < p->n_layers; ++l)
+            if (n_own[l] == 1)
+                sl[ns++] = l;
+        if (ns < 3)
+            continue;
+        const int32_t la = sl[0], lc = sl[ns - 1];
+        int32_t lb = -1, best_gap = 1 << 30;
+        for (int t = 1; t < ns - 1; ++t) {
+            const int32_t gap = abs(2 * sl[t] - (la + lc));
+            if (gap < best_gap) {
+                best_gap = gap;
+                lb = sl[t];
+            }
+        }
+        const int32_t ha = own_hit[la], hb = own_hit[lb], hc = own_hit[lc];
+        seeds[3 * m] = ha;
+        seeds[3 * m + 1] = hb;
+        seeds[3 * m + 2] = hc;
+        double xc, yc, R;
+        if (!or_circle3((double)x[ha], (double)y[ha], (double)x[hb], (double)y[hb],
+                        (double)x[hc], (double)y[hc], &xc, &yc, &R))
+            continue;
+        double best_d[16];
+        int32_t best_h[16];
+        for (int l = 0; l < 16; ++l) {
+            best_d[l] = 0.0;
+            best_h[l] = -1;
+        }
+        for (int64_t h = 0; h < n; ++h) {
+            if (!pool[h])
+                continue;
+            const double dx = (double)x[h] - xc, dy = (double)y[h] - yc;
+            const double d = fabs(sqrt(dx * dx + dy * dy) - R);
+            const int l = layer[h];
+            if (best_h[l] < 0 || d < best_d[l]) {
+                best_d[l] = d;
+                best_h[l] = (int32_t)h;
+            }
+        }
+        int32_t sc = 0;
+        for (int l = 0; l < p->n_layers; ++l)
+            if (best_h[l] >= 0 && best_d[l] < p->tol)
+                ++sc;
+        if (sc < p->min_layers)
+            continue;
+        score[m] = sc;
+        for (int l = 0; l < p->n_layers; ++l)
+            if (best_h[l] >= 0 && best_d[l] < p->tol)
+                inl[16 * m + l] = best_h[l];
+    }
+    free(own); free(pool);
+    free(phi0); free(sn); free(cs); free(rho);
+}
+
+/* Final assignment after confirmation (reading): hit h goes to the confirmed
+ * candidate that lists it as an inlier with the largest score, ties to the
+ * smallest candidate index; -1 when no confirmed candidate lists it.
+ * assign[0 .. n) is written. */
+void or_confirm_assign(const int32_t *score, const int32_t *inl, int64_t npk, int64_t n,
+                       int32_t *assign)
+{
+    int32_t *best = malloc(sizeof(int32_t) * (size_t)(n > 0 ? n : 1));
+    for (int64_t h = 0; h < n; ++h) {
+        assign[h] = -1;
+        best[h] = 0;
+    }
+    for (int64_t m = 0; m < npk; ++m) {
+        if (score[m] <= 0)
+            continue;
+        for (int l = 0; l < 16; ++l) {
+            const int32_t h = inl[16 * m + l];
+            if (h < 0)
+                continue;
+            if (score[m] > best[h]) {   /* candidates in increasing m: ties keep the first */
+                best[h] = score[m];
+                assign[h] = (int32_t)m;
+            }
+        }
+    }
+    free(best);
+}

@@ -50,6 +50,18 @@ class OrGeom(ctypes.Structure):
                 ("cot_max", ctypes.c_double)]
 
 
+class OrConfirm(ctypes.Structure):
+    _fields_ = [("pool", ctypes.c_int32), ("min_layers", ctypes.c_int32),
+                ("n_layers", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("tol", ctypes.c_double)]
+
+
+# Confirmation parameters of the dense-event track finder (see or_confirm):
+# inlier pool of +-4 bins, 8 inlier layers, ten layers, 100 um (5 sigma of
+# the 20 um hit resolution).
+CONFIRM_DEFAULT = dict(pool=4, min_layers=8, n_layers=10, tol=0.01)
+
+
 def _geom(g):
     cm = 65535 if g.get("count_bits", 32) == 16 else 2147483647
     return OrGeom(g["n_rho"], g["n_d0"], g["n_phi0"], g["n_z0"], g["n_cot"],
@@ -80,6 +92,12 @@ def lib():
             L.or_atan2_array.argtypes = [vp, vp, i64, vp]
             L.or_vote_z.argtypes = [G, vp, vp, vp, vp, vp, i64, vp, vp, vp]
             L.or_associate_dense.argtypes = [G, vp, vp, vp, i64, vp, vp, vp]
+            L.or_vote_layers.argtypes = [G, vp, vp, vp, vp, i64, i32, i32, vp, vp]
+            L.or_circle3.argtypes = [ctypes.c_double] * 6 + [vp, vp, vp]
+            L.or_circle3.restype = ctypes.c_int
+            L.or_confirm.argtypes = [G, ctypes.POINTER(OrConfirm), vp, vp, vp, i64, vp, i64,
+                                     i64, vp, vp, vp]
+            L.or_confirm_assign.argtypes = [vp, vp, i64, i64, vp]
             _lib = L
         return _lib
 
@@ -310,6 +328,100 @@ def atan2(y, x):
     out = np.empty_like(y)
     lib().or_atan2_array(_p(y), _p(x), y.shape[0], _p(out))
     return out
+
+
+def vote_layers(g, x, y, layer, masks=None, threads=None, rows=None):
+    """Distinct-layer accumulator int64 [n_rho, n_d0, n_phi0] (or rows
+    [a, b) only) and stats {votes, edge}: a cell counts the distinct layers
+    of the hits voting in it (or_vote_layers).  masks: None or one uint64
+    region set per hit (the per-hit proposal's halo rule)."""
+    G = _geom(g)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    layer = np.ascontiguousarray(layer, np.uint8)
+    assert layer.shape[0] == x.shape[0] and (layer.size == 0 or int(layer.max()) < 16)
+    m = None if masks is None else np.ascontiguousarray(np.asarray(masks, np.uint64))
+    if m is not None:
+        assert m.shape[0] == x.shape[0]
+    r0, r1 = (0, g["n_rho"]) if rows is None else rows
+    acc = np.zeros((r1 - r0, g["n_d0"], g["n_phi0"]), np.int64)
+    base = r0 * g["n_d0"] * g["n_phi0"] * 8
+    parts = [(a + r0, b + r0) for a, b in _chunks(r1 - r0, _threads(threads) * 2)]
+    stats = np.zeros((len(parts), 2), np.int64)
+    accp = acc.ctypes.data - base
+
+    def run(t):
+        a, b = parts[t]
+        lib().or_vote_layers(ctypes.byref(G), _p(x), _p(y), _p(layer),
+                             None if m is None else _p(m), x.shape[0], a, b,
+                             ctypes.c_void_p(accp), _p(stats[t]))
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(run, range(len(parts))))
+    tot = stats.sum(0)
+    return acc, {"votes": int(tot[0]), "edge": int(tot[1])}
+
+
+def circle3(p1, p2, p3):
+    """(xc, yc, R) of the circle through three points, or None if collinear."""
+    xc, yc, R = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    ok = lib().or_circle3(float(p1[0]), float(p1[1]), float(p2[0]), float(p2[1]),
+                          float(p3[0]), float(p3[1]), ctypes.byref(xc), ctypes.byref(yc),
+                          ctypes.byref(R))
+    return (xc.value, yc.value, R.value) if ok else None
+
+
+def _confirm_struct(cp):
+    c = dict(CONFIRM_DEFAULT)
+    c.update(cp or {})
+    assert 1 <= c["n_layers"] <= 16
+    return OrConfirm(c["pool"], c["min_layers"], c["n_layers"], 0, c["tol"])
+
+
+def confirm(g, x, y, layer, pk, cp=None, threads=None):
+    """Confirmation of every candidate (or_confirm): (score int32 [m],
+    seeds int32 [m, 3], inliers int32 [m, 16])."""
+    G = _geom(g)
+    C = _confirm_struct(cp)
+    x = np.ascontiguousarray(x, np.float32); y = np.ascontiguousarray(y, np.float32)
+    layer = np.ascontiguousarray(layer, np.uint8)
+    assert layer.shape[0] == x.shape[0] and (layer.size == 0 or int(layer.max()) < C.n_layers)
+    pk = np.ascontiguousarray(pk, np.int32).reshape(-1, 4)
+    npk = pk.shape[0]
+    score = np.zeros(npk, np.int32)
+    seeds = np.full((npk, 3), -1, np.int32)
+    inl = np.full((npk, 16), -1, np.int32)
+    parts = _chunks(npk, _threads(threads) * 4)
+
+    def run(ab):
+        a, b = ab
+        lib().or_confirm(ctypes.byref(G), ctypes.byref(C), _p(x), _p(y), _p(layer), x.shape[0],
+                         _p(pk), a, b, _p(score), _p(seeds), _p(inl))
+
+    if npk:
+        with ThreadPoolExecutor(_threads(threads)) as ex:
+            list(ex.map(run, parts))
+    return score, seeds, inl
+
+
+def confirm_assign(score, inl, n_hits):
+    """Hit -> confirmed candidate (or_confirm_assign): int32 [n_hits]."""
+    score = np.ascontiguousarray(score, np.int32)
+    inl = np.ascontiguousarray(inl, np.int32).reshape(-1, 16)
+    out = np.full(n_hits, -1, np.int32)
+    lib().or_confirm_assign(_p(score), _p(inl), score.shape[0], n_hits, _p(out))
+    return out
+
+
+def run_event_tracks(g, x, y, z, layer, cp=None, cap=None, masks=None, threads=None):
+    """The track-finding path on one event: distinct-layer vote, peaks,
+    confirmation, final assignment and the (z0, cot theta) vote."""
+    acc, st = vote_layers(g, x, y, layer, masks, threads)
+    pk, cnt = peaks(g, acc, cap, threads)
+    score, seeds, inl = confirm(g, x, y, layer, pk, cp, threads)
+    asg = confirm_assign(score, inl, x.shape[0])
+    zr = vote_z(g, x, y, z, asg, pk, threads=threads)
+    return dict(acc=acc, stats=st, peaks=pk, count=cnt, score=score, seeds=seeds, inliers=inl,
+                assign=asg, zres=zr)
 
 
 def run_event(g, x, y, z, cap=None, threads=None):
