@@ -227,6 +227,72 @@ ht_status ht_vote_swept(const ht_geometry *g, const float *x, const float *y, in
                         void *acc, uint64_t *stats, ht_stream stream);
 
 /* ------------------------------------------------------------------------
+ * Track finding in dense events: the distinct-layer vote and the candidate
+ * confirmation (Section 5: local maxima are candidates that costlier
+ * computations confirm; Fig. 5 refines them; Section 7 tunes the peak finder
+ * for tracks of at least seven hits).  A track leaves at most one hit per
+ * detector layer, and at thousands of hits per event the inner layers are
+ * so dense that with plain counts their hits pile tens of votes into every
+ * cell of the d0 band they reach; counting layers removes that pile-up.
+ * ------------------------------------------------------------------------ */
+
+/* Distinct-layer vote.  Every hit casts exactly ht_vote's votes; a cell's
+ * count is the number of distinct layers among the hits voting in it.
+ *   layer   n_hits uint8 (device), each in [0, 16).
+ *   acc     as ht_vote (uint16 or int32 cells, every cell written).
+ *   stats   NULL or 2 device uint64: votes cast, and float64 redos.
+ * Requires an even n_d0.  Peaks (ht_find_peaks) apply unchanged to acc, the
+ * threshold then counting layers.  Errors: as ht_vote; HT_ERR_ARG also for
+ * a null layer array or an odd n_d0. */
+ht_status ht_vote_layers(const ht_geometry *g, const float *x, const float *y,
+                         const uint8_t *layer, int32_t n_hits, void *acc, uint64_t *stats,
+                         ht_stream stream);
+
+/* Confirmation parameters.  pool: bins of the candidate's column around its
+ * bin that supply inlier hits (>= 0); min_layers: inlier layers needed
+ * (>= 1); n_layers: layers 0 .. n_layers - 1 take part (1 to 16); tol: inlier
+ * distance to the seed circle, cm (> 0).  The bands set, for the batched
+ * track path, each event's peak threshold from its hit count: an event of n
+ * hits takes band_threshold[b] for the first b < n_bands with
+ * n <= band_max_hits[b], else the geometry's threshold (n_bands 0 to 8). */
+typedef struct ht_confirm_desc {
+    int32_t pool, min_layers, n_layers, n_bands;
+    double tol;
+    int32_t band_max_hits[8];
+    int32_t band_threshold[8];
+} ht_confirm_desc;
+
+/* Confirmation of one event's candidates and the final hit assignment.
+ * Reading, for candidate m = (i, j, k) and every hit h, with b the bins of
+ * h's roots in column (rho_i, phi0_k) exactly as ht_vote casts them:
+ * own(h) iff some b == j; pool(h) iff some |b - j| <= pool.  Seed layers:
+ * the layers holding exactly one own hit, at least three of them; the seed
+ * circle passes through the own hits of the first, the last, and the one
+ * between them whose index is nearest the middle of those two (the smaller
+ * on a tie).  Inliers: per layer, the pool hit closest to the circle
+ * (|distance to the centre - radius|, the smaller hit index on a tie) if
+ * that distance is below tol.  Confirmed iff there are at least min_layers
+ * inlier layers.  Each hit is then assigned to the confirmed candidate that
+ * lists it with the most inlier layers, ties to the smallest m, else -1.
+ * Float32 decides a bin only where it is proven (else float64 in the
+ * definition's order); the circle and the distances are float64, one
+ * correctly rounded operation at a time: results are bit-identical to the
+ * float64 definition.
+ *   peaks, d_count, cap   candidates as ht_find_peaks wrote them.
+ *   score     cap int32 (device): inlier layers of candidate m, 0 when not
+ *             confirmed (only the first min(*d_count, cap) are written).
+ *   inliers   16 cap int32 (device): inliers[16 m + l] = the inlier hit of
+ *             layer l, -1 for none (all -1 when not confirmed).
+ *   assign    n_hits int32 (device).
+ *   workspace ht_confirm_workspace_size(g, n_hits) bytes, 256-byte aligned.
+ * Errors: HT_ERR_ARG (null pointers, parameters out of range), HT_ERR_CUDA. */
+size_t ht_confirm_workspace_size(const ht_geometry *g, int32_t n_hits);
+ht_status ht_confirm(const ht_geometry *g, const ht_confirm_desc *c, const float *x,
+                     const float *y, const uint8_t *layer, int32_t n_hits, const ht_peak *peaks,
+                     const int32_t *d_count, int32_t cap, int32_t *score, int32_t *inliers,
+                     int32_t *assign, void *workspace, size_t workspace_bytes, ht_stream stream);
+
+/* ------------------------------------------------------------------------
  * Region masks (learned proposal).  The paper has no learned part; these
  * calls restrict the Section 5 vote and peak finding to regions that a
  * per-hit network proposes.  Regions: an 8 x 8 grid of blocks over (rho
@@ -538,6 +604,35 @@ ht_status ht_batch_run_learned_hits(ht_batch *b, const float *x, const float *y,
                                     const ht_hit_proposal *prop, uint64_t *hit_masks,
                                     ht_peak *peaks, int32_t *counts, int32_t *assign,
                                     ht_zres *zres, uint64_t *stats, ht_stream stream);
+
+/* Switch on the batched track path (ht_batch_run_tracks) with confirmation
+ * parameters *c (see ht_confirm_desc; the bands give each event's peak
+ * threshold from its hit count).  The first call allocates the path's
+ * scratch: 64 bytes per candidate slot (max_events * cap) plus per-hit keys.
+ * Clears the captured graphs.  Errors: HT_ERR_ARG, HT_ERR_CUDA. */
+ht_status ht_batch_set_confirm(ht_batch *b, const ht_confirm_desc *c);
+
+/* The track path on a batch: per event, the distinct-layer vote
+ * (ht_vote_layers; with hit_masks each hit's votes restricted to its region
+ * set as in ht_vote_hit_masked), peaks at the event's band threshold,
+ * confirmation and final assignment (ht_confirm) instead of ht_associate,
+ * and the (z0, cot theta) vote of each candidate over its assigned hits.
+ * Results per event are those of the single-event calls.
+ *   layer      device uint8 per hit (indexed like x), each in [0, 16).
+ *   prop       NULL, or a per-hit proposal whose top-k region sets are
+ *              computed at the head of the graph into hit_masks.
+ *   hit_masks  NULL (no restriction), or device uint64 per hit: given sets
+ *              (prop NULL) or the proposal's output (prop set).
+ *   score      n_events * cap int32 (device): inlier layers of each
+ *              candidate slot, 0 when not confirmed.
+ *   peaks, counts, assign, zres, stats   as ht_batch_run; assign holds each
+ *              hit's confirmed candidate within its event, -1 none.
+ * Requires ht_batch_set_confirm.  Errors: as ht_batch_run. */
+ht_status ht_batch_run_tracks(ht_batch *b, const float *x, const float *y, const float *z,
+                              const uint8_t *layer, const int32_t *h_off, int32_t n_events,
+                              const ht_hit_proposal *prop, uint64_t *hit_masks, ht_peak *peaks,
+                              int32_t *counts, int32_t *score, int32_t *assign, ht_zres *zres,
+                              uint64_t *stats, ht_stream stream);
 
 /* Device time of the stages of the last completed batch run, in ms: ms[0]
  * proposal (0 without one), ms[1] vote, ms[2] peak finding and candidate

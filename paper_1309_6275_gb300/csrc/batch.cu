@@ -72,6 +72,12 @@ cudaError_t launch_vote_batch_hitmask(const DevGeom &G, const float *x, const fl
 cudaError_t launch_hit_masks(const void *params_bf16, const float *x, const float *y,
                              const float *z, const uint8_t *layer, int n, const int *d_n,
                              int topk, float pmin, unsigned long long *hit_masks, cudaStream_t st);
+cudaError_t launch_vote_batch_layers(const DevGeom &G, const float *x, const float *y,
+                                     const uint8_t *layer, const int *off, const int *order,
+                                     const int *d_nev, uint16_t *acc, size_t acc_stride,
+                                     unsigned long long *stats, int *head, int kt, int sms,
+                                     const unsigned long long *hit_masks, cudaStream_t st,
+                                     const HitBuckets *hb);
 }  // namespace ht
 
 namespace {
@@ -82,18 +88,22 @@ constexpr int kStages = 5;   // proposal, vote, peaks + lists, association, z vo
 
 struct GraphEntry {
     int n_ev;
-    const void *ptr[12];
+    const void *ptr[14];
     float tau, fmax, pmin;
     int grow, topk;
     cudaGraphExec_t exec;
 };
 
-// What restricts the vote of one run (all null: the plain path).
+// What restricts the vote of one run (all null: the plain path), and the
+// track path (layer set: distinct-layer vote, confirmation instead of the
+// association, confirmation scores written to score).
 struct Restrict {
     unsigned long long *masks;        // per event
     const ht_proposal *prop;          // writes masks first
     unsigned long long *hit_masks;    // per hit
     const ht_hit_proposal *hprop;     // writes hit_masks first
+    const uint8_t *layer;             // per hit: the track path
+    int32_t *score;                   // per candidate slot (track path)
 };
 
 }  // namespace
@@ -105,7 +115,8 @@ struct ht_batch {
     size_t cells;
     uint16_t *acc;
     int *meta;          // [0] n_big [1] pad [2] n_all [3] pad, off[max_events + 1],
-                        // order_big[max_events], order_all[max_events] (largest first)
+                        // order_big[max_events], order_all[max_events] (largest first),
+                        // thr[max_events] (peak threshold of each event slot)
     int *h_meta;        // pinned staging, same layout
     size_t meta_ints;
     cudaEvent_t meta_done;
@@ -124,6 +135,10 @@ struct ht_batch {
     float *mass;        // per-event region masses of the learned proposal
     char *bk_ws;        // per-event hit lists by column group (k_buckets.cu)
     ht::HitBuckets bk;
+    ht_confirm_desc conf;   // track path parameters (set by ht_batch_set_confirm)
+    bool conf_set;
+    int *inl;               // track path: 16 inlier hits per candidate slot
+    char *cf_ws;            // track path: confirmation scratch
     GraphEntry cache[kGraphCache];
     int ncache;
     bool use_graph;
@@ -136,6 +151,7 @@ namespace {
 int *off_of(int *meta) { return meta + 4; }
 int *order_big_of(int *meta, int me) { return meta + 4 + me + 1; }
 int *order_all_of(int *meta, int me) { return meta + 4 + 2 * me + 1; }
+int *thr_of(int *meta, int me) { return meta + 4 + 3 * me + 1; }
 
 void free_batch(ht_batch *b)
 {
@@ -154,6 +170,8 @@ void free_batch(ht_batch *b)
     cudaFree(b->z_ws);
     cudaFree(b->mass);
     cudaFree(b->bk_ws);
+    cudaFree(b->inl);
+    cudaFree(b->cf_ws);
     if (b->h_meta) cudaFreeHost(b->h_meta);
     if (b->meta_done) cudaEventDestroy(b->meta_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -223,23 +241,47 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
                      : ht::launch_vote_batch(G, x, y, off, order, d_nev, b->acc, b->cells, st64,
                                              head, pack, kt, b->sms, st, &b->bk);
     };
-    e = vote(order_big_of(meta, me), meta + 0, b->heads + 0, false, b->kt_big);
-    if (e != cudaSuccess) return e;
-    e = vote(order_all_of(meta, me), meta + 2, b->heads + 1, true, b->kt_pack);
+    const bool tracks = R.layer != nullptr;
+    if (tracks) {
+        // the distinct-layer vote packs every tile: one launch
+        e = ht::launch_vote_batch_layers(G, x, y, R.layer, off, order_all_of(meta, me), meta + 2,
+                                         b->acc, b->cells, st64, b->heads + 1, b->kt_pack,
+                                         b->sms, R.hit_masks, st, &b->bk);
+    } else {
+        e = vote(order_big_of(meta, me), meta + 0, b->heads + 0, false, b->kt_big);
+        if (e == cudaSuccess) e = vote(order_all_of(meta, me), meta + 2, b->heads + 1, true, b->kt_pack);
+    }
     if (e == cudaSuccess) e = mark(2);
     if (e != cudaSuccess) return e;
-    // peaks and candidate tile lists per event slot
+    // peaks (each event slot at its staged threshold on the track path) and
+    // the association's candidate tile lists per event slot
     for (int ev = 0; ev < n_ev; ++ev) {
         e = ht::launch_peaks(G, b->acc + (size_t)ev * b->cells, peaks + (size_t)ev * b->cap,
                              b->cap, counts + ev, b->pk_ws + (size_t)ev * b->pk_stride, st,
-                             masks ? masks + ev : nullptr);
+                             masks ? masks + ev : nullptr, tracks ? thr_of(meta, me) + ev : nullptr);
         if (e != cudaSuccess) return e;
+        if (tracks) continue;
         const size_t to = (size_t)ev * (b->ntiles + 1);
         e = ht::launch_cand_lists(G, b->kt_assoc, peaks + (size_t)ev * b->cap, counts + ev,
                                   b->cap, b->tcnt + to, b->toff + to, b->tcur + to,
                                   b->ttmp + (size_t)ev * b->ttmp_stride,
                                   b->tlist + (size_t)ev * b->lstride, st);
         if (e != cudaSuccess) return e;
+    }
+    if (tracks) {
+        // confirmation and final assignment over the whole batch
+        e = mark(3);
+        const ht::ConfirmDev P{b->conf.pool, b->conf.min_layers, b->conf.n_layers, b->conf.tol};
+        if (e == cudaSuccess)
+            e = ht::launch_confirm_batch(G, P, x, y, R.layer, off, meta + 2, b->max_events,
+                                         b->max_hits, peaks, counts, b->cap, R.score, b->inl,
+                                         assign, b->cf_ws, b->sms, st, &b->bk);
+        if (e == cudaSuccess) e = mark(4);
+        if (e == cudaSuccess)
+            e = ht::launch_vote_z_batch(G, x, y, z, assign, off, meta + 2, peaks, counts, b->cap,
+                                        n_ev, zres, b->z_ws, b->max_hits, st);
+        if (e == cudaSuccess) e = mark(5);
+        return e;
     }
     // association over the whole batch
     e = cudaMemsetAsync(b->gbest, 0, (size_t)b->max_hits * 8, st);
@@ -282,6 +324,18 @@ ht_status stage_meta(ht_batch *b, const int32_t *h_off, int n_ev, cudaStream_t s
     }
     hm[0] = nb;
     hm[2] = n_ev;
+    // peak threshold of each event slot (track path): the first band holding
+    // the event's hit count, else the geometry's threshold
+    for (int ev = 0; ev < n_ev; ++ev) {
+        const int nh = h_off[ev + 1] - h_off[ev];
+        int t = b->g->desc.threshold;
+        for (int q = 0; b->conf_set && q < b->conf.n_bands; ++q)
+            if (nh <= b->conf.band_max_hits[q]) {
+                t = b->conf.band_threshold[q];
+                break;
+            }
+        thr_of(hm, me)[ev] = t;
+    }
     for (int i = 0; i <= n_ev; ++i) off_of(hm)[i] = h_off[i];
     for (int i = n_ev + 1; i <= me; ++i) off_of(hm)[i] = h_off[n_ev];
     cudaError_t e = cudaMemcpyAsync(b->meta, hm, b->meta_ints * sizeof(int), cudaMemcpyHostToDevice,
@@ -338,7 +392,7 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     b->kt_big = 0;
     b->kt_assoc = ht::assoc32_kt(G);
     b->cells = (size_t)G.n_rho * G.n_d0 * G.n_phi0;
-    b->meta_ints = 4 + (size_t)max_events + 1 + 2 * (size_t)max_events;
+    b->meta_ints = 4 + (size_t)max_events + 1 + 3 * (size_t)max_events;
     b->pk_stride = ht::align256(ht::peaks_workspace_bytes(G));
     b->ntiles = ht::assoc32_ntiles(G, 1);   // the most tiles any tile width gives
     b->ttmp_stride = ht::scan_tmp_bytes(b->ntiles);
@@ -408,6 +462,9 @@ ht_status run_impl(ht_batch *b, const float *x, const float *y, const float *z,
         return ht::set_error(HT_ERR_ARG, "ht_batch_run_learned_hits: bad proposal argument");
     if (R.hit_masks && (reinterpret_cast<uintptr_t>(R.hit_masks) & 7u))
         return ht::set_error(HT_ERR_ARG, "ht_batch_run_hit_masked: hit_masks not 8-byte aligned");
+    if (R.layer && (!R.score || !b->conf_set))
+        return ht::set_error(HT_ERR_ARG,
+                             "ht_batch_run_tracks: null score, or ht_batch_set_confirm not called");
     ht_status s = check_offsets(b, h_off, n_events);
     if (s != HT_OK) return s;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
@@ -421,8 +478,8 @@ ht_status run_impl(ht_batch *b, const float *x, const float *y, const float *z,
     const void *params = prop ? prop->params_bf16 : R.hprop ? R.hprop->params_bf16 : nullptr;
     const void *layer = prop ? (const void *)prop->layer
                              : R.hprop ? (const void *)R.hprop->layer : nullptr;
-    const void *key[12] = {x,     y,     z,     peaks,  counts, assign,
-                           zres,  stats, R.masks, params, layer,  R.hit_masks};
+    const void *key[14] = {x,     y,     z,       peaks,  counts, assign,      zres,
+                           stats, R.masks, params, layer, R.hit_masks, R.layer, R.score};
     const float tau = prop ? prop->tau : 0.f, fmax = prop ? prop->fmax : 0.f;
     const int grow = prop ? prop->grow : 0;
     const int topk = R.hprop ? R.hprop->topk : 0;
@@ -524,6 +581,54 @@ ht_status ht_batch_run_learned_hits(ht_batch *b, const float *x, const float *y,
     Restrict R{};
     R.hit_masks = reinterpret_cast<unsigned long long *>(hit_masks);
     R.hprop = prop;
+    return run_impl(b, x, y, z, h_off, n_events, R, peaks, counts, assign, zres, stats, stream);
+}
+
+ht_status ht_batch_set_confirm(ht_batch *b, const ht_confirm_desc *c)
+{
+    if (!b || !c) return ht::set_error(HT_ERR_ARG, "ht_batch_set_confirm: null argument");
+    if (c->pool < 0 || c->min_layers < 1 || c->n_layers < 1 || c->n_layers > 16 ||
+        !(c->tol > 0.0) || c->n_bands < 0 || c->n_bands > 8)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_set_confirm: parameters out of range");
+    for (int q = 0; q < c->n_bands; ++q)
+        if (c->band_threshold[q] < 1)
+            return ht::set_error(HT_ERR_ARG, "ht_batch_set_confirm: band threshold below 1");
+    if (b->meta_pending) {
+        if (cudaEventSynchronize(b->meta_done) != cudaSuccess)
+            return ht::set_error(HT_ERR_CUDA, "ht_batch_set_confirm: staging wait");
+        b->meta_pending = false;
+    }
+    if (!b->inl) {
+        cudaError_t e = cudaMalloc((void **)&b->inl, (size_t)b->max_events * b->cap * 16 * 4);
+        if (e == cudaSuccess)
+            e = cudaMalloc((void **)&b->cf_ws,
+                           ht::confirm_workspace_bytes(b->max_events, b->max_hits));
+        if (e != cudaSuccess) {
+            cudaFree(b->inl);
+            b->inl = nullptr;
+            return ht::set_error(HT_ERR_CUDA, "ht_batch_set_confirm: allocation failed");
+        }
+    }
+    b->conf = *c;
+    b->conf_set = true;
+    clear_graphs(b);   // the parameters are part of every captured track graph
+    return HT_OK;
+}
+
+ht_status ht_batch_run_tracks(ht_batch *b, const float *x, const float *y, const float *z,
+                              const uint8_t *layer, const int32_t *h_off, int32_t n_events,
+                              const ht_hit_proposal *prop, uint64_t *hit_masks, ht_peak *peaks,
+                              int32_t *counts, int32_t *score, int32_t *assign, ht_zres *zres,
+                              uint64_t *stats, ht_stream stream)
+{
+    if (!b || !layer) return ht::set_error(HT_ERR_ARG, "ht_batch_run_tracks: null argument");
+    if (prop && !hit_masks)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run_tracks: a proposal needs hit_masks");
+    Restrict R{};
+    R.hit_masks = reinterpret_cast<unsigned long long *>(hit_masks);
+    R.hprop = prop;
+    R.layer = layer;
+    R.score = score;
     return run_impl(b, x, y, z, h_off, n_events, R, peaks, counts, assign, zres, stats, stream);
 }
 

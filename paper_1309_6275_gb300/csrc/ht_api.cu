@@ -25,6 +25,10 @@ cudaError_t prepare_swept_kernels(int max_smem);
 size_t swept_smem_need(const DevGeom &G);
 cudaError_t prepare_peaks_kernels();
 size_t z_big_smem(const DevGeom &G);
+cudaError_t prepare_layer_vote_kernels(int max_smem);
+cudaError_t launch_vote_layers(const DevGeom &G, const float *x, const float *y,
+                               const uint8_t *layer, int n, void *acc,
+                               unsigned long long *stats, cudaStream_t st);
 }  // namespace ht
 
 namespace {
@@ -200,6 +204,7 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     if (e == cudaSuccess) e = ht::prepare_tile_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_z_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_masked_vote_kernels(max_smem);
+    if (e == cudaSuccess) e = ht::prepare_layer_vote_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_swept_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_peaks_kernels();
     if (e == cudaSuccess) e = ht::prepare_mlp_kernels();
@@ -302,6 +307,54 @@ ht_status ht_vote_swept(const ht_geometry *g, const float *x, const float *y, in
         e = ht::launch_vote_swept(g->G, x, y, n_hits, acc,
                                   reinterpret_cast<unsigned long long *>(stats), S(stream));
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_swept");
+}
+
+ht_status ht_vote_layers(const ht_geometry *g, const float *x, const float *y,
+                         const uint8_t *layer, int32_t n_hits, void *acc, uint64_t *stats,
+                         ht_stream stream)
+{
+    if (!g || !acc) return fail(HT_ERR_ARG, "ht_vote_layers: null geometry or accumulator");
+    if (n_hits < 0 || n_hits > kMaxHits)
+        return fail(HT_ERR_ARG, "ht_vote_layers: n_hits %d outside [0, %d]", n_hits, kMaxHits);
+    if (n_hits > 0 && (!x || !y || !layer))
+        return fail(HT_ERR_ARG, "ht_vote_layers: null hit or layer arrays");
+    if (g->desc.n_d0 % 2 != 0) return fail(HT_ERR_ARG, "ht_vote_layers: n_d0 must be even");
+    if (!aligned(acc, 16) || (x && !aligned(x, 16)) || (y && !aligned(y, 16)))
+        return fail(HT_ERR_ARG, "ht_vote_layers: pointers must be 16-byte aligned");
+    cudaError_t e = cudaSuccess;
+    if (stats) e = cudaMemsetAsync(stats, 0, 2 * sizeof(uint64_t), S(stream));
+    if (e == cudaSuccess)
+        e = ht::launch_vote_layers(g->G, x, y, layer, n_hits, acc,
+                                   reinterpret_cast<unsigned long long *>(stats), S(stream));
+    return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_layers");
+}
+
+size_t ht_confirm_workspace_size(const ht_geometry *g, int32_t n_hits)
+{
+    (void)g;
+    return ht::confirm_workspace_bytes_single(n_hits > 0 ? n_hits : 0);
+}
+
+ht_status ht_confirm(const ht_geometry *g, const ht_confirm_desc *c, const float *x,
+                     const float *y, const uint8_t *layer, int32_t n_hits, const ht_peak *peaks,
+                     const int32_t *d_count, int32_t cap, int32_t *score, int32_t *inliers,
+                     int32_t *assign, void *workspace, size_t workspace_bytes, ht_stream stream)
+{
+    if (!g || !c || !d_count || !workspace || (cap > 0 && (!peaks || !score || !inliers)))
+        return fail(HT_ERR_ARG, "ht_confirm: null argument");
+    if (n_hits < 0 || n_hits > kMaxHits || cap < 0)
+        return fail(HT_ERR_ARG, "ht_confirm: n_hits %d or cap %d out of range", n_hits, cap);
+    if (n_hits > 0 && (!x || !y || !layer || !assign))
+        return fail(HT_ERR_ARG, "ht_confirm: null hit arrays");
+    if (c->pool < 0 || c->min_layers < 1 || c->n_layers < 1 || c->n_layers > 16 ||
+        !(c->tol > 0.0))
+        return fail(HT_ERR_ARG, "ht_confirm: parameters out of range");
+    if (workspace_bytes < ht::confirm_workspace_bytes_single(n_hits) || !aligned(workspace, 256))
+        return fail(HT_ERR_ARG, "ht_confirm: workspace too small or misaligned");
+    const ht::ConfirmDev P{c->pool, c->min_layers, c->n_layers, c->tol};
+    cudaError_t e = ht::launch_confirm(g->G, P, x, y, layer, n_hits, peaks, d_count, cap, score,
+                                       inliers, assign, workspace, S(stream));
+    return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_confirm");
 }
 
 size_t ht_find_peaks_workspace_size(const ht_geometry *g)

@@ -372,7 +372,7 @@ cudaError_t launch_vote_hitmask(const DevGeom &G, const float *x, const float *y
 // mask (device, or null for every cell): only peaks inside it are reported.
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
                          int *d_count, void *ws, cudaStream_t st,
-                         const unsigned long long *mask = nullptr);
+                         const unsigned long long *mask = nullptr, const int *d_thr = nullptr);
 size_t peaks_workspace_bytes(const DevGeom &G);
 cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, int n,
                              const ht_peak *peaks, const int *d_count, int cap, int *assign,
@@ -384,6 +384,27 @@ cudaError_t launch_vote_z(const DevGeom &G, const float *x, const float *y, cons
 size_t vote_z_workspace_bytes(const DevGeom &G, int n, int cap);
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// Candidate confirmation (k_confirm.cu): parameters as ht_confirm_desc.
+struct ConfirmDev {
+    int pool, min_layers, n_layers;
+    double tol;
+};
+// Batch: event e's hits at x[off[e] ..), candidates peaks[e cap ..), kept
+// counts min(counts[e], cap); score (n_ev cap), inl (16 n_ev cap) and
+// assign (batch hit index) written.  ws: confirm_workspace_bytes.
+size_t confirm_workspace_bytes(int max_events, int max_hits);
+cudaError_t launch_confirm_batch(const DevGeom &G, const ConfirmDev &P, const float *x,
+                                 const float *y, const uint8_t *layer, const int *off,
+                                 const int *d_nev, int max_events, int max_hits,
+                                 const ht_peak *peaks, const int *counts, int cap, int *score,
+                                 int *inl, int *assign, void *ws, int sms, cudaStream_t st,
+                                 const HitBuckets *hb);
+// One event of n hits (host) and *d_count candidates (device).
+size_t confirm_workspace_bytes_single(int n);
+cudaError_t launch_confirm(const DevGeom &G, const ConfirmDev &P, const float *x, const float *y,
+                           const uint8_t *layer, int n, const ht_peak *peaks, const int *d_count,
+                           int cap, int *score, int *inl, int *assign, void *ws, cudaStream_t st);
 
 // Records msg as this host thread's ht_last_error() text; returns s.
 ht_status set_error(ht_status s, const char *msg);

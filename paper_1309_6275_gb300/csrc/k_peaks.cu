@@ -48,12 +48,14 @@ constexpr size_t kPkSmemMax = Stage<int32_t>::kBytes;
 // MASKED: only cells inside *mask (a learned proposal's regions) can be
 // peaks; a CTA whose bins are all outside reads nothing.  An inside cell's
 // 26 neighbours lie in the mask's halo, which the masked vote fills exactly.
+// d_thr (null: the geometry's threshold): a device threshold for this event.
 template <typename T, bool WRITE, bool MASKED>
 __global__ void __launch_bounds__(kPkThreads)
 k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         const int *__restrict__ segoff, ht_peak *__restrict__ out, int cap,
-        const unsigned long long *__restrict__ mask)
+        const unsigned long long *__restrict__ mask, const int *__restrict__ d_thr)
 {
+    const int thr = d_thr ? *d_thr : G.threshold;
     extern __shared__ __align__(16) unsigned char smraw[];
     T *sw = reinterpret_cast<T *>(smraw);                // [slice][kSW], slice = r (kJB+2) + jj
     constexpr int kOff = Stage<T>::kOff, kSW = Stage<T>::kSW;
@@ -145,7 +147,7 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
             const int after = max(__vimax3_s32(cm[2][0], cm[2][1], cm[2][2]),
                                   __vimax3_s32(cm[1][2], wrap_lo ? c1[0] : 0,
                                                wrap_hi ? 0 : c1[2]));
-            const bool pk = cok && v >= G.threshold && v > before && v >= after &&
+            const bool pk = cok && v >= thr && v > before && v >= after &&
                             (!MASKED || ((inside >> region_block(j0 + jl, ND)) & 1u));
             const unsigned bal = __ballot_sync(0xffffffffu, pk);
             if (lane == 0) bal_s[jl][warp] = bal;
@@ -181,17 +183,17 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
 template <typename T, bool MASKED>
 cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, int *d_count,
                       int *segcnt, int *segoff, void *tmp, const unsigned long long *mask,
-                      cudaStream_t st)
+                      cudaStream_t st, const int *d_thr)
 {
     const int nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     dim3 grid(nkb, (G.n_d0 + kJB - 1) / kJB, G.n_rho);
     const int nseg = G.n_rho * G.n_d0 * nkb;
     k_peaks<T, false, MASKED><<<grid, kPkThreads, Stage<T>::kBytes, st>>>(
-        G, acc, segcnt, nullptr, nullptr, 0, mask);
+        G, acc, segcnt, nullptr, nullptr, 0, mask, d_thr);
     cudaError_t e = scan_exclusive(segcnt, segoff, nullptr, nseg, nullptr, d_count, tmp, st);
     if (e != cudaSuccess) return e;
     k_peaks<T, true, MASKED><<<grid, kPkThreads, Stage<T>::kBytes, st>>>(
-        G, acc, nullptr, segoff, peaks, cap, mask);
+        G, acc, nullptr, segoff, peaks, cap, mask, d_thr);
     return cudaGetLastError();
 }
 
@@ -222,7 +224,8 @@ size_t peaks_workspace_bytes(const DevGeom &G)
 }
 
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
-                         int *d_count, void *ws, cudaStream_t st, const unsigned long long *mask)
+                         int *d_count, void *ws, cudaStream_t st, const unsigned long long *mask,
+                         const int *d_thr)
 {
     const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     const size_t nseg = (size_t)G.n_rho * G.n_d0 * nkb;
@@ -235,15 +238,15 @@ cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int 
     if (mask) {
         if (G.count_bits == 16)
             return run_peaks<uint16_t, true>(G, a16, peaks, cap, d_count, segcnt, segoff, tmp,
-                                             mask, st);
+                                             mask, st, d_thr);
         return run_peaks<int32_t, true>(G, a32, peaks, cap, d_count, segcnt, segoff, tmp, mask,
-                                        st);
+                                        st, d_thr);
     }
     if (G.count_bits == 16)
         return run_peaks<uint16_t, false>(G, a16, peaks, cap, d_count, segcnt, segoff, tmp,
-                                          nullptr, st);
+                                          nullptr, st, d_thr);
     return run_peaks<int32_t, false>(G, a32, peaks, cap, d_count, segcnt, segoff, tmp, nullptr,
-                                     st);
+                                     st, d_thr);
 }
 
 }  // namespace ht

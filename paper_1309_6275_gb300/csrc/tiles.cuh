@@ -21,6 +21,15 @@ constexpr int kThreads = 256;
 // ht_internal.cuh).  Association replays votes under kModeEvent with a
 // candidate-box window in MaskCtx.
 constexpr int kModePlain = 0, kModeEvent = 1, kModeHit = 2;
+// Flag on a mode: the distinct-layer vote.  A cell counts the distinct
+// detector layers of the hits voting in it (a track leaves at most one hit
+// per layer); tile words hold 16-bit layer masks (bit l = layer l), set with
+// atomicOr, and the write-back stores their population counts.  An OR never
+// carries, so two masks always share a word, whatever the hit count.
+constexpr int kModeLayers = 4, kModeBase = 3;
+
+__host__ __device__ constexpr int base_mode(int m) { return m & kModeBase; }
+__host__ __device__ constexpr bool layer_mode(int m) { return (m & kModeLayers) != 0; }
 
 template <typename OutT>
 __device__ __forceinline__ OutT saturate(uint32_t v)
@@ -34,6 +43,7 @@ struct WorkList {
     float4 *a, *b;           // Item fields {s, c, r2, eD}, {E1, E2, Qa, Qb}
     int *meta;               // hit << 6 | needB << 5 | unsure << 4 | column-in-tile
     unsigned long long *hm;  // kModeHit: the hit's region set
+    unsigned char *lay;      // kModeLayers: the hit's layer
 };
 
 constexpr int kMetaUnsure = 16, kMetaNeedB = 32, kMetaCol = 15;
@@ -41,16 +51,18 @@ constexpr size_t kItemBytes = 36;
 
 __host__ __device__ constexpr size_t item_bytes(int mode)
 {
-    return kItemBytes + (mode == kModeHit ? 8 : 0);
+    return kItemBytes + (base_mode(mode) == kModeHit ? 8 : 0) + (layer_mode(mode) ? 1 : 0);
 }
 
-__device__ __forceinline__ WorkList carve_worklist(unsigned char *p, int cap)
+__device__ __forceinline__ WorkList carve_worklist(unsigned char *p, int cap,
+                                                   int mode = kModePlain)
 {
     WorkList w;
     w.a = reinterpret_cast<float4 *>(p);
     w.b = w.a + cap;
     w.meta = reinterpret_cast<int *>(w.b + cap);
     w.hm = reinterpret_cast<unsigned long long *>(w.meta + cap);   // cap is a multiple of 2
+    w.lay = reinterpret_cast<unsigned char *>(w.hm + (base_mode(mode) == kModeHit ? cap : 0));
     return w;
 }
 
@@ -163,8 +175,10 @@ template <int KT, int MODE = kModePlain>
 __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, float xh,
                                         float yh, int n, int h, int ha, int lane, int *q,
                                         const WorkList &W, const MaskCtx *M = nullptr,
-                                        const HitCtx *H = nullptr)
+                                        const HitCtx *H = nullptr,
+                                        const uint8_t *__restrict__ layer = nullptr)
 {
+    constexpr int BM = base_mode(MODE);
     float is_[KT], ic_[KT];
     int fl_[KT];
     unsigned sel = 0u;
@@ -172,7 +186,8 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
     unsigned long long hm = 0ull;
     float hwlo = 0.0f, hwhi = 0.0f;
     bool live = h < n;
-    if (MODE == kModeHit && live) {
+    const unsigned char lh = (layer_mode(MODE) && live) ? __ldg(layer + ha) : 0;
+    if (BM == kModeHit && live) {
         hm = H->masks[ha];
         unsigned tb = 0u;
         for (int b = H->rb_lo; b <= H->rb_hi; ++b) tb |= (unsigned)(hm >> (8 * b)) & 0xffu;
@@ -200,10 +215,10 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
                 f |= kMetaUnsure;
             } else if (c > 1.0f) {
                 float gmin, gmax;
-                if (MODE == kModeHit) {
+                if (BM == kModeHit) {
                     rho_range_w(hwlo + s, hwhi + s, c, gmin, gmax);
                     if (gmax < T.rho_lo || gmin > T.rho_hi) continue;
-                } else if (MODE == kModeEvent) {
+                } else if (BM == kModeEvent) {
                     bool reach = false;
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
@@ -255,7 +270,8 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
             W.a[pos] = make_float4(it.s, it.c, it.r2, it.eD);
             W.b[pos] = make_float4(it.E1, it.E2, it.Qa, it.Qb);
             W.meta[pos] = (h << 6) | fl_[kl] | kl;
-            if (MODE == kModeHit) W.hm[pos] = hm;
+            if (BM == kModeHit) W.hm[pos] = hm;
+            if (layer_mode(MODE)) W.lay[pos] = lh;
         }
     }
 }
@@ -406,29 +422,35 @@ __device__ __forceinline__ bool push_redo(const RedoQueue &Q, int *n, int hit, i
 // computation; with KT = 1 it holds bins 2w and 2w + 1.  Exact while no cell
 // can reach 65536 votes in the tile: a cell gets at most two votes per
 // scanned hit, so it is used only for tiles scanning at most kPackMaxHits.
-template <int KT, bool PACK>
+// LAY (the distinct-layer vote): the same words hold layer masks; a vote
+// ORs the hit's layer bit lbit (1 << layer) instead of adding one.
+template <int KT, bool PACK, bool LAY = false>
 struct TileCol {
     uint32_t *base;
     uint32_t inc;
 
-    __device__ __forceinline__ TileCol(uint32_t *cnt, int ND, int kl, int lane)
+    __device__ __forceinline__ TileCol(uint32_t *cnt, int ND, int kl, int lane,
+                                       uint32_t lbit = 1u)
     {
+        const uint32_t one = LAY ? lbit : 1u;
         if (PACK && KT > 1) {
             base = cnt + (kl >> 1) * ND * 32 + lane;
-            inc = 1u << ((kl & 1) << 4);
+            inc = one << ((kl & 1) << 4);
         } else if (PACK) {
             base = cnt + lane;
-            inc = 0u;
+            inc = one;
         } else {
             base = cnt + kl * ND * 32 + lane;
-            inc = 1u;
+            inc = one;
         }
     }
 
     __device__ __forceinline__ void add(int j) const
     {
-        if (PACK && KT == 1) atomicAdd(base + (j >> 1) * 32, 1u << ((j & 1) << 4));
-        else atomicAdd(base + j * 32, inc);
+        uint32_t *w = (PACK && KT == 1) ? base + (j >> 1) * 32 : base + j * 32;
+        const uint32_t v = (PACK && KT == 1) ? inc << ((j & 1) << 4) : inc;
+        if (LAY) atomicOr(w, v);
+        else atomicAdd(w, v);
     }
 };
 
@@ -463,15 +485,18 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                                           unsigned long long *__restrict__ stats, int tx, int ty,
                                           unsigned long long mask = ~0ull,
                                           const unsigned long long *__restrict__ hmask = nullptr,
-                                          const int *__restrict__ hl = nullptr, int nl = 0)
+                                          const int *__restrict__ hl = nullptr, int nl = 0,
+                                          const uint8_t *__restrict__ layer = nullptr)
 {
+    constexpr int BM = base_mode(MODE);
+    constexpr bool LAY = layer_mode(MODE);
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
     const int NW = PACK ? (ND >> 1) : ND;                  // words per column-row
     constexpr int QCAP = kThreads * KT;
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][NW][32]
     unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * NW * 32);
-    const WorkList W = carve_worklist(p, QCAP);
+    const WorkList W = carve_worklist(p, QCAP, MODE);
     const RedoQueue R = carve_redo(p + (size_t)QCAP * item_bytes(MODE));
     __shared__ int qn[2][2], rn;   // [parity][plain, others]
     __shared__ unsigned long long s_stats[2];
@@ -481,12 +506,12 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     TileCtx<KT> T;
     T.init(G, lane, tx, ty);
     MaskCtx M;
-    if (MODE == kModeEvent) {
+    if (BM == kModeEvent) {
         M.init(G, mask, T.i0, T.irow, T.row_ok);
         if (M.tile_bm == 0u) return;   // uniform: every warp sees the same rows
     }
     HitCtx H;
-    if (MODE == kModeHit) {
+    if (BM == kModeHit) {
         const int NR = G.n_rho;
         uint8_t *jm = p + (size_t)QCAP * item_bytes(MODE) + kRedoBytes;
         for (int j = threadIdx.x; j < ND; j += kThreads)
@@ -514,6 +539,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     __syncthreads();
 
     int my_fb = 0;
+    unsigned long long my_cast = 0;   // LAY: votes cast (cell sums are layer counts)
     int parity = 0;
     const HitSeq S{hl, hl ? nl : n};
     HitPrefetch pf;
@@ -523,7 +549,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         float xh, yh;
         pf.next(x, y, S, base, ha, xh, yh);
         collect<KT, MODE>(G, T, xh, yh, S.n, base + threadIdx.x, ha, lane, qn[parity], W, &M,
-                          &H);
+                          &H, layer);
         __syncthreads();
         const int nf = qn[parity][0], ns = qn[parity][1];
         if (threadIdx.x == 0) {   // last read before the previous barrier
@@ -535,11 +561,14 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 #pragma unroll 2
             for (int t = warp; t < nf; t += nwarps) {
                 const int m = W.meta[t];
-                const TileCol<KT, PACK> col(cnt, ND, m & kMetaCol, lane);
+                const TileCol<KT, PACK, LAY> col(cnt, ND, m & kMetaCol, lane,
+                                                 LAY ? 1u << W.lay[t] : 1u);
                 int j;
                 const int r = fast_bin32<KT>(G, T, W, t, j);
-                if (r == kFastVote && (MODE != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j])))
+                if (r == kFastVote && (BM != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j]))) {
                     col.add(j);
+                    if (LAY) ++my_cast;
+                }
                 // the usual case: no lane needs a redo (lanes of rows past n_rho
                 // do not run this loop, hence the active mask)
                 if (!__any_sync(__activemask(), r == kFastRedo)) continue;
@@ -549,14 +578,16 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                     if (push_redo(R, &rn, hh, lane, m & kMetaCol)) continue;
                     int jj[2];
                     int nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
-                    if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
+                    if (BM == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
                     for (int v = 0; v < nv; ++v) col.add(jj[v]);
+                    if (LAY) my_cast += nv;
                 }
             }
             // unsure items and items whose second root can reach the axis
             for (int t = kThreads * KT - ns + warp; t < kThreads * KT; t += nwarps) {
                 const int m = W.meta[t];
-                const TileCol<KT, PACK> col(cnt, ND, m & kMetaCol, lane);
+                const TileCol<KT, PACK, LAY> col(cnt, ND, m & kMetaCol, lane,
+                                                 LAY ? 1u << W.lay[t] : 1u);
                 int jj[2];
                 int nv = item_bins32<KT>(G, T, W, t, m, jj);
                 if (nv < 0) {
@@ -565,9 +596,10 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                     if (push_redo(R, &rn, hh, lane, m & kMetaCol)) continue;
                     nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
                 }
-                if (MODE == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
+                if (BM == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
                 if (nv > 0) col.add(jj[0]);
                 if (nv > 1) col.add(jj[1]);
+                if (LAY) my_cast += nv;
             }
         }
         __syncthreads();
@@ -579,11 +611,12 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                 const int il = rc >> 4, kl = rc & 15;
                 int jj[2];
                 int nv = redo_bins(G, x[h], y[h], T.i0 + il, T.k0 + kl, jj);
-                if (MODE == kModeHit)
+                if (BM == kModeHit)
                     nv = keep_allowed(halo_row_blocks(H.masks[h], T.i0 + il, G.n_rho), H.jmask, nv,
                                       jj);
-                const TileCol<KT, PACK> col(cnt, ND, kl, il);
+                const TileCol<KT, PACK, LAY> col(cnt, ND, kl, il, LAY ? 1u << __ldg(layer + h) : 1u);
                 for (int v = 0; v < nv; ++v) col.add(jj[v]);
+                if (LAY) my_cast += nv;
             }
             __syncthreads();
             if (threadIdx.x == 0) rn = 0;
@@ -599,12 +632,13 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         const int il = t & 31, j = t >> 5;   // il == lane
         const int i = T.i0 + il;
         if (i >= G.n_rho) continue;
-        const bool keep = MODE != kModeEvent || halo_bin(M.bm, j, ND);
+        const bool keep = BM != kModeEvent || halo_bin(M.bm, j, ND);
         __align__(16) OutT e[KT];
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
-            const uint32_t v = keep ? tile_get<KT, PACK>(cnt, ND, kl, j, il) : 0u;
-            my_votes += v;
+            uint32_t v = keep ? tile_get<KT, PACK>(cnt, ND, kl, j, il) : 0u;
+            if (LAY) v = (uint32_t)__popc(v);
+            else my_votes += v;
             e[kl] = saturate<OutT>(v);
         }
         OutT *dst = acc + ((size_t)i * ND + j) * G.n_phi0 + T.k0;
@@ -620,6 +654,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         }
     }
 
+    if (LAY) my_votes = my_cast;
     if (stats) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
@@ -635,15 +670,17 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     }
 }
 
-// mask: kModeEvent one device uint64, kModeHit one per hit, else unused.
+// mask: kModeEvent one device uint64, kModeHit one per hit, else unused;
+// layer: one uint8 per hit under kModeLayers, else unused.
 template <int KT, typename OutT, bool PACK, int MODE>
 __global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
 k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
        OutT *__restrict__ acc, unsigned long long *__restrict__ stats,
-       const unsigned long long *__restrict__ mask)
+       const unsigned long long *__restrict__ mask, const uint8_t *__restrict__ layer)
 {
     vote_tile<KT, OutT, PACK, MODE>(G, x, y, n, acc, stats, blockIdx.x, blockIdx.y,
-                                    MODE == kModeEvent ? *mask : ~0ull, mask);
+                                    base_mode(MODE) == kModeEvent ? *mask : ~0ull, mask,
+                                    nullptr, 0, layer);
 }
 
 // Persistent vote over a batch: CTAs pop (event, tile) items from a device
@@ -660,8 +697,9 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
              const int *__restrict__ d_nev,
              OutT *__restrict__ acc, size_t acc_stride, unsigned long long *__restrict__ stats,
              int *__restrict__ head, const unsigned long long *__restrict__ masks,
-             BucketView bk)
+             BucketView bk, const uint8_t *__restrict__ layer)
 {
+    constexpr int BM = base_mode(MODE);
     __shared__ int s_item;
     const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 31) / 32, ntiles = ntx * nty;
     const int total = *d_nev * ntiles;
@@ -679,12 +717,14 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
         // hits (a cell then holds at most 2 kPackMaxHits < 2^16 votes, so no
         // count carries into its neighbour), unpacked counters the others:
         // the two launches of a batch split every event's tiles between them
-        // by the scanned list's length (uniform over the CTA).
-        if (PACK == ((bk.ent ? nl : n) <= kPackMaxHits))
+        // by the scanned list's length (uniform over the CTA).  Layer masks
+        // never carry, so the distinct-layer vote packs every tile.
+        if (layer_mode(MODE) ? PACK : (PACK == ((bk.ent ? nl : n) <= kPackMaxHits)))
             vote_tile<KT, OutT, PACK, MODE>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
                                             stats ? stats + 2 * e : nullptr, t % ntx, t / ntx,
-                                            MODE == kModeEvent ? masks[e] : ~0ull,
-                                            MODE == kModeHit ? masks + a : nullptr, hl, nl);
+                                            BM == kModeEvent ? masks[e] : ~0ull,
+                                            BM == kModeHit ? masks + a : nullptr, hl, nl,
+                                            layer_mode(MODE) ? layer + a : nullptr);
         __syncthreads();
     }
 }
@@ -694,7 +734,7 @@ size_t vote_smem(const DevGeom &G, bool pack, int mode = kModePlain)
 {
     return (size_t)KT * 32 * (pack ? G.n_d0 / 2 : G.n_d0) * 4 +
            (size_t)kThreads * KT * item_bytes(mode) + kRedoBytes +
-           (mode == kModeHit ? ((size_t)G.n_d0 + 15) / 16 * 16 : 0);
+           (base_mode(mode) == kModeHit ? ((size_t)G.n_d0 + 15) / 16 * 16 : 0);
 }
 
 constexpr size_t kSmemBudget2 = 110 * 1024;   // two CTAs per SM
@@ -703,37 +743,50 @@ constexpr size_t kSmemBudget3 = 75 * 1024;    // three CTAs per SM
 template <int KT, typename OutT, bool PACK, int MODE>
 cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                            unsigned long long *stats, const unsigned long long *mask,
-                           cudaStream_t st)
+                           cudaStream_t st, const uint8_t *layer)
 {
     dim3 grid(G.n_phi0 / KT, (G.n_rho + 31) / 32);
     k_vote<KT, OutT, PACK, MODE><<<grid, kThreads, vote_smem<KT>(G, PACK, MODE), st>>>(
-        G, x, y, n, reinterpret_cast<OutT *>(acc), stats, mask);
+        G, x, y, n, reinterpret_cast<OutT *>(acc), stats, mask, layer);
     return cudaGetLastError();
 }
 
 // Tile shape: packed 16-bit counters with three CTAs per SM when the output
 // is uint16, n_d0 even and n <= 32767; otherwise 32-bit counters, two CTAs
-// per SM.  KT is the widest tile that fits.
+// per SM.  KT is the widest tile that fits.  The distinct-layer vote
+// (kModeLayers; n_d0 even) always packs, into either output type.
 template <int MODE>
 cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                           unsigned long long *stats, const unsigned long long *mask,
-                          cudaStream_t st)
+                          cudaStream_t st, const uint8_t *layer = nullptr)
 {
-#define HT_V(KTV, OT, PK) return launch_vote_kt<KTV, OT, PK, MODE>(G, x, y, n, acc, stats, mask, st)
-    if (G.count_bits == 16) {
-        if (n <= 32767 && G.n_d0 % 2 == 0) {
+#define HT_V(KTV, OT, PK)                                                                     \
+    return launch_vote_kt<KTV, OT, PK, MODE>(G, x, y, n, acc, stats, mask, st, layer)
+    if constexpr (layer_mode(MODE)) {
+        if (G.count_bits == 16) {
             if (vote_smem<4>(G, true, MODE) <= kSmemBudget3) HT_V(4, uint16_t, true);
             if (vote_smem<2>(G, true, MODE) <= kSmemBudget3) HT_V(2, uint16_t, true);
-            if (vote_smem<1>(G, true, MODE) <= kSmemBudget3) HT_V(1, uint16_t, true);
+            HT_V(1, uint16_t, true);
         }
-        if (vote_smem<8>(G, false, MODE) <= kSmemBudget2) HT_V(8, uint16_t, false);
-        if (vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_V(4, uint16_t, false);
-        if (vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_V(2, uint16_t, false);
-        HT_V(1, uint16_t, false);
+        if (vote_smem<4>(G, true, MODE) <= kSmemBudget3) HT_V(4, int32_t, true);
+        if (vote_smem<2>(G, true, MODE) <= kSmemBudget3) HT_V(2, int32_t, true);
+        HT_V(1, int32_t, true);
+    } else {
+        if (G.count_bits == 16) {
+            if (n <= 32767 && G.n_d0 % 2 == 0) {
+                if (vote_smem<4>(G, true, MODE) <= kSmemBudget3) HT_V(4, uint16_t, true);
+                if (vote_smem<2>(G, true, MODE) <= kSmemBudget3) HT_V(2, uint16_t, true);
+                if (vote_smem<1>(G, true, MODE) <= kSmemBudget3) HT_V(1, uint16_t, true);
+            }
+            if (vote_smem<8>(G, false, MODE) <= kSmemBudget2) HT_V(8, uint16_t, false);
+            if (vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_V(4, uint16_t, false);
+            if (vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_V(2, uint16_t, false);
+            HT_V(1, uint16_t, false);
+        }
+        if (vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_V(4, int32_t, false);
+        if (vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_V(2, int32_t, false);
+        HT_V(1, int32_t, false);
     }
-    if (vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_V(4, int32_t, false);
-    if (vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_V(2, int32_t, false);
-    HT_V(1, int32_t, false);
 #undef HT_V
 }
 
@@ -742,14 +795,16 @@ cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int 
 // kt selects the tile width (0 = default).  pack: this launch takes the
 // listed events' tiles that scan at most kPackMaxHits hits (a column group's
 // hit list with buckets, else the event) with 16-bit packed counters;
-// otherwise it takes their other tiles with 32-bit counters.  *head must be
-// zero.
+// otherwise it takes their other tiles with 32-bit counters.  The
+// distinct-layer vote takes every tile in its packed launch (layer: the
+// batch's layer array, indexed like x).  *head must be zero.
 template <int MODE>
 cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y, const int *off,
                                 const int *order, const int *d_nev, uint16_t *acc,
                                 size_t acc_stride, unsigned long long *stats, int *head,
                                 bool pack, int kt, int sms, const unsigned long long *masks,
-                                cudaStream_t st, BucketView bk = BucketView{})
+                                cudaStream_t st, BucketView bk = BucketView{},
+                                const uint8_t *layer = nullptr)
 {
 #define HT_VB(KTV, PK)                                                                        \
     do {                                                                                      \
@@ -759,26 +814,35 @@ cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y
             vote_smem<KTV>(G, PK, MODE));                                                     \
         k_vote_batch<KTV, uint16_t, PK, MODE><<<sms * (occ > 0 ? occ : 1), kThreads,         \
                                                 vote_smem<KTV>(G, PK, MODE), st>>>(           \
-            G, x, y, off, order, d_nev, acc, acc_stride, stats, head, masks, bk);             \
+            G, x, y, off, order, d_nev, acc, acc_stride, stats, head, masks, bk, layer);      \
         return cudaGetLastError();                                                            \
     } while (0)
-    if (pack) {
-        // the per-hit mode's larger items would drop a tuned width to two
-        // CTAs per SM: it keeps three
-        const size_t budget = MODE == kModeHit ? kSmemBudget3 : kSmemBudget2;
+    // the per-hit mode's larger items would drop a tuned width to two CTAs
+    // per SM: it keeps three
+    const size_t budget = base_mode(MODE) == kModeHit ? kSmemBudget3 : kSmemBudget2;
+    if constexpr (layer_mode(MODE)) {
+        if (!pack) return cudaSuccess;   // no unpacked tiles
         if (kt == 0) kt = vote_smem<4>(G, true, MODE) <= kSmemBudget3 ? 4
                         : vote_smem<2>(G, true, MODE) <= kSmemBudget3 ? 2 : 1;
         if (kt == 4 && vote_smem<4>(G, true, MODE) <= budget) HT_VB(4, true);
         if (kt >= 2 && vote_smem<2>(G, true, MODE) <= budget) HT_VB(2, true);
         HT_VB(1, true);
+    } else {
+        if (pack) {
+            if (kt == 0) kt = vote_smem<4>(G, true, MODE) <= kSmemBudget3 ? 4
+                            : vote_smem<2>(G, true, MODE) <= kSmemBudget3 ? 2 : 1;
+            if (kt == 4 && vote_smem<4>(G, true, MODE) <= budget) HT_VB(4, true);
+            if (kt >= 2 && vote_smem<2>(G, true, MODE) <= budget) HT_VB(2, true);
+            HT_VB(1, true);
+        }
+        if (kt == 0) kt = vote_smem<8>(G, false, MODE) <= kSmemBudget2 ? 8
+                        : vote_smem<4>(G, false, MODE) <= kSmemBudget2 ? 4
+                        : vote_smem<2>(G, false, MODE) <= kSmemBudget2 ? 2 : 1;
+        if (kt == 8 && vote_smem<8>(G, false, MODE) <= kSmemBudget2) HT_VB(8, false);
+        if (kt >= 4 && vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_VB(4, false);
+        if (kt >= 2 && vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_VB(2, false);
+        HT_VB(1, false);
     }
-    if (kt == 0) kt = vote_smem<8>(G, false, MODE) <= kSmemBudget2 ? 8
-                    : vote_smem<4>(G, false, MODE) <= kSmemBudget2 ? 4
-                    : vote_smem<2>(G, false, MODE) <= kSmemBudget2 ? 2 : 1;
-    if (kt == 8 && vote_smem<8>(G, false, MODE) <= kSmemBudget2) HT_VB(8, false);
-    if (kt >= 4 && vote_smem<4>(G, false, MODE) <= kSmemBudget2) HT_VB(4, false);
-    if (kt >= 2 && vote_smem<2>(G, false, MODE) <= kSmemBudget2) HT_VB(2, false);
-    HT_VB(1, false);
 #undef HT_VB
 }
 
@@ -800,25 +864,39 @@ inline cudaError_t allow_smem(const void *const *fns, int nf, int max_smem)
 template <int MODE>
 cudaError_t prepare_vote_kernels_t(int max_smem)
 {
-    const void *fns[] = {
-        (const void *)k_vote<4, uint16_t, true, MODE>,
-        (const void *)k_vote<2, uint16_t, true, MODE>,
-        (const void *)k_vote<1, uint16_t, true, MODE>,
-        (const void *)k_vote<8, uint16_t, false, MODE>,
-        (const void *)k_vote<4, uint16_t, false, MODE>,
-        (const void *)k_vote<2, uint16_t, false, MODE>,
-        (const void *)k_vote<1, uint16_t, false, MODE>,
-        (const void *)k_vote<4, int32_t, false, MODE>,
-        (const void *)k_vote<2, int32_t, false, MODE>,
-        (const void *)k_vote<1, int32_t, false, MODE>,
-        (const void *)k_vote_batch<4, uint16_t, true, MODE>,
-        (const void *)k_vote_batch<2, uint16_t, true, MODE>,
-        (const void *)k_vote_batch<1, uint16_t, true, MODE>,
-        (const void *)k_vote_batch<8, uint16_t, false, MODE>,
-        (const void *)k_vote_batch<4, uint16_t, false, MODE>,
-        (const void *)k_vote_batch<2, uint16_t, false, MODE>,
-        (const void *)k_vote_batch<1, uint16_t, false, MODE>};
-    return allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
+    if constexpr (layer_mode(MODE)) {
+        const void *fns[] = {
+            (const void *)k_vote<4, uint16_t, true, MODE>,
+            (const void *)k_vote<2, uint16_t, true, MODE>,
+            (const void *)k_vote<1, uint16_t, true, MODE>,
+            (const void *)k_vote<4, int32_t, true, MODE>,
+            (const void *)k_vote<2, int32_t, true, MODE>,
+            (const void *)k_vote<1, int32_t, true, MODE>,
+            (const void *)k_vote_batch<4, uint16_t, true, MODE>,
+            (const void *)k_vote_batch<2, uint16_t, true, MODE>,
+            (const void *)k_vote_batch<1, uint16_t, true, MODE>};
+        return allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
+    } else {
+        const void *fns[] = {
+            (const void *)k_vote<4, uint16_t, true, MODE>,
+            (const void *)k_vote<2, uint16_t, true, MODE>,
+            (const void *)k_vote<1, uint16_t, true, MODE>,
+            (const void *)k_vote<8, uint16_t, false, MODE>,
+            (const void *)k_vote<4, uint16_t, false, MODE>,
+            (const void *)k_vote<2, uint16_t, false, MODE>,
+            (const void *)k_vote<1, uint16_t, false, MODE>,
+            (const void *)k_vote<4, int32_t, false, MODE>,
+            (const void *)k_vote<2, int32_t, false, MODE>,
+            (const void *)k_vote<1, int32_t, false, MODE>,
+            (const void *)k_vote_batch<4, uint16_t, true, MODE>,
+            (const void *)k_vote_batch<2, uint16_t, true, MODE>,
+            (const void *)k_vote_batch<1, uint16_t, true, MODE>,
+            (const void *)k_vote_batch<8, uint16_t, false, MODE>,
+            (const void *)k_vote_batch<4, uint16_t, false, MODE>,
+            (const void *)k_vote_batch<2, uint16_t, false, MODE>,
+            (const void *)k_vote_batch<1, uint16_t, false, MODE>};
+        return allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
+    }
 }
 
 }  // namespace

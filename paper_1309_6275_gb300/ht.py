@@ -59,6 +59,26 @@ class _HitProposal(ctypes.Structure):
                 ("topk", ctypes.c_int32), ("pmin", ctypes.c_float)]
 
 
+class _ConfirmDesc(ctypes.Structure):
+    _fields_ = [("pool", ctypes.c_int32), ("min_layers", ctypes.c_int32),
+                ("n_layers", ctypes.c_int32), ("n_bands", ctypes.c_int32),
+                ("tol", ctypes.c_double), ("band_max_hits", ctypes.c_int32 * 8),
+                ("band_threshold", ctypes.c_int32 * 8)]
+
+
+def confirm_desc(c):
+    """ht_confirm_desc from a dict {pool, min_layers, n_layers, tol, bands}
+    (bands: [(max_hits, threshold), ...] in increasing max_hits)."""
+    bands = list(c.get("bands", ()))
+    assert len(bands) <= 8
+    d = _ConfirmDesc(int(c["pool"]), int(c["min_layers"]), int(c["n_layers"]), len(bands),
+                     float(c["tol"]))
+    for q, (mh, t) in enumerate(bands):
+        d.band_max_hits[q] = int(mh)
+        d.band_threshold[q] = int(t)
+    return d
+
+
 # (name, restype, argtypes) of every exported function, as in include/ht.h
 _P, _I32, _SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_size_t
 SIGNATURES = [
@@ -116,6 +136,13 @@ SIGNATURES = [
     ("ht_vertex_workspace_size", _SZ, [_P]),
     ("ht_vertex_vote", _I32, [_P, _P, _P, _I32, _I32, _P, _P, _P]),
     ("ht_vertex_find", _I32, [_P, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
+    ("ht_vote_layers", _I32, [_P, _P, _P, _P, _I32, _P, _P, _P]),
+    ("ht_confirm_workspace_size", _SZ, [_P, _I32]),
+    ("ht_confirm", _I32, [_P, ctypes.POINTER(_ConfirmDesc), _P, _P, _P, _I32, _P, _P, _I32,
+                          _P, _P, _P, _P, _SZ, _P]),
+    ("ht_batch_set_confirm", _I32, [_P, ctypes.POINTER(_ConfirmDesc)]),
+    ("ht_batch_run_tracks", _I32, [_P, _P, _P, _P, _P, _P, _I32, ctypes.POINTER(_HitProposal),
+                                   _P, _P, _P, _P, _P, _P, _P, _P]),
 ]
 
 
@@ -206,6 +233,27 @@ def ht_vote(g, x, y, acc, stats=None, stream=None):
     n = x.numel()
     _check(lib().ht_vote(g.handle, _ptr(x), _ptr(y), n, _ptr(acc), _ptr(stats),
                          _stream(stream)), "ht_vote")
+
+
+def ht_vote_layers(g, x, y, layer, acc, stats=None, stream=None):
+    """Distinct-layer vote: a cell counts the layers of the hits voting in it."""
+    _check(lib().ht_vote_layers(g.handle, _ptr(x), _ptr(y), _ptr(layer), x.numel(), _ptr(acc),
+                                _ptr(stats), _stream(stream)), "ht_vote_layers")
+
+
+def ht_confirm_workspace_size(g, n_hits):
+    return lib().ht_confirm_workspace_size(g.handle, n_hits)
+
+
+def ht_confirm(g, c, x, y, layer, peaks, d_count, cap, score, inliers, assign, workspace,
+               stream=None):
+    """Confirmation of the candidates and the final assignment (c: a dict
+    for confirm_desc); score int32 [cap], inliers int32 [cap, 16]."""
+    d = confirm_desc(c)
+    _check(lib().ht_confirm(g.handle, ctypes.byref(d), _ptr(x), _ptr(y), _ptr(layer),
+                            x.numel(), _ptr(peaks), _ptr(d_count), cap, _ptr(score),
+                            _ptr(inliers), _ptr(assign), _ptr(workspace), workspace.numel(),
+                            _stream(stream)), "ht_confirm")
 
 
 def ht_find_peaks(g, acc, peaks, cap, d_count, workspace, stream=None):
@@ -540,9 +588,41 @@ class Batch:
                                                _ptr(self.zres), _ptr(self.stats),
                                                _stream(stream)), "ht_batch_run_learned_hits")
 
+    def set_confirm(self, c):
+        """Switch on the track path with confirmation parameters c (a dict
+        for confirm_desc); allocates the per-candidate score output."""
+        self._conf = confirm_desc(c)
+        _check(lib().ht_batch_set_confirm(self.handle, ctypes.byref(self._conf)),
+               "ht_batch_set_confirm")
+        if getattr(self, "score", None) is None:
+            self.score = torch.zeros(self.max_events * self.cap, dtype=torch.int32,
+                                     device=self.peaks.device)
+
+    def run_tracks(self, x, y, z, layer, offsets, params_bf16=None, hit_masks=None, topk=8,
+                   pmin=0.0, stream=None):
+        """The track path (ht_batch_run_tracks): distinct-layer vote, peaks at
+        each event's band threshold, confirmation, z vote.  With params_bf16
+        the proposal's per-hit top-k sets restrict the vote (written to
+        hit_masks, device int64 [total hits]); with hit_masks alone, the given
+        sets do."""
+        off, p = self._offsets(offsets)
+        self._keep = off
+        prop = None
+        if params_bf16 is not None:
+            assert hit_masks is not None
+            self._hprop = _HitProposal(params_bf16.data_ptr(), layer.data_ptr(), int(topk),
+                                       float(pmin))
+            prop = ctypes.byref(self._hprop)
+        _check(lib().ht_batch_run_tracks(self.handle, _ptr(x), _ptr(y), _ptr(z), _ptr(layer), p,
+                                         off.shape[0] - 1, prop, _ptr(hit_masks),
+                                         _ptr(self.peaks), _ptr(self.counts), _ptr(self.score),
+                                         _ptr(self.assign), _ptr(self.zres), _ptr(self.stats),
+                                         _stream(stream)), "ht_batch_run_tracks")
+
     def stage_ms(self):
-        """[proposal, vote, peaks + candidate lists, association, decode + z
-        vote] ms of the last completed run (synchronise first)."""
+        """[proposal, vote, peaks + candidate lists, association (track path:
+        confirmation and assignment), decode + z vote] ms of the last
+        completed run (synchronise first)."""
         arr = (ctypes.c_float * 5)()
         _check(lib().ht_batch_stage_ms(self.handle, ctypes.cast(arr, ctypes.c_void_p)),
                "ht_batch_stage_ms")
@@ -564,7 +644,10 @@ class Batch:
         k = min(cnt, self.cap)
         a, b = int(offsets[e]), int(offsets[e + 1])
         base = e * self.cap
-        return dict(count=cnt, peaks=self.peaks[base:base + k].cpu().numpy(),
-                    zres=self.zres[base:base + k].cpu().numpy(),
-                    assign=self.assign[a:b].cpu().numpy(),
-                    votes=int(self.stats[2 * e].item()))
+        r = dict(count=cnt, peaks=self.peaks[base:base + k].cpu().numpy(),
+                 zres=self.zres[base:base + k].cpu().numpy(),
+                 assign=self.assign[a:b].cpu().numpy(),
+                 votes=int(self.stats[2 * e].item()))
+        if getattr(self, "score", None) is not None:
+            r["score"] = self.score[base:base + k].cpu().numpy()
+        return r
