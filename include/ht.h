@@ -284,9 +284,9 @@ typedef struct ht_confirm_desc {
  *   inliers   16 cap int32 (device): inliers[16 m + l] = the inlier hit of
  *             layer l, -1 for none (all -1 when not confirmed).
  *   assign    n_hits int32 (device).
- *   workspace ht_confirm_workspace_size(g, n_hits) bytes, 256-byte aligned.
+ *   workspace ht_confirm_workspace_size(g, n_hits, cap) bytes, 256-byte aligned.
  * Errors: HT_ERR_ARG (null pointers, parameters out of range), HT_ERR_CUDA. */
-size_t ht_confirm_workspace_size(const ht_geometry *g, int32_t n_hits);
+size_t ht_confirm_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap);
 ht_status ht_confirm(const ht_geometry *g, const ht_confirm_desc *c, const float *x,
                      const float *y, const uint8_t *layer, int32_t n_hits, const ht_peak *peaks,
                      const int32_t *d_count, int32_t cap, int32_t *score, int32_t *inliers,

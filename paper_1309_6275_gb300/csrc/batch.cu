@@ -602,7 +602,7 @@ ht_status ht_batch_set_confirm(ht_batch *b, const ht_confirm_desc *c)
         cudaError_t e = cudaMalloc((void **)&b->inl, (size_t)b->max_events * b->cap * 16 * 4);
         if (e == cudaSuccess)
             e = cudaMalloc((void **)&b->cf_ws,
-                           ht::confirm_workspace_bytes(b->max_events, b->max_hits));
+                           ht::confirm_workspace_bytes(b->g->G, b->max_events, b->max_hits, b->cap));
         if (e != cudaSuccess) {
             cudaFree(b->inl);
             b->inl = nullptr;

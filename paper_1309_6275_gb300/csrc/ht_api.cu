@@ -205,6 +205,7 @@ ht_status ht_geometry_create(const ht_geometry_desc *d, ht_geometry **out)
     if (e == cudaSuccess) e = ht::prepare_z_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_masked_vote_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_layer_vote_kernels(max_smem);
+    if (e == cudaSuccess) e = ht::prepare_confirm_kernels();
     if (e == cudaSuccess) e = ht::prepare_swept_kernels(max_smem);
     if (e == cudaSuccess) e = ht::prepare_peaks_kernels();
     if (e == cudaSuccess) e = ht::prepare_mlp_kernels();
@@ -329,10 +330,10 @@ ht_status ht_vote_layers(const ht_geometry *g, const float *x, const float *y,
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_vote_layers");
 }
 
-size_t ht_confirm_workspace_size(const ht_geometry *g, int32_t n_hits)
+size_t ht_confirm_workspace_size(const ht_geometry *g, int32_t n_hits, int32_t cap)
 {
-    (void)g;
-    return ht::confirm_workspace_bytes_single(n_hits > 0 ? n_hits : 0);
+    if (!g) return 0;
+    return ht::confirm_workspace_bytes_single(g->G, n_hits > 0 ? n_hits : 0, cap > 0 ? cap : 0);
 }
 
 ht_status ht_confirm(const ht_geometry *g, const ht_confirm_desc *c, const float *x,
@@ -349,7 +350,8 @@ ht_status ht_confirm(const ht_geometry *g, const ht_confirm_desc *c, const float
     if (c->pool < 0 || c->min_layers < 1 || c->n_layers < 1 || c->n_layers > 16 ||
         !(c->tol > 0.0))
         return fail(HT_ERR_ARG, "ht_confirm: parameters out of range");
-    if (workspace_bytes < ht::confirm_workspace_bytes_single(n_hits) || !aligned(workspace, 256))
+    if (workspace_bytes < ht::confirm_workspace_bytes_single(g->G, n_hits, cap) ||
+        !aligned(workspace, 256))
         return fail(HT_ERR_ARG, "ht_confirm: workspace too small or misaligned");
     const ht::ConfirmDev P{c->pool, c->min_layers, c->n_layers, c->tol};
     cudaError_t e = ht::launch_confirm(g->G, P, x, y, layer, n_hits, peaks, d_count, cap, score,

@@ -385,6 +385,27 @@ size_t vote_z_workspace_bytes(const DevGeom &G, int n, int cap);
 
 constexpr size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Per-event hit index by (layer, azimuth bin) (k_hitindex.cu): cell
+// (e * 16 + l) * kIdxAz + b holds positions offs[cell] .. offs[cell + 1) of
+// x, y (float32), h (event-local hit index) and l (layer); rmm[2 (e 16 + l)]
+// and [+ 1] are the float bits of the least and largest hit radius of the
+// layer (min > max: no hit).
+constexpr int kIdxAz = 256;
+struct HitIndex {
+    int *cnt, *offs, *cur;
+    unsigned *rmm;
+    float *x, *y;
+    int *h;
+    uint8_t *l;
+    void *tmp;
+    int ncells;
+};
+size_t hit_index_bytes(int max_events, int max_hits);
+HitIndex carve_hit_index(int max_events, int max_hits, void *ws);
+cudaError_t launch_hit_index(const float *x, const float *y, const uint8_t *layer,
+                             const int *off, const int *d_nev, int max_events, int max_hits,
+                             const HitIndex &I, int sms, cudaStream_t st);
+
 // Candidate confirmation (k_confirm.cu): parameters as ht_confirm_desc.
 struct ConfirmDev {
     int pool, min_layers, n_layers;
@@ -393,7 +414,8 @@ struct ConfirmDev {
 // Batch: event e's hits at x[off[e] ..), candidates peaks[e cap ..), kept
 // counts min(counts[e], cap); score (n_ev cap), inl (16 n_ev cap) and
 // assign (batch hit index) written.  ws: confirm_workspace_bytes.
-size_t confirm_workspace_bytes(int max_events, int max_hits);
+size_t confirm_workspace_bytes(const DevGeom &G, int max_events, int max_hits, int cap);
+cudaError_t prepare_confirm_kernels();
 cudaError_t launch_confirm_batch(const DevGeom &G, const ConfirmDev &P, const float *x,
                                  const float *y, const uint8_t *layer, const int *off,
                                  const int *d_nev, int max_events, int max_hits,
@@ -401,7 +423,7 @@ cudaError_t launch_confirm_batch(const DevGeom &G, const ConfirmDev &P, const fl
                                  int *inl, int *assign, void *ws, int sms, cudaStream_t st,
                                  const HitBuckets *hb);
 // One event of n hits (host) and *d_count candidates (device).
-size_t confirm_workspace_bytes_single(int n);
+size_t confirm_workspace_bytes_single(const DevGeom &G, int n, int cap);
 cudaError_t launch_confirm(const DevGeom &G, const ConfirmDev &P, const float *x, const float *y,
                            const uint8_t *layer, int n, const ht_peak *peaks, const int *d_count,
                            int cap, int *score, int *inl, int *assign, void *ws, cudaStream_t st);

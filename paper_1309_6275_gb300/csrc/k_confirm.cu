@@ -32,28 +32,47 @@ namespace ht {
 
 namespace {
 
-// The bins of hit (xf, yf) in column (rho_i, phi0_k), exactly as the vote
-// casts them; returns their number (0 to 2) and writes them to j[].
-__device__ __forceinline__ int column_bins(const DevGeom &G, float xf, float yf, int i, int k,
-                                           int j[2])
+// Per-candidate constants of its column (rho_i, phi0_k) for column_bins.
+struct ColumnCtx {
+    int i, k;
+    float sk, ck, rho, invrho, invrho_es, rt;
+    bool has_b;
+
+    __device__ __forceinline__ void init(const DevGeom &G, int i_, int k_)
+    {
+        i = i_;
+        k = k_;
+        sk = G.sn32[k];
+        ck = G.cs32[k];
+        rho = G.rho32[i];
+        invrho = G.invrho32[i];
+        invrho_es = fabsf(invrho) * G.err_scale;
+        rt = fabsf(rho) * 1.0001f;
+        has_b = G.rho64[i] != 0.0;
+    }
+};
+
+// The bins of hit (xf, yf) in the candidate's column, exactly as the vote
+// casts them (guarded float32, then the vote's double-float and float64
+// tiers for what float32 cannot prove); returns their number (0 to 2) and
+// writes them to j[].
+__device__ __forceinline__ int column_bins(const DevGeom &G, const ColumnCtx &C, float xf,
+                                           float yf, int j[2])
 {
-    const float sk = G.sn32[k], ck = G.cs32[k];
-    const float c = fmaf(xf, ck, yf * sk);
+    const float c = fmaf(xf, C.ck, yf * C.sk);
     const float R1 = fabsf(xf) + fabsf(yf);
     const float Ec = (kSafe * 3.0f * kEps) * R1;
     if (c < -Ec) return 0;   // c <= 0 proven: the hit is not on a first half turn here
-    int edge = 0;
-    if (c <= Ec) return cell_bins64(G, xf, yf, i, k, j, &edge);
-    const float s = fmaf(xf, sk, -(yf * ck));
+    if (c <= Ec) return redo_bins(G, xf, yf, C.i, C.k, j);
+    const float s = fmaf(xf, C.sk, -(yf * C.ck));
     const float r2 = fmaf(xf, xf, yf * yf);
-    const float rho = G.rho32[i], invrho = G.invrho32[i];
-    const Item it = make_item(G, s, c, r2, R1, fabsf(rho) * 1.0001f);
+    const Item it = make_item(G, s, c, r2, R1, C.rt);
     int jA, jB, r;
-    if (G.rho64[i] != 0.0)
-        r = eval32<true>(G, rho, fabsf(invrho) * G.err_scale, invrho, it, jA, jB);
+    if (C.has_b)
+        r = eval32<true>(G, C.rho, C.invrho_es, C.invrho, it, jA, jB);
     else
-        r = eval32<false>(G, rho, 0.0f, invrho, it, jA, jB);
-    if (r == kRedo) return cell_bins64(G, xf, yf, i, k, j, &edge);
+        r = eval32<false>(G, C.rho, 0.0f, C.invrho, it, jA, jB);
+    if (r == kRedo) return redo_bins(G, xf, yf, C.i, C.k, j);
     int nv = 0;
     if (jA >= 0) j[nv++] = jA;
     if (jB >= 0) j[nv++] = jB;
@@ -97,15 +116,39 @@ __device__ __forceinline__ bool closer(double d, int h, double bd, int bh)
 
 
 constexpr int kCfThreads = 256, kCfWarps = kCfThreads / 32;
-constexpr int kCfCap = 256;   // pool hits held per pass (more: further passes)
+constexpr int kCfCap = 256;        // pool hits held per pass (more: further passes)
 
 struct CfWarp {
-    int n_own[16], own_hit[16];
+    int n_own[16], own_pos[16];
     int best_h[16];
     double best_d[16];
-    int pool_h[kCfCap];
-    double pool_d[kCfCap];
+    unsigned lbmin[16];     // per layer: least lower bound of a pool hit's distance (float bits)
+    int q[64];              // screened positions waiting for the exact evaluation
+    int rs[32], rp[33];     // runs of index positions scanned: start, exclusive prefix of lengths
+    int pool_p[kCfCap], pool_h[kCfCap];   // index position and event-local hit index
+    float pool_d[kCfCap], pool_e[kCfCap];   // float32 distance and its error bound
     unsigned char pool_l[kCfCap];
+};
+
+// The hits a candidate scans: the t-th of the runs W.rs / W.rp of the
+// event's hit index (k_hitindex.cu).
+struct HitView {
+    const float *x, *y;
+    const int *h;
+    const uint8_t *l;
+    const CfWarp *W;
+    int n;   // total positions
+
+    __device__ __forceinline__ int pos(int t) const
+    {
+        int lo = 0, hi = 31;   // the last run r with rp[r] <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (W->rp[mid] <= t) lo = mid;
+            else hi = mid - 1;
+        }
+        return W->rs[lo] + (t - W->rp[lo]);
+    }
 };
 
 // Event of flattened candidate f: the last e with cpre[e] <= f (cpre is the
@@ -121,159 +164,409 @@ __device__ __forceinline__ int event_of(const int *cpre, int n_ev, int f)
     return lo;
 }
 
-// One pass over the hit sequence of a candidate: collects the pool hits of
-// rank [r0, r0 + kCfCap) into the warp's list (in hit order) and, when
-// count_own, the own hits per layer.  Returns the total number of pool hits.
-__device__ __forceinline__ int scan_pool(const DevGeom &G, const float *__restrict__ x,
-                                         const float *__restrict__ y,
-                                         const uint8_t *__restrict__ layer, const int *hl,
-                                         int nl, int i, int j, int k, int pool, int r0,
-                                         bool count_own, CfWarp &W, int lane)
+// Azimuth window of the hits of one layer that can have a root within
+// d0 in [lo, hi] (cm) in column (rho, phi0_k); returns its runs of index
+// cells as bins [b0, b1] (b1 - b0 + 1 >= kIdxAz or full: the whole layer;
+// empty: no hit can).  A root d0 of the circle equation gives
+//   s = -(2 d0 + rho (d0^2 + r^2)) / (2 (1 + rho d0)),
+// decreasing in d0 while (1 + rho d0)^2 + 1 > rho^2 r^2 and monotone in r^2
+// (sign -rho) while 1 + rho d0 > 0, so over the window and the layer's
+// radius range [rmin, rmax] s lies between its values at two corners; with
+// c > 0 the hit's azimuth is phi0_k - asin(s / r).  Margins (1e-3 cm plus
+// 1e-5 relative on s, 2e-3 rad on the azimuth) cover float32 rounding;
+// where the monotonicity conditions are not proven the whole layer is
+// scanned.
+__device__ __forceinline__ void layer_window(float rho, float phik, float lo, float hi,
+                                             float rmin, float rmax, bool &full, bool &empty,
+                                             int &b0, int &b1)
 {
-    int rank = 0;
-    for (int base = 0; base < nl; base += 32) {
-        const int p = base + lane;
-        int h = -1, l = 0;
+    full = false;
+    empty = !(rmin <= rmax);
+    b0 = b1 = 0;
+    if (empty) return;
+    const float tl = fmaf(rho, lo, 1.0f), th = fmaf(rho, hi, 1.0f);
+    const float tmin = fminf(tl, th);
+    if (!(tmin >= 0.05f) || !(rmin >= 1e-3f) ||
+        fmaf(rho * rho * 1.001f, rmax * rmax, 1e-3f) >= fmaf(tmin, tmin, 1.0f)) {
+        full = true;
+        return;
+    }
+    const float rA = rho > 0.0f ? rmin : rmax, rB = rho > 0.0f ? rmax : rmin;
+    float s_hi = -fmaf(rho, fmaf(lo, lo, rA * rA), 2.0f * lo) / (2.0f * tl);
+    float s_lo = -fmaf(rho, fmaf(hi, hi, rB * rB), 2.0f * hi) / (2.0f * th);
+    const float ms = fmaf(1e-5f, fabsf(s_hi) + fabsf(s_lo), 1e-3f);
+    s_hi += ms;
+    s_lo -= ms;
+    const float a_hi = s_hi / (s_hi > 0.0f ? rmin : rmax);
+    const float a_lo = s_lo / (s_lo < 0.0f ? rmin : rmax);
+    if (a_lo > 1.0f || a_hi < -1.0f) {
+        empty = true;
+        return;
+    }
+    const float dmax = asinf(fminf(a_hi, 1.0f)), dmin = asinf(fmaxf(a_lo, -1.0f));
+    const float k = kIdxAz / 6.28318531f;
+    b0 = (int)floorf((phik - dmax - 2e-3f + 3.14159265f) * k);
+    b1 = (int)floorf((phik - dmin + 2e-3f + 3.14159265f) * k);
+    if (b1 - b0 + 1 >= kIdxAz) full = true;
+}
+
+// Float32 screen of a hit against a candidate's pool: false only when both
+// roots certainly lie more than two bins outside [j - pool, j + pool].
+// Where D > 1e-3, |q| >= sqrt(D) > 0.03 and the float32 roots of any circle
+// with |d0| below a few tens of cm are within a few 1e-3 cm of the exact
+// ones (first-order bounds of the vote's guard, far below two bins); roots
+// far outside the axis stay far outside.  D <= 1e-3 (near tangent) always
+// goes to the exact evaluation; D < -1e-3 has no real root.
+struct PoolScreen {
+    float rho, invrho_d, lo, hi, sk, ck;
+    bool has_b;
+
+    __device__ __forceinline__ bool maybe(float xf, float yf, float inv_delta, float off) const
+    {
+        const float c = fmaf(xf, ck, yf * sk);
+        if (!(c > 0.0f)) return c > -1e-3f * (fabsf(xf) + fabsf(yf));
+        const float s = fmaf(xf, sk, -(yf * ck));
+        const float b = fmaf(rho, s, 1.0f);
+        const float pc = rho * c;
+        const float D = fmaf(-pc, pc, 1.0f);
+        if (D < -1e-3f) return false;
+        if (D <= 1e-3f) return true;
+        const float sq = D * rsqrt_approx(D);
+        const float q = -(b + copysignf(sq, b));
+        const float C = fmaf(rho, fmaf(xf, xf, yf * yf), s + s);
+        const float uA = fmaf(C * rcp_approx(q), inv_delta, off);
+        bool near = uA >= lo && uA < hi;
+        if (has_b) {
+            const float uB = fmaf(q, invrho_d, off);
+            near |= uB >= lo && uB < hi;
+        }
+        return near;
+    }
+};
+
+// One pass over a candidate's hit sequence: collects the pool hits of rank
+// [r0, r0 + kCfCap) into the warp's list (in sequence order) and, when
+// count_own, the own hits per layer.  Returns the total number of pool hits.
+// Hits that pass the float32 screen queue up in order and get the exact
+// evaluation 32 at a time, so that the lanes stay busy.
+__device__ __forceinline__ int scan_pool(const DevGeom &G, const HitView &V, int i, int j, int k,
+                                         int pool, int r0, bool count_own, CfWarp &W, int lane)
+{
+    ColumnCtx C;
+    C.init(G, i, k);
+    PoolScreen ps;
+    ps.rho = C.rho;
+    ps.invrho_d = C.invrho * G.inv_delta_f;
+    ps.has_b = C.has_b;
+    ps.lo = (float)(j - pool - 2);
+    ps.hi = (float)(j + pool + 3);
+    ps.sk = C.sk;
+    ps.ck = C.ck;
+    const unsigned lt = (1u << lane) - 1u;
+    int rank = 0, qn = 0;
+    // exact bins of the first cnt (<= 32) queued hits, one per lane, in order
+    auto drain = [&](int cnt) {
+        int p = -1, l = 0;
         bool own = false, inp = false;
-        if (p < nl) {
-            h = hl ? __ldg(hl + p) : p;
+        if (lane < cnt) {
+            p = W.q[lane];
             int jj[2];
-            const int nv = column_bins(G, __ldg(x + h), __ldg(y + h), i, k, jj);
+            const int nv = column_bins(G, C, V.x[p], V.y[p], jj);
             for (int v = 0; v < nv; ++v) {
                 own |= jj[v] == j;
                 inp |= abs(jj[v] - j) <= pool;
             }
-            if (inp) l = __ldg(layer + h) & 15;   // layers are 0 .. 15 (bounds the per-layer arrays)
+            if (inp) l = V.l[p];
         }
         if (count_own && own) {
             atomicAdd(&W.n_own[l], 1);
-            W.own_hit[l] = h;   // read only where the layer holds exactly one own hit
+            W.own_pos[l] = p;   // read only where the layer holds exactly one own hit
         }
         const unsigned bal = __ballot_sync(0xffffffffu, inp);
-        const int r = rank + __popc(bal & ((1u << lane) - 1u));
+        const int r = rank + __popc(bal & lt);
         if (inp && r >= r0 && r < r0 + kCfCap) {
-            W.pool_h[r - r0] = h;
+            W.pool_p[r - r0] = p;
+            W.pool_h[r - r0] = V.h[p];
             W.pool_l[r - r0] = (unsigned char)l;
         }
         rank += __popc(bal);
+    };
+    for (int base = 0; base < V.n; base += 32) {
+        const int t = base + lane;
+        bool nr = false;
+        int p = 0;
+        if (t < V.n) {
+            p = V.pos(t);
+            nr = ps.maybe(V.x[p], V.y[p], G.inv_delta_f, G.off_f);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, nr);
+        if (nr) W.q[qn + __popc(bal & lt)] = p;   // qn < 32 here, so below 64
+        qn += __popc(bal);
+        __syncwarp();
+        if (qn >= 32) {
+            drain(32);
+            __syncwarp();
+            const int rest = qn - 32;
+            const int v = lane < rest ? W.q[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) W.q[lane] = v;
+            qn = rest;
+            __syncwarp();
+        }
     }
+    if (qn > 0) drain(qn);
     __syncwarp();
     return rank;
 }
 
-// Confirmation of every kept candidate of a batch (see the file comment).
-// Event e's hits are x[off[e] ..), its candidates peaks[e cap ..
-// e cap + min(counts[e], cap)); cpre: exclusive prefix of those kept counts
-// (cpre[n_ev] = total).  Outputs per candidate slot e cap + m: score (0 =
-// not confirmed) and inl[16 (e cap + m) + l] (event-local inlier hit of
-// layer l, -1 none).  bk (ent null for none): per-event hit lists by column
-// group -- a superset of the hits with a root in any column of the group.
+__device__ __forceinline__ float warp_minf(float v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// The runs of index positions a candidate of event e in column (rho_i,
+// phi0_k) with bin j scans: per layer its azimuth window (layer_window) for
+// d0 within two bins beyond the pool, as one or two runs of cells (the
+// window may wrap); lane r takes run r = 2 l + part.
+__device__ __forceinline__ void candidate_runs(const DevGeom &G, const ConfirmDev &P,
+                                               const HitIndex &I, int e, int i, int j, int k,
+                                               CfWarp &W, HitView &V, int lane)
+{
+    const int l = lane >> 1, part = lane & 1;
+    int start = 0, len = 0;
+    if (l < P.n_layers) {
+        const float lo = ((float)(j - P.pool - 2) - G.off_f) * G.delta_f;
+        const float hi = ((float)(j + P.pool + 3) - G.off_f) * G.delta_f;
+        const float rmin = __uint_as_float(I.rmm[2 * (e * 16 + l)]);
+        const float rmax = __uint_as_float(I.rmm[2 * (e * 16 + l) + 1]);
+        bool full, empty;
+        int b0, b1;
+        layer_window(G.rho32[i], G.phi32[k], lo, hi, rmin, rmax, full, empty, b0, b1);
+        const int base = (e * 16 + l) * kIdxAz;
+        if (full) {
+            if (part == 0) {
+                start = I.offs[base];
+                len = I.offs[base + kIdxAz] - start;
+            }
+        } else if (!empty) {
+            const int b0m = ((b0 % kIdxAz) + kIdxAz) % kIdxAz, nb = b1 - b0 + 1;
+            if (b0m + nb <= kIdxAz) {
+                if (part == 0) {
+                    start = I.offs[base + b0m];
+                    len = I.offs[base + b0m + nb] - start;
+                }
+            } else if (part == 0) {
+                start = I.offs[base + b0m];
+                len = I.offs[base + kIdxAz] - start;
+            } else {
+                start = I.offs[base];
+                len = I.offs[base + b0m + nb - kIdxAz] - start;
+            }
+        }
+    }
+    int incl = len;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += v;
+    }
+    W.rs[lane] = start;
+    W.rp[lane + 1] = incl;
+    if (lane == 0) W.rp[0] = 0;
+    __syncwarp();
+    V.n = W.rp[32];
+}
+
+// Confirmation of one candidate by one warp (see the file comment).  Writes
+// score[slot] (0 = not confirmed) and inl[16 slot + l].
+//
+// Distances: a float32 estimate with a first-order error bound decides
+// every hit that is certainly farther than tol, or certainly not the
+// nearest of its layer; the float64 distance of the definition is computed
+// only for the rest.  The estimate works in the circle's local frame at the
+// first seed hit P1 (unit normal n towards the centre, curvature k = 1/R):
+// with w = P - P1 the signed distance is
+//   t = (k |w|^2 - 2 w.n) / (|k w - n| + 1),
+// whose terms are all of the order of |w| (no large centre coordinates), so
+// rounding the inputs and the frame to float32 moves t by a few 2^-24 |w|
+// (e = 6e-7 (k |w|^2 + 2 (|w_x| + |w_y|)) + 1e-6 cm covers it with a wide
+// margin).
+__device__ __forceinline__ void confirm_one(const DevGeom &G, const ConfirmDev &P,
+                                            const HitIndex &I, int e, const ht_peak pk,
+                                            size_t slot, float tol_hi, int *__restrict__ score,
+                                            int *__restrict__ inl, CfWarp &W, int lane)
+{
+    HitView V{I.x, I.y, I.h, I.l, &W, 0};
+    candidate_runs(G, P, I, e, pk.i_rho, pk.j_d0, pk.k_phi0, W, V, lane);
+    if (lane < 16) {
+        W.n_own[lane] = 0;
+        W.best_h[lane] = -1;
+        W.best_d[lane] = 0.0;
+    }
+    __syncwarp();
+    const int npool = scan_pool(G, V, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool, 0, true, W, lane);
+    // seed layers (every lane computes the same)
+    int la = -1, lc = -1, ns = 0;
+    for (int l = 0; l < P.n_layers; ++l)
+        if (W.n_own[l] == 1) {
+            if (la < 0) la = l;
+            lc = l;
+            ++ns;
+        }
+    int lb = -1, gap = 1 << 30;
+    for (int l = la + 1; ns >= 3 && l < lc; ++l)
+        if (W.n_own[l] == 1 && abs(2 * l - (la + lc)) < gap) {
+            gap = abs(2 * l - (la + lc));
+            lb = l;
+        }
+    double xc = 0.0, yc = 0.0, R = 0.0;
+    bool ok = ns >= 3;
+    float x1f = 0.0f, y1f = 0.0f;
+    if (ok) {
+        const int pa = W.own_pos[la], pb = W.own_pos[lb], pc = W.own_pos[lc];
+        x1f = V.x[pa];
+        y1f = V.y[pa];
+        ok = circle3((double)x1f, (double)y1f, (double)V.x[pb], (double)V.y[pb],
+                     (double)V.x[pc], (double)V.y[pc], xc, yc, R);
+    }
+    int sc = 0;
+    if (ok) {
+        const double iR = 1.0 / R;
+        const float nx = (float)(__dsub_rn(xc, (double)x1f) * iR);
+        const float ny = (float)(__dsub_rn(yc, (double)y1f) * iR);
+        const float kap = (float)iR;
+        for (int r0 = 0; r0 < npool; r0 += kCfCap) {
+            if (r0 > 0)
+                scan_pool(G, V, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool, r0, false, W, lane);
+            const int nq = min(npool - r0, kCfCap);
+            if (lane < 16) W.lbmin[lane] = 0x7f800000u;   // +inf
+            __syncwarp();
+            for (int q = lane; q < nq; q += 32) {
+                const int p = W.pool_p[q];
+                const float wx = V.x[p] - x1f, wy = V.y[p] - y1f;
+                const float w2 = fmaf(wx, wx, wy * wy);
+                const float wn = fmaf(wx, nx, wy * ny);
+                const float num = fmaf(kap, w2, -2.0f * wn);
+                const float qx = fmaf(kap, wx, -nx), qy = fmaf(kap, wy, -ny);
+                const float den = sqrtf(fmaf(qx, qx, qy * qy)) + 1.0f;
+                const float d = fabsf(num / den);
+                const float er =
+                    fmaf(6e-7f, fmaf(kap, w2, 2.0f * (fabsf(wx) + fabsf(wy))), 1e-6f);
+                W.pool_d[q] = d;
+                W.pool_e[q] = er;
+                atomicMin(&W.lbmin[W.pool_l[q]], __float_as_uint(fmaxf(d - er, 0.0f)));
+            }
+            __syncwarp();
+            if (npool <= kCfCap) {
+                // layers that can hold an inlier at all: too few, not confirmed
+                int poss = 0;
+                for (int l = 0; l < P.n_layers; ++l)
+                    poss += __uint_as_float(W.lbmin[l]) < tol_hi ? 1 : 0;
+                if (poss < P.min_layers) break;
+            }
+            for (int l = 0; l < P.n_layers; ++l) {
+                if (!(__uint_as_float(W.lbmin[l]) < tol_hi)) continue;   // uniform
+                float ub = 3.0e38f;   // the least upper bound on this layer
+                for (int q = lane; q < nq; q += 32)
+                    if (W.pool_l[q] == l) ub = fminf(ub, W.pool_d[q] + W.pool_e[q]);
+                ub = warp_minf(ub);
+                // contenders: may be the layer's nearest and below tol
+                double bd = 0.0;
+                int bh = -1;
+                for (int q = lane; q < nq; q += 32) {
+                    if (W.pool_l[q] != l) continue;
+                    const float lo = W.pool_d[q] - W.pool_e[q];
+                    if (!(lo <= ub && lo < tol_hi)) continue;
+                    const int p = W.pool_p[q], h = W.pool_h[q];
+                    const double dd = circle_dist(V.x[p], V.y[p], xc, yc, R);
+                    if (closer(dd, h, bd, bh)) {
+                        bd = dd;
+                        bh = h;
+                    }
+                }
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) {
+                    const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+                    const int oh = __shfl_xor_sync(0xffffffffu, bh, o);
+                    if (closer(od, oh, bd, bh)) {
+                        bd = od;
+                        bh = oh;
+                    }
+                }
+                if (lane == 0 && closer(bd, bh, W.best_d[l], W.best_h[l])) {
+                    W.best_d[l] = bd;
+                    W.best_h[l] = bh;
+                }
+            }
+            __syncwarp();
+        }
+        for (int l = 0; l < P.n_layers; ++l)
+            sc += (W.best_h[l] >= 0 && W.best_d[l] < P.tol) ? 1 : 0;
+    }
+    const bool conf = ok && sc >= P.min_layers;
+    if (lane < 16) {
+        const bool in = conf && lane < P.n_layers && W.best_h[lane] >= 0 && W.best_d[lane] < P.tol;
+        inl[slot * 16 + lane] = in ? W.best_h[lane] : -1;
+    }
+    if (lane == 0) score[slot] = conf ? sc : 0;
+    __syncwarp();
+}
+
+// Confirmation of every kept candidate of a batch.  The candidates are
+// ordered by (event, column group of kGroupCols columns) in order[] (flattened
+// indices; cpre is the exclusive prefix of the kept counts), so that the
+// warps of a CTA work on nearby columns of one event; a CTA takes chunks of
+// kCfChunk consecutive entries, one candidate per warp at a time.  I: the
+// batch's hit index (k_hitindex.cu).
+constexpr int kCfChunk = 64;
+
 __global__ void __launch_bounds__(kCfThreads)
-k_confirm(DevGeom G, ConfirmDev P, const float *__restrict__ x, const float *__restrict__ y,
-          const uint8_t *__restrict__ layer, const int *__restrict__ off,
-          const int *__restrict__ d_nev, const ht_peak *__restrict__ peaks, int cap,
-          const int *__restrict__ cpre, int *__restrict__ score, int *__restrict__ inl,
-          int *__restrict__ head, BucketView bk)
+k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
+          const ht_peak *__restrict__ peaks, int cap, const int *__restrict__ cpre,
+          const int *__restrict__ order, int *__restrict__ score, int *__restrict__ inl,
+          int *__restrict__ head)
 {
     __shared__ CfWarp sw[kCfWarps];
-    const int lane = threadIdx.x & 31;
-    CfWarp &W = sw[threadIdx.x >> 5];
+    __shared__ int s_chunk;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    CfWarp &W = sw[warp];
     const int n_ev = *d_nev;
     const int total = cpre[n_ev];
+    float tol_hi = (float)P.tol;   // tol rounded up to float32
+    if ((double)tol_hi < P.tol) tol_hi = nextafterf(tol_hi, 3.0e38f);
     for (;;) {
-        int f = 0;
-        if (lane == 0) f = atomicAdd(head, 1);
-        f = __shfl_sync(0xffffffffu, f, 0);
-        if (f >= total) break;
-        const int e = event_of(cpre, n_ev, f);
-        const int m = f - cpre[e];
-        const size_t slot = (size_t)e * cap + m;
-        const ht_peak pk = peaks[slot];
-        const int a = off[e], n = off[e + 1] - a;
-        const int *hl = nullptr;
-        int nl = n;
-        if (bk.ent) bk.list(e, pk.k_phi0, hl, nl);
-        if (lane < 16) {
-            W.n_own[lane] = 0;
-            W.best_h[lane] = -1;
-            W.best_d[lane] = 0.0;
+        if (threadIdx.x == 0) s_chunk = atomicAdd(head, 1);
+        __syncthreads();
+        const int t0 = s_chunk * kCfChunk;
+        __syncthreads();   // every thread has read s_chunk
+        if (t0 >= total) break;
+        const int t1 = min(t0 + kCfChunk, total);
+        for (int t = t0 + warp; t < t1; t += kCfWarps) {
+            const int f = __ldg(order + t);
+            const int e = event_of(cpre, n_ev, f);
+            const size_t slot = (size_t)e * cap + (f - cpre[e]);
+            confirm_one(G, P, I, e, peaks[slot], slot, tol_hi, score, inl, W, lane);
         }
-        __syncwarp();
-        const float *xe = x + a, *ye = y + a;
-        const uint8_t *le = layer + a;
-        const int npool = scan_pool(G, xe, ye, le, hl, nl, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool,
-                                    0, true, W, lane);
-        // seed layers (every lane computes the same)
-        int la = -1, lc = -1, ns = 0;
-        for (int l = 0; l < P.n_layers; ++l)
-            if (W.n_own[l] == 1) {
-                if (la < 0) la = l;
-                lc = l;
-                ++ns;
-            }
-        int lb = -1, gap = 1 << 30;
-        for (int l = la + 1; ns >= 3 && l < lc; ++l)
-            if (W.n_own[l] == 1 && abs(2 * l - (la + lc)) < gap) {
-                gap = abs(2 * l - (la + lc));
-                lb = l;
-            }
-        double xc = 0.0, yc = 0.0, R = 0.0;
-        bool ok = ns >= 3;
-        if (ok) {
-            const int ha = W.own_hit[la], hb = W.own_hit[lb], hc = W.own_hit[lc];
-            ok = circle3((double)xe[ha], (double)ye[ha], (double)xe[hb], (double)ye[hb],
-                         (double)xe[hc], (double)ye[hc], xc, yc, R);
-        }
-        int sc = 0;
-        if (ok) {
-            for (int r0 = 0; r0 < npool; r0 += kCfCap) {
-                if (r0 > 0)
-                    scan_pool(G, xe, ye, le, hl, nl, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool, r0,
-                              false, W, lane);
-                const int nq = min(npool - r0, kCfCap);
-                for (int q = lane; q < nq; q += 32) {
-                    const int h = W.pool_h[q];
-                    W.pool_d[q] = circle_dist(xe[h], ye[h], xc, yc, R);
-                }
-                __syncwarp();
-                for (int l = 0; l < P.n_layers; ++l) {
-                    double bd = 0.0;
-                    int bh = -1;
-                    for (int q = lane; q < nq; q += 32)
-                        if (W.pool_l[q] == l && closer(W.pool_d[q], W.pool_h[q], bd, bh)) {
-                            bd = W.pool_d[q];
-                            bh = W.pool_h[q];
-                        }
-#pragma unroll
-                    for (int o = 16; o > 0; o >>= 1) {
-                        const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-                        const int oh = __shfl_xor_sync(0xffffffffu, bh, o);
-                        if (closer(od, oh, bd, bh)) {
-                            bd = od;
-                            bh = oh;
-                        }
-                    }
-                    if (lane == 0 && closer(bd, bh, W.best_d[l], W.best_h[l])) {
-                        W.best_d[l] = bd;
-                        W.best_h[l] = bh;
-                    }
-                }
-                __syncwarp();
-            }
-            for (int l = 0; l < P.n_layers; ++l)
-                sc += (W.best_h[l] >= 0 && W.best_d[l] < P.tol) ? 1 : 0;
-        }
-        const bool conf = ok && sc >= P.min_layers;
-        if (lane < 16) {
-            const bool in = conf && lane < P.n_layers && W.best_h[lane] >= 0 &&
-                            W.best_d[lane] < P.tol;
-            inl[slot * 16 + lane] = in ? W.best_h[lane] : -1;
-        }
-        if (lane == 0) score[slot] = conf ? sc : 0;
-        __syncwarp();
     }
 }
 
+// Candidates of each (event, column group) item: counts, then positions.
+__global__ void k_cf_group(const int *__restrict__ d_nev, const int *__restrict__ cpre,
+                           const ht_peak *__restrict__ peaks, int cap, int ngroups,
+                           int *__restrict__ gcnt, int *__restrict__ gcur, int *__restrict__ order)
+{
+    const int n_ev = *d_nev;
+    const int total = cpre[n_ev];
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < total; f += gridDim.x * blockDim.x) {
+        const int e = event_of(cpre, n_ev, f);
+        const int k = peaks[(size_t)e * cap + (f - cpre[e])].k_phi0;
+        const int it = e * ngroups + k / kGroupCols;
+        if (gcur) order[atomicAdd(&gcur[it], 1)] = f;
+        else atomicAdd(&gcnt[it], 1);
+    }
+}
 
 // cpre[e] = sum over events before e of min(counts[e], cap); cpre[n_ev] is
 // the total.  One block; n_ev <= 4096.
@@ -341,12 +634,58 @@ __global__ void k_single_offsets(int *__restrict__ off, int *__restrict__ nev, i
 cudaError_t launch_assoc_final_batch(const unsigned long long *gbest, const int *off,
                                      const int *d_nev, int *assign, int max_hits, cudaStream_t st);
 
-// Confirmation and final assignment of a batch (device offsets and event
-// count).  ws: confirm_workspace_bytes(max_events, max_hits).
-size_t confirm_workspace_bytes(int max_events, int max_hits)
+size_t scan_tmp_bytes(int n_cap);
+cudaError_t scan_exclusive(const int *in, int *out, int *out2, int n_cap, const int *d_n,
+                           int *total, void *tmp, cudaStream_t st);
+
+namespace {
+
+struct CfWs {
+    int *cpre, *head, *gcnt, *gofs, *gcur, *order;
+    unsigned long long *gbest;
+    void *tmp;
+    HitIndex idx;
+};
+
+int cf_groups(const DevGeom &G) { return (G.n_phi0 + kGroupCols - 1) / kGroupCols; }
+
+// Carves (p non-null) or sizes the confirmation workspace.
+size_t cf_layout(const DevGeom &G, int max_events, int max_hits, int cap, char *p, CfWs *w)
 {
-    return align256((size_t)(max_events + 1) * 4) + align256(64) +
-           align256((size_t)(max_hits > 0 ? max_hits : 1) * 8);
+    const size_t ni = (size_t)max_events * cf_groups(G);
+    const size_t parts[] = {(size_t)(max_events + 1) * 4, 64, (size_t)(max_hits > 0 ? max_hits : 1) * 8,
+                            ni * 4, (ni + 1) * 4, (ni + 1) * 4,
+                            (size_t)max_events * (cap > 0 ? cap : 1) * 4,
+                            scan_tmp_bytes((int)ni), hit_index_bytes(max_events, max_hits)};
+    size_t at = 0;
+    char *q[9];
+    for (int i = 0; i < 9; ++i) {
+        q[i] = p ? p + at : nullptr;
+        at += align256(parts[i]);
+    }
+    if (w) {
+        w->cpre = reinterpret_cast<int *>(q[0]);
+        w->head = reinterpret_cast<int *>(q[1]);
+        w->gbest = reinterpret_cast<unsigned long long *>(q[2]);
+        w->gcnt = reinterpret_cast<int *>(q[3]);
+        w->gofs = reinterpret_cast<int *>(q[4]);
+        w->gcur = reinterpret_cast<int *>(q[5]);
+        w->order = reinterpret_cast<int *>(q[6]);
+        w->tmp = q[7];
+        if (p) w->idx = carve_hit_index(max_events, max_hits, q[8]);
+    }
+    return at;
+}
+
+}  // namespace
+
+cudaError_t prepare_confirm_kernels() { return cudaSuccess; }
+
+// Confirmation and final assignment of a batch (device offsets and event
+// count).  ws: confirm_workspace_bytes(G, max_events, max_hits, cap).
+size_t confirm_workspace_bytes(const DevGeom &G, int max_events, int max_hits, int cap)
+{
+    return cf_layout(G, max_events, max_hits, cap, nullptr, nullptr);
 }
 
 cudaError_t launch_confirm_batch(const DevGeom &G, const ConfirmDev &P, const float *x,
@@ -356,30 +695,36 @@ cudaError_t launch_confirm_batch(const DevGeom &G, const ConfirmDev &P, const fl
                                  int *inl, int *assign, void *ws, int sms, cudaStream_t st,
                                  const HitBuckets *hb)
 {
-    char *w = reinterpret_cast<char *>(ws);
-    int *cpre = reinterpret_cast<int *>(w);
-    w += align256((size_t)(max_events + 1) * 4);
-    int *head = reinterpret_cast<int *>(w);
-    w += align256(64);
-    unsigned long long *gbest = reinterpret_cast<unsigned long long *>(w);
-    cudaError_t e = cudaMemsetAsync(head, 0, 4, st);
-    if (e == cudaSuccess) e = cudaMemsetAsync(gbest, 0, (size_t)max_hits * 8, st);
+    (void)hb;
+    CfWs w;
+    cf_layout(G, max_events, max_hits, cap, reinterpret_cast<char *>(ws), &w);
+    const int ng = cf_groups(G), ni = max_events * ng;
+    cudaError_t e = cudaMemsetAsync(w.head, 0, 4, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.gbest, 0, (size_t)max_hits * 8, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(w.gcnt, 0, (size_t)ni * 4, st);
     if (e != cudaSuccess) return e;
-    k_cand_prefix<<<1, 1024, 0, st>>>(counts, d_nev, cap, cpre);
+    k_cand_prefix<<<1, 1024, 0, st>>>(counts, d_nev, cap, w.cpre);
+    // candidates by (event, column group): counts, offsets, positions
+    k_cf_group<<<sms * 4, 256, 0, st>>>(d_nev, w.cpre, peaks, cap, ng, w.gcnt, nullptr, nullptr);
+    e = scan_exclusive(w.gcnt, w.gofs, w.gcur, ni, nullptr, w.gofs + ni, w.tmp, st);
+    if (e != cudaSuccess) return e;
+    k_cf_group<<<sms * 4, 256, 0, st>>>(d_nev, w.cpre, peaks, cap, ng, nullptr, w.gcur, w.order);
+    e = launch_hit_index(x, y, layer, off, d_nev, max_events, max_hits, w.idx, sms, st);
+    if (e != cudaSuccess) return e;
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_confirm, kCfThreads, 0);
     k_confirm<<<sms * (occ > 0 ? occ : 1), kCfThreads, 0, st>>>(
-        G, P, x, y, layer, off, d_nev, peaks, cap, cpre, score, inl, head, bucket_view(hb));
-    k_confirm_offer<<<sms * 8, 256, 0, st>>>(off, d_nev, cpre, cap, score, inl, gbest);
+        G, P, w.idx, d_nev, peaks, cap, w.cpre, w.order, score, inl, w.head);
+    k_confirm_offer<<<sms * 8, 256, 0, st>>>(off, d_nev, w.cpre, cap, score, inl, w.gbest);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    return launch_assoc_final_batch(gbest, off, d_nev, assign, max_hits, st);
+    return launch_assoc_final_batch(w.gbest, off, d_nev, assign, max_hits, st);
 }
 
 // One event (host hit count n, device candidate count d_count).
-size_t confirm_workspace_bytes_single(int n)
+size_t confirm_workspace_bytes_single(const DevGeom &G, int n, int cap)
 {
-    return align256(16) + confirm_workspace_bytes(1, n);
+    return align256(16) + confirm_workspace_bytes(G, 1, n, cap);
 }
 
 cudaError_t launch_confirm(const DevGeom &G, const ConfirmDev &P, const float *x, const float *y,

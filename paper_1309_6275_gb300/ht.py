@@ -137,7 +137,7 @@ SIGNATURES = [
     ("ht_vertex_vote", _I32, [_P, _P, _P, _I32, _I32, _P, _P, _P]),
     ("ht_vertex_find", _I32, [_P, _P, _I32, _P, _I32, _P, _P, _P, _SZ, _P]),
     ("ht_vote_layers", _I32, [_P, _P, _P, _P, _I32, _P, _P, _P]),
-    ("ht_confirm_workspace_size", _SZ, [_P, _I32]),
+    ("ht_confirm_workspace_size", _SZ, [_P, _I32, _I32]),
     ("ht_confirm", _I32, [_P, ctypes.POINTER(_ConfirmDesc), _P, _P, _P, _I32, _P, _P, _I32,
                           _P, _P, _P, _P, _SZ, _P]),
     ("ht_batch_set_confirm", _I32, [_P, ctypes.POINTER(_ConfirmDesc)]),
@@ -241,8 +241,8 @@ def ht_vote_layers(g, x, y, layer, acc, stats=None, stream=None):
                                 _ptr(stats), _stream(stream)), "ht_vote_layers")
 
 
-def ht_confirm_workspace_size(g, n_hits):
-    return lib().ht_confirm_workspace_size(g.handle, n_hits)
+def ht_confirm_workspace_size(g, n_hits, cap):
+    return lib().ht_confirm_workspace_size(g.handle, n_hits, cap)
 
 
 def ht_confirm(g, c, x, y, layer, peaks, d_count, cap, score, inliers, assign, workspace,

@@ -34,7 +34,7 @@ def gpu_tracks_event(g, ev, cap, cp):
     peaks = torch.empty((c1, 4), dtype=torch.int32, device="cuda")
     count = torch.zeros(1, dtype=torch.int32, device="cuda")
     ws = torch.empty(max(G.find_peaks_workspace_size(), G.vote_z_workspace_size(max(n, 1), cap),
-                         ht.ht_confirm_workspace_size(G, n)), dtype=torch.uint8, device="cuda")
+                         ht.ht_confirm_workspace_size(G, n, cap)), dtype=torch.uint8, device="cuda")
     ht.ht_find_peaks(G, acc, peaks, cap, count, ws)
     score = torch.full((c1,), -7, dtype=torch.int32, device="cuda")
     inl = torch.full((c1, 16), -7, dtype=torch.int32, device="cuda")
