@@ -1,22 +1,25 @@
 #!/usr/bin/env python3
-"""Throughput of the Hough-transform track-finding path on GB300.
+"""Throughput of the Hough-transform track finder on GB300.
 
-One step = the whole path (vote, 3x3x3 peaks, hit association, (z0, cot theta)
-vote) over every event of the 100-event workload (~10k hits per event,
-256 rho x 128 d0 x 512 phi0 uint16 accumulator, 128 x 128 z grid), run by
-the batched runtime (ht_batch_run: persistent queue kernels, CUDA graph
-replay, 25 events per batch).  Hits are synthetic (seeded generator) and
-resident in HBM before timing; L2 is flushed (256 MiB write) before every
-timed step; each step is timed with CUDA events on the launching stream, and
-the stages inside each batch with CUDA events recorded in the graph.
+One step = the whole track path over every event of the batched-stream
+workload (2000 events, hit counts log-uniform on [2k, 60k], 256 rho x 128 d0
+x 512 phi0 uint16 accumulator, 128 x 128 (z0, cot theta) grid): the
+distinct-layer vote, 3x3x3 peaks at each event's band threshold, the
+candidate confirmation and hit assignment, and the (z0, cot theta) vote, run
+by the batched runtime (ht_batch_run_tracks: persistent queue kernels, CUDA
+graph replay, 50 events per batch).  Hits are synthetic (seeded generator)
+and resident in HBM before timing (442 MB, larger than L2, which is also
+flushed by a 256 MiB write before every timed step); steps are timed with
+CUDA events on the launching stream.  Stage times come from CUDA events
+recorded inside the graphs, in an untimed pass.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-N > 1 runs under torch.distributed (one process per GPU, launched by
-torch.distributed.run); every rank processes its own 100 events (weak
-scaling: events are independent, there is no data-path collective).
---impl reference times the CPU oracle (plain float64 C) on the host cores on
-one event per step.  Prints one JSON line on rank 0.
+N > 1 runs under torch.distributed (one process per GPU); every rank takes
+its LPT share of N x 2000 events (weak scaling: events are independent, no
+data-path collective).  --impl reference times the float64 CPU oracle on the
+host cores, one event of the workload per step.  Prints one JSON line on
+rank 0.
 """
 import argparse
 import json
@@ -34,31 +37,30 @@ sys.path.insert(0, ROOT)
 
 import synth  # noqa: E402
 
-WORKLOAD = "event100_256"
+WORKLOAD = "stream2000_256"
 METRIC = "events/s"
-CAP = 1 << 20          # candidate capacity per event (the 10k-hit events give ~5e5)
-CAP_OF = {"pileup_512": 1 << 22}   # the 50k-hit events give ~3.7e6
+# candidate capacity per event slot: the densest events give ~2e5 peaks at
+# their band threshold (10k-hit events at T = 9), the pile-up ones ~1.2e5
+CAP_OF = {"stream2000_256": 1 << 19, "event100_256": 1 << 19, "pileup_512": 1 << 21}
+BATCH_OF = {"stream2000_256": 50, "event100_256": 25, "pileup_512": 4}
+SECONDARY = ("event100_256", "pileup_512")
 
 
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=3)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--events", type=int, default=None, help="events per step (default: workload's)")
+    p.add_argument("--batch", type=int, default=None, help="events per ht_batch_run_tracks")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--no-single", action="store_true")
-    p.add_argument("--batch", type=int, default=25, help="events per ht_batch_run")
     p.add_argument("--no-learned", action="store_true")
+    p.add_argument("--no-secondary", action="store_true")
     p.add_argument("--no-vertex", action="store_true")
     p.add_argument("--no-swept", action="store_true")
-    p.add_argument("--no-autotune", action="store_true",
-                   help="default tile widths (a fixed launch sequence, for profiling)")
-    p.add_argument("--tau", type=float, default=0.02, help="proposal region threshold")
-    p.add_argument("--grow", type=int, default=1, help="proposal region growth (0 or 1)")
     p.add_argument("--topk", type=int, default=8, help="regions per hit of the per-hit proposal")
     return p.parse_args()
 
@@ -129,36 +131,46 @@ def measured_peaks():
         return {}
 
 
-def cpu_baseline(g, ev, cap):
-    """The oracle on one event of the workload, on all host cores."""
+def cpu_baseline(name, ev):
+    """The oracle's whole track path on one event of the workload, on all
+    host cores (a bounded sample of the workload)."""
     import oracle
     cores = os.cpu_count() or 1
+    g = synth.track_geometry(name, ev.n_hits)
     t = time.perf_counter()
-    oracle.run_event(g, ev.x, ev.y, ev.z, cap=cap, threads=cores)
+    oracle.run_event_tracks(g, ev.x, ev.y, ev.z, ev.layer, cp=synth.track_of(name),
+                            cap=CAP_OF.get(name), threads=cores)
     dt = time.perf_counter() - t
     return {"value": 1.0 / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
-            "sample": f"1 event of {ev.n_hits} hits (whole path, float64 C oracle, "
+            "sample": f"1 event of {ev.n_hits} hits of {name} (the whole track path: "
+                      f"distinct-layer vote, peaks, confirmation, z vote; float64 C oracle, "
                       f"{cores} threads), {dt:.1f} s"}
 
 
 def run_reference(args):
+    """The reference arm: the float64 CPU oracle (the only reference there is:
+    the reference directory holds the paper alone), one event per step."""
     world, rank, _ = dist_env()
     if rank != 0:
         return
     import oracle
-    cfg = synth.CONFIGS[args.workload]
-    g = dict(cfg["geom"])
-    n_ev = args.events or cfg["events"]
+    name = args.workload
+    cfg = synth.CONFIGS[name]
     cores = os.cpu_count() or 1
-    evs = [synth.make_event(cfg["gen"], cfg["seed0"] + e) for e in range(min(n_ev, args.warmup + args.steps))]
+    n = args.warmup + args.steps
+    evs = [synth.generate(cfg["gen"], cfg["seed0"] + e) for e in range(n)]
+
+    def one(ev):
+        g = synth.track_geometry(name, ev.n_hits)
+        oracle.run_event_tracks(g, ev.x, ev.y, ev.z, ev.layer, cp=synth.track_of(name),
+                                cap=CAP_OF.get(name), threads=cores)
+
     for s in range(args.warmup):
-        ev = evs[s % len(evs)]
-        oracle.run_event(g, ev.x, ev.y, ev.z, cap=CAP_OF.get(args.workload, CAP), threads=cores)
+        one(evs[s])
     times = []
     for s in range(args.steps):
-        ev = evs[(args.warmup + s) % len(evs)]
         t = time.perf_counter()
-        oracle.run_event(g, ev.x, ev.y, ev.z, cap=CAP_OF.get(args.workload, CAP), threads=cores)
+        one(evs[args.warmup + s])
         times.append(time.perf_counter() - t)
     tot = sum(times)
     value = args.steps / tot
@@ -167,35 +179,17 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * tot / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": args.workload, "events_per_step": 1,
-                   "note": "reference arm = plain float64 CPU oracle, one event per step"},
+        "config": {"workload": name, "events_per_step": 1,
+                   "note": "reference arm = plain float64 CPU oracle of the track path, one "
+                           "event of the workload per step"},
         "cpu_baseline": {"value": value, "unit": "events/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{args.steps} events, one per step, {cores} threads"},
+                         "sample": f"{args.steps} events (hits "
+                                   f"{[e.n_hits for e in evs[args.warmup:]]}), one per step, "
+                                   f"{cores} threads"},
         "e2e": {"value": value, "unit": "events/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
-
-
-# DRAM bytes (read + write) per event of the tile kernels, from one ncu
-# capture (profiles/k_assoc32_batch_event100_b4.md), valid only while the
-# kernel sources hash to the value recorded with it.
-PROFILED_TRAFFIC = {
-    "k_assoc32_batch": {"sha": "4e988085e54a9eab", "bytes_per_event": 54.394112e6 / 4},
-}
-KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_tiles.cu",
-                  "paper_1309_6275_gb300/csrc/tiles.cuh",
-                  "paper_1309_6275_gb300/csrc/ht_internal.cuh",
-                  "paper_1309_6275_gb300/csrc/df32.cuh"]
-
-
-def kernel_sha():
-    import hashlib
-    h = hashlib.sha256()
-    for p in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
-    return h.hexdigest()[:16]
 
 
 # Minimal float32 issue slots of one vote: b, rho*c, D (3 FMA/MUL), rsqrt,
@@ -209,119 +203,233 @@ def alu_peak_ops(dev_props, peaks):
     return dev_props.multi_processor_count * 128 * mhz * 1e6
 
 
-def learned_leg(args, ht, flush):
-    """The learned-proposal batched paths against the plain one on the
-    learned configuration's evaluation workload (100 events of the
-    2k-60k-hit batched stream, 25 per batch, resident on the device): the
-    per-event region mask (ht_batch_run_learned) and the per-hit top-k
-    region sets (ht_batch_run_learned_hits).  Events/s of each (same timing
-    rules as the headline), votes cast, candidates and track-finding
-    efficiency over all events."""
+def make_events(name, n_ev, world, rank):
+    """This rank's events: the job is world * n_ev seeded events, split over
+    the ranks by the LPT partition (weak scaling: about n_ev per rank)."""
+    cfg = synth.CONFIGS[name]
+    every = [synth.generate(cfg["gen"], cfg["seed0"] + e) for e in range(world * n_ev)]
+    if world == 1:
+        return list(range(n_ev)), every
+    from paper_1309_6275_gb300 import shard
+    mine = shard.partition([ev.n_hits for ev in every], world)[rank]
+    return mine, [every[e] for e in mine]
+
+
+class TrackRun:
+    """A workload's events as device-resident batches on the track path
+    (ht_batch_run_tracks), optionally with the per-hit learned proposal."""
+
+    def __init__(self, ht, name, events, B):
+        import torch
+        self.ht, self.name, self.events, self.B = ht, name, events, B
+        self.g = synth.track_geometry(name)     # per-event thresholds come from the bands
+        self.G = ht.Geometry(self.g)
+        self.batches = [events[i:i + B] for i in range(0, len(events), B)]
+        self.max_hits = max(sum(e.n_hits for e in b) for b in self.batches)
+        self.cap = CAP_OF[name]
+        self.bt = ht.Batch(self.G, max_events=B, max_hits=self.max_hits, cap=self.cap)
+        self.bt.set_confirm(synth.track_of(name))
+        self.dev = []
+        for b in self.batches:
+            off = np.zeros(len(b) + 1, np.int32)
+            off[1:] = np.cumsum([e.n_hits for e in b])
+            cat = lambda k, t: torch.from_numpy(
+                np.concatenate([getattr(e, k) for e in b]).astype(t)).cuda()
+            self.dev.append((off, cat("x", np.float32), cat("y", np.float32),
+                             cat("z", np.float32), cat("layer", np.uint8)))
+        self.hmasks = torch.empty(self.max_hits, dtype=torch.int64, device="cuda")
+        self.n_hits = sum(e.n_hits for e in events)
+
+    def run(self, d, params=None, topk=8):
+        off, x, y, z, l = d
+        if params is None:
+            self.bt.run_tracks(x, y, z, l, off)
+        else:
+            self.bt.run_tracks(x, y, z, l, off, params_bf16=params, hit_masks=self.hmasks,
+                               topk=topk)
+
+    def step(self, params=None, topk=8):
+        for d in self.dev:
+            self.run(d, params, topk)
+
+    def time_steps(self, steps, warmup, flush, params=None, topk=8):
+        """CUDA-event time (ms) of each of `steps` steps after `warmup`."""
+        import torch
+        for _ in range(warmup):
+            self.step(params, topk)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        out = []
+        for s in range(steps):
+            flush.fill_(s & 0xff)                      # evict L2 before the step
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            self.step(params, topk)
+            b.record(stream)
+            b.synchronize()
+            out.append(a.elapsed_time(b))
+        return out
+
+    def profile(self, params=None, topk=8):
+        """One untimed pass, batch by batch: stage ms, votes, float64 redos,
+        candidates, confirmed candidates and track-finding quality."""
+        import torch
+        from paper_1309_6275_gb300 import quality
+        stages = np.zeros(5)
+        votes = redo = cands = conf = 0
+        rows = []
+        for d, b in zip(self.dev, self.batches):
+            self.run(d, params, topk)
+            torch.cuda.synchronize()
+            stages += np.array(self.bt.stage_ms())
+            ne = len(b)
+            st = self.bt.stats[:2 * ne].view(-1, 2).sum(0).tolist()
+            votes += int(st[0])
+            redo += int(st[1])
+            cnt = self.bt.counts[:ne].cpu().numpy()
+            cands += int(cnt.sum())
+            score = self.bt.score[:ne * self.cap].view(ne, self.cap)
+            conf += int((score > 0).sum().item())
+            off = d[0]
+            asg = self.bt.assign[:int(off[-1])].cpu().numpy()
+            for e, ev in enumerate(b):
+                rows.append(quality.track_quality(self.g, ev, asg[off[e]:off[e + 1]]))
+        q = quality.summarize(rows)
+        n = len(self.events)
+        return dict(stage_ms=stages, votes=votes, redo=redo,
+                    candidates_per_event=cands / n, confirmed_per_event=conf / n,
+                    quality={k: q[k] for k in ("n_rec", "found", "efficiency", "track_cands",
+                                               "fakes", "fake_rate", "duplicates",
+                                               "duplicate_rate")})
+
+    def close(self):
+        self.bt.close()
+        self.G.close()
+
+
+def e2e_run(tr, steps):
+    """End to end through the host-buffer C call (ht_batch_run_tracks_host):
+    every step copies each batch's hits from pinned host memory, runs the
+    track path and copies back the found tracks and the hits' assignments.
+    Returns the JSON object and the per-event quality of the last step."""
     import torch
+    from paper_1309_6275_gb300 import quality
+    hin = []
+    for b in tr.batches:
+        off = np.zeros(len(b) + 1, np.int32)
+        off[1:] = np.cumsum([e.n_hits for e in b])
+        cat = lambda k, t: torch.from_numpy(
+            np.concatenate([getattr(e, k) for e in b]).astype(t)).pin_memory()
+        hin.append((off, cat("x", np.float32), cat("y", np.float32), cat("z", np.float32),
+                    cat("layer", np.uint8)))
+    tcap = tr.B * 16384
+    tracks = torch.zeros((tcap, 8), dtype=torch.int32).pin_memory()
+    ntr = torch.zeros(tr.B, dtype=torch.int32).pin_memory()
+    asg = torch.zeros(tr.max_hits, dtype=torch.int32).pin_memory()
+    h2d = d2h = 0
+
+    def one_step(keep=None):
+        nonlocal h2d, d2h
+        h2d = d2h = 0
+        for i, (off, x, y, z, l) in enumerate(hin):
+            ne, nh = len(off) - 1, int(off[-1])
+            ok = tr.bt.run_tracks_host(x, y, z, l, off, tracks, ntr, asg)
+            assert ok, "track capacity exceeded"
+            nt = int(ntr[:ne].sum())
+            h2d += 13 * nh
+            d2h += 32 * nt + 4 * nh + 4 * (ne + 1)
+            if keep is not None:
+                a = asg[:nh].numpy().copy()
+                for e, ev in enumerate(tr.batches[i]):
+                    keep.append(quality.track_quality(tr.g, ev, a[off[e]:off[e + 1]]))
+
+    rows = []
+    one_step(rows)                       # warm-up, and the quality of what the caller gets
+    tt = []
+    for _ in range(max(1, steps)):
+        t0 = time.perf_counter()
+        one_step()
+        tt.append(time.perf_counter() - t0)
+    q = quality.summarize(rows)
+    return {"value": len(tr.events) * len(tt) / sum(tt), "unit": "events/s",
+            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+            "api": "ht_batch_run_tracks_host: pinned host hits in, found tracks and hit "
+                   "assignments out, synchronous per batch of "
+                   f"{tr.B} events",
+            "efficiency": q["efficiency"], "fake_rate": q["fake_rate"]}
+
+
+STAGES = ["proposal", "vote", "peaks", "confirmation+assignment", "z vote"]
+
+
+def learned_leg(args, tr, plain, flush):
+    """The learned proposal on the track path against the plain track path,
+    on the same events (the learned configuration's evaluation: the batched
+    stream): each hit votes only in its network's top-k regions (computed in
+    the same graph by the tcgen05 forward pass); peaks, confirmation and the
+    z vote are unchanged.  Events/s (same timing rules as the headline) and
+    assignment-level efficiency, fakes, votes and candidates of both."""
     from paper_1309_6275_gb300 import learned
     path = learned.default_weights_path("event100_256")
     if not os.path.exists(path):
         return None
     params, meta = learned.load_weights(path)
     pb = learned.bf16_params(params)
-    name, n_ev, B = "stream2000_256", 100, 25
-    g = synth.geometry_of(name)
-    evs = list(synth.make_stream(name, n_ev, 0))
-    batches = [evs[i:i + B] for i in range(0, n_ev, B)]
-    max_hits = max(sum(e.n_hits for e in b) for b in batches)
-    G = ht.Geometry(g)
-    bt = ht.Batch(G, max_events=B, max_hits=max_hits, cap=CAP)
-    dev_in = []
-    for b in batches:
-        off = np.zeros(len(b) + 1, np.int32)
-        off[1:] = np.cumsum([e.n_hits for e in b])
-        cat = lambda k, t: torch.from_numpy(np.concatenate([getattr(e, k) for e in b]).astype(t)).cuda()
-        dev_in.append((off, cat("x", np.float32), cat("y", np.float32), cat("z", np.float32),
-                       cat("layer", np.uint8)))
-    tune = bt.autotune(dev_in[0][1], dev_in[0][2], dev_in[0][3], dev_in[0][0])
-    masks = torch.empty(B, dtype=torch.int64, device="cuda")
-    hmasks = torch.empty(max_hits, dtype=torch.int64, device="cuda")
-    fmax = 0.6
-
-    def run_one(mode, d):
-        off, x, y, z, l = d
-        if mode == "plain":
-            bt.run(x, y, z, off)
-        elif mode == "learned":
-            bt.run_learned(x, y, z, l, off, pb, masks, args.tau, fmax, args.grow)
-        else:
-            bt.run_learned_hits(x, y, z, l, off, pb, hmasks, args.topk, 0.0)
-
-    out = {}
-    stream = torch.cuda.current_stream()
-    for mode in ("learned", "hits", "plain"):
-        for _ in range(max(1, args.warmup)):
-            for d in dev_in:
-                run_one(mode, d)
-        torch.cuda.synchronize()
-        t = 0.0
-        for s_ in range(max(1, args.steps)):
-            flush.fill_(s_ & 0xff)
-            a = torch.cuda.Event(enable_timing=True)
-            b = torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for d in dev_in:
-                run_one(mode, d)
-            b.record(stream)
-            b.synchronize()
-            t += a.elapsed_time(b) / 1e3
-        out[mode] = {"value": n_ev * max(1, args.steps) / t}
-        # quality over every event (one more pass, batch by batch)
-        q = dict(votes=0, cands=0, n_rec=0, fa=0, fc=0)
-        stages = np.zeros(5)
-        regions = []
-        for d, b in zip(dev_in, batches):
-            run_one(mode, d)
-            torch.cuda.synchronize()
-            stages += np.array(bt.stage_ms())
-            for i, ev in enumerate(b):
-                r = bt.event_results(d[0], i)
-                nr, fa, fc = learned.efficiency(g, ev, r["peaks"], r["assign"])
-                q["votes"] += r["votes"]; q["cands"] += r["count"]
-                q["n_rec"] += nr; q["fa"] += fa; q["fc"] += fc
-            if mode == "learned":
-                regions += [int(v) & ((1 << 64) - 1) for v in masks[:len(b)].cpu().tolist()]
-        q["stage_ms_per_event"] = [round(v / n_ev, 4) for v in stages]
-        out[mode].update(q)
-        if mode == "learned":
-            out[mode]["mean_regions"] = float(np.mean([bin(m).count("1") for m in regions]))
-            out[mode]["fallback_frac"] = float(np.mean([m == (1 << 64) - 1 for m in regions]))
-    bt.close()
-    G.close()
-    L, P, H = out["learned"], out["plain"], out["hits"]
-    eff = lambda r, k: r[k] / max(r["n_rec"], 1)
-    per_hit = {"value": H["value"], "unit": "events/s", "speedup": H["value"] / P["value"],
-               "topk": args.topk, "pmin": 0.0,
-               "vote_frac": H["votes"] / max(P["votes"], 1),
-               "candidate_frac": H["cands"] / max(P["cands"], 1),
-               "eff_candidate": eff(H, "fc"), "eff_assign": eff(H, "fa"),
-               "stage_ms_per_event": H["stage_ms_per_event"],
-               "path": "ht_batch_run_learned_hits (proposal MLP top-k per hit + per-hit "
-                       "restricted vote in one graph)"}
-    return {"value": L["value"], "unit": "events/s", "plain_value": P["value"],
-            "speedup": L["value"] / P["value"],
-            "workload": f"{name}: {n_ev} events of the 2k-60k-hit stream, {B} per batch",
-            "autotune": tune,
-            "vote_frac": L["votes"] / max(P["votes"], 1),
-            "candidate_frac": L["cands"] / max(P["cands"], 1),
-            "eff_candidate": {"plain": eff(P, "fc"), "learned": eff(L, "fc")},
-            "eff_assign": {"plain": eff(P, "fa"), "learned": eff(L, "fa")},
-            "quality_sample": f"all {n_ev} events, {P['n_rec']} reconstructable tracks",
-            "mean_regions": L["mean_regions"], "fallback_frac": L["fallback_frac"],
-            "stage_ms_per_event": {"stages": ["proposal", "vote", "peaks+lists", "association",
-                                              "decode+z"],
-                                   "plain": P["stage_ms_per_event"],
-                                   "learned": L["stage_ms_per_event"]},
-            "tau": args.tau, "fmax": fmax, "grow": args.grow,
-            "per_hit": per_hit,
-            "path": "ht_batch_run_learned (proposal MLP + masked vote/peaks in one graph)",
+    ms = tr.time_steps(max(1, args.steps), max(1, args.warmup), flush, params=pb, topk=args.topk)
+    prof = tr.profile(params=pb, topk=args.topk)
+    n = len(tr.events)
+    value = n * len(ms) / (sum(ms) / 1e3)
+    P, L = plain["quality"], prof["quality"]
+    return {"value": value, "unit": "events/s", "plain_value": plain["value"],
+            "speedup": value / plain["value"],
+            "workload": f"{tr.name}: the headline's {n} events",
+            "efficiency": {"plain": P["efficiency"], "learned": L["efficiency"],
+                           "difference_points": 100.0 * (L["efficiency"] - P["efficiency"])},
+            "fake_rate": {"plain": P["fake_rate"], "learned": L["fake_rate"]},
+            "quality": {"plain": P, "learned": L},
+            "vote_frac": prof["votes"] / max(plain["votes"], 1),
+            "candidate_frac": prof["candidates_per_event"] / max(plain["candidates_per_event"], 1),
+            "stage_ms_per_event": {"stages": STAGES,
+                                   "plain": [round(v / n, 4) for v in plain["stage_ms"]],
+                                   "learned": [round(v / n, 4) for v in prof["stage_ms"]]},
+            "topk": args.topk, "pmin": 0.0,
+            "path": "ht_batch_run_tracks with a per-hit proposal (MLP top-k per hit, then the "
+                    "per-hit restricted distinct-layer vote, in one graph)",
             "weights": os.path.relpath(path, ROOT),
             "trained_on": f"{meta.get('n_events')} {meta.get('workload')} events"}
+
+
+def secondary_leg(args, ht, name, flush):
+    """Another configuration on the track path: events/s, hit-votes/s, stage
+    split, vote roofline fraction and track-finding quality."""
+    import torch
+    cfg = synth.CONFIGS[name]
+    evs = [synth.generate(cfg["gen"], cfg["seed0"] + e) for e in range(cfg["events"])]
+    tr = TrackRun(ht, name, evs, BATCH_OF[name])
+    ms = tr.time_steps(max(1, args.steps), max(1, args.warmup), flush)
+    prof = tr.profile()
+    n = len(evs)
+    t = sum(ms) / 1e3
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak_ops = alu_peak_ops(props, measured_peaks())
+    vote_s = prof["stage_ms"][1] / 1e3
+    g = tr.g
+    tk = synth.track_of(name)
+    out = {"value": n * len(ms) / t, "unit": "events/s", "events": n,
+           "hits_per_event": tr.n_hits / n,
+           "hit_votes_per_s": prof["votes"] / (prof["stage_ms"].sum() / 1e3),
+           "geometry": f"{g['n_rho']}x{g['n_d0']}x{g['n_phi0']} uint16, T={tk['threshold']} "
+                       f"layers, pool {tk['pool']}, {tk['min_layers']} inlier layers within "
+                       f"{tk['tol'] * 1e4:.0f} um",
+           "stage_ms_per_event": {s: round(v / n, 4) for s, v in zip(STAGES, prof["stage_ms"])},
+           "vote_alu_frac": OPS_PER_VOTE * prof["votes"] / vote_s / peak_ops,
+           "candidates_per_event": prof["candidates_per_event"],
+           "confirmed_per_event": prof["confirmed_per_event"],
+           "quality": prof["quality"],
+           "path": f"ht_batch_run_tracks, {tr.B} events per batch"}
+    tr.close()
+    return out
 
 
 def swept_leg(args):
@@ -461,14 +569,31 @@ def vertex_leg(args):
             "path": "ht_batch_run then ht_vertex_vote + ht_vertex_find, 25 events per batch"}
 
 
-def make_batches(cfg, n_ev, world, rank, B):
-    """This rank's events: the job is world * n_ev seeded events, split over
-    the ranks by the LPT partition (weak scaling: about n_ev per rank)."""
-    from paper_1309_6275_gb300 import shard
-    every = [synth.make_event(cfg["gen"], cfg["seed0"] + e) for e in range(world * n_ev)]
-    mine = shard.partition([ev.n_hits for ev in every], world)[rank]
-    events = [every[e] for e in mine]
-    return mine, events, [events[i:i + B] for i in range(0, len(events), B)]
+# DRAM bytes (read + write) per event of the dominant kernel, from one ncu
+# capture, valid only while the kernel sources hash to the recorded value.
+PROFILED_TRAFFIC = {}
+KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_vote_layers.cu",
+                  "paper_1309_6275_gb300/csrc/tiles.cuh",
+                  "paper_1309_6275_gb300/csrc/ht_internal.cuh",
+                  "paper_1309_6275_gb300/csrc/df32.cuh"]
+
+
+def kernel_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for p in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def launches_per_batch(ne, learned=False):
+    """Kernels one ht_batch_run_tracks replays: hit lists (count, 3-kernel
+    scan, fill), the vote, per event two peak passes and a 3-kernel scan,
+    the confirmation (prefix, grouping 2 + scan 3, hit index 3 + scan 3,
+    confirmation, offers, decode) and the z vote (4 + scan 3); with the
+    proposal one more (the network's top-k per hit)."""
+    return 5 + 1 + 5 * ne + 15 + 7 + (1 if learned else 0)
 
 
 def run_ours(args):
@@ -481,85 +606,31 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1309_6275_gb300 import ht
 
-    cfg = synth.CONFIGS[args.workload]
-    g = dict(cfg["geom"])
-    n_ev = args.events or cfg["events"]
-    B = args.batch
-    ids, events, batches = make_batches(cfg, n_ev, world, rank, B)
-    n_job = world * n_ev           # events of the whole job per step
-    n_ev = len(events)             # this rank's share
-    G = ht.Geometry(g)
-    cap = CAP_OF.get(args.workload, CAP)
-    max_hits = max(sum(ev.n_hits for ev in b) for b in batches)
-    bt = ht.Batch(G, max_events=B, max_hits=max_hits, cap=cap)
-    # inputs resident in HBM: one concatenated x, y, z per batch
-    dev_in = []
-    for b in batches:
-        off = np.zeros(len(b) + 1, np.int32)
-        off[1:] = np.cumsum([ev.n_hits for ev in b])
-        cat = [torch.from_numpy(np.concatenate([getattr(ev, k) for ev in b])).cuda() for k in "xyz"]
-        dev_in.append((off, cat))
+    name = args.workload
+    n_ev = args.events or synth.CONFIGS[name]["events"]
+    B = args.batch or BATCH_OF.get(name, 50)
+    ids, events = make_events(name, n_ev, world, rank)
+    n_job = world * n_ev
+    n_ev = len(events)
+    tr = TrackRun(ht, name, events, B)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    stream = torch.cuda.current_stream()
-    n_hits_total = sum(ev.n_hits for ev in events)
-    tune = None if args.no_autotune else bt.autotune(dev_in[0][1][0], dev_in[0][1][1],
-                                                     dev_in[0][1][2], dev_in[0][0])
 
-    stage_tot = np.zeros(5)
-    votes_total = 0
-    redo_total = 0
-
-    def step(record=False):
-        nonlocal votes_total, redo_total
-        for off, (x, y, z) in dev_in:
-            bt.run(x, y, z, off)
-            if record:
-                torch.cuda.current_stream().synchronize()
-                stage_tot[:] += np.array(bt.stage_ms())
-                st = bt.stats[:2 * (len(off) - 1)].view(-1, 2).sum(0).tolist()
-                votes_total += int(st[0])
-                redo_total += int(st[1])
-
-    for _ in range(args.warmup):        # the same code path as the timed steps
-        step(record=True)
-    stage_tot[:] = 0.0
-    votes_total = 0
-    redo_total = 0
+    for _ in range(args.warmup):
+        tr.step()
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-
     clocks = ClockSampler(local)
     if rank == 0:
         clocks.start()
         time.sleep(1.5)          # let nvidia-smi's start-up pass before the timed region
-    step_ms = []
-    for s in range(args.steps):
-        flush.fill_(s & 0xff)                          # evict L2 before the step
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        step(record=True)
-        b.record(stream)
-        b.synchronize()
-        step_ms.append(a.elapsed_time(b))
+    step_ms = tr.time_steps(args.steps, 0, flush)
     torch.cuda.synchronize()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
     clk = clocks.stop() if rank == 0 else None
-
-    # per-event results to rank 0 (the only collective; outside the timing)
-    from paper_1309_6275_gb300 import shard
-    local = {}
-    for (off, (x, y, z)), b, base in zip(dev_in, batches, range(0, n_ev, B)):
-        bt.run(x, y, z, off)
-        cnt = bt.counts[:len(b)].cpu().tolist()
-        for i in range(len(b)):
-            local[int(ids[base + i])] = int(cnt[i])
-    gathered = shard.gather_results(local)
-
     total_s = sum(step_ms) / 1e3
     t = torch.tensor([total_s], dtype=torch.float64, device="cuda")
     if dist:
@@ -567,190 +638,119 @@ def run_ours(args):
     max_s = float(t.item())
     value = n_job * args.steps / max_s
 
-    # ---- e2e: hits from pinned host memory, results read back, per batch.
-    # Two batch objects alternate: batch i's results go to the host on a copy
-    # stream while batch i + 1 runs on the compute stream.
+    plain = tr.profile()
+    plain["value"] = n_ev * args.steps / total_s
+
+    # per-event track counts to rank 0 (the only collective; outside the timing)
+    from paper_1309_6275_gb300 import shard
+    mine = {}
+    for d, b, base in zip(tr.dev, tr.batches, range(0, n_ev, B)):
+        tr.run(d)
+        ne = len(b)
+        score = tr.bt.score[:ne * tr.cap].view(ne, tr.cap)
+        conf = (score > 0).sum(1).cpu().tolist()
+        for i in range(ne):
+            mine[int(ids[base + i])] = int(conf[i])
+    gathered = shard.gather_results(mine)
+
     e2e = None
     if not args.no_e2e:
-        hin = [(off, [torch.from_numpy(np.concatenate([getattr(ev, k) for ev in b])).pin_memory()
-                      for k in "xyz"]) for b, (off, _) in zip(batches, dev_in)]
-        bts = [bt, ht.Batch(G, max_events=B, max_hits=max_hits, cap=cap)]
-        if tune is not None:
-            bts[1].autotune(dev_in[0][1][0], dev_in[0][1][1], dev_in[0][1][2], dev_in[0][0])
-        cs, xs = torch.cuda.Stream(), torch.cuda.Stream()
-        dbuf = [[torch.empty(max_hits, dtype=torch.float32, device="cuda") for _ in range(3)]
-                for _ in range(2)]
-        hp = [torch.empty((B * cap, 4), dtype=torch.int32).pin_memory() for _ in range(2)]
-        hz = [torch.empty((B * cap, 3), dtype=torch.int32).pin_memory() for _ in range(2)]
-        ha = [torch.empty(max_hits, dtype=torch.int32).pin_memory() for _ in range(2)]
-        hc = [torch.empty(B, dtype=torch.int32).pin_memory() for _ in range(2)]
-        h2d = 12 * n_hits_total
-        d2h = 0
-
-        def drain(slot, ne, nh, done):
-            nonlocal d2h
-            done.synchronize()                      # this batch's counts are on the host
-            with torch.cuda.stream(xs):
-                b_ = bts[slot]
-                ha[slot][:nh].copy_(b_.assign[:nh], non_blocking=True)
-                d2h += 4 * ne + 4 * nh
-                for e in range(ne):
-                    k = min(int(hc[slot][e]), cap)
-                    hp[slot][e * cap:e * cap + k].copy_(b_.peaks[e * cap:e * cap + k],
-                                                        non_blocking=True)
-                    hz[slot][e * cap:e * cap + k].copy_(b_.zres[e * cap:e * cap + k],
-                                                        non_blocking=True)
-                    d2h += 28 * k
-            xs.synchronize()
-
-        def e2e_step():
-            nonlocal d2h
-            d2h = 0
-            pending = None
-            for i, (off, hx) in enumerate(hin):
-                slot, nh, ne = i % 2, int(off[-1]), len(off) - 1
-                with torch.cuda.stream(cs):
-                    for d, h in zip(dbuf[slot], hx):
-                        d[:nh].copy_(h, non_blocking=True)
-                    bts[slot].run(dbuf[slot][0], dbuf[slot][1], dbuf[slot][2], off, stream=cs)
-                    hc[slot][:ne].copy_(bts[slot].counts[:ne], non_blocking=True)
-                    done = torch.cuda.Event()
-                    done.record(cs)
-                if pending:
-                    drain(*pending)                 # overlaps this batch's compute
-                pending = (slot, ne, nh, done)
-            drain(*pending)
-            cs.synchronize()
-
-        e2e_step()
-        tt = []
-        for s in range(max(1, args.steps)):
-            t0 = time.perf_counter()
-            e2e_step()
-            tt.append(time.perf_counter() - t0)
-        et = torch.tensor([sum(tt)], dtype=torch.float64, device="cuda")
+        e2e = e2e_run(tr, args.steps)
+        et = torch.tensor([n_ev / e2e["value"]], dtype=torch.float64, device="cuda")
         if dist:
             dist.all_reduce(et, op=dist.ReduceOp.MAX)
-        e2e = {"value": n_job * len(tt) / float(et.item()), "unit": "events/s",
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-               "api": "ht_batch_run with host copies of hits in and every result out; two "
-                      "batch objects, each batch's results copied out while the next runs"}
-        bts[1].close()
+        e2e["value"] = n_job / float(et.item())
 
     if rank != 0:
+        tr.close()
         if dist:
             dist.destroy_process_group()
         return
 
-    # ---- secondary figures: the single-event C-ABI calls on the same events
-    single = None
-    if not args.no_single:
-        pipe = ht.EventPipeline(G, max(ev.n_hits for ev in events), cap)
-        dev1 = [tuple(torch.from_numpy(getattr(ev, k)).cuda() for k in "xyz") for ev in events]
-        for (x, y, z) in dev1[:2]:
-            pipe.run(x, y, z)
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for (x, y, z) in dev1:
-            pipe.run(x, y, z)
-        b.record()
-        b.synchronize()
-        single = n_ev / (a.elapsed_time(b) / 1e3)
-
-    learned_res = None
-    if not args.no_learned:
-        learned_res = learned_leg(args, ht, flush)
-
-    swept_res = None
-    if not args.no_swept:
-        swept_res = swept_leg(args)
-
-    vertex_res = None
-    if not args.no_vertex:
-        vertex_res = vertex_leg(args)
+    learned_res = None if args.no_learned else learned_leg(args, tr, plain, flush)
+    secondary = {}
+    if not args.no_secondary:
+        for nm in SECONDARY:
+            if nm != name:
+                secondary[nm] = secondary_leg(args, ht, nm, flush)
+    swept_res = None if args.no_swept else swept_leg(args)
+    vertex_res = None if args.no_vertex else vertex_leg(args)
 
     props = torch.cuda.get_device_properties(local)
     peaks = measured_peaks()
     peak_ops = alu_peak_ops(props, peaks)
-    names = ["proposal", "vote", "peaks+candidate lists", "association", "decode+z vote"]
-    stage_s = stage_tot / 1e3
+    stage_s = plain["stage_ms"] / 1e3
     dom = int(np.argmax(stage_s))
-    dom_kernel = {1: "k_vote_batch", 3: "k_assoc32_batch"}.get(dom, names[dom])
-    achieved = OPS_PER_VOTE * votes_total / stage_s[dom] if dom in (1, 3) else None
-    atom_rate = ht.ht_probe_shared_atomic_rate(1 << 14)
-    prof = PROFILED_TRAFFIC.get(dom_kernel)
-    traffic = (prof["bytes_per_event"] * B if prof and prof["sha"] == kernel_sha() else None)
-    roof = {"bound": "alu", "kernel": dom_kernel,
-            "achieved": achieved / 1e9 if achieved else None,
-            "peak": peak_ops / 1e9, "unit": "Gop/s",
-            "frac": achieved / peak_ops if achieved else None,
-            "traffic": traffic,
-            "traffic_note": "ncu dram__bytes_read+write of a 4-event launch scaled to the "
-                            f"{B}-event launch (profiles/k_assoc32_batch_event100_b4.md)",
-            "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 lanes x "
-                           f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz (issue-limited), "
-                           f"{OPS_PER_VOTE} algorithmic ops per vote",
-            "stage_ms_per_event": {n: 1e3 * v / (args.steps * n_ev) for n, v in zip(names, stage_s)},
-            "vote_share_of_step": stage_s[1] / total_s,
-            "shared_atomic_frac_of_vote": (votes_total / stage_s[1]) / atom_rate,
-            "shared_atomic_peak_gops": atom_rate / 1e9,
-            "float64_redo_per_vote": redo_total / max(votes_total, 1),
-            # the HBM side of the path: two peak passes each read the accumulator
-            # once (the vote's own write of it is one more pass), against the
-            # measured copy bandwidth
-            "hbm_peaks_stage": {
-                "algorithmic_bytes_per_event": 2 * g["n_rho"] * g["n_d0"] * g["n_phi0"] * 2,
-                "achieved_gbs": (2 * g["n_rho"] * g["n_d0"] * g["n_phi0"] * 2) /
-                                (stage_s[2] / (args.steps * n_ev)) / 1e9,
-                "peak_gbs": peaks.get("hbm_gbs", 6800.0),
-                "frac": (2 * g["n_rho"] * g["n_d0"] * g["n_phi0"] * 2) /
-                        (stage_s[2] / (args.steps * n_ev)) / 1e9 /
-                        peaks.get("hbm_gbs", 6800.0),
-                "note": "peaks + candidate-list stage time; the stage is issue-bound "
-                        "(profiles/k_peaks_event100.md)"}}
-    # kernels one ht_batch_run replays (counted from the ncu launch list of a
-    # fixed sequence): per batch the hit lists (2 + a 3-kernel scan), two vote
-    # launches (packed and unpacked events), association and its decode, the
-    # z vote (4) and its scan (3); per event two peak passes, two
-    # candidate-list histograms and two 3-kernel scans
-    launches_per_batch = lambda ne: 16 + 10 * ne
+    votes = plain["votes"]
+    g = tr.g
+    cells = g["n_rho"] * g["n_d0"] * g["n_phi0"]
+    roof = {"kernel": {1: "k_vote_batch (distinct-layer mode)", 3: "k_confirm"}.get(dom, STAGES[dom]),
+            "stage_ms_per_event": {s: round(1e3 * v / n_ev, 4) for s, v in zip(STAGES, stage_s)}}
+    if dom == 1:
+        achieved = OPS_PER_VOTE * votes / stage_s[1]
+        prof = PROFILED_TRAFFIC.get("k_vote_batch")
+        atom = ht.ht_probe_shared_atomic_rate(1 << 14)
+        roof.update({"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
+                     "unit": "Gop/s", "frac": achieved / peak_ops,
+                     "traffic": (prof["bytes_per_event"] * B
+                                 if prof and prof["sha"] == kernel_sha() else None),
+                     "peak_source": f"derived: {props.multi_processor_count} SMs x 128 FP32 "
+                                    f"lanes x {peaks.get('sm_max_mhz', 2070.0):.0f} MHz "
+                                    f"(issue-limited), {OPS_PER_VOTE} algorithmic ops per vote",
+                     "shared_atomic_frac": (votes / stage_s[1]) / atom,
+                     "shared_atomic_peak_gops": atom / 1e9})
+    else:
+        roof.update({"bound": "alu", "achieved": None, "peak": peak_ops / 1e9, "unit": "Gop/s",
+                     "frac": None, "traffic": None,
+                     "note": "the dominant stage is not the vote; its work has no "
+                             "algorithmic op count here"})
+    roof["float64_redo_per_vote"] = plain["redo"] / max(votes, 1)
+    roof["hbm_peaks_stage"] = {
+        "algorithmic_bytes_per_event": 2 * cells * 2,
+        "achieved_gbs": 2 * cells * 2 / (stage_s[2] / n_ev) / 1e9,
+        "peak_gbs": peaks.get("hbm_gbs", 6800.0),
+        "frac": 2 * cells * 2 / (stage_s[2] / n_ev) / 1e9 / peaks.get("hbm_gbs", 6800.0),
+        "note": "peak finding reads each accumulator twice (count and write passes)"}
+    tk = synth.track_of(name)
     line = {
         "metric": METRIC, "value": value, "unit": "events/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
         "data": "synthetic (seeded detector MC)",
-        "config": {"workload": args.workload, "events_per_step": n_job,
-                   "hits_per_step": n_hits_total,
+        "config": {"workload": name, "events_per_step": n_job, "hits_per_step": tr.n_hits,
                    "geometry": f"{g['n_rho']}x{g['n_d0']}x{g['n_phi0']} uint16, "
-                               f"{g['n_z0']}x{g['n_cot']} z grid, T={g['threshold']}",
-                   "path": f"ht_batch_run, {B} events per batch, CUDA graph replay",
-                   "autotune": tune,
-                   "l2": "flushed (256 MiB write) before each timed step",
-                   "parallelism": f"events sharded (LPT by hits), {world} rank(s), no "
-                                  "data-path collective; per-event results gathered to "
-                                  "rank 0 after timing"},
-        "hit_votes_per_s": world * votes_total / max_s,
+                               f"{g['n_z0']}x{g['n_cot']} z grid",
+                   "track": {"threshold_bands": tk["bands"], "threshold_else": tk["threshold"],
+                             "pool": tk["pool"], "min_layers": tk["min_layers"],
+                             "tol_cm": tk["tol"]},
+                   "path": f"ht_batch_run_tracks, {B} events per batch, CUDA graph replay",
+                   "l2": "inputs larger than L2, and flushed (256 MiB write) before each timed step",
+                   "parallelism": f"events sharded (LPT by hits), {world} rank(s), no data-path "
+                                  "collective; per-event track counts gathered to rank 0 "
+                                  "after timing"},
+        "hit_votes_per_s": world * votes / (plain["stage_ms"].sum() / 1e3),
         "step_ms": [round(v, 3) for v in step_ms],
-        "gpu_launches": args.steps * sum(launches_per_batch(len(b)) for b in batches),
+        "gpu_launches": args.steps * sum(launches_per_batch(len(b)) for b in tr.batches),
+        "candidates_per_event": plain["candidates_per_event"],
+        "confirmed_per_event": plain["confirmed_per_event"],
+        "quality": plain["quality"],
         "roofline": roof,
         "clocks": clk,
     }
     if gathered is not None:
         line["events_gathered"] = len(gathered)
-    if single:
-        line["single_event_api_events_per_s"] = single
-    if learned_res:
-        line["learned"] = learned_res
-    if vertex_res:
-        line["displaced_jets"] = vertex_res
-    if swept_res:
-        line["swept_vote"] = swept_res
     if e2e:
         line["e2e"] = e2e
+    if learned_res:
+        line["learned"] = learned_res
+    line.update(secondary)
+    if swept_res:
+        line["swept_vote"] = swept_res
+    if vertex_res:
+        line["displaced_jets"] = vertex_res
     if world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, events[0], CAP_OF.get(args.workload, CAP))
+        line["cpu_baseline"] = cpu_baseline(name, events[0])
+    tr.close()
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()

@@ -634,6 +634,42 @@ ht_status ht_batch_run_tracks(ht_batch *b, const float *x, const float *y, const
                               int32_t *counts, int32_t *score, int32_t *assign, ht_zres *zres,
                               uint64_t *stats, ht_stream stream);
 
+/* A found track: a confirmed candidate and its (z0, cot theta) result. */
+typedef struct ht_track_out {
+    int32_t i_rho, j_d0, k_phi0;   /* the candidate's cell */
+    int32_t count;                 /* its distinct-layer count */
+    int32_t score;                 /* inlier layers of its confirmation */
+    int32_t n_z0, m_cot, zcount;   /* its (z0, cot theta) vote result */
+} ht_track_out;
+
+/* ht_batch_run_tracks from HOST buffers, synchronous: copies the hits to
+ * the device, runs the track path on `stream`, keeps each event's confirmed
+ * candidates (score > 0, in candidate order) as its tracks, copies back only
+ * the tracks and the hits' assignments to them, and synchronises the stream
+ * before returning.
+ *   hx, hy, hz, hlayer   host arrays of h_off[n_events] hits (float32, and
+ *                        uint8 layers); pinned memory copies faster.
+ *   prop        NULL or a per-hit proposal (as ht_batch_run_tracks); its
+ *               params_bf16 is DEVICE memory and its layer field is ignored
+ *               (the copied layers are used).
+ *   h_tracks    host, track_cap entries: event e's tracks follow those of
+ *               events 0 .. e - 1.
+ *   h_ntracks   host, n_events int32: each event's number of tracks.
+ *   h_assign    host, h_off[n_events] int32: the index of the hit's track
+ *               within its event's tracks, -1 for none.
+ *   h_stats     host, NULL or 2 * n_events uint64 (as ht_batch_run).
+ * The first call allocates the device buffers it needs (hits for max_hits,
+ * candidates for max_events * cap).  When all events' tracks exceed
+ * track_cap, the first track_cap are copied, h_ntracks still gives every
+ * event's total and the call returns HT_ERR_CAPACITY.  Requires
+ * ht_batch_set_confirm.  Errors: as ht_batch_run_tracks. */
+ht_status ht_batch_run_tracks_host(ht_batch *b, const float *hx, const float *hy,
+                                   const float *hz, const uint8_t *hlayer, const int32_t *h_off,
+                                   int32_t n_events, const ht_hit_proposal *prop,
+                                   ht_track_out *h_tracks, int32_t track_cap,
+                                   int32_t *h_ntracks, int32_t *h_assign, uint64_t *h_stats,
+                                   ht_stream stream);
+
 /* Device time of the stages of the last completed batch run, in ms: ms[0]
  * proposal (0 without one), ms[1] vote, ms[2] peak finding and candidate
  * lists, ms[3] association, ms[4] assignment decode and (z0, cot theta)

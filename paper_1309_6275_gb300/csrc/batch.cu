@@ -139,6 +139,19 @@ struct ht_batch {
     bool conf_set;
     int *inl;               // track path: 16 inlier hits per candidate slot
     char *cf_ws;            // track path: confirmation scratch
+    struct HostPath {       // buffers of ht_batch_run_tracks_host (allocated on first use)
+        float *x, *y, *z;
+        uint8_t *layer;
+        unsigned long long *hmasks;
+        ht_peak *peaks;
+        ht_zres *zres;
+        int *counts, *score, *assign, *assign_c, *tfirst, *ntot;
+        uint64_t *stats;
+        ht_track_out *tracks;
+        int tcap;
+        char *ws;
+        int *h_small;       // pinned: tfirst and the total
+    } hp;
     GraphEntry cache[kGraphCache];
     int ncache;
     bool use_graph;
@@ -172,6 +185,13 @@ void free_batch(ht_batch *b)
     cudaFree(b->bk_ws);
     cudaFree(b->inl);
     cudaFree(b->cf_ws);
+    {
+        ht_batch::HostPath &h = b->hp;
+        void *bufs[] = {h.x, h.y, h.z, h.layer, h.hmasks, h.peaks, h.zres, h.counts, h.score,
+                        h.assign, h.assign_c, h.tfirst, h.ntot, h.stats, h.tracks, h.ws};
+        for (void *q : bufs) cudaFree(q);
+        if (h.h_small) cudaFreeHost(h.h_small);
+    }
     if (b->h_meta) cudaFreeHost(b->h_meta);
     if (b->meta_done) cudaEventDestroy(b->meta_done);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
@@ -630,6 +650,105 @@ ht_status ht_batch_run_tracks(ht_batch *b, const float *x, const float *y, const
     R.layer = layer;
     R.score = score;
     return run_impl(b, x, y, z, h_off, n_events, R, peaks, counts, assign, zres, stats, stream);
+}
+
+ht_status ht_batch_run_tracks_host(ht_batch *b, const float *hx, const float *hy,
+                                   const float *hz, const uint8_t *hlayer, const int32_t *h_off,
+                                   int32_t n_events, const ht_hit_proposal *prop,
+                                   ht_track_out *h_tracks, int32_t track_cap,
+                                   int32_t *h_ntracks, int32_t *h_assign, uint64_t *h_stats,
+                                   ht_stream stream)
+{
+    if (!b || !hx || !hy || !hz || !hlayer || !h_ntracks || !h_assign ||
+        (track_cap > 0 && !h_tracks) || track_cap < 0)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run_tracks_host: null argument");
+    if (!b->conf_set)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run_tracks_host: ht_batch_set_confirm not called");
+    if (n_events < 1 || n_events > b->max_events)
+        return ht::set_error(HT_ERR_ARG, "ht_batch_run_tracks_host: n_events out of range");
+    ht_status s = check_offsets(b, h_off, n_events);
+    if (s != HT_OK) return s;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    ht_batch::HostPath &h = b->hp;
+    const size_t ne = (size_t)b->max_events, mh = (size_t)b->max_hits, nc = ne * b->cap;
+    if (!h.x) {
+        h.tcap = (int)std::min<size_t>(nc, ne * 16384);
+        cudaError_t e = cudaSuccess;
+        auto M = [&](void **q, size_t bytes) {
+            if (e == cudaSuccess) e = cudaMalloc(q, bytes);
+        };
+        M((void **)&h.x, mh * 4);
+        M((void **)&h.y, mh * 4);
+        M((void **)&h.z, mh * 4);
+        M((void **)&h.layer, mh);
+        M((void **)&h.hmasks, mh * 8);
+        M((void **)&h.peaks, nc * sizeof(ht_peak));
+        M((void **)&h.zres, nc * sizeof(ht_zres));
+        M((void **)&h.counts, ne * 4);
+        M((void **)&h.score, nc * 4);
+        M((void **)&h.assign, mh * 4);
+        M((void **)&h.assign_c, mh * 4);
+        M((void **)&h.tfirst, (ne + 1) * 4);
+        M((void **)&h.ntot, 16);
+        M((void **)&h.stats, ne * 16);
+        M((void **)&h.tracks, (size_t)h.tcap * sizeof(ht_track_out));
+        M((void **)&h.ws, ht::track_compact_bytes(b->max_events, b->cap));
+        if (e == cudaSuccess) e = cudaMallocHost((void **)&h.h_small, (ne + 2) * 4);
+        if (e != cudaSuccess) {
+            void *bufs[] = {h.x, h.y, h.z, h.layer, h.hmasks, h.peaks, h.zres, h.counts,
+                            h.score, h.assign, h.assign_c, h.tfirst, h.ntot, h.stats, h.tracks,
+                            h.ws};
+            for (void *q : bufs) cudaFree(q);
+            if (h.h_small) cudaFreeHost(h.h_small);
+            h = ht_batch::HostPath{};
+            return ht::set_error(HT_ERR_CUDA, "ht_batch_run_tracks_host: allocation failed");
+        }
+    }
+    const size_t n = (size_t)h_off[n_events];
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(h.x, hx, n * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.y, hy, n * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.z, hz, n * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h.layer, hlayer, n, cudaMemcpyHostToDevice, st);
+    }
+    if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, "ht_batch_run_tracks_host: copy in");
+    ht_hit_proposal pcopy{};
+    Restrict R{};
+    R.layer = h.layer;
+    R.score = h.score;
+    if (prop) {
+        pcopy = *prop;
+        pcopy.layer = h.layer;
+        R.hprop = &pcopy;
+        R.hit_masks = h.hmasks;
+    }
+    s = run_impl(b, h.x, h.y, h.z, h_off, n_events, R, h.peaks, h.counts, h.assign, h.zres,
+                 h_stats ? h.stats : nullptr, stream);
+    if (s != HT_OK) return s;
+    e = ht::launch_track_compact(off_of(b->meta), b->meta + 2, b->max_events, b->max_hits,
+                                 h.peaks, h.counts, b->cap, h.score, h.zres, h.assign, h.tracks,
+                                 h.tcap, h.tfirst, h.ntot, h.assign_c, h.ws, b->sms, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h.h_small, h.tfirst, (size_t)(n_events + 1) * 4,
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+    const int total = h.h_small[n_events];
+    for (int ev = 0; ev < n_events; ++ev) h_ntracks[ev] = h.h_small[ev + 1] - h.h_small[ev];
+    const int ncopy = std::min(total, std::min(track_cap, h.tcap));
+    if (ncopy > 0)
+        e = cudaMemcpyAsync(h_tracks, h.tracks, (size_t)ncopy * sizeof(ht_track_out),
+                            cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && n > 0)
+        e = cudaMemcpyAsync(h_assign, h.assign_c, n * 4, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess && h_stats)
+        e = cudaMemcpyAsync(h_stats, h.stats, (size_t)n_events * 16, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
+    if (total > track_cap || total > h.tcap)
+        return ht::set_error(HT_ERR_CAPACITY, "ht_batch_run_tracks_host: more tracks than track_cap");
+    return HT_OK;
 }
 
 ht_status ht_batch_stage_ms(const ht_batch *b, float *ms)

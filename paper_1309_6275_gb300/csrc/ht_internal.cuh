@@ -416,6 +416,16 @@ struct ConfirmDev {
 // assign (batch hit index) written.  ws: confirm_workspace_bytes.
 size_t confirm_workspace_bytes(const DevGeom &G, int max_events, int max_hits, int cap);
 cudaError_t prepare_confirm_kernels();
+// Compact found tracks of a batch (k_confirm.cu): tracks[tfirst[e] ..
+// tfirst[e + 1]) are event e's confirmed candidates in candidate order (the
+// first tcap of all written), *ntot their total, assign_out each hit's index
+// into its event's tracks (-1 none).  ws: track_compact_bytes.
+size_t track_compact_bytes(int max_events, int cap);
+cudaError_t launch_track_compact(const int *off, const int *d_nev, int max_events, int max_hits,
+                                 const ht_peak *peaks, const int *counts, int cap,
+                                 const int *score, const ht_zres *zres, const int *assign,
+                                 ht_track_out *tracks, int tcap, int *tfirst, int *ntot,
+                                 int *assign_out, void *ws, int sms, cudaStream_t st);
 cudaError_t launch_confirm_batch(const DevGeom &G, const ConfirmDev &P, const float *x,
                                  const float *y, const uint8_t *layer, const int *off,
                                  const int *d_nev, int max_events, int max_hits,

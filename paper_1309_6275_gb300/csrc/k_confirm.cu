@@ -16,12 +16,18 @@
 // Then each hit goes to the confirmed candidate that lists it with the most
 // inlier layers, ties to the smallest candidate index.
 //
-// One warp per candidate, persistent over every candidate of a batch.  The
-// bins are decided by the vote's guarded float32 evaluation, redone in
-// float64 in the definition's operation order where float32 cannot prove
-// them, so own and pool membership are exactly the vote's; the circle and
-// the distances are float64 with one correctly rounded operation at a time
-// (no contraction), in the order of the plain definition.
+// One warp per candidate, persistent over the candidates of a batch grouped
+// by (event, column group).  A candidate scans only the hits of each layer
+// whose azimuth can give a root near its bin (a per-event index by layer and
+// azimuth, k_hitindex.cu; a superset of the pool).  A float32 screen drops
+// hits whose roots are certainly far; the rest get the vote's exact bin
+// decision (guarded float32, then double-float, then float64 in the
+// definition's operation order), so own and pool membership are exactly
+// the vote's.  The seed circle is float64 in the definition's order;
+// distances are estimated in float32 with an error bound, and the float64
+// distance of the definition is computed for every hit the bound cannot
+// settle, so every decision is the definition's.  The results are
+// bit-identical to the float64 plain definition.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -736,6 +742,112 @@ cudaError_t launch_confirm(const DevGeom &G, const ConfirmDev &P, const float *x
     return launch_confirm_batch(G, P, x, y, layer, meta, meta + 2, 1, n, peaks, d_count, cap,
                                 score, inl, assign, reinterpret_cast<char *>(ws) + align256(16),
                                 device_sms(), st, nullptr);
+}
+
+
+// ------------------------------------------------------------ compaction
+// The confirmed candidates (score > 0) of every event, in candidate order,
+// as a compact list of found tracks, and each hit's assignment as an index
+// into its event's tracks (ht_batch_run_tracks_host).
+namespace {
+
+__global__ void k_track_flags(const int *__restrict__ d_nev, const int *__restrict__ cpre,
+                              int cap, const int *__restrict__ score, int *__restrict__ flag)
+{
+    const int n_ev = *d_nev, total = cpre[n_ev];
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < total; f += gridDim.x * blockDim.x) {
+        const int e = event_of(cpre, n_ev, f);
+        flag[f] = score[(size_t)e * cap + (f - cpre[e])] > 0 ? 1 : 0;
+    }
+}
+
+// tfirst[e] = the compact index of event e's first track (e <= n_ev)
+__global__ void k_track_first(const int *__restrict__ d_nev, const int *__restrict__ cpre,
+                              const int *__restrict__ pos, const int *__restrict__ ntot,
+                              int *__restrict__ tfirst)
+{
+    const int n_ev = *d_nev, total = cpre[n_ev];
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e <= n_ev; e += gridDim.x * blockDim.x)
+        tfirst[e] = cpre[e] < total ? pos[cpre[e]] : *ntot;
+}
+
+__global__ void k_track_write(const int *__restrict__ d_nev, const int *__restrict__ cpre,
+                              int cap, const int *__restrict__ flag, const int *__restrict__ pos,
+                              const int *__restrict__ tfirst, const ht_peak *__restrict__ peaks,
+                              const int *__restrict__ score, const ht_zres *__restrict__ zres,
+                              ht_track_out *__restrict__ tracks, int tcap, int *__restrict__ map)
+{
+    const int n_ev = *d_nev, total = cpre[n_ev];
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < total; f += gridDim.x * blockDim.x) {
+        if (!flag[f]) continue;
+        const int e = event_of(cpre, n_ev, f);
+        const size_t slot = (size_t)e * cap + (f - cpre[e]);
+        const int t = pos[f];
+        map[slot] = t - tfirst[e];
+        if (t < tcap) {
+            const ht_peak pk = peaks[slot];
+            const ht_zres zr = zres[slot];
+            tracks[t] = ht_track_out{pk.i_rho, pk.j_d0, pk.k_phi0, pk.count, score[slot],
+                                     zr.n_z0, zr.m_cot, zr.count};
+        }
+    }
+}
+
+__global__ void k_track_assign(const int *__restrict__ off, const int *__restrict__ d_nev,
+                               int cap, const int *__restrict__ assign,
+                               const int *__restrict__ map, int *__restrict__ out)
+{
+    const int n_ev = *d_nev, n = off[n_ev];
+    for (int h = blockIdx.x * blockDim.x + threadIdx.x; h < n; h += gridDim.x * blockDim.x) {
+        int lo = 0, hi = n_ev - 1;   // the hit's event
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (off[mid] <= h) lo = mid;
+            else hi = mid - 1;
+        }
+        const int a = assign[h];
+        out[h] = a >= 0 ? map[(size_t)lo * cap + a] : -1;
+    }
+}
+
+}  // namespace
+
+size_t track_compact_bytes(int max_events, int cap)
+{
+    const size_t nk = (size_t)max_events * (cap > 0 ? cap : 1);
+    return align256((size_t)(max_events + 1) * 4) + 2 * align256((size_t)(max_events + 1) * 4) +
+           3 * align256(nk * 4) + align256(16) + scan_tmp_bytes((int)nk);
+}
+
+cudaError_t launch_track_compact(const int *off, const int *d_nev, int max_events, int max_hits,
+                                 const ht_peak *peaks, const int *counts, int cap,
+                                 const int *score, const ht_zres *zres, const int *assign,
+                                 ht_track_out *tracks, int tcap, int *tfirst, int *ntot,
+                                 int *assign_out, void *ws, int sms, cudaStream_t st)
+{
+    const size_t nk = (size_t)max_events * (cap > 0 ? cap : 1);
+    char *p = reinterpret_cast<char *>(ws);
+    int *cpre = reinterpret_cast<int *>(p);
+    p += align256((size_t)(max_events + 1) * 4);
+    p += 2 * align256((size_t)(max_events + 1) * 4);
+    int *flag = reinterpret_cast<int *>(p);
+    p += align256(nk * 4);
+    int *pos = reinterpret_cast<int *>(p);
+    p += align256(nk * 4);
+    int *map = reinterpret_cast<int *>(p);
+    p += align256(nk * 4);
+    p += align256(16);
+    void *tmp = p;
+    k_cand_prefix<<<1, 1024, 0, st>>>(counts, d_nev, cap, cpre);
+    k_track_flags<<<sms * 4, 256, 0, st>>>(d_nev, cpre, cap, score, flag);
+    cudaError_t e = scan_exclusive(flag, pos, nullptr, (int)nk, nullptr, ntot, tmp, st);
+    if (e != cudaSuccess) return e;
+    k_track_first<<<(max_events + 256) / 256, 256, 0, st>>>(d_nev, cpre, pos, ntot, tfirst);
+    k_track_write<<<sms * 4, 256, 0, st>>>(d_nev, cpre, cap, flag, pos, tfirst, peaks, score, zres,
+                                            tracks, tcap, map);
+    k_track_assign<<<sms * 4, 256, 0, st>>>(off, d_nev, cap, assign, map, assign_out);
+    (void)max_hits;
+    return cudaGetLastError();
 }
 
 }  // namespace ht

@@ -143,6 +143,8 @@ SIGNATURES = [
     ("ht_batch_set_confirm", _I32, [_P, ctypes.POINTER(_ConfirmDesc)]),
     ("ht_batch_run_tracks", _I32, [_P, _P, _P, _P, _P, _P, _I32, ctypes.POINTER(_HitProposal),
                                    _P, _P, _P, _P, _P, _P, _P, _P]),
+    ("ht_batch_run_tracks_host", _I32, [_P, _P, _P, _P, _P, _P, _I32,
+                                        ctypes.POINTER(_HitProposal), _P, _I32, _P, _P, _P, _P]),
 ]
 
 
@@ -618,6 +620,35 @@ class Batch:
                                          _ptr(self.peaks), _ptr(self.counts), _ptr(self.score),
                                          _ptr(self.assign), _ptr(self.zres), _ptr(self.stats),
                                          _stream(stream)), "ht_batch_run_tracks")
+
+    def run_tracks_host(self, hx, hy, hz, hlayer, offsets, tracks, ntracks, assign,
+                        params_bf16=None, topk=8, pmin=0.0, stats=None, stream=None):
+        """ht_batch_run_tracks_host: host (numpy or pinned torch) hit arrays
+        in; tracks (int32 [track_cap, 8] host: i, j, k, count, score, n_z0,
+        m_cot, zcount), ntracks (int32 [n_events]) and assign (int32 [hits])
+        host outputs written; synchronous.  Returns False when the tracks
+        exceeded track_cap (the first track_cap were written)."""
+        off, p = self._offsets(offsets)
+        prop = None
+        if params_bf16 is not None:
+            self._hprop = _HitProposal(params_bf16.data_ptr(), None, int(topk), float(pmin))
+            prop = ctypes.byref(self._hprop)
+
+        def hp(a):
+            if a is None:
+                return None
+            if isinstance(a, torch.Tensor):
+                return ctypes.c_void_p(a.data_ptr())
+            return a.ctypes.data_as(ctypes.c_void_p)
+
+        st = lib().ht_batch_run_tracks_host(self.handle, hp(hx), hp(hy), hp(hz), hp(hlayer), p,
+                                            off.shape[0] - 1, prop, hp(tracks),
+                                            int(tracks.shape[0]), hp(ntracks), hp(assign),
+                                            hp(stats), _stream(stream))
+        if st == 2:   # HT_ERR_CAPACITY: counts still written
+            return False
+        _check(st, "ht_batch_run_tracks_host")
+        return True
 
     def stage_ms(self):
         """[proposal, vote, peaks + candidate lists, association (track path:

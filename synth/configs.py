@@ -27,6 +27,14 @@ HIT_SIGMA = 20e-4      # 20 um r-phi and z smear
 Z0_SIGMA = 5.0
 
 
+def _track(threshold, pool=4, min_layers=8, tol=0.01, bands=()):
+    """Parameters of the dense-event track path (distinct-layer vote, peak
+    threshold T counted in layers, confirmation; bands give the batched
+    stream each event's T from its hit count: [(max_hits, T), ...])."""
+    return dict(threshold=threshold, pool=pool, min_layers=min_layers, n_layers=10, tol=tol,
+                bands=list(bands))
+
+
 def _geom(n_rho, n_d0, n_phi0, pt_min, d0_half, count_bits, threshold=7,
           n_z0=128, n_cot=128, z0_max=32.0, cot_max=6.5):
     return dict(n_rho=n_rho, n_d0=n_d0, n_phi0=n_phi0,
@@ -42,6 +50,8 @@ CONFIGS = {
         geom=_geom(64, 64, 64, pt_min=1.0, d0_half=10.0, count_bits=32),
         gen=dict(n_tracks=25, n_displaced=5, d0_disp=10.0, pt_kind="trunc_exp",
                  pt_min=1.0, pt_scale=1.0, pt_max=20.0, noise_frac=0.10),
+        # a column spans 10.8 cm at 110 cm: a wide pool, 6 layers, T = 3
+        track=_track(3, pool=20, min_layers=6),
         events=1, seed0=0),
     # 100 events of ~10k hits: 5% displaced (|d0| < 20 cm), 15% noise.
     "event100_256": dict(
@@ -49,6 +59,7 @@ CONFIGS = {
         gen=dict(target_hits=10000, disp_frac=0.05, d0_disp=20.0,
                  pt_kind="trunc_exp", pt_min=1.0, pt_scale=1.0, pt_max=20.0,
                  noise_frac=0.15),
+        track=_track(9),
         events=100, seed0=0),
     # Pile-up-like: 20 events of ~50k hits, pT = 0.5 GeV + exponential(0.7 GeV)
     # capped at 100 GeV, 2% displaced (|d0| < 30 cm), 20% noise.
@@ -57,6 +68,7 @@ CONFIGS = {
         gen=dict(target_hits=50000, disp_frac=0.02, d0_disp=30.0,
                  pt_kind="shifted_exp", pt_min=0.5, pt_scale=0.7, pt_max=100.0,
                  noise_frac=0.20),
+        track=_track(10, tol=0.006),
         events=20, seed0=0),
     # Batched stream: 2000 events, hit counts log-uniform on [2k, 60k],
     # generator mix and geometry of the 100-event case.
@@ -65,6 +77,9 @@ CONFIGS = {
         gen=dict(target_hits=None, hits_loguniform=(2000, 60000), disp_frac=0.05,
                  d0_disp=20.0, pt_kind="trunc_exp", pt_min=1.0, pt_scale=1.0,
                  pt_max=20.0, noise_frac=0.15),
+        # per-event T by hit count; 60 um (3 sigma) inliers against the
+        # random coincidences of the 20k-60k-hit events
+        track=_track(10, tol=0.006, bands=[(4000, 7), (7000, 8), (12000, 9)]),
         events=2000, seed0=0),
     # Displaced jets (the scenario of Figs. 6 and 8-9): 4 jets of 10 tracks
     # from vertices at 5-25 cm, dispersion 15-60 degrees, jet tracks
@@ -90,6 +105,26 @@ CONFIGS = {
         vertex=dict(n_r=16, n_theta=64, r_max=32.0, threshold=5, min_count=9, r_keep=3.0),
         events=20, seed0=0),
 }
+
+
+def track_of(name):
+    """The track path's parameters of a workload (None if it has none)."""
+    t = CONFIGS[name].get("track")
+    return None if t is None else dict(t, bands=list(t["bands"]))
+
+
+def track_geometry(name, n_hits=None):
+    """The workload's geometry with the track path's peak threshold (the
+    band's for an event of n_hits hits, when bands are set)."""
+    t = CONFIGS[name]["track"]
+    g = geometry_of(name)
+    g["threshold"] = t["threshold"]
+    if n_hits is not None:
+        for mh, thr in t["bands"]:
+            if n_hits <= mh:
+                g["threshold"] = thr
+                break
+    return g
 
 
 def geometry_of(name, **overrides):

@@ -1,7 +1,7 @@
 """bench.py's host logic, without a GPU: the clock record parsing and its
 throttle reasons, the issue-limited ALU peak, the LPT split of a job's
-events over ranks, and the reference arm's JSON line (the oracle on a tiny
-workload)."""
+events over ranks, the launch count per batch, and the reference arm's JSON
+line (the oracle's track path on a tiny workload)."""
 import json
 import os
 import subprocess
@@ -42,16 +42,20 @@ def test_alu_peak_is_sms_times_128_lanes_times_clock():
     assert bench.alu_peak_ops(Props(2), {}) == 2 * 128 * 2070e6
 
 
-def test_make_batches_splits_the_job_over_ranks_once():
-    import synth
-    cfg = dict(synth.CONFIGS["single_64"])
+def test_make_events_splits_the_job_over_ranks_once():
     seen = []
     for rank in range(3):
-        ids, events, batches = bench.make_batches(cfg, 4, 3, rank, 2)
-        assert len(events) == len(ids) and sum(len(b) for b in batches) == len(events)
-        assert all(len(b) <= 2 for b in batches)
+        ids, events = bench.make_events("single_64", 4, 3, rank)
+        assert len(events) == len(ids)
         seen += list(ids)
     assert sorted(seen) == list(range(12))
+    ids, events = bench.make_events("single_64", 4, 1, 0)
+    assert ids == [0, 1, 2, 3] and len(events) == 4
+
+
+def test_launch_count_per_batch_grows_by_five_per_event():
+    assert bench.launches_per_batch(2) - bench.launches_per_batch(1) == 5
+    assert bench.launches_per_batch(3, learned=True) == bench.launches_per_batch(3) + 1
 
 
 def test_reference_arm_prints_one_json_line_of_the_contract():

@@ -215,3 +215,44 @@ def test_batch_tracks_with_per_hit_region_sets():
         assert np.array_equal(r["score"], o["score"]), e
         assert np.array_equal(r["assign"], o["assign"]), e
         assert np.array_equal(r["zres"], o["zres"]), e
+
+
+def test_host_buffer_call_returns_the_confirmed_candidates():
+    """ht_batch_run_tracks_host: the tracks of each event are its confirmed
+    candidates in candidate order with their z results, and each hit's
+    assignment points at its candidate's track; a too-small track_cap gives
+    the first tracks and the capacity status."""
+    import torch
+    from paper_1309_6275_gb300 import ht
+    g0 = dict(synth.geometry_of("stream2000_256"), threshold=10)
+    sizes = [3000, 11000, 6000]
+    evs, off, x, y, z, lay = make_batch(720, sizes)
+    cap = 1 << 19
+    dev = run_batch(g0, evs, off, x, y, z, lay, cap)[0]
+    G = ht.Geometry(g0)
+    B = ht.Batch(G, max_events=len(evs), max_hits=int(off[-1]) + 64, cap=cap)
+    B.set_confirm(dict(CP, bands=BANDS))
+    tracks = np.zeros((1 << 16, 8), np.int32)
+    ntr = np.zeros(len(evs), np.int32)
+    asg = np.zeros(int(off[-1]), np.int32)
+    assert B.run_tracks_host(x, y, z, lay, off, tracks, ntr, asg)
+    base = 0
+    for e, r in enumerate(dev):
+        conf = np.flatnonzero(r["score"] > 0)
+        assert ntr[e] == conf.size, e
+        t = tracks[base:base + ntr[e]]
+        assert np.array_equal(t[:, :4], r["peaks"][conf]), e
+        assert np.array_equal(t[:, 4], r["score"][conf]), e
+        assert np.array_equal(t[:, 5:8], r["zres"][conf]), e
+        remap = np.full(r["count"], -1, np.int64)
+        remap[conf] = np.arange(conf.size)
+        a = r["assign"]
+        want = np.where(a >= 0, remap[np.maximum(a, 0)], -1)
+        assert np.array_equal(asg[off[e]:off[e + 1]], want), e
+        base += ntr[e]
+    small = np.zeros((5, 8), np.int32)
+    ntr2 = np.zeros(len(evs), np.int32)
+    assert not B.run_tracks_host(x, y, z, lay, off, small, ntr2, asg)
+    assert np.array_equal(ntr2, ntr) and np.array_equal(small, tracks[:5])
+    B.close()
+    G.close()
