@@ -61,7 +61,8 @@ def parse():
     p.add_argument("--no-secondary", action="store_true")
     p.add_argument("--no-vertex", action="store_true")
     p.add_argument("--no-swept", action="store_true")
-    p.add_argument("--topk", type=int, default=8, help="regions per hit of the per-hit proposal")
+    p.add_argument("--topk", type=int, default=None,
+                   help="regions per hit of the per-hit proposal (default: the workload's)")
     return p.parse_args()
 
 
@@ -368,32 +369,54 @@ def learned_leg(args, tr, plain, flush):
     on the same events (the learned configuration's evaluation: the batched
     stream): each hit votes only in its network's top-k regions (computed in
     the same graph by the tcgen05 forward pass); peaks, confirmation and the
-    z vote are unchanged.  Events/s (same timing rules as the headline) and
-    assignment-level efficiency, fakes, votes and candidates of both."""
+    z vote are unchanged.  Two thresholds: the learned configuration's own
+    (one layer lower: the restricted vote lacks most background votes) and
+    the plain path's.  Events/s (same timing rules as the headline) and
+    assignment-level efficiency, fakes, votes and candidates of each."""
     from paper_1309_6275_gb300 import learned
     path = learned.default_weights_path("event100_256")
-    if not os.path.exists(path):
+    lcfg = synth.learned_of(tr.name)
+    if not os.path.exists(path) or lcfg is None:
         return None
     params, meta = learned.load_weights(path)
     pb = learned.bf16_params(params)
-    ms = tr.time_steps(max(1, args.steps), max(1, args.warmup), flush, params=pb, topk=args.topk)
-    prof = tr.profile(params=pb, topk=args.topk)
+    topk = args.topk if args.topk is not None else lcfg["topk"]
     n = len(tr.events)
-    value = n * len(ms) / (sum(ms) / 1e3)
-    P, L = plain["quality"], prof["quality"]
-    return {"value": value, "unit": "events/s", "plain_value": plain["value"],
-            "speedup": value / plain["value"],
+    P = plain["quality"]
+
+    def measure(track):
+        tr.bt.set_confirm(track)
+        ms = tr.time_steps(max(1, args.steps), max(1, args.warmup), flush, params=pb, topk=topk)
+        prof = tr.profile(params=pb, topk=topk)
+        L = prof["quality"]
+        return {"value": n * len(ms) / (sum(ms) / 1e3), "efficiency": L["efficiency"],
+                "difference_points": 100.0 * (L["efficiency"] - P["efficiency"]),
+                "fake_rate": L["fake_rate"], "quality": L,
+                "vote_frac": prof["votes"] / max(plain["votes"], 1),
+                "candidate_frac": prof["candidates_per_event"] /
+                                  max(plain["candidates_per_event"], 1),
+                "stage_ms_per_event": [round(v / n, 4) for v in prof["stage_ms"]],
+                "bands": track["bands"]}
+
+    own = measure(lcfg["track"])
+    same = measure(synth.track_of(tr.name))
+    tr.bt.set_confirm(synth.track_of(tr.name))
+    return {"value": own["value"], "unit": "events/s", "plain_value": plain["value"],
+            "speedup": own["value"] / plain["value"],
             "workload": f"{tr.name}: the headline's {n} events",
-            "efficiency": {"plain": P["efficiency"], "learned": L["efficiency"],
-                           "difference_points": 100.0 * (L["efficiency"] - P["efficiency"])},
-            "fake_rate": {"plain": P["fake_rate"], "learned": L["fake_rate"]},
-            "quality": {"plain": P, "learned": L},
-            "vote_frac": prof["votes"] / max(plain["votes"], 1),
-            "candidate_frac": prof["candidates_per_event"] / max(plain["candidates_per_event"], 1),
+            "efficiency": {"plain": P["efficiency"], "learned": own["efficiency"],
+                           "difference_points": own["difference_points"]},
+            "fake_rate": {"plain": P["fake_rate"], "learned": own["fake_rate"]},
+            "quality": {"plain": P, "learned": own["quality"]},
+            "vote_frac": own["vote_frac"], "candidate_frac": own["candidate_frac"],
             "stage_ms_per_event": {"stages": STAGES,
                                    "plain": [round(v / n, 4) for v in plain["stage_ms"]],
-                                   "learned": [round(v / n, 4) for v in prof["stage_ms"]]},
-            "topk": args.topk, "pmin": 0.0,
+                                   "learned": own["stage_ms_per_event"]},
+            "thresholds": {"plain": synth.track_of(tr.name)["bands"], "learned": own["bands"]},
+            "at_plain_thresholds": {k: same[k] for k in ("value", "efficiency",
+                                                         "difference_points", "fake_rate",
+                                                         "vote_frac", "candidate_frac")},
+            "topk": topk, "pmin": 0.0,
             "path": "ht_batch_run_tracks with a per-hit proposal (MLP top-k per hit, then the "
                     "per-hit restricted distinct-layer vote, in one graph)",
             "weights": os.path.relpath(path, ROOT),
@@ -689,7 +712,8 @@ def run_ours(args):
     if dom == 1:
         achieved = OPS_PER_VOTE * votes / stage_s[1]
         prof = PROFILED_TRAFFIC.get("k_vote_batch")
-        atom = ht.ht_probe_shared_atomic_rate(1 << 14)
+        from paper_1309_6275_gb300 import probe
+        atom = probe.shared_atomic_rate(1 << 14)
         roof.update({"bound": "alu", "achieved": achieved / 1e9, "peak": peak_ops / 1e9,
                      "unit": "Gop/s", "frac": achieved / peak_ops,
                      "traffic": (prof["bytes_per_event"] * B

@@ -143,6 +143,8 @@ ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks,
  *   exits); larger geometries get HT_ERR_CAPACITY.
  *   The first call on a device (made with that device current) looks up the
  *   scratch's device address; make that first call before any stream capture.
+ *   A failed lookup is not remembered (the next call tries again); after a
+ *   cudaDeviceReset the remembered address is stale, so restart the process.
  *   All calls share the one array: calls that overlap on the GPU (different
  *   streams, or different host threads) race and give wrong results, so
  *   serialise them.  Nothing in the array needs clearing between calls.

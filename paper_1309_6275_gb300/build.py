@@ -1,8 +1,9 @@
 """Build libht (the CUDA library behind include/ht.h) in-tree for sm_103a.
 
 Each .cu file under csrc/ is compiled in parallel with nvcc, then linked into
-paper_1309_6275_gb300/_build/libht.so.  Rebuilds only when a source is newer
-than the library (or when forced).
+paper_1309_6275_gb300/_build/libht.so.  The benchmark's roofline probe
+(probe/, include/ht_probe.h) is a separate library, _build/libht_probe.so.
+Rebuilds only when a source is newer than the library (or when forced).
 """
 import glob
 import os
@@ -14,6 +15,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libht.so")
+PROBE_SRC = os.path.join(HERE, "probe", "probe.cu")
+PROBE_LIB = os.path.join(BUILD, "libht_probe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 
@@ -68,6 +71,23 @@ def build(force=False, verbose=False, ptxas_info=False):
         raise RuntimeError(f"link failed:\n{r.stderr}")
     os.replace(tmp, LIB)
     return LIB
+
+
+def build_probe(force=False):
+    """Compile the roofline probe library (benchmark only); returns its path."""
+    deps = [PROBE_SRC, os.path.join(os.path.dirname(HERE), "include", "ht_probe.h"),
+            os.path.join(os.path.dirname(HERE), "include", "ht.h"), __file__]
+    if (not force and os.path.exists(PROBE_LIB) and
+            all(os.path.getmtime(p) <= os.path.getmtime(PROBE_LIB) for p in deps)):
+        return PROBE_LIB
+    os.makedirs(BUILD, exist_ok=True)
+    tmp = PROBE_LIB + f".tmp{os.getpid()}"
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, "-shared", "-o", tmp, PROBE_SRC, "-lcudart"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{r.stderr}")
+    os.replace(tmp, PROBE_LIB)
+    return PROBE_LIB
 
 
 if __name__ == "__main__":

@@ -259,10 +259,11 @@ cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int 
 // the scan's block sums -- lives here in a file-scope device array, sized
 // for at most kNoallocMaxSegments segments.  Every GPU that loads the library
 // holds it until the process exits.  The array's name is only a host-side
-// stand-in in host code, so its device address is looked up once per device
-// with cudaGetSymbolAddress (on the first call made with that device
-// current) and passed to the kernels.  Nothing in it needs clearing between
-// calls: each word a call reads was written earlier in the same call.
+// stand-in in host code, so its device address is looked up per device with
+// cudaGetSymbolAddress (on the first successful call made with that device
+// current; a failed lookup is not cached, so the next call tries again) and
+// passed to the kernels.  Nothing in it needs clearing between calls: each
+// word a call reads was written earlier in the same call.
 #include <mutex>
 
 namespace {
@@ -275,9 +276,8 @@ constexpr int kNoallocMaxDevices = 64;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
 
-std::once_flag g_noalloc_once[kNoallocMaxDevices];
-void *g_noalloc_ptr[kNoallocMaxDevices];
-cudaError_t g_noalloc_status[kNoallocMaxDevices];
+std::mutex g_noalloc_mutex;
+void *g_noalloc_ptr[kNoallocMaxDevices];   // null until a lookup on that device succeeds
 
 }  // namespace
 
@@ -300,13 +300,21 @@ extern "C" ht_status ht_find_peaks_noalloc(const ht_geometry *g, const void *acc
     if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, "ht_find_peaks_noalloc: cudaGetDevice");
     if (dev < 0 || dev >= kNoallocMaxDevices)
         return ht::set_error(HT_ERR_ARG, "ht_find_peaks_noalloc: device index above 63");
-    std::call_once(g_noalloc_once[dev], [dev] {
-        g_noalloc_status[dev] = cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch);
-    });
-    if (g_noalloc_status[dev] != cudaSuccess)
-        return ht::set_error(HT_ERR_CUDA,
-                             "ht_find_peaks_noalloc: cudaGetSymbolAddress of the scratch failed");
-    e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, g_noalloc_ptr[dev],
+    void *scratch = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+        if (!g_noalloc_ptr[dev]) {
+            void *p = nullptr;
+            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+                cudaGetLastError();   // clear it: the next call looks the address up again
+                return ht::set_error(HT_ERR_CUDA, "ht_find_peaks_noalloc: cudaGetSymbolAddress "
+                                                  "of the scratch failed (retried next call)");
+            }
+            g_noalloc_ptr[dev] = p;
+        }
+        scratch = g_noalloc_ptr[dev];
+    }
+    e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, scratch,
                          reinterpret_cast<cudaStream_t>(stream));
     if (e != cudaSuccess) return ht::set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     return HT_OK;

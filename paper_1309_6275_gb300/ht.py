@@ -96,7 +96,6 @@ SIGNATURES = [
     ("ht_vote_z", _I32, [_P, _P, _P, _P, _I32, _P, _P, _P, _I32, _P, _P, _SZ, _P]),
     ("ht_event_workspace_size", _SZ, [_P, _I32, _I32]),
     ("ht_run_event", _I32, [_P, _P, _P, _P, _I32, _P, _SZ, _P, _I32, _P, _P, _P, _P, _P]),
-    ("ht_probe_shared_atomic_rate", _I32, [_I32, ctypes.POINTER(ctypes.c_double), _P]),
     ("ht_batch_create", _I32, [_P, _I32, _I32, _I32, ctypes.POINTER(_P)]),
     ("ht_batch_destroy", _I32, [_P]),
     ("ht_batch_set_graphs", _I32, [_P, _I32]),
@@ -361,17 +360,6 @@ def ht_run_event(g, hx, hy, hz, workspace, h_peaks, cap, h_count, h_assign, h_zr
                               _ptr(workspace), workspace.numel(), _ptr(h_peaks), cap,
                               _ptr(h_count), _ptr(h_assign), _ptr(h_zres), _ptr(h_stats),
                               _stream(stream)), "ht_run_event")
-
-
-def ht_probe_shared_atomic_rate(iters=4096, stream=None):
-    """Measured conflict-free shared-memory atomicAdd rate (atomics/s)."""
-    v = ctypes.c_double()
-    _check(lib().ht_probe_shared_atomic_rate(iters, ctypes.byref(v), _stream(stream)),
-           "ht_probe_shared_atomic_rate")
-    return v.value
-
-
-TRACK_FIELDS = ["rho", "d0", "phi0", "sig_rho", "sig_d0", "sig_phi0"]
 
 
 def ht_fit_tracks(G, x, y, d_off, assign, peaks, d_count, cap, out, workspace, min_hits=4,

@@ -1,5 +1,6 @@
 // probe.cu -- microbenchmark of shared-memory atomic throughput (the roofline
-// of the vote's counting); declared in include/ht_probe.h.
+// of the vote's counting); declared in include/ht_probe.h.  Built as its own
+// library (libht_probe.so), used by the benchmark only: not part of libht.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

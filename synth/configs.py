@@ -80,6 +80,11 @@ CONFIGS = {
         # per-event T by hit count; 60 um (3 sigma) inliers against the
         # random coincidences of the 20k-60k-hit events
         track=_track(10, tol=0.006, bands=[(4000, 7), (7000, 8), (12000, 9)]),
+        # the learned proposal on this stream: each hit's top-8 regions; its
+        # restricted vote lacks most background votes, so its thresholds sit
+        # one layer lower
+        learned=dict(topk=8, track=_track(10, tol=0.006, bands=[(4000, 6), (7000, 7),
+                                                                  (12000, 8), (1 << 30, 9)])),
         events=2000, seed0=0),
     # Displaced jets (the scenario of Figs. 6 and 8-9): 4 jets of 10 tracks
     # from vertices at 5-25 cm, dispersion 15-60 degrees, jet tracks
@@ -111,6 +116,13 @@ def track_of(name):
     """The track path's parameters of a workload (None if it has none)."""
     t = CONFIGS[name].get("track")
     return None if t is None else dict(t, bands=list(t["bands"]))
+
+
+def learned_of(name):
+    """The learned proposal's parameters on a workload (None if none):
+    {topk, track}."""
+    l = CONFIGS[name].get("learned")
+    return None if l is None else dict(topk=l["topk"], track=dict(l["track"], bands=list(l["track"]["bands"])))
 
 
 def track_geometry(name, n_hits=None):

@@ -1,5 +1,6 @@
 """The C-ABI library builds, loads and exports every symbol include/ht.h
-declares (no compute call: this runs without a GPU)."""
+declares, and the benchmark's probe library those of include/ht_probe.h
+(no compute call: this runs without a GPU)."""
 import ctypes
 import os
 import re
@@ -10,14 +11,10 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def declared_symbols():
-    syms = set()
-    for name in sorted(os.listdir(os.path.join(ROOT, "include"))):
-        if name.endswith(".h"):
-            hdr = open(os.path.join(ROOT, "include", name)).read()
-            syms |= set(re.findall(r"^(?:ht_status|size_t|int32_t|int64_t|const char \*)\s*\**\s*(ht_\w+)\(",
-                                   hdr, re.M))
-    return syms
+def declared_symbols(header="ht.h"):
+    hdr = open(os.path.join(ROOT, "include", header)).read()
+    return set(re.findall(r"^(?:ht_status|size_t|int32_t|int64_t|const char \*)\s*\**\s*(ht_\w+)\(",
+                          hdr, re.M))
 
 
 def test_header_declares_the_path():
@@ -45,6 +42,18 @@ def test_library_exports_every_declared_symbol():
     lib = ctypes.CDLL(path)
     for s in declared_symbols():
         assert hasattr(lib, s)
+    assert not exported & declared_symbols("ht_probe.h"), "the probe is not part of libht"
+
+
+def test_probe_library_exports_its_header():
+    from paper_1309_6275_gb300 import build
+    if not _have_nvcc():
+        pytest.skip("no nvcc on this machine")
+    path = build.build_probe()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r"\bT (ht_\w+)$", out, re.M))
+    assert declared_symbols("ht_probe.h") == {"ht_probe_shared_atomic_rate"} <= exported
 
 
 def test_binding_signatures_cover_the_header():
@@ -74,10 +83,9 @@ def test_every_call_rejects_null_arguments_before_any_cuda_call():
     if not _have_nvcc():
         pytest.skip("no nvcc on this machine")
     lib = ht.lib()
-    device_only = {"ht_probe_shared_atomic_rate"}   # times a kernel: needs a GPU
     checked = 0
     for name, res, args in ht.SIGNATURES:
-        if res is not ht._I32 or name in device_only or name == "ht_mlp_param_count":
+        if res is not ht._I32 or name == "ht_mlp_param_count":
             continue
         vals = [0.0 if a in (ctypes.c_float, ctypes.c_double)
                 else 0 if a in (ht._I32, ht._SZ, ctypes.c_int64) else None for a in args]

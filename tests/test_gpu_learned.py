@@ -311,56 +311,55 @@ def test_batch_masked_and_learned_runs():
 
 def test_trained_proposal_gain_over_the_plain_path():
     """What the committed, trained network buys on the batched-stream
-    workload: with the per-event mask, far fewer votes and candidates at a
-    small loss of candidate-level efficiency (tracks outside the proposed
-    regions); with the per-hit top-k sets, fewer still and no loss; the same
-    assignment-level efficiency in both."""
+    workload, judged by assignment-level efficiency on the track path: each
+    hit voting only in its top-8 regions casts under a third of the votes,
+    and at the learned configuration's thresholds (one layer lower) finds
+    tracks within half a point of the plain path's efficiency, with no more
+    fakes.  200 events, so that half a point is well above the sampling
+    noise."""
     import torch
-    from paper_1309_6275_gb300 import ht, learned
+    from paper_1309_6275_gb300 import ht, learned, quality
     name = "stream2000_256"
-    g = synth.geometry_of(name)
-    evs = list(synth.make_stream(name, 8, 5000))
-    off = np.zeros(len(evs) + 1, np.int32)
-    off[1:] = np.cumsum([e.n_hits for e in evs])
-    cat = lambda k, t: to_dev(np.concatenate([getattr(e, k) for e in evs]).astype(t))
-    x, y, z, layer = cat("x", np.float32), cat("y", np.float32), cat("z", np.float32), cat("layer", np.uint8)
+    evs = list(synth.make_stream(name, 200, 5000))
     params, meta = learned.load_weights(learned.default_weights_path("event100_256"))
     assert meta["n_events"] >= 100000
     pb = learned.bf16_params(params)
-    G = ht.Geometry(g)
-    B = ht.Batch(G, max_events=len(evs), max_hits=int(off[-1]), cap=1 << 20)
-    masks = torch.empty(len(evs), dtype=torch.int64, device="cuda")
-    res = {}
-    for mode in ("plain", "learned"):
-        if mode == "plain":
-            B.run(x, y, z, off)
-        else:
-            B.run_learned(x, y, z, layer, off, pb, masks, 0.02, 0.6, 1)
-        torch.cuda.synchronize()
-        q = np.zeros(5, np.int64)
-        for e, ev in enumerate(evs):
-            r = batch_event(B, off, e)
-            q += [r["votes"], r["count"], *learned.efficiency(g, ev, r["peaks"], r["assign"])]
-        res[mode] = q
-    P, L = res["plain"], res["learned"]
-    mk = [int(v) & ((1 << 64) - 1) for v in masks.cpu().tolist()]
-    assert all(m != (1 << 64) - 1 for m in mk)          # no fallback to the full vote
-    assert L[0] < 0.7 * P[0] and L[1] < 0.7 * P[1]      # votes, candidates
-    eff = lambda q, k: q[k] / max(q[2], 1)
-    assert eff(L, 4) >= eff(P, 4) - 0.05                # candidate-level efficiency
-    assert abs(eff(L, 3) - eff(P, 3)) <= 0.005          # assignment-level efficiency
-    # the per-hit proposal (each hit's top 8 regions): a quarter of the votes,
-    # a sixth of the candidates, and no loss of efficiency
-    hm = torch.empty(int(off[-1]), dtype=torch.int64, device="cuda")
-    B.run_learned_hits(x, y, z, layer, off, pb, hm, 8, 0.0)
-    torch.cuda.synchronize()
-    H = np.zeros(5, np.int64)
-    for e, ev in enumerate(evs):
-        r = batch_event(B, off, e)
-        H += [r["votes"], r["count"], *learned.efficiency(g, ev, r["peaks"], r["assign"])]
-    assert H[0] < 0.35 * P[0] and H[1] < 0.3 * P[1]
-    assert eff(H, 4) >= eff(P, 4) - 0.005
-    assert abs(eff(H, 3) - eff(P, 3)) <= 0.005
+    lcfg = synth.learned_of(name)
+    G = ht.Geometry(synth.track_geometry(name))
+    Bn = 50
+    batches = [evs[i:i + Bn] for i in range(0, len(evs), Bn)]
+    mh = max(sum(e.n_hits for e in b) for b in batches)
+    B = ht.Batch(G, max_events=Bn, max_hits=mh, cap=1 << 19)
+    hm = torch.empty(mh, dtype=torch.int64, device="cuda")
+
+    def run(track, params=None):
+        B.set_confirm(track)
+        votes, rows = 0, []
+        for b in batches:
+            off = np.zeros(len(b) + 1, np.int32)
+            off[1:] = np.cumsum([e.n_hits for e in b])
+            cat = lambda k, t: to_dev(np.concatenate([getattr(e, k) for e in b]).astype(t))
+            x, y, z, l = cat("x", np.float32), cat("y", np.float32), cat("z", np.float32), \
+                cat("layer", np.uint8)
+            if params is None:
+                B.run_tracks(x, y, z, l, off)
+            else:
+                B.run_tracks(x, y, z, l, off, params_bf16=params, hit_masks=hm,
+                             topk=lcfg["topk"])
+            torch.cuda.synchronize()
+            votes += int(B.stats[:2 * len(b)].view(-1, 2)[:, 0].sum())
+            asg = B.assign[:int(off[-1])].cpu().numpy()
+            for e, ev in enumerate(b):
+                rows.append(quality.track_quality(synth.track_geometry(name), ev,
+                                                  asg[off[e]:off[e + 1]]))
+        return votes, quality.summarize(rows)
+
+    vp, P = run(synth.track_of(name))
+    vl, L = run(lcfg["track"], pb)
+    assert P["efficiency"] > 0.08 and P["found"] > 1000   # the plain path finds tracks
+    assert vl < 0.35 * vp                                  # votes cast
+    assert L["efficiency"] >= P["efficiency"] - 0.005      # assignment-level efficiency
+    assert L["fake_rate"] <= P["fake_rate"]
     B.close()
     G.close()
 
