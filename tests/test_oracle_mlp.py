@@ -116,3 +116,103 @@ def test_masked_event_keeps_exactly_the_inside_peaks():
     assert np.array_equal(allm["assign"], full["assign"])
     assert np.array_equal(allm["zres"], full["zres"])
     assert allm["votes"] == full["stats"]["votes"]
+
+
+# ------------------------------------------------ hand-computed pins of the network
+def _features_pin(features):
+    """features() at hand-placed hits; every expected value is exact in BF16.
+    (0, -55) lies at azimuth -pi/2, which fixes the sign of the azimuth; z is
+    a quarter of the z scale 110 sinh 2.5 (a float32 product, so the quarter
+    divides back exactly)."""
+    zs = np.float32(110.0) * np.float32(math.sinh(2.5))
+    x = np.array([110.0, 0.0, -27.5], np.float32)
+    y = np.array([0.0, -55.0, 0.0], np.float32)
+    z = np.array([0.0, zs * np.float32(0.25), -zs], np.float32)
+    lay = np.array([9, 0, 3])
+    want = np.array([[1.0, 0.0, 0.0, 1.0, 0.0, 1.0],
+                     [0.0, -0.5, 0.25, 0.5, -0.5, 0.0],
+                     [-0.25, 0.0, -1.0, 0.25, 1.0, 0.333984375]])   # bf16(float32(3 / 9))
+    return np.array_equal(features(x, y, z, lay), want)
+
+
+def _dyadic_params():
+    """Parameters with a few dyadic entries (exact in BF16): hidden units
+    that go negative (so each ReLU matters) and an asymmetric W2 (so a
+    transposed layer shows)."""
+    p = np.zeros(mlp.n_params())
+    W1, b1, W2, b2, W3, b3 = mlp.unpack(p)
+    W1[0, 0] = 1.0                  # u0 = f0
+    W1[0, 1] = -1.0                 # u1 = -f0 (negative for f0 > 0)
+    W1[1, 2] = 0.5; b1[2] = 0.25    # u2 = f1 / 2 + 1/4
+    W2[0, 0] = 1.0; W2[1, 0] = 2.0; W2[2, 0] = -1.0   # v0 = h0 + 2 h1 - h2
+    W2[0, 1] = -1.0                                    # v1 = -h0
+    W2[2, 2] = 1.0; b2[2] = 0.5                        # v2 = h2 + 1/2
+    W2[1, 3] = 4.0                                     # v3 = 4 h1 (row 1 != column 1)
+    W3[0, 0] = 1.0                                     # logit0 = w0
+    W3[2, 1] = 2.0                                     # logit1 = 2 w2
+    W3[1, 2] = 1.0                                     # logit2 = w1
+    W3[0, 3] = -1.0; b3[3] = 1.0                       # logit3 = 1 - w0
+    W3[3, 4] = 1.0                                     # logit4 = w3
+    return p
+
+
+def _forward_pin(forward):
+    """Two hits by hand.  Hit A (f0 = 1, f1 = 1/2): u = (1, -1, 1/2) ->
+    h1 = (1, 0, 1/2); v = (1/2, -1, 1, 0) -> h2 = (1/2, 0, 1, 0); logits
+    (1/2, 2, 0, 1/2, 0, 0 ...).  Hit B (f0 = -1/2, f1 = -1/2): u = (-1/2,
+    1/2, 0) -> h1 = (0, 1/2, 0); v = (1, 0, 1/2, 2) -> h2 = (1, 0, 1/2, 2);
+    logits (1, 1, 0, 0, 2, 0 ...).  The other 59 logits are 0."""
+    f = np.array([[1.0, 0.5, 0.0, 0.0, 0.0, 0.0],
+                  [-0.5, -0.5, 0.0, 0.0, 0.0, 0.0]])
+    logits, prob, _ = forward(_dyadic_params(), f)
+    want = np.zeros((2, 64))
+    want[0, :5] = [0.5, 2.0, 0.0, 0.5, 0.0]
+    want[1, :5] = [1.0, 1.0, 0.0, 0.0, 2.0]
+    if not np.array_equal(logits, want):
+        return False
+    e = np.exp(want - want.max(axis=1, keepdims=True))
+    return np.allclose(prob, e / e.sum(axis=1, keepdims=True), rtol=1e-15, atol=0)
+
+
+def test_features_at_hand_placed_hits():
+    assert _features_pin(mlp.features)
+
+
+def test_forward_pass_by_hand_through_both_relus():
+    assert _forward_pin(mlp.forward)
+    assert _forward_pin(lambda p, f: mlp.forward(p, f, round_bf16=False))
+
+
+def test_planted_network_mistakes_fail_the_pins():
+    """A copy of the oracle's forward pass or features with one step wrong --
+    a ReLU dropped, W2 used transposed, x scaled by 1/100, the azimuth's sign
+    flipped -- fails the hand-computed pins."""
+    def forward_variant(no_relu1=False, no_relu2=False, w2_t=False):
+        def fwd(p, f):
+            W1, b1, W2, b2, W3, b3 = mlp.unpack(mlp.bf16(np.asarray(p, np.float64)))
+            a1 = f @ W1 + b1
+            h1 = mlp.bf16(a1 if no_relu1 else np.maximum(a1, 0.0))
+            a2 = h1 @ (W2.T if w2_t else W2) + b2
+            h2 = mlp.bf16(a2 if no_relu2 else np.maximum(a2, 0.0))
+            logits = h2 @ W3 + b3
+            z = logits - logits.max(axis=1, keepdims=True)
+            e = np.exp(z)
+            return logits, e / e.sum(axis=1, keepdims=True), None
+        return fwd
+
+    assert _forward_pin(forward_variant())                 # the copy itself is right
+    assert not _forward_pin(forward_variant(no_relu1=True))
+    assert not _forward_pin(forward_variant(no_relu2=True))
+    assert not _forward_pin(forward_variant(w2_t=True))
+
+    def features_variant(scale=110.0, az_sign=1.0):
+        def feat(x, y, z, layer):
+            f = mlp.features(x, y, z, layer).copy()
+            f[:, 0] = mlp.bf16(np.asarray(x, np.float32) / np.float32(scale))
+            f[:, 4] = az_sign * f[:, 4]
+            return f
+        return feat
+
+    assert _features_pin(features_variant())
+    assert not _features_pin(features_variant(scale=100.0))
+    assert not _features_pin(features_variant(az_sign=-1.0))
