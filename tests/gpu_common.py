@@ -68,3 +68,33 @@ def assert_same_acc(gpu_acc, ora_acc):
     bad = np.argwhere(a != b)
     assert bad.shape[0] == 0, (f"{bad.shape[0]} cells differ; first {bad[:5].tolist()} "
                                f"gpu {a[tuple(bad[:5].T)].tolist()} oracle {b[tuple(bad[:5].T)].tolist()}")
+
+
+def oracle_sampled_check(g, ev, r, cap, n_hits=256, n_cands=8, seed=0, acc=None):
+    """The oracle against a GPU result r of the plain path (peaks, count,
+    assign, zres) on one event: the whole peak list; the association of
+    n_hits sampled hits; the (z0, cot theta) result of n_cands sampled
+    candidates that received hits.  The oracle finds each sampled
+    candidate's hits itself: the hits compatible with it alone, then their
+    assignment among all candidates.  Returns the oracle's peaks."""
+    if acc is None:
+        acc, _ = oracle.vote(g, ev.x, ev.y)
+    pk, cnt = oracle.peaks(g, acc, cap=cap)
+    del acc
+    assert r["count"] == cnt
+    assert np.array_equal(r["peaks"], pk)
+    rng = np.random.default_rng(seed)
+    sel = rng.choice(ev.n_hits, min(n_hits, ev.n_hits), replace=False)
+    asg = oracle.associate_dense(g, ev.x, ev.y, pk, hit_idx=sel)
+    assert np.array_equal(np.asarray(r["assign"])[sel], asg)
+    got = np.asarray(r["assign"])
+    owners = np.unique(got[got >= 0])
+    if owners.size:
+        for m in rng.choice(owners, min(n_cands, owners.size), replace=False):
+            comp = np.flatnonzero(oracle.associate(g, ev.x, ev.y, pk[[m]]) == 0)
+            a = oracle.associate_dense(g, ev.x, ev.y, pk, hit_idx=comp)
+            full = np.full(ev.n_hits, -1, np.int32)
+            full[comp] = a
+            zo = oracle.vote_z(g, ev.x, ev.y, ev.z, full, pk, cand=np.array([m]))
+            assert np.array_equal(np.asarray(r["zres"])[m], zo[0]), m
+    return pk

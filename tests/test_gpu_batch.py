@@ -6,7 +6,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import batch_event, cuda_ok, gpu_event, to_dev
+from gpu_common import oracle_sampled_check, batch_event, cuda_ok, gpu_event, to_dev
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
@@ -43,7 +43,8 @@ def test_batch_equals_oracle_and_single_event_path():
         assert np.array_equal(r["assign"], s["assign"]), e
         assert np.array_equal(r["zres"], s["zres"]), e
         assert r["votes"] == int(s["stats"][0]), e
-    # the smallest event against the oracle directly
+    # every event against the oracle: the smallest whole, the others with
+    # the whole peak list and sampled association and z results
     ev = evs[0]
     o = oracle.run_event(g, ev.x, ev.y, ev.z, cap=cap)
     r = batch_event(B, off, 0)
@@ -51,6 +52,9 @@ def test_batch_equals_oracle_and_single_event_path():
     assert np.array_equal(r["peaks"], o["peaks"])
     assert np.array_equal(r["assign"], o["assign"])
     assert np.array_equal(r["zres"], o["zres"])
+    for e in range(1, len(evs)):
+        oracle_sampled_check(g, evs[e], batch_event(B, off, e), cap, n_hits=128, n_cands=4,
+                             seed=e)
     B.close()
     G.close()
 

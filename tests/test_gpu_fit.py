@@ -142,3 +142,39 @@ def test_fit_in_batch_layout_and_noise_free_tracks():
         assert abs(t[m]["d0"] - d0) < 2e-4 and abs(t[m]["rho"] - rho) < 1e-6
         assert abs(math.remainder(t[m]["phi0"] - phi0, 2 * math.pi)) < 1e-5
     G.close()
+
+
+def test_fit_of_confirmed_tracks_with_road_and_cut():
+    """The refinement of the track path's confirmed candidates on a whole
+    10k-hit event (each holds 8-10 hits of one track), with the road and the
+    outlier cut: most fits settle, and those are compared with the oracle's;
+    the GPU's assignment is the oracle's (checked here too)."""
+    import torch
+    from paper_1309_6275_gb300 import ht
+    name = "event100_256"
+    g = synth.track_geometry(name)
+    tk = synth.track_of(name)
+    ev = synth.make_event(synth.CONFIGS[name]["gen"], 3)
+    n, cap = ev.n_hits, 1 << 19
+    G = ht.Geometry(g)
+    x, y, lay = to_dev(ev.x), to_dev(ev.y), to_dev(ev.layer.astype(np.uint8))
+    acc = G.new_accumulator()
+    ht.ht_vote_layers(G, x, y, lay, acc)
+    peaks = torch.empty((cap, 4), dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(max(G.find_peaks_workspace_size(), ht.ht_confirm_workspace_size(G, n, cap)),
+                     dtype=torch.uint8, device="cuda")
+    ht.ht_find_peaks(G, acc, peaks, cap, count, ws)
+    score = torch.zeros(cap, dtype=torch.int32, device="cuda")
+    inl = torch.zeros((cap, 16), dtype=torch.int32, device="cuda")
+    assign = torch.empty(n, dtype=torch.int32, device="cuda")
+    ht.ht_confirm(G, tk, x, y, lay, peaks, count, cap, score, inl, assign, ws)
+    sel = dict(road=1.0, cut=5.0)
+    tr = gpu_fit(G, ht, x, y, [0, n], assign, peaks, count, cap, **sel)
+    o = oracle.run_event_tracks(g, ev.x, ev.y, ev.z, ev.layer, cp=tk, cap=cap)
+    k = int(count.item())
+    assert np.array_equal(assign.cpu().numpy(), o["assign"])
+    assert np.array_equal(peaks[:k].cpu().numpy(), o["peaks"])
+    nf, nc = compare(g, ev.x, ev.y, o["assign"], o["peaks"], tr[:k], **sel)
+    assert nf > 300 and nc >= 0.5 * nf, (nf, nc)
+    G.close()

@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 import synth
-from gpu_common import assert_same_acc, cuda_ok, gpu_event, oracle_event, to_dev
+from gpu_common import oracle_sampled_check, assert_same_acc, cuda_ok, gpu_event, oracle_event, to_dev
 
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not cuda_ok(), reason="needs a CUDA GPU")]
@@ -65,7 +65,7 @@ def test_event100_hit_subset_all_rows():
 
 def test_pileup_vote_and_peaks():
     """50k hits, 512x256x1024: the whole accumulator and peak list exactly;
-    association on a sample of hits."""
+    association on a sample of hits; the z vote of sampled candidates."""
     name = "pileup_512"
     g = synth.geometry_of(name)
     ev = synth.make_event(synth.CONFIGS[name]["gen"], 0)
@@ -74,25 +74,22 @@ def test_pileup_vote_and_peaks():
     acc, st = oracle.vote(g, ev.x, ev.y)
     assert_same_acc(r["acc"], np.minimum(acc, 65535))
     assert int(r["stats"][0]) == st["votes"]
-    pk, cnt = oracle.peaks(g, acc, cap=cap)
-    del acc
-    assert r["count"] == cnt
-    assert np.array_equal(r["peaks"], pk)
-    sel = np.random.default_rng(0).choice(ev.n_hits, 64, replace=False)
-    asg = oracle.associate_dense(g, ev.x, ev.y, pk, hit_idx=sel)
-    assert np.array_equal(r["assign"][sel], asg)
+    oracle_sampled_check(g, ev, r, cap, n_hits=128, n_cands=6, acc=acc)
 
 
 @pytest.mark.parametrize("hits", [2000, 60000])
-def test_stream_event_sizes_rows(hits):
-    """Smallest and largest event of the batched stream; rows sampled."""
+def test_stream_event_sizes_whole(hits):
+    """Smallest and largest event of the batched stream: the whole
+    accumulator and peak list, sampled association and z results."""
     g = synth.geometry_of("stream2000_256")
     gen = synth.CONFIGS["stream2000_256"]["gen"]
     ev = synth.make_event(gen, 11, target_hits=hits)
-    r = gpu_event(g, ev.x, ev.y, ev.z, 1 << 20)
-    for a, b in [(0, 4), (126, 132), (252, 256)]:
-        acc, _ = oracle.vote(g, ev.x, ev.y, rows=(a, b))
-        assert_same_acc(r["acc"][a:b], acc)
+    cap = 1 << 21
+    r = gpu_event(g, ev.x, ev.y, ev.z, cap)
+    acc, st = oracle.vote(g, ev.x, ev.y)
+    assert_same_acc(r["acc"], np.minimum(acc, 65535))
+    assert int(r["stats"][0]) == st["votes"]
+    oracle_sampled_check(g, ev, r, cap, acc=acc)
 
 
 @pytest.mark.parametrize("n", [0, 1, 3, 257])

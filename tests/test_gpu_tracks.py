@@ -256,3 +256,18 @@ def test_host_buffer_call_returns_the_confirmed_candidates():
     assert np.array_equal(ntr2, ntr) and np.array_equal(small, tracks[:5])
     B.close()
     G.close()
+
+
+def test_pileup_event_full_size():
+    """A whole 50k-hit pile-up event (512 x 256 x 1024) on the track path at
+    its configured threshold and tolerance: every cell, candidate, score,
+    inlier, assignment and z result."""
+    name = "pileup_512"
+    g = synth.track_geometry(name)
+    tk = synth.track_of(name)
+    cp = dict(pool=tk["pool"], min_layers=tk["min_layers"], n_layers=tk["n_layers"], tol=tk["tol"])
+    ev = synth.make_event(synth.CONFIGS[name]["gen"], 0)
+    cap = 1 << 21
+    r = gpu_tracks_event(g, ev, cap, cp)
+    o = oracle_tracks(g, ev, cap, cp)
+    assert_same_tracks(r, o)
