@@ -362,6 +362,9 @@ def ht_run_event(g, hx, hy, hz, workspace, h_peaks, cap, h_count, h_assign, h_zr
                               _stream(stream)), "ht_run_event")
 
 
+TRACK_FIELDS = ["rho", "d0", "phi0", "sig_rho", "sig_d0", "sig_phi0"]
+
+
 def ht_fit_tracks(G, x, y, d_off, assign, peaks, d_count, cap, out, workspace, min_hits=4,
                   iters=5, sigma=20e-4, road=0.0, cut=0.0, iters2=3, stream=None):
     """Refit candidates.  out: uint8 tensor of n_events * cap * 64 bytes (one
