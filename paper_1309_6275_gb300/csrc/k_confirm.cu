@@ -112,29 +112,99 @@ __device__ __forceinline__ double circle_dist(float xf, float yf, double xc, dou
     return fabs(__dsub_rn(__dsqrt_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy))), R));
 }
 
-// (d, h) < (bd, bh) lexicographically; h < 0 is "none" (larger than all).
-__device__ __forceinline__ bool closer(double d, int h, double bd, int bh)
+// Float32 frame of the seed circle at its first point P1, for the distance
+// estimate t(w) = (k |w|^2 - 2 w.n) / (|k w - n| + 1), w = P - P1 (exact for
+// a unit n towards the centre and k = 1 / R), and the coefficients of a
+// bound e(w) = B2 |w|^2 + B1 (|w_x| + |w_y|) + B0 on |t(w)| minus the
+// float64 distance of the definition (circle3, then circle_dist).  With
+// a = P2 - P1, b = P3 - P1 (exact in float64), c = a_x b_y - a_y b_x and
+// v = (b_y |a|^2 - a_y |b|^2, a_x |b|^2 - b_x |a|^2), the centre is
+// P1 + v / (2 c) and |v| = |a| |b| |b - a|, so n = sign(c) v / |v| and
+// k = 2 |c| / |v|: v and c take float64 products and sums only (no division
+// or square root), the rest is float32.  The terms of the bound, u = 2^-24,
+// r = (|a| + |b|) / |b - a|, S = |a| |b| / |c| (one over the sine of the
+// angle at P1):
+//  - turning n by an angle moves t by at most |w| times it (a rotation
+//    about P1), a norm 1 + eta by at most 3 |eta| |w|: 13 u |w| for float32,
+//    2^-53 (6 sqrt2 r + 1) |w| for the float64 error of v;
+//  - |dt/dk| <= 2 |w|^2 (a circle through P1 is within |w| of P), times
+//    k's relative error 5.5 u + 2^-53 (S + 8.5 r + 2);
+//  - the float64 definition is within 2^-53 R (17 r + 2 S + 13) (+1e-12 cm)
+//    of the exact circle through the three points (R = 1 / k);
+//  - the float32 evaluation of t: 6e-7 (k |w|^2 + 2 (|w_x| + |w_y|)) + 1e-6
+//    cm;
+// each first-order and taken with a margin.  Returns false exactly when
+// circle3 does (c == 0 in its operation order).  A degenerate frame (an
+// underflow, r or S huge) gets B0 = +inf, which sends every distance to the
+// float64 definition.
+struct SeedFrame {
+    float x1, y1, nx, ny, kap, B0, B1, B2;
+};
+
+__device__ __forceinline__ bool seed_frame(float x1, float y1, float x2, float y2, float x3,
+                                           float y3, SeedFrame &F)
 {
-    if (h < 0) return false;
-    if (bh < 0) return true;
-    return d < bd || (d == bd && h < bh);
+    const double ax = __dsub_rn((double)x2, (double)x1), ay = __dsub_rn((double)y2, (double)y1);
+    const double bx = __dsub_rn((double)x3, (double)x1), by = __dsub_rn((double)y3, (double)y1);
+    const double c = __dsub_rn(__dmul_rn(ax, by), __dmul_rn(ay, bx));
+    if (c == 0.0) return false;
+    const double a2 = __fma_rn(ax, ax, __dmul_rn(ay, ay));
+    const double b2 = __fma_rn(bx, bx, __dmul_rn(by, by));
+    const float vx = (float)__fma_rn(by, a2, -__dmul_rn(ay, b2));
+    const float vy = (float)__fma_rn(ax, b2, -__dmul_rn(bx, a2));
+    const float cf = fabsf((float)c);
+    const float vn = sqrtf(fmaf(vx, vx, vy * vy));
+    const float ex = (float)__dsub_rn((double)x3, (double)x2);
+    const float ey = (float)__dsub_rn((double)y3, (double)y2);
+    const float la = sqrtf((float)a2), lb = sqrtf((float)b2);
+    const float r = 1.001f * (la + lb) / sqrtf(fmaf(ex, ex, ey * ey));
+    const float S = 1.001f * (la * lb) / cf;
+    F.x1 = x1;
+    F.y1 = y1;
+    if (!(vn > 0.0f && vn < 3.0e38f && cf > 0.0f && r < 1.0e6f && S < 1.0e9f)) {
+        F.nx = 1.0f;
+        F.ny = 0.0f;
+        F.kap = 0.0f;
+        F.B2 = F.B1 = 0.0f;
+        F.B0 = __int_as_float(0x7f800000);
+        return true;
+    }
+    const float sg = c > 0.0 ? 1.0f : -1.0f;
+    F.nx = sg * (vx / vn);
+    F.ny = sg * (vy / vn);
+    F.kap = 2.0f * cf / vn;
+    const float R = vn / (2.0f * cf);
+    F.B2 = F.kap * (1.3e-6f + 2.5e-16f * S + 2.2e-15f * r + 5e-16f);
+    F.B1 = 2.0e-6f + 1.2e-15f * r;
+    F.B0 = 1.0e-6f + 1.0e-12f + 1.22e-16f * R * (17.0f * r + 2.0f * S + 13.0f);
+    return true;
 }
 
-
-constexpr int kCfThreads = 256, kCfWarps = kCfThreads / 32;
-constexpr int kCfCap = 256;        // pool hits held per pass (more: further passes)
+constexpr int kCfThreads = 128, kCfWarps = kCfThreads / 32;
+constexpr int kCfCap = 512;        // pool hits held per pass (more: further passes)
 
 struct CfWarp {
     int n_own[16], own_pos[16];
     int best_h[16];
     double best_d[16];
-    unsigned lbmin[16];     // per layer: least lower bound of a pool hit's distance (float bits)
+    // per layer, over the pool hits of the pass: least lower and upper bound
+    // of a distance (float bits), contenders (count, one of them) and the
+    // pass's positions [qs, qe) (the pool is in layer order)
+    unsigned lbmin[16], ubmin[16];
+    int ncont[16], cq[16], qs[16], qe[16];
     int q[64];              // screened positions waiting for the exact evaluation
     int rs[32], rp[33];     // runs of index positions scanned: start, exclusive prefix of lengths
     int pool_p[kCfCap], pool_h[kCfCap];   // index position and event-local hit index
-    float pool_d[kCfCap], pool_e[kCfCap];   // float32 distance and its error bound
+    float pool_lo[kCfCap], pool_hi[kCfCap];   // bounds on the hit's float64 distance
     unsigned char pool_l[kCfCap];
+    SeedFrame F;            // the candidate's float32 seed frame
+    double xc, yc, R;       // and its float64 seed circle, once computed
+    int seed_pos[3];        // index positions of the three seed hits
 };
+
+// The warps' state of k_confirm (at namespace scope, so that the functions
+// that take a warp's index address it as shared memory).
+__shared__ CfWarp g_cfw[kCfWarps];
 
 // The hits a candidate scans: the t-th of the runs W.rs / W.rp of the
 // event's hit index (k_hitindex.cu).
@@ -142,18 +212,18 @@ struct HitView {
     const float *x, *y;
     const int *h;
     const uint8_t *l;
-    const CfWarp *W;
-    int n;   // total positions
+    int wid;   // the warp's state in g_cfw
+    int n;     // total positions
 
     __device__ __forceinline__ int pos(int t) const
     {
         int lo = 0, hi = 31;   // the last run r with rp[r] <= t
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (W->rp[mid] <= t) lo = mid;
+            if (g_cfw[wid].rp[mid] <= t) lo = mid;
             else hi = mid - 1;
         }
-        return W->rs[lo] + (t - W->rp[lo]);
+        return g_cfw[wid].rs[lo] + (t - g_cfw[wid].rp[lo]);
     }
 };
 
@@ -255,9 +325,10 @@ struct PoolScreen {
 // count_own, the own hits per layer.  Returns the total number of pool hits.
 // Hits that pass the float32 screen queue up in order and get the exact
 // evaluation 32 at a time, so that the lanes stay busy.
-__device__ __forceinline__ int scan_pool(const DevGeom &G, const HitView &V, int i, int j, int k,
-                                         int pool, int r0, bool count_own, CfWarp &W, int lane)
+__device__ __noinline__ int scan_pool(const DevGeom &G, const HitView V, int i, int j, int k,
+                                      int pool, int r0, bool count_own, int lane)
 {
+    CfWarp &W = g_cfw[V.wid];
     ColumnCtx C;
     C.init(G, i, k);
     PoolScreen ps;
@@ -325,13 +396,6 @@ __device__ __forceinline__ int scan_pool(const DevGeom &G, const HitView &V, int
     return rank;
 }
 
-__device__ __forceinline__ float warp_minf(float v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
-
 // The runs of index positions a candidate of event e in column (rho_i,
 // phi0_k) with bin j scans: per layer its azimuth window (layer_window) for
 // d0 within two bins beyond the pool, as one or two runs of cells (the
@@ -388,23 +452,26 @@ __device__ __forceinline__ void candidate_runs(const DevGeom &G, const ConfirmDe
 // Confirmation of one candidate by one warp (see the file comment).  Writes
 // score[slot] (0 = not confirmed) and inl[16 slot + l].
 //
-// Distances: a float32 estimate with a first-order error bound decides
-// every hit that is certainly farther than tol, or certainly not the
-// nearest of its layer; the float64 distance of the definition is computed
-// only for the rest.  The estimate works in the circle's local frame at the
-// first seed hit P1 (unit normal n towards the centre, curvature k = 1/R):
-// with w = P - P1 the signed distance is
-//   t = (k |w|^2 - 2 w.n) / (|k w - n| + 1),
-// whose terms are all of the order of |w| (no large centre coordinates), so
-// rounding the inputs and the frame to float32 moves t by a few 2^-24 |w|
-// (e = 6e-7 (k |w|^2 + 2 (|w_x| + |w_y|)) + 1e-6 cm covers it with a wide
-// margin).
+// Distances: the float32 estimate of seed_frame and its bound give every
+// pool hit an interval [lo, hi] holding its float64 distance.  Per layer
+// the contenders are the hits with lo at most the layer's least hi and
+// below tol; the layer's nearest hit is one of them.  A layer without a
+// contender has no inlier, a single contender certainly below tol is the
+// inlier, and otherwise the float64 distances of the contenders decide
+// (the definition's seed circle is computed then, once per candidate).
+// When fewer than min_layers layers can hold an inlier the candidate is not
+// confirmed, without any float64 distance.  Pools larger than kCfCap go in
+// passes of kCfCap hits, every contender by its float64 distance.
 __device__ __forceinline__ void confirm_one(const DevGeom &G, const ConfirmDev &P,
                                             const HitIndex &I, int e, const ht_peak pk,
-                                            size_t slot, float tol_hi, int *__restrict__ score,
-                                            int *__restrict__ inl, CfWarp &W, int lane)
+                                            size_t slot, float tol_lo, float tol_hi,
+                                            int *__restrict__ score, int *__restrict__ inl,
+                                            int wid, int lane)
 {
-    HitView V{I.x, I.y, I.h, I.l, &W, 0};
+    CfWarp &W = g_cfw[wid];
+    constexpr unsigned kAll = 0xffffffffu;
+    const float kInf = __int_as_float(0x7f800000);
+    HitView V{I.x, I.y, I.h, I.l, wid, 0};
     candidate_runs(G, P, I, e, pk.i_rho, pk.j_d0, pk.k_phi0, W, V, lane);
     if (lane < 16) {
         W.n_own[lane] = 0;
@@ -412,110 +479,166 @@ __device__ __forceinline__ void confirm_one(const DevGeom &G, const ConfirmDev &
         W.best_d[lane] = 0.0;
     }
     __syncwarp();
-    const int npool = scan_pool(G, V, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool, 0, true, W, lane);
-    // seed layers (every lane computes the same)
-    int la = -1, lc = -1, ns = 0;
-    for (int l = 0; l < P.n_layers; ++l)
-        if (W.n_own[l] == 1) {
-            if (la < 0) la = l;
-            lc = l;
-            ++ns;
+    const long long tol_bits = __double_as_longlong(P.tol);
+    const SeedFrame &F = W.F;
+    bool ok = false, exact = false, rejected = false;
+    const int npool = scan_pool(G, V, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool, 0, true, lane);
+    {
+        // seed layers (every lane computes the same)
+        int la = -1, lb = -1, lc = -1, ns = 0;
+        for (int l = 0; l < P.n_layers; ++l)
+            if (W.n_own[l] == 1) {
+                if (la < 0) la = l;
+                lc = l;
+                ++ns;
+            }
+        int gap = 1 << 30;
+        for (int l = la + 1; ns >= 3 && l < lc; ++l)
+            if (W.n_own[l] == 1 && abs(2 * l - (la + lc)) < gap) {
+                gap = abs(2 * l - (la + lc));
+                lb = l;
+            }
+        if (ns >= 3) {
+            if (lane == 0) {
+                const int pa = W.own_pos[la], pb = W.own_pos[lb], pc = W.own_pos[lc];
+                const bool f = seed_frame(V.x[pa], V.y[pa], V.x[pb], V.y[pb], V.x[pc], V.y[pc], W.F);
+                W.seed_pos[0] = f ? pa : -1;
+                W.seed_pos[1] = pb;
+                W.seed_pos[2] = pc;
+            }
+            __syncwarp();
+            ok = W.seed_pos[0] >= 0;
         }
-    int lb = -1, gap = 1 << 30;
-    for (int l = la + 1; ns >= 3 && l < lc; ++l)
-        if (W.n_own[l] == 1 && abs(2 * l - (la + lc)) < gap) {
-            gap = abs(2 * l - (la + lc));
-            lb = l;
-        }
-    double xc = 0.0, yc = 0.0, R = 0.0;
-    bool ok = ns >= 3;
-    float x1f = 0.0f, y1f = 0.0f;
-    if (ok) {
-        const int pa = W.own_pos[la], pb = W.own_pos[lb], pc = W.own_pos[lc];
-        x1f = V.x[pa];
-        y1f = V.y[pa];
-        ok = circle3((double)x1f, (double)y1f, (double)V.x[pb], (double)V.y[pb],
-                     (double)V.x[pc], (double)V.y[pc], xc, yc, R);
     }
-    int sc = 0;
-    if (ok) {
-        const double iR = 1.0 / R;
-        const float nx = (float)(__dsub_rn(xc, (double)x1f) * iR);
-        const float ny = (float)(__dsub_rn(yc, (double)y1f) * iR);
-        const float kap = (float)iR;
-        for (int r0 = 0; r0 < npool; r0 += kCfCap) {
-            if (r0 > 0)
-                scan_pool(G, V, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool, r0, false, W, lane);
-            const int nq = min(npool - r0, kCfCap);
-            if (lane < 16) W.lbmin[lane] = 0x7f800000u;   // +inf
-            __syncwarp();
-            for (int q = lane; q < nq; q += 32) {
+    for (int r0 = 0; ok && r0 < npool; r0 += kCfCap) {
+        if (r0 > 0) scan_pool(G, V, pk.i_rho, pk.j_d0, pk.k_phi0, P.pool, r0, false, lane);
+        const bool single = npool <= kCfCap;
+        const int nq = min(npool - r0, kCfCap);
+        if (lane < 16) {
+            W.lbmin[lane] = W.ubmin[lane] = 0x7f800000u;   // +inf
+            W.ncont[lane] = 0;
+            W.qs[lane] = kCfCap;
+            W.qe[lane] = 0;
+        }
+        __syncwarp();
+        // the bounds of every pool hit, and their least values per layer
+        // (the pool is in layer order: each layer is one run of lanes)
+        for (int q0 = 0; q0 < nq; q0 += 32) {
+            const int q = q0 + lane;
+            int l = 16;
+            float lo = kInf, hi = kInf;
+            if (q < nq) {
                 const int p = W.pool_p[q];
-                const float wx = V.x[p] - x1f, wy = V.y[p] - y1f;
+                l = W.pool_l[q];
+                const float wx = V.x[p] - F.x1, wy = V.y[p] - F.y1;
                 const float w2 = fmaf(wx, wx, wy * wy);
-                const float wn = fmaf(wx, nx, wy * ny);
-                const float num = fmaf(kap, w2, -2.0f * wn);
-                const float qx = fmaf(kap, wx, -nx), qy = fmaf(kap, wy, -ny);
-                const float den = sqrtf(fmaf(qx, qx, qy * qy)) + 1.0f;
-                const float d = fabsf(num / den);
-                const float er =
-                    fmaf(6e-7f, fmaf(kap, w2, 2.0f * (fabsf(wx) + fabsf(wy))), 1e-6f);
-                W.pool_d[q] = d;
-                W.pool_e[q] = er;
-                atomicMin(&W.lbmin[W.pool_l[q]], __float_as_uint(fmaxf(d - er, 0.0f)));
+                const float wn = fmaf(wx, F.nx, wy * F.ny);
+                const float num = fmaf(F.kap, w2, -2.0f * wn);
+                const float qx = fmaf(F.kap, wx, -F.nx), qy = fmaf(F.kap, wy, -F.ny);
+                const float d = fabsf(num / (sqrtf(fmaf(qx, qx, qy * qy)) + 1.0f));
+                const float er = fmaf(F.B2, w2, fmaf(F.B1, fabsf(wx) + fabsf(wy), F.B0));
+                const float dl = __fsub_rd(d, er);
+                lo = dl > 0.0f ? dl : 0.0f;   // +0 (the bits order as the values)
+                hi = __fadd_ru(d, er);
+                W.pool_lo[q] = lo;
+                W.pool_hi[q] = hi;
+            }
+            float slo = lo, shi = hi;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const float olo = __shfl_down_sync(kAll, slo, o);
+                const float ohi = __shfl_down_sync(kAll, shi, o);
+                const int ol = __shfl_down_sync(kAll, l, o);
+                if (lane + o < 32 && ol == l) {
+                    slo = fminf(slo, olo);
+                    shi = fminf(shi, ohi);
+                }
+            }
+            const int lp = __shfl_up_sync(kAll, l, 1), ln = __shfl_down_sync(kAll, l, 1);
+            if (q < nq && (lane == 0 || lp != l)) {
+                atomicMin(&W.lbmin[l], __float_as_uint(slo));
+                atomicMin(&W.ubmin[l], __float_as_uint(shi));
+                atomicMin(&W.qs[l], q);
+            }
+            if (q < nq && (lane == 31 || ln != l)) atomicMax(&W.qe[l], q + 1);
+        }
+        __syncwarp();
+        if (single) {
+            // layers that can hold an inlier at all: too few, not confirmed
+            const bool can = lane < P.n_layers && __uint_as_float(W.lbmin[lane]) < tol_hi;
+            if (__popc(__ballot_sync(kAll, can)) < P.min_layers) {
+                rejected = true;
+                break;
+            }
+        }
+        for (int q = lane; q < nq; q += 32) {
+            const int l = W.pool_l[q];
+            const float lo = W.pool_lo[q];
+            if (lo <= __uint_as_float(W.ubmin[l]) && lo < tol_hi) {
+                atomicAdd(&W.ncont[l], 1);
+                W.cq[l] = q;   // read only where the layer has one contender
+            }
+        }
+        __syncwarp();
+        bool need = false;
+        if (lane < P.n_layers) {
+            const int nc = W.ncont[lane];
+            if (single && nc == 1 && W.pool_hi[W.cq[lane]] < tol_lo) {
+                W.best_h[lane] = W.pool_h[W.cq[lane]];   // certainly the inlier
+                W.best_d[lane] = 0.0;                     // (below tol)
+            } else {
+                need = nc > 0;
+            }
+        }
+        const unsigned need_m = __ballot_sync(kAll, need);
+        if (need_m != 0u && !exact) {
+            if (lane == 0) {
+                const int pa = W.seed_pos[0], pb = W.seed_pos[1], pc = W.seed_pos[2];
+                circle3((double)V.x[pa], (double)V.y[pa], (double)V.x[pb], (double)V.y[pb],
+                        (double)V.x[pc], (double)V.y[pc], W.xc, W.yc, W.R);
             }
             __syncwarp();
-            if (npool <= kCfCap) {
-                // layers that can hold an inlier at all: too few, not confirmed
-                int poss = 0;
-                for (int l = 0; l < P.n_layers; ++l)
-                    poss += __uint_as_float(W.lbmin[l]) < tol_hi ? 1 : 0;
-                if (poss < P.min_layers) break;
+            exact = true;
+        }
+        for (unsigned m = need_m; m != 0u; m &= m - 1u) {
+            const int l = __ffs(m) - 1;
+            const float ub = __uint_as_float(W.ubmin[l]);
+            long long bk = 0x7fffffffffffffffll;   // none: above every distance's bits
+            int bh = -1;
+            for (int q = W.qs[l] + lane; q < W.qe[l]; q += 32) {
+                const float lo = W.pool_lo[q];
+                if (!(lo <= ub && lo < tol_hi)) continue;
+                const int p = W.pool_p[q], h = W.pool_h[q];
+                const long long key = __double_as_longlong(circle_dist(V.x[p], V.y[p], W.xc, W.yc, W.R));
+                if (key < bk || (key == bk && h < bh)) {
+                    bk = key;
+                    bh = h;
+                }
             }
-            for (int l = 0; l < P.n_layers; ++l) {
-                if (!(__uint_as_float(W.lbmin[l]) < tol_hi)) continue;   // uniform
-                float ub = 3.0e38f;   // the least upper bound on this layer
-                for (int q = lane; q < nq; q += 32)
-                    if (W.pool_l[q] == l) ub = fminf(ub, W.pool_d[q] + W.pool_e[q]);
-                ub = warp_minf(ub);
-                // contenders: may be the layer's nearest and below tol
-                double bd = 0.0;
-                int bh = -1;
-                for (int q = lane; q < nq; q += 32) {
-                    if (W.pool_l[q] != l) continue;
-                    const float lo = W.pool_d[q] - W.pool_e[q];
-                    if (!(lo <= ub && lo < tol_hi)) continue;
-                    const int p = W.pool_p[q], h = W.pool_h[q];
-                    const double dd = circle_dist(V.x[p], V.y[p], xc, yc, R);
-                    if (closer(dd, h, bd, bh)) {
-                        bd = dd;
-                        bh = h;
-                    }
-                }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    const double od = __shfl_xor_sync(0xffffffffu, bd, o);
-                    const int oh = __shfl_xor_sync(0xffffffffu, bh, o);
-                    if (closer(od, oh, bd, bh)) {
-                        bd = od;
-                        bh = oh;
-                    }
+            for (int o = 16; o > 0; o >>= 1) {
+                const long long ok2 = __shfl_xor_sync(kAll, bk, o);
+                const int oh = __shfl_xor_sync(kAll, bh, o);
+                if (ok2 < bk || (ok2 == bk && oh < bh)) {
+                    bk = ok2;
+                    bh = oh;
                 }
-                if (lane == 0 && closer(bd, bh, W.best_d[l], W.best_h[l])) {
-                    W.best_d[l] = bd;
+            }
+            if (lane == 0 && bh >= 0) {
+                const long long cur = __double_as_longlong(W.best_d[l]);
+                if (W.best_h[l] < 0 || bk < cur || (bk == cur && bh < W.best_h[l])) {
+                    W.best_d[l] = __longlong_as_double(bk);
                     W.best_h[l] = bh;
                 }
             }
-            __syncwarp();
         }
-        for (int l = 0; l < P.n_layers; ++l)
-            sc += (W.best_h[l] >= 0 && W.best_d[l] < P.tol) ? 1 : 0;
+        __syncwarp();
     }
-    const bool conf = ok && sc >= P.min_layers;
-    if (lane < 16) {
-        const bool in = conf && lane < P.n_layers && W.best_h[lane] >= 0 && W.best_d[lane] < P.tol;
-        inl[slot * 16 + lane] = in ? W.best_h[lane] : -1;
-    }
+    const bool in_l = ok && !rejected && lane < P.n_layers && W.best_h[lane] >= 0 &&
+                      __double_as_longlong(W.best_d[lane]) < tol_bits;
+    const int sc = __popc(__ballot_sync(kAll, in_l));
+    const bool conf = ok && !rejected && sc >= P.min_layers;
+    if (lane < 16) inl[slot * 16 + lane] = conf && in_l ? W.best_h[lane] : -1;
     if (lane == 0) score[slot] = conf ? sc : 0;
     __syncwarp();
 }
@@ -528,20 +651,20 @@ __device__ __forceinline__ void confirm_one(const DevGeom &G, const ConfirmDev &
 // batch's hit index (k_hitindex.cu).
 constexpr int kCfChunk = 64;
 
-__global__ void __launch_bounds__(kCfThreads)
+__global__ void __launch_bounds__(kCfThreads, 5)
 k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
           const ht_peak *__restrict__ peaks, int cap, const int *__restrict__ cpre,
           const int *__restrict__ order, int *__restrict__ score, int *__restrict__ inl,
           int *__restrict__ head)
 {
-    __shared__ CfWarp sw[kCfWarps];
     __shared__ int s_chunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    CfWarp &W = sw[warp];
     const int n_ev = *d_nev;
     const int total = cpre[n_ev];
     float tol_hi = (float)P.tol;   // tol rounded up to float32
     if ((double)tol_hi < P.tol) tol_hi = nextafterf(tol_hi, 3.0e38f);
+    float tol_lo = (float)P.tol;   // and down
+    if ((double)tol_lo > P.tol) tol_lo = nextafterf(tol_lo, 0.0f);
     for (;;) {
         if (threadIdx.x == 0) s_chunk = atomicAdd(head, 1);
         __syncthreads();
@@ -553,7 +676,7 @@ k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
             const int f = __ldg(order + t);
             const int e = event_of(cpre, n_ev, f);
             const size_t slot = (size_t)e * cap + (f - cpre[e]);
-            confirm_one(G, P, I, e, peaks[slot], slot, tol_hi, score, inl, W, lane);
+            confirm_one(G, P, I, e, peaks[slot], slot, tol_lo, tol_hi, score, inl, warp, lane);
         }
     }
 }
