@@ -230,26 +230,34 @@ __device__ __forceinline__ float hit_cos_window(const DevGeom &G, float r2)
 }
 
 // Curvature range reached by circles through a hit (s, c) with perigee d0 in
-// the (extended) axis: rho = g(w) = -2 w / (w^2 + c^2), w = d0 + s, which
-// falls on |w| < c and rises outside, so its extremes over an interval are at
-// the ends or at w = -c (max 1/c) and w = c (min -1/c).  Used only to skip
-// (hit, column) pairs that cannot vote in a block of rows; callers keep a
-// full-row margin and skip the test for c <= 1 cm.
-__device__ __forceinline__ void rho_range_w(float wlo, float whi, float c, float &gmin,
+// the (extended) axis: the circle equation is rho (w^2 + c^2) + 2 w = 0 with
+// w = d0 + s, so rho = g(w) = -2 w / (w^2 + c^2), which falls on |w| < c and
+// rises outside; its extremes over an interval are at the ends or at w = -c
+// (max 1/c) and w = c (min -1/c).  Used only to skip (hit, column) pairs
+// that cannot vote in a block of rows, and widened so that it holds the
+// range of the float64 s and c: e bounds the float32 error of both (the
+// caller's 3 2^-24 (|x| + |y|) from the rounded tables and products), the
+// window grows by e, and the range by 1.5 e / c^2 (|dg/dc| <= 1.3 / c^2)
+// plus 1e-6 / c for the float32 evaluation (|g| <= 1 / c; a few ulp).
+// Callers keep a one-row margin besides and skip the test for c <= 1 cm.
+__device__ __forceinline__ void rho_range_w(float wlo, float whi, float c, float e, float &gmin,
                                             float &gmax)
 {
+    wlo -= e;
+    whi += e;
     const float c2 = c * c;
     const float glo = __fdividef(-2.0f * wlo, fmaf(wlo, wlo, c2));
     const float ghi = __fdividef(-2.0f * whi, fmaf(whi, whi, c2));
-    const float ic = rcp_approx(c);   // a few ulp: far inside the callers' one-row margin
-    gmax = (wlo <= -c && -c <= whi) ? ic : fmaxf(glo, ghi);
-    gmin = (wlo <= c && c <= whi) ? -ic : fminf(glo, ghi);
+    const float ic = rcp_approx(c);
+    const float m = fmaf(1.5f * e, ic * ic, 1e-6f * ic);
+    gmax = ((wlo <= -c && -c <= whi) ? ic : fmaxf(glo, ghi)) + m;
+    gmin = ((wlo <= c && c <= whi) ? -ic : fminf(glo, ghi)) - m;
 }
 
-__device__ __forceinline__ void rho_range(const DevGeom &G, float s, float c,
+__device__ __forceinline__ void rho_range(const DevGeom &G, float s, float c, float e,
                                           float &gmin, float &gmax)
 {
-    rho_range_w(G.d0lo_f + s, G.d0hi_f + s, c, gmin, gmax);
+    rho_range_w(G.d0lo_f + s, G.d0hi_f + s, c, e, gmin, gmax);
 }
 
 // ---------------------------------------------------------------------------

@@ -6,7 +6,9 @@
 // A hit can vote in column k only where c = r cos(phi0_k - psi) reaches the
 // hit's angular window (hit_cos_window, ht_internal.cuh): |phi0_k - psi| <= w
 // with cos w = cmin / r.  The lists keep every hit whose widened window
-// (0.02 cm on c, 2e-3 rad on the angle, one column on each side) meets a
+// (0.02 cm plus 4e-7 (|x| + |y|) on c, the bound of phase 1's float32
+// error in c; 2e-3 rad on the angle, which also covers acos near 1 for an
+// error below 2e-6 in its argument; one column on each side) meets a
 // column of the group -- a superset of what phase 1 keeps, which still
 // tests every column, so the votes are the same.  Hits within a list are in
 // no particular order; nothing downstream depends on it.
@@ -37,7 +39,7 @@ __device__ __forceinline__ void hit_groups(const DevGeom &G, float x, float y, i
     const float r2 = fmaf(x, x, y * y);
     const float r = sqrtf(r2);
     const float cmin = hit_cos_window(G, r2);
-    const float thr = (cmin - 0.02f) / r;
+    const float thr = (cmin - fmaf(4e-7f, fabsf(x) + fabsf(y), 0.02f)) / r;
     if (!(thr > -1.0f)) {            // window covers the circle (or r == 0)
         g_lo = 0;
         ng = NG;

@@ -287,12 +287,16 @@ __device__ __forceinline__ void layer_window(float rho, float phik, float lo, fl
 }
 
 // Float32 screen of a hit against a candidate's pool: false only when both
-// roots certainly lie more than two bins outside [j - pool, j + pool].
-// Where D > 1e-3, |q| >= sqrt(D) > 0.03 and the float32 roots of any circle
-// with |d0| below a few tens of cm are within a few 1e-3 cm of the exact
-// ones (first-order bounds of the vote's guard, far below two bins); roots
-// far outside the axis stay far outside.  D <= 1e-3 (near tangent) always
-// goes to the exact evaluation; D < -1e-3 has no real root.
+// roots certainly lie outside [lo, hi) = [j - pool - 2, j + pool + 3) (bin
+// coordinates), which holds every root whose bin is within pool of j.  D is
+// within 4e-7 (rho c)^2 of its float64 value; past eD = 1e-3 + that bound
+// the sign is certain (below -eD no real root; within +-eD the hit goes to
+// the exact evaluation), and |q| >= sqrt(D) > 0.03.  Root A = C / q then has
+// a first-order float32 error below 4e-7 (|rho| r^2 + 2 (|x| + |y|) + |C|)
+// / |q| cm (the inputs s and c carry 3 2^-24 (|x| + |y|), C and q a few ulp
+// each), plus 3e-7 |u| + 1e-3 bins for the conversion to a bin coordinate:
+// the test widens [lo, hi) by that.  Root B = q / rho has a relative error
+// of a few ulp, far below the two bins of margin for any root near the axis.
 struct PoolScreen {
     float rho, invrho_d, lo, hi, sk, ck;
     bool has_b;
@@ -305,13 +309,18 @@ struct PoolScreen {
         const float b = fmaf(rho, s, 1.0f);
         const float pc = rho * c;
         const float D = fmaf(-pc, pc, 1.0f);
-        if (D < -1e-3f) return false;
-        if (D <= 1e-3f) return true;
+        const float eD = fmaf(4e-7f, pc * pc, 1e-3f);
+        if (D < -eD) return false;
+        if (D <= eD) return true;
         const float sq = D * rsqrt_approx(D);
         const float q = -(b + copysignf(sq, b));
-        const float C = fmaf(rho, fmaf(xf, xf, yf * yf), s + s);
-        const float uA = fmaf(C * rcp_approx(q), inv_delta, off);
-        bool near = uA >= lo && uA < hi;
+        const float r2 = fmaf(xf, xf, yf * yf);
+        const float C = fmaf(rho, r2, s + s);
+        const float iq = rcp_approx(q);
+        const float uA = fmaf(C * iq, inv_delta, off);
+        const float ec = 4e-7f * (fmaf(fabsf(rho), r2, 2.0f * (fabsf(xf) + fabsf(yf))) + fabsf(C));
+        const float eA = fmaf(ec * fabsf(iq), inv_delta, fmaf(3e-7f, fabsf(uA), 1e-3f));
+        bool near = uA >= lo - eA && uA < hi + eA;
         if (has_b) {
             const float uB = fmaf(q, invrho_d, off);
             near |= uB >= lo && uB < hi;

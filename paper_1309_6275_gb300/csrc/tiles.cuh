@@ -90,11 +90,14 @@ struct TileCtx {
         rt = fmaxf(fabsf(G.rho32[i0]), fabsf(G.rho32[ilast])) * 1.0001f;
         // the second root q / rho can reach the axis only if |1 + rho s| <=
         // |rho| dext, i.e. |s| >= 1 / rt - dext for the rows of this tile
-        sB = rt > 0.0f ? __frcp_rn(rt) - G.dext_f - 0.01f : 3.0e38f;
+        // (|q| >= |b|); the float32 bound is lowered by 1e-6 relative and
+        // 0.01 cm (its own rounding), and phase 1 lowers it further by the
+        // error of the hit's float32 s
+        sB = rt > 0.0f ? fmaf(__frcp_rn(rt) - G.dext_f, 1.0f - 1e-6f, -0.01f) : 3.0e38f;
         // |q| = |b| + sqrt(D) >= sqrt(1 - rho^2 c^2), so q / rho also needs
-        // c^2 >= 1 / rho^2 - dext^2 >= 1 / rt^2 - dext^2
+        // c^2 >= 1 / rho^2 - dext^2 >= 1 / rt^2 - dext^2 (same margins)
         const float ir = rt > 0.0f ? __frcp_rn(rt) : 3.0e19f;
-        cB = sqrtf(fmaxf(fmaf(ir, ir, -G.dext_f * G.dext_f), 0.0f)) - 0.05f;
+        cB = fmaf(sqrtf(fmaxf(fmaf(ir, ir, -G.dext_f * G.dext_f), 0.0f)), 1.0f - 1e-6f, -0.05f);
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
             sk[kl] = G.sn32[k0 + kl];
@@ -205,6 +208,9 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
         R1 = fabsf(xh) + fabsf(yh);
         const float cmin = hit_cos_window(G, r2);
         const float Ec = (kSafe * 3.0f * kEps) * R1;
+        // float32 s and c are within 3 2^-24 R1 of the float64 ones (the
+        // tables' and the products' rounding): 4e-7 R1 bounds it
+        const float eS = 4e-7f * R1;
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
             const float c = fmaf(xh, T.ck[kl], yh * T.sk[kl]);
@@ -216,24 +222,24 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
             } else if (c > 1.0f) {
                 float gmin, gmax;
                 if (BM == kModeHit) {
-                    rho_range_w(hwlo + s, hwhi + s, c, gmin, gmax);
+                    rho_range_w(hwlo + s, hwhi + s, c, eS, gmin, gmax);
                     if (gmax < T.rho_lo || gmin > T.rho_hi) continue;
                 } else if (BM == kModeEvent) {
                     bool reach = false;
 #pragma unroll
                     for (int r = 0; r < 4; ++r) {
                         if (r < M->nrun) {
-                            rho_range_w(M->wlo[r] + s, M->whi[r] + s, c, gmin, gmax);
+                            rho_range_w(M->wlo[r] + s, M->whi[r] + s, c, eS, gmin, gmax);
                             reach |= !(gmax < M->rho_lo || gmin > M->rho_hi);
                         }
                     }
                     if (!reach) continue;
                 } else {
-                    rho_range(G, s, c, gmin, gmax);
+                    rho_range(G, s, c, eS, gmin, gmax);
                     if (gmax < T.rho_lo || gmin > T.rho_hi) continue;
                 }
             }
-            if (fabsf(s) >= T.sB && c >= T.cB) f |= kMetaNeedB;
+            if (fabsf(s) + eS >= T.sB && c + eS >= T.cB) f |= kMetaNeedB;
             sel |= 1u << kl;
             fl_[kl] = f;
             is_[kl] = s;

@@ -98,3 +98,64 @@ def oracle_sampled_check(g, ev, r, cap, n_hits=256, n_cands=8, seed=0, acc=None)
             zo = oracle.vote_z(g, ev.x, ev.y, ev.z, full, pk, cand=np.array([m]))
             assert np.array_equal(np.asarray(r["zres"])[m], zo[0]), m
     return pk
+
+
+# ------------------------------------------------------------------ track path
+def gpu_tracks_event(g, ev, cap, cp):
+    """The five calls of the track path on one event; numpy results."""
+    import torch
+    from paper_1309_6275_gb300 import ht
+    G = ht.Geometry(g)
+    n = ev.n_hits
+    x, y, z = to_dev(ev.x), to_dev(ev.y), to_dev(ev.z)
+    lay = to_dev(ev.layer.astype(np.uint8))
+    acc = G.new_accumulator()
+    stats = torch.zeros(2, dtype=torch.int64, device="cuda")
+    ht.ht_vote_layers(G, x, y, lay, acc, stats)
+    c1 = max(cap, 1)
+    peaks = torch.empty((c1, 4), dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(max(G.find_peaks_workspace_size(), G.vote_z_workspace_size(max(n, 1), cap),
+                         ht.ht_confirm_workspace_size(G, n, cap)), dtype=torch.uint8, device="cuda")
+    ht.ht_find_peaks(G, acc, peaks, cap, count, ws)
+    score = torch.full((c1,), -7, dtype=torch.int32, device="cuda")
+    inl = torch.full((c1, 16), -7, dtype=torch.int32, device="cuda")
+    assign = torch.full((max(n, 1),), -7, dtype=torch.int32, device="cuda")
+    ht.ht_confirm(G, cp, x, y, lay, peaks, count, cap, score, inl, assign[:n], ws)
+    zres = torch.empty((c1, 3), dtype=torch.int32, device="cuda")
+    ht.ht_vote_z(G, x, y, z, assign[:n], peaks, count, cap, zres, ws)
+    torch.cuda.synchronize()
+    cnt = int(count.item())
+    k = min(cnt, cap)
+    a = acc.cpu().numpy()
+    r = dict(acc=a.view(np.uint16) if a.dtype == np.int16 else a, count=cnt,
+             peaks=peaks[:k].cpu().numpy(), score=score[:k].cpu().numpy(),
+             inl=inl[:k].cpu().numpy(), assign=assign[:n].cpu().numpy(),
+             zres=zres[:k].cpu().numpy(), votes=int(stats[0].item()))
+    G.close()
+    check_assign(r["assign"], r["count"])
+    return r
+
+
+def oracle_tracks(g, ev, cap, cp, masks=None):
+    acc, st = oracle.vote_layers(g, ev.x, ev.y, ev.layer, masks)
+    pk, cnt = oracle.peaks(g, acc, cap)
+    score, seeds, inl = oracle.confirm(g, ev.x, ev.y, ev.layer, pk, cp)
+    asg = oracle.confirm_assign(score, inl, ev.n_hits)
+    zr = oracle.vote_z(g, ev.x, ev.y, ev.z, asg, pk)
+    return dict(acc=acc, votes=st["votes"], peaks=pk, count=cnt, score=score, inl=inl,
+                assign=asg, zres=zr)
+
+
+def assert_same_tracks(r, o, acc=True):
+    if acc:
+        assert_same_acc(r["acc"], o["acc"])
+        assert r["votes"] == o["votes"]
+    assert r["count"] == o["count"]
+    assert np.array_equal(r["peaks"], o["peaks"])
+    bad = np.flatnonzero(r["score"] != o["score"])
+    assert bad.size == 0, f"{bad.size} scores differ, first {bad[:5]}: {r['score'][bad[:5]]} vs {o['score'][bad[:5]]}"
+    assert np.array_equal(r["inl"], o["inl"])
+    bad = np.flatnonzero(r["assign"] != o["assign"])
+    assert bad.size == 0, f"{bad.size} assignments differ, first {bad[:5]}"
+    assert np.array_equal(r["zres"], o["zres"])
