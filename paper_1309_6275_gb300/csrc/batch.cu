@@ -125,6 +125,7 @@ struct ht_batch {
     unsigned long long *gbest;
     char *pk_ws;
     size_t pk_stride;
+    char *pk_spill;     // one spill buffer: the events' peak launches run in turn
     int ntiles;
     int *tcnt, *toff, *tcur;
     char *ttmp;
@@ -175,6 +176,7 @@ void free_batch(ht_batch *b)
     cudaFree(b->heads);
     cudaFree(b->gbest);
     cudaFree(b->pk_ws);
+    cudaFree(b->pk_spill);
     cudaFree(b->tcnt);
     cudaFree(b->toff);
     cudaFree(b->tcur);
@@ -278,7 +280,8 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     for (int ev = 0; ev < n_ev; ++ev) {
         e = ht::launch_peaks(G, b->acc + (size_t)ev * b->cells, peaks + (size_t)ev * b->cap,
                              b->cap, counts + ev, b->pk_ws + (size_t)ev * b->pk_stride, st,
-                             masks ? masks + ev : nullptr, tracks ? thr_of(meta, me) + ev : nullptr);
+                             masks ? masks + ev : nullptr, tracks ? thr_of(meta, me) + ev : nullptr,
+                             b->pk_spill);
         if (e != cudaSuccess) return e;
         if (tracks) continue;
         const size_t to = (size_t)ev * (b->ntiles + 1);
@@ -426,6 +429,7 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     M((void **)&b->heads, 256);
     M((void **)&b->gbest, (size_t)max_hits * 8);
     M((void **)&b->pk_ws, b->pk_stride * max_events);
+    M((void **)&b->pk_spill, ht::peak_spill_bytes(G));
     M((void **)&b->tcnt, tl);
     M((void **)&b->toff, tl);
     M((void **)&b->tcur, tl);

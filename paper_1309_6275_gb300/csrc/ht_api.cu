@@ -359,9 +359,20 @@ ht_status ht_confirm(const ht_geometry *g, const ht_confirm_desc *c, const float
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_confirm");
 }
 
+// The workspace: the segment counts and offsets and the scan's scratch
+// (peaks_workspace_bytes, enough), then the spill buffer that saves the
+// second stencil pass when the workspace also holds it.
 size_t ht_find_peaks_workspace_size(const ht_geometry *g)
 {
-    return g ? ht::peaks_workspace_bytes(g->G) : 0;
+    return g ? ht::align256(ht::peaks_workspace_bytes(g->G)) + ht::peak_spill_bytes(g->G) : 0;
+}
+
+static void *peak_spill_of(const ht::DevGeom &G, void *workspace, size_t workspace_bytes)
+{
+    const size_t a = ht::align256(ht::peaks_workspace_bytes(G));
+    return workspace_bytes >= a + ht::peak_spill_bytes(G)
+               ? reinterpret_cast<char *>(workspace) + a
+               : nullptr;
 }
 
 ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks, int32_t cap,
@@ -376,7 +387,9 @@ ht_status ht_find_peaks(const ht_geometry *g, const void *acc, ht_peak *peaks, i
                     ht::peaks_workspace_bytes(g->G));
     if (!aligned(workspace, 256) || !aligned(acc, 16))
         return fail(HT_ERR_ARG, "ht_find_peaks: workspace or accumulator alignment");
-    cudaError_t e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, workspace, S(stream));
+    cudaError_t e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, workspace, S(stream),
+                                     nullptr, nullptr,
+                                     peak_spill_of(g->G, workspace, workspace_bytes));
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_find_peaks");
 }
 
@@ -393,7 +406,8 @@ ht_status ht_find_peaks_masked(const ht_geometry *g, const void *acc, const uint
     if (!aligned(workspace, 256) || !aligned(mask, 8) || !aligned(acc, 16))
         return fail(HT_ERR_ARG, "ht_find_peaks_masked: pointer alignment");
     cudaError_t e = ht::launch_peaks(g->G, acc, peaks, cap, d_count, workspace, S(stream),
-                                     reinterpret_cast<const unsigned long long *>(mask));
+                                     reinterpret_cast<const unsigned long long *>(mask), nullptr,
+                                     peak_spill_of(g->G, workspace, workspace_bytes));
     return e == cudaSuccess ? HT_OK : cuda_fail(e, "ht_find_peaks_masked");
 }
 
@@ -472,7 +486,7 @@ EventWs carve_event(const ht_geometry *g, void *base, int32_t n, int32_t cap)
     w.assign = reinterpret_cast<int32_t *>(p); p += align256(nh * 4);
     w.zres = reinterpret_cast<ht_zres *>(p); p += align256((size_t)(cap > 0 ? cap : 1) * 12);
     w.stats = reinterpret_cast<uint64_t *>(p); p += 256;
-    size_t s = ht::peaks_workspace_bytes(g->G);
+    size_t s = ht_find_peaks_workspace_size(g);
     const size_t sa = ht::associate_workspace_bytes(g->G, n, cap);
     const size_t sz = ht::vote_z_workspace_bytes(g->G, n, cap);
     if (sa > s) s = sa;

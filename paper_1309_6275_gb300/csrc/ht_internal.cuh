@@ -378,10 +378,14 @@ cudaError_t launch_vote_hitmask(const DevGeom &G, const float *x, const float *y
                                 void *acc, unsigned long long *stats,
                                 const unsigned long long *hit_masks, cudaStream_t st);
 // mask (device, or null for every cell): only peaks inside it are reported.
+// spill (peak_spill_bytes, or null): lets the stencil run once instead of
+// twice; it may be shared by launches that run one after another.
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
                          int *d_count, void *ws, cudaStream_t st,
-                         const unsigned long long *mask = nullptr, const int *d_thr = nullptr);
+                         const unsigned long long *mask = nullptr, const int *d_thr = nullptr,
+                         void *spill = nullptr);
 size_t peaks_workspace_bytes(const DevGeom &G);
+size_t peak_spill_bytes(const DevGeom &G);
 cudaError_t launch_associate(const DevGeom &G, const float *x, const float *y, int n,
                              const ht_peak *peaks, const int *d_count, int cap, int *assign,
                              void *ws, cudaStream_t st);

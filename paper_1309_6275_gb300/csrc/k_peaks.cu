@@ -45,35 +45,54 @@ struct Stage {
 };
 constexpr size_t kPkSmemMax = Stage<int32_t>::kBytes;
 
+// Spilled peaks (single stencil pass): the count pass also writes the
+// peaks of every tile that has at most q of them into the tile's q slots, in
+// the tile's l order, with each peak's rank within its segment; tiletot
+// holds every tile's peak count.  The write pass then copies a spilled tile's
+// peaks to their segment offsets and runs the stencil again only for tiles
+// with more than q peaks.  q == 0: no spill (every tile's stencil runs
+// twice).
+struct PeakSpill {
+    ht_peak *pk;
+    int *rk;
+    int *tiletot;
+    int q;
+};
+
+// One tile: (rho row i, 16 d0 bins from j0 = jb * kJB, 256 phi0 columns
+// from k0 = kb * kPkThreads), tile index t.  Count pass (!WRITE): the
+// segment counts, the tile's total and, when sp.q allows, the spilled peaks.
+// Write pass: every peak at its segment offset.
+//
 // MASKED: only cells inside *mask (a learned proposal's regions) can be
-// peaks; a CTA whose bins are all outside reads nothing.  An inside cell's
+// peaks; a tile whose bins are all outside reads nothing.  An inside cell's
 // 26 neighbours lie in the mask's halo, which the masked vote fills exactly.
-// d_thr (null: the geometry's threshold): a device threshold for this event.
 template <typename T, bool WRITE, bool MASKED>
-__global__ void __launch_bounds__(kPkThreads)
-k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
-        const int *__restrict__ segoff, ht_peak *__restrict__ out, int cap,
-        const unsigned long long *__restrict__ mask, const int *__restrict__ d_thr)
+__device__ __forceinline__ void peaks_tile(const DevGeom &G, const T *__restrict__ acc, int kb,
+                                           int jb, int i, int t, int thr,
+                                           int *__restrict__ segcnt,
+                                           const int *__restrict__ segoff,
+                                           ht_peak *__restrict__ out, int cap,
+                                           const unsigned long long *__restrict__ mask,
+                                           const PeakSpill &sp, T *sw,
+                                           unsigned (*bal_s)[kPkThreads / 32], int *s_jpre)
 {
-    const int thr = d_thr ? *d_thr : G.threshold;
-    extern __shared__ __align__(16) unsigned char smraw[];
-    T *sw = reinterpret_cast<T *>(smraw);                // [slice][kSW], slice = r (kJB+2) + jj
     constexpr int kOff = Stage<T>::kOff, kSW = Stage<T>::kSW;
-    __shared__ unsigned bal_s[kJB][kPkThreads / 32];
     const int NP = G.n_phi0, ND = G.n_d0, NR = G.n_rho;
     const int nkb = (NP + kPkThreads - 1) / kPkThreads;
-    const int kb = blockIdx.x, i = blockIdx.z;
     const int k0 = kb * kPkThreads, ncol = min(kPkThreads, NP - k0);
-    const int j0 = blockIdx.y * kJB, j1 = min(j0 + kJB, ND);
+    const int j0 = jb * kJB, j1 = min(j0 + kJB, ND);
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     unsigned inside = 0xffu;   // d0 blocks inside the mask in row i's rho block
     if (MASKED) {
         inside = (unsigned)(*mask >> (8 * region_block(i, NR))) & 0xffu;
         const int b0 = region_block(j0, ND), b1 = region_block(j1 - 1, ND);
         if (!(inside & ((2u << b1) - 1u) & ~((1u << b0) - 1u))) {
-            if (!WRITE)
+            if (!WRITE) {
                 for (int j = j0 + threadIdx.x; j < j1; j += kPkThreads)
                     segcnt[(i * ND + j) * nkb + kb] = 0;
+                if (sp.q > 0 && threadIdx.x == 0) sp.tiletot[t] = 0;
+            }
             return;   // uniform over the CTA
         }
     }
@@ -161,39 +180,124 @@ k_peaks(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
         }
     }
     __syncthreads();
+    // rank of the lane's peak in bin jl within its segment (CTA order = l order)
+    auto seg_rank = [&](int jl) {
+        int r = __popc(bal_s[jl][warp] & ((1u << lane) - 1u));
+        for (int w2 = 0; w2 < warp; ++w2) r += __popc(bal_s[jl][w2]);
+        return r;
+    };
     if constexpr (!WRITE) {
-        for (int jl = threadIdx.x; jl < j1 - j0; jl += kPkThreads) {
+        for (int jl = threadIdx.x; jl < nj; jl += kPkThreads) {
             int cnt = 0;
 #pragma unroll
             for (int w2 = 0; w2 < kPkThreads / 32; ++w2) cnt += __popc(bal_s[jl][w2]);
             segcnt[(i * ND + j0 + jl) * nkb + kb] = cnt;
+            if (sp.q > 0) s_jpre[jl + 1] = cnt;
+        }
+        if (sp.q > 0) {
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                s_jpre[0] = 0;
+                for (int jl = 0; jl < nj; ++jl) s_jpre[jl + 1] += s_jpre[jl];
+                sp.tiletot[t] = s_jpre[nj];
+            }
+            __syncthreads();
+            if (s_jpre[nj] <= sp.q) {   // uniform
+                while (mine) {
+                    const int jl = __ffs(mine) - 1;
+                    mine &= mine - 1u;
+                    const int r = seg_rank(jl);
+                    const size_t slot = (size_t)t * sp.q + s_jpre[jl] + r;
+                    sp.pk[slot] = ht_peak{i, j0 + jl, k, (int)S(1, jl + 1)[0]};
+                    sp.rk[slot] = r;
+                }
+            }
         }
     } else {
         while (mine) {
             const int jl = __ffs(mine) - 1;
             mine &= mine - 1u;
-            const int seg = (i * ND + j0 + jl) * nkb + kb;
-            int pos = segoff[seg] + __popc(bal_s[jl][warp] & ((1u << lane) - 1u));
-            for (int w2 = 0; w2 < warp; ++w2) pos += __popc(bal_s[jl][w2]);
+            const int pos = segoff[(i * ND + j0 + jl) * nkb + kb] + seg_rank(jl);
             if (pos < cap) out[pos] = ht_peak{i, j0 + jl, k, (int)S(1, jl + 1)[0]};
         }
+    }
+}
+
+// d_thr (null: the geometry's threshold): a device threshold for this event.
+// Count pass: one CTA per tile.
+template <typename T, bool MASKED>
+__global__ void __launch_bounds__(kPkThreads)
+k_peaks_count(DevGeom G, const T *__restrict__ acc, int *__restrict__ segcnt,
+              const unsigned long long *__restrict__ mask, const int *__restrict__ d_thr,
+              PeakSpill sp)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ unsigned bal_s[kJB][kPkThreads / 32];
+    __shared__ int s_jpre[kJB + 1];
+    const int thr = d_thr ? *d_thr : G.threshold;
+    const int t = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
+    peaks_tile<T, false, MASKED>(G, acc, blockIdx.x, blockIdx.y, blockIdx.z, t, thr, segcnt,
+                                 nullptr, nullptr, 0, mask, sp, reinterpret_cast<T *>(smraw),
+                                 bal_s, s_jpre);
+}
+
+// Write pass, persistent over the tiles: a spilled tile is copied, the
+// others run the stencil again.
+template <typename T, bool MASKED>
+__global__ void __launch_bounds__(kPkThreads)
+k_peaks_write(DevGeom G, const T *__restrict__ acc, const int *__restrict__ segoff,
+              ht_peak *__restrict__ out, int cap, const unsigned long long *__restrict__ mask,
+              const int *__restrict__ d_thr, PeakSpill sp, int nkb, int njb)
+{
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ unsigned bal_s[kJB][kPkThreads / 32];
+    const int thr = d_thr ? *d_thr : G.threshold;
+    const int ND = G.n_d0;
+    const int ntiles = nkb * njb * G.n_rho;
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const int kb = t % nkb, jb = (t / nkb) % njb, i = t / (nkb * njb);
+        if (sp.q > 0) {
+            const int tot = sp.tiletot[t];
+            if (tot <= sp.q) {   // uniform
+                for (int r = threadIdx.x; r < tot; r += kPkThreads) {
+                    const size_t slot = (size_t)t * sp.q + r;
+                    const ht_peak pk = sp.pk[slot];
+                    const int pos = segoff[(pk.i_rho * ND + pk.j_d0) * nkb + kb] + sp.rk[slot];
+                    if (pos < cap) out[pos] = pk;
+                }
+                continue;
+            }
+        }
+        peaks_tile<T, true, MASKED>(G, acc, kb, jb, i, t, thr, nullptr, segoff, out, cap, mask,
+                                    sp, reinterpret_cast<T *>(smraw), bal_s, nullptr);
+        __syncthreads();   // the staged window is refilled by the next tile
     }
 }
 
 template <typename T, bool MASKED>
 cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, int *d_count,
                       int *segcnt, int *segoff, void *tmp, const unsigned long long *mask,
-                      cudaStream_t st, const int *d_thr)
+                      cudaStream_t st, const int *d_thr, const PeakSpill &sp)
 {
     const int nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
-    dim3 grid(nkb, (G.n_d0 + kJB - 1) / kJB, G.n_rho);
+    const int njb = (G.n_d0 + kJB - 1) / kJB;
+    dim3 grid(nkb, njb, G.n_rho);
     const int nseg = G.n_rho * G.n_d0 * nkb;
-    k_peaks<T, false, MASKED><<<grid, kPkThreads, Stage<T>::kBytes, st>>>(
-        G, acc, segcnt, nullptr, nullptr, 0, mask, d_thr);
+    k_peaks_count<T, MASKED><<<grid, kPkThreads, Stage<T>::kBytes, st>>>(G, acc, segcnt, mask,
+                                                                         d_thr, sp);
     cudaError_t e = scan_exclusive(segcnt, segoff, nullptr, nseg, nullptr, d_count, tmp, st);
     if (e != cudaSuccess) return e;
-    k_peaks<T, true, MASKED><<<grid, kPkThreads, Stage<T>::kBytes, st>>>(
-        G, acc, nullptr, segoff, peaks, cap, mask, d_thr);
+    int dev = 0, sms = 0, occ = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_peaks_write<T, MASKED>,
+                                                          kPkThreads, Stage<T>::kBytes);
+    if (e != cudaSuccess) return e;
+    const int ntiles = nkb * njb * G.n_rho;
+    const int pgrid = min(ntiles, sms * (occ > 0 ? occ : 1));
+    k_peaks_write<T, MASKED><<<pgrid, kPkThreads, Stage<T>::kBytes, st>>>(
+        G, acc, segoff, peaks, cap, mask, d_thr, sp, nkb, njb);
     return cudaGetLastError();
 }
 
@@ -204,10 +308,10 @@ cudaError_t run_peaks(const DevGeom &G, const T *acc, ht_peak *peaks, int cap, i
 cudaError_t prepare_peaks_kernels()
 {
     const void *fns[] = {
-        (const void *)k_peaks<uint16_t, false, false>, (const void *)k_peaks<uint16_t, true, false>,
-        (const void *)k_peaks<uint16_t, false, true>,  (const void *)k_peaks<uint16_t, true, true>,
-        (const void *)k_peaks<int32_t, false, false>,  (const void *)k_peaks<int32_t, true, false>,
-        (const void *)k_peaks<int32_t, false, true>,   (const void *)k_peaks<int32_t, true, true>};
+        (const void *)k_peaks_count<uint16_t, false>, (const void *)k_peaks_write<uint16_t, false>,
+        (const void *)k_peaks_count<uint16_t, true>,  (const void *)k_peaks_write<uint16_t, true>,
+        (const void *)k_peaks_count<int32_t, false>,  (const void *)k_peaks_write<int32_t, false>,
+        (const void *)k_peaks_count<int32_t, true>,   (const void *)k_peaks_write<int32_t, true>};
     for (const void *f : fns) {
         const cudaError_t e =
             cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPkSmemMax);
@@ -223,9 +327,22 @@ size_t peaks_workspace_bytes(const DevGeom &G)
     return 2 * align256((nseg + 1) * 4) + scan_tmp_bytes((int)nseg);
 }
 
+// Spill slots per tile: a tile (one row, 16 bins, 256 columns) has at most
+// 1024 peaks (no two peaks are neighbours), usually a few; tiles above this
+// run the stencil twice.
+constexpr int kSpillQ = 64;
+
+size_t peak_spill_bytes(const DevGeom &G)
+{
+    const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
+    const size_t nt = nkb * ((G.n_d0 + kJB - 1) / kJB) * G.n_rho;
+    return align256(nt * 4) + align256(nt * kSpillQ * sizeof(ht_peak)) +
+           align256(nt * kSpillQ * 4);
+}
+
 cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int cap,
                          int *d_count, void *ws, cudaStream_t st, const unsigned long long *mask,
-                         const int *d_thr)
+                         const int *d_thr, void *spill)
 {
     const size_t nkb = (G.n_phi0 + kPkThreads - 1) / kPkThreads;
     const size_t nseg = (size_t)G.n_rho * G.n_d0 * nkb;
@@ -233,20 +350,31 @@ cudaError_t launch_peaks(const DevGeom &G, const void *acc, ht_peak *peaks, int 
     int *segcnt = reinterpret_cast<int *>(p);
     int *segoff = reinterpret_cast<int *>(p + align256((nseg + 1) * 4));
     void *tmp = p + 2 * align256((nseg + 1) * 4);
+    PeakSpill sp{nullptr, nullptr, nullptr, 0};
+    if (spill) {
+        const size_t nt = nkb * ((G.n_d0 + kJB - 1) / kJB) * G.n_rho;
+        char *q = reinterpret_cast<char *>(spill);
+        sp.tiletot = reinterpret_cast<int *>(q);
+        q += align256(nt * 4);
+        sp.pk = reinterpret_cast<ht_peak *>(q);
+        q += align256(nt * kSpillQ * sizeof(ht_peak));
+        sp.rk = reinterpret_cast<int *>(q);
+        sp.q = kSpillQ;
+    }
     const uint16_t *a16 = reinterpret_cast<const uint16_t *>(acc);
     const int32_t *a32 = reinterpret_cast<const int32_t *>(acc);
     if (mask) {
         if (G.count_bits == 16)
             return run_peaks<uint16_t, true>(G, a16, peaks, cap, d_count, segcnt, segoff, tmp,
-                                             mask, st, d_thr);
+                                             mask, st, d_thr, sp);
         return run_peaks<int32_t, true>(G, a32, peaks, cap, d_count, segcnt, segoff, tmp, mask,
-                                        st, d_thr);
+                                        st, d_thr, sp);
     }
     if (G.count_bits == 16)
         return run_peaks<uint16_t, false>(G, a16, peaks, cap, d_count, segcnt, segoff, tmp,
-                                          nullptr, st, d_thr);
+                                          nullptr, st, d_thr, sp);
     return run_peaks<int32_t, false>(G, a32, peaks, cap, d_count, segcnt, segoff, tmp, nullptr,
-                                     st, d_thr);
+                                     st, d_thr, sp);
 }
 
 }  // namespace ht
