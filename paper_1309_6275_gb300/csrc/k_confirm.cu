@@ -19,11 +19,10 @@
 // One warp per candidate, persistent over the candidates of a batch grouped
 // by (event, column group).  A candidate scans only the hits of each layer
 // whose azimuth can give a root near its bin (a per-event index by layer and
-// azimuth, k_hitindex.cu; a superset of the pool).  A float32 screen drops
-// hits whose roots are certainly far; the rest get the vote's exact bin
-// decision (guarded float32, then double-float, then float64 in the
-// definition's operation order), so own and pool membership are exactly
-// the vote's.  The seed circle is float64 in the definition's order;
+// azimuth, k_hitindex.cu; a superset of the pool).  Each of those hits
+// gets the vote's exact bin decision (guarded float32, then double-float,
+// then float64 in the definition's operation order), so own and pool
+// membership are exactly the vote's.  The seed circle is float64 in the definition's order;
 // distances are estimated in float32 with an error bound, and the float64
 // distance of the definition is computed for every hit the bound cannot
 // settle, so every decision is the definition's.  The results are
@@ -182,6 +181,7 @@ __device__ __forceinline__ bool seed_frame(float x1, float y1, float x2, float y
 
 constexpr int kCfThreads = 128, kCfWarps = kCfThreads / 32;
 constexpr int kCfCap = 512;        // pool hits held per pass (more: further passes)
+constexpr int kCfBlk = 256;        // 32-hit blocks of a scan whose pool counts are kept
 
 struct CfWarp {
     int n_own[16], own_pos[16];
@@ -192,8 +192,8 @@ struct CfWarp {
     // pass's positions [qs, qe) (the pool is in layer order)
     unsigned lbmin[16], ubmin[16];
     int ncont[16], cq[16], qs[16], qe[16];
-    int q[64];              // screened positions waiting for the exact evaluation
     int rs[32], rp[33];     // runs of index positions scanned: start, exclusive prefix of lengths
+    unsigned short blk[kCfBlk];   // pool hits of each 32-hit block of the first pass
     int pool_p[kCfCap], pool_h[kCfCap];   // index position and event-local hit index
     float pool_lo[kCfCap], pool_hi[kCfCap];   // bounds on the hit's float64 distance
     unsigned char pool_l[kCfCap];
@@ -244,14 +244,18 @@ __device__ __forceinline__ int event_of(const int *cpre, int n_ev, int f)
 // d0 in [lo, hi] (cm) in column (rho, phi0_k); returns its runs of index
 // cells as bins [b0, b1] (b1 - b0 + 1 >= kIdxAz or full: the whole layer;
 // empty: no hit can).  A root d0 of the circle equation gives
-//   s = -(2 d0 + rho (d0^2 + r^2)) / (2 (1 + rho d0)),
-// decreasing in d0 while (1 + rho d0)^2 + 1 > rho^2 r^2 and monotone in r^2
-// (sign -rho) while 1 + rho d0 > 0, so over the window and the layer's
-// radius range [rmin, rmax] s lies between its values at two corners; with
-// c > 0 the hit's azimuth is phi0_k - asin(s / r).  Margins (1e-3 cm plus
-// 1e-5 relative on s, 2e-3 rad on the azimuth) cover float32 rounding;
-// where the monotonicity conditions are not proven the whole layer is
-// scanned.
+//   s = -(2 d0 + rho (d0^2 + r^2)) / (2 u),   u = 1 + rho d0,
+// with ds/dd0 = -(u^2 + 1 - rho^2 r^2) / (2 u^2) and ds/d(r^2) = -rho / (2 u):
+// for u > 0, s is monotone in r^2 (sign -rho), and in d0 (decreasing) while
+// u^2 + 1 > rho^2 r^2; otherwise |ds/dd0| <= (1 + (1 + rho^2 r^2) / u^2) / 2
+// bounds it around the middle of [lo, hi].  So over the window and the
+// layer's radius range [rmin, rmax] s lies in an interval given by two
+// corners (or the middle and that bound); with c > 0 the hit's azimuth is
+// phi0_k - asin(s / r).  A layer beyond the circles' reach (the farthest
+// point of a circle with perigee d0 is |d0 + 1/rho| + 1/|rho| from the
+// origin) is empty.  Margins (1e-3 cm plus 1e-5 relative on s and on the
+// reach, 2e-3 rad on the azimuth) cover float32 rounding; where u > 0 is not
+// proven the whole layer is scanned.
 __device__ __forceinline__ void layer_window(float rho, float phik, float lo, float hi,
                                              float rmin, float rmax, bool &full, bool &empty,
                                              int &b0, int &b1)
@@ -262,14 +266,28 @@ __device__ __forceinline__ void layer_window(float rho, float phik, float lo, fl
     if (empty) return;
     const float tl = fmaf(rho, lo, 1.0f), th = fmaf(rho, hi, 1.0f);
     const float tmin = fminf(tl, th);
-    if (!(tmin >= 0.05f) || !(rmin >= 1e-3f) ||
-        fmaf(rho * rho * 1.001f, rmax * rmax, 1e-3f) >= fmaf(tmin, tmin, 1.0f)) {
+    if (!(tmin >= 0.05f) || !(rmin >= 1e-3f)) {
         full = true;
         return;
     }
+    const float ir = 1.0f / rho;   // +-inf for rho = 0: no reach limit
+    const float reach = fmaxf(fabsf(lo + ir), fabsf(hi + ir)) + fabsf(ir);
+    if (rmin > fmaf(reach, 1.0f + 1e-5f, 1e-3f)) {
+        empty = true;
+        return;
+    }
     const float rA = rho > 0.0f ? rmin : rmax, rB = rho > 0.0f ? rmax : rmin;
-    float s_hi = -fmaf(rho, fmaf(lo, lo, rA * rA), 2.0f * lo) / (2.0f * tl);
-    float s_lo = -fmaf(rho, fmaf(hi, hi, rB * rB), 2.0f * hi) / (2.0f * th);
+    float s_hi, s_lo;
+    if (fmaf(rho * rho * 1.001f, rmax * rmax, 1e-3f) < fmaf(tmin, tmin, 1.0f)) {
+        s_hi = -fmaf(rho, fmaf(lo, lo, rA * rA), 2.0f * lo) / (2.0f * tl);
+        s_lo = -fmaf(rho, fmaf(hi, hi, rB * rB), 2.0f * hi) / (2.0f * th);
+    } else {
+        const float mid = 0.5f * (lo + hi), tm = fmaf(rho, mid, 1.0f);
+        const float L = 0.5f * (1.0f + fmaf(rho * rho, rmax * rmax, 1.0f) / (tmin * tmin));
+        const float ds = 1.001f * L * 0.5f * (hi - lo);
+        s_hi = -fmaf(rho, fmaf(mid, mid, rA * rA), 2.0f * mid) / (2.0f * tm) + ds;
+        s_lo = -fmaf(rho, fmaf(mid, mid, rB * rB), 2.0f * mid) / (2.0f * tm) - ds;
+    }
     const float ms = fmaf(1e-5f, fabsf(s_hi) + fabsf(s_lo), 1e-3f);
     s_hi += ms;
     s_lo -= ms;
@@ -286,76 +304,38 @@ __device__ __forceinline__ void layer_window(float rho, float phik, float lo, fl
     if (b1 - b0 + 1 >= kIdxAz) full = true;
 }
 
-// Float32 screen of a hit against a candidate's pool: false only when both
-// roots certainly lie outside [lo, hi) = [j - pool - 2, j + pool + 3) (bin
-// coordinates), which holds every root whose bin is within pool of j.  D is
-// within 4e-7 (rho c)^2 of its float64 value; past eD = 1e-3 + that bound
-// the sign is certain (below -eD no real root; within +-eD the hit goes to
-// the exact evaluation), and |q| >= sqrt(D) > 0.03.  Root A = C / q then has
-// a first-order float32 error below 4e-7 (|rho| r^2 + 2 (|x| + |y|) + |C|)
-// / |q| cm (the inputs s and c carry 3 2^-24 (|x| + |y|), C and q a few ulp
-// each), plus 3e-7 |u| + 1e-3 bins for the conversion to a bin coordinate:
-// the test widens [lo, hi) by that.  Root B = q / rho has a relative error
-// of a few ulp, far below the two bins of margin for any root near the axis.
-struct PoolScreen {
-    float rho, invrho_d, lo, hi, sk, ck;
-    bool has_b;
-
-    __device__ __forceinline__ bool maybe(float xf, float yf, float inv_delta, float off) const
-    {
-        const float c = fmaf(xf, ck, yf * sk);
-        if (!(c > 0.0f)) return c > -1e-3f * (fabsf(xf) + fabsf(yf));
-        const float s = fmaf(xf, sk, -(yf * ck));
-        const float b = fmaf(rho, s, 1.0f);
-        const float pc = rho * c;
-        const float D = fmaf(-pc, pc, 1.0f);
-        const float eD = fmaf(4e-7f, pc * pc, 1e-3f);
-        if (D < -eD) return false;
-        if (D <= eD) return true;
-        const float sq = D * rsqrt_approx(D);
-        const float q = -(b + copysignf(sq, b));
-        const float r2 = fmaf(xf, xf, yf * yf);
-        const float C = fmaf(rho, r2, s + s);
-        const float iq = rcp_approx(q);
-        const float uA = fmaf(C * iq, inv_delta, off);
-        const float ec = 4e-7f * (fmaf(fabsf(rho), r2, 2.0f * (fabsf(xf) + fabsf(yf))) + fabsf(C));
-        const float eA = fmaf(ec * fabsf(iq), inv_delta, fmaf(3e-7f, fabsf(uA), 1e-3f));
-        bool near = uA >= lo - eA && uA < hi + eA;
-        if (has_b) {
-            const float uB = fmaf(q, invrho_d, off);
-            near |= uB >= lo && uB < hi;
-        }
-        return near;
-    }
-};
-
 // One pass over a candidate's hit sequence: collects the pool hits of rank
 // [r0, r0 + kCfCap) into the warp's list (in sequence order) and, when
-// count_own, the own hits per layer.  Returns the total number of pool hits.
-// Hits that pass the float32 screen queue up in order and get the exact
-// evaluation 32 at a time, so that the lanes stay busy.
+// count_own (the first pass, r0 = 0), the own hits per layer.  Returns the
+// total number of pool hits (first pass).  Every scanned hit gets the
+// vote's exact bin decision in the candidate's column, one hit per lane
+// (the index windows already hold few hits far from the pool, so no cheaper
+// screen pays for itself).  The first pass keeps each 32-hit block's pool
+// count, so a later pass evaluates only the blocks whose pool hits can fall
+// in its rank range.
 __device__ __noinline__ int scan_pool(const DevGeom &G, const HitView V, int i, int j, int k,
                                       int pool, int r0, bool count_own, int lane)
 {
     CfWarp &W = g_cfw[V.wid];
     ColumnCtx C;
     C.init(G, i, k);
-    PoolScreen ps;
-    ps.rho = C.rho;
-    ps.invrho_d = C.invrho * G.inv_delta_f;
-    ps.has_b = C.has_b;
-    ps.lo = (float)(j - pool - 2);
-    ps.hi = (float)(j + pool + 3);
-    ps.sk = C.sk;
-    ps.ck = C.ck;
     const unsigned lt = (1u << lane) - 1u;
-    int rank = 0, qn = 0;
-    // exact bins of the first cnt (<= 32) queued hits, one per lane, in order
-    auto drain = [&](int cnt) {
+    int rank = 0;
+    for (int base = 0; base < V.n; base += 32) {
+        const int b = base >> 5;
+        if (!count_own && b < kCfBlk) {   // uniform
+            const int cnt = W.blk[b];
+            if (rank + cnt <= r0) {
+                rank += cnt;
+                continue;
+            }
+            if (rank >= r0 + kCfCap) break;
+        }
+        const int t = base + lane;
         int p = -1, l = 0;
         bool own = false, inp = false;
-        if (lane < cnt) {
-            p = W.q[lane];
+        if (t < V.n) {
+            p = V.pos(t);
             int jj[2];
             const int nv = column_bins(G, C, V.x[p], V.y[p], jj);
             for (int v = 0; v < nv; ++v) {
@@ -375,32 +355,9 @@ __device__ __noinline__ int scan_pool(const DevGeom &G, const HitView V, int i, 
             W.pool_h[r - r0] = V.h[p];
             W.pool_l[r - r0] = (unsigned char)l;
         }
+        if (count_own && lane == 0 && b < kCfBlk) W.blk[b] = (unsigned short)__popc(bal);
         rank += __popc(bal);
-    };
-    for (int base = 0; base < V.n; base += 32) {
-        const int t = base + lane;
-        bool nr = false;
-        int p = 0;
-        if (t < V.n) {
-            p = V.pos(t);
-            nr = ps.maybe(V.x[p], V.y[p], G.inv_delta_f, G.off_f);
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, nr);
-        if (nr) W.q[qn + __popc(bal & lt)] = p;   // qn < 32 here, so below 64
-        qn += __popc(bal);
-        __syncwarp();
-        if (qn >= 32) {
-            drain(32);
-            __syncwarp();
-            const int rest = qn - 32;
-            const int v = lane < rest ? W.q[32 + lane] : 0;
-            __syncwarp();
-            if (lane < rest) W.q[lane] = v;
-            qn = rest;
-            __syncwarp();
-        }
     }
-    if (qn > 0) drain(qn);
     __syncwarp();
     return rank;
 }
@@ -658,7 +615,7 @@ __device__ __forceinline__ void confirm_one(const DevGeom &G, const ConfirmDev &
 // warps of a CTA work on nearby columns of one event; a CTA takes chunks of
 // kCfChunk consecutive entries, one candidate per warp at a time.  I: the
 // batch's hit index (k_hitindex.cu).
-constexpr int kCfChunk = 64;
+constexpr int kCfChunk = 32;
 
 __global__ void __launch_bounds__(kCfThreads, 5)
 k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
