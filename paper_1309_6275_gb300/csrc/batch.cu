@@ -438,7 +438,7 @@ ht_status ht_batch_create(const ht_geometry *g, int32_t max_events, int32_t max_
     M((void **)&b->z_ws, ht::vote_z_batch_workspace_bytes(max_events, cap, max_hits));
     M((void **)&b->mass, (size_t)max_events * 64 * sizeof(float));
     M((void **)&b->bk_ws, ht::hit_bucket_bytes(G, max_events, max_hits));
-    if (e == cudaSuccess) b->bk = ht::carve_hit_buckets(G, max_events, b->bk_ws);
+    if (e == cudaSuccess) b->bk = ht::carve_hit_buckets(G, max_events, max_hits, b->bk_ws);
     if (e == cudaSuccess) e = cudaMallocHost((void **)&b->h_meta, b->meta_ints * 4);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->meta_done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);

@@ -343,6 +343,7 @@ constexpr int kGroupCols = 8;
 constexpr int kPackMaxHits = 32767;
 struct HitBuckets {
     int *cnt, *start, *cursor, *ent;
+    int *hg;   // per hit: first group | group count << 16
     void *tmp;
     int ngroups, ncells;
 };
@@ -364,7 +365,7 @@ inline BucketView bucket_view(const HitBuckets *b)
              : BucketView{nullptr, nullptr, nullptr, 0};
 }
 size_t hit_bucket_bytes(const DevGeom &G, int max_events, int max_hits);
-HitBuckets carve_hit_buckets(const DevGeom &G, int max_events, void *ws);
+HitBuckets carve_hit_buckets(const DevGeom &G, int max_events, int max_hits, void *ws);
 cudaError_t launch_hit_buckets(const DevGeom &G, const float *x, const float *y, const int *off,
                                const int *d_nev, int max_hits, const HitBuckets &b, int sms,
                                cudaStream_t st);
