@@ -26,7 +26,6 @@ namespace {
 constexpr int kIn = 6, kH = 128, kOut = 64;
 constexpr int oW1 = 0, ob1 = oW1 + kIn * kH, oW2 = ob1 + kH, ob2 = oW2 + kH * kH,
               oW3 = ob2 + kH, ob3 = oW3 + kH * kOut, kParams = ob3 + kOut;
-constexpr int kFwdThreads = 128;   // one hit per thread (backward pass)
 constexpr float kSinhEta = 6.0502044810397875f;   // sinh(2.5)
 
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
@@ -68,77 +67,15 @@ __device__ __forceinline__ int event_of_hit(const int *off, int n_ev, int h)
 
 #include "mlp_tc.cuh"
 
-// Backward through the activations of one minibatch: dL = (p - onehot) / nl
-// (0 for unlabelled hits), dH2 = (dL W3^T) o [h2 > 0], dH1 = (dH2 W2^T) o [h1 > 0].
-__global__ void __launch_bounds__(kFwdThreads)
-k_mlp_bwd_act(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ prob,
-              const int *__restrict__ labels, const __nv_bfloat16 *__restrict__ h1,
-              const __nv_bfloat16 *__restrict__ h2, int n, const int *__restrict__ d_nlab,
-              float *__restrict__ dL, float *__restrict__ dH2, float *__restrict__ dH1)
-{
-    extern __shared__ __align__(16) unsigned char smem[];
-    __nv_bfloat16 *sW2 = reinterpret_cast<__nv_bfloat16 *>(smem);
-    __nv_bfloat16 *sW3 = sW2 + kH * kH;
-    float (*dT)[kFwdThreads + 1] = reinterpret_cast<float (*)[kFwdThreads + 1]>(sW3 + kH * kOut);
-    for (int t = threadIdx.x; t < kH * kH; t += kFwdThreads) sW2[t] = w[oW2 + t];
-    for (int t = threadIdx.x; t < kH * kOut; t += kFwdThreads) sW3[t] = w[oW3 + t];
-    __syncthreads();
-    const float inv_nl = 1.0f / (float)max(*d_nlab, 1);
-    for (int base = blockIdx.x * kFwdThreads; base < n; base += gridDim.x * kFwdThreads) {
-        const int h = base + threadIdx.x;
-        const bool act = h < n;
-        const int lab = act ? labels[h] : -1;
-        float d[kOut];
-#pragma unroll
-        for (int c = 0; c < kOut; ++c) {
-            const float pv = act ? prob[(size_t)h * kOut + c] : 0.f;
-            d[c] = lab >= 0 ? (pv - (c == lab ? 1.f : 0.f)) * inv_nl : 0.f;
-        }
-        if (act) {
-            float4 *dp = reinterpret_cast<float4 *>(dL + (size_t)h * kOut);
-#pragma unroll
-            for (int c4 = 0; c4 < kOut / 4; ++c4)
-                dp[c4] = make_float4(d[4 * c4], d[4 * c4 + 1], d[4 * c4 + 2], d[4 * c4 + 3]);
-        }
-        for (int o = 0; o < kH; ++o) {
-            const uint4 *wr = reinterpret_cast<const uint4 *>(&sW3[o * kOut]);
-            float a = 0.f;
-#pragma unroll
-            for (int c8 = 0; c8 < kOut / 8; ++c8) {
-                const uint4 wv = wr[c8];
-                const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) a = fmaf(d[c8 * 8 + q], __bfloat162float(wb[q]), a);
-            }
-            const float hv = act ? __bfloat162float(h2[(size_t)h * kH + o]) : 0.f;
-            const float g = hv > 0.f ? a : 0.f;
-            dT[o][threadIdx.x] = g;
-            if (act) dH2[(size_t)h * kH + o] = g;
-        }
-        __syncthreads();
-        for (int i = 0; i < kH; ++i) {
-            const uint4 *wr = reinterpret_cast<const uint4 *>(&sW2[i * kH]);
-            float a = 0.f;
-            for (int o8 = 0; o8 < kH / 8; ++o8) {
-                const uint4 wv = wr[o8];
-                const __nv_bfloat16 *wb = reinterpret_cast<const __nv_bfloat16 *>(&wv);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) a = fmaf(dT[o8 * 8 + q][threadIdx.x], __bfloat162float(wb[q]), a);
-            }
-            const float hv = act ? __bfloat162float(h1[(size_t)h * kH + i]) : 0.f;
-            if (act) dH1[(size_t)h * kH + i] = hv > 0.f ? a : 0.f;
-        }
-        __syncthreads();
-    }
-}
-
 // Split z of C[M][N] = sum_h A[h][M] B[h][N] (A BF16 with row stride lda,
 // B float32 with row stride ldb) and, when bias is set, of bias[N] =
-// sum_h B[h][N]: the hits are split across gridDim.z and split z stores its
-// partial sums at C + z pstride and bias + z pstride (plain stores: every
-// entry of a split is written by exactly one CTA); k_wgrad_reduce adds the
-// splits in a fixed order, so a training step is bit-reproducible.
-// CTA: 256 threads, a 64 x 64 output tile (4 x 4 per thread).
+// sum_h B[h][N], on the CUDA cores, for the first layer (M = 6 inputs; the
+// 128-row layers use k_wgrad_tc): the hits are split across gridDim.z and
+// split z stores its partial sums at C + z pstride and bias + z pstride
+// (plain stores: every entry of a split is written by exactly one CTA);
+// k_wgrad_reduce adds the splits in a fixed order, so a training step is
+// bit-reproducible.  CTA: 256 threads, a 64 x 64 output tile (4 x 4 per
+// thread).
 constexpr int kGT = 64, kGH = 32;
 constexpr int kMaxSplits = 128;
 __global__ void __launch_bounds__(256)
@@ -249,7 +186,6 @@ __global__ void k_region_mask(const float *__restrict__ mass, const int *__restr
     mask[e] = ((float)__popcll(bits) > fmax * (float)kOut || n == 0) ? ~0ull : bits;
 }
 
-constexpr size_t kBwdSmem = (size_t)(kH * kH + kH * kOut) * 2 + (size_t)kH * (kFwdThreads + 1) * 4;
 
 }  // namespace
 
@@ -317,8 +253,11 @@ cudaError_t prepare_mlp_kernels()
     cudaError_t e = cudaFuncSetAttribute(k_mlp_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kTcSmem);
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(k_mlp_bwd_act, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)kBwdSmem);
+        e = cudaFuncSetAttribute(k_mlp_bwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kBwdTcSmem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)kWgTcSmem);
     return e;
 }
 
@@ -421,17 +360,15 @@ ht_status ht_mlp_backward(const void *params_bf16, const int32_t *labels, int32_
     if (e == cudaSuccess) e = cudaMemsetAsync(part, 0, (size_t)splits * kParams * 4, st);
     if (e != cudaSuccess) return set_error(HT_ERR_CUDA, cudaGetErrorString(e));
     k_count_labels<<<min(1024, (n + 255) / 256), 256, 0, st>>>(labels, n, nl);
-    const int blocks = min((n + kFwdThreads - 1) / kFwdThreads, device_sms() * 4);
-    k_mlp_bwd_act<<<blocks, kFwdThreads, kBwdSmem, st>>>((const __nv_bfloat16 *)params_bf16, prob, labels,
-                                                  (const __nv_bfloat16 *)h1,
-                                                  (const __nv_bfloat16 *)h2, n, nl, dL, dH2, dH1);
-    // dW3 = h2^T dL, db3
-    k_wgrad<<<dim3(kH / kGT, 1, splits), 256, 0, st>>>((const __nv_bfloat16 *)h2, kH, dL, kOut, n,
-                                                       kH, kOut, part + oW3, part + ob3, kParams);
-    // dW2 = h1^T dH2, db2
-    k_wgrad<<<dim3(kH / kGT, kH / kGT, splits), 256, 0, st>>>((const __nv_bfloat16 *)h1, kH, dH2,
-                                                              kH, n, kH, kH, part + oW2,
-                                                              part + ob2, kParams);
+    const int blocks = min((n + kTcM - 1) / kTcM, device_sms() * 2);
+    k_mlp_bwd_tc<<<blocks, kTcM, kBwdTcSmem, st>>>((const __nv_bfloat16 *)params_bf16, prob,
+                                                   labels, (const __nv_bfloat16 *)h1,
+                                                   (const __nv_bfloat16 *)h2, n, nl, dL, dH2, dH1);
+    // dW3 = h2^T dL, db3 and dW2 = h1^T dH2, db2 on the tensor cores
+    k_wgrad_tc<<<splits, kTcM, kWgTcSmem, st>>>((const __nv_bfloat16 *)h2, kH, dL, kOut, n, kOut,
+                                                part + oW3, part + ob3, kParams);
+    k_wgrad_tc<<<splits, kTcM, kWgTcSmem, st>>>((const __nv_bfloat16 *)h1, kH, dH2, kH, n, kH,
+                                                part + oW2, part + ob2, kParams);
     // dW1 = f^T dH1, db1
     k_wgrad<<<dim3(1, kH / kGT, splits), 256, 0, st>>>((const __nv_bfloat16 *)feat, 8, dH1, kH, n,
                                                        kIn, kH, part + oW1, part + ob1, kParams);

@@ -356,3 +356,286 @@ k_mlp_fwd_tc(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ x,
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
                      "r"(kTcCols) : "memory");
 }
+
+// ---------------------------------------------------------------------------
+// Training contractions on the tensor cores.
+//
+// Backward through the activations (k_mlp_bwd_tc), per tile of 128 hits:
+//   dL  = (p - onehot) / nl                      (CUDA cores, thread = hit)
+//   dH2 = (dL W3^T) o [h2 > 0]    M 128, N 128, K 64  (tcgen05)
+//   dH1 = (dH2 W2^T) o [h1 > 0]   M 128, N 128, K 128 (tcgen05)
+// with W3 stored [hidden][class] and W2 [in][out], so both B operands are
+// the stored rows (n = the hidden unit, k contiguous).  dL and dH2 enter the
+// tensor cores rounded to BF16; the accumulators and the stored gradients
+// are float32.
+//
+// Weight gradients (k_wgrad_tc): C[m][n] = sum_h A[h][m] B[h][n] for one
+// split of the hits, M = 128, N = 128 or 64, K = 128 hits per step: A^T and
+// B^T are staged K-major (eight hits per 16-byte core-matrix row) and the
+// split's sum accumulates in tensor memory.  B (a float32 gradient) enters
+// rounded to BF16; the bias sum over the same hits is float32 in hit order.
+// Splits are reduced in a fixed order (k_wgrad_reduce), so a training step is
+// reproducible bit for bit.
+
+constexpr uint32_t kSBO64 = 1024;                 // 8-row group stride for K = 64
+constexpr size_t kBwdTcSmem = (size_t)kH * kOut * 2 + (size_t)kH * kH * 2 +
+                              (size_t)kTcM * kOut * 2 + (size_t)kTcM * kH * 2;
+constexpr size_t kWgTcSmem = (size_t)kTcM * kTcM * 2 + (size_t)kH * kTcM * 2;
+constexpr uint32_t kWgTcCols = 128;
+
+// Byte offset of element (row, k) of a K = 64 operand in the core layout.
+__device__ __forceinline__ uint32_t core_off64(int row, int k)
+{
+    return (uint32_t)((row >> 3) * kSBO64 + (k >> 3) * kLBO + (row & 7) * 16 + (k & 7) * 2);
+}
+
+__device__ __forceinline__ uint64_t smem_desc_sbo(uint32_t addr, uint32_t sbo)
+{
+    return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((kLBO >> 4) & 0x3FFFu) << 16) |
+           ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// One CTA's tensor-memory columns and completion barrier (warp 0 allocates).
+__device__ __forceinline__ uint32_t tc_setup(uint32_t mbar, uint32_t *s_tmem, uint32_t cols)
+{
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if ((threadIdx.x >> 5) == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;"
+                     ::"r"(smem_u32(s_tmem)), "r"(cols) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return *s_tmem;
+}
+
+// After a bounded wait failed: count it, one more bounded wait for the
+// outstanding MMAs; then (every path) free the tensor memory.
+__device__ __forceinline__ void tc_teardown(bool failed, uint32_t mbar, uint32_t phase,
+                                            uint32_t tmem, uint32_t cols)
+{
+    if (failed) {
+        if (threadIdx.x == 0) atomicAdd(&g_mlp_timeouts, 1u);
+        mbar_wait(mbar, phase);
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(cols) : "memory");
+}
+
+// The operand writes above are visible to the tensor cores, and every
+// thread reaches the MMA issue point.
+__device__ __forceinline__ void tc_publish()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+__global__ void __launch_bounds__(kTcM)
+k_mlp_bwd_tc(const __nv_bfloat16 *__restrict__ w, const float *__restrict__ prob,
+             const int *__restrict__ labels, const __nv_bfloat16 *__restrict__ h1,
+             const __nv_bfloat16 *__restrict__ h2, int n, const int *__restrict__ d_nlab,
+             float *__restrict__ dL, float *__restrict__ dH2, float *__restrict__ dH1)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *sB3 = smem;                          // W3: N 128 (hidden) x K 64 (class)
+    unsigned char *sB2 = sB3 + kH * kOut * 2;           // W2: N 128 (in) x K 128 (out)
+    unsigned char *sA1 = sB2 + kH * kH * 2;             // dL: 128 hits x K 64
+    unsigned char *sA2 = sA1 + kTcM * kOut * 2;         // dH2: 128 hits x K 128
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int t = tid; t < kH * kOut; t += kTcM)         // B3(n = o, k = c) = W3[o][c]
+        *reinterpret_cast<__nv_bfloat16 *>(sB3 + core_off64(t / kOut, t % kOut)) = w[oW3 + t];
+    for (int t = tid; t < kH * kH; t += kTcM)           // B2(n = i, k = o) = W2[i][o]
+        *reinterpret_cast<__nv_bfloat16 *>(sB2 + core_off(t / kH, t % kH)) = w[oW2 + t];
+    const uint32_t mbar = smem_u32(&s_mbar);
+    const uint32_t tmem = tc_setup(mbar, &s_tmem, kTcCols);
+    const uint32_t d1 = tmem, d2 = tmem + kH;
+    const uint32_t row_base = (uint32_t)(warp * 32) << 16;
+    const uint32_t aA1 = smem_u32(sA1), aA2 = smem_u32(sA2), aB3 = smem_u32(sB3),
+                   aB2 = smem_u32(sB2);
+    const float inv_nl = 1.0f / (float)max(*d_nlab, 1);
+    uint32_t phase = 0;
+    bool failed = false;
+    for (int base = blockIdx.x * kTcM; base < n; base += gridDim.x * kTcM) {
+        const int h = base + tid;
+        const bool act = h < n;
+        const int lab = act ? labels[h] : -1;
+        // ---- dL (thread = hit): global float32, BF16 into the A tile
+        for (int c0 = 0; c0 < kOut; c0 += 8) {
+            float v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const float pv = act ? prob[(size_t)h * kOut + c0 + u] : 0.f;
+                v[u] = lab >= 0 ? (pv - (c0 + u == lab ? 1.f : 0.f)) * inv_nl : 0.f;
+            }
+            if (act) {
+                float4 *dp = reinterpret_cast<float4 *>(dL + (size_t)h * kOut + c0);
+                dp[0] = make_float4(v[0], v[1], v[2], v[3]);
+                dp[1] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+            __align__(16) __nv_bfloat16 b[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) b[u] = __float2bfloat16_rn(v[u]);
+            *reinterpret_cast<uint4 *>(sA1 + core_off64(tid, c0)) = *reinterpret_cast<uint4 *>(b);
+        }
+        tc_publish();
+        // ---- D1 = dL x W3^T (M 128, N 128, K 64 in 4 steps of 16)
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kOut / 16; ++kk)
+                tc_mma(d1, smem_desc_sbo(aA1 + kk * 2 * kLBO, kSBO64),
+                       smem_desc_sbo(aB3 + kk * 2 * kLBO, kSBO64), mma_idesc(kTcM, kH), kk > 0);
+            tc_commit(mbar);
+        }
+        if (!__syncthreads_and(mbar_wait(mbar, phase))) {
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        // ---- dH2 = D1 o [h2 > 0]: global float32, BF16 into the second A tile
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            uint32_t r[32];
+            tc_ld32(d1 + row_base + c0, r);
+#pragma unroll
+            for (int q = 0; q < 32; q += 8) {
+                __align__(16) __nv_bfloat16 hv[8];
+                *reinterpret_cast<uint4 *>(hv) =
+                    act ? *reinterpret_cast<const uint4 *>(h2 + (size_t)h * kH + c0 + q)
+                        : make_uint4(0, 0, 0, 0);
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = __bfloat162float(hv[u]) > 0.f ? __uint_as_float(r[q + u]) : 0.f;
+                if (act) {
+                    float4 *dp = reinterpret_cast<float4 *>(dH2 + (size_t)h * kH + c0 + q);
+                    dp[0] = make_float4(v[0], v[1], v[2], v[3]);
+                    dp[1] = make_float4(v[4], v[5], v[6], v[7]);
+                }
+                st_core8(sA2, tid, c0 + q, v);
+            }
+        }
+        tc_publish();
+        // ---- D2 = dH2 x W2^T (M 128, N 128, K 128)
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kH / 16; ++kk)
+                tc_mma(d2, smem_desc(aA2 + kk * 2 * kLBO), smem_desc(aB2 + kk * 2 * kLBO),
+                       mma_idesc(kTcM, kH), kk > 0);
+            tc_commit(mbar);
+        }
+        if (!__syncthreads_and(mbar_wait(mbar, phase))) {
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();
+        // ---- dH1 = D2 o [h1 > 0]
+        for (int c0 = 0; c0 < kH; c0 += 32) {
+            uint32_t r[32];
+            tc_ld32(d2 + row_base + c0, r);
+#pragma unroll
+            for (int q = 0; q < 32; q += 8) {
+                if (!act) continue;
+                __align__(16) __nv_bfloat16 hv[8];
+                *reinterpret_cast<uint4 *>(hv) =
+                    *reinterpret_cast<const uint4 *>(h1 + (size_t)h * kH + c0 + q);
+                float v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u)
+                    v[u] = __bfloat162float(hv[u]) > 0.f ? __uint_as_float(r[q + u]) : 0.f;
+                float4 *dp = reinterpret_cast<float4 *>(dH1 + (size_t)h * kH + c0 + q);
+                dp[0] = make_float4(v[0], v[1], v[2], v[3]);
+                dp[1] = make_float4(v[4], v[5], v[6], v[7]);
+            }
+        }
+        tc_fence_before();
+        __syncthreads();      // D1, D2 and both A tiles are free again
+        tc_fence_after();
+    }
+    tc_teardown(failed, mbar, phase, tmem, kTcCols);
+}
+
+// Split blockIdx.x of C[128][N] = sum_h A[h][m] B[h][n] (A BF16, row stride
+// lda; B float32, row stride ldb) and of bias[n] = sum_h B[h][n], over the
+// split's hits; stored at C + split pstride and bias + split pstride.
+__global__ void __launch_bounds__(kTcM)
+k_wgrad_tc(const __nv_bfloat16 *__restrict__ A, int lda, const float *__restrict__ B, int ldb,
+           int n, int N, float *__restrict__ C, float *__restrict__ bias, size_t pstride)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    unsigned char *sA = smem;                           // A^T: M 128 x K 128 hits
+    unsigned char *sB = smem + kTcM * kTcM * 2;         // B^T: N x K 128 hits
+    __shared__ __align__(8) unsigned long long s_mbar;
+    __shared__ uint32_t s_tmem;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    C += (size_t)blockIdx.x * pstride;
+    bias += (size_t)blockIdx.x * pstride;
+    const int per = (n + gridDim.x - 1) / gridDim.x;
+    const int h0 = blockIdx.x * per, h1 = min(n, h0 + per);
+    const uint32_t mbar = smem_u32(&s_mbar);
+    const uint32_t tmem = tc_setup(mbar, &s_tmem, kWgTcCols);
+    const uint32_t aA = smem_u32(sA), aB = smem_u32(sB);
+    uint32_t phase = 0;
+    bool failed = false, any = false;
+    float bacc = 0.f;
+    for (int hb = h0; hb < h1; hb += kTcM) {
+        // ---- stage: thread = row m of A^T (and n of B^T), eight hits per store
+        for (int g = 0; g < kTcM / 8; ++g) {
+            __align__(16) __nv_bfloat16 av[8], bv[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int hh = hb + 8 * g + u;
+                const bool in = hh < h1;
+                av[u] = in ? A[(size_t)hh * lda + tid] : __float2bfloat16_rn(0.f);
+                float b = 0.f;
+                if (tid < N && in) b = B[(size_t)hh * ldb + tid];
+                bacc += b;
+                bv[u] = __float2bfloat16_rn(b);
+            }
+            *reinterpret_cast<uint4 *>(sA + core_off(tid, 8 * g)) = *reinterpret_cast<uint4 *>(av);
+            if (tid < N)
+                *reinterpret_cast<uint4 *>(sB + core_off(tid, 8 * g)) =
+                    *reinterpret_cast<uint4 *>(bv);
+        }
+        tc_publish();
+        if (tid == 0) {
+#pragma unroll
+            for (int kk = 0; kk < kTcM / 16; ++kk)
+                tc_mma(tmem, smem_desc(aA + kk * 2 * kLBO), smem_desc(aB + kk * 2 * kLBO),
+                       mma_idesc(kTcM, N), (any || kk > 0) ? 1u : 0u);
+            tc_commit(mbar);
+        }
+        any = true;
+        if (!__syncthreads_and(mbar_wait(mbar, phase))) {
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        tc_fence_after();   // the tiles may be overwritten: the MMAs are done
+    }
+    if (!failed) {
+        // thread = row m: the split's sums (zero when it had no hits)
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            uint32_t r[32];
+            if (any) tc_ld32(tmem + ((uint32_t)(warp * 32) << 16) + c0, r);
+#pragma unroll
+            for (int q = 0; q < 32; ++q)
+                C[(size_t)tid * N + c0 + q] = any ? __uint_as_float(r[q]) : 0.f;
+        }
+        if (tid < N) bias[tid] = bacc;
+    }
+    tc_teardown(failed, mbar, phase, tmem, kWgTcCols);
+}
