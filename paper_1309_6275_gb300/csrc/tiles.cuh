@@ -72,6 +72,7 @@ struct TileCtx {
     int i0, k0, irow;
     bool row_ok, has_b;
     float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB, cB;
+    float rho2, arho;   // the lane's rho^2 and |rho| (float32), for near-axis items
     float sk[KT], ck[KT];
 
     __device__ __forceinline__ void init(const DevGeom &G, int lane, int tx, int ty)
@@ -84,6 +85,8 @@ struct TileCtx {
         invrho = row_ok ? G.invrho32[irow] : 0.0f;
         has_b = row_ok && (G.rho64[irow] != 0.0);
         invrho_es = fabsf(invrho) * G.err_scale;
+        rho2 = rho * rho;
+        arho = fabsf(rho);
         const int ilast = min(i0 + 31, G.n_rho - 1);
         rho_lo = G.rho32[i0] - G.drho_f;
         rho_hi = G.rho32[ilast] + G.drho_f;
@@ -169,12 +172,120 @@ struct HitCtx {
     }
 };
 
+// ------------------------------------------------------------------ A-form items
+// The vote's common case: a (hit, column) item whose second root is proven out
+// of the axis, with b = 1 + rho s > 0 on every row of the tile (so the one
+// root is C / q, the smaller in magnitude) and whose discriminant
+// D = 1 - rho^2 c^2 stays at or above 1/16 for every |rho| <= rt.  With w = d0 + s the circle equation reads
+// rho w^2 + 2 w + rho c^2 = 0; the root continuous with w = 0 at rho = 0 is the
+// one with |w| < c, w = (sqrt(D) - 1) / rho = -rho c^2 / (1 + sqrt(D)), and it
+// is the same real number as C / q.  Its bin coordinate is
+//   u = A0 - rho c2d / (1 + sqrt(1 - rho^2 c^2)),  A0 = off - s / delta,  c2d = c^2 / delta,
+// A0 and c2d per item: a row costs one rsqrt, one rcp and five FMA-pipe
+// operations, and 1 + sqrt(D) >= 1 keeps every step well conditioned.
+//
+// Error of the float32 coordinate against the exact root of the float64
+// definition's s, c, rho (first order; u = 2^-24; eS = 4e-7 R1 >= 3u R1
+// bounds the float32 s and c; rsqrt.approx and rcp.approx within 4.3u, 2u):
+//   A0 = fma(-s, 1/delta, off):     (eS + u|s|) / delta + u|A0|
+//   c^2 relative 2 eS/c + u; c2d 2 eS/c + 3u; rho c2d 2 eS/c + 5u
+//   D = fma(-rho^2, c^2, 1):        |dD| <= t (2 eS/c + 5u) + u,  t = rt^2 c^2
+//   1 + D rsqrt(D) >= 1, relative:  5.3u + |dD| / sqrt(Dmin); its rcp 2u more
+//   final fma: u (|A0| + |rho| c2d)
+// The second term is at most |rho| c2d, so the bound is affine in |rho|:
+//   e = eA + |rho| eB,  eA = kSafe ((eS + u|s|)/delta + 2u|A0|) + e64,
+//                       eB = kSafe c2d (2 eS/c + 14.3u + |dD| / sqrt(Dmin)).
+// e64 covers the float64 definition's own rounding against the exact root:
+// its C = rho r^2 + 2s (and r^2 against s^2 + c^2) is off by a few 2^-53 of
+// rho R1^2 + 2 R1, divided by |q| >= sqrt(D) >= 1/4, plus a few 2^-53 of |u|.
+// Only items with c > 1 cm and c >= 4e-4 R1 take this form (relative errors
+// far below 1e-3, where first order holds under kSafe), and only while
+// |u| < 2^21 everywhere on the tile, for the floor below.
+constexpr float kMagic = 12582912.0f;       // 1.5 2^23: rd(x + kMagic) - kMagic = floor(x), |x| < 2^22
+constexpr int kMagicBits = 0x4B400000;      // its bits
+
+// Whether a plain item (not unsure, root B proven out) takes the A-form.  A
+// plain item can have b = 1 + rho s <= 0 when its c alone keeps root B out of
+// the axis; its one root is then branch B, so the A-form also needs
+// rt (|s| + eS) < 1, with a margin for the float32 rt and s.
+__device__ __forceinline__ bool aform_ok(const DevGeom &G, float s, float c, float R1, float rt)
+{
+    if (!(c > 1.0f) || c < 4e-4f * R1) return false;
+    const float t = rt * rt * (c * c) * 1.001f;
+    return (rt * fmaf(4e-7f, R1, fabsf(s)) < 0.99f) && (1.0f - t >= 0.0625f) &&
+           fmaf(R1 + rt * c * c, G.inv_delta_f, G.off_f + 1.0f) < 2.0e6f;
+}
+
+// The A-form record {A0, c^2, c2d, eA} and eB of an item that passed aform_ok.
+__device__ __forceinline__ float4 make_aform(const DevGeom &G, float s, float c, float R1,
+                                             float rt, float &eB)
+{
+    const float eS = 4e-7f * R1;
+    const float c2 = c * c;
+    const float t = rt * rt * c2 * 1.001f;
+    const float A0 = fmaf(-s, G.inv_delta_f, G.off_f);
+    const float c2d = c2 * G.inv_delta_f;
+    const float rc = 2.0f * eS * rcp_approx(c) * 1.001f;
+    const float dD = fmaf(t, rc + 5.0f * kEps, kEps);
+    const float isD = rsqrt_approx(1.0f - t) * 1.001f;
+    const float aA = fabsf(A0);
+    const float e64 = 8e-15f * fmaf(rt * R1, R1, 2.0f * R1) * G.inv_delta_f +
+                      4e-15f * (aA + rt * c2d + G.off_f);
+    const float eA = (kSafe * 1.001f) * (fmaf(kEps, fabsf(s), eS) * G.inv_delta_f +
+                                         2.0f * kEps * aA) + e64;
+    eB = (kSafe * 1.001f) * c2d * (rc + 14.3f * kEps + dD * isD);
+    return make_float4(A0, c2, c2d, eA);
+}
+
+// Bin of an A-form item for the lane's row: vote (bin in j), redo (an
+// integer lies within the bound), or neither (certainly outside the axis).
+// The floors of u - e and u + e, rounded outwards, come from one round-down
+// addition of kMagic each (exact integers plus kMagic): equal floors inside
+// the axis prove the bin.
+template <int KT>
+__device__ __forceinline__ void aform_bin(const TileCtx<KT> &T, const float4 a, float eB,
+                                          float mnd, int &j, bool &vote, bool &redo)
+{
+    const float D = fmaf(-T.rho2, a.y, 1.0f);
+    const float rs = rsqrt_approx(D);
+    const float den = fmaf(D, rs, 1.0f);
+    const float ir = rcp_approx(den);
+    const float u = fmaf(-(T.rho * a.z), ir, a.x);
+    const float e = fmaf(T.arho, eB, a.w);
+    const float lo = __fadd_rd(__fsub_rd(u, e), kMagic);
+    const float hi = __fadd_rd(__fadd_ru(u, e), kMagic);
+    j = __float_as_int(lo) - kMagicBits;
+    vote = (lo == hi) & (lo >= kMagic) & (lo < mnd);
+    redo = (lo != hi) & (hi >= kMagic) & (lo < mnd);
+}
+
+// Word offset (from the lane's first word) and increment of column kl's
+// counters in a tile with the layout of TileCol.
+template <int KT, bool PACK>
+__device__ __forceinline__ void col_word(int ND, int kl, uint32_t one, uint32_t &woff,
+                                         uint32_t &inc)
+{
+    if (PACK && KT > 1) {
+        woff = (uint32_t)((kl >> 1) * ND * 32);
+        inc = one << ((kl & 1) << 4);
+    } else if (PACK) {
+        woff = 0u;
+        inc = one;
+    } else {
+        woff = (uint32_t)(kl * ND * 32);
+        inc = one;
+    }
+}
+
 // Phase 1 for the hit at position h of the tile's hit sequence (h >= n: no
 // items), hit index ha, at (xh, yh).  Items record the position.  Appends
 // this warp's items to the list (all 32 lanes must call): plain items
 // (neither unsure nor needing root B) from the front, counted in q[0], the
 // others from the back of the kThreads * KT slots, counted in q[1].
-template <int KT, int MODE = kModePlain>
+// AFORM (the vote tile): the front list takes only A-form items, with the
+// A-form record and their counter word (PACK: the tile's counter layout);
+// other plain items join the back list with the general record.
+template <int KT, int MODE = kModePlain, bool AFORM = false, bool PACK = false>
 __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, float xh,
                                         float yh, int n, int h, int ha, int lane, int *q,
                                         const WorkList &W, const MaskCtx *M = nullptr,
@@ -184,7 +295,7 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
     constexpr int BM = base_mode(MODE);
     float is_[KT], ic_[KT];
     int fl_[KT];
-    unsigned sel = 0u;
+    unsigned sel = 0u, af = 0u;
     float r2 = 0.0f, R1 = 0.0f;
     unsigned long long hm = 0ull;
     float hwlo = 0.0f, hwhi = 0.0f;
@@ -240,6 +351,7 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
                 }
             }
             if (fabsf(s) + eS >= T.sB && c + eS >= T.cB) f |= kMetaNeedB;
+            if (AFORM && f == 0 && aform_ok(G, s, c, R1, T.rt)) af |= 1u << kl;
             sel |= 1u << kl;
             fl_[kl] = f;
             is_[kl] = s;
@@ -249,7 +361,9 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
     unsigned slow = 0u;
 #pragma unroll
     for (int kl = 0; kl < KT; ++kl)
-        if ((sel & (1u << kl)) && (fl_[kl] & (kMetaUnsure | kMetaNeedB))) slow |= 1u << kl;
+        if ((sel & (1u << kl)) && (AFORM ? !(af & (1u << kl))
+                                         : (fl_[kl] & (kMetaUnsure | kMetaNeedB)) != 0))
+            slow |= 1u << kl;
     // one scan of both counts (plain in the low half, others in the high)
     const int mine = __popc(sel & ~slow) | (__popc(slow) << 16);
     int incl = mine;
@@ -272,9 +386,17 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
     for (int kl = 0; kl < KT; ++kl) {
         if (sel & (1u << kl)) {
             const int pos = (slow & (1u << kl)) ? kThreads * KT - 1 - ps++ : pf++;
-            const Item it = make_item(G, is_[kl], ic_[kl], r2, R1, T.rt);
-            W.a[pos] = make_float4(it.s, it.c, it.r2, it.eD);
-            W.b[pos] = make_float4(it.E1, it.E2, it.Qa, it.Qb);
+            if (AFORM && (af & (1u << kl))) {
+                float eB;
+                W.a[pos] = make_aform(G, is_[kl], ic_[kl], R1, T.rt, eB);
+                uint32_t woff, inc;
+                col_word<KT, PACK>(G.n_d0, kl, layer_mode(MODE) ? 1u << lh : 1u, woff, inc);
+                W.b[pos] = make_float4(__uint_as_float(woff), __uint_as_float(inc), eB, 0.0f);
+            } else {
+                const Item it = make_item(G, is_[kl], ic_[kl], r2, R1, T.rt);
+                W.a[pos] = make_float4(it.s, it.c, it.r2, it.eD);
+                W.b[pos] = make_float4(it.E1, it.E2, it.Qa, it.Qb);
+            }
             W.meta[pos] = (h << 6) | fl_[kl] | kl;
             if (BM == kModeHit) W.hm[pos] = hm;
             if (layer_mode(MODE)) W.lay[pos] = lh;
@@ -460,6 +582,17 @@ struct TileCol {
     }
 };
 
+// An A-form item's vote: its counter word woff (from the lane's first word
+// cntl) and increment inc, as col_word gave them, in bin j.
+template <int KT, bool PACK, bool LAY>
+__device__ __forceinline__ void add_word(uint32_t *cntl, uint32_t woff, uint32_t inc, int j)
+{
+    uint32_t *w = (PACK && KT == 1) ? cntl + woff + (j >> 1) * 32 : cntl + woff + j * 32;
+    const uint32_t v = (PACK && KT == 1) ? inc << ((j & 1) << 4) : inc;
+    if (LAY) atomicOr(w, v);
+    else atomicAdd(w, v);
+}
+
 template <int KT, bool PACK>
 __device__ __forceinline__ uint32_t tile_get(const uint32_t *cnt, int ND, int kl, int j, int il)
 {
@@ -545,7 +678,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     __syncthreads();
 
     int my_fb = 0;
-    unsigned long long my_cast = 0;   // LAY: votes cast (cell sums are layer counts)
+    unsigned my_cast = 0;   // LAY: votes cast by this thread in the tile (< 2^32: 2 KT per hit)
     int parity = 0;
     const HitSeq S{hl, hl ? nl : n};
     HitPrefetch pf;
@@ -554,8 +687,8 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         int ha;
         float xh, yh;
         pf.next(x, y, S, base, ha, xh, yh);
-        collect<KT, MODE>(G, T, xh, yh, S.n, base + threadIdx.x, ha, lane, qn[parity], W, &M,
-                          &H, layer);
+        collect<KT, MODE, true, PACK>(G, T, xh, yh, S.n, base + threadIdx.x, ha, lane,
+                                      qn[parity], W, &M, &H, layer);
         __syncthreads();
         const int nf = qn[parity][0], ns = qn[parity][1];
         if (threadIdx.x == 0) {   // last read before the previous barrier
@@ -563,33 +696,57 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
             qn[parity ^ 1][1] = 0;
         }
         if (T.row_ok) {
-            // plain items: one root, no flags to test
-#pragma unroll 2
-            for (int t = warp; t < nf; t += nwarps) {
-                const int m = W.meta[t];
+            // A-form items: one root, no flags to test, the counter word and
+            // increment precomputed.  A warp takes two items per iteration:
+            // both are loaded before either votes (a shared atomic orders
+            // the loads behind it), their evaluations are independent, and
+            // one warp vote covers both redo tests (rare).
+            uint32_t *const cntl = cnt + lane;
+            const float mnd = kMagic + (float)ND;
+            auto redo_item = [&](int tt) {
+                ++my_fb;
+                const int m = W.meta[tt];
+                const int hh = S.hit(m >> 6);
+                if (push_redo(R, &rn, hh, lane, m & kMetaCol)) return;
                 const TileCol<KT, PACK, LAY> col(cnt, ND, m & kMetaCol, lane,
-                                                 LAY ? 1u << W.lay[t] : 1u);
-                int j;
-                const int r = fast_bin32<KT>(G, T, W, t, j);
-                if (r == kFastVote && (BM != kModeHit || (H.row_bits(W.hm[t]) & H.jmask[j]))) {
-                    col.add(j);
+                                                 LAY ? 1u << W.lay[tt] : 1u);
+                int jj[2];
+                int nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
+                if (BM == kModeHit) nv = keep_allowed(H.row_bits(W.hm[tt]), H.jmask, nv, jj);
+                for (int v = 0; v < nv; ++v) col.add(jj[v]);
+                if (LAY) my_cast += nv;
+            };
+            auto vote_item = [&](int tt, const float4 &b, int j, bool vote) {
+                if (vote && (BM != kModeHit || (H.row_bits(W.hm[tt]) & H.jmask[j]))) {
+                    add_word<KT, PACK, LAY>(cntl, __float_as_uint(b.x), __float_as_uint(b.y), j);
                     if (LAY) ++my_cast;
                 }
-                // the usual case: no lane needs a redo (lanes of rows past n_rho
-                // do not run this loop, hence the active mask)
-                if (!__any_sync(__activemask(), r == kFastRedo)) continue;
-                if (r == kFastRedo) {
-                    ++my_fb;
-                    const int hh = S.hit(m >> 6);
-                    if (push_redo(R, &rn, hh, lane, m & kMetaCol)) continue;
-                    int jj[2];
-                    int nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
-                    if (BM == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
-                    for (int v = 0; v < nv; ++v) col.add(jj[v]);
-                    if (LAY) my_cast += nv;
-                }
+            };
+            int t = warp;
+            for (; t + nwarps < nf; t += 2 * nwarps) {
+                const float4 a0 = W.a[t], b0 = W.b[t];
+                const float4 a1 = W.a[t + nwarps], b1 = W.b[t + nwarps];
+                int j0, j1;
+                bool v0, v1, r0, r1;
+                aform_bin<KT>(T, a0, b0.z, mnd, j0, v0, r0);
+                aform_bin<KT>(T, a1, b1.z, mnd, j1, v1, r1);
+                vote_item(t, b0, j0, v0);
+                vote_item(t + nwarps, b1, j1, v1);
+                // lanes of rows past n_rho do not run this loop, hence the active mask
+                if (!__any_sync(__activemask(), r0 | r1)) continue;
+                if (r0) redo_item(t);
+                if (r1) redo_item(t + nwarps);
             }
-            // unsure items and items whose second root can reach the axis
+            if (t < nf) {
+                const float4 a0 = W.a[t], b0 = W.b[t];
+                int j0;
+                bool v0, r0;
+                aform_bin<KT>(T, a0, b0.z, mnd, j0, v0, r0);
+                vote_item(t, b0, j0, v0);
+                if (r0) redo_item(t);
+            }
+            // unsure items, items whose second root can reach the axis and the
+            // other plain items
             for (int t = kThreads * KT - ns + warp; t < kThreads * KT; t += nwarps) {
                 const int m = W.meta[t];
                 const TileCol<KT, PACK, LAY> col(cnt, ND, m & kMetaCol, lane,
