@@ -66,20 +66,16 @@ __device__ __forceinline__ WorkList carve_worklist(unsigned char *p, int cap,
     return w;
 }
 
-// Per-tile constants of the lane's row and of the tile's columns.
-template <int KT>
-struct TileCtx {
-    int i0, k0, irow;
+// Constants of one row of a tile as a lane sees it.
+struct RowCtx {
+    int irow;
     bool row_ok, has_b;
-    float rho, invrho, invrho_es, rho_lo, rho_hi, rt, sB, cB;
-    float rho2, arho;   // the lane's rho^2 and |rho| (float32), for near-axis items
-    float sk[KT], ck[KT];
+    float rho, invrho, invrho_es;
+    float rho2, arho;   // rho^2 and |rho| (float32), for A-form items
 
-    __device__ __forceinline__ void init(const DevGeom &G, int lane, int tx, int ty)
+    __device__ __forceinline__ void init_row(const DevGeom &G, int i)
     {
-        k0 = tx * KT;
-        i0 = ty * 32;
-        irow = i0 + lane;
+        irow = i;
         row_ok = irow < G.n_rho;
         rho = row_ok ? G.rho32[irow] : 0.0f;
         invrho = row_ok ? G.invrho32[irow] : 0.0f;
@@ -87,7 +83,26 @@ struct TileCtx {
         invrho_es = fabsf(invrho) * G.err_scale;
         rho2 = rho * rho;
         arho = fabsf(rho);
-        const int ilast = min(i0 + 31, G.n_rho - 1);
+    }
+};
+
+// Per-tile constants of the lane's rows and of the tile's columns.  A tile
+// has 32 RW rows: the lane's first row (i0 + lane) is the base RowCtx, its
+// second (i0 + 32 + lane, RW = 2) is r1.
+template <int KT, int RW = 1>
+struct TileCtx : RowCtx {
+    int i0, k0;
+    float rho_lo, rho_hi, rt, sB, cB;
+    float sk[KT], ck[KT];
+    RowCtx r1;
+
+    __device__ __forceinline__ void init(const DevGeom &G, int lane, int tx, int ty)
+    {
+        k0 = tx * KT;
+        i0 = ty * 32 * RW;
+        init_row(G, i0 + lane);
+        if (RW == 2) r1.init_row(G, i0 + 32 + lane);
+        const int ilast = min(i0 + 32 * RW - 1, G.n_rho - 1);
         rho_lo = G.rho32[i0] - G.drho_f;
         rho_hi = G.rho32[ilast] + G.drho_f;
         rt = fmaxf(fabsf(G.rho32[i0]), fabsf(G.rho32[ilast])) * 1.0001f;
@@ -242,9 +257,8 @@ __device__ __forceinline__ float4 make_aform(const DevGeom &G, float s, float c,
 // The floors of u - e and u + e, rounded outwards, come from one round-down
 // addition of kMagic each (exact integers plus kMagic): equal floors inside
 // the axis prove the bin.
-template <int KT>
-__device__ __forceinline__ void aform_bin(const TileCtx<KT> &T, const float4 a, float eB,
-                                          float mnd, int &j, bool &vote, bool &redo)
+__device__ __forceinline__ void aform_bin(const RowCtx &T, const float4 a, float eB, float mnd,
+                                          int &j, bool &vote, bool &redo)
 {
     const float D = fmaf(-T.rho2, a.y, 1.0f);
     const float rs = rsqrt_approx(D);
@@ -260,19 +274,19 @@ __device__ __forceinline__ void aform_bin(const TileCtx<KT> &T, const float4 a, 
 }
 
 // Word offset (from the lane's first word) and increment of column kl's
-// counters in a tile with the layout of TileCol.
-template <int KT, bool PACK>
+// counters in a tile of 32 RW rows with the layout of TileCol.
+template <int KT, bool PACK, int RW = 1>
 __device__ __forceinline__ void col_word(int ND, int kl, uint32_t one, uint32_t &woff,
                                          uint32_t &inc)
 {
     if (PACK && KT > 1) {
-        woff = (uint32_t)((kl >> 1) * ND * 32);
+        woff = (uint32_t)((kl >> 1) * ND * 32 * RW);
         inc = one << ((kl & 1) << 4);
     } else if (PACK) {
         woff = 0u;
         inc = one;
     } else {
-        woff = (uint32_t)(kl * ND * 32);
+        woff = (uint32_t)(kl * ND * 32 * RW);
         inc = one;
     }
 }
@@ -285,8 +299,8 @@ __device__ __forceinline__ void col_word(int ND, int kl, uint32_t one, uint32_t 
 // AFORM (the vote tile): the front list takes only A-form items, with the
 // A-form record and their counter word (PACK: the tile's counter layout);
 // other plain items join the back list with the general record.
-template <int KT, int MODE = kModePlain, bool AFORM = false, bool PACK = false>
-__device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, float xh,
+template <int KT, int MODE = kModePlain, bool AFORM = false, bool PACK = false, int RW = 1>
+__device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT, RW> &T, float xh,
                                         float yh, int n, int h, int ha, int lane, int *q,
                                         const WorkList &W, const MaskCtx *M = nullptr,
                                         const HitCtx *H = nullptr,
@@ -390,7 +404,7 @@ __device__ __forceinline__ void collect(const DevGeom &G, const TileCtx<KT> &T, 
                 float eB;
                 W.a[pos] = make_aform(G, is_[kl], ic_[kl], R1, T.rt, eB);
                 uint32_t woff, inc;
-                col_word<KT, PACK>(G.n_d0, kl, layer_mode(MODE) ? 1u << lh : 1u, woff, inc);
+                col_word<KT, PACK, RW>(G.n_d0, kl, layer_mode(MODE) ? 1u << lh : 1u, woff, inc);
                 W.b[pos] = make_float4(__uint_as_float(woff), __uint_as_float(inc), eB, 0.0f);
             } else {
                 const Item it = make_item(G, is_[kl], ic_[kl], r2, R1, T.rt);
@@ -456,7 +470,7 @@ struct HitPrefetch {
 // Bins of work item t for the lane's row by guarded float32: the number of
 // bins written to jj, or -1 when the column must be redone in float64.
 template <int KT>
-__device__ __forceinline__ int item_bins32(const DevGeom &G, const TileCtx<KT> &T,
+__device__ __forceinline__ int item_bins32(const DevGeom &G, const RowCtx &T,
                                            const WorkList &W, int t, int m, int jj[2])
 {
     if (m & kMetaUnsure) return -1;
@@ -552,7 +566,9 @@ __device__ __forceinline__ bool push_redo(const RedoQueue &Q, int *n, int hit, i
 // scanned hit, so it is used only for tiles scanning at most kPackMaxHits.
 // LAY (the distinct-layer vote): the same words hold layer masks; a vote
 // ORs the hit's layer bit lbit (1 << layer) instead of adding one.
-template <int KT, bool PACK, bool LAY = false>
+// RW: the tile has 32 RW rows (row fastest, 32 RW words per bin); lane is
+// the row within the tile.
+template <int KT, bool PACK, bool LAY = false, int RW = 1>
 struct TileCol {
     uint32_t *base;
     uint32_t inc;
@@ -562,20 +578,20 @@ struct TileCol {
     {
         const uint32_t one = LAY ? lbit : 1u;
         if (PACK && KT > 1) {
-            base = cnt + (kl >> 1) * ND * 32 + lane;
+            base = cnt + (kl >> 1) * ND * 32 * RW + lane;
             inc = one << ((kl & 1) << 4);
         } else if (PACK) {
             base = cnt + lane;
             inc = one;
         } else {
-            base = cnt + kl * ND * 32 + lane;
+            base = cnt + kl * ND * 32 * RW + lane;
             inc = one;
         }
     }
 
     __device__ __forceinline__ void add(int j) const
     {
-        uint32_t *w = (PACK && KT == 1) ? base + (j >> 1) * 32 : base + j * 32;
+        uint32_t *w = (PACK && KT == 1) ? base + (j >> 1) * 32 * RW : base + j * 32 * RW;
         const uint32_t v = (PACK && KT == 1) ? inc << ((j & 1) << 4) : inc;
         if (LAY) atomicOr(w, v);
         else atomicAdd(w, v);
@@ -584,21 +600,23 @@ struct TileCol {
 
 // An A-form item's vote: its counter word woff (from the lane's first word
 // cntl) and increment inc, as col_word gave them, in bin j.
-template <int KT, bool PACK, bool LAY>
+template <int KT, bool PACK, bool LAY, int RW = 1>
 __device__ __forceinline__ void add_word(uint32_t *cntl, uint32_t woff, uint32_t inc, int j)
 {
-    uint32_t *w = (PACK && KT == 1) ? cntl + woff + (j >> 1) * 32 : cntl + woff + j * 32;
+    uint32_t *w = (PACK && KT == 1) ? cntl + woff + (j >> 1) * 32 * RW
+                                    : cntl + woff + j * 32 * RW;
     const uint32_t v = (PACK && KT == 1) ? inc << ((j & 1) << 4) : inc;
     if (LAY) atomicOr(w, v);
     else atomicAdd(w, v);
 }
 
-template <int KT, bool PACK>
+template <int KT, bool PACK, int RW = 1>
 __device__ __forceinline__ uint32_t tile_get(const uint32_t *cnt, int ND, int kl, int j, int il)
 {
-    if (PACK && KT > 1) return (cnt[((kl >> 1) * ND + j) * 32 + il] >> ((kl & 1) << 4)) & 0xffffu;
-    if (PACK) return (cnt[(j >> 1) * 32 + il] >> ((j & 1) << 4)) & 0xffffu;
-    return cnt[(kl * ND + j) * 32 + il];
+    constexpr int R = 32 * RW;
+    if (PACK && KT > 1) return (cnt[((kl >> 1) * ND + j) * R + il] >> ((kl & 1) << 4)) & 0xffffu;
+    if (PACK) return (cnt[(j >> 1) * R + il] >> ((j & 1) << 4)) & 0xffffu;
+    return cnt[(kl * ND + j) * R + il];
 }
 
 // Keep the bins jj[0 .. nv) that the hit's region set allows in the lane's
@@ -617,7 +635,10 @@ __device__ __forceinline__ int keep_allowed(unsigned bm, const uint8_t *jmask, i
 // cell is written.
 // hl (optional): the tile scans only the nl hits hl[0 .. nl) of the event
 // (a superset of those that can vote in its columns); otherwise all n.
-template <int KT, typename OutT, bool PACK, int MODE = kModePlain>
+// RW = 2 (the plain and distinct-layer votes only): tiles of 64 rows, each
+// lane evaluating rows lane and 32 + lane of every item, so that an item's
+// loads, its phase-1 work and the warp's bookkeeping serve twice the votes.
+template <int KT, typename OutT, bool PACK, int MODE = kModePlain, int RW = 1>
 __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restrict__ x,
                                           const float *__restrict__ y, int n,
                                           OutT *__restrict__ acc,
@@ -629,12 +650,14 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 {
     constexpr int BM = base_mode(MODE);
     constexpr bool LAY = layer_mode(MODE);
+    static_assert(RW == 1 || (RW == 2 && BM == kModePlain), "64-row tiles: plain modes only");
+    constexpr int TR = 32 * RW;                            // rows per tile
     extern __shared__ __align__(16) unsigned char smem[];
     const int ND = G.n_d0;
     const int NW = PACK ? (ND >> 1) : ND;                  // words per column-row
     constexpr int QCAP = kThreads * KT;
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][NW][32]
-    unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * NW * 32);
+    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem);    // [KT][NW][TR]
+    unsigned char *p = reinterpret_cast<unsigned char *>(cnt + KT * NW * TR);
     const WorkList W = carve_worklist(p, QCAP, MODE);
     const RedoQueue R = carve_redo(p + (size_t)QCAP * item_bytes(MODE));
     __shared__ int qn[2][2], rn;   // [parity][plain, others]
@@ -642,7 +665,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     constexpr int nwarps = kThreads / 32;
-    TileCtx<KT> T;
+    TileCtx<KT, RW> T;
     T.init(G, lane, tx, ty);
     MaskCtx M;
     if (BM == kModeEvent) {
@@ -670,7 +693,7 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     }
     {
         uint4 *c4 = reinterpret_cast<uint4 *>(cnt);
-        for (int t = threadIdx.x; t < KT * NW * 8; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
+        for (int t = threadIdx.x; t < KT * NW * 8 * RW; t += kThreads) c4[t] = make_uint4(0, 0, 0, 0);
     }
     if (threadIdx.x < 4) qn[threadIdx.x >> 1][threadIdx.x & 1] = 0;
     if (threadIdx.x < 2) s_stats[threadIdx.x] = 0ull;
@@ -687,8 +710,8 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
         int ha;
         float xh, yh;
         pf.next(x, y, S, base, ha, xh, yh);
-        collect<KT, MODE, true, PACK>(G, T, xh, yh, S.n, base + threadIdx.x, ha, lane,
-                                      qn[parity], W, &M, &H, layer);
+        collect<KT, MODE, true, PACK, RW>(G, T, xh, yh, S.n, base + threadIdx.x, ha, lane,
+                                          qn[parity], W, &M, &H, layer);
         __syncthreads();
         const int nf = qn[parity][0], ns = qn[parity][1];
         if (threadIdx.x == 0) {   // last read before the previous barrier
@@ -700,25 +723,29 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
             // increment precomputed.  A warp takes two items per iteration:
             // both are loaded before either votes (a shared atomic orders
             // the loads behind it), their evaluations are independent, and
-            // one warp vote covers both redo tests (rare).
+            // one warp vote covers both redo tests (rare).  With RW = 2 each
+            // lane also evaluates its second row (32 + lane) of both items.
             uint32_t *const cntl = cnt + lane;
             const float mnd = kMagic + (float)ND;
-            auto redo_item = [&](int tt) {
+            const RowCtx &T1 = T.r1;
+            const bool ok1 = RW == 2 && T1.row_ok;
+            auto redo_item = [&](int tt, const RowCtx &Rw, int il) {
                 ++my_fb;
                 const int m = W.meta[tt];
                 const int hh = S.hit(m >> 6);
-                if (push_redo(R, &rn, hh, lane, m & kMetaCol)) return;
-                const TileCol<KT, PACK, LAY> col(cnt, ND, m & kMetaCol, lane,
-                                                 LAY ? 1u << W.lay[tt] : 1u);
+                if (push_redo(R, &rn, hh, il, m & kMetaCol)) return;
+                const TileCol<KT, PACK, LAY, RW> col(cnt, ND, m & kMetaCol, il,
+                                                     LAY ? 1u << W.lay[tt] : 1u);
                 int jj[2];
-                int nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
+                int nv = redo_bins(G, x[hh], y[hh], Rw.irow, T.k0 + (m & kMetaCol), jj);
                 if (BM == kModeHit) nv = keep_allowed(H.row_bits(W.hm[tt]), H.jmask, nv, jj);
                 for (int v = 0; v < nv; ++v) col.add(jj[v]);
                 if (LAY) my_cast += nv;
             };
-            auto vote_item = [&](int tt, const float4 &b, int j, bool vote) {
+            auto vote_item = [&](int tt, const float4 &b, int j, bool vote, int r) {
                 if (vote && (BM != kModeHit || (H.row_bits(W.hm[tt]) & H.jmask[j]))) {
-                    add_word<KT, PACK, LAY>(cntl, __float_as_uint(b.x), __float_as_uint(b.y), j);
+                    add_word<KT, PACK, LAY, RW>(cntl + 32 * r, __float_as_uint(b.x),
+                                                __float_as_uint(b.y), j);
                     if (LAY) ++my_cast;
                 }
             };
@@ -726,43 +753,70 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
             for (; t + nwarps < nf; t += 2 * nwarps) {
                 const float4 a0 = W.a[t], b0 = W.b[t];
                 const float4 a1 = W.a[t + nwarps], b1 = W.b[t + nwarps];
-                int j0, j1;
-                bool v0, v1, r0, r1;
-                aform_bin<KT>(T, a0, b0.z, mnd, j0, v0, r0);
-                aform_bin<KT>(T, a1, b1.z, mnd, j1, v1, r1);
-                vote_item(t, b0, j0, v0);
-                vote_item(t + nwarps, b1, j1, v1);
+                int j0, j1, j2 = 0, j3 = 0;
+                bool v0, v1, r0, r1, v2 = false, v3 = false, r2 = false, r3 = false;
+                aform_bin(T, a0, b0.z, mnd, j0, v0, r0);
+                aform_bin(T, a1, b1.z, mnd, j1, v1, r1);
+                if (RW == 2) {
+                    aform_bin(T1, a0, b0.z, mnd, j2, v2, r2);
+                    aform_bin(T1, a1, b1.z, mnd, j3, v3, r3);
+                    v2 &= ok1;
+                    v3 &= ok1;
+                    r2 &= ok1;
+                    r3 &= ok1;
+                }
+                vote_item(t, b0, j0, v0, 0);
+                vote_item(t + nwarps, b1, j1, v1, 0);
+                if (RW == 2) {
+                    vote_item(t, b0, j2, v2, 1);
+                    vote_item(t + nwarps, b1, j3, v3, 1);
+                }
                 // lanes of rows past n_rho do not run this loop, hence the active mask
-                if (!__any_sync(__activemask(), r0 | r1)) continue;
-                if (r0) redo_item(t);
-                if (r1) redo_item(t + nwarps);
+                if (!__any_sync(__activemask(), r0 | r1 | r2 | r3)) continue;
+                if (r0) redo_item(t, T, lane);
+                if (r1) redo_item(t + nwarps, T, lane);
+                if (RW == 2) {
+                    if (r2) redo_item(t, T1, 32 + lane);
+                    if (r3) redo_item(t + nwarps, T1, 32 + lane);
+                }
             }
             if (t < nf) {
                 const float4 a0 = W.a[t], b0 = W.b[t];
                 int j0;
                 bool v0, r0;
-                aform_bin<KT>(T, a0, b0.z, mnd, j0, v0, r0);
-                vote_item(t, b0, j0, v0);
-                if (r0) redo_item(t);
+                aform_bin(T, a0, b0.z, mnd, j0, v0, r0);
+                vote_item(t, b0, j0, v0, 0);
+                if (r0) redo_item(t, T, lane);
+                if (RW == 2 && ok1) {
+                    aform_bin(T1, a0, b0.z, mnd, j0, v0, r0);
+                    vote_item(t, b0, j0, v0, 1);
+                    if (r0) redo_item(t, T1, 32 + lane);
+                }
             }
             // unsure items, items whose second root can reach the axis and the
             // other plain items
             for (int t = kThreads * KT - ns + warp; t < kThreads * KT; t += nwarps) {
                 const int m = W.meta[t];
-                const TileCol<KT, PACK, LAY> col(cnt, ND, m & kMetaCol, lane,
-                                                 LAY ? 1u << W.lay[t] : 1u);
-                int jj[2];
-                int nv = item_bins32<KT>(G, T, W, t, m, jj);
-                if (nv < 0) {
-                    ++my_fb;
-                    const int hh = S.hit(m >> 6);
-                    if (push_redo(R, &rn, hh, lane, m & kMetaCol)) continue;
-                    nv = redo_bins(G, x[hh], y[hh], T.irow, T.k0 + (m & kMetaCol), jj);
+#pragma unroll
+                for (int r = 0; r < RW; ++r) {
+                    const RowCtx &Rw = r == 0 ? static_cast<const RowCtx &>(T) : T1;
+                    if (r == 1 && !ok1) break;
+                    const int il = lane + 32 * r;
+                    const TileCol<KT, PACK, LAY, RW> col(cnt, ND, m & kMetaCol, il,
+                                                         LAY ? 1u << W.lay[t] : 1u);
+                    int jj[2];
+                    int nv = item_bins32<KT>(G, Rw, W, t, m, jj);
+                    if (nv < 0) {
+                        ++my_fb;
+                        const int hh = S.hit(m >> 6);
+                        if (push_redo(R, &rn, hh, il, m & kMetaCol)) continue;
+                        nv = redo_bins(G, x[hh], y[hh], Rw.irow, T.k0 + (m & kMetaCol), jj);
+                    }
+                    if (BM == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
+                    if (nv > 0) col.add(jj[0]);
+                    if (nv > 1) col.add(jj[1]);
+                    if (LAY) my_cast += nv;
                 }
-                if (BM == kModeHit) nv = keep_allowed(H.row_bits(W.hm[t]), H.jmask, nv, jj);
-                if (nv > 0) col.add(jj[0]);
-                if (nv > 1) col.add(jj[1]);
-                if (LAY) my_cast += nv;
             }
         }
         __syncthreads();
@@ -777,7 +831,8 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
                 if (BM == kModeHit)
                     nv = keep_allowed(halo_row_blocks(H.masks[h], T.i0 + il, G.n_rho), H.jmask, nv,
                                       jj);
-                const TileCol<KT, PACK, LAY> col(cnt, ND, kl, il, LAY ? 1u << __ldg(layer + h) : 1u);
+                const TileCol<KT, PACK, LAY, RW> col(cnt, ND, kl, il,
+                                                     LAY ? 1u << __ldg(layer + h) : 1u);
                 for (int v = 0; v < nv; ++v) col.add(jj[v]);
                 if (LAY) my_cast += nv;
             }
@@ -791,15 +846,15 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
     // one vector of KT * sizeof(OutT) bytes.  Votes are summed here (tile
     // counters never saturate: they hold at most 2 n).
     unsigned long long my_votes = 0;
-    for (int t = threadIdx.x; t < 32 * ND; t += kThreads) {
-        const int il = t & 31, j = t >> 5;   // il == lane
+    for (int t = threadIdx.x; t < TR * ND; t += kThreads) {
+        const int il = t & (TR - 1), j = t / TR;   // il == lane (RW = 1) or lane + 32 (RW = 2)
         const int i = T.i0 + il;
         if (i >= G.n_rho) continue;
         const bool keep = BM != kModeEvent || halo_bin(M.bm, j, ND);
         __align__(16) OutT e[KT];
 #pragma unroll
         for (int kl = 0; kl < KT; ++kl) {
-            uint32_t v = keep ? tile_get<KT, PACK>(cnt, ND, kl, j, il) : 0u;
+            uint32_t v = keep ? tile_get<KT, PACK, RW>(cnt, ND, kl, j, il) : 0u;
             if (LAY) v = (uint32_t)__popc(v);
             else my_votes += v;
             e[kl] = saturate<OutT>(v);
@@ -835,13 +890,13 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 
 // mask: kModeEvent one device uint64, kModeHit one per hit, else unused;
 // layer: one uint8 per hit under kModeLayers, else unused.
-template <int KT, typename OutT, bool PACK, int MODE>
+template <int KT, typename OutT, bool PACK, int MODE, int RW = 1>
 __global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
 k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
        OutT *__restrict__ acc, unsigned long long *__restrict__ stats,
        const unsigned long long *__restrict__ mask, const uint8_t *__restrict__ layer)
 {
-    vote_tile<KT, OutT, PACK, MODE>(G, x, y, n, acc, stats, blockIdx.x, blockIdx.y,
+    vote_tile<KT, OutT, PACK, MODE, RW>(G, x, y, n, acc, stats, blockIdx.x, blockIdx.y,
                                     base_mode(MODE) == kModeEvent ? *mask : ~0ull, mask,
                                     nullptr, 0, layer);
 }
@@ -853,7 +908,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
 // set per hit of the batch (indexed like x).
 // bk (optional, ent null for none): per-event hit lists by column group; a
 // tile scans its group's list instead of the whole event.
-template <int KT, typename OutT, bool PACK, int MODE>
+template <int KT, typename OutT, bool PACK, int MODE, int RW = 1>
 __global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
 k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
              const int *__restrict__ off, const int *__restrict__ order,
@@ -864,7 +919,7 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
 {
     constexpr int BM = base_mode(MODE);
     __shared__ int s_item;
-    const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 31) / 32, ntiles = ntx * nty;
+    const int ntx = G.n_phi0 / KT, nty = (G.n_rho + 32 * RW - 1) / (32 * RW), ntiles = ntx * nty;
     const int total = *d_nev * ntiles;
     for (;;) {
         if (threadIdx.x == 0) s_item = atomicAdd(head, 1);
@@ -883,7 +938,7 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
         // by the scanned list's length (uniform over the CTA).  Layer masks
         // never carry, so the distinct-layer vote packs every tile.
         if (layer_mode(MODE) ? PACK : (PACK == ((bk.ent ? nl : n) <= kPackMaxHits)))
-            vote_tile<KT, OutT, PACK, MODE>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
+            vote_tile<KT, OutT, PACK, MODE, RW>(G, x + a, y + a, n, acc + (size_t)e * acc_stride,
                                             stats ? stats + 2 * e : nullptr, t % ntx, t / ntx,
                                             BM == kModeEvent ? masks[e] : ~0ull,
                                             BM == kModeHit ? masks + a : nullptr, hl, nl,
@@ -893,9 +948,9 @@ k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y
 }
 
 template <int KT>
-size_t vote_smem(const DevGeom &G, bool pack, int mode = kModePlain)
+size_t vote_smem(const DevGeom &G, bool pack, int mode = kModePlain, int rw = 1)
 {
-    return (size_t)KT * 32 * (pack ? G.n_d0 / 2 : G.n_d0) * 4 +
+    return (size_t)KT * 32 * rw * (pack ? G.n_d0 / 2 : G.n_d0) * 4 +
            (size_t)kThreads * KT * item_bytes(mode) + kRedoBytes +
            (base_mode(mode) == kModeHit ? ((size_t)G.n_d0 + 15) / 16 * 16 : 0);
 }
@@ -903,15 +958,23 @@ size_t vote_smem(const DevGeom &G, bool pack, int mode = kModePlain)
 constexpr size_t kSmemBudget2 = 110 * 1024;   // two CTAs per SM
 constexpr size_t kSmemBudget3 = 75 * 1024;    // three CTAs per SM
 
-template <int KT, typename OutT, bool PACK, int MODE>
+template <int KT, typename OutT, bool PACK, int MODE, int RW = 1>
 cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                            unsigned long long *stats, const unsigned long long *mask,
                            cudaStream_t st, const uint8_t *layer)
 {
-    dim3 grid(G.n_phi0 / KT, (G.n_rho + 31) / 32);
-    k_vote<KT, OutT, PACK, MODE><<<grid, kThreads, vote_smem<KT>(G, PACK, MODE), st>>>(
+    dim3 grid(G.n_phi0 / KT, (G.n_rho + 32 * RW - 1) / (32 * RW));
+    k_vote<KT, OutT, PACK, MODE, RW><<<grid, kThreads, vote_smem<KT>(G, PACK, MODE, RW), st>>>(
         G, x, y, n, reinterpret_cast<OutT *>(acc), stats, mask, layer);
     return cudaGetLastError();
+}
+
+// The distinct-layer vote's default tile: 64 rows of two columns when it
+// fits three CTAs per SM (plain base mode only).
+template <int MODE>
+constexpr bool tall_tiles_ok()
+{
+    return layer_mode(MODE) && base_mode(MODE) == kModePlain;
 }
 
 // Tile shape: packed 16-bit counters with three CTAs per SM when the output
@@ -925,6 +988,15 @@ cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int 
 {
 #define HT_V(KTV, OT, PK)                                                                     \
     return launch_vote_kt<KTV, OT, PK, MODE>(G, x, y, n, acc, stats, mask, st, layer)
+    if constexpr (tall_tiles_ok<MODE>()) {
+        if (vote_smem<2>(G, true, MODE, 2) <= kSmemBudget3) {
+            if (G.count_bits == 16)
+                return launch_vote_kt<2, uint16_t, true, MODE, 2>(G, x, y, n, acc, stats, mask,
+                                                                  st, layer);
+            return launch_vote_kt<2, int32_t, true, MODE, 2>(G, x, y, n, acc, stats, mask, st,
+                                                             layer);
+        }
+    }
     if constexpr (layer_mode(MODE)) {
         if (G.count_bits == 16) {
             if (vote_smem<4>(G, true, MODE) <= kSmemBudget3) HT_V(4, uint16_t, true);
@@ -969,20 +1041,25 @@ cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y
                                 cudaStream_t st, BucketView bk = BucketView{},
                                 const uint8_t *layer = nullptr)
 {
-#define HT_VB(KTV, PK)                                                                        \
+#define HT_VB2(KTV, PK, RWV)                                                                  \
     do {                                                                                      \
         int occ = 0;                                                                          \
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(                                        \
-            &occ, k_vote_batch<KTV, uint16_t, PK, MODE>, kThreads,                            \
-            vote_smem<KTV>(G, PK, MODE));                                                     \
-        k_vote_batch<KTV, uint16_t, PK, MODE><<<sms * (occ > 0 ? occ : 1), kThreads,         \
-                                                vote_smem<KTV>(G, PK, MODE), st>>>(           \
+            &occ, k_vote_batch<KTV, uint16_t, PK, MODE, RWV>, kThreads,                       \
+            vote_smem<KTV>(G, PK, MODE, RWV));                                                \
+        k_vote_batch<KTV, uint16_t, PK, MODE, RWV><<<sms * (occ > 0 ? occ : 1), kThreads,    \
+                                                     vote_smem<KTV>(G, PK, MODE, RWV), st>>>( \
             G, x, y, off, order, d_nev, acc, acc_stride, stats, head, masks, bk, layer);      \
         return cudaGetLastError();                                                            \
     } while (0)
+#define HT_VB(KTV, PK) HT_VB2(KTV, PK, 1)
     // the per-hit mode's larger items would drop a tuned width to two CTAs
     // per SM: it keeps three
     const size_t budget = base_mode(MODE) == kModeHit ? kSmemBudget3 : kSmemBudget2;
+    if constexpr (tall_tiles_ok<MODE>()) {
+        // kt = 0 (the default): 64-row tiles of two columns where they fit
+        if (pack && kt == 0 && vote_smem<2>(G, true, MODE, 2) <= kSmemBudget3) HT_VB2(2, true, 2);
+    }
     if constexpr (layer_mode(MODE)) {
         if (!pack) return cudaSuccess;   // no unpacked tiles
         if (kt == 0) kt = vote_smem<4>(G, true, MODE) <= kSmemBudget3 ? 4
@@ -1007,6 +1084,7 @@ cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y
         HT_VB(1, false);
     }
 #undef HT_VB
+#undef HT_VB2
 }
 
 inline cudaError_t allow_smem(const void *const *fns, int nf, int max_smem)
@@ -1027,6 +1105,14 @@ inline cudaError_t allow_smem(const void *const *fns, int nf, int max_smem)
 template <int MODE>
 cudaError_t prepare_vote_kernels_t(int max_smem)
 {
+    if constexpr (tall_tiles_ok<MODE>()) {
+        const void *fns[] = {
+            (const void *)k_vote<2, uint16_t, true, MODE, 2>,
+            (const void *)k_vote<2, int32_t, true, MODE, 2>,
+            (const void *)k_vote_batch<2, uint16_t, true, MODE, 2>};
+        const cudaError_t e = allow_smem(fns, (int)(sizeof fns / sizeof fns[0]), max_smem);
+        if (e != cudaSuccess) return e;
+    }
     if constexpr (layer_mode(MODE)) {
         const void *fns[] = {
             (const void *)k_vote<4, uint16_t, true, MODE>,
