@@ -191,7 +191,7 @@ struct HitCtx {
 // The vote's common case: a (hit, column) item whose second root is proven out
 // of the axis, with b = 1 + rho s > 0 on every row of the tile (so the one
 // root is C / q, the smaller in magnitude) and whose discriminant
-// D = 1 - rho^2 c^2 stays at or above 1/16 for every |rho| <= rt.  With w = d0 + s the circle equation reads
+// D = 1 - rho^2 c^2 stays at or above 1/64 for every |rho| <= rt.  With w = d0 + s the circle equation reads
 // rho w^2 + 2 w + rho c^2 = 0; the root continuous with w = 0 at rho = 0 is the
 // one with |w| < c, w = (sqrt(D) - 1) / rho = -rho c^2 / (1 + sqrt(D)), and it
 // is the same real number as C / q.  Its bin coordinate is
@@ -212,10 +212,11 @@ struct HitCtx {
 //                       eB = kSafe c2d (2 eS/c + 14.3u + |dD| / sqrt(Dmin)).
 // e64 covers the float64 definition's own rounding against the exact root:
 // its C = rho r^2 + 2s (and r^2 against s^2 + c^2) is off by a few 2^-53 of
-// rho R1^2 + 2 R1, divided by |q| >= sqrt(D) >= 1/4, plus a few 2^-53 of |u|.
-// Only items with c > 1 cm and c >= 4e-4 R1 take this form (relative errors
-// far below 1e-3, where first order holds under kSafe), and only while
-// |u| < 2^21 everywhere on the tile, for the floor below.
+// rho R1^2 + 2 R1, divided by |q| >= sqrt(D) >= 1/8, plus a few 2^-53 of |u|.
+// Only items with c >= 4e-4 R1 take this form (the relative error of c is
+// then at most 2e-3, where first order holds under kSafe; c > 0 is proven,
+// the item is not unsure), and only while |u| < 2^21 everywhere on the tile,
+// for the floor below.
 constexpr float kMagic = 12582912.0f;       // 1.5 2^23: rd(x + kMagic) - kMagic = floor(x), |x| < 2^22
 constexpr int kMagicBits = 0x4B400000;      // its bits
 
@@ -225,9 +226,9 @@ constexpr int kMagicBits = 0x4B400000;      // its bits
 // rt (|s| + eS) < 1, with a margin for the float32 rt and s.
 __device__ __forceinline__ bool aform_ok(const DevGeom &G, float s, float c, float R1, float rt)
 {
-    if (!(c > 1.0f) || c < 4e-4f * R1) return false;
+    if (!(c >= 4e-4f * R1)) return false;
     const float t = rt * rt * (c * c) * 1.001f;
-    return (rt * fmaf(4e-7f, R1, fabsf(s)) < 0.99f) && (1.0f - t >= 0.0625f) &&
+    return (rt * fmaf(4e-7f, R1, fabsf(s)) < 0.99f) && (1.0f - t >= 0.015625f) &&
            fmaf(R1 + rt * c * c, G.inv_delta_f, G.off_f + 1.0f) < 2.0e6f;
 }
 
@@ -244,7 +245,7 @@ __device__ __forceinline__ float4 make_aform(const DevGeom &G, float s, float c,
     const float dD = fmaf(t, rc + 5.0f * kEps, kEps);
     const float isD = rsqrt_approx(1.0f - t) * 1.001f;
     const float aA = fabsf(A0);
-    const float e64 = 8e-15f * fmaf(rt * R1, R1, 2.0f * R1) * G.inv_delta_f +
+    const float e64 = 1.6e-14f * fmaf(rt * R1, R1, 2.0f * R1) * G.inv_delta_f +
                       4e-15f * (aA + rt * c2d + G.off_f);
     const float eA = (kSafe * 1.001f) * (fmaf(kEps, fabsf(s), eS) * G.inv_delta_f +
                                          2.0f * kEps * aA) + e64;
@@ -890,8 +891,11 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 
 // mask: kModeEvent one device uint64, kModeHit one per hit, else unused;
 // layer: one uint8 per hit under kModeLayers, else unused.
+// 64-row tiles (RW = 2) take four CTAs per SM: their 32 KB of counters and
+// two-column work list fit four in shared memory, and 64 registers spill no
+// more than 80 do.
 template <int KT, typename OutT, bool PACK, int MODE, int RW = 1>
-__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, RW == 2 ? 4 : (PACK ? 3 : 2))
 k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
        OutT *__restrict__ acc, unsigned long long *__restrict__ stats,
        const unsigned long long *__restrict__ mask, const uint8_t *__restrict__ layer)
@@ -909,7 +913,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
 // bk (optional, ent null for none): per-event hit lists by column group; a
 // tile scans its group's list instead of the whole event.
 template <int KT, typename OutT, bool PACK, int MODE, int RW = 1>
-__global__ void __launch_bounds__(kThreads, PACK ? 3 : 2)
+__global__ void __launch_bounds__(kThreads, RW == 2 ? 4 : (PACK ? 3 : 2))
 k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
              const int *__restrict__ off, const int *__restrict__ order,
              const int *__restrict__ d_nev,
@@ -970,7 +974,7 @@ cudaError_t launch_vote_kt(const DevGeom &G, const float *x, const float *y, int
 }
 
 // The distinct-layer vote's default tile: 64 rows of two columns when it
-// fits three CTAs per SM (plain base mode only).
+// fits in the three-CTA budget (plain base mode only).
 template <int MODE>
 constexpr bool tall_tiles_ok()
 {

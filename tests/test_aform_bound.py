@@ -11,7 +11,8 @@ multiply-adds formed in float64 and rounded once; the approximate rsqrt and
 rcp pushed to both ends of their error bounds) and check, on the geometries
 of every workload and of the extreme-geometry GPU tests, that the float32
 coordinate lies within e of the coordinate the float64 definition gives
-(b = 1 + rho s, q = -(b + sgn(b) sqrt(D)), root C / q, u = root / delta + off).
+(b = 1 + rho s, q = -(b + sgn(b) sqrt(D)), root C / q, u = root / delta + off),
+on tiles of 32 and of 64 rows.
 A bound a twentieth as large fails, so the check has teeth, and dropping the
 b > 0 condition of the A-form (the item's one root is then the other branch)
 is caught too.
@@ -41,8 +42,8 @@ def fma32(a, b, c):
     return F32(np.float64(a) * np.float64(b) + np.float64(c))
 
 
-def items(geom, rr, n, seed):
-    """Random hits x random columns x random 32-row tiles of a geometry."""
+def items(geom, rr, n, seed, TR=32):
+    """Random hits x random columns x random TR-row tiles of a geometry."""
     NR, ND, NP, rmax, dh = geom
     rng = np.random.default_rng(seed)
     r = np.exp(rng.uniform(math.log(rr[0]), math.log(rr[1]), n))
@@ -50,12 +51,13 @@ def items(geom, rr, n, seed):
     x = (r * np.cos(ph)).astype(F32)
     y = (r * np.sin(ph)).astype(F32)
     k = rng.integers(0, NP, n)
-    t0 = rng.integers(0, (NR + 31) // 32, n) * 32
-    i = np.minimum(t0 + rng.integers(0, 32, n), NR - 1)
-    return x, y, k, t0, i
+    t0 = rng.integers(0, (NR + TR - 1) // TR, n) * TR
+    i = np.minimum(t0 + rng.integers(0, TR, n), NR - 1)
+    return x, y, k, t0, i, TR
 
 
-def emulate(geom, x, y, k, t0, i, scale=1.0, need_b_positive=True, rsq_err=0.0, rcp_err=0.0):
+def emulate(geom, x, y, k, t0, i, TR, scale=1.0, need_b_positive=True, rsq_err=0.0,
+            rcp_err=0.0):
     """Float32 A-form coordinate, its bound and the float64 definition's
     coordinate for the items the kernel would put in A-form."""
     NR, ND, NP, rmax, dh = geom
@@ -66,7 +68,7 @@ def emulate(geom, x, y, k, t0, i, scale=1.0, need_b_positive=True, rsq_err=0.0, 
     phi = (2 * np.arange(NP) + 1 - NP) * (math.pi / NP)
     sn64, cs64 = np.sin(phi), np.cos(phi)
     sn32, cs32 = sn64.astype(F32), cs64.astype(F32)
-    ilast = np.minimum(t0 + 31, NR - 1)
+    ilast = np.minimum(t0 + TR - 1, NR - 1)
     rt = np.maximum(np.abs(rho64[t0]), np.abs(rho64[ilast])).astype(F32) * F32(1.0001)
     s = fma32(x, sn32[k], -(y * cs32[k]))
     c = fma32(x, cs32[k], y * sn32[k])
@@ -78,7 +80,7 @@ def emulate(geom, x, y, k, t0, i, scale=1.0, need_b_positive=True, rsq_err=0.0, 
     cB = np.sqrt(np.maximum(1.0 / rt ** 2 - dext * dext, 0.0)) * (1 - 1e-6) - 0.05
     plain = ~((np.abs(s) + eS >= sB) & (c + eS >= cB)) & (c > F32(12 * U) * R1)
     t = rt * rt * (c * c) * F32(1.001)
-    ok = plain & (c > 1) & (c >= F32(4e-4) * R1) & (1 - t >= 0.0625)
+    ok = plain & (c >= F32(4e-4) * R1) & (1 - t >= 0.015625)
     ok &= (R1 + rt * c * c) * invd + off_f + 1 < 2e6
     if need_b_positive:
         ok &= rt * (F32(4e-7) * R1 + np.abs(s)) < 0.99
@@ -93,7 +95,7 @@ def emulate(geom, x, y, k, t0, i, scale=1.0, need_b_positive=True, rsq_err=0.0, 
     dD = fma32(t, rc + F32(5 * U), F32(U))
     isD = F32(1.0 / np.sqrt(1.0 - t)) * F32(1.001)
     aA = np.abs(A0)
-    e64 = 8e-15 * (rt * R1 * R1 + 2 * R1) * invd + 4e-15 * (aA + rt * c2d + off_f)
+    e64 = 1.6e-14 * (rt * R1 * R1 + 2 * R1) * invd + 4e-15 * (aA + rt * c2d + off_f)
     eA = F32(4.004 * ((U * np.abs(s) + eS) * invd + 2 * U * aA) + e64)
     eB = F32(4.004 * c2d * (rc + 14.3 * U + dD * isD))
     # the lane's row (aform_bin)
@@ -115,15 +117,18 @@ def emulate(geom, x, y, k, t0, i, scale=1.0, need_b_positive=True, rsq_err=0.0, 
     return np.float64(u32), np.float64(e), u64
 
 
+@pytest.mark.parametrize("TR", [32, 64])
 @pytest.mark.parametrize("name", sorted(GEOMS))
-def test_float32_coordinate_within_the_bound(name):
+def test_float32_coordinate_within_the_bound(name, TR):
+    """Tiles of 32 rows (the masked and per-hit votes) and 64 rows (the
+    distinct-layer vote)."""
     geom, rr = GEOMS[name]
-    x, y, k, t0, i = items(geom, rr, 60000, seed=zlib.crc32(name.encode()) & 0xffff)
+    it = items(geom, rr, 60000, seed=zlib.crc32(name.encode()) & 0xffff, TR=TR)
     worst = 0.0
     n = 0
     for rsq in (-2 ** -22.9, 2 ** -22.9):
         for rcp in (-2 ** -23.0, 2 ** -23.0):
-            u32, e, u64 = emulate(geom, x, y, k, t0, i, rsq_err=rsq, rcp_err=rcp)
+            u32, e, u64 = emulate(geom, *it, rsq_err=rsq, rcp_err=rcp)
             n = u32.size
             assert np.all(np.isfinite(u32)) and np.all(e > 0)
             worst = max(worst, float(np.max(np.abs(u32 - u64) / e)))
@@ -134,8 +139,8 @@ def test_float32_coordinate_within_the_bound(name):
 def test_bound_has_teeth():
     """A twentieth of the bound is exceeded on the 10k-hit geometry."""
     geom, rr = GEOMS["event100_256"]
-    x, y, k, t0, i = items(geom, rr, 60000, seed=7)
-    u32, e, u64 = emulate(geom, x, y, k, t0, i, scale=0.05, rsq_err=2 ** -22.9)
+    it = items(geom, rr, 60000, seed=7)
+    u32, e, u64 = emulate(geom, *it, scale=0.05, rsq_err=2 ** -22.9)
     assert np.any(np.abs(u32 - u64) > e)
 
 
@@ -143,8 +148,8 @@ def test_b_positive_condition_is_needed():
     """Without b > 0 on the tile, tight curls put items in A-form whose one
     root is the other branch: the coordinates then differ by whole bins."""
     geom, rr = GEOMS["tight_curls"]
-    x, y, k, t0, i = items(geom, rr, 60000, seed=11)
-    u32, e, u64 = emulate(geom, x, y, k, t0, i, need_b_positive=False)
+    it = items(geom, rr, 60000, seed=11)
+    u32, e, u64 = emulate(geom, *it, need_b_positive=False)
     assert np.max(np.abs(u32 - u64)) > 1.0
-    u32, e, u64 = emulate(geom, x, y, k, t0, i)
+    u32, e, u64 = emulate(geom, *it)
     assert np.max(np.abs(u32 - u64) / e) <= 1.0
