@@ -612,10 +612,11 @@ __device__ __forceinline__ void confirm_one(const DevGeom &G, const ConfirmDev &
 // Confirmation of every kept candidate of a batch.  The candidates are
 // ordered by (event, column group of kGroupCols columns) in order[] (flattened
 // indices; cpre is the exclusive prefix of the kept counts), so that the
-// warps of a CTA work on nearby columns of one event; a CTA takes chunks of
-// kCfChunk consecutive entries, one candidate per warp at a time.  I: the
-// batch's hit index (k_hitindex.cu).
-constexpr int kCfChunk = 32;
+// consecutive candidates are nearby columns of one event; each warp takes
+// chunks of kCfChunk consecutive entries from a device counter (*head, zero
+// at launch) and confirms them one after another.  I: the batch's hit index
+// (k_hitindex.cu).
+constexpr int kCfChunk = 8;
 
 __global__ void __launch_bounds__(kCfThreads, 5)
 k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
@@ -623,7 +624,6 @@ k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
           const int *__restrict__ order, int *__restrict__ score, int *__restrict__ inl,
           int *__restrict__ head)
 {
-    __shared__ int s_chunk;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int n_ev = *d_nev;
     const int total = cpre[n_ev];
@@ -631,14 +631,15 @@ k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
     if ((double)tol_hi < P.tol) tol_hi = nextafterf(tol_hi, 3.0e38f);
     float tol_lo = (float)P.tol;   // and down
     if ((double)tol_lo > P.tol) tol_lo = nextafterf(tol_lo, 0.0f);
+    // each warp claims its own chunks (its state in g_cfw is private and it
+    // synchronises only itself), so a warp never waits for its CTA's others
     for (;;) {
-        if (threadIdx.x == 0) s_chunk = atomicAdd(head, 1);
-        __syncthreads();
-        const int t0 = s_chunk * kCfChunk;
-        __syncthreads();   // every thread has read s_chunk
+        int c = 0;
+        if (lane == 0) c = atomicAdd(head, 1);
+        const int t0 = __shfl_sync(0xffffffffu, c, 0) * kCfChunk;
         if (t0 >= total) break;
         const int t1 = min(t0 + kCfChunk, total);
-        for (int t = t0 + warp; t < t1; t += kCfWarps) {
+        for (int t = t0; t < t1; ++t) {
             const int f = __ldg(order + t);
             const int e = event_of(cpre, n_ev, f);
             const size_t slot = (size_t)e * cap + (f - cpre[e]);
