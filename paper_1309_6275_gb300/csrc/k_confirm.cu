@@ -180,7 +180,7 @@ __device__ __forceinline__ bool seed_frame(float x1, float y1, float x2, float y
 }
 
 constexpr int kCfThreads = 128, kCfWarps = kCfThreads / 32;
-constexpr int kCfCap = 512;        // pool hits held per pass (more: further passes)
+constexpr int kCfCap = 384;        // pool hits held per pass (more: further passes)
 constexpr int kCfBlk = 256;        // 32-hit blocks of a scan whose pool counts are kept
 
 struct CfWarp {
@@ -618,7 +618,7 @@ __device__ __forceinline__ void confirm_one(const DevGeom &G, const ConfirmDev &
 // (k_hitindex.cu).
 constexpr int kCfChunk = 8;
 
-__global__ void __launch_bounds__(kCfThreads, 5)
+__global__ void __launch_bounds__(kCfThreads, 6)
 k_confirm(DevGeom G, ConfirmDev P, HitIndex I, const int *__restrict__ d_nev,
           const ht_peak *__restrict__ peaks, int cap, const int *__restrict__ cpre,
           const int *__restrict__ order, int *__restrict__ score, int *__restrict__ inl,
