@@ -593,13 +593,11 @@ def vertex_leg(args):
 
 
 # DRAM bytes (read + write) per event of the dominant kernel, from one ncu
-# capture, valid only while the kernel sources hash to the recorded value.
-# DRAM bytes (read + write) per event of the dominant kernel, from one ncu
 # capture of a smaller case (8 stream events in one launch: the traffic is
-# the accumulator write-back plus the hits, in proportion to the events);
-# reported only while the kernel's sources hash to the same value.
-PROFILED_TRAFFIC = {"k_vote_batch": {"sha": "a74188a8e68d461a",
-                                     "bytes_per_event": (17999104 + 222497792) / 8}}
+# the accumulator write-back plus the hits and hit lists, in proportion to
+# the events); reported only while the kernel's sources hash to the same value.
+PROFILED_TRAFFIC = {"k_vote_batch": {"sha": "3290e8835294efed",
+                                     "bytes_per_event": (78121216 + 293925632) / 8}}
 KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_vote_layers.cu",
                   "paper_1309_6275_gb300/csrc/tiles.cuh",
                   "paper_1309_6275_gb300/csrc/ht_internal.cuh",

@@ -984,7 +984,9 @@ constexpr bool tall_tiles_ok()
 // Tile shape: packed 16-bit counters with three CTAs per SM when the output
 // is uint16, n_d0 even and n <= 32767; otherwise 32-bit counters, two CTAs
 // per SM.  KT is the widest tile that fits.  The distinct-layer vote
-// (kModeLayers; n_d0 even) always packs, into either output type.
+// (kModeLayers; n_d0 even) always packs, into either output type, on 64-row
+// tiles of two columns (four CTAs per SM) where they fit the three-CTA
+// budget, else on 32-row tiles.
 template <int MODE>
 cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int n, void *acc,
                           unsigned long long *stats, const unsigned long long *mask,
@@ -1036,7 +1038,9 @@ cudaError_t launch_vote_t(const DevGeom &G, const float *x, const float *y, int 
 // hit list with buckets, else the event) with 16-bit packed counters;
 // otherwise it takes their other tiles with 32-bit counters.  The
 // distinct-layer vote takes every tile in its packed launch (layer: the
-// batch's layer array, indexed like x).  *head must be zero.
+// batch's layer array, indexed like x), by default on 64-row tiles of two
+// columns (an explicit kt selects 32-row tiles of that width).  *head must
+// be zero.
 template <int MODE>
 cudaError_t launch_vote_batch_t(const DevGeom &G, const float *x, const float *y, const int *off,
                                 const int *order, const int *d_nev, uint16_t *acc,
