@@ -682,7 +682,9 @@ ht_status ht_batch_stage_ms(const ht_batch *b, float *ms);
 /* Autotune the tile widths (phi0 columns per tile of the packed and unpacked
  * vote, and of the association) by timing whole batches on the given sample
  * (arguments as ht_batch_run).  *choice = kt_pack | kt_unpacked << 8 |
- * kt_assoc << 16.  Synchronises the stream.  Errors: as ht_batch_run. */
+ * kt_assoc << 16.  The widths apply to ht_batch_run and the masked runs; the
+ * track path's distinct-layer vote keeps its own default tile.  Synchronises
+ * the stream.  Errors: as ht_batch_run. */
 ht_status ht_batch_autotune(ht_batch *b, const float *x, const float *y, const float *z,
                             const int32_t *h_off, int32_t n_events, ht_peak *peaks,
                             int32_t *counts, int32_t *assign, ht_zres *zres, int32_t *choice,

@@ -265,10 +265,11 @@ cudaError_t enqueue(ht_batch *b, const float *x, const float *y, const float *z,
     };
     const bool tracks = R.layer != nullptr;
     if (tracks) {
-        // the distinct-layer vote packs every tile: one launch
+        // the distinct-layer vote packs every tile: one launch, always with its
+        // default tile (the widths ht_batch_autotune tunes are the plain path's)
         e = ht::launch_vote_batch_layers(G, x, y, R.layer, off, order_all_of(meta, me), meta + 2,
-                                         b->acc, b->cells, st64, b->heads + 1, b->kt_pack,
-                                         b->sms, R.hit_masks, st, &b->bk);
+                                         b->acc, b->cells, st64, b->heads + 1, 0, b->sms,
+                                         R.hit_masks, st, &b->bk);
     } else {
         e = vote(order_big_of(meta, me), meta + 0, b->heads + 0, false, b->kt_big);
         if (e == cudaSuccess) e = vote(order_all_of(meta, me), meta + 2, b->heads + 1, true, b->kt_pack);
