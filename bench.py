@@ -596,7 +596,7 @@ def vertex_leg(args):
 # capture of a smaller case (8 stream events in one launch: the traffic is
 # the accumulator write-back plus the hits and hit lists, in proportion to
 # the events); reported only while the kernel's sources hash to the same value.
-PROFILED_TRAFFIC = {"k_vote_batch": {"sha": "3290e8835294efed",
+PROFILED_TRAFFIC = {"k_vote_batch": {"sha": "c8576bebcabab381",
                                      "bytes_per_event": (78121216 + 293925632) / 8}}
 KERNEL_SOURCES = ["paper_1309_6275_gb300/csrc/k_vote_layers.cu",
                   "paper_1309_6275_gb300/csrc/tiles.cuh",

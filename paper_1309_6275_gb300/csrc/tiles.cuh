@@ -891,11 +891,12 @@ __device__ __forceinline__ void vote_tile(const DevGeom &G, const float *__restr
 
 // mask: kModeEvent one device uint64, kModeHit one per hit, else unused;
 // layer: one uint8 per hit under kModeLayers, else unused.
-// 64-row tiles (RW = 2) take four CTAs per SM: their 32 KB of counters and
-// two-column work list fit four in shared memory, and 64 registers spill no
-// more than 80 do.
+// The distinct-layer vote's tiles of at most two columns (64-row tiles, and
+// the 32-row tiles of the pile-up geometry and of the per-hit mode) take four
+// CTAs per SM: their counters and two-column work list fit four in shared
+// memory, and 64 registers spill about as little as 80 do.
 template <int KT, typename OutT, bool PACK, int MODE, int RW = 1>
-__global__ void __launch_bounds__(kThreads, RW == 2 ? 4 : (PACK ? 3 : 2))
+__global__ void __launch_bounds__(kThreads, (RW == 2 || (layer_mode(MODE) && KT <= 2)) ? 4 : (PACK ? 3 : 2))
 k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int n,
        OutT *__restrict__ acc, unsigned long long *__restrict__ stats,
        const unsigned long long *__restrict__ mask, const uint8_t *__restrict__ layer)
@@ -913,7 +914,7 @@ k_vote(DevGeom G, const float *__restrict__ x, const float *__restrict__ y, int 
 // bk (optional, ent null for none): per-event hit lists by column group; a
 // tile scans its group's list instead of the whole event.
 template <int KT, typename OutT, bool PACK, int MODE, int RW = 1>
-__global__ void __launch_bounds__(kThreads, RW == 2 ? 4 : (PACK ? 3 : 2))
+__global__ void __launch_bounds__(kThreads, (RW == 2 || (layer_mode(MODE) && KT <= 2)) ? 4 : (PACK ? 3 : 2))
 k_vote_batch(DevGeom G, const float *__restrict__ x, const float *__restrict__ y,
              const int *__restrict__ off, const int *__restrict__ order,
              const int *__restrict__ d_nev,
