@@ -46,7 +46,8 @@ def test_dense_event_full_size():
 
 
 def test_wide_pool_takes_several_passes():
-    """pool = 40 bins: most candidates' pools exceed one pass of 256 hits."""
+    """pool = 40 bins: most candidates' pools exceed one pass (384 hits), so
+    the later passes, their block skipping and their float64 contenders run."""
     g = synth.geometry_of("event100_256")
     g["threshold"] = 10
     ev = synth.make_event(synth.CONFIGS["event100_256"]["gen"], 1)
