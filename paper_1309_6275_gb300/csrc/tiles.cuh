@@ -215,8 +215,9 @@ struct HitCtx {
 // rho R1^2 + 2 R1, divided by |q| >= sqrt(D) >= 1/8, plus a few 2^-53 of |u|.
 // Only items with c >= 4e-4 R1 take this form (the relative error of c is
 // then at most 2e-3, where first order holds under kSafe; c > 0 is proven,
-// the item is not unsure), and only while |u| < 2^21 everywhere on the tile,
-// for the floor below.
+// the item is not unsure), only hits with R1 >= 1e-20 cm (nearer the origin
+// c and c^2 underflow and the bound's float32 terms would be 0 x inf), and
+// only while |u| < 2^21 everywhere on the tile, for the floor below.
 constexpr float kMagic = 12582912.0f;       // 1.5 2^23: rd(x + kMagic) - kMagic = floor(x), |x| < 2^22
 constexpr int kMagicBits = 0x4B400000;      // its bits
 
@@ -226,7 +227,7 @@ constexpr int kMagicBits = 0x4B400000;      // its bits
 // rt (|s| + eS) < 1, with a margin for the float32 rt and s.
 __device__ __forceinline__ bool aform_ok(const DevGeom &G, float s, float c, float R1, float rt)
 {
-    if (!(c >= 4e-4f * R1)) return false;
+    if (!(c >= 4e-4f * R1) || !(R1 >= 1e-20f)) return false;
     const float t = rt * rt * (c * c) * 1.001f;
     return (rt * fmaf(4e-7f, R1, fabsf(s)) < 0.99f) && (1.0f - t >= 0.015625f) &&
            fmaf(R1 + rt * c * c, G.inv_delta_f, G.off_f + 1.0f) < 2.0e6f;

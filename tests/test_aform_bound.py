@@ -80,7 +80,7 @@ def emulate(geom, x, y, k, t0, i, TR, scale=1.0, need_b_positive=True, rsq_err=0
     cB = np.sqrt(np.maximum(1.0 / rt ** 2 - dext * dext, 0.0)) * (1 - 1e-6) - 0.05
     plain = ~((np.abs(s) + eS >= sB) & (c + eS >= cB)) & (c > F32(12 * U) * R1)
     t = rt * rt * (c * c) * F32(1.001)
-    ok = plain & (c >= F32(4e-4) * R1) & (1 - t >= 0.015625)
+    ok = plain & (c >= F32(4e-4) * R1) & (R1 >= F32(1e-20)) & (1 - t >= 0.015625)
     ok &= (R1 + rt * c * c) * invd + off_f + 1 < 2e6
     if need_b_positive:
         ok &= rt * (F32(4e-7) * R1 + np.abs(s)) < 0.99
