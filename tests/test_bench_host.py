@@ -1,7 +1,8 @@
 """bench.py's host logic, without a GPU: the clock record parsing and its
 throttle reasons, the issue-limited ALU peak, the LPT split of a job's
-events over ranks, the launch count per batch, and the reference arm's JSON
-line (the oracle's track path on a tiny workload)."""
+events over ranks, the launch count per batch, the reference arm's JSON
+line (the oracle's track path on a tiny workload) and the CPU baseline's
+bounded, hit-scaled sample."""
 import json
 import os
 import subprocess
@@ -70,3 +71,29 @@ def test_reference_arm_prints_one_json_line_of_the_contract():
     assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["value"] == d["value"]
+
+
+def test_cpu_baseline_stops_after_its_budget_and_scales_by_hits(monkeypatch):
+    """The oracle runs events in order until the budget has passed; the value
+    is the sample's hits per second over the workload's mean hits per event."""
+    import time as _time
+    import oracle
+    Ev = namedtuple("Ev", "n_hits x y z layer")
+    events = [Ev(n, None, None, None, None) for n in (1000, 3000, 2000, 6000)]
+    clock = {"t": 0.0}
+    ran = []
+
+    def fake_run(g, x, y, z, layer, cp=None, cap=None, threads=1):
+        ran.append(g)
+        clock["t"] += 1.0 if len(ran) < 3 else 4.0   # seconds per event
+
+    monkeypatch.setattr(oracle, "run_event_tracks", fake_run)
+    monkeypatch.setattr(bench.synth, "track_geometry", lambda name, n: n)
+    monkeypatch.setattr(bench.time, "perf_counter", lambda: clock["t"])
+    r = bench.cpu_baseline("stream2000_256", events, budget_s=5.0)
+    # 1 s + 1 s + 4 s: the third event crosses the budget, the fourth is not run
+    assert ran == [1000, 3000, 2000]
+    mean = (1000 + 3000 + 2000 + 6000) / 4
+    assert abs(r["value"] - (6000 / 6.0) / mean) < 1e-12
+    assert abs(r["sample_events_per_s"] - 3 / 6.0) < 1e-12
+    assert r["kind"] == "oracle" and "first 3 events" in r["sample"]
